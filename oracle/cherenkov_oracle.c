@@ -1,0 +1,722 @@
+/*
+ * FP64 CPU oracle for Cherenkov photon generation and propagation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no source,
+ * header, table or helper with the CUDA path; the two are independent
+ * implementations of the same method and are compared photon by photon.
+ *
+ * Everything here is plain, unblocked FP64 and follows the thesis
+ * (D. Baack, "Optical Photon Emission in Extended Airshowers", 2023):
+ *
+ *   photon yield          Sec. 2.2.1, Eq. 2.2-2.5 (Frank-Tamm, threshold,
+ *                         location-dependent Cherenkov angle)
+ *   random numbers        Sec. 3.1 (counter-based Philox, Salmon et al. 2011)
+ *   atmosphere            Sec. 3.3.1-3.3.2 (homogeneous, planar layered),
+ *                         Sec. 6.3.1 (linear test profile)
+ *   straight line         Sec. 3.4.1, Eq. 3.1-3.3
+ *   Snell vector stepper  Sec. 3.4.2, Eq. 3.6-3.15
+ *   refraction invariant  Sec. 3.4.3, Eq. 3.17-3.18 (n sin(theta) = const),
+ *                         linear profile Eq. 3.19-3.23 and Appendix A.1
+ *   photon generation     Sec. 4.2 (cone vector, Euler-Rodrigues 180-degree
+ *                         rotation about the bisector, translation along the
+ *                         track) and Sec. 4.2.1 (sub-stepping)
+ *   absorption            Sec. 2.3.2 and Sec. 4.3.1 (survival test r < p)
+ *   correction target     Sec. 4.4.1 (the exact path that the correction
+ *                         tables approximate)
+ *
+ * Where the thesis is silent the oracle takes the documented readings
+ * (layer parameters, transmission constants, stochastic rounding of the
+ * photon count, sub-step midpoint for the angle, edge bands).
+ *
+ * The refraction integrals are evaluated per photon by adaptive
+ * Gauss-Legendre quadrature split at every layer boundary; a second,
+ * independent path evaluates the same integrals in closed form per
+ * exponential layer, and a third (the thesis's own Snell stepper) must
+ * converge to both.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_C_LIGHT 299792458.0           /* m/s */
+#define ORC_ALPHA   7.2973525693e-3       /* fine-structure constant (CODATA 2018) */
+#define ORC_PI      3.14159265358979323846
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).                 */
+/* ------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {               /* Weyl key schedule between rounds */
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* 24-bit uniform in [0, 1): exact in both FP32 and FP64. */
+static double orc_uniform(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+
+/* ------------------------------------------------------------------ */
+/* Atmosphere (Sec. 3.3).                                             */
+/* ------------------------------------------------------------------ */
+enum { ORC_ATM_LAYERED = 0, ORC_ATM_LINEAR = 1, ORC_ATM_HOMOGENEOUS = 2 };
+
+typedef struct {
+    int kind;
+    int n_layers;          /* layered kind: number of layers (<= 8)               */
+    int last_linear;       /* layered kind: top layer has T linear in h            */
+    int pad;
+    double layer_h[8];     /* layer bottoms [m], ascending; layer_h[0] is the ground */
+    double a[8], b[8], c[8];  /* T(h) = a + b exp(-h/c) [g/cm^2], c in cm          */
+    double h_top;          /* top of the atmosphere [m]; vacuum above              */
+    double kappa;          /* n - 1 = kappa * rho(h) / rho(0)                       */
+    double lin_h0, lin_h1; /* linear kind: n = n0 at h0 falling to n1 at h1        */
+    double lin_n0, lin_n1;
+    double hom_delta;      /* homogeneous kind: n - 1                              */
+} orc_atm;
+
+static int orc_layer_of(const orc_atm* a, double h)
+{
+    int i = 0;
+    while (i + 1 < a->n_layers && h >= a->layer_h[i + 1]) ++i;   /* half-open [h_i, h_i+1) */
+    return i;
+}
+
+/* Vertical column depth above h [g/cm^2]. */
+double orc_atm_T(const orc_atm* a, double h)
+{
+    if (a->kind != ORC_ATM_LAYERED) return 0.0;
+    if (h >= a->h_top) return 0.0;
+    int i = orc_layer_of(a, h);
+    double hc = h * 100.0;
+    if (a->last_linear && i == a->n_layers - 1) return a->a[i] - a->b[i] * hc / a->c[i];
+    return a->a[i] + a->b[i] * exp(-hc / a->c[i]);
+}
+
+/* Density rho = -dT/dh [g/cm^3]. */
+double orc_atm_rho(const orc_atm* a, double h)
+{
+    if (a->kind != ORC_ATM_LAYERED) return 0.0;
+    if (h >= a->h_top) return 0.0;
+    int i = orc_layer_of(a, h);
+    if (a->last_linear && i == a->n_layers - 1) return a->b[i] / a->c[i];
+    return a->b[i] / a->c[i] * exp(-h * 100.0 / a->c[i]);
+}
+
+/* Layer i's own column law evaluated at h (no layer lookup). */
+static double orc_T_layer(const orc_atm* a, int i, double h)
+{
+    double hc = h * 100.0;
+    if (a->last_linear && i == a->n_layers - 1) return a->a[i] - a->b[i] * hc / a->c[i];
+    return a->a[i] + a->b[i] * exp(-hc / a->c[i]);
+}
+
+/* Vertical column between lo < hi, i.e. the integral of rho: the sum over
+ * layers of each layer's column law differenced at its clipped ends (the
+ * piecewise fit is continuous only to about 1e-3 g/cm^2 at the boundaries). */
+double orc_column(const orc_atm* a, double lo, double hi)
+{
+    if (a->kind != ORC_ATM_LAYERED) return 0.0;
+    double X = 0.0;
+    for (int i = 0; i < a->n_layers; ++i) {
+        double l0 = (i == 0) ? -1e30 : a->layer_h[i];
+        double l1 = (i + 1 < a->n_layers) ? a->layer_h[i + 1] : a->h_top;
+        double p = fmax(lo, l0), q = fmin(hi, l1);
+        if (q > p) X += orc_T_layer(a, i, p) - orc_T_layer(a, i, q);
+    }
+    return X;
+}
+
+static double orc_rho0(const orc_atm* a) { return a->b[0] / a->c[0]; }   /* rho at h = 0 */
+
+/* Reduced refractive index n(h) - 1. */
+double orc_atm_delta(const orc_atm* a, double h)
+{
+    switch (a->kind) {
+    case ORC_ATM_LAYERED:
+        return a->kappa * orc_atm_rho(a, h) / orc_rho0(a);
+    case ORC_ATM_LINEAR: {
+        if (h >= a->lin_h1) return a->lin_n1 - 1.0;
+        double f = (h - a->lin_h0) / (a->lin_h1 - a->lin_h0);
+        return (a->lin_n0 - 1.0) - f * (a->lin_n0 - a->lin_n1);
+    }
+    default:
+        return a->hom_delta;
+    }
+}
+
+static double orc_n(const orc_atm* a, double h) { return 1.0 + orc_atm_delta(a, h); }
+
+/* Heights in (lo, hi) where n(h) is not smooth; returns their count. */
+static int orc_breakpoints(const orc_atm* a, double lo, double hi, double* bp)
+{
+    int m = 0;
+    if (a->kind == ORC_ATM_LAYERED) {
+        for (int i = 1; i < a->n_layers; ++i)
+            if (a->layer_h[i] > lo && a->layer_h[i] < hi) bp[m++] = a->layer_h[i];
+        if (a->h_top > lo && a->h_top < hi) bp[m++] = a->h_top;
+    } else if (a->kind == ORC_ATM_LINEAR) {
+        if (a->lin_h1 > lo && a->lin_h1 < hi) bp[m++] = a->lin_h1;
+    }
+    return m;
+}
+
+/* ------------------------------------------------------------------ */
+/* Adaptive Gauss-Legendre quadrature.                                */
+/* ------------------------------------------------------------------ */
+#define ORC_GL_N 10
+static double g_gl_x[ORC_GL_N], g_gl_w[ORC_GL_N];
+static int g_gl_ready = 0;
+
+/* Nodes and weights of the n-point Gauss-Legendre rule by Newton iteration
+ * on the Legendre polynomial P_n (three-term recurrence). */
+void orc_gauss_legendre(int n, double* x, double* w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = cos(ORC_PI * (i + 0.75) / (n + 0.5));   /* initial guess for root i */
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p_prev = 1.0, p = z;                     /* P_0, P_1 */
+            for (int k = 2; k <= n; ++k) {
+                double p_next = ((2.0 * k - 1.0) * z * p - (k - 1.0) * p_prev) / k;
+                p_prev = p; p = p_next;
+            }
+            dp = n * (z * p - p_prev) / (z * z - 1.0);      /* P_n'(z) */
+            double dz = p / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+static void orc_gl_init(void)
+{
+    if (!g_gl_ready) {
+        orc_gauss_legendre(ORC_GL_N, g_gl_x, g_gl_w);
+        g_gl_ready = 1;
+    }
+}
+
+/* Fill the rule once at load time so concurrent callers only read it. */
+__attribute__((constructor)) static void orc_load(void) { orc_gl_init(); }
+
+typedef double (*orc_fn)(double h, const void* ctx);
+
+static double orc_gl(orc_fn f, const void* ctx, double lo, double hi)
+{
+    double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo), s = 0.0;
+    for (int i = 0; i < ORC_GL_N; ++i) s += g_gl_w[i] * f(mid + half * g_gl_x[i], ctx);
+    return s * half;
+}
+
+static double orc_adapt(orc_fn f, const void* ctx, double lo, double hi, double whole,
+                        double rtol, int depth)
+{
+    double mid = 0.5 * (lo + hi);
+    double left = orc_gl(f, ctx, lo, mid), right = orc_gl(f, ctx, mid, hi);
+    double both = left + right;
+    if (depth >= 40 || fabs(both - whole) <= rtol * fabs(both) + 1e-300) return both;
+    return orc_adapt(f, ctx, lo, mid, left, rtol, depth + 1) +
+           orc_adapt(f, ctx, mid, hi, right, rtol, depth + 1);
+}
+
+/* Integral of f over [lo, hi], split at the atmosphere's breakpoints. */
+static double orc_integrate(const orc_atm* a, orc_fn f, const void* ctx, double lo, double hi,
+                            double rtol)
+{
+    orc_gl_init();
+    double bp[16];
+    int m = orc_breakpoints(a, lo, hi, bp);
+    double edges[18];
+    edges[0] = lo;
+    for (int i = 0; i < m; ++i) edges[i + 1] = bp[i];
+    edges[m + 1] = hi;
+    double total = 0.0;
+    for (int i = 0; i <= m; ++i) {
+        double piece_lo = edges[i], piece_hi = edges[i + 1];
+        if (piece_hi <= piece_lo) continue;
+        /* Start from a few equal sub-intervals so a single rule never spans
+         * many scale heights. */
+        int nsub = 1 + (int)((piece_hi - piece_lo) / 2000.0);
+        double step = (piece_hi - piece_lo) / nsub;
+        for (int j = 0; j < nsub; ++j) {
+            double s0 = piece_lo + j * step, s1 = (j + 1 == nsub) ? piece_hi : s0 + step;
+            total += orc_adapt(f, ctx, s0, s1, orc_gl(f, ctx, s0, s1), rtol, 0);
+        }
+    }
+    return total;
+}
+
+/* ------------------------------------------------------------------ */
+/* Exact planar refraction integrals (Eq. 3.17-3.18).                 */
+/*                                                                    */
+/* With the invariant n(h) sin(theta(h)) = s = n(h_e) sin(theta0), a  */
+/* photon that descends dh moves horizontally by s / sqrt(n^2 - s^2)  */
+/* dh and spends n^2 / (c sqrt(n^2 - s^2)) dh of time (path length    */
+/* n / sqrt(n^2 - s^2) dh at speed c / n).                            */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const orc_atm* atm;
+    double s;      /* Snell invariant */
+    double H_A;    /* aerosol scale height [m] */
+} orc_rctx;
+
+static double orc_q(const orc_rctx* r, double h, double* n_out)
+{
+    double n = orc_n(r->atm, h);
+    *n_out = n;
+    return sqrt(n * n - r->s * r->s);
+}
+static double orc_fR(double h, const void* p)
+{
+    const orc_rctx* r = (const orc_rctx*)p; double n; double q = orc_q(r, h, &n);
+    return r->s / q;
+}
+static double orc_fT(double h, const void* p)
+{
+    const orc_rctx* r = (const orc_rctx*)p; double n; double q = orc_q(r, h, &n);
+    return n * n / q / ORC_C_LIGHT;
+}
+static double orc_fX(double h, const void* p)
+{
+    const orc_rctx* r = (const orc_rctx*)p; double n; double q = orc_q(r, h, &n);
+    return 100.0 * orc_atm_rho(r->atm, h) * n / q;     /* dh in cm -> g/cm^2 */
+}
+static double orc_fA(double h, const void* p)
+{
+    const orc_rctx* r = (const orc_rctx*)p; double n; double q = orc_q(r, h, &n);
+    return exp(-h / r->H_A) * n / q;
+}
+
+/* out = {R [m], t_path [s], X_slant [g/cm^2], A_slant [m]} for a photon
+ * emitted at h_e with zenith theta0 that descends to h_obs. */
+void orc_refract_quad(const orc_atm* a, double h_obs, double h_e, double theta0, double H_A,
+                      double rtol, double out[4])
+{
+    orc_rctx r = { a, orc_n(a, h_e) * sin(theta0), H_A };
+    out[0] = orc_integrate(a, orc_fR, &r, h_obs, h_e, rtol);
+    out[1] = orc_integrate(a, orc_fT, &r, h_obs, h_e, rtol);
+    out[2] = orc_integrate(a, orc_fX, &r, h_obs, h_e, rtol);
+    out[3] = orc_integrate(a, orc_fA, &r, h_obs, h_e, rtol);
+}
+
+/* Straight-line propagation (Sec. 3.4.1, Eq. 3.3): same outputs with the
+ * atmosphere neglected for the geometry and the time (vacuum light speed);
+ * the column integrals follow the straight path. */
+void orc_straight(const orc_atm* a, double h_obs, double h_e, double theta0, double H_A,
+                  double out[4])
+{
+    double cz = cos(theta0), dz = h_e - h_obs;
+    out[0] = dz * tan(theta0);
+    out[1] = dz / cz / ORC_C_LIGHT;
+    out[2] = orc_column(a, h_obs, h_e) / cz;
+    out[3] = H_A * (exp(-h_obs / H_A) - exp(-h_e / H_A)) / cz;
+}
+
+/* ------------------------------------------------------------------ */
+/* Second, independent path: the same integrals in closed form.       */
+/*                                                                    */
+/* Exponential layer n = 1 + D exp(-h/H): dh = -H dn / (n - 1), and   */
+/*   int dn / ((n-1) q)  = -(1/k) ln[(n - s^2 + k q) / (n - 1)],       */
+/*   int n dn / q        = q,                                          */
+/*   int dn / q          = ln(n + q),                                  */
+/* with q = sqrt(n^2 - s^2), k = sqrt(1 - s^2).  In such a layer       */
+/* rho = (n - 1) rho0 / kappa, so the column integral is H (rho0 /     */
+/* kappa) [q].  Constant-n layers are straight lines.  The linear kind */
+/* (dn/dh = -c1) integrates to arcosh forms (Eq. 3.20-3.23, App. A.1). */
+/* ------------------------------------------------------------------ */
+static double orc_F(double n, double s)
+{
+    double k = sqrt(1.0 - s * s), q = sqrt(n * n - s * s);
+    return -log((n - s * s + k * q) / (n - 1.0)) / k;
+}
+
+/* out = {R, t_path, X_slant}; aerosol has no closed form in general. */
+int orc_refract_closed(const orc_atm* a, double h_obs, double h_e, double theta0, double out[3])
+{
+    double s = orc_n(a, h_e) * sin(theta0);
+    double R = 0.0, T = 0.0, X = 0.0;
+    if (a->kind == ORC_ATM_HOMOGENEOUS) {
+        double n = 1.0 + a->hom_delta, q = sqrt(n * n - s * s), dz = h_e - h_obs;
+        out[0] = dz * s / q; out[1] = dz * n * n / q / ORC_C_LIGHT; out[2] = 0.0;
+        return 0;
+    }
+    if (a->kind == ORC_ATM_LINEAR) {
+        if (h_e > a->lin_h1) return -1;
+        double c1 = (a->lin_n0 - a->lin_n1) / (a->lin_h1 - a->lin_h0);
+        double n_lo = orc_n(a, h_obs), n_hi = orc_n(a, h_e);
+        double q_lo = sqrt(n_lo * n_lo - s * s), q_hi = sqrt(n_hi * n_hi - s * s);
+        out[0] = s / c1 * (acosh(n_lo / s) - acosh(n_hi / s));
+        double G_lo = 0.5 * (n_lo * q_lo + s * s * log(n_lo + q_lo));
+        double G_hi = 0.5 * (n_hi * q_hi + s * s * log(n_hi + q_hi));
+        out[1] = (G_lo - G_hi) / (c1 * ORC_C_LIGHT);
+        out[2] = 0.0;
+        return 0;
+    }
+    /* layered */
+    double rho0 = orc_rho0(a);
+    for (int i = 0; i < a->n_layers; ++i) {
+        double lo = a->layer_h[i];
+        double hi = (i + 1 < a->n_layers) ? a->layer_h[i + 1] : a->h_top;
+        if (lo < h_obs) lo = h_obs;
+        if (hi > h_e) hi = h_e;
+        if (hi <= lo) continue;
+        if (a->last_linear && i == a->n_layers - 1) {
+            double rho = a->b[i] / a->c[i];
+            double n = 1.0 + a->kappa * rho / rho0, q = sqrt(n * n - s * s);
+            R += (hi - lo) * s / q;
+            T += (hi - lo) * n * n / q / ORC_C_LIGHT;
+            X += 100.0 * rho * (hi - lo) * n / q;
+            continue;
+        }
+        double H = a->c[i] / 100.0;                     /* scale height [m] */
+        double D = a->kappa * (a->b[i] / a->c[i]) / rho0; /* n - 1 at h = 0 of this layer's law */
+        double n_lo = 1.0 + D * exp(-lo / H), n_hi = 1.0 + D * exp(-hi / H);
+        double q_lo = sqrt(n_lo * n_lo - s * s), q_hi = sqrt(n_hi * n_hi - s * s);
+        double F_lo = orc_F(n_lo, s), F_hi = orc_F(n_hi, s);
+        /* int_lo^hi f(h) dh = H int_{n_hi}^{n_lo} f / (n - 1) dn */
+        R += H * s * (F_lo - F_hi);
+        T += H / ORC_C_LIGHT * ((q_lo - q_hi) + (log(n_lo + q_lo) - log(n_hi + q_hi)) + (F_lo - F_hi));
+        X += 100.0 * H * (rho0 / a->kappa) * (q_lo - q_hi);
+    }
+    out[0] = R; out[1] = T; out[2] = X;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* The thesis's numerical tracer: Snell's law in vector form at the   */
+/* boundaries of homogeneous slabs of thickness dh (Eq. 3.15).        */
+/* out = {R, t_path}.                                                 */
+/* ------------------------------------------------------------------ */
+void orc_snell_stepper(const orc_atm* a, double h_obs, double h_e, double theta0, double dh,
+                       double out[2])
+{
+    /* 2-D: direction (horizontal, vertical); N = (0, -1) is the downward normal */
+    double dir_x = sin(theta0), dir_z = -cos(theta0);
+    double h = h_e, x = 0.0, t = 0.0;
+    int nsteps = (int)ceil((h_e - h_obs) / dh - 1e-9);
+    double step = (h_e - h_obs) / nsteps;
+    double n1 = orc_n(a, h_e - 0.5 * step);
+    for (int j = 0; j < nsteps; ++j) {
+        /* straight through slab j with index n1 */
+        double path = step / (-dir_z);
+        x += path * dir_x;
+        t += path * n1 / ORC_C_LIGHT;
+        h -= step;
+        if (j + 1 == nsteps) break;
+        double n2 = orc_n(a, h - 0.5 * step);
+        /* optical vectors A' = n A; A2' = A1' + (sqrt(n2^2 - n1^2 + n1^2 cos^2 a1) - n1 cos a1) N */
+        double cos_a1 = -dir_z;                       /* A1 . N with N = (0, -1) */
+        double c = sqrt(n2 * n2 - n1 * n1 + n1 * n1 * cos_a1 * cos_a1) - n1 * cos_a1;
+        double Ax = n1 * dir_x, Az = n1 * dir_z - c;  /* + c N = (0, -c) */
+        dir_x = Ax / n2; dir_z = Az / n2;
+        n1 = n2;
+    }
+    out[0] = x; out[1] = t;
+}
+
+/* ------------------------------------------------------------------ */
+/* Full photon generation and propagation.                            */
+/* ------------------------------------------------------------------ */
+typedef struct {               /* input segment, 64 bytes */
+    double x0, y0, z0;         /* start point [m] */
+    double t0;                 /* time at the start point [s] */
+    float ux, uy, uz;          /* direction */
+    float length;              /* [m] */
+    float inv_gamma2;          /* 1 / gamma^2 */
+    float charge;              /* z */
+    uint32_t shower_id;
+    uint32_t flags;
+} orc_segment;
+
+typedef struct {
+    double h_obs;
+    double lambda1, lambda2;   /* band [m] */
+    double s_max;              /* sub-step length [m] */
+    int bunch;
+    int refraction;            /* 0: straight line, 1: exact planar refraction */
+    int transmission;          /* 0: off, 1: Rayleigh + aerosol */
+    int use_domain;            /* 1: photons with tan^2(theta0) > w_max are out of domain */
+    double w_max;
+    double rayl_X0, rayl_lambda0;                 /* X_R(l) = X0 (l / l0)^4          */
+    double aer_tau0, aer_lambda0, aer_alpha, aer_H; /* tau_A(l) = tau0 (l / l0)^-alpha */
+    uint64_t seed;
+    uint64_t seg_base;         /* global index of segs[0] */
+    int n_showers;
+    int hist_nx, hist_ny;
+    int n_tel;
+    double hist_x0, hist_y0, hist_dx, hist_dy;
+    const double* tel;         /* n_tel x {x, y, z, r} */
+    /* edge bands used only to flag photons for the parity comparison */
+    double band_pos, band_count, band_T, band_h, band_w;
+    double quad_rtol;
+} orc_config;
+
+enum { ORC_ST_LANDED = 0, ORC_ST_UPWARD = 1, ORC_ST_BELOW = 2, ORC_ST_DOMAIN = 3,
+       ORC_ST_ABSORBED = 4, ORC_ST_SUBSTEP_FLAG = 5 };
+enum { ORC_FL_COUNT = 1, ORC_FL_ABSORB = 2, ORC_FL_HIST_EDGE = 4, ORC_FL_TEL_EDGE = 8,
+       ORC_FL_DOMAIN = 16, ORC_FL_BELOW = 32, ORC_FL_UPWARD = 64, ORC_FL_LAYER = 128 };
+
+typedef struct {
+    uint64_t seg;
+    uint32_t k, i;
+    double x, y;               /* ground position [m] (landed and absorbed photons) */
+    double dt;                 /* arrival time minus segment t0 [s] */
+    double lambda;             /* [m] */
+    double ex, ey, h_e;        /* emission point [m] */
+    double ux, uy, uz;         /* emission direction */
+    double theta0, T, nbar;
+    int32_t status, tel, bin;
+    uint32_t flags;
+} orc_record;
+
+typedef struct {
+    uint64_t* hist;            /* n_showers x ny x nx (photons) */
+    uint64_t* tel_counts;      /* n_showers x n_tel (photons) */
+    double* tel_time;          /* n_showers x n_tel: sum of photons x absolute arrival time [s] */
+    uint64_t counters[8];      /* emitted, absorbed, hist, tel, missed_hist, missed_tel, upward, invalid_segments */
+    orc_record* records;
+    size_t capacity;
+    size_t count;
+} orc_output;
+
+static double orc_floor_dist(double v)     /* distance of v to the nearest integer */
+{
+    double f = v - floor(v);
+    return f < 0.5 ? f : 1.0 - f;
+}
+
+static void orc_push(orc_output* o, const orc_record* r)
+{
+    if (o->records && o->count < o->capacity) o->records[o->count] = *r;
+    o->count++;
+}
+
+static int orc_segment_valid(const orc_segment* s, int n_showers)
+{
+    if (!isfinite(s->x0) || !isfinite(s->y0) || !isfinite(s->z0) || !isfinite(s->t0)) return 0;
+    if (!isfinite(s->ux) || !isfinite(s->uy) || !isfinite(s->uz)) return 0;
+    if (!(s->length > 0.0f) || !isfinite(s->length)) return 0;
+    if (!(s->inv_gamma2 > 0.0f) || !(s->inv_gamma2 < 1.0f)) return 0;
+    if (!isfinite(s->charge)) return 0;
+    if (!(s->uz < 0.99f)) return 0;              /* bisector rotation needs P != (0,0,1) */
+    double n2 = (double)s->ux * s->ux + (double)s->uy * s->uy + (double)s->uz * s->uz;
+    if (fabs(n2 - 1.0) > 1e-4) return 0;
+    if ((int64_t)s->shower_id >= n_showers) return 0;
+    return 1;
+}
+
+int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
+                  const orc_config* cfg, orc_output* out)
+{
+    const double inv_l1 = 1.0 / cfg->lambda1, inv_l2 = 1.0 / cfg->lambda2;
+    /* Frank-Tamm (Eq. 2.2/2.4) integrated over the band with mu_r = 1 and
+     * no dispersion: dN/dx = 2 pi alpha z^2 (1/l1 - 1/l2) sin^2(theta). */
+    const double ft = 2.0 * ORC_PI * ORC_ALPHA * (inv_l1 - inv_l2);
+    const double b = (double)cfg->bunch;
+    const uint32_t key[2] = { (uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32) };
+    const double n_obs = orc_n(atm, cfg->h_obs);
+    const int use_tables = cfg->use_domain;
+
+    for (size_t is = 0; is < n_segs; ++is) {
+        const orc_segment* sg = &segs[is];
+        const uint64_t gid = cfg->seg_base + is;
+        if (!orc_segment_valid(sg, cfg->n_showers)) { out->counters[7]++; continue; }
+
+        double un = sqrt((double)sg->ux * sg->ux + (double)sg->uy * sg->uy + (double)sg->uz * sg->uz);
+        const double P[3] = { sg->ux / un, sg->uy / un, sg->uz / un };
+        const double L = sg->length, g = sg->inv_gamma2, z = sg->charge;
+        const double beta = sqrt(1.0 - g);
+        const int K = (int)fmax(1.0, ceil(L / cfg->s_max));
+        const int shower = (int)sg->shower_id;
+
+        /* Euler-Rodrigues rotation by 180 degrees about the bisector A of
+         * D = (0,0,-1) and P: M = 2 A A^T - 1 (Sec. 4.2), A normalised. */
+        double A[3] = { P[0], P[1], P[2] - 1.0 };
+        double an = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+        A[0] /= an; A[1] /= an; A[2] /= an;
+        double M[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) M[r][c] = 2.0 * A[r] * A[c] - (r == c ? 1.0 : 0.0);
+
+        for (int k = 0; k < K; ++k) {
+            /* Sub-step k (Sec. 4.2.1): n and the angle at its midpoint. */
+            double h_mid = sg->z0 + (k + 0.5) / K * L * P[2];
+            double n_k = orc_n(atm, h_mid);
+            double sin2 = 1.0 - 1.0 / (beta * beta * n_k * n_k);    /* Eq. 2.3 */
+            double nbar = sin2 > 0.0 ? ft * z * z * sin2 * (L / K) / b : 0.0;  /* threshold */
+            uint32_t ctr_c[4] = { (uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0xFFFFFFFFu };
+            uint32_t rc[4];
+            orc_philox4x32_10(ctr_c, key, rc);
+            double uk = orc_uniform(rc[0]);
+            double fl = floor(nbar);
+            int N = (int)fl + (uk < nbar - fl ? 1 : 0);               /* stochastic rounding */
+            int count_flag = orc_floor_dist(nbar - uk) < cfg->band_count;
+            if (count_flag) {
+                orc_record fr; memset(&fr, 0, sizeof fr);
+                fr.seg = gid; fr.k = (uint32_t)k; fr.i = 0xFFFFFFFFu;
+                fr.status = ORC_ST_SUBSTEP_FLAG; fr.nbar = nbar; fr.flags = ORC_FL_COUNT;
+                fr.tel = -1; fr.bin = -1;
+                orc_push(out, &fr);
+            }
+            if (N == 0) continue;
+            double cos_t = 1.0 / (beta * n_k), sin_t = sqrt(sin2);
+
+            for (int i = 0; i < N; ++i) {
+                uint32_t ctr[4] = { (uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, (uint32_t)i };
+                uint32_t r4[4];
+                orc_philox4x32_10(ctr, key, r4);
+                double u0 = orc_uniform(r4[0]), u1 = orc_uniform(r4[1]);
+                double u2 = orc_uniform(r4[2]), u3 = orc_uniform(r4[3]);
+
+                orc_record rec; memset(&rec, 0, sizeof rec);
+                rec.seg = gid; rec.k = (uint32_t)k; rec.i = (uint32_t)i;
+                rec.tel = -1; rec.bin = -1; rec.nbar = nbar;
+                if (count_flag && i == N - 1) rec.flags |= ORC_FL_COUNT;
+
+                /* translation to a random point of the sub-step (Fig. 4.2c) */
+                double ell = (k + u0) / K * L;
+                double E[3] = { sg->x0 + ell * P[0], sg->y0 + ell * P[1], sg->z0 + ell * P[2] };
+                double t_emit_rel = ell / (beta * ORC_C_LIGHT);
+                /* cone vector (Sec. 4.2) and wavelength from the 1/lambda^2 law */
+                double phi = 2.0 * ORC_PI * u1;
+                double inv_l = inv_l1 - u2 * (inv_l1 - inv_l2);
+                rec.lambda = 1.0 / inv_l;
+                double p[3] = { cos(phi) * sin_t, sin(phi) * sin_t, -cos_t };
+                double u[3];
+                for (int r = 0; r < 3; ++r) u[r] = M[r][0] * p[0] + M[r][1] * p[1] + M[r][2] * p[2];
+                rec.ex = E[0]; rec.ey = E[1]; rec.h_e = E[2];
+                rec.ux = u[0]; rec.uy = u[1]; rec.uz = u[2];
+                out->counters[0] += (uint64_t)cfg->bunch;
+
+                if (fabs(u[2]) < cfg->band_w) rec.flags |= ORC_FL_UPWARD;
+                if (fabs(E[2] - cfg->h_obs) < cfg->band_h) rec.flags |= ORC_FL_BELOW;
+                if (use_tables && atm->kind == ORC_ATM_LAYERED) {
+                    for (int li = 1; li < atm->n_layers; ++li)
+                        if (fabs(E[2] - atm->layer_h[li]) < cfg->band_h) rec.flags |= ORC_FL_LAYER;
+                }
+                if (!(u[2] < 0.0)) {                    /* not downward: discarded (Sec. 5.3.4) */
+                    rec.status = ORC_ST_UPWARD;
+                    out->counters[4] += cfg->bunch; out->counters[5] += cfg->bunch;
+                    out->counters[6] += cfg->bunch;
+                    orc_push(out, &rec);
+                    continue;
+                }
+                if (E[2] < cfg->h_obs) {                /* emitted below the observation level */
+                    rec.status = ORC_ST_BELOW;
+                    out->counters[4] += cfg->bunch; out->counters[5] += cfg->bunch;
+                    orc_push(out, &rec);
+                    continue;
+                }
+                double theta0 = acos(-u[2]);
+                rec.theta0 = theta0;
+                double w = (u[0] * u[0] + u[1] * u[1]) / (u[2] * u[2]);   /* tan^2(theta0) */
+                if (use_tables && fabs(w - cfg->w_max) < cfg->band_w * cfg->w_max) rec.flags |= ORC_FL_DOMAIN;
+                if (use_tables && w > cfg->w_max) {
+                    rec.status = ORC_ST_DOMAIN;
+                    out->counters[4] += cfg->bunch; out->counters[5] += cfg->bunch;
+                    orc_push(out, &rec);
+                    continue;
+                }
+                double path[4];
+                if (cfg->refraction) orc_refract_quad(atm, cfg->h_obs, E[2], theta0, cfg->aer_H, cfg->quad_rtol, path);
+                else orc_straight(atm, cfg->h_obs, E[2], theta0, cfg->aer_H, path);
+
+                /* ground point: E_xy + R along the horizontal unit of u */
+                double uh = sqrt(u[0] * u[0] + u[1] * u[1]);
+                double ex = uh > 0.0 ? u[0] / uh : 0.0, ey = uh > 0.0 ? u[1] / uh : 0.0;
+                double gx = E[0] + path[0] * ex, gy = E[1] + path[0] * ey;
+                rec.x = gx; rec.y = gy;
+                double t_arr = sg->t0 + t_emit_rel + path[1];
+                rec.dt = t_emit_rel + path[1];
+
+                /* arrival direction: zenith from the invariant, azimuth kept */
+                double ug[3];
+                if (cfg->refraction) {
+                    double s = orc_n(atm, E[2]) * sin(theta0);
+                    double sg_ = s / n_obs, cg = sqrt(1.0 - sg_ * sg_);
+                    ug[0] = sg_ * ex; ug[1] = sg_ * ey; ug[2] = -cg;
+                } else { ug[0] = u[0]; ug[1] = u[1]; ug[2] = u[2]; }
+
+                if (cfg->transmission) {
+                    double lam = rec.lambda;
+                    double XR = cfg->rayl_X0 * pow(lam / cfg->rayl_lambda0, 4.0);
+                    double tauA = cfg->aer_tau0 * pow(lam / cfg->aer_lambda0, -cfg->aer_alpha);
+                    double T = exp(-path[2] / XR - tauA * path[3] / cfg->aer_H);
+                    rec.T = T;
+                    if (fabs(u3 - T) < cfg->band_T) rec.flags |= ORC_FL_ABSORB;
+                    if (!(u3 < T)) {
+                        rec.status = ORC_ST_ABSORBED;
+                        out->counters[1] += cfg->bunch;
+                        orc_push(out, &rec);
+                        continue;
+                    }
+                } else rec.T = 1.0;
+                rec.status = ORC_ST_LANDED;
+
+                /* ground histogram */
+                if (cfg->hist_nx > 0) {
+                    double fx = (gx - cfg->hist_x0) / cfg->hist_dx, fy = (gy - cfg->hist_y0) / cfg->hist_dy;
+                    double ix = floor(fx), iy = floor(fy);
+                    double ex_d = fmin(fx - ix, ix + 1.0 - fx) * cfg->hist_dx;
+                    double ey_d = fmin(fy - iy, iy + 1.0 - fy) * cfg->hist_dy;
+                    int near_x = fx > -1.0 && fx < cfg->hist_nx + 1.0 && fy > -1.0 && fy < cfg->hist_ny + 1.0;
+                    if (near_x && (ex_d < cfg->band_pos || ey_d < cfg->band_pos)) rec.flags |= ORC_FL_HIST_EDGE;
+                    if (ix >= 0 && ix < cfg->hist_nx && iy >= 0 && iy < cfg->hist_ny) {
+                        int bin = (int)iy * cfg->hist_nx + (int)ix;
+                        rec.bin = bin;
+                        out->hist[((size_t)shower * cfg->hist_ny * cfg->hist_nx) + bin] += cfg->bunch;
+                        out->counters[2] += cfg->bunch;
+                    } else out->counters[4] += cfg->bunch;
+                } else out->counters[4] += cfg->bunch;
+
+                /* telescopes: distance from the sphere centre to the arrival line */
+                int best = -1; double best_d = 0.0;
+                for (int it = 0; it < cfg->n_tel; ++it) {
+                    const double* T4 = cfg->tel + 4 * it;
+                    double d0 = T4[0] - gx, d1 = T4[1] - gy, d2 = T4[2] - cfg->h_obs;
+                    double along = d0 * ug[0] + d1 * ug[1] + d2 * ug[2];
+                    double dist2 = d0 * d0 + d1 * d1 + d2 * d2 - along * along;
+                    double dist = sqrt(fmax(dist2, 0.0));
+                    if (fabs(dist - T4[3]) < cfg->band_pos) rec.flags |= ORC_FL_TEL_EDGE;
+                    if (dist < T4[3]) {
+                        if (best >= 0 && fabs(dist - best_d) < cfg->band_pos) rec.flags |= ORC_FL_TEL_EDGE;
+                        if (best < 0 || dist < best_d) { best = it; best_d = dist; }
+                    }
+                }
+                if (best >= 0) {
+                    rec.tel = best;
+                    out->tel_counts[(size_t)shower * cfg->n_tel + best] += cfg->bunch;
+                    out->tel_time[(size_t)shower * cfg->n_tel + best] += cfg->bunch * t_arr;
+                    out->counters[3] += cfg->bunch;
+                } else out->counters[5] += cfg->bunch;
+                orc_push(out, &rec);
+            }
+        }
+    }
+    return 0;
+}
+
+/* Sizes of the structs, so the Python side can check its mirror layout. */
+size_t orc_sizeof_segment(void) { return sizeof(orc_segment); }
+size_t orc_sizeof_record(void) { return sizeof(orc_record); }
+size_t orc_sizeof_config(void) { return sizeof(orc_config); }
+size_t orc_sizeof_atm(void) { return sizeof(orc_atm); }
