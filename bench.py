@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark: Cherenkov photons propagated per second on GB300.
+
+Workload (default): the refraction-corrected exact tracer -- 1e6 track
+segments from 10 seeded 1 TeV-class showers at 20 deg zenith, bunch size 5,
+US-standard layered atmosphere with refraction tables and Rayleigh + aerosol
+transmission, a 400 x 400 ground histogram of 1 m cells per shower and 100
+telescope spheres of 6 m radius on a 100 m grid, observation level 2 km.
+
+One step = one call of the C ABI over the whole batch (zeroing the outputs,
+importing the segments, generating, propagating and detecting every bunch).
+Inputs are resident in HBM for ``value``; ``e2e`` repeats the measurement
+through the host-pointer call (segments copied in, outputs copied out).
+Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Cherenkov photons propagated/sec on 1 GB300 (exact vs surrogate) at stated error"
+UNIT = "photons/s"
+WORKLOAD = "refraction-corrected exact tracer: 1e6 segments, 10 showers, zenith 20 deg, bunch 5, 100 telescopes"
+
+# Algorithmic FP32/INT lane operations of the method (counted from its formula
+# sequence, not from the compiled code): per bunch, per sub-step, per segment.
+OPS_PER_BUNCH = 285
+OPS_PER_SUBSTEP = 150
+OPS_PER_SEGMENT = 120
+SM_COUNT_NOMINAL = 152
+LANES_PER_SM = 128
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def workload(seed, n_showers=10, per_shower=100_000):
+    from paper_2405_04229_gb300 import synth
+    segs = synth.refraction_showers(n_showers=n_showers, per_shower=per_shower, seed=seed)
+    return segs, synth.grid_telescopes(), synth.histogram_400()
+
+
+def substeps(segs, s_max=1.0):
+    L = segs["length"].astype(np.float32)
+    return int(np.maximum(1, np.ceil(L / np.float32(s_max))).sum())
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.strip().split("\n") if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(segs, tel, hist, budget_s=12.0, chunk=250, bunch=5, seed=0):
+    """The FP64 oracle as it stands, on the host cores, over a bounded prefix
+    of every shower of the workload; returns (photons/s, threads, sample)."""
+    import concurrent.futures as cf
+
+    import oracle
+    from paper_2405_04229_gb300 import synth
+    atm = oracle.make_atm(oracle.ATM_LAYERED, layered=synth.US_STANDARD)
+    n = len(segs["z0"])
+    n_showers = int(segs["shower_id"].max()) + 1
+    per = n // n_showers
+    threads = os.cpu_count() or 1
+    # interleave chunks across showers so the sample has every shower's shape
+    starts = [s * per + j for j in range(0, per, chunk) for s in range(n_showers)]
+    done_photons, done_segs = 0, 0
+    t0 = time.perf_counter()
+    lock = threading.Lock()
+
+    def work(st):
+        sl = slice(st, min(st + chunk, n))
+        r = oracle.propagate(synth.take(segs, sl), atm, hist=hist, tel=tel, bunch=bunch, refraction=True,
+                             transmission=True, seed=seed, seg_base=st, n_showers=n_showers, records=False)
+        return int(r["counters"][0]), sl.stop - sl.start
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        it = iter(starts)
+        futs = set()
+        for _ in range(threads):
+            st = next(it, None)
+            if st is not None:
+                futs.add(ex.submit(work, st))
+        while futs:
+            done, futs = cf.wait(futs, return_when=cf.FIRST_COMPLETED)
+            for f in done:
+                p, s = f.result()
+                with lock:
+                    done_photons += p
+                    done_segs += s
+            if time.perf_counter() - t0 < budget_s:
+                for _ in done:
+                    st = next(it, None)
+                    if st is not None:
+                        futs.add(ex.submit(work, st))
+    dt = time.perf_counter() - t0
+    return done_photons / dt, threads, "%d segments (%d-segment chunks spread over all %d showers), %.1f s" % (
+        done_segs, chunk, n_showers, dt)
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    segs, tel, hist = workload(args.seed)
+    budget = max(5.0, min(60.0, 3.0 * (args.steps + args.warmup)))
+    rate, cores, sample = cpu_oracle_rate(segs, tel, hist, budget_s=budget)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "inputs re-read per chunk on the host"},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--per-shower", type=int, default=100_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2405_04229_gb300 import binding as B
+    from paper_2405_04229_gb300 import synth
+
+    bunch = 5
+    # weak scaling: every rank propagates its own batch of showers (seeds differ,
+    # segment ids are disjoint), no collective on the data path
+    segs, tel, hist = workload(args.seed + 1000 * rank, per_shower=args.per_shower)
+    n = len(segs["z0"])
+    seg_base = rank * n
+    n_sub = substeps(segs)
+    arr = B.pack_segments(segs)
+    atm = B.Atmosphere(layered=synth.US_STANDARD, refraction=True, transmission=True)
+    det = B.Detector(n_showers=10, hist=hist, tel=tel)
+    d_segs = torch.from_numpy(arr.view(np.uint8)).to(dev)
+    hist_t = torch.zeros((10, 400, 400), dtype=torch.int64, device=dev)
+    tel_c = torch.zeros((10, tel.shape[0]), dtype=torch.int64, device=dev)
+    tel_t = torch.zeros((10, tel.shape[0]), dtype=torch.float64, device=dev)
+    cnt = torch.zeros(8, dtype=torch.int64, device=dev)
+    out = B.cs_output()
+    out.hist, out.tel_counts, out.tel_time, out.counters = (hist_t.data_ptr(), tel_c.data_ptr(), tel_t.data_ptr(),
+                                                            cnt.data_ptr())
+    stream = torch.cuda.current_stream()
+    sp = C.c_void_p(stream.cuda_stream)
+    o = B.cs_opts_default()
+    o.bunch, o.device_ptrs, o.seg_base = bunch, 1, seg_base
+
+    def step(accumulate=0):
+        o.accumulate = accumulate
+        st = B.cs_propagate_ex(C.c_void_p(d_segs.data_ptr()), n, atm.handle, det.handle, args.seed, o, out, sp)
+        if st != B.CS_OK:
+            raise B.CSError(st, "cs_propagate_ex")
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    photons_per_step = int(cnt[0].item())
+    bunches_per_step = photons_per_step // bunch
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        time.sleep(0.5)   # let the sampler start before the timed region
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    assert int(cnt[0].item()) == photons_per_step
+    total_photons = photons_per_step * world * args.steps
+    value = total_photons / (ms_max / 1e3)
+
+    # kernel-only timing for the roofline: the same launch without the output memsets
+    kstarts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        kstarts[k].record(stream)
+        step(accumulate=1)
+        kends[k].record(stream)
+    torch.cuda.synchronize()
+    k_ms = sum(s.elapsed_time(e) for s, e in zip(kstarts, kends)) / args.steps
+    sm_clk = clk.summary()
+    ops = OPS_PER_BUNCH * bunches_per_step + OPS_PER_SUBSTEP * n_sub + OPS_PER_SEGMENT * n
+    achieved = ops / (k_ms / 1e3) / 1e12
+    max_mhz = 2070.0
+    try:
+        max_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", max_mhz)
+    except Exception:
+        pass
+    n_sm = B.cs_device_sm_count()
+    peak = n_sm * LANES_PER_SM * max_mhz * 1e6 / 1e12
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        traffic = tr.get("propagate_kernel_bytes_per_launch")
+    except Exception:
+        pass
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the host-pointer call: pinned segments in, outputs out
+        seg_pin = torch.from_numpy(arr.view(np.uint8)).pin_memory()
+        hist_h = torch.zeros((10, 400, 400), dtype=torch.int64).pin_memory()
+        tel_h = torch.zeros((10, tel.shape[0]), dtype=torch.int64).pin_memory()
+        tt_h = torch.zeros((10, tel.shape[0]), dtype=torch.float64).pin_memory()
+        cnt_h = torch.zeros(8, dtype=torch.int64).pin_memory()
+        rc_h = torch.zeros(1, dtype=torch.int64).pin_memory()
+        oh = B.cs_output()
+        oh.hist, oh.tel_counts, oh.tel_time, oh.counters, oh.record_count = (
+            hist_h.data_ptr(), tel_h.data_ptr(), tt_h.data_ptr(), cnt_h.data_ptr(), rc_h.data_ptr())
+        oo = B.cs_opts_default()
+        oo.bunch, oo.seg_base = bunch, seg_base
+
+        def hstep():
+            st = B.cs_propagate_ex(C.c_void_p(seg_pin.data_ptr()), n, atm.handle, det.handle, args.seed, oo, oh, sp)
+            if st != B.CS_OK:
+                raise B.CSError(st, "cs_propagate_ex(host)")
+
+        for _ in range(3):
+            hstep()
+        torch.cuda.synchronize()
+        e2e_s = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            hstep()
+            e2e_s += time.perf_counter() - a   # synchronous: copies in, kernel, copies out
+        assert int(cnt_h[0].item()) == photons_per_step
+        h2d = arr.nbytes
+        d2h = hist_h.numel() * 8 + tel_h.numel() * 16 + 8 * 8 + 8
+        e2e = {"value": photons_per_step * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        rate, cores, sample = cpu_oracle_rate(segs, tel, hist)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "segments_per_gpu": n, "bunch": bunch,
+                       "bunches_per_step_per_gpu": bunches_per_step, "form": "exact tracer (tables)",
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": "dp%d (shards)" % world},
+            "bunches_per_s": value / bunch,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "note": "FP32/INT lane ops of the method per launch / kernel time; peak = SMs x 128 lanes "
+                                 "x max SM clock"},
+            "kernel_ms": k_ms,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": sm_clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * cherenkov.h - C ABI of the GB300 (sm_103a) Cherenkov photon library.
+ *
+ * The library generates Cherenkov photons (or bunches of photons) along
+ * charged track segments and propagates them through a layered atmosphere
+ * to an observation level, where they are binned into ground histograms and
+ * hit-tested against telescope spheres.  It follows D. Baack, "Optical
+ * Photon Emission in Extended Airshowers" (TU Dortmund, 2023):
+ *
+ *   yield and angle      Sec. 2.2.1, Eq. 2.2-2.5
+ *   random numbers       Sec. 3.1 (counter-based Philox)
+ *   atmosphere           Sec. 3.3 and Sec. 4.1
+ *   straight line        Sec. 3.4.1, Eq. 3.3
+ *   exact refraction     Sec. 3.4.3, Eq. 3.17-3.18
+ *   photon generation    Sec. 4.2 and 4.2.1
+ *   absorption           Sec. 4.3.1
+ *   correction tables    Sec. 4.4.1 ("interpolation tracing")
+ *   GPU pipeline         Sec. 5.3 (import, generate, filter, propagate, store)
+ *
+ * Conventions.  Lengths in metres, times in seconds, heights above sea level
+ * on the z axis, the detector frame's origin at the array centre.  All calls
+ * return a cs_status; no C++ exception crosses this boundary.  Handles are
+ * immutable after creation and may be shared between host threads and CUDA
+ * streams; the calls themselves are not re-entrant on one output buffer.
+ * A call that fails with CS_ERR_CUDA leaves a message in cs_last_error().
+ */
+#ifndef CHERENKOV_H
+#define CHERENKOV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum cs_status {
+    CS_OK = 0,
+    CS_ERR_INVALID_ARG = 1,   /* a NULL pointer, a size or a parameter out of range */
+    CS_ERR_CUDA = 2,          /* a CUDA runtime call failed; see cs_last_error() */
+    CS_ERR_CAPACITY = 3,      /* more photon records than record_capacity (counts stay valid) */
+    CS_ERR_TIMEOUT = 4,       /* a bounded device wait gave up */
+    CS_ERR_DOMAIN = 5,        /* a table or network was asked outside its domain */
+    CS_ERR_NO_DEVICE = 6      /* no CUDA device of compute capability 10.3 */
+} cs_status;
+
+/* Human-readable name of a status code (static storage). */
+const char* cs_status_string(cs_status s);
+/* Message of the last CS_ERR_CUDA on the calling thread (static storage). */
+const char* cs_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Charged track segment, 64 bytes, array-of-structs at the boundary.
+ *
+ * The thesis's GPU segment (Sec. 5.3.1) carries position, direction, mass,
+ * energy, charge and age; mass and energy are folded here into 1/gamma^2
+ * (the thesis folds them into a "light yield parameter"), and a length is
+ * carried because a segment is a start point plus a straight step.
+ * A segment is skipped and counted as invalid if any field is not finite,
+ * length <= 0, inv_gamma2 is not in (0, 1), uz >= 0.99, |u|^2 differs from
+ * 1 by more than 1e-4, or shower_id >= the detector's n_showers.
+ * ---------------------------------------------------------------------- */
+typedef struct cs_segment {
+    double x0, y0, z0;   /* start point [m] */
+    double t0;           /* time at the start point [s] (e.g. since the first interaction) */
+    float ux, uy, uz;    /* unit direction of motion */
+    float length;        /* [m] */
+    float inv_gamma2;    /* 1 / gamma^2 of the particle */
+    float charge;        /* charge number z (only z^2 enters) */
+    uint32_t shower_id;  /* selects the per-shower histogram and telescope counters */
+    uint32_t flags;      /* reserved, 0 */
+} cs_segment;
+
+/* ------------------------------------------------------------------------
+ * Atmosphere.
+ * ---------------------------------------------------------------------- */
+enum {
+    CS_ATM_LAYERED = 0,      /* CORSIKA-style layers: T(h) = a + b exp(-h/c), top layer linear */
+    CS_ATM_LINEAR = 1,       /* n falls linearly from lin_n0 at lin_h0 to lin_n1 at lin_h1 (Sec. 6.3.1) */
+    CS_ATM_HOMOGENEOUS = 2   /* constant n = 1 + hom_delta (Sec. 3.3.1) */
+};
+
+typedef struct cs_atmosphere_desc {
+    int kind;                    /* CS_ATM_* */
+    int n_layers;                /* layered: 1..8 */
+    const double* layer_h;       /* layered: layer bottoms [m], ascending (host, n_layers) */
+    const double* layer_a;       /* layered: a_i [g/cm^2] */
+    const double* layer_b;       /* layered: b_i [g/cm^2] */
+    const double* layer_c;       /* layered: c_i [cm]; the top layer has T = a - b h / c */
+    double h_top;                /* layered: top of the atmosphere [m]; vacuum above */
+    double kappa;                /* layered: n - 1 = kappa rho(h) / rho(0), e.g. 2.9e-4 */
+    double lin_h0, lin_h1, lin_n0, lin_n1;   /* linear kind */
+    double hom_delta;            /* homogeneous kind: n - 1 */
+    double h_obs;                /* observation level [m] */
+    double lambda_min, lambda_max;   /* wavelength band [m], e.g. 300e-9 .. 600e-9 */
+    int refraction;              /* 0: straight line (Eq. 3.3); 1: exact planar refraction via tables */
+    int transmission;            /* 0: off; 1: Rayleigh + exponential aerosol survival test */
+    double rayl_X0, rayl_lambda0;    /* Rayleigh length X_R = X0 (lambda / lambda0)^4 [g/cm^2] */
+    double aer_tau0, aer_lambda0, aer_alpha, aer_H;  /* aerosol depth tau0 (lambda/lambda0)^-alpha per scale height aer_H [m] */
+    double theta_max;            /* table domain: photons steeper than this zenith [rad] are "out of
+                                    domain" (missed) when refraction or transmission is on; 0 = 75 deg */
+    int table_nw;                /* 0 = default number of tan^2(theta) columns */
+    double table_dh;             /* 0 = default row spacing [m]; must divide the layer bottoms - h_obs */
+} cs_atmosphere_desc;
+
+typedef struct cs_atmosphere cs_atmosphere;
+
+/* Builds the atmosphere on the current CUDA device: its FP64 refraction,
+ * time-delay, slant-column and aerosol tables (Sec. 4.4.1) are integrated on
+ * the GPU in FP64 and stored as FP32.  The descriptor's arrays are read
+ * during the call only.  Errors: CS_ERR_INVALID_ARG for inconsistent
+ * parameters, CS_ERR_CUDA / CS_ERR_NO_DEVICE for device failures. */
+cs_status cs_atmosphere_create(const cs_atmosphere_desc* desc, cs_atmosphere** out);
+void cs_atmosphere_destroy(cs_atmosphere* atm);
+
+/* Shape of the correction table: rows h_obs + j dh (j < nh), columns
+ * tan^2(theta0) = m dw (m < nw). */
+cs_status cs_atmosphere_table_info(const cs_atmosphere* atm, int* nh, int* nw, double* h0,
+                                   double* dh, double* dw);
+/* Copies the table to host memory: nh * nw * 8 floats, row-major, per node
+ * {G_R, G_t, G_X, G_A at h_j from above, the same four at h_j+1 from below
+ * minus those at h_j}; see the design notes for the normalisations. */
+cs_status cs_atmosphere_copy_table(const cs_atmosphere* atm, float* host_dst, size_t n_floats);
+
+/* ------------------------------------------------------------------------
+ * Detector: per-shower ground histograms and telescope spheres.
+ * ---------------------------------------------------------------------- */
+typedef struct cs_detector_desc {
+    int n_showers;               /* >= 1: number of per-shower output slots */
+    double h_obs;                /* observation level [m]; must equal the atmosphere's at propagation */
+    int hist_nx, hist_ny;        /* 0 = no histogram */
+    double hist_x0, hist_y0;     /* lower-left corner [m] */
+    double hist_dx, hist_dy;     /* cell size [m] */
+    int n_tel;                   /* 0 = no telescopes */
+    const double* tel_xyzr;      /* host, n_tel x {x, y, z, radius} [m] */
+} cs_detector_desc;
+
+typedef struct cs_detector cs_detector;
+
+/* Copies the layout to the device and builds its telescope grid hash.
+ * A photon hits telescope i if its arrival line passes within radius_i of
+ * the sphere's centre; the closest centre wins, then the lowest index. */
+cs_status cs_detector_create(const cs_detector_desc* desc, cs_detector** out);
+void cs_detector_destroy(cs_detector* det);
+
+/* ------------------------------------------------------------------------
+ * Outputs.  All counts are in photons (each bunch adds its bunch size).
+ * ---------------------------------------------------------------------- */
+enum {
+    CS_CNT_EMITTED = 0, CS_CNT_ABSORBED = 1, CS_CNT_HIST = 2, CS_CNT_TEL = 3,
+    CS_CNT_MISSED_HIST = 4, CS_CNT_MISSED_TEL = 5, CS_CNT_UPWARD = 6,
+    CS_CNT_INVALID_SEGMENTS = 7,      /* in segments, not photons */
+    CS_N_COUNTERS = 8
+};
+/* Conservation: emitted = absorbed + hist + missed_hist = absorbed + tel + missed_tel. */
+
+enum { CS_ST_LANDED = 0, CS_ST_UPWARD = 1, CS_ST_BELOW = 2, CS_ST_DOMAIN = 3, CS_ST_ABSORBED = 4 };
+
+/* Optional per-bunch record (parity mode), 48 bytes.  Records are written in
+ * no particular order; (seg, k, i) identifies a bunch uniquely. */
+typedef struct cs_record {
+    uint64_t seg;        /* global segment index (seg_base + position in the input) */
+    uint32_t k;          /* sub-step index */
+    uint32_t i;          /* bunch index within the sub-step */
+    float x, y;          /* ground position [m] (landed and absorbed bunches) */
+    float dt_ns;         /* arrival time minus the segment's t0 [ns] */
+    float lambda_nm;     /* wavelength [nm] */
+    int32_t tel;         /* telescope hit or -1 */
+    int32_t bin;         /* histogram cell iy * nx + ix or -1 */
+    uint32_t status;     /* CS_ST_* */
+    uint32_t reserved;
+} cs_record;
+
+typedef struct cs_output {
+    uint64_t* hist;          /* n_showers x hist_ny x hist_nx, or NULL if no histogram */
+    uint64_t* tel_counts;    /* n_showers x n_tel, or NULL if no telescopes */
+    double* tel_time;        /* n_showers x n_tel: sum over hits of bunch size x absolute arrival
+                                time [s], accumulated in FP64; NULL allowed */
+    uint64_t* counters;      /* CS_N_COUNTERS */
+    cs_record* records;      /* NULL: throughput mode (no per-bunch output) */
+    uint64_t record_capacity;
+    uint64_t* record_count;  /* 1 element: records produced (may exceed the capacity) */
+} cs_output;
+
+typedef struct cs_opts {
+    int bunch;               /* photons per bunch, >= 1 */
+    double s_max;            /* maximum sub-step length [m] (Sec. 4.2.1), > 0 */
+    uint64_t seg_base;       /* global index of segs[0]; keys the random draws */
+    int device_ptrs;         /* 0: segs and all output arrays are host memory; 1: device memory */
+    int accumulate;          /* 0: outputs are zeroed before the call; 1: added to */
+    int block_threads;       /* 0 = default */
+    int blocks_per_sm;       /* 0 = default */
+} cs_opts;
+
+/* Defaults: bunch 1, s_max 1 m, seg_base 0, host pointers, no accumulation. */
+void cs_opts_default(cs_opts* opts);
+
+/* Generates and propagates the photons of n segments (Sec. 5.3 pipeline).
+ * Random draws are keyed by (seed, global segment index, sub-step, bunch),
+ * so any split of the input into calls gives identical totals.
+ * Host-pointer mode copies segs to the device, runs, copies the outputs
+ * back and synchronises.  Device-pointer mode enqueues everything on
+ * `stream` (a cudaStream_t, NULL = legacy default stream) and returns
+ * without synchronising; outputs must not be read before the stream is.
+ * Errors: CS_ERR_INVALID_ARG (NULL handles/outputs, bad options),
+ * CS_ERR_CAPACITY (host mode only: more records than the capacity),
+ * CS_ERR_CUDA. */
+cs_status cs_propagate(const cs_segment* segs, size_t n, const cs_atmosphere* atm,
+                       const cs_detector* det, uint64_t seed, cs_output* out);
+cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_atmosphere* atm,
+                          const cs_detector* det, uint64_t seed, const cs_opts* opts,
+                          cs_output* out, void* stream);
+
+/* Philox4x32-10 (Salmon et al. 2011) on the device, for bit-exact checks:
+ * out[4 j .. 4 j + 3] = philox(ctr[4 j .. 4 j + 3], key).  Device pointers,
+ * enqueued on `stream`. */
+cs_status cs_philox4x32_10(const uint32_t* ctr, size_t n, uint32_t key0, uint32_t key1,
+                           uint32_t* out, void* stream);
+
+/* Number of SMs of the current device (for grid sizing by callers). */
+cs_status cs_device_sm_count(int* n_sm);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHERENKOV_H */

@@ -50,6 +50,7 @@ class Config(C.Structure):
     _fields_ = [("h_obs", C.c_double), ("lambda1", C.c_double), ("lambda2", C.c_double),
                 ("s_max", C.c_double), ("bunch", C.c_int), ("refraction", C.c_int),
                 ("transmission", C.c_int), ("use_domain", C.c_int), ("w_max", C.c_double),
+                ("h_dom_top", C.c_double),
                 ("rayl_X0", C.c_double), ("rayl_lambda0", C.c_double),
                 ("aer_tau0", C.c_double), ("aer_lambda0", C.c_double), ("aer_alpha", C.c_double),
                 ("aer_H", C.c_double), ("seed", C.c_uint64), ("seg_base", C.c_uint64),
@@ -223,6 +224,12 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
         use_domain = bool(refraction or transmission)
     cfg.use_domain = int(use_domain)
     cfg.w_max = w_max if w_max is not None else float(np.tan(np.radians(75.0)) ** 2)
+    if atm.kind == ATM_LAYERED:
+        cfg.h_dom_top = atm.h_top
+    elif atm.kind == ATM_LINEAR:
+        cfg.h_dom_top = atm.lin_h1
+    else:
+        cfg.h_dom_top = h_obs + 1e5
     tp = dict(rayl_X0=2974.0, rayl_lambda0=400e-9, aer_tau0=0.05, aer_lambda0=350e-9,
               aer_alpha=1.3, aer_H=1200.0)
     if transmission_params:

@@ -454,8 +454,10 @@ typedef struct {
     int bunch;
     int refraction;            /* 0: straight line, 1: exact planar refraction */
     int transmission;          /* 0: off, 1: Rayleigh + aerosol */
-    int use_domain;            /* 1: photons with tan^2(theta0) > w_max are out of domain */
+    int use_domain;            /* 1: photons with tan^2(theta0) > w_max or emitted at or above
+                                  h_dom_top are out of the correction tables' domain */
     double w_max;
+    double h_dom_top;
     double rayl_X0, rayl_lambda0;                 /* X_R(l) = X0 (l / l0)^4          */
     double aer_tau0, aer_lambda0, aer_alpha, aer_H; /* tau_A(l) = tau0 (l / l0)^-alpha */
     uint64_t seed;
@@ -545,7 +547,9 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
         const double P[3] = { sg->ux / un, sg->uy / un, sg->uz / un };
         const double L = sg->length, g = sg->inv_gamma2, z = sg->charge;
         const double beta = sqrt(1.0 - g);
-        const int K = (int)fmax(1.0, ceil(L / cfg->s_max));
+        /* the integer K is decided in FP32 (the kernel's precision) */
+        const float Kf = ceilf(sg->length / (float)cfg->s_max);
+        const int K = Kf < 1.0f ? 1 : (int)Kf;
         const int shower = (int)sg->shower_id;
 
         /* Euler-Rodrigues rotation by 180 degrees about the bisector A of
@@ -561,6 +565,10 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
             /* Sub-step k (Sec. 4.2.1): n and the angle at its midpoint. */
             double h_mid = sg->z0 + (k + 0.5) / K * L * P[2];
             double n_k = orc_n(atm, h_mid);
+            int mid_layer_flag = 0;       /* angle and yield may come from the other layer's law */
+            if (atm->kind == ORC_ATM_LAYERED)
+                for (int li = 1; li < atm->n_layers; ++li)
+                    if (fabs(h_mid - atm->layer_h[li]) < cfg->band_h) mid_layer_flag = 1;
             double sin2 = 1.0 - 1.0 / (beta * beta * n_k * n_k);    /* Eq. 2.3 */
             double nbar = sin2 > 0.0 ? ft * z * z * sin2 * (L / K) / b : 0.0;  /* threshold */
             uint32_t ctr_c[4] = { (uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0xFFFFFFFFu };
@@ -569,7 +577,7 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
             double uk = orc_uniform(rc[0]);
             double fl = floor(nbar);
             int N = (int)fl + (uk < nbar - fl ? 1 : 0);               /* stochastic rounding */
-            int count_flag = orc_floor_dist(nbar - uk) < cfg->band_count;
+            int count_flag = orc_floor_dist(nbar - uk) < cfg->band_count || mid_layer_flag;
             if (count_flag) {
                 orc_record fr; memset(&fr, 0, sizeof fr);
                 fr.seg = gid; fr.k = (uint32_t)k; fr.i = 0xFFFFFFFFu;
@@ -591,6 +599,7 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                 rec.seg = gid; rec.k = (uint32_t)k; rec.i = (uint32_t)i;
                 rec.tel = -1; rec.bin = -1; rec.nbar = nbar;
                 if (count_flag && i == N - 1) rec.flags |= ORC_FL_COUNT;
+                if (mid_layer_flag) rec.flags |= ORC_FL_LAYER;
 
                 /* translation to a random point of the sub-step (Fig. 4.2c) */
                 double ell = (k + u0) / K * L;
@@ -630,7 +639,8 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                 rec.theta0 = theta0;
                 double w = (u[0] * u[0] + u[1] * u[1]) / (u[2] * u[2]);   /* tan^2(theta0) */
                 if (use_tables && fabs(w - cfg->w_max) < cfg->band_w * cfg->w_max) rec.flags |= ORC_FL_DOMAIN;
-                if (use_tables && w > cfg->w_max) {
+                if (use_tables && fabs(E[2] - cfg->h_dom_top) < cfg->band_h) rec.flags |= ORC_FL_DOMAIN;
+                if (use_tables && (w > cfg->w_max || E[2] >= cfg->h_dom_top)) {
                     rec.status = ORC_ST_DOMAIN;
                     out->counters[4] += cfg->bunch; out->counters[5] += cfg->bunch;
                     orc_push(out, &rec);

@@ -1,0 +1,327 @@
+"""Thin ctypes binding of the C ABI in ``include/cherenkov.h``.
+
+Argument marshalling only: every step of the photon path runs in the CUDA
+library.  The library is loaded from the package's ``lib/`` directory and is
+never replaced by a CPU fallback: if it is missing or cannot load, the first
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libcherenkov.so")
+_lock = threading.Lock()
+_lib = None
+
+CS_OK, CS_ERR_INVALID_ARG, CS_ERR_CUDA, CS_ERR_CAPACITY, CS_ERR_TIMEOUT, CS_ERR_DOMAIN, CS_ERR_NO_DEVICE = range(7)
+CS_ATM_LAYERED, CS_ATM_LINEAR, CS_ATM_HOMOGENEOUS = 0, 1, 2
+(CS_CNT_EMITTED, CS_CNT_ABSORBED, CS_CNT_HIST, CS_CNT_TEL, CS_CNT_MISSED_HIST, CS_CNT_MISSED_TEL,
+ CS_CNT_UPWARD, CS_CNT_INVALID_SEGMENTS) = range(8)
+CS_N_COUNTERS = 8
+CS_ST_LANDED, CS_ST_UPWARD, CS_ST_BELOW, CS_ST_DOMAIN, CS_ST_ABSORBED = range(5)
+
+
+class CSError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        msg = "%s failed: %s" % (where, status_string(status))
+        if status == CS_ERR_CUDA:
+            msg += " (%s)" % last_error()
+        super().__init__(msg)
+
+
+SEGMENT_DTYPE = np.dtype([("x0", "<f8"), ("y0", "<f8"), ("z0", "<f8"), ("t0", "<f8"),
+                          ("ux", "<f4"), ("uy", "<f4"), ("uz", "<f4"), ("length", "<f4"),
+                          ("inv_gamma2", "<f4"), ("charge", "<f4"), ("shower_id", "<u4"),
+                          ("flags", "<u4")])
+RECORD_DTYPE = np.dtype([("seg", "<u8"), ("k", "<u4"), ("i", "<u4"), ("x", "<f4"), ("y", "<f4"),
+                         ("dt_ns", "<f4"), ("lambda_nm", "<f4"), ("tel", "<i4"), ("bin", "<i4"),
+                         ("status", "<u4"), ("reserved", "<u4")])
+
+
+class cs_atmosphere_desc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n_layers", C.c_int),
+                ("layer_h", C.POINTER(C.c_double)), ("layer_a", C.POINTER(C.c_double)),
+                ("layer_b", C.POINTER(C.c_double)), ("layer_c", C.POINTER(C.c_double)),
+                ("h_top", C.c_double), ("kappa", C.c_double),
+                ("lin_h0", C.c_double), ("lin_h1", C.c_double), ("lin_n0", C.c_double), ("lin_n1", C.c_double),
+                ("hom_delta", C.c_double), ("h_obs", C.c_double),
+                ("lambda_min", C.c_double), ("lambda_max", C.c_double),
+                ("refraction", C.c_int), ("transmission", C.c_int),
+                ("rayl_X0", C.c_double), ("rayl_lambda0", C.c_double),
+                ("aer_tau0", C.c_double), ("aer_lambda0", C.c_double), ("aer_alpha", C.c_double),
+                ("aer_H", C.c_double), ("theta_max", C.c_double), ("table_nw", C.c_int),
+                ("table_dh", C.c_double)]
+
+
+class cs_detector_desc(C.Structure):
+    _fields_ = [("n_showers", C.c_int), ("h_obs", C.c_double), ("hist_nx", C.c_int), ("hist_ny", C.c_int),
+                ("hist_x0", C.c_double), ("hist_y0", C.c_double), ("hist_dx", C.c_double),
+                ("hist_dy", C.c_double), ("n_tel", C.c_int), ("tel_xyzr", C.POINTER(C.c_double))]
+
+
+class cs_output(C.Structure):
+    _fields_ = [("hist", C.c_void_p), ("tel_counts", C.c_void_p), ("tel_time", C.c_void_p),
+                ("counters", C.c_void_p), ("records", C.c_void_p), ("record_capacity", C.c_uint64),
+                ("record_count", C.c_void_p)]
+
+
+class cs_opts(C.Structure):
+    _fields_ = [("bunch", C.c_int), ("s_max", C.c_double), ("seg_base", C.c_uint64),
+                ("device_ptrs", C.c_int), ("accumulate", C.c_int), ("block_threads", C.c_int),
+                ("blocks_per_sm", C.c_int)]
+
+
+def lib():
+    """The loaded CUDA library (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError("CUDA library not built: %s (run __graft_entry__.build())" % _LIB_PATH)
+            L = C.CDLL(_LIB_PATH)
+            vp, st = C.c_void_p, C.c_int
+            L.cs_status_string.restype = C.c_char_p
+            L.cs_status_string.argtypes = [st]
+            L.cs_last_error.restype = C.c_char_p
+            L.cs_atmosphere_create.argtypes = [C.POINTER(cs_atmosphere_desc), C.POINTER(vp)]
+            L.cs_atmosphere_create.restype = st
+            L.cs_atmosphere_destroy.argtypes = [vp]
+            L.cs_atmosphere_table_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                                   C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                                   C.POINTER(C.c_double)]
+            L.cs_atmosphere_table_info.restype = st
+            L.cs_atmosphere_copy_table.argtypes = [vp, vp, C.c_size_t]
+            L.cs_atmosphere_copy_table.restype = st
+            L.cs_detector_create.argtypes = [C.POINTER(cs_detector_desc), C.POINTER(vp)]
+            L.cs_detector_create.restype = st
+            L.cs_detector_destroy.argtypes = [vp]
+            L.cs_opts_default.argtypes = [C.POINTER(cs_opts)]
+            L.cs_propagate.argtypes = [vp, C.c_size_t, vp, vp, C.c_uint64, C.POINTER(cs_output)]
+            L.cs_propagate.restype = st
+            L.cs_propagate_ex.argtypes = [vp, C.c_size_t, vp, vp, C.c_uint64, C.POINTER(cs_opts),
+                                          C.POINTER(cs_output), vp]
+            L.cs_propagate_ex.restype = st
+            L.cs_philox4x32_10.argtypes = [vp, C.c_size_t, C.c_uint32, C.c_uint32, vp, vp]
+            L.cs_philox4x32_10.restype = st
+            L.cs_device_sm_count.argtypes = [C.POINTER(C.c_int)]
+            L.cs_device_sm_count.restype = st
+            _lib = L
+    return _lib
+
+
+def status_string(s):
+    return lib().cs_status_string(int(s)).decode()
+
+
+def last_error():
+    return lib().cs_last_error().decode()
+
+
+def _check(status, where):
+    if status != CS_OK:
+        raise CSError(status, where)
+
+
+def _dptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+# --------------------------------------------------------------------------
+# C-ABI calls (same names as include/cherenkov.h)
+# --------------------------------------------------------------------------
+def cs_atmosphere_create(desc: cs_atmosphere_desc):
+    h = C.c_void_p()
+    _check(lib().cs_atmosphere_create(C.byref(desc), C.byref(h)), "cs_atmosphere_create")
+    return h
+
+
+def cs_atmosphere_destroy(h):
+    lib().cs_atmosphere_destroy(h)
+
+
+def cs_atmosphere_table_info(h):
+    nh, nw = C.c_int(), C.c_int()
+    h0, dh, dw = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().cs_atmosphere_table_info(h, C.byref(nh), C.byref(nw), C.byref(h0), C.byref(dh), C.byref(dw)),
+           "cs_atmosphere_table_info")
+    return dict(nh=nh.value, nw=nw.value, h0=h0.value, dh=dh.value, dw=dw.value)
+
+
+def cs_atmosphere_copy_table(h):
+    info = cs_atmosphere_table_info(h)
+    buf = np.zeros((info["nh"], info["nw"], 2, 4), np.float32)
+    _check(lib().cs_atmosphere_copy_table(h, _dptr(buf), buf.size), "cs_atmosphere_copy_table")
+    return buf
+
+
+def cs_detector_create(desc: cs_detector_desc):
+    h = C.c_void_p()
+    _check(lib().cs_detector_create(C.byref(desc), C.byref(h)), "cs_detector_create")
+    return h
+
+
+def cs_detector_destroy(h):
+    lib().cs_detector_destroy(h)
+
+
+def cs_opts_default():
+    o = cs_opts()
+    lib().cs_opts_default(C.byref(o))
+    return o
+
+
+def cs_propagate(segs_ptr, n, atm, det, seed, out: cs_output):
+    return lib().cs_propagate(segs_ptr, n, atm, det, seed, C.byref(out))
+
+
+def cs_propagate_ex(segs_ptr, n, atm, det, seed, opts: cs_opts, out: cs_output, stream=None):
+    return lib().cs_propagate_ex(segs_ptr, n, atm, det, seed, C.byref(opts), C.byref(out), stream)
+
+
+def cs_philox4x32_10(ctr_ptr, n, key0, key1, out_ptr, stream=None):
+    return lib().cs_philox4x32_10(ctr_ptr, n, key0, key1, out_ptr, stream)
+
+
+def cs_device_sm_count():
+    n = C.c_int()
+    _check(lib().cs_device_sm_count(C.byref(n)), "cs_device_sm_count")
+    return n.value
+
+
+# --------------------------------------------------------------------------
+# Descriptor and buffer helpers
+# --------------------------------------------------------------------------
+def pack_segments(cols) -> np.ndarray:
+    n = len(cols["z0"])
+    a = np.zeros(n, SEGMENT_DTYPE)
+    for k in SEGMENT_DTYPE.names:
+        if k in cols:
+            a[k] = cols[k]
+    return a
+
+
+class Atmosphere:
+    """Owns a cs_atmosphere handle."""
+
+    def __init__(self, kind=CS_ATM_LAYERED, layered=None, linear=None, hom_delta=0.0, h_obs=2000.0,
+                 lambda_nm=(300.0, 600.0), refraction=False, transmission=False, transmission_params=None,
+                 theta_max_deg=75.0, table_nw=0, table_dh=0.0):
+        d = cs_atmosphere_desc()
+        d.kind = kind
+        self._keep = []
+        if kind == CS_ATM_LAYERED:
+            n = len(layered["layer_h"])
+            arrs = [np.ascontiguousarray(layered[k], np.float64) for k in ("layer_h", "a", "b", "c")]
+            self._keep += arrs
+            d.n_layers = n
+            d.layer_h, d.layer_a, d.layer_b, d.layer_c = (a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs)
+            d.h_top, d.kappa = layered["h_top"], layered["kappa"]
+        elif kind == CS_ATM_LINEAR:
+            d.lin_h0, d.lin_h1, d.lin_n0, d.lin_n1 = (linear[k] for k in ("lin_h0", "lin_h1", "lin_n0", "lin_n1"))
+        else:
+            d.hom_delta = hom_delta
+        d.h_obs = h_obs
+        d.lambda_min, d.lambda_max = lambda_nm[0] * 1e-9, lambda_nm[1] * 1e-9
+        d.refraction, d.transmission = int(refraction), int(transmission)
+        tp = dict(rayl_X0=2974.0, rayl_lambda0=400e-9, aer_tau0=0.05, aer_lambda0=350e-9, aer_alpha=1.3,
+                  aer_H=1200.0)
+        if transmission_params:
+            tp.update(transmission_params)
+        for k, v in tp.items():
+            setattr(d, k, v)
+        d.theta_max = math.radians(theta_max_deg)
+        d.table_nw, d.table_dh = table_nw, table_dh
+        self.desc = d
+        self.h_obs = h_obs
+        self.handle = cs_atmosphere_create(d)
+
+    def table(self):
+        return cs_atmosphere_copy_table(self.handle), cs_atmosphere_table_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            cs_atmosphere_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Detector:
+    """Owns a cs_detector handle."""
+
+    def __init__(self, n_showers=1, h_obs=2000.0, hist=None, tel=None):
+        d = cs_detector_desc()
+        d.n_showers, d.h_obs = n_showers, h_obs
+        if hist:
+            d.hist_nx, d.hist_ny = hist["nx"], hist["ny"]
+            d.hist_x0, d.hist_y0, d.hist_dx, d.hist_dy = hist["x0"], hist["y0"], hist["dx"], hist["dy"]
+        self.tel = np.ascontiguousarray(np.zeros((0, 4)) if tel is None else np.asarray(tel, np.float64))
+        d.n_tel = self.tel.shape[0]
+        d.tel_xyzr = self.tel.ctypes.data_as(C.POINTER(C.c_double))
+        self.n_showers, self.nx, self.ny, self.n_tel = n_showers, d.hist_nx, d.hist_ny, d.n_tel
+        self.desc = d
+        self.handle = cs_detector_create(d)
+
+    def close(self):
+        if self.handle:
+            cs_detector_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=1.0, seg_base=0,
+                   records=False, record_capacity=None, blocks_per_sm=0):
+    """cs_propagate_ex with host numpy buffers; returns a dict of outputs."""
+    arr = segs if isinstance(segs, np.ndarray) else pack_segments(segs)
+    arr = np.ascontiguousarray(arr)
+    hist = np.zeros((det.n_showers, det.ny, det.nx), np.uint64)
+    tel_counts = np.zeros((det.n_showers, det.n_tel), np.uint64)
+    tel_time = np.zeros((det.n_showers, det.n_tel), np.float64)
+    counters = np.zeros(CS_N_COUNTERS, np.uint64)
+    rc = np.zeros(1, np.uint64)
+    out = cs_output()
+    out.hist = _dptr(hist) if det.nx else None
+    out.tel_counts = _dptr(tel_counts) if det.n_tel else None
+    out.tel_time = _dptr(tel_time) if det.n_tel else None
+    out.counters = _dptr(counters)
+    out.record_count = _dptr(rc)
+    rec = None
+    if records:
+        cap = record_capacity if record_capacity is not None else max(1024, 120 * len(arr))
+        rec = np.zeros(cap, RECORD_DTYPE)
+        out.records, out.record_capacity = _dptr(rec), cap
+    o = cs_opts_default()
+    o.bunch, o.s_max, o.seg_base, o.device_ptrs, o.blocks_per_sm = bunch, s_max, seg_base, 0, blocks_per_sm
+    st = cs_propagate_ex(_dptr(arr) if len(arr) else None, len(arr), atm.handle, det.handle, seed, o, out)
+    _check(st, "cs_propagate_ex")
+    res = dict(hist=hist, tel_counts=tel_counts, tel_time=tel_time, counters=counters, n_records=int(rc[0]))
+    if records:
+        res["records"] = rec[: int(rc[0])]
+    return res
+
+
+def philox_device(ctr, key):
+    """Philox4x32-10 of host counters (n x 4 uint32) on the device."""
+    import torch
+    c = torch.as_tensor(np.ascontiguousarray(ctr, np.uint32).view(np.int32)).cuda()
+    o = torch.empty_like(c)
+    st = cs_philox4x32_10(C.c_void_p(c.data_ptr()), c.shape[0], key[0], key[1], C.c_void_p(o.data_ptr()),
+                          C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    _check(st, "cs_philox4x32_10")
+    torch.cuda.synchronize()
+    return o.cpu().numpy().view(np.uint32)

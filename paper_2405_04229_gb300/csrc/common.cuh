@@ -1,0 +1,124 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cherenkov.h"
+
+namespace cs {
+
+constexpr double kC = 299792458.0;          // m/s
+constexpr double kAlpha = 7.2973525693e-3;  // fine-structure constant
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kLog2e = 1.4426950408889634;
+constexpr int kMaxLayers = 8;
+
+// Correction table: per node two float4 {value at h_j from above, change to
+// h_j+1 from below}; the four fields are
+//   G_R = dR cos^3(theta0) / sin(theta0)   (dR: displacement minus straight line)
+//   G_t = c dt cos(theta0)                 (dt: optical minus vacuum straight-line time)
+//   G_X = X_slant cos(theta0)              [g/cm^2]
+//   G_A = A_slant cos(theta0)              [m], aerosol-weighted path
+// on rows h_obs + j dh and columns tan^2(theta0) = m dw (Sec. 4.4.1).
+struct TableView {
+    const float4* tab;   // [nh][nw][2]
+    int nh, nw;
+    float inv_dh, inv_dw;
+    float dz_max;        // emission heights above h_obs + dz_max are out of domain
+    float w_max;         // tan^2 of the domain's maximum zenith
+};
+
+// Everything a kernel needs about the atmosphere, passed by value.
+struct AtmParams {
+    int kind;            // CS_ATM_*
+    int n_layers;
+    int refraction;
+    int transmission;
+    int use_tables;      // refraction || transmission
+    // delta(h) = n - 1 at a height dz = h - h_obs above the observation level:
+    // layer i (dz >= lay_lo[i]) has delta = lay_D[i] * exp2(lay_c2[i] * dz)
+    float lay_lo[kMaxLayers];
+    float lay_D[kMaxLayers];
+    float lay_c2[kMaxLayers];
+    float top_rel;       // vacuum above h_top - h_obs
+    float lin_d0, lin_slope, lin_top_rel, lin_d1;   // linear kind, relative to h_obs
+    float hom_delta;
+    float n_obs;         // n(h_obs)
+    double h_obs;
+    float inv_l1_nm, dinv_l_nm;  // 1/lambda_min and 1/lambda_min - 1/lambda_max [1/nm]
+    float ft;            // 2 pi alpha (1/lambda_min - 1/lambda_max) [1/m]
+    // transmission: exponent in log2 units = (G_X kR + G_A kA) / |u_z|
+    float kR0;           // log2(e) lambda0_R^4 / X0_R [nm^4 cm^2/g]
+    float kA0;           // log2(e) tau0 / H_A [1/m]
+    float lamA_nm;       // aerosol reference wavelength [nm]
+    float aer_alpha;
+    TableView tv;
+};
+
+struct DetParams {
+    int n_showers;
+    float h_obs_f;        // observation level the telescopes were placed for
+    double h_obs;
+    int nx, ny;           // 0: no histogram
+    float hx0_hi, hx0_lo, hy0_hi, hy0_lo;   // histogram corner as float-float [m]
+    float inv_dx, inv_dy;
+    int n_tel;
+    const float4* tel;    // {x_hi, y_hi, z - h_obs, radius}
+    const float2* tel_lo; // {x_lo, y_lo}
+    // uniform grid hash over the telescopes' reach discs
+    float gx0, gy0, inv_cell;
+    int gnx, gny;
+    const int* cell_start;  // gnx * gny + 1
+    const int* cell_tel;
+    float hash_sin2_max;    // photons arriving steeper than this use the full list
+    float bx0, bx1, by0, by1;  // bounding box of all reach discs
+};
+
+struct OutParams {
+    unsigned long long* hist;
+    unsigned long long* tel_counts;
+    double* tel_time;
+    unsigned long long* counters;
+    cs_record* records;
+    unsigned long long record_capacity;
+    unsigned long long* record_count;
+};
+
+struct PropParams {
+    const cs_segment* segs;
+    long long n;
+    unsigned long long seg_base;
+    uint32_t key0, key1;
+    int bunch;
+    float s_max;
+};
+
+// ---- host-side helpers ------------------------------------------------------
+void set_last_error(const char* where, cudaError_t e);
+cs_status check_device();
+int device_sm_count();
+
+}  // namespace cs
+
+struct cs_atmosphere {
+    cs::AtmParams p;
+    float4* d_tab;         // device table (owned)
+    double h0, dh, dw;
+    int device;
+};
+
+struct cs_detector {
+    cs::DetParams p;
+    void* d_mem;           // one device allocation holding all arrays (owned)
+    int device;
+};
+
+#define CS_CUDA_TRY(call)                                     \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) {                              \
+            cs::set_last_error(#call, e_);                    \
+            return CS_ERR_CUDA;                               \
+        }                                                     \
+    } while (0)

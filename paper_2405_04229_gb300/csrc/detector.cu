@@ -1,0 +1,132 @@
+// Detector handle: per-shower ground histogram geometry and telescope
+// spheres with a uniform grid hash, so each photon tests only the spheres
+// whose reach covers its ground point (the telescope layouts of the thesis's
+// App. B.3 have tens to thousands of spheres).
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr double kHashTheta = 60.0 * 3.14159265358979323846 / 180.0;  // hash serves zenith <= 60 deg
+
+void split(double v, float* hi, float* lo) {
+    *hi = (float)v;
+    *lo = (float)(v - (double)*hi);
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector** out) {
+    if (!d || !out) return CS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (d->n_showers < 1) return CS_ERR_INVALID_ARG;
+    if (d->hist_nx < 0 || d->hist_ny < 0 || (d->hist_nx > 0) != (d->hist_ny > 0)) return CS_ERR_INVALID_ARG;
+    if (d->hist_nx > 0 && (!(d->hist_dx > 0.0) || !(d->hist_dy > 0.0))) return CS_ERR_INVALID_ARG;
+    if ((double)d->hist_nx * d->hist_ny * d->n_showers > 4e9) return CS_ERR_INVALID_ARG;
+    if (d->n_tel < 0 || (d->n_tel > 0 && !d->tel_xyzr)) return CS_ERR_INVALID_ARG;
+    for (int i = 0; i < d->n_tel; ++i) {
+        const double* t = d->tel_xyzr + 4 * i;
+        if (!isfinite(t[0]) || !isfinite(t[1]) || !isfinite(t[2]) || !(t[3] > 0.0)) return CS_ERR_INVALID_ARG;
+    }
+    cs_status st = cs::check_device();
+    if (st != CS_OK) return st;
+
+    cs_detector* h = new cs_detector;
+    memset(h, 0, sizeof *h);
+    cudaGetDevice(&h->device);
+    cs::DetParams& p = h->p;
+    p.n_showers = d->n_showers;
+    p.h_obs = d->h_obs;
+    p.h_obs_f = (float)d->h_obs;
+    p.nx = d->hist_nx;
+    p.ny = d->hist_ny;
+    if (p.nx > 0) {
+        split(d->hist_x0, &p.hx0_hi, &p.hx0_lo);
+        split(d->hist_y0, &p.hy0_hi, &p.hy0_lo);
+        p.inv_dx = (float)(1.0 / d->hist_dx);
+        p.inv_dy = (float)(1.0 / d->hist_dy);
+    }
+    p.n_tel = d->n_tel;
+
+    // host-side layout: tel float4, tel_lo float2, cell_start, cell_tel
+    std::vector<float4> tel(d->n_tel);
+    std::vector<float2> tel_lo(d->n_tel);
+    std::vector<int> cell_start(1, 0), cell_tel;
+    if (d->n_tel > 0) {
+        double reach_max = 0.0, x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+        std::vector<double> reach(d->n_tel);
+        for (int i = 0; i < d->n_tel; ++i) {
+            const double* t = d->tel_xyzr + 4 * i;
+            float lo;
+            split(t[0], &tel[i].x, &lo); tel_lo[i].x = lo;
+            split(t[1], &tel[i].y, &lo); tel_lo[i].y = lo;
+            tel[i].z = (float)(t[2] - d->h_obs);
+            tel[i].w = (float)t[3];
+            // ground points whose arrival line (zenith <= 60 deg) passes within r of
+            // the centre lie within r / cos + |dz| tan of the centre's footprint
+            reach[i] = t[3] / cos(kHashTheta) + fabs(t[2] - d->h_obs) * tan(kHashTheta) + 0.01;
+            reach_max = fmax(reach_max, reach[i]);
+            x0 = fmin(x0, t[0] - reach[i]); x1 = fmax(x1, t[0] + reach[i]);
+            y0 = fmin(y0, t[1] - reach[i]); y1 = fmax(y1, t[1] + reach[i]);
+        }
+        double cell = fmax(2.0 * reach_max, 1.0);
+        int gnx = (int)ceil((x1 - x0) / cell), gny = (int)ceil((y1 - y0) / cell);
+        while ((double)gnx * gny > 4e6) { cell *= 2.0; gnx = (int)ceil((x1 - x0) / cell); gny = (int)ceil((y1 - y0) / cell); }
+        gnx = gnx < 1 ? 1 : gnx;
+        gny = gny < 1 ? 1 : gny;
+        std::vector<std::vector<int>> lists((size_t)gnx * gny);
+        for (int i = 0; i < d->n_tel; ++i) {   // ascending index within every cell
+            const double* t = d->tel_xyzr + 4 * i;
+            int cx0 = (int)floor((t[0] - reach[i] - x0) / cell), cx1 = (int)floor((t[0] + reach[i] - x0) / cell);
+            int cy0 = (int)floor((t[1] - reach[i] - y0) / cell), cy1 = (int)floor((t[1] + reach[i] - y0) / cell);
+            for (int cy = cy0 < 0 ? 0 : cy0; cy <= cy1 && cy < gny; ++cy)
+                for (int cx = cx0 < 0 ? 0 : cx0; cx <= cx1 && cx < gnx; ++cx)
+                    lists[(size_t)cy * gnx + cx].push_back(i);
+        }
+        cell_start.assign((size_t)gnx * gny + 1, 0);
+        for (size_t c = 0; c < lists.size(); ++c) cell_start[c + 1] = cell_start[c] + (int)lists[c].size();
+        cell_tel.reserve(cell_start.back());
+        for (auto& l : lists) cell_tel.insert(cell_tel.end(), l.begin(), l.end());
+        p.gx0 = (float)x0;
+        p.gy0 = (float)y0;
+        p.inv_cell = (float)(1.0 / cell);
+        p.gnx = gnx;
+        p.gny = gny;
+        p.bx0 = (float)x0; p.bx1 = (float)(x0 + gnx * cell);
+        p.by0 = (float)y0; p.by1 = (float)(y0 + gny * cell);
+        p.hash_sin2_max = (float)(sin(kHashTheta) * sin(kHashTheta));
+    }
+    const size_t o_tel = 0;
+    const size_t o_lo = align_up(o_tel + tel.size() * sizeof(float4));
+    const size_t o_cs = align_up(o_lo + tel_lo.size() * sizeof(float2));
+    const size_t o_ct = align_up(o_cs + cell_start.size() * sizeof(int));
+    const size_t total = align_up(o_ct + (cell_tel.size() + 1) * sizeof(int));
+    cudaError_t e = cudaMalloc(&h->d_mem, total);
+    if (e != cudaSuccess) { cs::set_last_error("detector alloc", e); delete h; return CS_ERR_CUDA; }
+    char* base = (char*)h->d_mem;
+    std::vector<char> host(total, 0);
+    if (!tel.empty()) memcpy(host.data() + o_tel, tel.data(), tel.size() * sizeof(float4));
+    if (!tel_lo.empty()) memcpy(host.data() + o_lo, tel_lo.data(), tel_lo.size() * sizeof(float2));
+    memcpy(host.data() + o_cs, cell_start.data(), cell_start.size() * sizeof(int));
+    if (!cell_tel.empty()) memcpy(host.data() + o_ct, cell_tel.data(), cell_tel.size() * sizeof(int));
+    e = cudaMemcpy(h->d_mem, host.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cs::set_last_error("detector copy", e); cudaFree(h->d_mem); delete h; return CS_ERR_CUDA; }
+    p.tel = (const float4*)(base + o_tel);
+    p.tel_lo = (const float2*)(base + o_lo);
+    p.cell_start = (const int*)(base + o_cs);
+    p.cell_tel = (const int*)(base + o_ct);
+    *out = h;
+    return CS_OK;
+}
+
+extern "C" void cs_detector_destroy(cs_detector* det) {
+    if (!det) return;
+    cudaFree(det->d_mem);
+    delete det;
+}

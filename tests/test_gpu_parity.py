@@ -1,0 +1,258 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_04229_gb300 import binding as B
+from paper_2405_04229_gb300 import synth
+from tests import parity_util as PU
+
+pytestmark = pytest.mark.gpu
+
+ORC_ATM = oracle.make_atm(oracle.ATM_LAYERED, layered=synth.US_STANDARD)
+HIST = synth.histogram_400()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _atm(refr, trans, **kw):
+    return B.Atmosphere(layered=synth.US_STANDARD, refraction=refr, transmission=trans, **kw)
+
+
+def test_philox_bit_exact():
+    rng = np.random.default_rng(5)
+    ctr = rng.integers(0, 2**32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    for key in [(0, 0), (0xFFFFFFFF, 0xFFFFFFFF), (123456789, 987654321)]:
+        out = B.philox_device(ctr, key)
+        ref = np.array([oracle.philox(c, key) for c in ctr[:512]], np.uint32)
+        assert np.array_equal(out[:512], ref)
+    out = B.philox_device(np.array([[0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344]], np.uint32),
+                          (0xa4093822, 0x299f31d0))
+    assert list(out[0]) == [0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1]
+
+
+@pytest.mark.parametrize("refr", [True, False])
+def test_fp64_table_builder_matches_oracle_quadrature(refr):
+    atm = _atm(refr, True)
+    tab, info = atm.table()
+    rng = np.random.default_rng(2)
+    C = 299792458.0
+    for _ in range(60):
+        j = int(rng.integers(0, 1500))
+        m = int(rng.integers(0, info["nw"]))
+        h_e = info["h0"] + j * info["dh"]
+        w = max(m * info["dw"], 1e-8)
+        th = math.atan(math.sqrt(w))
+        c, s = math.cos(th), math.sin(th)
+        if refr:
+            q = oracle.refract_quad(ORC_ATM, 2000.0, h_e, th, rtol=1e-13)
+            want = np.array([(q[0] - (h_e - 2000.0) * math.tan(th)) * c**3 / s,
+                             (q[1] * C - (h_e - 2000.0) / c) * c, q[2] * c, q[3] * c])
+        else:
+            want = np.array([0.0, 0.0, oracle.column(ORC_ATM, 2000.0, h_e),
+                             1200.0 * (math.exp(-2000.0 / 1200.0) - math.exp(-h_e / 1200.0))])
+        got = tab[j, m, 0].astype(np.float64)
+        scale = np.maximum(np.abs(want), [1e-3, 1e-3, 1e-2, 1e-2])
+        assert np.all(np.abs(got - want) <= 2e-6 * scale + 1e-9), (j, m, got, want)
+
+
+def _run_both(segs, refr, trans, bunch, tel=None, n_showers=1, seed=0, seg_base=0, **kw):
+    atm = _atm(refr, trans)
+    det = B.Detector(n_showers=n_showers, hist=HIST, tel=tel)
+    g = B.propagate_host(segs, atm, det, seed=seed, bunch=bunch, records=True, seg_base=seg_base, **kw)
+    o = oracle.propagate(segs, ORC_ATM, hist=HIST, tel=tel, bunch=bunch, refraction=refr, transmission=trans,
+                         seed=seed, n_showers=n_showers, seg_base=seg_base)
+    return g, o
+
+
+def test_tiny_straight_line_config_parity():
+    """1,000 near-vertical segments, straight line, no transmission, bunch 1."""
+    segs = synth.tiny_vertical_segments(1000, seed=0)
+    g, o = _run_both(segs, False, False, 1)
+    st = PU.compare(g, o, bunch=1)
+    assert st["matched"] > 30000
+    PU.check_conservation(g["counters"])
+    assert np.array_equal(g["counters"], o["counters"]) or st["flagged"] > 0
+    diff = np.abs(g["hist"].astype(np.int64) - o["hist"].astype(np.int64)).sum()
+    assert diff <= 2 * (st["bin_flips"] + st["only_gpu"] + st["only_oracle"])
+
+
+def test_refraction_transmission_telescopes_parity():
+    segs = synth.refraction_showers(n_showers=2, per_shower=1200, seed=3)
+    tel = synth.grid_telescopes()
+    g, o = _run_both(segs, True, True, 5, tel=tel, n_showers=2)
+    st = PU.compare(g, o, bunch=5, shower_of_seg=segs["shower_id"])
+    assert st["matched"] > 20000
+    PU.check_conservation(g["counters"])
+    assert g["counters"][B.CS_CNT_TEL] > 0 and g["counters"][B.CS_CNT_ABSORBED] > 0
+    # telescope counts: equal up to flagged flips
+    d = np.abs(g["tel_counts"].astype(np.int64) - o["tel_counts"].astype(np.int64)).sum()
+    assert d <= 5 * 2 * (st["tel_flips"] + st["status_flips"] + st["only_gpu"] + st["only_oracle"])
+    # FP64 arrival-time sums per telescope: t0 (FP64) + the FP32 relative time, whose
+    # relative 1e-5 bound is a 1e-6 bound on the absolute time (t_rel < t0 / 10 here)
+    m = (g["tel_counts"] == o["tel_counts"]) & (g["tel_counts"] > 0)
+    assert m.sum() > 10
+    np.testing.assert_allclose(g["tel_time"][m], o["tel_time"][m], rtol=1e-6)
+
+
+def test_straight_line_with_transmission_and_inclined_showers():
+    segs = synth.shower_segments(1500, 45.0, 30.0, 1e12, seed=9)
+    tel = synth.grid_telescopes(nx=5, ny=5, pitch=150.0)
+    g, o = _run_both(segs, False, True, 2, tel=tel)
+    PU.compare(g, o, bunch=2)
+    PU.check_conservation(g["counters"])
+
+
+def test_ragged_sizes_and_tiles():
+    for n in (1, 255, 257, 513):
+        segs = synth.tiny_vertical_segments(n, seed=n)
+        g, o = _run_both(segs, True, False, 1)
+        PU.compare(g, o, bunch=1)
+        PU.check_conservation(g["counters"])
+
+
+def test_empty_input():
+    atm = _atm(False, False)
+    det = B.Detector(hist=HIST)
+    g = B.propagate_host(synth.tiny_vertical_segments(0), atm, det, records=True)
+    assert g["counters"].sum() == 0 and g["hist"].sum() == 0
+
+
+def test_long_segments_exercise_substep_rounds():
+    """A tile whose sub-steps exceed one shared-memory round."""
+    segs = synth.tiny_vertical_segments(300, seed=4)
+    segs["length"][:] = np.float32(37.5)        # 38 sub-steps each, 11,400 per tile
+    g, o = _run_both(segs, True, True, 10)
+    PU.compare(g, o, bunch=10)
+    PU.check_conservation(g["counters"])
+
+
+def test_invalid_and_degenerate_segments():
+    segs = synth.tiny_vertical_segments(40, seed=6)
+    segs["length"][0] = 0.0
+    segs["inv_gamma2"][1] = 1.5
+    segs["uz"][2] = np.nan
+    segs["shower_id"][3] = 5
+    segs["ux"][4], segs["uy"][4], segs["uz"][4] = 0.0, 0.0, 1.0
+    segs["z0"][5] = 1500.0                        # below the observation level
+    segs["ux"][6], segs["uy"][6], segs["uz"][6] = 0.6, 0.0, 0.8   # upward track
+    segs["ux"][7], segs["uy"][7], segs["uz"][7] = 1.0, 0.0, 0.0   # horizontal track
+    segs["inv_gamma2"][8] = np.float32(1.0 / 60.0**2)             # below threshold at ~10 km
+    g, o = _run_both(segs, True, True, 1)
+    assert g["counters"][B.CS_CNT_INVALID_SEGMENTS] == 5 == o["counters"][7]
+    PU.compare(g, o, bunch=1)
+    PU.check_conservation(g["counters"])
+    assert g["counters"][B.CS_CNT_UPWARD] > 0
+
+
+def test_split_calls_equal_one_call():
+    segs = synth.refraction_showers(n_showers=1, per_shower=3000, seed=8)
+    atm = _atm(True, True)
+    det = B.Detector(hist=HIST, tel=synth.grid_telescopes())
+    whole = B.propagate_host(segs, atm, det, seed=3, bunch=5)
+    a = B.propagate_host(synth.take(segs, slice(0, 1111)), atm, det, seed=3, bunch=5)
+    b = B.propagate_host(synth.take(segs, slice(1111, 3000)), atm, det, seed=3, bunch=5, seg_base=1111)
+    assert np.array_equal(whole["hist"], a["hist"] + b["hist"])
+    assert np.array_equal(whole["tel_counts"], a["tel_counts"] + b["tel_counts"])
+    assert np.array_equal(whole["counters"], a["counters"] + b["counters"])
+
+
+def test_throughput_mode_equals_record_mode():
+    segs = synth.refraction_showers(n_showers=1, per_shower=2000, seed=1)
+    atm = _atm(True, True)
+    det = B.Detector(hist=HIST, tel=synth.grid_telescopes())
+    r = B.propagate_host(segs, atm, det, seed=2, bunch=5, records=True)
+    t = B.propagate_host(segs, atm, det, seed=2, bunch=5, records=False)
+    for k in ("hist", "tel_counts", "counters"):
+        assert np.array_equal(r[k], t[k])
+
+
+def test_record_capacity_overflow_reports_capacity_error():
+    segs = synth.tiny_vertical_segments(50, seed=1)
+    atm = _atm(False, False)
+    det = B.Detector(hist=HIST)
+    with pytest.raises(B.CSError) as e:
+        B.propagate_host(segs, atm, det, records=True, record_capacity=10)
+    assert e.value.status == B.CS_ERR_CAPACITY
+
+
+def test_linear_profile_and_homogeneous_media():
+    """Sec. 6.3.1 linear profile (n 1.5 -> 1.0) and Sec. 3.3.1 homogeneous medium."""
+    segs = synth.tiny_vertical_segments(40, seed=2)
+    segs["z0"][:] = segs["z0"] * 0.5           # 4-6 km
+    segs["inv_gamma2"][:] = np.float32(0.4)    # beta ~ 0.77: above threshold only in dense media
+    for kind, kw, okw in [(B.CS_ATM_LINEAR, dict(linear=synth.LINEAR_TEST), dict(linear=synth.LINEAR_TEST)),
+                          (B.CS_ATM_HOMOGENEOUS, dict(hom_delta=0.33), dict(hom_delta=0.33))]:
+        atm = B.Atmosphere(kind=kind, refraction=True, h_obs=0.0, **kw)
+        det = B.Detector(hist=HIST, h_obs=0.0)
+        g = B.propagate_host(segs, atm, det, seed=4, bunch=500, records=True, s_max=0.5)
+        okind = oracle.ATM_LINEAR if kind == B.CS_ATM_LINEAR else oracle.ATM_HOMOGENEOUS
+        o = oracle.propagate(segs, oracle.make_atm(okind, **okw), hist=HIST, bunch=500, refraction=True,
+                             seed=4, h_obs=0.0, s_max=0.5)
+        st = PU.compare(g, o, bunch=500)
+        assert st["matched"] > 500
+
+
+def test_full_size_refraction_workload_sampled():
+    """1e6 segments (10 showers x 1e5) in the benchmark's launch configuration,
+    device pointers; 400 sampled segments checked photon by photon, the rest by
+    conservation and by aggregate = records."""
+    torch = pytest.importorskip("torch")
+    import ctypes as C
+    segs = synth.refraction_showers(10, 100_000, seed=0)
+    arr = B.pack_segments(segs)
+    n = len(arr)
+    tel = synth.grid_telescopes()
+    atm = _atm(True, True)
+    det = B.Detector(n_showers=10, hist=HIST, tel=tel)
+    dev = torch.device("cuda:0")
+    d_segs = torch.from_numpy(arr.view(np.uint8)).to(dev)
+    hist = torch.zeros((10, 400, 400), dtype=torch.int64, device=dev)
+    tel_counts = torch.zeros((10, 100), dtype=torch.int64, device=dev)
+    tel_time = torch.zeros((10, 100), dtype=torch.float64, device=dev)
+    counters = torch.zeros(8, dtype=torch.int64, device=dev)
+    cap = 60_000_000
+    recs = torch.zeros(cap * 48, dtype=torch.uint8, device=dev)
+    rc = torch.zeros(1, dtype=torch.int64, device=dev)
+    out = B.cs_output()
+    out.hist, out.tel_counts, out.tel_time = hist.data_ptr(), tel_counts.data_ptr(), tel_time.data_ptr()
+    out.counters, out.records, out.record_capacity, out.record_count = (counters.data_ptr(), recs.data_ptr(), cap,
+                                                                        rc.data_ptr())
+    o = B.cs_opts_default()
+    o.bunch, o.device_ptrs = 5, 1
+    st = B.cs_propagate_ex(C.c_void_p(d_segs.data_ptr()), n, atm.handle, det.handle, 0, o, out,
+                           C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == B.CS_OK
+    torch.cuda.synchronize()
+    nrec = int(rc.item())
+    assert nrec <= cap
+    c = counters.cpu().numpy().astype(np.uint64)
+    PU.check_conservation(c)
+    assert int(c[0]) == 5 * nrec
+    rec_np_all = recs[: nrec * 48].cpu().numpy().view(B.RECORD_DTYPE)
+    # aggregate histogram == records' histogram, at full size
+    h = np.zeros((10, 400 * 400), np.int64)
+    m = rec_np_all["bin"] >= 0
+    np.add.at(h, (segs["shower_id"][rec_np_all["seg"][m].astype(np.int64)], rec_np_all["bin"][m]), 5)
+    assert np.array_equal(h.reshape(10, 400, 400), hist.cpu().numpy())
+    # sampled photon-by-photon parity
+    rng = np.random.default_rng(11)
+    sample = np.sort(rng.choice(n, 400, replace=False))
+    sel = np.isin(rec_np_all["seg"], sample)
+    g = dict(records=rec_np_all[sel], n_records=int(sel.sum()))
+    o_recs = []
+    for s in sample:
+        r = oracle.propagate(synth.take(segs, slice(s, s + 1)), ORC_ATM, hist=HIST, tel=tel, bunch=5,
+                             refraction=True, transmission=True, seed=0, seg_base=int(s), n_showers=10)
+        o_recs.append(r["records"])
+    orc = dict(records=np.concatenate(o_recs))
+    st = PU.compare(g, orc, bunch=5, check_hist=False)
+    assert st["matched"] > 2000
