@@ -1,0 +1,114 @@
+// Device-side building blocks of the photon kernels: the counter-based RNG,
+// float-float helpers, the closed-form refractive index, a sin/cos of 2 pi u
+// and approximate transcendental wrappers.
+#pragma once
+
+#include "common.cuh"
+
+namespace cs {
+
+constexpr float kInvC = (float)(1.0 / kC);
+
+// Philox4x32-10 (Salmon et al., SC'11): per round two 32x32 -> 64 multiplies,
+// the Weyl key schedule between rounds.
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                        uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// 24-bit uniform in [0, 1), exact in FP32 and FP64
+__device__ __forceinline__ float uniform24(uint32_t x) { return __uint2float_rn(x >> 8) * 0x1p-24f; }
+
+// ---- float-float (error-free transformations) ------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// floor(s + t) for |t| below one ulp of s
+__device__ __forceinline__ int ff_floor(float s, float t) {
+    const float f = floorf(s);
+    int i = (int)f;
+    if (t >= (f + 1.0f) - s) i += 1;
+    else if (s == f && t < 0.0f) i -= 1;
+    return i;
+}
+
+// (a_hi + a_lo) * m as float-float
+__device__ __forceinline__ void ff_scale(float a_hi, float a_lo, float m, float& hi, float& lo) {
+    hi = a_hi * m;
+    lo = fmaf(a_hi, m, -hi) + a_lo * m;
+    float s, e;
+    two_sum(hi, lo, s, e);
+    hi = s;
+    lo = e;
+}
+
+// ---- approximate transcendental functions (PTX .approx forms) -------------
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// sin and cos of 2 pi u for u in [0, 1): exact quadrant reduction of 4u and
+// Taylor polynomials on |x| <= pi/4 (truncation below 3e-8).
+__device__ __forceinline__ void sincos_2pi(float u, float& s, float& c) {
+    const float v = 4.0f * u;                    // exact
+    const float q = rintf(v);
+    const float x = (v - q) * 1.57079632679489662f;   // |x| <= pi/4
+    const float x2 = x * x;
+    float sp = fmaf(x2, 2.75573192e-6f, -1.98412698e-4f);   //  1/9!, -1/7!
+    sp = fmaf(x2, sp, 8.33333333e-3f);                      //  1/5!
+    sp = fmaf(x2, sp, -1.66666667e-1f);                     // -1/3!
+    const float sx = fmaf(x * x2, sp, x);
+    float cp = fmaf(x2, 2.48015873e-5f, -1.38888889e-3f);   //  1/8!, -1/6!
+    cp = fmaf(x2, cp, 4.16666667e-2f);                      //  1/4!
+    cp = fmaf(x2, cp, -0.5f);                               // -1/2!
+    const float cx = fmaf(x2, cp, 1.0f);
+    const int qi = ((int)q) & 3;
+    s = (qi == 0) ? sx : (qi == 1) ? cx : (qi == 2) ? -sx : -cx;
+    c = (qi == 0) ? cx : (qi == 1) ? -sx : (qi == 2) ? -cx : sx;
+}
+
+// ---- refractive index n - 1 at dz above the observation level --------------
+// closed form per layer (half-open layers [h_i, h_i+1)), FP32
+__device__ __forceinline__ float delta_at(const AtmParams& a, float dz) {
+    if (a.kind == CS_ATM_LAYERED) {
+        if (dz >= a.top_rel) return 0.0f;
+        int i = 0;
+#pragma unroll
+        for (int k = 1; k < kMaxLayers; ++k)
+            if (k < a.n_layers && dz >= a.lay_lo[k]) i = k;
+        return a.lay_D[i] * exp2f(a.lay_c2[i] * dz);
+    }
+    if (a.kind == CS_ATM_LINEAR) return dz >= a.lin_top_rel ? a.lin_d1 : a.lin_d0 + a.lin_slope * dz;
+    return a.hom_delta;
+}
+
+}  // namespace cs
