@@ -211,6 +211,28 @@ cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_atmosphere*
                           const cs_detector* det, uint64_t seed, const cs_opts* opts,
                           cs_output* out, void* stream);
 
+/* Allocation-free form of the device-pointer call (the thesis has no
+ * counterpart; this is a library service).  For callers that cannot let the
+ * library allocate device memory: code running while a memory pool or arena
+ * owns the device, real-time or embedded hosts that allow no allocation after
+ * start-up, callers that must account for every byte in advance.  It does
+ * what cs_propagate_ex does with opts->device_ptrs = 1 (opts must say so;
+ * host pointers are rejected with CS_ERR_INVALID_ARG), but its only scratch,
+ * the dynamic scheduler's tile counter, lives in a 256-byte array that the
+ * library declares statically on every device that loads it (held until the
+ * process exits) instead of in memory the library allocates.  It calls no
+ * cudaMalloc or cudaFree.
+ * Limits and rules: one 32-bit counter, so inputs needing 2^32 - 65537 or
+ * more tiles of 256 segments are rejected with CS_ERR_INVALID_ARG.  The first
+ * call on a device looks up the array's device address, so make that first
+ * call before any stream capture.  Every call reuses the same array and
+ * resets the counter on its stream before the kernel; two calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race on
+ * the counter and give wrong results, so serialise them. */
+cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, const cs_atmosphere* atm,
+                               const cs_detector* det, uint64_t seed, const cs_opts* opts,
+                               cs_output* out, void* stream);
+
 /* Philox4x32-10 (Salmon et al. 2011) on the device, for bit-exact checks:
  * out[4 j .. 4 j + 3] = philox(ctr[4 j .. 4 j + 3], key).  Device pointers,
  * enqueued on `stream`. */

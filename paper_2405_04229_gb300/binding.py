@@ -107,6 +107,8 @@ def lib():
             L.cs_propagate_ex.argtypes = [vp, C.c_size_t, vp, vp, C.c_uint64, C.POINTER(cs_opts),
                                           C.POINTER(cs_output), vp]
             L.cs_propagate_ex.restype = st
+            L.cs_propagate_noalloc.argtypes = L.cs_propagate_ex.argtypes
+            L.cs_propagate_noalloc.restype = st
             L.cs_philox4x32_10.argtypes = [vp, C.c_size_t, C.c_uint32, C.c_uint32, vp, vp]
             L.cs_philox4x32_10.restype = st
             L.cs_device_sm_count.argtypes = [C.POINTER(C.c_int)]
@@ -182,6 +184,10 @@ def cs_propagate(segs_ptr, n, atm, det, seed, out: cs_output):
 
 def cs_propagate_ex(segs_ptr, n, atm, det, seed, opts: cs_opts, out: cs_output, stream=None):
     return lib().cs_propagate_ex(segs_ptr, n, atm, det, seed, C.byref(opts), C.byref(out), stream)
+
+
+def cs_propagate_noalloc(segs_ptr, n, atm, det, seed, opts: cs_opts, out: cs_output, stream=None):
+    return lib().cs_propagate_noalloc(segs_ptr, n, atm, det, seed, C.byref(opts), C.byref(out), stream)
 
 
 def cs_philox4x32_10(ctr_ptr, n, key0, key1, out_ptr, stream=None):

@@ -620,3 +620,103 @@ extern "C" cs_status cs_philox4x32_10(const uint32_t* ctr, size_t n, uint32_t ke
     CS_CUDA_TRY(cudaGetLastError());
     return CS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the device-pointer call.
+//
+// Some callers cannot let a library call cudaMalloc: code that runs while a
+// memory pool or arena owns the whole device (so a surprise allocation would
+// fail or fragment it), real-time or embedded hosts that allow no allocation
+// after start-up, and callers that must keep every byte the library uses
+// accounted for in advance.  The regular device-pointer call allocates, once
+// per device, the ring of tile counters its dynamic scheduler uses; this
+// variant uses a counter in a file-scope device array instead, which the CUDA
+// module loader creates on every GPU that loads the library and which lives
+// until the process exits.
+// ---------------------------------------------------------------------------
+namespace cs {
+namespace {
+
+// One 32-bit tile counter per call, padded to one 256-byte line.  A call can
+// schedule at most 2^32 - 1 tiles of kTile segments.
+constexpr int kNoAllocScratchWords = 64;
+static __device__ __align__(256) unsigned int g_noalloc_scratch[kNoAllocScratchWords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned int* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the first call on a device does this set-up).
+cs_status noalloc_scratch(unsigned int** out) {
+    int dev = 0;
+    CS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return CS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        CS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = (unsigned int*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return CS_OK;
+}
+
+}  // namespace
+}  // namespace cs
+
+extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, const cs_atmosphere* atm,
+                                          const cs_detector* det, uint64_t seed, const cs_opts* opts,
+                                          cs_output* out, void* stream_) {
+    if (!atm || !det || !out || !out->counters) return CS_ERR_INVALID_ARG;
+    cs_opts o;
+    if (opts) o = *opts; else cs_opts_default(&o);
+    if (o.bunch < 1 || !(o.s_max > 0.0) || (n > 0 && !segs)) return CS_ERR_INVALID_ARG;
+    if (!o.device_ptrs) return CS_ERR_INVALID_ARG;           // host buffers would need staging memory
+    if (((uintptr_t)segs & 15) != 0) return CS_ERR_INVALID_ARG;
+    if (det->p.nx > 0 && !out->hist) return CS_ERR_INVALID_ARG;
+    if (det->p.n_tel > 0 && !out->tel_counts) return CS_ERR_INVALID_ARG;
+    if (out->records && !out->record_count) return CS_ERR_INVALID_ARG;
+    if (fabs(det->p.h_obs - atm->p.h_obs) > 1e-9 * fmax(1.0, fabs(atm->p.h_obs))) return CS_ERR_INVALID_ARG;
+    // the counter is 32 bits wide: reject inputs with more tiles than it can count
+    if ((n + kTile - 1) / kTile >= 0xFFFFFFFFull - 65536ull) return CS_ERR_INVALID_ARG;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const DetParams& dp = det->p;
+    unsigned int* ctr = nullptr;
+    cs_status st = noalloc_scratch(&ctr);
+    if (st != CS_OK) return st;
+    if (!o.accumulate) {
+        if (out->hist) CS_CUDA_TRY(cudaMemsetAsync(out->hist, 0, (size_t)dp.n_showers * dp.nx * dp.ny * 8, stream));
+        if (out->tel_counts) CS_CUDA_TRY(cudaMemsetAsync(out->tel_counts, 0, (size_t)dp.n_showers * dp.n_tel * 8, stream));
+        if (out->tel_time) CS_CUDA_TRY(cudaMemsetAsync(out->tel_time, 0, (size_t)dp.n_showers * dp.n_tel * 8, stream));
+        CS_CUDA_TRY(cudaMemsetAsync(out->counters, 0, CS_N_COUNTERS * 8, stream));
+        if (out->record_count) CS_CUDA_TRY(cudaMemsetAsync(out->record_count, 0, 8, stream));
+    }
+    if (n == 0) return CS_OK;
+    PropParams pp;
+    pp.segs = segs;
+    pp.n = (long long)n;
+    pp.seg_base = o.seg_base;
+    pp.key0 = (uint32_t)seed;
+    pp.key1 = (uint32_t)(seed >> 32);
+    pp.bunch = o.bunch;
+    pp.s_max = (float)o.s_max;
+    OutParams op;
+    op.hist = (unsigned long long*)out->hist;
+    op.tel_counts = (unsigned long long*)out->tel_counts;
+    op.tel_time = out->tel_time;
+    op.counters = (unsigned long long*)out->counters;
+    op.records = out->records;
+    op.record_capacity = out->records ? out->record_capacity : 0;
+    op.record_count = (unsigned long long*)out->record_count;
+    const size_t smem = sizeof(TileSmem);
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int per_sm = o.blocks_per_sm > 0 ? o.blocks_per_sm : 4;
+    const long long tiles = ((long long)n + kTile - 1) / kTile;
+    const long long grid = std::min<long long>(tiles, (long long)device_sm_count() * per_sm);
+    // the array keeps the previous call's count: start this call's schedule at zero
+    CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), stream));
+    propagate_kernel<<<(unsigned)grid, kThreads, smem, stream>>>(pp, atm->p, dp, op, ctr);
+    CS_CUDA_TRY(cudaGetLastError());
+    return CS_OK;
+}
