@@ -211,6 +211,50 @@ cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_atmosphere*
                           const cs_detector* det, uint64_t seed, const cs_opts* opts,
                           cs_output* out, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batched uneven showers: many showers of uneven size in one persistent
+ * launch (blocks take tiles of 256 segments from a work counter until the
+ * batch is done), captured once into a CUDA graph and replayed.  The thesis
+ * batches tens of thousands of tracks per kernel call (Sec. 5.1, 5.4).
+ * ---------------------------------------------------------------------- */
+typedef struct cs_batch cs_batch;
+
+/* Captures [output zeroing unless opts->accumulate, work-counter reset,
+ * kernel] for these device buffers into a graph.  Device pointers only
+ * (opts->device_ptrs must be 1).  shower_bunch: host array of n_showers
+ * bunch sizes (>= 1), or NULL to use opts->bunch for every shower.  The
+ * buffers must stay valid and are re-read at every launch.  Errors:
+ * CS_ERR_INVALID_ARG, CS_ERR_CUDA. */
+cs_status cs_batch_create(const cs_segment* segs, size_t n, const cs_atmosphere* atm, const cs_detector* det,
+                          uint64_t seed, const int* shower_bunch, const cs_opts* opts, cs_output* out,
+                          cs_batch** out_batch);
+/* Replays the captured graph on `stream` (cudaStream_t). */
+cs_status cs_batch_launch(cs_batch* batch, void* stream);
+void cs_batch_destroy(cs_batch* batch);
+
+typedef struct cs_tune_result {
+    int blocks_per_sm;   /* fastest resident blocks per SM (256 threads each) */
+    int n_tried;
+    float ms[8];         /* mean kernel time per tried setting, index blocks_per_sm - 1 */
+} cs_tune_result;
+
+/* Times 1..4 resident blocks per SM on this batch (3 timed runs each after a
+ * warm-up, CUDA events on `stream`) and returns the fastest.  Overwrites the
+ * outputs.  Device pointers only. */
+cs_status cs_autotune_tiling(const cs_segment* segs, size_t n, const cs_atmosphere* atm, const cs_detector* det,
+                             uint64_t seed, const int* shower_bunch, const cs_opts* opts, cs_output* out,
+                             void* stream, cs_tune_result* result);
+
+/* Per-shower bunch sizes: a pilot run with the largest allowed bunch gives
+ * each shower's mean photon count c over its 100 densest ground cells;
+ * bunching multiplies a cell's variance by b, so the shower gets the largest
+ * allowed b with sqrt(b / c) <= rel_noise (else the smallest allowed).  Needs
+ * a ground histogram; overwrites the outputs; shower_bunch is a host array of
+ * n_showers.  Device pointers only. */
+cs_status cs_autotune_bunches(const cs_segment* segs, size_t n, const cs_atmosphere* atm, const cs_detector* det,
+                              uint64_t seed, double rel_noise, const int* allowed, int n_allowed,
+                              const cs_opts* opts, cs_output* out, void* stream, int* shower_bunch);
+
 /* Allocation-free form of the device-pointer call (the thesis has no
  * counterpart; this is a library service).  For callers that cannot let the
  * library allocate device memory: code running while a memory pool or arena

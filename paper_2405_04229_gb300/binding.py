@@ -71,6 +71,10 @@ class cs_output(C.Structure):
                 ("record_count", C.c_void_p)]
 
 
+class cs_tune_result(C.Structure):
+    _fields_ = [("blocks_per_sm", C.c_int), ("n_tried", C.c_int), ("ms", C.c_float * 8)]
+
+
 class cs_opts(C.Structure):
     _fields_ = [("bunch", C.c_int), ("s_max", C.c_double), ("seg_base", C.c_uint64),
                 ("device_ptrs", C.c_int), ("accumulate", C.c_int), ("block_threads", C.c_int),
@@ -107,6 +111,18 @@ def lib():
             L.cs_propagate_ex.argtypes = [vp, C.c_size_t, vp, vp, C.c_uint64, C.POINTER(cs_opts),
                                           C.POINTER(cs_output), vp]
             L.cs_propagate_ex.restype = st
+            L.cs_batch_create.argtypes = [vp, C.c_size_t, vp, vp, C.c_uint64, vp, C.POINTER(cs_opts),
+                                          C.POINTER(cs_output), C.POINTER(vp)]
+            L.cs_batch_create.restype = st
+            L.cs_batch_launch.argtypes = [vp, vp]
+            L.cs_batch_launch.restype = st
+            L.cs_batch_destroy.argtypes = [vp]
+            L.cs_autotune_tiling.argtypes = [vp, C.c_size_t, vp, vp, C.c_uint64, vp, C.POINTER(cs_opts),
+                                             C.POINTER(cs_output), vp, C.POINTER(cs_tune_result)]
+            L.cs_autotune_tiling.restype = st
+            L.cs_autotune_bunches.argtypes = [vp, C.c_size_t, vp, vp, C.c_uint64, C.c_double, vp, C.c_int,
+                                              C.POINTER(cs_opts), C.POINTER(cs_output), vp, vp]
+            L.cs_autotune_bunches.restype = st
             L.cs_propagate_noalloc.argtypes = L.cs_propagate_ex.argtypes
             L.cs_propagate_noalloc.restype = st
             L.cs_philox4x32_10.argtypes = [vp, C.c_size_t, C.c_uint32, C.c_uint32, vp, vp]
@@ -184,6 +200,40 @@ def cs_propagate(segs_ptr, n, atm, det, seed, out: cs_output):
 
 def cs_propagate_ex(segs_ptr, n, atm, det, seed, opts: cs_opts, out: cs_output, stream=None):
     return lib().cs_propagate_ex(segs_ptr, n, atm, det, seed, C.byref(opts), C.byref(out), stream)
+
+
+def cs_batch_create(segs_ptr, n, atm, det, seed, shower_bunch, opts: cs_opts, out: cs_output):
+    """shower_bunch: numpy int32 array (n_showers) or None."""
+    h = C.c_void_p()
+    sb = None if shower_bunch is None else np.ascontiguousarray(shower_bunch, np.int32)
+    _check(lib().cs_batch_create(segs_ptr, n, atm, det, seed, None if sb is None else _dptr(sb), C.byref(opts),
+                                 C.byref(out), C.byref(h)), "cs_batch_create")
+    return h
+
+
+def cs_batch_launch(batch, stream=None):
+    return lib().cs_batch_launch(batch, stream)
+
+
+def cs_batch_destroy(batch):
+    lib().cs_batch_destroy(batch)
+
+
+def cs_autotune_tiling(segs_ptr, n, atm, det, seed, shower_bunch, opts: cs_opts, out: cs_output, stream=None):
+    r = cs_tune_result()
+    sb = None if shower_bunch is None else np.ascontiguousarray(shower_bunch, np.int32)
+    _check(lib().cs_autotune_tiling(segs_ptr, n, atm, det, seed, None if sb is None else _dptr(sb), C.byref(opts),
+                                    C.byref(out), stream, C.byref(r)), "cs_autotune_tiling")
+    return r
+
+
+def cs_autotune_bunches(segs_ptr, n, atm, det, seed, rel_noise, allowed, opts: cs_opts, out: cs_output,
+                        n_showers, stream=None):
+    al = np.ascontiguousarray(allowed, np.int32)
+    res = np.zeros(n_showers, np.int32)
+    _check(lib().cs_autotune_bunches(segs_ptr, n, atm, det, seed, rel_noise, _dptr(al), len(al), C.byref(opts),
+                                     C.byref(out), stream, _dptr(res)), "cs_autotune_bunches")
+    return res
 
 
 def cs_propagate_noalloc(segs_ptr, n, atm, det, seed, opts: cs_opts, out: cs_output, stream=None):
@@ -331,3 +381,44 @@ def philox_device(ctr, key):
     _check(st, "cs_philox4x32_10")
     torch.cuda.synchronize()
     return o.cpu().numpy().view(np.uint32)
+
+
+class DeviceOutputs:
+    """Device output buffers (torch tensors) for a detector, with the matching
+    cs_output struct."""
+
+    def __init__(self, det: Detector, record_capacity=0, device="cuda:0"):
+        import torch
+        self.torch = torch
+        d = torch.device(device)
+        self.hist = torch.zeros((det.n_showers, max(det.ny, 1), max(det.nx, 1)), dtype=torch.int64, device=d)
+        self.tel_counts = torch.zeros((det.n_showers, max(det.n_tel, 1)), dtype=torch.int64, device=d)
+        self.tel_time = torch.zeros((det.n_showers, max(det.n_tel, 1)), dtype=torch.float64, device=d)
+        self.counters = torch.zeros(CS_N_COUNTERS, dtype=torch.int64, device=d)
+        self.record_count = torch.zeros(1, dtype=torch.int64, device=d)
+        self.records = torch.zeros(record_capacity * RECORD_DTYPE.itemsize, dtype=torch.uint8, device=d) \
+            if record_capacity else None
+        o = cs_output()
+        o.hist = self.hist.data_ptr() if det.nx else None
+        o.tel_counts = self.tel_counts.data_ptr() if det.n_tel else None
+        o.tel_time = self.tel_time.data_ptr() if det.n_tel else None
+        o.counters = self.counters.data_ptr()
+        o.record_count = self.record_count.data_ptr()
+        if record_capacity:
+            o.records, o.record_capacity = self.records.data_ptr(), record_capacity
+        self.out = o
+
+    def host(self):
+        self.torch.cuda.synchronize()
+        r = dict(hist=self.hist.cpu().numpy().astype(np.uint64), tel_counts=self.tel_counts.cpu().numpy().astype(np.uint64),
+                 tel_time=self.tel_time.cpu().numpy(), counters=self.counters.cpu().numpy().astype(np.uint64),
+                 n_records=int(self.record_count.item()))
+        if self.records is not None:
+            n = min(r["n_records"], self.out.record_capacity)
+            r["records"] = self.records[: n * RECORD_DTYPE.itemsize].cpu().numpy().view(RECORD_DTYPE)
+        return r
+
+
+def stream_ptr():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)

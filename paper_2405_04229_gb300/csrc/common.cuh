@@ -90,7 +90,8 @@ struct PropParams {
     long long n;
     unsigned long long seg_base;
     uint32_t key0, key1;
-    int bunch;
+    int bunch;                 // photons per bunch when shower_bunch is null
+    const int* shower_bunch;   // per-shower bunch sizes (device), or null
     float s_max;
 };
 

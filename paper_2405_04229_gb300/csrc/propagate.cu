@@ -16,7 +16,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <mutex>
+#include <vector>
 
 #include "device_math.cuh"
 
@@ -40,6 +42,7 @@ struct TileSmem {
     double t0[kTile];
     float g[kTile], z2[kTile];
     int shower[kTile];
+    int bunch[kTile];     // photons per bunch of the segment's shower
     int offK[kTile + 1];
     float4 sub[kSubCap];  // cos(theta), sin(theta), n - 1, segment | k << 8
     int nsub_ph[kSubCap]; // bunches of each sub-step
@@ -149,6 +152,7 @@ __device__ __forceinline__ int import_segment(TileSmem& S, int t, const cs_segme
     S.g[t] = g;
     S.z2[t] = z * z;
     S.shower[t] = (int)shower;
+    S.bunch[t] = pp.shower_bunch ? __ldg(pp.shower_bunch + shower) : pp.bunch;
     return K;
 }
 
@@ -156,7 +160,7 @@ __device__ __forceinline__ int import_segment(TileSmem& S, int t, const cs_segme
 // slot q: angle and mean bunch count at the sub-step midpoint, stochastic
 // rounding with the sub-step's own draw.  Returns the bunch count.
 __device__ __forceinline__ int substep(TileSmem& S, int q, int sg, int k, long long base, const PropParams& pp,
-                                       const AtmParams& ap, float inv_b) {
+                                       const AtmParams& ap) {
     const float4 B = S.segB[sg];
     const float Pz = S.segA[sg].z;
     const float dz_mid = B.x + (B.y + ((float)k + 0.5f) * B.z * Pz);
@@ -166,7 +170,7 @@ __device__ __forceinline__ int substep(TileSmem& S, int q, int sg, int k, long l
     // 1 - 1/(beta n)^2 without forming 1/(beta n)^2 (cancellation-free)
     const float sin2 = (d * (2.0f + d) - onepd * onepd * g) * rcp_approx(onepd * onepd * (1.0f - g));
     float nbar = 0.0f;
-    if (sin2 > 0.0f) nbar = ap.ft * S.z2[sg] * sin2 * B.z * inv_b;
+    if (sin2 > 0.0f) nbar = ap.ft * S.z2[sg] * sin2 * B.z / (float)S.bunch[sg];
     const unsigned long long gid = pp.seg_base + (unsigned long long)(base + sg);
     const uint4 rc = philox((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0xFFFFFFFFu, pp.key0, pp.key1);
     const float uk = uniform24(rc.x);
@@ -197,6 +201,7 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, long long
     const float u0 = uniform24(r4.x), u1 = uniform24(r4.y), u2 = uniform24(r4.z), u3 = uniform24(r4.w);
     const float4 A = S.segA[sg], B = S.segB[sg];
     const float Px = A.x, Py = A.y, Pz = A.z;
+    const unsigned int b = (unsigned int)S.bunch[sg];
     // translation to a random point of the sub-step (Fig. 4.2c)
     const float ell = ((float)k + u0) * B.z;
     const float dz = B.x + (B.y + ell * Pz);
@@ -279,7 +284,7 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, long long
                     const int iy = (int)floorf(D.z + fmaf(ry, dp.inv_dy, D.w));
                     if (ix >= 0 && ix < dp.nx && iy >= 0 && iy < dp.ny) {
                         bin = iy * dp.nx + ix;
-                        atomicAdd(op.hist + ((size_t)sh * dp.ny * dp.nx + bin), (unsigned long long)pp.bunch);
+                        atomicAdd(op.hist + ((size_t)sh * dp.ny * dp.nx + bin), (unsigned long long)b);
                     }
                 }
                 // telescopes: distance from the sphere centre to the arrival line below the radius
@@ -319,17 +324,17 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, long long
                     }
                     if (tel >= 0) {
                         const size_t slot = (size_t)sh * dp.n_tel + tel;
-                        atomicAdd(op.tel_counts + slot, (unsigned long long)pp.bunch);
-                        if (op.tel_time) atomicAdd(op.tel_time + slot, (double)pp.bunch * (S.t0[sg] + (double)t_rel));
+                        atomicAdd(op.tel_counts + slot, (unsigned long long)b);
+                        if (op.tel_time) atomicAdd(op.tel_time + slot, (double)b * (S.t0[sg] + (double)t_rel));
                     }
                 }
             }
         }
     }
-    T.absorbed += status == CS_ST_ABSORBED;
-    T.upward += status == CS_ST_UPWARD;
-    T.hist += bin >= 0;
-    T.tel += tel >= 0;
+    T.absorbed += status == CS_ST_ABSORBED ? b : 0;
+    T.upward += status == CS_ST_UPWARD ? b : 0;
+    T.hist += bin >= 0 ? b : 0;
+    T.tel += tel >= 0 ? b : 0;
     if (want_records) emit_record(op, gid, k, i, x, y, t_rel, inv_l, tel, bin, status);
 }
 
@@ -339,7 +344,6 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
     const int t = threadIdx.x;
-    const float inv_b = 1.0f / (float)pp.bunch;
     const bool want_records = op.records != nullptr;
     const long long n_tiles = (pp.n + kTile - 1) / kTile;
     unsigned int emitted = 0, invalid = 0;
@@ -368,6 +372,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
             const int per = (nsub + kThreads - 1) / kThreads;
             const int q0 = min(t * per, nsub), q1 = min(q0 + per, nsub);
             int my_ph = 0;
+            unsigned int my_emit = 0;
             if (q0 < q1) {
                 int lo = 0, hi = kTile;   // offK[lo] <= sub0 + q0 < offK[lo + 1]
                 const int first = sub0 + q0;
@@ -380,12 +385,14 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                 for (int q = q0; q < q1; ++q) {
                     const int qq = sub0 + q;
                     while (S.offK[sg + 1] <= qq) ++sg;   // next non-empty segment
-                    my_ph += substep(S, q, sg, qq - S.offK[sg], base, pp, ap, inv_b);
+                    const int N = substep(S, q, sg, qq - S.offK[sg], base, pp, ap);
+                    my_ph += N;
+                    my_emit += (unsigned int)N * (unsigned int)S.bunch[sg];
                 }
             }
             int M;
             const int ph0 = block_scan(my_ph, S.wsum, buf, &M);
-            emitted += (unsigned int)my_ph * (unsigned int)pp.bunch;
+            emitted += my_emit;
 
             // ---- stages 3-5 over windows of the bunch map ------------------------
             for (int p0 = 0; p0 < M; p0 += kMapCap) {
@@ -411,15 +418,14 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
     // ---- counter flush: missed = emitted - absorbed - detected.  A thread's
     // emitted bunches and the bunches it propagated are different sets, so the
     // per-thread differences are signed; their 64-bit sum (mod 2^64) is exact.
-    const int b = pp.bunch;
     int v[CS_N_COUNTERS];
     v[CS_CNT_EMITTED] = (int)emitted;
-    v[CS_CNT_ABSORBED] = (int)T.absorbed * b;
-    v[CS_CNT_HIST] = (int)T.hist * b;
-    v[CS_CNT_TEL] = (int)T.tel * b;
-    v[CS_CNT_MISSED_HIST] = (int)emitted - ((int)T.absorbed + (int)T.hist) * b;
-    v[CS_CNT_MISSED_TEL] = (int)emitted - ((int)T.absorbed + (int)T.tel) * b;
-    v[CS_CNT_UPWARD] = (int)T.upward * b;
+    v[CS_CNT_ABSORBED] = (int)T.absorbed;
+    v[CS_CNT_HIST] = (int)T.hist;
+    v[CS_CNT_TEL] = (int)T.tel;
+    v[CS_CNT_MISSED_HIST] = (int)emitted - (int)T.absorbed - (int)T.hist;
+    v[CS_CNT_MISSED_TEL] = (int)emitted - (int)T.absorbed - (int)T.tel;
+    v[CS_CNT_UPWARD] = (int)T.upward;
     v[CS_CNT_INVALID_SEGMENTS] = (int)invalid;
 #pragma unroll
     for (int c = 0; c < CS_N_COUNTERS; ++c) {
@@ -503,6 +509,7 @@ cs_status launch(const cs_segment* d_segs, size_t n, const cs_atmosphere* atm, c
     pp.key0 = (uint32_t)seed;
     pp.key1 = (uint32_t)(seed >> 32);
     pp.bunch = o.bunch;
+    pp.shower_bunch = nullptr;
     pp.s_max = (float)o.s_max;
     const size_t smem = sizeof(TileSmem);
     static bool attr_done = false;
@@ -700,6 +707,7 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     pp.key0 = (uint32_t)seed;
     pp.key1 = (uint32_t)(seed >> 32);
     pp.bunch = o.bunch;
+    pp.shower_bunch = nullptr;
     pp.s_max = (float)o.s_max;
     OutParams op;
     op.hist = (unsigned long long*)out->hist;
@@ -718,5 +726,265 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), stream));
     propagate_kernel<<<(unsigned)grid, kThreads, smem, stream>>>(pp, atm->p, dp, op, ctr);
     CS_CUDA_TRY(cudaGetLastError());
+    return CS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched uneven showers: one persistent launch over many showers of uneven
+// size (the dynamic tile scheduler balances them), captured once into a CUDA
+// graph and replayed; plus the autotuner for block tiling and per-shower
+// bunch sizes.
+// ---------------------------------------------------------------------------
+struct cs_batch {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned int* d_ctr = nullptr;   // the batch's own tile counter
+    int* d_bunch = nullptr;          // per-shower bunch sizes
+    int device = 0;
+};
+
+namespace cs {
+namespace {
+
+cs_status check_device_call(const cs_segment* segs, size_t n, const cs_atmosphere* atm, const cs_detector* det,
+                            const cs_opts& o, const cs_output* out) {
+    if (!atm || !det || !out || !out->counters) return CS_ERR_INVALID_ARG;
+    if (o.bunch < 1 || !(o.s_max > 0.0) || (n > 0 && !segs) || !o.device_ptrs) return CS_ERR_INVALID_ARG;
+    if (((uintptr_t)segs & 15) != 0) return CS_ERR_INVALID_ARG;
+    if (det->p.nx > 0 && !out->hist) return CS_ERR_INVALID_ARG;
+    if (det->p.n_tel > 0 && !out->tel_counts) return CS_ERR_INVALID_ARG;
+    if (out->records && !out->record_count) return CS_ERR_INVALID_ARG;
+    if (fabs(det->p.h_obs - atm->p.h_obs) > 1e-9 * fmax(1.0, fabs(atm->p.h_obs))) return CS_ERR_INVALID_ARG;
+    if (n > (size_t)1 << 40) return CS_ERR_INVALID_ARG;
+    return CS_OK;
+}
+
+// Grid of the persistent launch; also sets the kernel's shared-memory limit
+// (host-side calls kept out of stream capture).
+cs_status prepare_launch(size_t n, const cs_opts& o, unsigned int* grid) {
+    const size_t smem = sizeof(TileSmem);
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int per_sm = o.blocks_per_sm > 0 ? o.blocks_per_sm : 4;
+    const long long tiles = ((long long)n + kTile - 1) / kTile;
+    *grid = (unsigned)std::max<long long>(1, std::min<long long>(tiles, (long long)device_sm_count() * per_sm));
+    return CS_OK;
+}
+
+// Zeroing (unless accumulating), counter reset and the kernel, on `stream`;
+// only stream operations, so it can be captured.
+cs_status enqueue(const cs_segment* segs, size_t n, const cs_atmosphere* atm, const cs_detector* det,
+                  uint64_t seed, const int* d_bunch, const cs_opts& o, const cs_output* out, unsigned int* ctr,
+                  unsigned int grid, cudaStream_t stream) {
+    const DetParams& dp = det->p;
+    if (!o.accumulate) {
+        if (out->hist) CS_CUDA_TRY(cudaMemsetAsync(out->hist, 0, (size_t)dp.n_showers * dp.nx * dp.ny * 8, stream));
+        if (out->tel_counts) CS_CUDA_TRY(cudaMemsetAsync(out->tel_counts, 0, (size_t)dp.n_showers * dp.n_tel * 8, stream));
+        if (out->tel_time) CS_CUDA_TRY(cudaMemsetAsync(out->tel_time, 0, (size_t)dp.n_showers * dp.n_tel * 8, stream));
+        CS_CUDA_TRY(cudaMemsetAsync(out->counters, 0, CS_N_COUNTERS * 8, stream));
+        if (out->record_count) CS_CUDA_TRY(cudaMemsetAsync(out->record_count, 0, 8, stream));
+    }
+    if (n == 0) return CS_OK;
+    PropParams pp;
+    pp.segs = segs;
+    pp.n = (long long)n;
+    pp.seg_base = o.seg_base;
+    pp.key0 = (uint32_t)seed;
+    pp.key1 = (uint32_t)(seed >> 32);
+    pp.bunch = o.bunch;
+    pp.shower_bunch = d_bunch;
+    pp.s_max = (float)o.s_max;
+    OutParams op;
+    op.hist = (unsigned long long*)out->hist;
+    op.tel_counts = (unsigned long long*)out->tel_counts;
+    op.tel_time = out->tel_time;
+    op.counters = (unsigned long long*)out->counters;
+    op.records = out->records;
+    op.record_capacity = out->records ? out->record_capacity : 0;
+    op.record_count = (unsigned long long*)out->record_count;
+    CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), stream));
+    propagate_kernel<<<grid, kThreads, sizeof(TileSmem), stream>>>(pp, atm->p, dp, op, ctr);
+    CS_CUDA_TRY(cudaGetLastError());
+    return CS_OK;
+}
+
+cs_status upload_bunches(const cs_detector* det, const int* shower_bunch, int** d_bunch) {
+    *d_bunch = nullptr;
+    if (!shower_bunch) return CS_OK;
+    for (int s = 0; s < det->p.n_showers; ++s)
+        if (shower_bunch[s] < 1) return CS_ERR_INVALID_ARG;
+    CS_CUDA_TRY(cudaMalloc(d_bunch, sizeof(int) * det->p.n_showers));
+    cudaError_t e = cudaMemcpy(*d_bunch, shower_bunch, sizeof(int) * det->p.n_showers, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        set_last_error("bunch upload", e);
+        cudaFree(*d_bunch);
+        *d_bunch = nullptr;
+        return CS_ERR_CUDA;
+    }
+    return CS_OK;
+}
+
+}  // namespace
+}  // namespace cs
+
+extern "C" cs_status cs_batch_create(const cs_segment* segs, size_t n, const cs_atmosphere* atm,
+                                     const cs_detector* det, uint64_t seed, const int* shower_bunch,
+                                     const cs_opts* opts, cs_output* out, cs_batch** out_batch) {
+    if (!out_batch) return CS_ERR_INVALID_ARG;
+    *out_batch = nullptr;
+    cs_opts o;
+    if (opts) o = *opts; else cs_opts_default(&o);
+    cs_status st = check_device_call(segs, n, atm, det, o, out);
+    if (st != CS_OK) return st;
+    cs_batch* b = new cs_batch;
+    cudaGetDevice(&b->device);
+    cudaStream_t cap = nullptr;
+    auto fail = [&](cs_status s) {
+        if (cap) cudaStreamDestroy(cap);
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        cudaFree(b->d_ctr);
+        cudaFree(b->d_bunch);
+        delete b;
+        return s;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->d_ctr, 256)) != cudaSuccess) { set_last_error("batch counter", e); return fail(CS_ERR_CUDA); }
+    if ((st = upload_bunches(det, shower_bunch, &b->d_bunch)) != CS_OK) return fail(st);
+    unsigned int grid = 1;
+    if ((st = prepare_launch(n, o, &grid)) != CS_OK) return fail(st);
+    if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) {
+        set_last_error("capture stream", e);
+        return fail(CS_ERR_CUDA);
+    }
+    if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        set_last_error("begin capture", e);
+        return fail(CS_ERR_CUDA);
+    }
+    st = enqueue(segs, n, atm, det, seed, b->d_bunch, o, out, b->d_ctr, grid, cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    b->graph = g;
+    if (st != CS_OK) return fail(st);
+    if (e != cudaSuccess) { set_last_error("end capture", e); return fail(CS_ERR_CUDA); }
+    if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) {
+        set_last_error("graph instantiate", e);
+        return fail(CS_ERR_CUDA);
+    }
+    cudaStreamDestroy(cap);
+    *out_batch = b;
+    return CS_OK;
+}
+
+extern "C" cs_status cs_batch_launch(cs_batch* b, void* stream) {
+    if (!b || !b->exec) return CS_ERR_INVALID_ARG;
+    CS_CUDA_TRY(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    return CS_OK;
+}
+
+extern "C" void cs_batch_destroy(cs_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->d_ctr);
+    cudaFree(b->d_bunch);
+    delete b;
+}
+
+extern "C" cs_status cs_autotune_tiling(const cs_segment* segs, size_t n, const cs_atmosphere* atm,
+                                        const cs_detector* det, uint64_t seed, const int* shower_bunch,
+                                        const cs_opts* opts, cs_output* out, void* stream_,
+                                        cs_tune_result* res) {
+    if (!res) return CS_ERR_INVALID_ARG;
+    cs_opts o;
+    if (opts) o = *opts; else cs_opts_default(&o);
+    cs_status st = check_device_call(segs, n, atm, det, o, out);
+    if (st != CS_OK) return st;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    int* d_bunch = nullptr;
+    if ((st = upload_bunches(det, shower_bunch, &d_bunch)) != CS_OK) return st;
+    unsigned int* ctr = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e;
+    auto done = [&](cs_status s) {
+        cudaFree(d_bunch);
+        cudaFree(ctr);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return s;
+    };
+    if ((e = cudaMalloc(&ctr, 256)) != cudaSuccess) { set_last_error("tune counter", e); return done(CS_ERR_CUDA); }
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        set_last_error("tune events", e);
+        return done(CS_ERR_CUDA);
+    }
+    memset(res, 0, sizeof *res);
+    float best = 3.0e38f;
+    for (int bpm = 1; bpm <= 4; ++bpm) {
+        o.blocks_per_sm = bpm;
+        unsigned int grid = 1;
+        if ((st = prepare_launch(n, o, &grid)) != CS_OK) return done(st);
+        if ((st = enqueue(segs, n, atm, det, seed, d_bunch, o, out, ctr, grid, stream)) != CS_OK) return done(st);
+        float total = 0.0f;
+        for (int r = 0; r < 3; ++r) {
+            float ms = 0.0f;
+            if ((e = cudaEventRecord(e0, stream)) != cudaSuccess) { set_last_error("tune", e); return done(CS_ERR_CUDA); }
+            if ((st = enqueue(segs, n, atm, det, seed, d_bunch, o, out, ctr, grid, stream)) != CS_OK) return done(st);
+            if ((e = cudaEventRecord(e1, stream)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+                (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+                set_last_error("tune timing", e);
+                return done(CS_ERR_CUDA);
+            }
+            total += ms;
+        }
+        res->ms[bpm - 1] = total / 3.0f;
+        res->n_tried = bpm;
+        if (res->ms[bpm - 1] < best) {
+            best = res->ms[bpm - 1];
+            res->blocks_per_sm = bpm;
+        }
+    }
+    return done(CS_OK);
+}
+
+extern "C" cs_status cs_autotune_bunches(const cs_segment* segs, size_t n, const cs_atmosphere* atm,
+                                         const cs_detector* det, uint64_t seed, double rel_noise,
+                                         const int* allowed, int n_allowed, const cs_opts* opts, cs_output* out,
+                                         void* stream_, int* shower_bunch) {
+    if (!allowed || n_allowed < 1 || !shower_bunch || !(rel_noise > 0.0)) return CS_ERR_INVALID_ARG;
+    if (det && det->p.nx <= 0) return CS_ERR_INVALID_ARG;   // the rule reads the ground histogram
+    cs_opts o;
+    if (opts) o = *opts; else cs_opts_default(&o);
+    int bmin = allowed[0], bmax = allowed[0];
+    for (int i = 0; i < n_allowed; ++i) {
+        if (allowed[i] < 1) return CS_ERR_INVALID_ARG;
+        bmin = std::min(bmin, allowed[i]);
+        bmax = std::max(bmax, allowed[i]);
+    }
+    o.bunch = bmax;
+    o.accumulate = 0;
+    cs_status st = check_device_call(segs, n, atm, det, o, out);
+    if (st != CS_OK) return st;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    // pilot run with the largest bunch: per-shower photon density in the light-pool core
+    st = cs_propagate_ex(segs, n, atm, det, seed, &o, out, stream);
+    if (st != CS_OK) return st;
+    const DetParams& dp = det->p;
+    const size_t cells = (size_t)dp.nx * dp.ny;
+    std::vector<unsigned long long> h(cells * dp.n_showers);
+    CS_CUDA_TRY(cudaMemcpyAsync(h.data(), out->hist, h.size() * 8, cudaMemcpyDeviceToHost, stream));
+    CS_CUDA_TRY(cudaStreamSynchronize(stream));
+    const size_t top = std::min<size_t>(100, cells);
+    for (int s = 0; s < dp.n_showers; ++s) {
+        auto first = h.begin() + (size_t)s * cells, last = first + cells;
+        std::nth_element(first, first + (top - 1), last, std::greater<unsigned long long>());
+        double mean = 0.0;
+        for (size_t i = 0; i < top; ++i) mean += (double)first[i];
+        mean /= (double)top;
+        // bunching multiplies a cell's variance by b: keep sqrt(b / mean) <= rel_noise
+        int pick = bmin;
+        for (int i = 0; i < n_allowed; ++i)
+            if (allowed[i] > pick && sqrt((double)allowed[i] / fmax(mean, 1e-300)) <= rel_noise) pick = allowed[i];
+        shower_bunch[s] = pick;
+    }
     return CS_OK;
 }
