@@ -239,6 +239,7 @@ def main():
     ap.add_argument("--per-shower", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -348,6 +349,37 @@ def main():
     except Exception:
         pass
 
+    # the surrogate form: the network replaces the table lookups inside its domain
+    surrogate = None
+    if not args.no_surrogate:
+        t_tr = time.perf_counter()
+        sur = B.Surrogate(atm)
+        train_s = time.perf_counter() - t_tr
+        o.surrogate = sur.handle
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        s_photons = int(cnt[0].item())
+        s_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for a, b_ in s_ev:
+            flush.zero_()
+            a.record(stream)
+            step()
+            b_.record(stream)
+        torch.cuda.synchronize()
+        s_ms = sum(a.elapsed_time(b_) for a, b_ in s_ev)
+        o.surrogate = None
+        s_value = s_photons * args.steps / (s_ms / 1e3)
+        surrogate = {"value": s_value, "unit": UNIT, "ms_per_step": s_ms / args.steps,
+                     "speedup_vs_exact": s_value / (photons_per_step * args.steps / (ms_max / 1e3)),
+                     "heldout_p99": {"displacement_m": sur.stats["p99"][0], "delay_s": sur.stats["p99"][1],
+                                     "transmission": sur.stats["p99"][2]},
+                     "heldout_max": {"displacement_m": sur.stats["max"][0], "delay_s": sur.stats["max"][1],
+                                     "transmission": sur.stats["max"][2]},
+                     "train_seconds": round(train_s, 2), "train_steps": sur.stats["steps"],
+                     "network": "MLP 3-64-64-64-3 tanh, BF16 weights, FP32 accumulation (mma.sync m16n8k16)"}
+        sur.close()
+
     e2e = None
     if not args.no_e2e:
         # end to end through the host-pointer call: pinned segments in, outputs out
@@ -404,6 +436,7 @@ def main():
                                  "x max SM clock"},
             "kernel_ms": k_ms,
             "cpu_baseline": cpu,
+            "surrogate": surrogate,
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": sm_clk,

@@ -182,6 +182,8 @@ typedef struct cs_output {
     uint64_t* record_count;  /* 1 element: records produced (may exceed the capacity) */
 } cs_output;
 
+typedef struct cs_surrogate cs_surrogate;
+
 typedef struct cs_opts {
     int bunch;               /* photons per bunch, >= 1 */
     double s_max;            /* maximum sub-step length [m] (Sec. 4.2.1), > 0 */
@@ -190,6 +192,8 @@ typedef struct cs_opts {
     int accumulate;          /* 0: outputs are zeroed before the call; 1: added to */
     int block_threads;       /* 0 = default */
     int blocks_per_sm;       /* 0 = default */
+    const cs_surrogate* surrogate;  /* NULL: exact tracer (tables); else the network replaces the
+                                       refraction/time/transmission lookups inside its domain */
 } cs_opts;
 
 /* Defaults: bunch 1, s_max 1 m, seg_base 0, host pointers, no accumulation. */
@@ -254,6 +258,67 @@ cs_status cs_autotune_tiling(const cs_segment* segs, size_t n, const cs_atmosphe
 cs_status cs_autotune_bunches(const cs_segment* segs, size_t n, const cs_atmosphere* atm, const cs_detector* det,
                               uint64_t seed, double rel_noise, const int* allowed, int n_allowed,
                               const cs_opts* opts, cs_output* out, void* stream, int* shower_bunch);
+
+/* ------------------------------------------------------------------------
+ * Learned surrogate of the refraction integral (no thesis counterpart; the
+ * thesis's interpolation tracer of Sec. 4.4.1 is what it replaces).  A tanh
+ * MLP 3 -> 64 -> 64 -> 64 -> 3 maps (emission height, cos(zenith),
+ * 1/wavelength) to the displacement field G_R, the delay field G_t and the
+ * transmission T.  Training samples have uniform height in [h_min, h_max],
+ * uniform zenith in [0, theta_max] and uniform wavelength in the atmosphere's
+ * band (minus bands around the layer boundaries, where n(h) and hence the
+ * exact fields are discontinuous), labelled by the FP64 quadrature of the
+ * exact path.  Hidden layers run
+ * on the tensor cores (BF16 weights, FP32 accumulation); the 3-input layer
+ * runs in FP32.  Outside its domain the photon kernel uses the tables.
+ * ---------------------------------------------------------------------- */
+typedef struct cs_surrogate_config {
+    int n_train;             /* training samples (default 2^20) */
+    int n_heldout;           /* held-out samples (default 2^16) */
+    int batch;               /* mini-batch (default 16384) */
+    int epochs;              /* passes over the training set (default 800) */
+    uint64_t seed;
+    double lr, lr_min;       /* Adam learning rate (default 1e-2), cosine-decayed to lr_min (1e-5) */
+    double h_min, h_max;     /* emission heights [m] (default 2 km .. 30 km) */
+    double theta_max;        /* largest zenith [rad] (default 60 deg) */
+    int split_activations;   /* 1: hidden activations enter the MMAs as BF16 hi + lo pairs */
+    double boundary_band;    /* half-width [m] of the bands around layer boundaries left to the tables
+                                (the exact fields jump there with n(h_e)); default 500 m */
+    double height_scale;     /* > 0: the height enters as exp(-(h - h_obs) / height_scale) (default
+                                8 km, the fields are nearly linear in this density-like coordinate);
+                                0: linear in h */
+} cs_surrogate_config;
+
+typedef struct cs_surrogate_stats {
+    double heldout_p99[3];   /* held-out 99th percentile |error|: displacement [m], delay [s], transmission */
+    double heldout_max[3];   /* held-out maximum |error|, same order */
+    double final_loss;       /* MSE of the last mini-batch (normalised targets) */
+    int steps;
+    double train_seconds;
+} cs_surrogate_stats;
+
+void cs_surrogate_config_default(cs_surrogate_config* cfg);
+/* Samples, labels and trains on the device of `atm` (which must have
+ * refraction on); errors against the held-out set go to *stats. */
+cs_status cs_surrogate_train(const cs_atmosphere* atm, const cs_surrogate_config* cfg, cs_surrogate** out,
+                             cs_surrogate_stats* stats);
+void cs_surrogate_destroy(cs_surrogate* s);
+/* Runs the network (the photon kernel's inference code) on device float4
+ * inputs {h_e - h_obs [m], cos(theta0), 1/lambda [1/nm], unused}; writes
+ * float4 {G_R [m], G_t [m], T, 0}.  16-byte aligned device pointers. */
+cs_status cs_surrogate_eval(const cs_surrogate* s, const float* d_in, size_t n, float* d_out, void* stream);
+/* Host copies of the parameters as inference uses them (flat FP32, the
+ * tensor-core weights already rounded to BF16; layout W1[64][3] b1[64]
+ * W2[64][64] b2 W3[64][64] b3 W4[8][64] b4[8]), the training statistics, and
+ * 15 normalisation floats (input scale[3], shift[3], output half-range[3],
+ * mid[3], dz_min, dz_max, cos(theta_max)).  Any pointer may be NULL. */
+cs_status cs_surrogate_info(const cs_surrogate* s, float* params, size_t n_params, cs_surrogate_stats* stats,
+                            float* norm);
+/* One forward and backward pass of the training path on B rows (host
+ * arrays: params in the layout above, x and t B x 3 normalised): the loss
+ * (1/B) sum (y - t)^2 and its gradient (host, same layout).  For checking
+ * the tensor-core training kernels against a reference. */
+cs_status cs_mlp_loss_grad(const float* params, const float* x, const float* t, int B, float* grad, float* loss);
 
 /* Allocation-free form of the device-pointer call (the thesis has no
  * counterpart; this is a library service).  For callers that cannot let the

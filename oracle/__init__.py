@@ -101,6 +101,12 @@ def lib():
             L.orc_propagate.argtypes = [C.c_void_p, C.c_size_t, C.POINTER(Atm), C.POINTER(Config),
                                         C.POINTER(Output)]
             L.orc_propagate.restype = C.c_int
+            L.orc_mlp_n_params.argtypes = [C.c_int, C.c_int, C.c_int]
+            L.orc_mlp_n_params.restype = C.c_size_t
+            L.orc_mlp_forward.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp, C.c_int, dp, dp]
+            L.orc_mlp_loss_grad.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, dp]
+            L.orc_mlp_loss_grad.restype = d
+            L.orc_adam.argtypes = [dp, dp, dp, dp, C.c_size_t, d, d, d, d, C.c_int]
             for f in ("orc_sizeof_segment", "orc_sizeof_record", "orc_sizeof_config", "orc_sizeof_atm"):
                 getattr(L, f).restype = C.c_size_t
             assert L.orc_sizeof_segment() == SEGMENT_DTYPE.itemsize
@@ -273,3 +279,40 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
             raise RuntimeError("record capacity %d too small (%d)" % (cap, out.count))
         res["records"] = rec[: out.count].copy()
     return res
+
+
+# ---------------------------------------------------------------------------
+# surrogate network (FP64)
+# ---------------------------------------------------------------------------
+def _p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def mlp_n_params(din=3, dh=64, dout=3):
+    return int(lib().orc_mlp_n_params(din, dh, dout))
+
+
+def mlp_forward(theta, x, din=3, dh=64, dout=3, return_acts=False):
+    theta = np.ascontiguousarray(theta, np.float64)
+    x = np.ascontiguousarray(x, np.float64)
+    B = x.shape[0]
+    y = np.zeros((B, dout))
+    acts = np.zeros((B, 3, dh)) if return_acts else None
+    lib().orc_mlp_forward(_p(theta), din, dh, dout, _p(x), B, _p(y), _p(acts) if return_acts else None)
+    return (y, acts) if return_acts else y
+
+
+def mlp_loss_grad(theta, x, t, din=3, dh=64, dout=3):
+    theta = np.ascontiguousarray(theta, np.float64)
+    x = np.ascontiguousarray(x, np.float64)
+    t = np.ascontiguousarray(t, np.float64)
+    g = np.zeros_like(theta)
+    loss = lib().orc_mlp_loss_grad(_p(theta), din, dh, dout, _p(x), _p(t), x.shape[0], _p(g))
+    return loss, g
+
+
+def adam(theta, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
+    for a in (theta, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    grad = np.ascontiguousarray(grad, np.float64)
+    lib().orc_adam(_p(theta), _p(grad), _p(m), _p(v), theta.size, lr, beta1, beta2, eps, step)

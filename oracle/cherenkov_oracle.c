@@ -730,3 +730,140 @@ size_t orc_sizeof_segment(void) { return sizeof(orc_segment); }
 size_t orc_sizeof_record(void) { return sizeof(orc_record); }
 size_t orc_sizeof_config(void) { return sizeof(orc_config); }
 size_t orc_sizeof_atm(void) { return sizeof(orc_atm); }
+
+/* ------------------------------------------------------------------ */
+/* Surrogate network (no thesis counterpart): a tanh MLP              */
+/* din -> dh -> dh -> dh -> dout in FP64, MSE loss and Adam.          */
+/* Parameters are one flat array: W1 (dh x din), b1, W2 (dh x dh),    */
+/* b2, W3 (dh x dh), b3, W4 (dout x dh), b4; W rows are output units. */
+/* ------------------------------------------------------------------ */
+size_t orc_mlp_n_params(int din, int dh, int dout)
+{
+    return (size_t)dh * din + dh + 2 * ((size_t)dh * dh + dh) + (size_t)dout * dh + dout;
+}
+
+static void orc_dense(const double* W, const double* b, const double* x, int nin, int nout, double* z)
+{
+    for (int o = 0; o < nout; ++o) {
+        double s = b[o];
+        for (int i = 0; i < nin; ++i) s += W[(size_t)o * nin + i] * x[i];
+        z[o] = s;
+    }
+}
+
+/* y (B x dout); acts, if given, receives the three hidden layers' outputs
+ * (B x 3 x dh). */
+void orc_mlp_forward(const double* theta, int din, int dh, int dout, const double* x, int B, double* y,
+                     double* acts)
+{
+    const double* W1 = theta;
+    const double* b1 = W1 + (size_t)dh * din;
+    const double* W2 = b1 + dh;
+    const double* b2 = W2 + (size_t)dh * dh;
+    const double* W3 = b2 + dh;
+    const double* b3 = W3 + (size_t)dh * dh;
+    const double* W4 = b3 + dh;
+    const double* b4 = W4 + (size_t)dout * dh;
+    double* h1 = malloc(sizeof(double) * dh);
+    double* h2 = malloc(sizeof(double) * dh);
+    double* h3 = malloc(sizeof(double) * dh);
+    for (int r = 0; r < B; ++r) {
+        orc_dense(W1, b1, x + (size_t)r * din, din, dh, h1);
+        for (int j = 0; j < dh; ++j) h1[j] = tanh(h1[j]);
+        orc_dense(W2, b2, h1, dh, dh, h2);
+        for (int j = 0; j < dh; ++j) h2[j] = tanh(h2[j]);
+        orc_dense(W3, b3, h2, dh, dh, h3);
+        for (int j = 0; j < dh; ++j) h3[j] = tanh(h3[j]);
+        orc_dense(W4, b4, h3, dh, dout, y + (size_t)r * dout);
+        if (acts) {
+            memcpy(acts + ((size_t)r * 3 + 0) * dh, h1, sizeof(double) * dh);
+            memcpy(acts + ((size_t)r * 3 + 1) * dh, h2, sizeof(double) * dh);
+            memcpy(acts + ((size_t)r * 3 + 2) * dh, h3, sizeof(double) * dh);
+        }
+    }
+    free(h1); free(h2); free(h3);
+}
+
+/* Loss L = (1/B) sum_r sum_o (y_ro - t_ro)^2 and its gradient with respect
+ * to every parameter (same flat layout), by the chain rule layer by layer. */
+double orc_mlp_loss_grad(const double* theta, int din, int dh, int dout, const double* x, const double* t,
+                         int B, double* grad)
+{
+    const size_t np = orc_mlp_n_params(din, dh, dout);
+    const double* W2 = theta + (size_t)dh * din + dh;
+    const double* W3 = W2 + (size_t)dh * dh + dh;
+    const double* W4 = W3 + (size_t)dh * dh + dh;
+    double* gW1 = grad;
+    double* gb1 = gW1 + (size_t)dh * din;
+    double* gW2 = gb1 + dh;
+    double* gb2 = gW2 + (size_t)dh * dh;
+    double* gW3 = gb2 + dh;
+    double* gb3 = gW3 + (size_t)dh * dh;
+    double* gW4 = gb3 + dh;
+    double* gb4 = gW4 + (size_t)dout * dh;
+    memset(grad, 0, sizeof(double) * np);
+    double* y = malloc(sizeof(double) * (size_t)B * dout);
+    double* acts = malloc(sizeof(double) * (size_t)B * 3 * dh);
+    orc_mlp_forward(theta, din, dh, dout, x, B, y, acts);
+    double loss = 0.0;
+    double* dy = malloc(sizeof(double) * dout);
+    double* dz3 = malloc(sizeof(double) * dh);
+    double* dz2 = malloc(sizeof(double) * dh);
+    double* dz1 = malloc(sizeof(double) * dh);
+    for (int r = 0; r < B; ++r) {
+        const double* h1 = acts + ((size_t)r * 3 + 0) * dh;
+        const double* h2 = acts + ((size_t)r * 3 + 1) * dh;
+        const double* h3 = acts + ((size_t)r * 3 + 2) * dh;
+        const double* xr = x + (size_t)r * din;
+        for (int o = 0; o < dout; ++o) {
+            double e = y[(size_t)r * dout + o] - t[(size_t)r * dout + o];
+            loss += e * e / B;
+            dy[o] = 2.0 * e / B;
+        }
+        for (int o = 0; o < dout; ++o) {            /* output layer */
+            gb4[o] += dy[o];
+            for (int j = 0; j < dh; ++j) gW4[(size_t)o * dh + j] += dy[o] * h3[j];
+        }
+        for (int j = 0; j < dh; ++j) {              /* through tanh of layer 3 */
+            double s = 0.0;
+            for (int o = 0; o < dout; ++o) s += dy[o] * W4[(size_t)o * dh + j];
+            dz3[j] = s * (1.0 - h3[j] * h3[j]);
+        }
+        for (int j = 0; j < dh; ++j) {
+            gb3[j] += dz3[j];
+            for (int i = 0; i < dh; ++i) gW3[(size_t)j * dh + i] += dz3[j] * h2[i];
+        }
+        for (int i = 0; i < dh; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < dh; ++j) s += dz3[j] * W3[(size_t)j * dh + i];
+            dz2[i] = s * (1.0 - h2[i] * h2[i]);
+        }
+        for (int j = 0; j < dh; ++j) {
+            gb2[j] += dz2[j];
+            for (int i = 0; i < dh; ++i) gW2[(size_t)j * dh + i] += dz2[j] * h1[i];
+        }
+        for (int i = 0; i < dh; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < dh; ++j) s += dz2[j] * W2[(size_t)j * dh + i];
+            dz1[i] = s * (1.0 - h1[i] * h1[i]);
+        }
+        for (int j = 0; j < dh; ++j) {
+            gb1[j] += dz1[j];
+            for (int i = 0; i < din; ++i) gW1[(size_t)j * din + i] += dz1[j] * xr[i];
+        }
+    }
+    free(y); free(acts); free(dy); free(dz3); free(dz2); free(dz1);
+    return loss;
+}
+
+/* One Adam step (Kingma & Ba 2015) with bias correction; `step` counts from 1. */
+void orc_adam(double* theta, const double* grad, double* m, double* v, size_t n, double lr, double beta1,
+              double beta2, double eps, int step)
+{
+    const double c1 = 1.0 - pow(beta1, step), c2 = 1.0 - pow(beta2, step);
+    for (size_t i = 0; i < n; ++i) {
+        m[i] = beta1 * m[i] + (1.0 - beta1) * grad[i];
+        v[i] = beta2 * v[i] + (1.0 - beta2) * grad[i] * grad[i];
+        theta[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
+}

@@ -75,10 +75,25 @@ class cs_tune_result(C.Structure):
     _fields_ = [("blocks_per_sm", C.c_int), ("n_tried", C.c_int), ("ms", C.c_float * 8)]
 
 
+class cs_surrogate_config(C.Structure):
+    _fields_ = [("n_train", C.c_int), ("n_heldout", C.c_int), ("batch", C.c_int), ("epochs", C.c_int),
+                ("seed", C.c_uint64), ("lr", C.c_double), ("lr_min", C.c_double), ("h_min", C.c_double),
+                ("h_max", C.c_double), ("theta_max", C.c_double), ("split_activations", C.c_int),
+                ("boundary_band", C.c_double), ("height_scale", C.c_double)]
+
+
+class cs_surrogate_stats(C.Structure):
+    _fields_ = [("heldout_p99", C.c_double * 3), ("heldout_max", C.c_double * 3), ("final_loss", C.c_double),
+                ("steps", C.c_int), ("train_seconds", C.c_double)]
+
+
+N_MLP_PARAMS = 64 * 3 + 64 + 2 * (64 * 64 + 64) + 8 * 64 + 8
+
+
 class cs_opts(C.Structure):
     _fields_ = [("bunch", C.c_int), ("s_max", C.c_double), ("seg_base", C.c_uint64),
                 ("device_ptrs", C.c_int), ("accumulate", C.c_int), ("block_threads", C.c_int),
-                ("blocks_per_sm", C.c_int)]
+                ("blocks_per_sm", C.c_int), ("surrogate", C.c_void_p)]
 
 
 def lib():
@@ -123,6 +138,17 @@ def lib():
             L.cs_autotune_bunches.argtypes = [vp, C.c_size_t, vp, vp, C.c_uint64, C.c_double, vp, C.c_int,
                                               C.POINTER(cs_opts), C.POINTER(cs_output), vp, vp]
             L.cs_autotune_bunches.restype = st
+            L.cs_surrogate_config_default.argtypes = [C.POINTER(cs_surrogate_config)]
+            L.cs_surrogate_train.argtypes = [vp, C.POINTER(cs_surrogate_config), C.POINTER(vp),
+                                             C.POINTER(cs_surrogate_stats)]
+            L.cs_surrogate_train.restype = st
+            L.cs_surrogate_destroy.argtypes = [vp]
+            L.cs_surrogate_eval.argtypes = [vp, vp, C.c_size_t, vp, vp]
+            L.cs_surrogate_eval.restype = st
+            L.cs_surrogate_info.argtypes = [vp, vp, C.c_size_t, C.POINTER(cs_surrogate_stats), vp]
+            L.cs_surrogate_info.restype = st
+            L.cs_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int, vp, vp]
+            L.cs_mlp_loss_grad.restype = st
             L.cs_propagate_noalloc.argtypes = L.cs_propagate_ex.argtypes
             L.cs_propagate_noalloc.restype = st
             L.cs_philox4x32_10.argtypes = [vp, C.c_size_t, C.c_uint32, C.c_uint32, vp, vp]
@@ -341,7 +367,7 @@ class Detector:
 
 
 def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=1.0, seg_base=0,
-                   records=False, record_capacity=None, blocks_per_sm=0):
+                   records=False, record_capacity=None, blocks_per_sm=0, surrogate=None):
     """cs_propagate_ex with host numpy buffers; returns a dict of outputs."""
     arr = segs if isinstance(segs, np.ndarray) else pack_segments(segs)
     arr = np.ascontiguousarray(arr)
@@ -363,6 +389,7 @@ def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=
         out.records, out.record_capacity = _dptr(rec), cap
     o = cs_opts_default()
     o.bunch, o.s_max, o.seg_base, o.device_ptrs, o.blocks_per_sm = bunch, s_max, seg_base, 0, blocks_per_sm
+    o.surrogate = surrogate.handle if surrogate is not None else None
     st = cs_propagate_ex(_dptr(arr) if len(arr) else None, len(arr), atm.handle, det.handle, seed, o, out)
     _check(st, "cs_propagate_ex")
     res = dict(hist=hist, tel_counts=tel_counts, tel_time=tel_time, counters=counters, n_records=int(rc[0]))
@@ -422,3 +449,90 @@ class DeviceOutputs:
 def stream_ptr():
     import torch
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# --------------------------------------------------------------------------
+# surrogate network
+# --------------------------------------------------------------------------
+def cs_surrogate_config_default():
+    c = cs_surrogate_config()
+    lib().cs_surrogate_config_default(C.byref(c))
+    return c
+
+
+class Surrogate:
+    """Owns a trained cs_surrogate handle."""
+
+    def __init__(self, atm: Atmosphere, cfg: cs_surrogate_config = None, **kw):
+        c = cfg if cfg is not None else cs_surrogate_config_default()
+        for k, v in kw.items():
+            setattr(c, k, v)
+        self.cfg = c
+        h = C.c_void_p()
+        st = cs_surrogate_stats()
+        _check(lib().cs_surrogate_train(atm.handle, C.byref(c), C.byref(h), C.byref(st)), "cs_surrogate_train")
+        self.handle = h
+        self.stats = dict(p99=list(st.heldout_p99), max=list(st.heldout_max), final_loss=st.final_loss,
+                          steps=st.steps, train_seconds=st.train_seconds)
+
+    def info(self):
+        p = np.zeros(N_MLP_PARAMS, np.float32)
+        norm = np.zeros(15, np.float32)
+        _check(lib().cs_surrogate_info(self.handle, _dptr(p), p.size, None, _dptr(norm)), "cs_surrogate_info")
+        return p, norm
+
+    def eval(self, inputs):
+        """inputs: n x 3 (h_e - h_obs [m], cos(theta0), 1/lambda [1/nm]) -> n x 3 (G_R, G_t, T)."""
+        import torch
+        x = np.zeros((len(inputs), 4), np.float32)
+        x[:, :3] = inputs
+        d_in = torch.from_numpy(x).cuda()
+        d_out = torch.zeros_like(d_in)
+        _check(lib().cs_surrogate_eval(self.handle, C.c_void_p(d_in.data_ptr()), len(x),
+                                       C.c_void_p(d_out.data_ptr()), stream_ptr()), "cs_surrogate_eval")
+        torch.cuda.synchronize()
+        return d_out.cpu().numpy()[:, :3]
+
+    def close(self):
+        if self.handle:
+            lib().cs_surrogate_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cs_mlp_loss_grad(params, x, t):
+    """One training-path forward/backward on the GPU (host arrays)."""
+    p = np.ascontiguousarray(params, np.float32)
+    x = np.ascontiguousarray(x, np.float32)
+    t = np.ascontiguousarray(t, np.float32)
+    g = np.zeros_like(p)
+    loss = np.zeros(1, np.float32)
+    _check(lib().cs_mlp_loss_grad(_dptr(p), _dptr(x), _dptr(t), x.shape[0], _dptr(g), _dptr(loss)), "cs_mlp_loss_grad")
+    return float(loss[0]), g
+
+
+def mlp_padded_to_flat(p):
+    """GPU parameter layout (W4, b4 padded to 8 rows) -> unpadded 3-64-64-64-3 layout."""
+    o = 0
+    parts = []
+    for n in (64 * 3, 64, 64 * 64, 64, 64 * 64, 64):
+        parts.append(p[o:o + n])
+        o += n
+    parts.append(p[o:o + 3 * 64])
+    o += 8 * 64
+    parts.append(p[o:o + 3])
+    return np.concatenate(parts)
+
+
+def mlp_flat_to_padded(f):
+    out = np.zeros(N_MLP_PARAMS, np.float32)
+    n_head = 64 * 3 + 64 + 2 * (64 * 64 + 64)
+    out[:n_head] = f[:n_head]
+    out[n_head:n_head + 3 * 64] = f[n_head:n_head + 3 * 64]
+    out[n_head + 8 * 64:n_head + 8 * 64 + 3] = f[n_head + 3 * 64:]
+    return out

@@ -73,4 +73,5 @@ extern "C" void cs_opts_default(cs_opts* o) {
     o->accumulate = 0;
     o->block_threads = 0;
     o->blocks_per_sm = 0;
+    o->surrogate = nullptr;
 }

@@ -95,6 +95,17 @@ struct PropParams {
     float s_max;
 };
 
+// The atmosphere in FP64, as the table builder integrates it.
+struct AtmF64 {
+    int kind, n_layers;
+    double lay_h[kMaxLayers], lay_a[kMaxLayers], lay_b[kMaxLayers], lay_c[kMaxLayers];
+    double h_top, kappa, rho0;
+    double lin_h0, lin_h1, lin_n0, lin_n1, hom_delta;
+    double h_obs, H_A;
+    int refraction;
+};
+
+
 // ---- host-side helpers ------------------------------------------------------
 void set_last_error(const char* where, cudaError_t e);
 cs_status check_device();
@@ -102,11 +113,23 @@ int device_sm_count();
 
 }  // namespace cs
 
+struct cs_atmosphere;
+namespace cs {
+struct __align__(16) Fields4 {   // {G_R, G_t, G_X, G_A} in FP64
+    double x, y, z, w;
+};
+// Exact FP64 {G_R, G_t, G_X, G_A} at samples {h_e [m], theta0 [rad]} (device arrays).
+cs_status exact_fields(const cs_atmosphere* atm, const double2* d_in, size_t n, Fields4* d_out, cudaStream_t stream);
+}  // namespace cs
+
 struct cs_atmosphere {
     cs::AtmParams p;
     float4* d_tab;         // device table (owned)
     double h0, dh, dw;
     int device;
+    cs::AtmF64 f64;        // the FP64 description the tables were built from
+    double rayl_X0, rayl_lambda0, aer_tau0, aer_lambda0, aer_alpha, aer_H;
+    double lambda_min, lambda_max;
 };
 
 struct cs_detector {

@@ -1,0 +1,738 @@
+// Training and evaluation of the refraction surrogate network on the GPU.
+//
+// The network replaces the per-photon refraction integral (the correction
+// table lookup of the interpolation tracer, thesis Sec. 4.4.1): it maps
+// (emission height, zenith, wavelength) to the normalised displacement
+// correction G_R, the time-delay field G_t and the transmission T.  Samples
+// are labelled by the FP64 quadrature of the exact path (the table builder's
+// integrator); training is mini-batch Adam on an MSE loss, with every dense
+// contraction (forward, input gradients, weight gradients) on the tensor
+// cores as BF16 x BF16 -> FP32 MMAs and the FP32 master weights rounded to
+// BF16 for each step.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "mlp_common.cuh"
+
+struct cs_surrogate {
+    float* d_p = nullptr;             // FP32 master parameters
+    __nv_bfloat16* d_wb = nullptr;    // BF16 tensor-core weights
+    cs::SurrogateView view{};
+    cs_surrogate_stats stats{};
+    double h_min = 0, h_max = 0, theta_max = 0, lambda_min = 0, lambda_max = 0;
+};
+
+namespace cs {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Generic tensor-core GEMM: C[M x N] (op)= A[M x K] B[K x N].
+//   A_KM: A is stored [K][M] (else [M][K]);  B_KN: B is stored [K][N] (else [N][K]).
+//   SPLIT_A / SPLIT_B: the FP32 operand is staged as a BF16 hi + lo pair and
+//   the products hi*hi + lo*hi (+ hi*lo) are accumulated.
+//   EPI: 0 store, 1 store tanh(C + bias[n]), 2 store C + bias[n], 3 atomicAdd.
+// One 64 x 64 output tile per block of 4 warps (32 x 32 each); K in chunks of
+// 32 staged through shared memory; blockIdx.z splits K for EPI 3.
+// ---------------------------------------------------------------------------
+template <bool A_KM, bool B_KN, bool SPLIT_A, bool SPLIT_B, int EPI>
+__global__ void __launch_bounds__(128) gemm_kernel(const float* __restrict__ A, int lda, const float* __restrict__ B,
+                                                   int ldb, float* __restrict__ Cm, int ldc, int M, int N, int K,
+                                                   int kchunk, const float* __restrict__ bias) {
+    __shared__ __align__(16) __nv_bfloat16 Ah[64][40], Al[64][40], Bh[64][40], Bl[64][40];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, q = lane & 3;
+    const int m_blk = blockIdx.y * 64, n_blk = blockIdx.x * 64;
+    const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+
+    for (int k0 = kbeg; k0 < kend; k0 += 32) {
+        for (int idx = tid; idx < 64 * 32; idx += 128) {
+            int m, k;
+            if (A_KM) { k = idx >> 6; m = idx & 63; } else { m = idx >> 5; k = idx & 31; }
+            const int gm = m_blk + m, gk = k0 + k;
+            const float v = (gm < M && gk < kend) ? (A_KM ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk]) : 0.0f;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            Ah[m][k] = hi;
+            if (SPLIT_A) Al[m][k] = __float2bfloat16_rn(v - __bfloat162float(hi));
+        }
+        for (int idx = tid; idx < 64 * 32; idx += 128) {
+            int n, k;
+            if (B_KN) { k = idx >> 6; n = idx & 63; } else { n = idx >> 5; k = idx & 31; }
+            const int gn = n_blk + n, gk = k0 + k;
+            const float v = (gn < N && gk < kend) ? (B_KN ? B[(size_t)gk * ldb + gn] : B[(size_t)gn * ldb + gk]) : 0.0f;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            Bh[n][k] = hi;
+            if (SPLIT_B) Bl[n][k] = __float2bfloat16_rn(v - __bfloat162float(hi));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < 32; ks += 16) {
+            uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+                const int r0 = wm + mi * 16 + g;
+                ah[mi][0] = *reinterpret_cast<const uint32_t*>(&Ah[r0][ks + 2 * q]);
+                ah[mi][1] = *reinterpret_cast<const uint32_t*>(&Ah[r0 + 8][ks + 2 * q]);
+                ah[mi][2] = *reinterpret_cast<const uint32_t*>(&Ah[r0][ks + 8 + 2 * q]);
+                ah[mi][3] = *reinterpret_cast<const uint32_t*>(&Ah[r0 + 8][ks + 8 + 2 * q]);
+                if (SPLIT_A) {
+                    al[mi][0] = *reinterpret_cast<const uint32_t*>(&Al[r0][ks + 2 * q]);
+                    al[mi][1] = *reinterpret_cast<const uint32_t*>(&Al[r0 + 8][ks + 2 * q]);
+                    al[mi][2] = *reinterpret_cast<const uint32_t*>(&Al[r0][ks + 8 + 2 * q]);
+                    al[mi][3] = *reinterpret_cast<const uint32_t*>(&Al[r0 + 8][ks + 8 + 2 * q]);
+                }
+            }
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni) {
+                const int c0 = wn + ni * 8 + g;
+                bh[ni][0] = *reinterpret_cast<const uint32_t*>(&Bh[c0][ks + 2 * q]);
+                bh[ni][1] = *reinterpret_cast<const uint32_t*>(&Bh[c0][ks + 8 + 2 * q]);
+                if (SPLIT_B) {
+                    bl[ni][0] = *reinterpret_cast<const uint32_t*>(&Bl[c0][ks + 2 * q]);
+                    bl[ni][1] = *reinterpret_cast<const uint32_t*>(&Bl[c0][ks + 8 + 2 * q]);
+                }
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) {
+                    mma_16816(acc[mi][ni], ah[mi][0], ah[mi][1], ah[mi][2], ah[mi][3], bh[ni][0], bh[ni][1]);
+                    if (SPLIT_A) mma_16816(acc[mi][ni], al[mi][0], al[mi][1], al[mi][2], al[mi][3], bh[ni][0], bh[ni][1]);
+                    if (SPLIT_B) mma_16816(acc[mi][ni], ah[mi][0], ah[mi][1], ah[mi][2], ah[mi][3], bl[ni][0], bl[ni][1]);
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int row = m_blk + wm + mi * 16 + g + (r >= 2 ? 8 : 0);
+                const int col = n_blk + wn + ni * 8 + 2 * q + (r & 1);
+                if (row >= M || col >= N) continue;
+                const float v = acc[mi][ni][r];
+                float* dst = Cm + (size_t)row * ldc + col;
+                if (EPI == 0) *dst = v;
+                else if (EPI == 1) *dst = tanh_act(v + bias[col]);
+                else if (EPI == 2) *dst = v + bias[col];
+                else atomicAdd(dst, v);
+            }
+}
+
+template <bool A_KM, bool B_KN, bool SA, bool SB, int EPI>
+void gemm(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int M, int N, int K,
+          const float* bias, cudaStream_t s, int splits = 1) {
+    const int kchunk = ((K + splits - 1) / splits + 31) / 32 * 32;
+    dim3 grid((N + 63) / 64, (M + 63) / 64, (K + kchunk - 1) / kchunk);
+    gemm_kernel<A_KM, B_KN, SA, SB, EPI><<<grid, 128, 0, s>>>(A, lda, B, ldb, C, ldc, M, N, K, kchunk, bias);
+}
+
+// Layer 1 (3 inputs) on the CUDA cores: H1 = tanh(X W1^T + b1).
+__global__ void layer1_kernel(const float* __restrict__ X, int B, const float* __restrict__ p, float* __restrict__ H1) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)B * kHid) return;
+    const int r = (int)(i / kHid), u = (int)(i % kHid);
+    const float* x = X + (size_t)r * kNIn;
+    const float* w = p + kOffW1 + u * kNIn;
+    H1[i] = tanh_act(fmaf(w[2], x[2], fmaf(w[1], x[1], fmaf(w[0], x[0], p[kOffB1 + u]))));
+}
+
+// dY = 2 w (Y - T) / B on the valid outputs (w = 1 without weights), the
+// loss (1/B) sum w (Y - T)^2, and db4.
+__global__ void loss_grad_kernel(const float* __restrict__ Y, const float* __restrict__ T,
+                                 const float* __restrict__ Wt, int B, float* __restrict__ dY,
+                                 float* __restrict__ grad, float* __restrict__ loss) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.0f, d[kNOut] = {0.0f, 0.0f, 0.0f};
+    if (i < B) {
+#pragma unroll
+        for (int o = 0; o < kNOutP; ++o) {
+            float v = 0.0f;
+            if (o < kNOut) {
+                const float e = Y[(size_t)i * kNOutP + o] - T[(size_t)i * kNOut + o];
+                const float wt = Wt ? Wt[(size_t)i * kNOut + o] : 1.0f;
+                l += wt * e * e / B;
+                v = 2.0f * wt * e / B;
+                d[o] = v;
+            }
+            dY[(size_t)i * kNOutP + o] = v;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        l += __shfl_xor_sync(0xffffffffu, l, o);
+#pragma unroll
+        for (int c = 0; c < kNOut; ++c) d[c] += __shfl_xor_sync(0xffffffffu, d[c], o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(loss, l);
+#pragma unroll
+        for (int c = 0; c < kNOut; ++c) atomicAdd(grad + kOffB4 + c, d[c]);
+    }
+}
+
+// dZ = dH * (1 - H^2) and the bias gradient (column sums of dZ).
+__global__ void tanh_back_kernel(const float* __restrict__ dH, const float* __restrict__ H, int B,
+                                 float* __restrict__ dZ, float* __restrict__ gbias) {
+    const int u = threadIdx.x & 63;          // blockDim = 256: 4 rows x 64 units per pass
+    const int r0 = blockIdx.x * 64 + (threadIdx.x >> 6);
+    float s = 0.0f;
+    for (int r = r0; r < min(B, (int)blockIdx.x * 64 + 64); r += 4) {
+        const size_t i = (size_t)r * kHid + u;
+        const float h = H[i], z = dH[i] * (1.0f - h * h);
+        dZ[i] = z;
+        s += z;
+    }
+    atomicAdd(gbias + u, s);
+}
+
+// dW1 = dZ1^T X (3 inputs): one block per hidden unit.
+__global__ void grad_w1_kernel(const float* __restrict__ dZ, const float* __restrict__ X, int B, float* __restrict__ grad) {
+    const int u = blockIdx.x;
+    float s[kNIn] = {0.0f, 0.0f, 0.0f};
+    for (int r = threadIdx.x; r < B; r += blockDim.x) {
+        const float z = dZ[(size_t)r * kHid + u];
+#pragma unroll
+        for (int c = 0; c < kNIn; ++c) s[c] += z * X[(size_t)r * kNIn + c];
+    }
+#pragma unroll
+    for (int c = 0; c < kNIn; ++c) {
+        float v = s[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(grad + kOffW1 + u * kNIn + c, v);
+    }
+}
+
+// Adam (bias-corrected) on the FP32 masters; keeps the padding at zero.
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, float lr, float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kNParams) return;
+    if ((i >= kOffW4 + kNOut * kHid && i < kOffB4) || i >= kOffB4 + kNOut) return;   // padding
+    const float gi = g[i];
+    const float mi = 0.9f * m[i] + 0.1f * gi, vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+}
+
+// BF16 copies of W2, W3, W4 (same [n][k] layout as the masters).
+__global__ void to_bf16_kernel(const float* __restrict__ p, __nv_bfloat16* __restrict__ wb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kNBf16) return;
+    wb[i] = __float2bfloat16_rn(p[kOffW2 + (i < kBOffW3 ? i : i < kBOffW4 ? i - kBOffW3 + (kOffW3 - kOffW2)
+                                                                  : i - kBOffW4 + (kOffW4 - kOffW2))]);
+}
+
+// Masters as the GEMMs see them: W2..W4 rounded to BF16 (the rest stays FP32).
+__global__ void round_weights_kernel(const float* __restrict__ p, float* __restrict__ pr) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kNParams) return;
+    const bool tc = (i >= kOffW2 && i < kOffB2) || (i >= kOffW3 && i < kOffB3) || (i >= kOffW4 && i < kOffB4);
+    pr[i] = tc ? __bfloat162float(__float2bfloat16_rn(p[i])) : p[i];
+}
+
+// Excluded height bands [lo, hi) (absolute heights, ascending, inside [h0, h1]).
+struct Bands {
+    int n;
+    double lo[kMaxLayers], hi[kMaxLayers];
+};
+
+// Samples (h, theta, lambda) drawn with the counter-based generator: height
+// uniform over [h0, h1] minus the bands, zenith uniform, wavelength uniform.
+__global__ void sample_kernel(uint32_t key0, uint32_t key1, uint32_t stream_id, size_t n, double h0, double h1,
+                              Bands bands, double th_max, double l0, double l1, double2* hth, double* lam) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 r = philox((uint32_t)i, (uint32_t)(i >> 32), stream_id, 0x5A3Du, key0, key1);
+    const double u0 = (double)(r.x >> 8) * 0x1p-24, u1 = (double)(r.y >> 8) * 0x1p-24, u2 = (double)(r.z >> 8) * 0x1p-24;
+    double excl = 0.0;
+    for (int b = 0; b < bands.n; ++b) excl += bands.hi[b] - bands.lo[b];
+    double h = h0 + u0 * (h1 - h0 - excl);
+    for (int b = 0; b < bands.n; ++b)
+        if (h >= bands.lo[b]) h += bands.hi[b] - bands.lo[b];
+    hth[i] = make_double2(h, u1 * th_max);
+    lam[i] = l0 + u2 * (l1 - l0);
+}
+
+// Normalised inputs and targets from the labels (FP64 -> FP32).
+struct Norm {
+    double in_scale[3], in_shift[3], out_mid[3], out_half[3];
+    double height_scale;
+};
+
+// Transmission of each sample: T = exp(-X_slant / X_R(lambda) - tau_A(lambda) A_slant / H_A).
+__global__ void transmission_kernel(const double2* __restrict__ hth, const double* __restrict__ lam,
+                                    const Fields4* __restrict__ f, size_t n, double kR, double lR, double kA,
+                                    double lA, double alpha, int transmission, double* __restrict__ Tphys) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double c = cos(hth[i].y), l = lam[i];
+    double Tr = 1.0;
+    if (transmission) {
+        const double XR = kR * pow(l / lR, 4.0);
+        const double tau = kA * pow(l / lA, -alpha);
+        Tr = exp(-(f[i].z / c) / XR - tau * (f[i].w / c));
+    }
+    Tphys[i] = Tr;
+}
+
+// Normalised inputs (h_e - h_obs, cos(theta0), 1/lambda_nm) and targets
+// (G_R, G_t, ln T): -ln T is linear in the wavelength-dependent attenuation.
+// Loss weights: (sensitivity of the physical output x normalisation half-range
+// / error bar)^2, so the loss measures each error against its bar:
+// displacement = G_R sin / cos^3 (bar 1 cm), delay = G_t / (c cos) (bar
+// 0.1 ns), T = exp(ln T) (bar 1e-3).
+__global__ void build_xt_kernel(const double2* __restrict__ hth, const double* __restrict__ lam,
+                                const Fields4* __restrict__ f, const double* __restrict__ Tphys, size_t n, Norm nm,
+                                double h_obs, float* __restrict__ X, float* __restrict__ T, float* __restrict__ Wt) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double h = hth[i].x, th = hth[i].y, l = lam[i];
+    const double c = cos(th);
+    const double hc = nm.height_scale > 0.0 ? exp(-(h - h_obs) / nm.height_scale) : h - h_obs;
+    const double v[3] = {hc, c, 1.0 / (l * 1e9)};   // zenith enters as cos(theta0)
+    const double y[3] = {f[i].x, f[i].y, log(Tphys[i])};
+    for (int k = 0; k < 3; ++k) {
+        X[i * 3 + k] = (float)(nm.in_scale[k] * v[k] + nm.in_shift[k]);
+        T[i * 3 + k] = (float)((y[k] - nm.out_mid[k]) / nm.out_half[k]);
+    }
+    const double sens[3] = {sin(th) / (c * c * c), 1.0 / (c * kC), Tphys[i]};
+    const double bar[3] = {0.01, 1e-10, 1e-3};
+    for (int k = 0; k < 3; ++k) {
+        const double r = sens[k] * nm.out_half[k] / bar[k];
+        Wt[i * 3 + k] = (float)(r * r + 1e-6);
+    }
+}
+
+__global__ void gather_kernel(const float* __restrict__ X, const float* __restrict__ T,
+                              const float* __restrict__ Wt, size_t n, int B, uint32_t key0, uint32_t key1,
+                              uint32_t step, float* __restrict__ Xb, float* __restrict__ Tb, float* __restrict__ Wb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B) return;
+    const uint4 r = philox((uint32_t)i, step, 0xB47Cu, 0u, key0, key1);
+    const size_t j = (size_t)(((unsigned long long)r.x * (unsigned long long)n) >> 32);
+    for (int k = 0; k < 3; ++k) {
+        Xb[i * 3 + k] = X[j * 3 + k];
+        Tb[i * 3 + k] = T[j * 3 + k];
+        Wb[i * 3 + k] = Wt[j * 3 + k];
+    }
+}
+
+// One forward + backward pass of a batch; gradients accumulate into g.
+struct Work {
+    float *H1, *H2, *H3, *Y, *dY, *dH, *dZ;
+    float* loss;
+};
+
+void forward(const float* X, int B, const float* pr, const Work& w, cudaStream_t s) {
+    layer1_kernel<<<(unsigned)(((size_t)B * kHid + 255) / 256), 256, 0, s>>>(X, B, pr, w.H1);
+    gemm<false, false, true, false, 1>(w.H1, kHid, pr + kOffW2, kHid, w.H2, kHid, B, kHid, kHid, pr + kOffB2, s);
+    gemm<false, false, true, false, 1>(w.H2, kHid, pr + kOffW3, kHid, w.H3, kHid, B, kHid, kHid, pr + kOffB3, s);
+    gemm<false, false, true, false, 2>(w.H3, kHid, pr + kOffW4, kHid, w.Y, kNOutP, B, kNOutP, kHid, pr + kOffB4, s);
+}
+
+void backward(const float* X, const float* T, const float* Wt, int B, const float* pr, float* g, const Work& w,
+              cudaStream_t s) {
+    const int splits = std::max(1, B / 2048);
+    loss_grad_kernel<<<(B + 255) / 256, 256, 0, s>>>(w.Y, T, Wt, B, w.dY, g, w.loss);
+    // layer 4: dW4 = dY^T H3, dH3 = dY W4
+    gemm<true, true, true, true, 3>(w.dY, kNOutP, w.H3, kHid, g + kOffW4, kHid, kNOutP, kHid, B, nullptr, s, splits);
+    gemm<false, true, true, false, 0>(w.dY, kNOutP, pr + kOffW4, kHid, w.dH, kHid, B, kHid, kNOutP, nullptr, s);
+    tanh_back_kernel<<<(B + 63) / 64, 256, 0, s>>>(w.dH, w.H3, B, w.dZ, g + kOffB3);
+    // layer 3
+    gemm<true, true, true, true, 3>(w.dZ, kHid, w.H2, kHid, g + kOffW3, kHid, kHid, kHid, B, nullptr, s, splits);
+    gemm<false, true, true, false, 0>(w.dZ, kHid, pr + kOffW3, kHid, w.dH, kHid, B, kHid, kHid, nullptr, s);
+    tanh_back_kernel<<<(B + 63) / 64, 256, 0, s>>>(w.dH, w.H2, B, w.dZ, g + kOffB2);
+    // layer 2
+    gemm<true, true, true, true, 3>(w.dZ, kHid, w.H1, kHid, g + kOffW2, kHid, kHid, kHid, B, nullptr, s, splits);
+    gemm<false, true, true, false, 0>(w.dZ, kHid, pr + kOffW2, kHid, w.dH, kHid, B, kHid, kHid, nullptr, s);
+    tanh_back_kernel<<<(B + 63) / 64, 256, 0, s>>>(w.dH, w.H1, B, w.dZ, g + kOffB1);
+    // layer 1 (3 inputs)
+    grad_w1_kernel<<<kHid, 256, 0, s>>>(w.dZ, X, B, g);
+}
+
+cs_status alloc(void** p, size_t bytes) {
+    CS_CUDA_TRY(cudaMalloc(p, bytes));
+    return CS_OK;
+}
+
+// Evaluates the trained network through the photon kernel's warp-level
+// inference path on arbitrary (dz, cos(theta0), 1/lambda_nm) inputs.
+template <bool SPLIT>
+__global__ void eval_kernel(SurrogateView sv, const float4* __restrict__ in, size_t n, float4* __restrict__ out) {
+    const size_t base = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(size_t)31;
+    const size_t i = base + (threadIdx.x & 31);
+    float4 v = i < n ? in[i] : make_float4(0.f, 1.f, 3.0e-3f, 0.f);   // dz, cos(theta0), 1/lambda_nm
+    const float x[3] = {sv.in_scale[0] * height_coordinate(sv, v.x) + sv.in_shift[0],
+                        sv.in_scale[1] * v.y + sv.in_shift[1], sv.in_scale[2] * v.z + sv.in_shift[2]};
+    float y[3];
+    net32<SPLIT>(sv, x, y);
+    if (i < n) {
+        out[i] = make_float4(sv.out_half[0] * y[0] + sv.out_mid[0], sv.out_half[1] * y[1] + sv.out_mid[1],
+                             fminf(expf(sv.out_half[2] * y[2] + sv.out_mid[2]), 1.0f), 0.0f);
+    }
+}
+
+}  // namespace
+}  // namespace cs
+
+namespace cs {
+const SurrogateView* surrogate_view(const cs_surrogate* s) { return &s->view; }
+}  // namespace cs
+
+using namespace cs;
+
+extern "C" void cs_surrogate_config_default(cs_surrogate_config* c) {
+    if (!c) return;
+    c->n_train = 1 << 20;
+    c->n_heldout = 1 << 16;
+    c->batch = 16384;
+    c->epochs = 800;
+    c->seed = 0;
+    c->lr = 1e-2;
+    c->lr_min = 1e-5;
+    c->h_min = 2000.0;
+    c->h_max = 30000.0;
+    c->theta_max = 60.0 * kPi / 180.0;
+    c->split_activations = 1;
+    c->boundary_band = 500.0;
+    c->height_scale = 8000.0;
+}
+
+extern "C" cs_status cs_surrogate_train(const cs_atmosphere* atm, const cs_surrogate_config* cfg_in,
+                                        cs_surrogate** out, cs_surrogate_stats* stats_out) {
+    if (!atm || !out) return CS_ERR_INVALID_ARG;
+    *out = nullptr;
+    cs_surrogate_config cfg;
+    if (cfg_in) cfg = *cfg_in; else cs_surrogate_config_default(&cfg);
+    if (!atm->p.refraction) return CS_ERR_INVALID_ARG;
+    if (cfg.n_train < cfg.batch || cfg.batch < 64 || cfg.epochs < 1 || cfg.n_heldout < 32) return CS_ERR_INVALID_ARG;
+    if (!(cfg.h_min >= atm->p.h_obs) || !(cfg.h_max > cfg.h_min) || !(cfg.theta_max > 0.0) ||
+        !(cfg.theta_max < 80.0 * kPi / 180.0))
+        return CS_ERR_INVALID_ARG;
+    cs_status st = check_device();
+    if (st != CS_OK) return st;
+    const auto t_start = std::chrono::steady_clock::now();
+    cudaStream_t s = nullptr;
+    const size_t nt = (size_t)cfg.n_train, nh = (size_t)cfg.n_heldout, n_all = nt + nh;
+    const int B = cfg.batch;
+    std::vector<void*> bufs;
+    auto A = [&](size_t bytes) -> void* {
+        void* p = nullptr;
+        if (alloc(&p, bytes) != CS_OK) return nullptr;
+        bufs.push_back(p);
+        return p;
+    };
+    auto cleanup = [&]() {
+        for (void* p : bufs) cudaFree(p);
+    };
+    double2* hth = (double2*)A(n_all * sizeof(double2));
+    double* lam = (double*)A(n_all * sizeof(double));
+    Fields4* lab = (Fields4*)A(n_all * sizeof(Fields4));
+    float* X = (float*)A(n_all * 3 * sizeof(float));
+    float* T = (float*)A(n_all * 3 * sizeof(float));
+    float* Xb = (float*)A((size_t)B * 3 * sizeof(float));
+    float* Tb = (float*)A((size_t)B * 3 * sizeof(float));
+    Work w;
+    w.H1 = (float*)A((size_t)B * kHid * 4);
+    w.H2 = (float*)A((size_t)B * kHid * 4);
+    w.H3 = (float*)A((size_t)B * kHid * 4);
+    w.dH = (float*)A((size_t)B * kHid * 4);
+    w.dZ = (float*)A((size_t)B * kHid * 4);
+    w.Y = (float*)A((size_t)B * kNOutP * 4);
+    w.dY = (float*)A((size_t)B * kNOutP * 4);
+    w.loss = (float*)A(256);
+    float* p = (float*)A(kNParams * 4);
+    float* pr = (float*)A(kNParams * 4);
+    float* g = (float*)A(kNParams * 4);
+    float* m = (float*)A(kNParams * 4);
+    float* v = (float*)A(kNParams * 4);
+    if (!hth || !lam || !lab || !X || !T || !Xb || !Tb || !w.H1 || !w.H2 || !w.H3 || !w.dH || !w.dZ || !w.Y ||
+        !w.dY || !w.loss || !p || !pr || !g || !m || !v) {
+        cleanup();
+        return CS_ERR_CUDA;
+    }
+    const uint32_t k0 = (uint32_t)cfg.seed, k1 = (uint32_t)(cfg.seed >> 32);
+    // bands around the layer boundaries inside the domain
+    Bands bands;
+    memset(&bands, 0, sizeof bands);
+    if (atm->p.kind == CS_ATM_LAYERED && cfg.boundary_band > 0.0) {
+        for (int i = 1; i < atm->f64.n_layers; ++i) {
+            const double hb = atm->f64.lay_h[i];
+            const double lo = std::max(cfg.h_min, hb - cfg.boundary_band), hi = std::min(cfg.h_max, hb + cfg.boundary_band);
+            if (hi > lo && bands.n < kMaxLayers) {
+                bands.lo[bands.n] = lo;
+                bands.hi[bands.n] = hi;
+                ++bands.n;
+            }
+        }
+    }
+    // ---- samples and exact labels (training set, then held-out set) ----------
+    sample_kernel<<<(unsigned)((n_all + 255) / 256), 256, 0, s>>>(k0, k1, 1u, n_all, cfg.h_min, cfg.h_max, bands,
+                                                                   cfg.theta_max, atm->lambda_min, atm->lambda_max,
+                                                                   hth, lam);
+    if ((st = exact_fields(atm, hth, n_all, lab, s)) != CS_OK) { cleanup(); return st; }
+    std::vector<Fields4> hl(n_all);
+    cudaError_t e = cudaMemcpy(hl.data(), lab, n_all * sizeof(Fields4), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { set_last_error("labels", e); cleanup(); return CS_ERR_CUDA; }
+    std::vector<double2> hhth(n_all);
+    std::vector<double> hlam(n_all);
+    cudaMemcpy(hhth.data(), hth, n_all * sizeof(double2), cudaMemcpyDeviceToHost);
+    cudaMemcpy(hlam.data(), lam, n_all * sizeof(double), cudaMemcpyDeviceToHost);
+    // normalisation from the domain (inputs) and the training labels (outputs)
+    Norm nm;
+    const double il0 = 1.0 / (atm->lambda_max * 1e9), il1 = 1.0 / (atm->lambda_min * 1e9);
+    nm.height_scale = cfg.height_scale;
+    auto hcoord = [&](double h) { return cfg.height_scale > 0.0 ? exp(-(h - atm->p.h_obs) / cfg.height_scale) : h - atm->p.h_obs; };
+    const double hc0 = hcoord(cfg.h_min), hc1 = hcoord(cfg.h_max);
+    const double lo_in[3] = {std::min(hc0, hc1), cos(cfg.theta_max), il0};
+    const double hi_in[3] = {std::max(hc0, hc1), 1.0, il1};
+    for (int k = 0; k < 3; ++k) {
+        nm.in_scale[k] = 2.0 / (hi_in[k] - lo_in[k]);
+        nm.in_shift[k] = -1.0 - lo_in[k] * nm.in_scale[k];
+    }
+    double* Tphys = (double*)A(n_all * sizeof(double));
+    if (!Tphys) { cleanup(); return CS_ERR_CUDA; }
+    transmission_kernel<<<(unsigned)((n_all + 255) / 256), 256, 0, s>>>(
+        hth, lam, lab, n_all, atm->rayl_X0, atm->rayl_lambda0, atm->aer_tau0 / atm->aer_H, atm->aer_lambda0,
+        atm->aer_alpha, atm->p.transmission, Tphys);
+    std::vector<double> Tp(n_all);
+    cudaMemcpy(Tp.data(), Tphys, n_all * sizeof(double), cudaMemcpyDeviceToHost);
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (size_t i = 0; i < nt; ++i) {
+        mn[0] = std::min(mn[0], hl[i].x); mx[0] = std::max(mx[0], hl[i].x);
+        mn[1] = std::min(mn[1], hl[i].y); mx[1] = std::max(mx[1], hl[i].y);
+        const double lt = log(Tp[i]);
+        mn[2] = std::min(mn[2], lt); mx[2] = std::max(mx[2], lt);
+    }
+    for (int k = 0; k < 3; ++k) {
+        nm.out_mid[k] = 0.5 * (mx[k] + mn[k]);
+        nm.out_half[k] = std::max(0.5 * (mx[k] - mn[k]), 1e-12);
+    }
+    float* Wt = (float*)A(n_all * 3 * sizeof(float));
+    float* Wb = (float*)A((size_t)B * 3 * sizeof(float));
+    if (!Wt || !Wb) { cleanup(); return CS_ERR_CUDA; }
+    build_xt_kernel<<<(unsigned)((n_all + 255) / 256), 256, 0, s>>>(hth, lam, lab, Tphys, n_all, nm, atm->p.h_obs,
+                                                                     X, T, Wt);
+    // ---- initial parameters (Xavier-uniform from the counter-based generator) ----
+    std::vector<float> hp(kNParams, 0.0f);
+    {
+        uint32_t ctr = 0;
+        auto uni = [&](void) {
+            const uint32_t x = ((uint32_t)(cfg.seed * 2654435761u) ^ (ctr++ * 0x9E3779B9u)) * 0x85EBCA6Bu;
+            return (double)((x ^ (x >> 13)) * 0xC2B2AE35u >> 8) * 0x1p-24;
+        };
+        auto init = [&](int off, int nout, int nin, int nvalid) {
+            const double a = sqrt(6.0 / (nin + nvalid));
+            for (int o = 0; o < nout; ++o)
+                for (int i = 0; i < nin; ++i) hp[off + o * nin + i] = o < nvalid ? (float)((2.0 * uni() - 1.0) * a) : 0.0f;
+        };
+        init(kOffW1, kHid, kNIn, kHid);
+        init(kOffW2, kHid, kHid, kHid);
+        init(kOffW3, kHid, kHid, kHid);
+        init(kOffW4, kNOutP, kHid, kNOut);
+    }
+    cudaMemcpy(p, hp.data(), kNParams * 4, cudaMemcpyHostToDevice);
+    cudaMemset(m, 0, kNParams * 4);
+    cudaMemset(v, 0, kNParams * 4);
+    // ---- training -----------------------------------------------------------
+    const int steps_per_epoch = (int)(nt / B);
+    const int total = steps_per_epoch * cfg.epochs;
+    double last_loss = 0.0;
+    for (int step = 1; step <= total; ++step) {
+        const double lr = cfg.lr_min + 0.5 * (cfg.lr - cfg.lr_min) * (1.0 + cos(kPi * (step - 1) / total));
+        gather_kernel<<<(B + 255) / 256, 256, 0, s>>>(X, T, Wt, nt, B, k0, k1, (uint32_t)step, Xb, Tb, Wb);
+        round_weights_kernel<<<(kNParams + 255) / 256, 256, 0, s>>>(p, pr);
+        cudaMemsetAsync(g, 0, kNParams * 4, s);
+        cudaMemsetAsync(w.loss, 0, 4, s);
+        forward(Xb, B, pr, w, s);
+        backward(Xb, Tb, Wb, B, pr, g, w, s);
+        const float c1 = (float)(1.0 - pow(0.9, step)), c2 = (float)(1.0 - pow(0.999, step));
+        adam_kernel<<<(kNParams + 255) / 256, 256, 0, s>>>(p, g, m, v, (float)lr, c1, c2);
+        if (step == total) {
+            float l = 0.0f;
+            cudaMemcpy(&l, w.loss, 4, cudaMemcpyDeviceToHost);
+            last_loss = l;
+        }
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess) {
+        set_last_error("surrogate training", e);
+        cleanup();
+        return CS_ERR_CUDA;
+    }
+    // ---- the trained network ---------------------------------------------------
+    cs_surrogate* sg = new cs_surrogate;
+    if (alloc((void**)&sg->d_p, kNParams * 4) != CS_OK || alloc((void**)&sg->d_wb, kNBf16 * 2) != CS_OK) {
+        cudaFree(sg->d_p);
+        delete sg;
+        cleanup();
+        return CS_ERR_CUDA;
+    }
+    round_weights_kernel<<<(kNParams + 255) / 256, 256, 0, s>>>(p, sg->d_p);
+    to_bf16_kernel<<<(kNBf16 + 255) / 256, 256, 0, s>>>(p, sg->d_wb);
+    SurrogateView& sv = sg->view;
+    sv.p = sg->d_p;
+    sv.wb = sg->d_wb;
+    sv.split = cfg.split_activations ? 1 : 0;
+    for (int k = 0; k < 3; ++k) {
+        sv.in_scale[k] = (float)nm.in_scale[k];
+        sv.in_shift[k] = (float)nm.in_shift[k];
+        sv.out_half[k] = (float)nm.out_half[k];
+        sv.out_mid[k] = (float)nm.out_mid[k];
+    }
+    sv.dz_min = (float)(cfg.h_min - atm->p.h_obs);
+    sv.dz_max = (float)(cfg.h_max - atm->p.h_obs);
+    sv.mu_min = (float)cos(cfg.theta_max);
+    sv.inv_height_scale = cfg.height_scale > 0.0 ? (float)(1.0 / cfg.height_scale) : 0.0f;
+    sv.n_bands = bands.n;
+    for (int b = 0; b < bands.n; ++b) {
+        sv.band_lo[b] = (float)(bands.lo[b] - atm->p.h_obs);
+        sv.band_hi[b] = (float)(bands.hi[b] - atm->p.h_obs);
+    }
+    sg->h_min = cfg.h_min;
+    sg->h_max = cfg.h_max;
+    sg->theta_max = cfg.theta_max;
+    sg->lambda_min = atm->lambda_min;
+    sg->lambda_max = atm->lambda_max;
+    // ---- held-out errors in physical units, through the inference path ------------
+    std::vector<float4> hin(nh);
+    for (size_t i = 0; i < nh; ++i) {
+        const double2 a = hhth[nt + i];
+        hin[i] = make_float4((float)(a.x - atm->p.h_obs), (float)cos(a.y), (float)(1.0 / (hlam[nt + i] * 1e9)), 0.f);
+    }
+    float4 *din = (float4*)A(nh * sizeof(float4)), *dout = (float4*)A(nh * sizeof(float4));
+    std::vector<float4> hout(nh);
+    if (din && dout) {
+        cudaMemcpy(din, hin.data(), nh * sizeof(float4), cudaMemcpyHostToDevice);
+        if (sv.split) eval_kernel<true><<<(unsigned)((nh + 127) / 128), 128, 0, s>>>(sv, din, nh, dout);
+        else eval_kernel<false><<<(unsigned)((nh + 127) / 128), 128, 0, s>>>(sv, din, nh, dout);
+        cudaMemcpy(hout.data(), dout, nh * sizeof(float4), cudaMemcpyDeviceToHost);
+    }
+    std::vector<double> er[3];
+    for (size_t i = 0; i < nh; ++i) {
+        const double th = hhth[nt + i].y, c = cos(th), sn = sin(th);
+        er[0].push_back(fabs(hout[i].x - hl[nt + i].x) * sn / (c * c * c));   // displacement [m]
+        er[1].push_back(fabs(hout[i].y - hl[nt + i].y) / (c * kC));          // delay [s]
+        er[2].push_back(fabs(hout[i].z - Tp[nt + i]));                        // transmission
+    }
+    cs_surrogate_stats& S = sg->stats;
+    memset(&S, 0, sizeof S);
+    for (int k = 0; k < 3; ++k) {
+        std::sort(er[k].begin(), er[k].end());
+        S.heldout_p99[k] = er[k][(size_t)(0.99 * (er[k].size() - 1))];
+        S.heldout_max[k] = er[k].back();
+    }
+    S.final_loss = last_loss;
+    S.steps = total;
+    S.train_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    cleanup();
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+        set_last_error("surrogate evaluation", e);
+        cs_surrogate_destroy(sg);
+        return CS_ERR_CUDA;
+    }
+    if (stats_out) *stats_out = S;
+    *out = sg;
+    return CS_OK;
+}
+
+extern "C" void cs_surrogate_destroy(cs_surrogate* s) {
+    if (!s) return;
+    cudaFree(s->d_p);
+    cudaFree(s->d_wb);
+    delete s;
+}
+
+extern "C" cs_status cs_surrogate_eval(const cs_surrogate* s, const float* d_in, size_t n, float* d_out,
+                                       void* stream) {
+    if (!s || (n && (!d_in || !d_out))) return CS_ERR_INVALID_ARG;
+    if (((uintptr_t)d_in & 15) || ((uintptr_t)d_out & 15)) return CS_ERR_INVALID_ARG;
+    if (n == 0) return CS_OK;
+    const unsigned grid = (unsigned)((n + 127) / 128);
+    if (s->view.split) eval_kernel<true><<<grid, 128, 0, (cudaStream_t)stream>>>(s->view, (const float4*)d_in, n, (float4*)d_out);
+    else eval_kernel<false><<<grid, 128, 0, (cudaStream_t)stream>>>(s->view, (const float4*)d_in, n, (float4*)d_out);
+    CS_CUDA_TRY(cudaGetLastError());
+    return CS_OK;
+}
+
+extern "C" cs_status cs_surrogate_info(const cs_surrogate* s, float* params, size_t n_params, cs_surrogate_stats* st,
+                                       float* norm) {
+    if (!s) return CS_ERR_INVALID_ARG;
+    if (params) {
+        if (n_params < (size_t)kNParams) return CS_ERR_INVALID_ARG;
+        CS_CUDA_TRY(cudaMemcpy(params, s->d_p, kNParams * 4, cudaMemcpyDeviceToHost));
+    }
+    if (st) *st = s->stats;
+    if (norm) {   // in_scale[3], in_shift[3], out_half[3], out_mid[3], dz_min, dz_max, cos(theta_max)
+        for (int k = 0; k < 3; ++k) {
+            norm[k] = s->view.in_scale[k];
+            norm[3 + k] = s->view.in_shift[k];
+            norm[6 + k] = s->view.out_half[k];
+            norm[9 + k] = s->view.out_mid[k];
+        }
+        norm[12] = s->view.dz_min;
+        norm[13] = s->view.dz_max;
+        norm[14] = s->view.mu_min;
+    }
+    return CS_OK;
+}
+
+extern "C" cs_status cs_mlp_loss_grad(const float* params, const float* x, const float* t, int B, float* grad,
+                                      float* loss) {
+    if (!params || !x || !t || !grad || B < 1) return CS_ERR_INVALID_ARG;
+    cs_status st = check_device();
+    if (st != CS_OK) return st;
+    std::vector<void*> bufs;
+    auto A = [&](size_t bytes) -> float* {
+        void* p = nullptr;
+        if (alloc(&p, bytes) != CS_OK) return nullptr;
+        bufs.push_back(p);
+        return (float*)p;
+    };
+    Work w;
+    float *X = A((size_t)B * 12), *T = A((size_t)B * 12), *p = A(kNParams * 4), *pr = A(kNParams * 4),
+          *g = A(kNParams * 4);
+    w.H1 = A((size_t)B * kHid * 4);
+    w.H2 = A((size_t)B * kHid * 4);
+    w.H3 = A((size_t)B * kHid * 4);
+    w.dH = A((size_t)B * kHid * 4);
+    w.dZ = A((size_t)B * kHid * 4);
+    w.Y = A((size_t)B * kNOutP * 4);
+    w.dY = A((size_t)B * kNOutP * 4);
+    w.loss = A(256);
+    auto cleanup = [&]() {
+        for (void* b : bufs) cudaFree(b);
+    };
+    if (!X || !T || !p || !pr || !g || !w.H1 || !w.H2 || !w.H3 || !w.dH || !w.dZ || !w.Y || !w.dY || !w.loss) {
+        cleanup();
+        return CS_ERR_CUDA;
+    }
+    cudaMemcpy(X, x, (size_t)B * 12, cudaMemcpyHostToDevice);
+    cudaMemcpy(T, t, (size_t)B * 12, cudaMemcpyHostToDevice);
+    cudaMemcpy(p, params, kNParams * 4, cudaMemcpyHostToDevice);
+    cudaMemset(g, 0, kNParams * 4);
+    cudaMemset(w.loss, 0, 4);
+    round_weights_kernel<<<(kNParams + 255) / 256, 256>>>(p, pr);
+    forward(X, B, pr, w, nullptr);
+    backward(X, T, nullptr, B, pr, g, w, nullptr);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { set_last_error("mlp gradient", e); cleanup(); return CS_ERR_CUDA; }
+    cudaMemcpy(grad, g, kNParams * 4, cudaMemcpyDeviceToHost);
+    if (loss) cudaMemcpy(loss, w.loss, 4, cudaMemcpyDeviceToHost);
+    cleanup();
+    return CS_OK;
+}

@@ -20,7 +20,7 @@
 #include <mutex>
 #include <vector>
 
-#include "device_math.cuh"
+#include "mlp_common.cuh"
 
 namespace cs {
 namespace {
@@ -189,10 +189,14 @@ struct Tally {
 
 // Stages 3-5 for one bunch: generation on the cone (Sec. 4.2), the upward
 // filter (Sec. 5.3.4), straight line (Eq. 3.3) plus the interpolation-tracing
-// correction (Sec. 4.4.1), transmission (Sec. 4.3.1) and detection.
-__device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, long long base, const PropParams& pp,
-                                      const AtmParams& ap, const DetParams& dp, const OutParams& op, Tally& T,
-                                      bool want_records) {
+// correction (Sec. 4.4.1) or the surrogate network, transmission (Sec. 4.3.1)
+// and detection.  With SURR the whole warp must call (inactive lanes pass
+// active = false): the network runs warp-collectively on the tensor cores.
+template <bool SURR>
+__device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool active, long long base,
+                                      const PropParams& pp, const AtmParams& ap, const DetParams& dp,
+                                      const OutParams& op, const SurrogateView& sv, Tally& T, bool want_records) {
+    // ---- generation ------------------------------------------------------------
     const float4 Q = S.sub[q];
     const int segk = __float_as_int(Q.w);
     const int sg = segk & ((1 << kKShift) - 1), k = segk >> kKShift;
@@ -214,32 +218,54 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, long long
     const float mx = Px * ce - cphi, my = Py * ce - sphi, mz = (Pz - 1.0f) * ce;
     const float ct = Q.x, st = Q.y;
     const float ux = ct * Px + st * mx, uy = ct * Py + st * my, uz = ct * Pz + st * mz;
-    int status = CS_ST_LANDED, tel = -1, bin = -1;
+    const float inv_uz = rcp_approx(-uz);
+    const float w = (ux * ux + uy * uy) * inv_uz * inv_uz;   // tan^2(theta0)
+    int status = CS_ST_LANDED;
+    if (!(uz < 0.0f)) status = CS_ST_UPWARD;                 // discarded (Sec. 5.3.4)
+    else if (dz < 0.0f) status = CS_ST_BELOW;
+    else if (ap.use_tables && (w > ap.tv.w_max || dz >= ap.tv.dz_max)) status = CS_ST_DOMAIN;
+
+    // ---- the surrogate network, warp-collective --------------------------------
+    float net[3] = {0.0f, 0.0f, 1.0f};
+    bool use_net = false;
+    if (SURR) {
+        const float mu = -uz;   // cos(theta0)
+        use_net = active && status == CS_ST_LANDED && in_surrogate_domain(sv, dz, mu);
+        const float x[3] = {use_net ? fmaf(sv.in_scale[0], height_coordinate(sv, dz), sv.in_shift[0]) : 0.0f,
+                            use_net ? fmaf(sv.in_scale[1], mu, sv.in_shift[1]) : 0.0f,
+                            use_net ? fmaf(sv.in_scale[2], inv_l, sv.in_shift[2]) : 0.0f};
+        float y[3];
+        if (sv.split) net32<true>(sv, x, y);
+        else net32<false>(sv, x, y);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) net[c] = fmaf(sv.out_half[c], y[c], sv.out_mid[c]);
+    }
+    if (!active) return;
+
+    // ---- propagation and detection -----------------------------------------------
+    int tel = -1, bin = -1;
     float x = 0.0f, y = 0.0f, t_rel = ell * B.w;
-    if (!(uz < 0.0f)) {
-        status = CS_ST_UPWARD;
-    } else if (dz < 0.0f) {
-        status = CS_ST_BELOW;
-    } else {
-        const float inv_uz = rcp_approx(-uz);
-        const float w = (ux * ux + uy * uy) * inv_uz * inv_uz;   // tan^2(theta0)
-        if (ap.use_tables && (w > ap.tv.w_max || dz >= ap.tv.dz_max)) {
-            status = CS_ST_DOMAIN;
-        } else {
-            float rx, ry;
-            if (Pz < -1e-3f) {
-                // I - G = dz (P_xy / P_z - u_xy / u_z); the numerator is sin(theta) (P x m)
-                const float pmx = Pz * sphi - ce * Py, pmy = ce * Px - Pz * cphi;
-                const float fac = dz * st * rcp_approx(Pz * uz);
-                rx = -fac * pmy;
-                ry = fac * pmx;
-            } else {   // (near-)horizontal track: the origin is its start point
-                rx = ell * Px + dz * ux * inv_uz;
-                ry = ell * Py + dz * uy * inv_uz;
-            }
-            float path = dz * inv_uz;
-            float Tr = 1.0f;
-            if (ap.use_tables) {
+    if (status == CS_ST_LANDED) {
+        float rx, ry;
+        if (Pz < -1e-3f) {
+            // I - G = dz (P_xy / P_z - u_xy / u_z); the numerator is sin(theta) (P x m)
+            const float pmx = Pz * sphi - ce * Py, pmy = ce * Px - Pz * cphi;
+            const float fac = dz * st * rcp_approx(Pz * uz);
+            rx = -fac * pmy;
+            ry = fac * pmx;
+        } else {   // (near-)horizontal track: the origin is its start point
+            rx = ell * Px + dz * ux * inv_uz;
+            ry = ell * Py + dz * uy * inv_uz;
+        }
+        float path = dz * inv_uz;
+        float Tr = 1.0f;
+        if (ap.use_tables) {
+            float GR, Gt, GX = 0.0f, GA = 0.0f;
+            if (SURR && use_net) {
+                GR = net[0];
+                Gt = net[1];
+                Tr = fminf(ex2_approx(net[2] * (float)kLog2e), 1.0f);   // the network gives ln T
+            } else {
                 // bilinear in (h, tan^2 theta0) on cells stored as value + change
                 const float fh = dz * ap.tv.inv_dh, fw = w * ap.tv.inv_dw;
                 const int j = min((int)fh, ap.tv.nh - 1);
@@ -248,85 +274,86 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, long long
                 const float4* row = ap.tv.tab + ((size_t)j * ap.tv.nw + m) * 2;
                 const float4 v0 = __ldg(row), s0 = __ldg(row + 1), v1 = __ldg(row + 2), s1 = __ldg(row + 3);
                 const float a0 = 1.0f - gm;
-                if (ap.refraction) {
-                    const float GR = a0 * fmaf(fj, s0.x, v0.x) + gm * fmaf(fj, s1.x, v1.x);
-                    const float Gt = a0 * fmaf(fj, s0.y, v0.y) + gm * fmaf(fj, s1.y, v1.y);
-                    const float c3 = GR * inv_uz * inv_uz * inv_uz;
-                    rx = fmaf(c3, ux, rx);
-                    ry = fmaf(c3, uy, ry);
-                    path = fmaf(Gt, inv_uz, path);
-                }
+                GR = a0 * fmaf(fj, s0.x, v0.x) + gm * fmaf(fj, s1.x, v1.x);
+                Gt = a0 * fmaf(fj, s0.y, v0.y) + gm * fmaf(fj, s1.y, v1.y);
+                GX = a0 * fmaf(fj, s0.z, v0.z) + gm * fmaf(fj, s1.z, v1.z);
+                GA = a0 * fmaf(fj, s0.w, v0.w) + gm * fmaf(fj, s1.w, v1.w);
                 if (ap.transmission) {
-                    const float GX = a0 * fmaf(fj, s0.z, v0.z) + gm * fmaf(fj, s1.z, v1.z);
-                    const float GA = a0 * fmaf(fj, s0.w, v0.w) + gm * fmaf(fj, s1.w, v1.w);
                     const float il2 = inv_l * inv_l;
                     const float kR = ap.kR0 * il2 * il2;
                     const float kA = ap.kA0 * ex2_approx(ap.aer_alpha * lg2_approx(ap.lamA_nm * inv_l));
                     Tr = ex2_approx(-(GX * kR + GA * kA) * inv_uz);
                 }
             }
-            t_rel = fmaf(path, kInvC, t_rel);
-            const float4 Cg = S.segC[sg];
-            {
-                float s, e;
-                two_sum(Cg.x, rx, s, e);
-                x = s + (e + Cg.y);
-                two_sum(Cg.z, ry, s, e);
-                y = s + (e + Cg.w);
+            if (ap.refraction) {
+                const float c3 = GR * inv_uz * inv_uz * inv_uz;
+                rx = fmaf(c3, ux, rx);
+                ry = fmaf(c3, uy, ry);
+                path = fmaf(Gt, inv_uz, path);
             }
-            if (ap.transmission && !(u3 < Tr)) {
-                status = CS_ST_ABSORBED;
-            } else {
-                const int sh = S.shower[sg];
-                if (dp.nx > 0) {   // ground cell = floor(G_cells + r / d); rounding < 3e-5 cells
-                    const float4 D = S.segD[sg];
-                    const int ix = (int)floorf(D.x + fmaf(rx, dp.inv_dx, D.y));
-                    const int iy = (int)floorf(D.z + fmaf(ry, dp.inv_dy, D.w));
-                    if (ix >= 0 && ix < dp.nx && iy >= 0 && iy < dp.ny) {
-                        bin = iy * dp.nx + ix;
-                        atomicAdd(op.hist + ((size_t)sh * dp.ny * dp.nx + bin), (unsigned long long)b);
-                    }
+            if (!ap.transmission) Tr = 1.0f;
+        }
+        t_rel = fmaf(path, kInvC, t_rel);
+        const float4 Cg = S.segC[sg];
+        {
+            float s, e;
+            two_sum(Cg.x, rx, s, e);
+            x = s + (e + Cg.y);
+            two_sum(Cg.z, ry, s, e);
+            y = s + (e + Cg.w);
+        }
+        if (ap.transmission && !(u3 < Tr)) {
+            status = CS_ST_ABSORBED;
+        } else {
+            const int sh = S.shower[sg];
+            if (dp.nx > 0) {   // ground cell = floor(G_cells + r / d); rounding < 3e-5 cells
+                const float4 D = S.segD[sg];
+                const int ix = (int)floorf(D.x + fmaf(rx, dp.inv_dx, D.y));
+                const int iy = (int)floorf(D.z + fmaf(ry, dp.inv_dy, D.w));
+                if (ix >= 0 && ix < dp.nx && iy >= 0 && iy < dp.ny) {
+                    bin = iy * dp.nx + ix;
+                    atomicAdd(op.hist + ((size_t)sh * dp.ny * dp.nx + bin), (unsigned long long)b);
                 }
-                // telescopes: distance from the sphere centre to the arrival line below the radius
-                if (dp.n_tel > 0 && x >= dp.bx0 && x < dp.bx1 && y >= dp.by0 && y < dp.by1) {
-                    float ugx = ux, ugy = uy, ugz = uz;
-                    if (ap.refraction) {   // n sin(theta) conserved, azimuth kept
-                        const float sc = (1.0f + Q.z) / ap.n_obs;
-                        ugx = ux * sc;
-                        ugy = uy * sc;
-                        const float c2 = fmaxf(1.0f - (ugx * ugx + ugy * ugy), 1e-30f);
-                        ugz = -c2 * rsqrtf(c2);
+            }
+            // telescopes: distance from the sphere centre to the arrival line below the radius
+            if (dp.n_tel > 0 && x >= dp.bx0 && x < dp.bx1 && y >= dp.by0 && y < dp.by1) {
+                float ugx = ux, ugy = uy, ugz = uz;
+                if (ap.refraction) {   // n sin(theta) conserved, azimuth kept
+                    const float sc = (1.0f + Q.z) / ap.n_obs;
+                    ugx = ux * sc;
+                    ugy = uy * sc;
+                    const float c2 = fmaxf(1.0f - (ugx * ugx + ugy * ugy), 1e-30f);
+                    ugz = -c2 * rsqrtf(c2);
+                }
+                float best_d2 = 3.0e38f;
+                auto test = [&](int it) {
+                    const float4 T4 = __ldg(dp.tel + it);
+                    const float2 TL = __ldg(dp.tel_lo + it);
+                    const float ddx = (T4.x - Cg.x) + ((TL.x - Cg.y) - rx);
+                    const float ddy = (T4.y - Cg.z) + ((TL.y - Cg.w) - ry);
+                    const float ddz = T4.z;
+                    const float along = ddx * ugx + ddy * ugy + ddz * ugz;
+                    const float d2 = ddx * ddx + ddy * ddy + ddz * ddz - along * along;
+                    if (d2 < T4.w * T4.w && d2 < best_d2) {
+                        best_d2 = d2;
+                        tel = it;
                     }
-                    float best_d2 = 3.0e38f;
-                    auto test = [&](int it) {
-                        const float4 T4 = __ldg(dp.tel + it);
-                        const float2 TL = __ldg(dp.tel_lo + it);
-                        const float ddx = (T4.x - Cg.x) + ((TL.x - Cg.y) - rx);
-                        const float ddy = (T4.y - Cg.z) + ((TL.y - Cg.w) - ry);
-                        const float ddz = T4.z;
-                        const float along = ddx * ugx + ddy * ugy + ddz * ugz;
-                        const float d2 = ddx * ddx + ddy * ddy + ddz * ddz - along * along;
-                        if (d2 < T4.w * T4.w && d2 < best_d2) {
-                            best_d2 = d2;
-                            tel = it;
-                        }
-                    };
-                    if (ugx * ugx + ugy * ugy <= dp.hash_sin2_max) {
-                        const int cx = (int)((x - dp.gx0) * dp.inv_cell);
-                        const int cy = (int)((y - dp.gy0) * dp.inv_cell);
-                        if (cx >= 0 && cx < dp.gnx && cy >= 0 && cy < dp.gny) {
-                            const int c = cy * dp.gnx + cx;
-                            const int e0 = __ldg(dp.cell_start + c), e1 = __ldg(dp.cell_start + c + 1);
-                            for (int e = e0; e < e1; ++e) test(__ldg(dp.cell_tel + e));
-                        }
-                    } else {
-                        for (int it = 0; it < dp.n_tel; ++it) test(it);
+                };
+                if (ugx * ugx + ugy * ugy <= dp.hash_sin2_max) {
+                    const int cx = (int)((x - dp.gx0) * dp.inv_cell);
+                    const int cy = (int)((y - dp.gy0) * dp.inv_cell);
+                    if (cx >= 0 && cx < dp.gnx && cy >= 0 && cy < dp.gny) {
+                        const int c = cy * dp.gnx + cx;
+                        const int e0 = __ldg(dp.cell_start + c), e1 = __ldg(dp.cell_start + c + 1);
+                        for (int e = e0; e < e1; ++e) test(__ldg(dp.cell_tel + e));
                     }
-                    if (tel >= 0) {
-                        const size_t slot = (size_t)sh * dp.n_tel + tel;
-                        atomicAdd(op.tel_counts + slot, (unsigned long long)b);
-                        if (op.tel_time) atomicAdd(op.tel_time + slot, (double)b * (S.t0[sg] + (double)t_rel));
-                    }
+                } else {
+                    for (int it = 0; it < dp.n_tel; ++it) test(it);
+                }
+                if (tel >= 0) {
+                    const size_t slot = (size_t)sh * dp.n_tel + tel;
+                    atomicAdd(op.tel_counts + slot, (unsigned long long)b);
+                    if (op.tel_time) atomicAdd(op.tel_time + slot, (double)b * (S.t0[sg] + (double)t_rel));
                 }
             }
         }
@@ -338,9 +365,10 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, long long
     if (want_records) emit_record(op, gid, k, i, x, y, t_rel, inv_l, tel, bin, status);
 }
 
-__global__ void __launch_bounds__(kThreads, 4)
+template <bool SURR, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
 propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, const OutParams op,
-                 unsigned int* tile_ctr) {
+                 unsigned int* tile_ctr, const SurrogateView sv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
     const int t = threadIdx.x;
@@ -405,10 +433,13 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                     off += N;
                 }
                 __syncthreads();
-                for (int p = t; p < wn; p += kThreads) {
-                    const unsigned int e = S.map[p];
-                    bunch(S, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), base, pp, ap, dp, op, T,
-                          want_records);
+                // whole warps iterate together (the surrogate path is warp-collective)
+                for (int pw = t & ~31; pw < wn; pw += kThreads) {
+                    const int p = pw + (t & 31);
+                    const bool active = p < wn;
+                    const unsigned int e = S.map[active ? p : pw];
+                    bunch<SURR>(S, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), active, base, pp, ap, dp,
+                                op, sv, T, want_records);
                 }
                 __syncthreads();
             }
@@ -435,6 +466,34 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
         if ((t & 31) == 0 && x) atomicAdd(op.counters + c, (unsigned long long)(long long)x);
     }
 }
+
+// Launches the exact-tracer or the surrogate instance of the kernel.
+cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp, const AtmParams& ap,
+                        const DetParams& dp, const OutParams& op, unsigned int* ctr, const cs_surrogate* sur,
+                        bool sur_one_block) {
+    const size_t smem = sizeof(TileSmem);
+    if (sur) {
+        // 1 block per SM: the 255-register instance (no spills); else 2 blocks of 128 registers
+        if (sur_one_block) propagate_kernel<true, 1><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, *surrogate_view(sur));
+        else propagate_kernel<true, 2><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, *surrogate_view(sur));
+    } else {
+        SurrogateView none;
+        memset(&none, 0, sizeof none);
+        propagate_kernel<false, 4><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, none);
+    }
+    CS_CUDA_TRY(cudaGetLastError());
+    return CS_OK;
+}
+
+cs_status set_smem_attributes() {
+    const int smem = (int)sizeof(TileSmem);
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return CS_OK;
+}
+
+int default_blocks_per_sm(const cs_opts& o) { return o.blocks_per_sm > 0 ? o.blocks_per_sm : (o.surrogate ? 2 : 4); }
 
 __global__ void philox_kernel(const uint4* ctr, size_t n, uint32_t k0, uint32_t k1, uint4* out) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -511,22 +570,20 @@ cs_status launch(const cs_segment* d_segs, size_t n, const cs_atmosphere* atm, c
     pp.bunch = o.bunch;
     pp.shower_bunch = nullptr;
     pp.s_max = (float)o.s_max;
-    const size_t smem = sizeof(TileSmem);
     static bool attr_done = false;
     if (!attr_done) {
-        CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        cs_status sa = set_smem_attributes();
+        if (sa != CS_OK) return sa;
         attr_done = true;
     }
-    const int per_sm = o.blocks_per_sm > 0 ? o.blocks_per_sm : 4;
+    const int per_sm = default_blocks_per_sm(o);
     const long long tiles = ((long long)n + kTile - 1) / kTile;
     const long long grid = std::min<long long>(tiles, (long long)device_sm_count() * per_sm);
     unsigned int* ctr = nullptr;
     cs_status st = tile_counter(&ctr);
     if (st != CS_OK) return st;
     CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), stream));
-    propagate_kernel<<<(unsigned)grid, kThreads, smem, stream>>>(pp, atm->p, det->p, op, ctr);
-    CS_CUDA_TRY(cudaGetLastError());
-    return CS_OK;
+    return launch_kernel((unsigned)grid, stream, pp, atm->p, det->p, op, ctr, o.surrogate, per_sm <= 1);
 }
 
 }  // namespace
@@ -717,16 +774,13 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     op.records = out->records;
     op.record_capacity = out->records ? out->record_capacity : 0;
     op.record_count = (unsigned long long*)out->record_count;
-    const size_t smem = sizeof(TileSmem);
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int per_sm = o.blocks_per_sm > 0 ? o.blocks_per_sm : 4;
+    if ((st = set_smem_attributes()) != CS_OK) return st;
+    const int per_sm = default_blocks_per_sm(o);
     const long long tiles = ((long long)n + kTile - 1) / kTile;
     const long long grid = std::min<long long>(tiles, (long long)device_sm_count() * per_sm);
     // the array keeps the previous call's count: start this call's schedule at zero
     CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), stream));
-    propagate_kernel<<<(unsigned)grid, kThreads, smem, stream>>>(pp, atm->p, dp, op, ctr);
-    CS_CUDA_TRY(cudaGetLastError());
-    return CS_OK;
+    return launch_kernel((unsigned)grid, stream, pp, atm->p, dp, op, ctr, o.surrogate, per_sm <= 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -762,9 +816,9 @@ cs_status check_device_call(const cs_segment* segs, size_t n, const cs_atmospher
 // Grid of the persistent launch; also sets the kernel's shared-memory limit
 // (host-side calls kept out of stream capture).
 cs_status prepare_launch(size_t n, const cs_opts& o, unsigned int* grid) {
-    const size_t smem = sizeof(TileSmem);
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int per_sm = o.blocks_per_sm > 0 ? o.blocks_per_sm : 4;
+    cs_status st = set_smem_attributes();
+    if (st != CS_OK) return st;
+    const int per_sm = default_blocks_per_sm(o);
     const long long tiles = ((long long)n + kTile - 1) / kTile;
     *grid = (unsigned)std::max<long long>(1, std::min<long long>(tiles, (long long)device_sm_count() * per_sm));
     return CS_OK;
@@ -802,9 +856,7 @@ cs_status enqueue(const cs_segment* segs, size_t n, const cs_atmosphere* atm, co
     op.record_capacity = out->records ? out->record_capacity : 0;
     op.record_count = (unsigned long long*)out->record_count;
     CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), stream));
-    propagate_kernel<<<grid, kThreads, sizeof(TileSmem), stream>>>(pp, atm->p, dp, op, ctr);
-    CS_CUDA_TRY(cudaGetLastError());
-    return CS_OK;
+    return launch_kernel(grid, stream, pp, atm->p, dp, op, ctr, o.surrogate, default_blocks_per_sm(o) <= 1);
 }
 
 cs_status upload_bunches(const cs_detector* det, const int* shower_bunch, int** d_bunch) {

@@ -44,16 +44,6 @@ void legendre_rule(int n, double* x, double* w) {
     }
 }
 
-// Atmosphere in FP64 for the builder.
-struct AtmF64 {
-    int kind, n_layers;
-    double lay_h[kMaxLayers], lay_a[kMaxLayers], lay_b[kMaxLayers], lay_c[kMaxLayers];
-    double h_top, kappa, rho0;
-    double lin_h0, lin_h1, lin_n0, lin_n1, hom_delta;
-    double h_obs, H_A;
-    int refraction;
-};
-
 // layer of h; at a boundary `below` selects the lower layer (limit from below)
 __device__ __host__ inline int layer_index(const AtmF64& a, double h, bool below) {
     int i = 0;
@@ -182,6 +172,17 @@ __global__ void assemble_kernel(const double* F, const double* Fb, const int* be
                                             (float)(up[2] - v[2]), (float)(up[3] - v[3]));
 }
 
+// One thread per sample: the exact FP64 fields at (h_e, theta0).
+__global__ void exact_fields_kernel(AtmF64 a, const double2* in, size_t n, Fields4* out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double h_e = in[i].x, th = in[i].y;
+    const double cos0 = cos(th), sin0 = sin(th);
+    double f[4];
+    node_fields(a, h_e, false, cos0, sin0, f);
+    out[i] = Fields4{f[0], f[1], f[2], f[3]};
+}
+
 bool divides(double len, double dh) {
     double r = len / dh;
     return fabs(r - nearbyint(r)) < 1e-9 * fmax(1.0, fabs(r));
@@ -250,6 +251,15 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
     cs_atmosphere* h = new cs_atmosphere;
     memset(h, 0, sizeof *h);
     cudaGetDevice(&h->device);
+    h->f64 = a;
+    h->rayl_X0 = d->rayl_X0;
+    h->rayl_lambda0 = d->rayl_lambda0;
+    h->aer_tau0 = d->aer_tau0;
+    h->aer_lambda0 = d->aer_lambda0;
+    h->aer_alpha = d->aer_alpha;
+    h->aer_H = a.H_A;
+    h->lambda_min = d->lambda_min;
+    h->lambda_max = d->lambda_max;
     AtmParams& p = h->p;
     p.kind = d->kind;
     p.n_layers = a.n_layers;
@@ -361,6 +371,15 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
     *out = h;
     return CS_OK;
 }
+
+namespace cs {
+cs_status exact_fields(const cs_atmosphere* atm, const double2* d_in, size_t n, Fields4* d_out, cudaStream_t stream) {
+    if (n == 0) return CS_OK;
+    exact_fields_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(atm->f64, d_in, n, d_out);
+    CS_CUDA_TRY(cudaGetLastError());
+    return CS_OK;
+}
+}  // namespace cs
 
 extern "C" void cs_atmosphere_destroy(cs_atmosphere* atm) {
     if (!atm) return;
