@@ -43,6 +43,27 @@ SM_COUNT_NOMINAL = 152
 LANES_PER_SM = 128
 
 
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("propagate.cu", "device_math.cuh", "common.cuh", "mlp_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2405_04229_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def kernel_traffic():
+    """DRAM bytes per launch from the committed ncu capture, or None when the
+    kernel sources changed since it was taken."""
+    try:
+        kv = dict(l.strip().split("=", 1) for l in open(os.path.join(ROOT, "profiles", "propagate_kernel_traffic.txt"))
+                  if "=" in l and not l.startswith("#"))
+        if kv.get("kernel_sources_sha256") == kernel_sources_hash():
+            return float(kv["bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
 def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
@@ -342,12 +363,7 @@ def main():
         pass
     n_sm = B.cs_device_sm_count()
     peak = n_sm * LANES_PER_SM * max_mhz * 1e6 / 1e12
-    traffic = None
-    try:
-        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        traffic = tr.get("propagate_kernel_bytes_per_launch")
-    except Exception:
-        pass
+    traffic = kernel_traffic()
 
     # the surrogate form: the network replaces the table lookups inside its domain
     surrogate = None
