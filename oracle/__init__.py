@@ -58,7 +58,8 @@ class Config(C.Structure):
                 ("hist_x0", C.c_double), ("hist_y0", C.c_double), ("hist_dx", C.c_double),
                 ("hist_dy", C.c_double), ("tel", C.POINTER(C.c_double)),
                 ("band_pos", C.c_double), ("band_count", C.c_double), ("band_T", C.c_double),
-                ("band_h", C.c_double), ("band_w", C.c_double), ("quad_rtol", C.c_double)]
+                ("band_h", C.c_double), ("band_w", C.c_double), ("quad_rtol", C.c_double),
+                ("spherical", C.c_int), ("pad2", C.c_int), ("earth_radius", C.c_double)]
 
 
 SEGMENT_DTYPE = np.dtype([("x0", "<f8"), ("y0", "<f8"), ("z0", "<f8"), ("t0", "<f8"),
@@ -98,6 +99,8 @@ def lib():
             L.orc_refract_closed.argtypes = [C.POINTER(Atm), d, d, d, dp]
             L.orc_refract_closed.restype = C.c_int
             L.orc_snell_stepper.argtypes = [C.POINTER(Atm), d, d, d, d, dp]
+            L.orc_sph_path.argtypes = [C.POINTER(Atm), d, d, d, d, d, C.c_int, d, dp]
+            L.orc_ae_inverse.argtypes = [d, d, d, d, d, dp]
             L.orc_propagate.argtypes = [C.c_void_p, C.c_size_t, C.POINTER(Atm), C.POINTER(Config),
                                         C.POINTER(Output)]
             L.orc_propagate.restype = C.c_int
@@ -197,6 +200,22 @@ def snell_stepper(atm, h_obs, h_e, theta0, dh):
     return np.array(out[:])
 
 
+EARTH_RADIUS = 6_370_000.0
+
+
+def sph_path(atm, h_obs, h_e, psi0, refraction=True, R=EARTH_RADIUS, H_A=1200.0, rtol=1e-12):
+    """{central angle, t_path, X_slant, A_slant} in the spherical-shell atmosphere."""
+    out = (C.c_double * 4)()
+    lib().orc_sph_path(C.byref(atm), R, h_obs, h_e, psi0, H_A, int(refraction), rtol, out)
+    return np.array(out[:])
+
+
+def ae_inverse(x, y, dz=0.0, h_obs=2000.0, R=EARTH_RADIUS):
+    out = (C.c_double * 3)()
+    lib().orc_ae_inverse(R, h_obs, x, y, dz, out)
+    return np.array(out[:])
+
+
 def pack_segments(cols) -> np.ndarray:
     n = len(cols["z0"])
     a = np.zeros(n, SEGMENT_DTYPE)
@@ -212,7 +231,7 @@ DEFAULT_BANDS = dict(band_pos=1e-4, band_count=1e-4, band_T=1e-5, band_h=1e-3, b
 def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, bunch=1,
               refraction=False, transmission=False, use_domain=None, w_max=None, seed=0,
               seg_base=0, n_showers=1, hist=None, tel=None, records=True, record_capacity=None,
-              transmission_params=None, bands=None, quad_rtol=1e-10):
+              transmission_params=None, bands=None, quad_rtol=1e-10, spherical=False, earth_radius=EARTH_RADIUS):
     """Run the oracle over ``segs`` (dict of columns or SEGMENT_DTYPE array).
 
     Returns a dict with hist [n_showers, ny, nx], tel_counts [n_showers, n_tel],
@@ -256,6 +275,7 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
     for k, v in b.items():
         setattr(cfg, k, v)
     cfg.quad_rtol = quad_rtol
+    cfg.spherical, cfg.earth_radius = int(spherical), earth_radius
 
     hist_out = np.zeros((n_showers, max(h["ny"], 0), max(h["nx"], 0)), np.uint64)
     tel_counts = np.zeros((n_showers, cfg.n_tel), np.uint64)

@@ -434,6 +434,105 @@ void orc_snell_stepper(const orc_atm* a, double h_obs, double h_e, double theta0
 }
 
 /* ------------------------------------------------------------------ */
+/* Spherical-shell atmosphere (Sec. 3.3.4): n depends on the altitude */
+/* h = r - R_E only, and Bouguer's law n(r) r sin(psi) = K holds      */
+/* along the path (the spherical form of Eq. 3.17).  A photon that    */
+/* descends from r_e to the ground sphere r_g sweeps the central      */
+/* angle  int K / (r sqrt(n^2 r^2 - K^2)) dr  and spends              */
+/* int n^2 r / (c sqrt(n^2 r^2 - K^2)) dr  of time.                   */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const orc_atm* atm;
+    double K, R, H_A;
+} orc_sctx;
+
+static double orc_sq(const orc_sctx* c, double h, double* n_out, double* r_out)
+{
+    double n = orc_n(c->atm, h), r = c->R + h;
+    *n_out = n; *r_out = r;
+    return sqrt(n * n * r * r - c->K * c->K);
+}
+static double orc_sPhi(double h, const void* p)
+{
+    const orc_sctx* c = (const orc_sctx*)p; double n, r; double q = orc_sq(c, h, &n, &r);
+    return c->K / (r * q);
+}
+static double orc_sT(double h, const void* p)
+{
+    const orc_sctx* c = (const orc_sctx*)p; double n, r; double q = orc_sq(c, h, &n, &r);
+    return n * n * r / q / ORC_C_LIGHT;
+}
+static double orc_sX(double h, const void* p)
+{
+    const orc_sctx* c = (const orc_sctx*)p; double n, r; double q = orc_sq(c, h, &n, &r);
+    return 100.0 * orc_atm_rho(c->atm, h) * n * r / q;
+}
+static double orc_sA(double h, const void* p)
+{
+    const orc_sctx* c = (const orc_sctx*)p; double n, r; double q = orc_sq(c, h, &n, &r);
+    return exp(-h / c->H_A) * n * r / q;
+}
+
+static double orc_sX_straight(double h, const void* p)
+{
+    const orc_sctx* c = (const orc_sctx*)p; double r = c->R + h;
+    return 100.0 * orc_atm_rho(c->atm, h) * r / sqrt(r * r - c->K * c->K);
+}
+static double orc_sA_straight(double h, const void* p)
+{
+    const orc_sctx* c = (const orc_sctx*)p; double r = c->R + h;
+    return exp(-h / c->H_A) * r / sqrt(r * r - c->K * c->K);
+}
+
+/* out = {central angle Phi [rad], t_path [s], X_slant [g/cm^2], A_slant [m]}
+ * for a photon at altitude h_e with local zenith psi0 descending to h_obs;
+ * refraction = 0 gives the vacuum straight line (n = 1 for the geometry and
+ * the time, the columns along that line). */
+void orc_sph_path(const orc_atm* a, double R, double h_obs, double h_e, double psi0, double H_A, int refraction,
+                  double rtol, double out[4])
+{
+    double n_e = refraction ? orc_n(a, h_e) : 1.0;
+    orc_sctx c = { a, n_e * (R + h_e) * sin(psi0), R, H_A };
+    if (refraction) {
+        out[0] = orc_integrate(a, orc_sPhi, &c, h_obs, h_e, rtol);
+        out[1] = orc_integrate(a, orc_sT, &c, h_obs, h_e, rtol);
+        out[2] = orc_integrate(a, orc_sX, &c, h_obs, h_e, rtol);
+        out[3] = orc_integrate(a, orc_sA, &c, h_obs, h_e, rtol);
+    } else {
+        /* straight line: r(s)^2 = r_e^2 - 2 r_e cos(psi0) s + s^2 meets r_g */
+        double re = R + h_e, rg = R + h_obs, K = re * sin(psi0);
+        double len = sqrt(re * re - K * K) - sqrt(rg * rg - K * K);
+        out[0] = asin(K / rg) - asin(K / re);
+        out[1] = len / ORC_C_LIGHT;
+        /* columns along the straight line (n = 1 in the geometry) */
+        orc_sctx v = { a, K, R, H_A };
+        out[2] = orc_integrate(a, orc_sX_straight, &v, h_obs, h_e, rtol);
+        out[3] = orc_integrate(a, orc_sA_straight, &v, h_obs, h_e, rtol);
+    }
+}
+
+/* Azimuthal-equidistant coordinates about the array centre (the point of the
+ * ground sphere above the Earth's centre) of a point G (frame coordinates,
+ * Earth centre at (0, 0, -R)); rg = R + h_obs. */
+static void orc_ae(double R, double rg, const double G[3], double* x, double* y)
+{
+    double rho = sqrt(G[0] * G[0] + G[1] * G[1]);
+    double alpha = atan2(rho, G[2] + R);
+    if (rho > 0.0) { *x = rg * alpha * G[0] / rho; *y = rg * alpha * G[1] / rho; }
+    else { *x = 0.0; *y = 0.0; }
+}
+
+/* Frame coordinates of the point at altitude h_obs + dz above AE (x, y). */
+void orc_ae_inverse(double R, double h_obs, double x, double y, double dz, double out[3])
+{
+    double rg = R + h_obs, s = sqrt(x * x + y * y), alpha = s / rg, r = rg + dz;
+    double cx = s > 0.0 ? x / s : 1.0, cy = s > 0.0 ? y / s : 0.0;
+    out[0] = r * sin(alpha) * cx;
+    out[1] = r * sin(alpha) * cy;
+    out[2] = r * cos(alpha) - R;
+}
+
+/* ------------------------------------------------------------------ */
 /* Full photon generation and propagation.                            */
 /* ------------------------------------------------------------------ */
 typedef struct {               /* input segment, 64 bytes */
@@ -470,6 +569,9 @@ typedef struct {
     /* edge bands used only to flag photons for the parity comparison */
     double band_pos, band_count, band_T, band_h, band_w;
     double quad_rtol;
+    int spherical;             /* 1: spherical-shell atmosphere, Earth centre at (0, 0, -earth_radius) */
+    int pad2;
+    double earth_radius;
 } orc_config;
 
 enum { ORC_ST_LANDED = 0, ORC_ST_UPWARD = 1, ORC_ST_BELOW = 2, ORC_ST_DOMAIN = 3,
@@ -612,59 +714,95 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                 double p[3] = { cos(phi) * sin_t, sin(phi) * sin_t, -cos_t };
                 double u[3];
                 for (int r = 0; r < 3; ++r) u[r] = M[r][0] * p[0] + M[r][1] * p[1] + M[r][2] * p[2];
-                rec.ex = E[0]; rec.ey = E[1]; rec.h_e = E[2];
                 rec.ux = u[0]; rec.uy = u[1]; rec.uz = u[2];
                 out->counters[0] += (uint64_t)cfg->bunch;
 
-                if (fabs(u[2]) < cfg->band_w) rec.flags |= ORC_FL_UPWARD;
-                if (fabs(E[2] - cfg->h_obs) < cfg->band_h) rec.flags |= ORC_FL_BELOW;
+                /* local vertical and altitude of the emission point */
+                const double R = cfg->earth_radius;
+                double vloc[3] = { 0.0, 0.0, 1.0 }, h_e = E[2];
+                if (cfg->spherical) {
+                    double d[3] = { E[0], E[1], E[2] + R };
+                    double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                    for (int c = 0; c < 3; ++c) vloc[c] = d[c] / r;
+                    h_e = r - R;
+                    double G0[3] = { E[0], E[1], E[2] };
+                    orc_ae(R, R + cfg->h_obs, G0, &rec.ex, &rec.ey);   /* footprint of E */
+                } else {
+                    rec.ex = E[0]; rec.ey = E[1];
+                }
+                rec.h_e = h_e;
+                const double cos_z = -(u[0] * vloc[0] + u[1] * vloc[1] + u[2] * vloc[2]);   /* cos(local zenith) */
+
+                if (fabs(cos_z) < cfg->band_w) rec.flags |= ORC_FL_UPWARD;
+                if (fabs(h_e - cfg->h_obs) < cfg->band_h) rec.flags |= ORC_FL_BELOW;
                 if (use_tables && atm->kind == ORC_ATM_LAYERED) {
                     for (int li = 1; li < atm->n_layers; ++li)
-                        if (fabs(E[2] - atm->layer_h[li]) < cfg->band_h) rec.flags |= ORC_FL_LAYER;
+                        if (fabs(h_e - atm->layer_h[li]) < cfg->band_h) rec.flags |= ORC_FL_LAYER;
                 }
-                if (!(u[2] < 0.0)) {                    /* not downward: discarded (Sec. 5.3.4) */
+                if (!(cos_z > 0.0)) {                   /* not descending: discarded (Sec. 5.3.4) */
                     rec.status = ORC_ST_UPWARD;
                     out->counters[4] += cfg->bunch; out->counters[5] += cfg->bunch;
                     out->counters[6] += cfg->bunch;
                     orc_push(out, &rec);
                     continue;
                 }
-                if (E[2] < cfg->h_obs) {                /* emitted below the observation level */
+                if (h_e < cfg->h_obs) {                 /* emitted below the observation level */
                     rec.status = ORC_ST_BELOW;
                     out->counters[4] += cfg->bunch; out->counters[5] += cfg->bunch;
                     orc_push(out, &rec);
                     continue;
                 }
-                double theta0 = acos(-u[2]);
+                double theta0 = acos(cos_z);
                 rec.theta0 = theta0;
-                double w = (u[0] * u[0] + u[1] * u[1]) / (u[2] * u[2]);   /* tan^2(theta0) */
+                double sin_z = sin(theta0);
+                double w = sin_z * sin_z / (cos_z * cos_z);   /* tan^2 of the local zenith */
                 if (use_tables && fabs(w - cfg->w_max) < cfg->band_w * cfg->w_max) rec.flags |= ORC_FL_DOMAIN;
-                if (use_tables && fabs(E[2] - cfg->h_dom_top) < cfg->band_h) rec.flags |= ORC_FL_DOMAIN;
-                if (use_tables && (w > cfg->w_max || E[2] >= cfg->h_dom_top)) {
+                if (use_tables && fabs(h_e - cfg->h_dom_top) < cfg->band_h) rec.flags |= ORC_FL_DOMAIN;
+                if (use_tables && (w > cfg->w_max || h_e >= cfg->h_dom_top)) {
                     rec.status = ORC_ST_DOMAIN;
                     out->counters[4] += cfg->bunch; out->counters[5] += cfg->bunch;
                     orc_push(out, &rec);
                     continue;
                 }
-                double path[4];
-                if (cfg->refraction) orc_refract_quad(atm, cfg->h_obs, E[2], theta0, cfg->aer_H, cfg->quad_rtol, path);
-                else orc_straight(atm, cfg->h_obs, E[2], theta0, cfg->aer_H, path);
+                /* horizontal unit of u in the local frame (the plane of travel) */
+                double hv[3] = { u[0] + cos_z * vloc[0], u[1] + cos_z * vloc[1], u[2] + cos_z * vloc[2] };
+                double hn = sqrt(hv[0] * hv[0] + hv[1] * hv[1] + hv[2] * hv[2]);
+                if (hn > 0.0) { hv[0] /= hn; hv[1] /= hn; hv[2] /= hn; }
+                else { hv[0] = 1.0; hv[1] = 0.0; hv[2] = 0.0; }
 
-                /* ground point: E_xy + R along the horizontal unit of u */
-                double uh = sqrt(u[0] * u[0] + u[1] * u[1]);
-                double ex = uh > 0.0 ? u[0] / uh : 0.0, ey = uh > 0.0 ? u[1] / uh : 0.0;
-                double gx = E[0] + path[0] * ex, gy = E[1] + path[0] * ey;
+                double path[4], G3[3], ug[3], gx, gy;
+                if (!cfg->spherical) {
+                    if (cfg->refraction) orc_refract_quad(atm, cfg->h_obs, h_e, theta0, cfg->aer_H, cfg->quad_rtol, path);
+                    else orc_straight(atm, cfg->h_obs, h_e, theta0, cfg->aer_H, path);
+                    /* ground point: E_xy + R along the horizontal unit of u */
+                    gx = E[0] + path[0] * hv[0];
+                    gy = E[1] + path[0] * hv[1];
+                    G3[0] = gx; G3[1] = gy; G3[2] = cfg->h_obs;
+                    /* arrival direction: zenith from the invariant, azimuth kept */
+                    if (cfg->refraction) {
+                        double sg_ = orc_n(atm, h_e) * sin_z / n_obs, cg = sqrt(1.0 - sg_ * sg_);
+                        ug[0] = sg_ * hv[0]; ug[1] = sg_ * hv[1]; ug[2] = -cg;
+                    } else { ug[0] = u[0]; ug[1] = u[1]; ug[2] = u[2]; }
+                } else {
+                    /* the path stays in the plane (centre, E, u): rotate the vertical by the
+                     * central angle Phi towards hv; Bouguer's invariant gives the arrival zenith */
+                    orc_sph_path(atm, R, cfg->h_obs, h_e, theta0, cfg->aer_H, cfg->refraction, cfg->quad_rtol, path);
+                    const double rg = R + cfg->h_obs, Phi = path[0];
+                    double vG[3], hG[3];
+                    for (int c = 0; c < 3; ++c) {
+                        vG[c] = cos(Phi) * vloc[c] + sin(Phi) * hv[c];
+                        hG[c] = -sin(Phi) * vloc[c] + cos(Phi) * hv[c];
+                        G3[c] = rg * vG[c];
+                    }
+                    G3[2] -= R;
+                    orc_ae(R, rg, G3, &gx, &gy);
+                    const double n_e = cfg->refraction ? orc_n(atm, h_e) : 1.0, n_g = cfg->refraction ? n_obs : 1.0;
+                    const double sg_ = n_e * (R + h_e) * sin_z / (n_g * rg), cg = sqrt(1.0 - sg_ * sg_);
+                    for (int c = 0; c < 3; ++c) ug[c] = -cg * vG[c] + sg_ * hG[c];
+                }
                 rec.x = gx; rec.y = gy;
                 double t_arr = sg->t0 + t_emit_rel + path[1];
                 rec.dt = t_emit_rel + path[1];
-
-                /* arrival direction: zenith from the invariant, azimuth kept */
-                double ug[3];
-                if (cfg->refraction) {
-                    double s = orc_n(atm, E[2]) * sin(theta0);
-                    double sg_ = s / n_obs, cg = sqrt(1.0 - sg_ * sg_);
-                    ug[0] = sg_ * ex; ug[1] = sg_ * ey; ug[2] = -cg;
-                } else { ug[0] = u[0]; ug[1] = u[1]; ug[2] = u[2]; }
 
                 if (cfg->transmission) {
                     double lam = rec.lambda;
@@ -682,7 +820,7 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                 } else rec.T = 1.0;
                 rec.status = ORC_ST_LANDED;
 
-                /* ground histogram */
+                /* ground histogram (planar coordinates, or azimuthal-equidistant on the sphere) */
                 if (cfg->hist_nx > 0) {
                     double fx = (gx - cfg->hist_x0) / cfg->hist_dx, fy = (gy - cfg->hist_y0) / cfg->hist_dy;
                     double ix = floor(fx), iy = floor(fy);
@@ -702,7 +840,9 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                 int best = -1; double best_d = 0.0;
                 for (int it = 0; it < cfg->n_tel; ++it) {
                     const double* T4 = cfg->tel + 4 * it;
-                    double d0 = T4[0] - gx, d1 = T4[1] - gy, d2 = T4[2] - cfg->h_obs;
+                    double Tc[3] = { T4[0], T4[1], T4[2] };
+                    if (cfg->spherical) orc_ae_inverse(R, cfg->h_obs, T4[0], T4[1], T4[2] - cfg->h_obs, Tc);
+                    double d0 = Tc[0] - G3[0], d1 = Tc[1] - G3[1], d2 = Tc[2] - G3[2];
                     double along = d0 * ug[0] + d1 * ug[1] + d2 * ug[2];
                     double dist2 = d0 * d0 + d1 * d1 + d2 * d2 - along * along;
                     double dist = sqrt(fmax(dist2, 0.0));
