@@ -664,8 +664,16 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
             for (int c = 0; c < 3; ++c) M[r][c] = 2.0 * A[r] * A[c] - (r == c ? 1.0 : 0.0);
 
         for (int k = 0; k < K; ++k) {
-            /* Sub-step k (Sec. 4.2.1): n and the angle at its midpoint. */
-            double h_mid = sg->z0 + (k + 0.5) / K * L * P[2];
+            /* Sub-step k (Sec. 4.2.1): n and the angle at its midpoint, whose
+             * altitude on the spherical shell is its distance from the Earth's
+             * centre minus R_E (Sec. 3.3.4). */
+            const double s_mid = (k + 0.5) / K * L;
+            double h_mid = sg->z0 + s_mid * P[2];
+            if (cfg->spherical) {
+                const double mx = sg->x0 + s_mid * P[0], my = sg->y0 + s_mid * P[1];
+                const double mz = h_mid + cfg->earth_radius;
+                h_mid = sqrt(mx * mx + my * my + mz * mz) - cfg->earth_radius;
+            }
             double n_k = orc_n(atm, h_mid);
             int mid_layer_flag = 0;       /* angle and yield may come from the other layer's law */
             if (atm->kind == ORC_ATM_LAYERED)

@@ -270,3 +270,34 @@ def test_propagate_infinite_earth_is_planar():
     same = (a["status"] == b["status"]).mean()
     assert same > 0.999
     assert (a["tel"][ok] == b["tel"][ok]).mean() > 0.999
+
+
+def test_substep_yield_uses_the_altitude_on_the_sphere():
+    """60 km from the array centre a point at frame height z lies ~283 m
+    higher above the ground sphere: the sub-step's mean count (Eq. 2.2-2.5)
+    takes n at that altitude, not at z."""
+    n = 4
+    segs = synth._empty(n)
+    segs["x0"][:] = 60000.0
+    segs["z0"][:] = [6000.0, 9000.0, 12000.0, 15000.0]
+    segs["uz"][:] = -1.0
+    segs["length"][:] = 2.0
+    segs["inv_gamma2"][:] = np.float32(1e-8)
+    res = oracle.propagate(segs, ATM, spherical=True, bunch=1, seed=1)
+    rec = res["records"]
+    alpha = 7.2973525693e-3
+    ft = 2.0 * math.pi * alpha * (1.0 / 300e-9 - 1.0 / 600e-9)
+    beta2 = 1.0 - float(np.float32(1e-8))
+    for j in range(n):
+        r = rec[rec["seg"] == j]
+        assert len(r) > 0
+        for k in (0, 1):
+            z_mid = segs["z0"][j] - (k + 0.5)
+            alt = math.sqrt(60000.0**2 + (z_mid + R_E) ** 2) - R_E
+            assert alt - z_mid == pytest.approx(60000.0**2 / (2 * R_E), rel=1e-2)
+            nn = 1.0 + oracle.atm_delta(ATM, alt)
+            want = ft * (1.0 - 1.0 / (beta2 * nn * nn))
+            got = r["nbar"][r["k"] == k]
+            assert len(got) > 0 and np.allclose(got, want, rtol=1e-12)
+            n_flat = 1.0 + oracle.atm_delta(ATM, z_mid)
+            assert abs(ft * (1.0 - 1.0 / (beta2 * n_flat * n_flat)) / want - 1.0) > 5e-3
