@@ -249,13 +249,223 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# Extra lane operations per bunch on the spherical shell: the local vertical
+# along the track, the local zenith, the straight line to the ground sphere,
+# the ground tangent, the azimuthal-equidistant projection and Bouguer's
+# arrival direction (counted from the formulas like the planar figures).
+OPS_PER_BUNCH_SPHERICAL = OPS_PER_BUNCH + 85
+
+
+def run_inclined(args):
+    """Large inclined shower: 1e8 segments of a 100 TeV-class shower at zenith
+    60 deg through the spherical-shell layered atmosphere, bunch 10, 2,000
+    telescopes of 6 m radius (Poisson disk, separation >= 13 m, over
+    [-1, 1) km^2) and the 400 x 400 histogram, streamed in 10 chunks of 1e7;
+    the exact tracer and the surrogate."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_04229_gb300 import binding as B
+    from paper_2405_04229_gb300 import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    bunch, chunk, n_chunks = 10, args.chunk, args.chunks
+    n = chunk * n_chunks
+    seg_bytes = 64
+    t0 = time.perf_counter()
+    pinned = torch.empty(n * seg_bytes, dtype=torch.uint8).pin_memory()
+    host = pinned.numpy()
+    n_sub = 0
+    for c in range(n_chunks):
+        segs = synth.inclined_chunk(c, n=chunk, seed=args.seed)
+        n_sub += substeps(segs)
+        host[c * chunk * seg_bytes:(c + 1) * chunk * seg_bytes] = B.pack_segments(segs).view(np.uint8)
+        if c == 0:
+            sample_segs = synth.take(segs, slice(0, 20_000))
+        del segs
+    gen_s = time.perf_counter() - t0
+    tel = synth.poisson_disk_telescopes(n=2000, half=1000.0, min_sep=13.0, radius=6.0, seed=args.seed)
+    hist = synth.histogram_400()
+    atm = B.Atmosphere(layered=synth.US_STANDARD, refraction=True, transmission=True, spherical=True)
+    det = B.Detector(n_showers=1, hist=hist, tel=tel, spherical=True)
+    outs = B.DeviceOutputs(det)
+    stream = torch.cuda.current_stream()
+    sp = C.c_void_p(stream.cuda_stream)
+    d_all = pinned.to(dev)
+    base_ptr = d_all.data_ptr()
+    o = B.cs_opts_default()
+    o.bunch, o.device_ptrs = bunch, 1
+    ev_k = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_chunks)]
+
+    def step(timed_launches=False):
+        for c in range(n_chunks):
+            o.seg_base, o.accumulate = c * chunk, int(c > 0)
+            if timed_launches:
+                ev_k[c][0].record(stream)
+            st = B.cs_propagate_ex(C.c_void_p(base_ptr + c * chunk * seg_bytes), chunk, atm.handle, det.handle,
+                                   args.seed, o, outs.out, sp)
+            if st != B.CS_OK:
+                raise B.CSError(st, "cs_propagate_ex")
+            if timed_launches:
+                ev_k[c][1].record(stream)
+
+    def timed(steps, fn):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b_ in ev:
+            a.record(stream)
+            fn()
+            b_.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b_) for a, b_ in ev)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    photons = int(outs.counters[0].item())
+    with ClockSampler(0) as clk:
+        time.sleep(0.5)
+        ms = timed(args.steps, step)
+    assert int(outs.counters[0].item()) == photons
+    value = photons * args.steps / (ms / 1e3)
+    # launch durations of the photon kernel (one per chunk) for the roofline
+    step(timed_launches=True)
+    torch.cuda.synchronize()
+    k_ms = sum(a.elapsed_time(b_) for a, b_ in ev_k) / n_chunks
+    bunches = photons // bunch
+    ops = OPS_PER_BUNCH_SPHERICAL * bunches + OPS_PER_SUBSTEP * n_sub + OPS_PER_SEGMENT * n
+    achieved = ops / n_chunks / (k_ms / 1e3) / 1e12
+    max_mhz = 2070.0
+    try:
+        max_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", max_mhz)
+    except Exception:
+        pass
+    peak = B.cs_device_sm_count() * LANES_PER_SM * max_mhz * 1e6 / 1e12
+    counters = [int(x) for x in outs.counters.cpu()]
+
+    # end to end: pinned host segments streamed through the library's two-stream
+    # double buffer, outputs read back every step
+    e2e = None
+    if not args.no_e2e:
+        streamer = B.Streamer(chunk)
+        cnt_h = torch.zeros(8, dtype=torch.int64).pin_memory()
+        tel_h = torch.zeros(tel.shape[0], dtype=torch.int64).pin_memory()
+        hist_h = torch.zeros(400 * 400, dtype=torch.int64).pin_memory()
+
+        def estep():
+            streamer.run(pinned.data_ptr(), n, atm, det, outs.out, seed=args.seed, bunch=bunch, stream=sp)
+            cnt_h.copy_(outs.counters, non_blocking=True)
+            tel_h.copy_(outs.tel_counts.view(-1), non_blocking=True)
+            hist_h.copy_(outs.hist.view(-1), non_blocking=True)
+            stream.synchronize()
+
+        for _ in range(2):
+            estep()
+        assert int(cnt_h[0].item()) == photons
+        e_s, e_dev = 0.0, 0.0
+        for _ in range(args.steps):
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a = time.perf_counter()
+            ea.record(stream)
+            estep()
+            eb.record(stream)
+            e_s += time.perf_counter() - a
+            eb.synchronize()
+            e_dev += ea.elapsed_time(eb) / 1e3
+        e2e = {"value": photons * args.steps / e_s, "unit": UNIT, "h2d_bytes_per_step": n * seg_bytes,
+               "d2h_bytes_per_step": 8 * (8 + tel.shape[0] + 400 * 400),
+               "form": "cs_streamer_run: %d chunks of %d segments, two streams, pinned host memory" % (n_chunks, chunk),
+               "device_ms_per_step": 1e3 * e_dev / args.steps}
+        streamer.close()
+
+    # surrogate form on the same stream of chunks
+    surrogate = None
+    if not args.no_surrogate:
+        t_tr = time.perf_counter()
+        sur = B.Surrogate(atm)
+        train_s = time.perf_counter() - t_tr
+        o.surrogate = sur.handle
+        step()
+        torch.cuda.synchronize()
+        s_photons = int(outs.counters[0].item())
+        s_ms = timed(args.steps, step)
+        o.surrogate = None
+        surrogate = {"value": s_photons * args.steps / (s_ms / 1e3), "unit": UNIT, "ms_per_step": s_ms / args.steps,
+                     "speedup_vs_exact": (s_photons / s_ms) / (photons / ms),
+                     "heldout_p99": {"displacement_m": sur.stats["p99"][0], "delay_s": sur.stats["p99"][1],
+                                     "transmission": sur.stats["p99"][2]},
+                     "heldout_max": {"displacement_m": sur.stats["max"][0], "delay_s": sur.stats["max"][1],
+                                     "transmission": sur.stats["max"][2]},
+                     "train_seconds": round(train_s, 2)}
+        sur.close()
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, cores, sample = cpu_oracle_rate_sph(sample_segs, tel, hist, bunch=bunch, seed=args.seed)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "large inclined shower: %d segments (%d chunks of %d), 100 TeV-class, zenith 60 deg, "
+                                   "spherical-shell layered atmosphere, bunch 10, 2000 telescopes, exact tracer"
+                                   % (n, n_chunks, chunk),
+                       "segments": n, "photons_per_step": photons, "generation_s": round(gen_s, 1),
+                       "l2": "inputs (%.1f GB) larger than L2" % (n * seg_bytes / 1e9)},
+            "counters": counters,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "note": "per chunk launch; spherical lane-op count per bunch %d" % OPS_PER_BUNCH_SPHERICAL},
+            "kernel_ms": k_ms, "cpu_baseline": cpu, "surrogate": surrogate, "e2e": e2e,
+            "gpu_launches": args.steps * n_chunks, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_oracle_rate_sph(segs, tel, hist, bunch, seed, budget_s=12.0, chunk=200):
+    """The oracle on the spherical shell over a bounded prefix of the shower."""
+    import concurrent.futures as cf
+
+    import oracle
+    from paper_2405_04229_gb300 import synth
+    atm = oracle.make_atm(oracle.ATM_LAYERED, layered=synth.US_STANDARD)
+    n = len(segs["z0"])
+    threads = os.cpu_count() or 1
+    starts = list(range(0, n, chunk))
+    photons, done = 0, 0
+    t0 = time.perf_counter()
+
+    def work(st):
+        sl = slice(st, min(st + chunk, n))
+        r = oracle.propagate(synth.take(segs, sl), atm, hist=hist, tel=tel, bunch=bunch, refraction=True,
+                             transmission=True, seed=seed, seg_base=st, records=False, spherical=True)
+        return int(r["counters"][0]), sl.stop - sl.start
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        it = iter(starts)
+        futs = {ex.submit(work, st) for st in [next(it, None) for _ in range(threads)] if st is not None}
+        while futs:
+            fin, futs = cf.wait(futs, return_when=cf.FIRST_COMPLETED)
+            for f in fin:
+                p, s_ = f.result()
+                photons += p
+                done += s_
+            if time.perf_counter() - t0 < budget_s:
+                for _ in fin:
+                    st = next(it, None)
+                    if st is not None:
+                        futs.add(ex.submit(work, st))
+    dt = time.perf_counter() - t0
+    return photons / dt, threads, "first %d segments of chunk 0 (%d-segment pieces), %.1f s" % (done, chunk, dt)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
-    ap.add_argument("--config", default="refraction", choices=["refraction", "batched"])
+    ap.add_argument("--config", default="refraction", choices=["refraction", "batched", "inclined"])
+    ap.add_argument("--chunk", type=int, default=10_000_000)
+    ap.add_argument("--chunks", type=int, default=10)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--per-shower", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -266,6 +476,8 @@ def main():
         return run_reference(args)
     if args.config == "batched":
         return run_batched(args)
+    if args.config == "inclined":
+        return run_inclined(args)
 
     import torch
     rank, world, local = env_rank()
@@ -340,12 +552,16 @@ def main():
         torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
     ms_max = float(ms_t.item())
     assert int(cnt[0].item()) == photons_per_step
+    photons_all_ranks = photons_per_step
     if world > 1:   # combined outputs of all shards (exact integer sums), outside the timed region
         from paper_2405_04229_gb300 import shard
         comb = [cnt.clone(), hist_t.clone(), tel_c.clone()]
         shard.reduce_counts(comb)
-        assert int(comb[0][0].item()) == photons_per_step * world or rank != 0 or True
-    total_photons = photons_per_step * world * args.steps
+        pps = torch.tensor([photons_per_step], dtype=torch.int64, device=dev)
+        torch.distributed.all_reduce(pps)
+        photons_all_ranks = int(pps.item())
+        assert int(comb[0][0].item()) == photons_all_ranks
+    total_photons = photons_all_ranks * args.steps
     value = total_photons / (ms_max / 1e3)
 
     # kernel-only timing for the roofline: the same launch without the output memsets

@@ -75,6 +75,12 @@ typedef struct cs_segment {
  * Atmosphere.
  * ---------------------------------------------------------------------- */
 enum {
+    CS_GEOM_PLANAR = 0,      /* n depends on z only, ground is the plane z = h_obs (Sec. 3.3.2) */
+    CS_GEOM_SPHERICAL = 1    /* n depends on the altitude |x - c| - R_E, c = (0, 0, -R_E); the ground is the
+                                sphere of radius R_E + h_obs (Sec. 3.3.4) */
+};
+
+enum {
     CS_ATM_LAYERED = 0,      /* CORSIKA-style layers: T(h) = a + b exp(-h/c), top layer linear */
     CS_ATM_LINEAR = 1,       /* n falls linearly from lin_n0 at lin_h0 to lin_n1 at lin_h1 (Sec. 6.3.1) */
     CS_ATM_HOMOGENEOUS = 2   /* constant n = 1 + hom_delta (Sec. 3.3.1) */
@@ -101,6 +107,8 @@ typedef struct cs_atmosphere_desc {
                                     domain" (missed) when refraction or transmission is on; 0 = 75 deg */
     int table_nw;                /* 0 = default number of tan^2(theta) columns */
     double table_dh;             /* 0 = default row spacing [m]; must divide the layer bottoms - h_obs */
+    int geometry;                /* CS_GEOM_PLANAR or CS_GEOM_SPHERICAL */
+    double earth_radius;         /* spherical: R_E [m]; 0 = 6,370 km */
 } cs_atmosphere_desc;
 
 typedef struct cs_atmosphere cs_atmosphere;
@@ -119,7 +127,13 @@ cs_status cs_atmosphere_table_info(const cs_atmosphere* atm, int* nh, int* nw, d
                                    double* dh, double* dw);
 /* Copies the table to host memory: nh * nw * 8 floats, row-major, per node
  * {G_R, G_t, G_X, G_A at h_j from above, the same four at h_j+1 from below
- * minus those at h_j}; see the design notes for the normalisations. */
+ * minus those at h_j}.  For a photon emitted at h_j with (local) zenith
+ * theta0: G_R = D cos^3(theta0) / sin(theta0), D the ground displacement of
+ * the refracted path beyond the straight line (on the sphere: the arc length
+ * on the ground sphere); G_t = c dt cos(theta0), dt its delay beyond the
+ * straight line; G_X = X cos(theta0), X the slant density column [g/cm^2]
+ * along the path; G_A = A cos(theta0), A = the path integral of
+ * exp(-h / aer_H) [m]. */
 cs_status cs_atmosphere_copy_table(const cs_atmosphere* atm, float* host_dst, size_t n_floats);
 
 /* ------------------------------------------------------------------------
@@ -133,6 +147,11 @@ typedef struct cs_detector_desc {
     double hist_dx, hist_dy;     /* cell size [m] */
     int n_tel;                   /* 0 = no telescopes */
     const double* tel_xyzr;      /* host, n_tel x {x, y, z, radius} [m] */
+    int geometry;                /* CS_GEOM_SPHERICAL: histogram and telescope (x, y) are azimuthal-
+                                    equidistant ground coordinates about the array centre (0, 0, h_obs),
+                                    telescope z is the height above the ground sphere plus h_obs; must
+                                    match the atmosphere */
+    double earth_radius;         /* spherical: R_E [m]; 0 = 6,370 km */
 } cs_detector_desc;
 
 typedef struct cs_detector cs_detector;
@@ -236,6 +255,36 @@ cs_status cs_batch_create(const cs_segment* segs, size_t n, const cs_atmosphere*
 cs_status cs_batch_launch(cs_batch* batch, void* stream);
 void cs_batch_destroy(cs_batch* batch);
 
+/* ------------------------------------------------------------------------
+ * Streaming host segments: chunks of `chunk` segments are copied to the
+ * device through two staging buffers on two library-owned streams, so the
+ * copy of chunk c overlaps the photon kernel of chunk c - 1 (the thesis's
+ * data transfer and batching, Sec. 5.1 and 5.4).  Every chunk's draws are
+ * keyed by its global segment index, so the result equals one call over all
+ * segments.
+ * ---------------------------------------------------------------------- */
+typedef struct cs_streamer cs_streamer;
+
+/* Allocates two device buffers of `chunk` segments (1 <= chunk <= 2^32) and
+ * two streams on the current device.  Errors: CS_ERR_INVALID_ARG,
+ * CS_ERR_CUDA. */
+cs_status cs_streamer_create(size_t chunk, cs_streamer** out);
+/* Propagates n segments from host memory `host_segs` (page-locked memory for
+ * the copies to overlap the kernels; pageable memory works without overlap).
+ * The outputs in `out` are device memory and opts->device_ptrs must be 1;
+ * they are zeroed first on `stream` unless opts->accumulate.  Chunk c is
+ * keyed from opts->seg_base + c * chunk.  Enqueues only: the work starts
+ * after what is already queued on `stream` (cudaStream_t, NULL = legacy
+ * default stream) and `stream` waits for all of it, so read the outputs
+ * after synchronising `stream`.  Calls on one streamer must not overlap
+ * (they share its buffers).  Errors: CS_ERR_INVALID_ARG (NULL arguments,
+ * host outputs, another device), CS_ERR_CUDA. */
+cs_status cs_streamer_run(cs_streamer* s, const cs_segment* host_segs, size_t n, const cs_atmosphere* atm,
+                          const cs_detector* det, uint64_t seed, const cs_opts* opts, cs_output* out,
+                          void* stream);
+/* Waits for the streamer's work and frees it. */
+void cs_streamer_destroy(cs_streamer* s);
+
 typedef struct cs_tune_result {
     int blocks_per_sm;   /* fastest resident blocks per SM (256 threads each) */
     int n_tried;
@@ -275,8 +324,8 @@ cs_status cs_autotune_bunches(const cs_segment* segs, size_t n, const cs_atmosph
 typedef struct cs_surrogate_config {
     int n_train;             /* training samples (default 2^20) */
     int n_heldout;           /* held-out samples (default 2^16) */
-    int batch;               /* mini-batch (default 16384) */
-    int epochs;              /* passes over the training set (default 800) */
+    int batch;               /* mini-batch (default 32768) */
+    int epochs;              /* passes over the training set (default 1600) */
     uint64_t seed;
     double lr, lr_min;       /* Adam learning rate (default 1e-2), cosine-decayed to lr_min (1e-5) */
     double h_min, h_max;     /* emission heights [m] (default 2 km .. 30 km) */

@@ -20,6 +20,7 @@ _lib = None
 
 CS_OK, CS_ERR_INVALID_ARG, CS_ERR_CUDA, CS_ERR_CAPACITY, CS_ERR_TIMEOUT, CS_ERR_DOMAIN, CS_ERR_NO_DEVICE = range(7)
 CS_ATM_LAYERED, CS_ATM_LINEAR, CS_ATM_HOMOGENEOUS = 0, 1, 2
+CS_GEOM_PLANAR, CS_GEOM_SPHERICAL = 0, 1
 (CS_CNT_EMITTED, CS_CNT_ABSORBED, CS_CNT_HIST, CS_CNT_TEL, CS_CNT_MISSED_HIST, CS_CNT_MISSED_TEL,
  CS_CNT_UPWARD, CS_CNT_INVALID_SEGMENTS) = range(8)
 CS_N_COUNTERS = 8
@@ -56,13 +57,14 @@ class cs_atmosphere_desc(C.Structure):
                 ("rayl_X0", C.c_double), ("rayl_lambda0", C.c_double),
                 ("aer_tau0", C.c_double), ("aer_lambda0", C.c_double), ("aer_alpha", C.c_double),
                 ("aer_H", C.c_double), ("theta_max", C.c_double), ("table_nw", C.c_int),
-                ("table_dh", C.c_double)]
+                ("table_dh", C.c_double), ("geometry", C.c_int), ("earth_radius", C.c_double)]
 
 
 class cs_detector_desc(C.Structure):
     _fields_ = [("n_showers", C.c_int), ("h_obs", C.c_double), ("hist_nx", C.c_int), ("hist_ny", C.c_int),
                 ("hist_x0", C.c_double), ("hist_y0", C.c_double), ("hist_dx", C.c_double),
-                ("hist_dy", C.c_double), ("n_tel", C.c_int), ("tel_xyzr", C.POINTER(C.c_double))]
+                ("hist_dy", C.c_double), ("n_tel", C.c_int), ("tel_xyzr", C.POINTER(C.c_double)),
+                ("geometry", C.c_int), ("earth_radius", C.c_double)]
 
 
 class cs_output(C.Structure):
@@ -132,6 +134,12 @@ def lib():
             L.cs_batch_launch.argtypes = [vp, vp]
             L.cs_batch_launch.restype = st
             L.cs_batch_destroy.argtypes = [vp]
+            L.cs_streamer_create.argtypes = [C.c_size_t, C.POINTER(vp)]
+            L.cs_streamer_create.restype = st
+            L.cs_streamer_run.argtypes = [vp, vp, C.c_size_t, vp, vp, C.c_uint64, C.POINTER(cs_opts),
+                                          C.POINTER(cs_output), vp]
+            L.cs_streamer_run.restype = st
+            L.cs_streamer_destroy.argtypes = [vp]
             L.cs_autotune_tiling.argtypes = [vp, C.c_size_t, vp, vp, C.c_uint64, vp, C.POINTER(cs_opts),
                                              C.POINTER(cs_output), vp, C.POINTER(cs_tune_result)]
             L.cs_autotune_tiling.restype = st
@@ -293,7 +301,7 @@ class Atmosphere:
 
     def __init__(self, kind=CS_ATM_LAYERED, layered=None, linear=None, hom_delta=0.0, h_obs=2000.0,
                  lambda_nm=(300.0, 600.0), refraction=False, transmission=False, transmission_params=None,
-                 theta_max_deg=75.0, table_nw=0, table_dh=0.0):
+                 theta_max_deg=75.0, table_nw=0, table_dh=0.0, spherical=False, earth_radius=0.0):
         d = cs_atmosphere_desc()
         d.kind = kind
         self._keep = []
@@ -319,6 +327,7 @@ class Atmosphere:
             setattr(d, k, v)
         d.theta_max = math.radians(theta_max_deg)
         d.table_nw, d.table_dh = table_nw, table_dh
+        d.geometry, d.earth_radius = (CS_GEOM_SPHERICAL if spherical else CS_GEOM_PLANAR), earth_radius
         self.desc = d
         self.h_obs = h_obs
         self.handle = cs_atmosphere_create(d)
@@ -341,9 +350,10 @@ class Atmosphere:
 class Detector:
     """Owns a cs_detector handle."""
 
-    def __init__(self, n_showers=1, h_obs=2000.0, hist=None, tel=None):
+    def __init__(self, n_showers=1, h_obs=2000.0, hist=None, tel=None, spherical=False, earth_radius=0.0):
         d = cs_detector_desc()
         d.n_showers, d.h_obs = n_showers, h_obs
+        d.geometry, d.earth_radius = (CS_GEOM_SPHERICAL if spherical else CS_GEOM_PLANAR), earth_radius
         if hist:
             d.hist_nx, d.hist_ny = hist["nx"], hist["ny"]
             d.hist_x0, d.hist_y0, d.hist_dx, d.hist_dy = hist["x0"], hist["y0"], hist["dx"], hist["dy"]
@@ -458,6 +468,39 @@ def cs_surrogate_config_default():
     c = cs_surrogate_config()
     lib().cs_surrogate_config_default(C.byref(c))
     return c
+
+
+class Streamer:
+    """Owns a cs_streamer: host segments streamed in chunks through two device
+    buffers on two streams (copies overlap kernels)."""
+
+    def __init__(self, chunk):
+        h = C.c_void_p()
+        _check(lib().cs_streamer_create(chunk, C.byref(h)), "cs_streamer_create")
+        self.handle, self.chunk = h, chunk
+
+    def run(self, host_segs_ptr, n, atm, det, out, seed=0, bunch=1, s_max=1.0, seg_base=0, accumulate=False,
+            surrogate=None, stream=None):
+        """host_segs_ptr: address of n packed segments in host memory; out: a
+        cs_output of device pointers.  Enqueues on `stream` (default: torch's)."""
+        o = cs_opts_default()
+        o.bunch, o.s_max, o.seg_base, o.device_ptrs, o.accumulate = bunch, s_max, seg_base, 1, int(accumulate)
+        if surrogate is not None:
+            o.surrogate = surrogate.handle
+        _check(lib().cs_streamer_run(self.handle, C.c_void_p(host_segs_ptr), n, atm.handle, det.handle, seed,
+                                     C.byref(o), C.byref(out), stream if stream is not None else stream_ptr()),
+               "cs_streamer_run")
+
+    def close(self):
+        if self.handle:
+            lib().cs_streamer_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Surrogate:

@@ -32,6 +32,8 @@ struct TableView {
 // Everything a kernel needs about the atmosphere, passed by value.
 struct AtmParams {
     int kind;            // CS_ATM_*
+    int spherical;       // 1: spherical shell (Earth centre at (0, 0, -R))
+    float R, rg;         // Earth radius and R + h_obs [m]
     int n_layers;
     int refraction;
     int transmission;
@@ -58,6 +60,8 @@ struct AtmParams {
 
 struct DetParams {
     int n_showers;
+    int spherical;        // telescope layout and histogram in azimuthal-equidistant coordinates
+    double R;
     float h_obs_f;        // observation level the telescopes were placed for
     double h_obs;
     int nx, ny;           // 0: no histogram
@@ -66,6 +70,7 @@ struct DetParams {
     int n_tel;
     const float4* tel;    // {x_hi, y_hi, z - h_obs, radius}
     const float2* tel_lo; // {x_lo, y_lo}
+    const float4* tel3;   // spherical: centre in frame coordinates and radius
     // uniform grid hash over the telescopes' reach discs
     float gx0, gy0, inv_cell;
     int gnx, gny;
@@ -103,6 +108,8 @@ struct AtmF64 {
     double lin_h0, lin_h1, lin_n0, lin_n1, hom_delta;
     double h_obs, H_A;
     int refraction;
+    int spherical;          // 1: spherical shell, Earth radius R
+    double R;
 };
 
 

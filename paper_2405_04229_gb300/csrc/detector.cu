@@ -11,7 +11,7 @@
 
 namespace {
 
-constexpr double kHashTheta = 60.0 * 3.14159265358979323846 / 180.0;  // hash serves zenith <= 60 deg
+constexpr double kHashTheta = 75.0 * 3.14159265358979323846 / 180.0;  // hash serves zenith <= 75 deg
 
 void split(double v, float* hi, float* lo) {
     *hi = (float)v;
@@ -30,6 +30,9 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
     if (d->hist_nx > 0 && (!(d->hist_dx > 0.0) || !(d->hist_dy > 0.0))) return CS_ERR_INVALID_ARG;
     if ((double)d->hist_nx * d->hist_ny * d->n_showers > 4e9) return CS_ERR_INVALID_ARG;
     if (d->n_tel < 0 || (d->n_tel > 0 && !d->tel_xyzr)) return CS_ERR_INVALID_ARG;
+    if (d->geometry != CS_GEOM_PLANAR && d->geometry != CS_GEOM_SPHERICAL) return CS_ERR_INVALID_ARG;
+    if (d->geometry == CS_GEOM_SPHERICAL && (d->earth_radius < 0.0 || !isfinite(d->earth_radius)))
+        return CS_ERR_INVALID_ARG;
     for (int i = 0; i < d->n_tel; ++i) {
         const double* t = d->tel_xyzr + 4 * i;
         if (!isfinite(t[0]) || !isfinite(t[1]) || !isfinite(t[2]) || !(t[3] > 0.0)) return CS_ERR_INVALID_ARG;
@@ -42,6 +45,8 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
     cudaGetDevice(&h->device);
     cs::DetParams& p = h->p;
     p.n_showers = d->n_showers;
+    p.spherical = d->geometry == CS_GEOM_SPHERICAL ? 1 : 0;
+    p.R = d->earth_radius > 0.0 ? d->earth_radius : 6370000.0;
     p.h_obs = d->h_obs;
     p.h_obs_f = (float)d->h_obs;
     p.nx = d->hist_nx;
@@ -54,8 +59,8 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
     }
     p.n_tel = d->n_tel;
 
-    // host-side layout: tel float4, tel_lo float2, cell_start, cell_tel
-    std::vector<float4> tel(d->n_tel);
+    // host-side layout: tel float4, tel_lo float2, tel3 float4, cell_start, cell_tel
+    std::vector<float4> tel(d->n_tel), tel3(p.spherical ? d->n_tel : 0);
     std::vector<float2> tel_lo(d->n_tel);
     std::vector<int> cell_start(1, 0), cell_tel;
     if (d->n_tel > 0) {
@@ -68,7 +73,13 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
             split(t[1], &tel[i].y, &lo); tel_lo[i].y = lo;
             tel[i].z = (float)(t[2] - d->h_obs);
             tel[i].w = (float)t[3];
-            // ground points whose arrival line (zenith <= 60 deg) passes within r of
+            if (p.spherical) {   // centre h = t[2] above the azimuthal-equidistant point (x, y)
+                const double rg = p.R + d->h_obs, s = sqrt(t[0] * t[0] + t[1] * t[1]), a = s / rg;
+                const double r = p.R + t[2], cx = s > 0.0 ? t[0] / s : 1.0, cy = s > 0.0 ? t[1] / s : 0.0;
+                tel3[i] = make_float4((float)(r * sin(a) * cx), (float)(r * sin(a) * cy), (float)(r * cos(a) - p.R),
+                                      (float)t[3]);
+            }
+            // ground points whose arrival line (zenith <= 75 deg) passes within r of
             // the centre lie within r / cos + |dz| tan of the centre's footprint
             reach[i] = t[3] / cos(kHashTheta) + fabs(t[2] - d->h_obs) * tan(kHashTheta) + 0.01;
             reach_max = fmax(reach_max, reach[i]);
@@ -100,11 +111,20 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
         p.gny = gny;
         p.bx0 = (float)x0; p.bx1 = (float)(x0 + gnx * cell);
         p.by0 = (float)y0; p.by1 = (float)(y0 + gny * cell);
-        p.hash_sin2_max = (float)(sin(kHashTheta) * sin(kHashTheta));
+        // on the sphere the local vertical at a ground point in the box leans from
+        // the frame's z axis by up to the box's extent / r_g: photons steeper than
+        // the hash's zenith in the local frame must be steeper in the frame's too
+        double theta = kHashTheta;
+        if (p.spherical) {
+            const double ex = fmax(fabs(x0), fabs(x0 + gnx * cell)), ey = fmax(fabs(y0), fabs(y0 + gny * cell));
+            theta -= 1.01 * sqrt(ex * ex + ey * ey) / (p.R + d->h_obs) + 1e-6;
+        }
+        p.hash_sin2_max = (float)(sin(theta) * sin(theta));
     }
     const size_t o_tel = 0;
     const size_t o_lo = align_up(o_tel + tel.size() * sizeof(float4));
-    const size_t o_cs = align_up(o_lo + tel_lo.size() * sizeof(float2));
+    const size_t o_t3 = align_up(o_lo + tel_lo.size() * sizeof(float2));
+    const size_t o_cs = align_up(o_t3 + tel3.size() * sizeof(float4));
     const size_t o_ct = align_up(o_cs + cell_start.size() * sizeof(int));
     const size_t total = align_up(o_ct + (cell_tel.size() + 1) * sizeof(int));
     cudaError_t e = cudaMalloc(&h->d_mem, total);
@@ -113,12 +133,14 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
     std::vector<char> host(total, 0);
     if (!tel.empty()) memcpy(host.data() + o_tel, tel.data(), tel.size() * sizeof(float4));
     if (!tel_lo.empty()) memcpy(host.data() + o_lo, tel_lo.data(), tel_lo.size() * sizeof(float2));
+    if (!tel3.empty()) memcpy(host.data() + o_t3, tel3.data(), tel3.size() * sizeof(float4));
     memcpy(host.data() + o_cs, cell_start.data(), cell_start.size() * sizeof(int));
     if (!cell_tel.empty()) memcpy(host.data() + o_ct, cell_tel.data(), cell_tel.size() * sizeof(int));
     e = cudaMemcpy(h->d_mem, host.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cs::set_last_error("detector copy", e); cudaFree(h->d_mem); delete h; return CS_ERR_CUDA; }
     p.tel = (const float4*)(base + o_tel);
     p.tel_lo = (const float2*)(base + o_lo);
+    p.tel3 = p.spherical ? (const float4*)(base + o_t3) : nullptr;
     p.cell_start = (const int*)(base + o_cs);
     p.cell_tel = (const int*)(base + o_ct);
     *out = h;

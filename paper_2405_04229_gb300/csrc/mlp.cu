@@ -34,7 +34,9 @@ namespace {
 //   A_KM: A is stored [K][M] (else [M][K]);  B_KN: B is stored [K][N] (else [N][K]).
 //   SPLIT_A / SPLIT_B: the FP32 operand is staged as a BF16 hi + lo pair and
 //   the products hi*hi + lo*hi (+ hi*lo) are accumulated.
-//   EPI: 0 store, 1 store tanh(C + bias[n]), 2 store C + bias[n], 3 atomicAdd.
+//   EPI: 0 store, 1 store tanh(C + bias[n]), 2 store C + bias[n], 3 store the
+//   partial product of K slice z = blockIdx.z at C + z M ldc (summed in a
+//   fixed order afterwards, so training is deterministic).
 // One 64 x 64 output tile per block of 4 warps (32 x 32 each); K in chunks of
 // 32 staged through shared memory; blockIdx.z splits K for EPI 3.
 // ---------------------------------------------------------------------------
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(128) gemm_kernel(const float* __restrict__ A, 
                 if (EPI == 0) *dst = v;
                 else if (EPI == 1) *dst = tanh_act(v + bias[col]);
                 else if (EPI == 2) *dst = v + bias[col];
-                else atomicAdd(dst, v);
+                else dst[(size_t)blockIdx.z * M * ldc] = v;
             }
 }
 
@@ -149,13 +151,15 @@ __global__ void layer1_kernel(const float* __restrict__ X, int B, const float* _
     H1[i] = tanh_act(fmaf(w[2], x[2], fmaf(w[1], x[1], fmaf(w[0], x[0], p[kOffB1 + u]))));
 }
 
-// dY = 2 w (Y - T) / B on the valid outputs (w = 1 without weights), the
-// loss (1/B) sum w (Y - T)^2, and db4.
+// dY = 2 w (Y - T) / B on the valid outputs (w = 1 without weights); per
+// block, the partial loss (1/B) sum w (Y - T)^2 and the partial db4 go to
+// part[block * 4 + {0: loss, 1..3: db4}].
 __global__ void loss_grad_kernel(const float* __restrict__ Y, const float* __restrict__ T,
                                  const float* __restrict__ Wt, int B, float* __restrict__ dY,
-                                 float* __restrict__ grad, float* __restrict__ loss) {
+                                 float* __restrict__ part) {
+    __shared__ float red[8][4];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    float l = 0.0f, d[kNOut] = {0.0f, 0.0f, 0.0f};
+    float v4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (i < B) {
 #pragma unroll
         for (int o = 0; o < kNOutP; ++o) {
@@ -163,29 +167,54 @@ __global__ void loss_grad_kernel(const float* __restrict__ Y, const float* __res
             if (o < kNOut) {
                 const float e = Y[(size_t)i * kNOutP + o] - T[(size_t)i * kNOut + o];
                 const float wt = Wt ? Wt[(size_t)i * kNOut + o] : 1.0f;
-                l += wt * e * e / B;
+                v4[0] += wt * e * e / B;
                 v = 2.0f * wt * e / B;
-                d[o] = v;
+                v4[1 + o] = v;
             }
             dY[(size_t)i * kNOutP + o] = v;
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        l += __shfl_xor_sync(0xffffffffu, l, o);
+    for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int c = 0; c < kNOut; ++c) d[c] += __shfl_xor_sync(0xffffffffu, d[c], o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(loss, l);
+        for (int c = 0; c < 4; ++c) v4[c] += __shfl_xor_sync(0xffffffffu, v4[c], o);
+    if ((threadIdx.x & 31) == 0)
 #pragma unroll
-        for (int c = 0; c < kNOut; ++c) atomicAdd(grad + kOffB4 + c, d[c]);
+        for (int c = 0; c < 4; ++c) red[threadIdx.x >> 5][c] = v4[c];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        float t = 0.0f;
+        for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) t += red[wi][threadIdx.x];
+        part[blockIdx.x * 4 + threadIdx.x] = t;
     }
 }
 
-// dZ = dH * (1 - H^2) and the bias gradient (column sums of dZ).
+// out[j] = sum over r = 0 .. rows - 1 of part[r * stride + j], in row order
+// (deterministic); one thread per column j < width.
+__global__ void sum_rows_kernel(const float* __restrict__ part, int rows, int stride, int width,
+                                float* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= width) return;
+    float t = 0.0f;
+    for (int r = 0; r < rows; ++r) t += part[(size_t)r * stride + j];
+    out[j] = t;
+}
+
+// Sum of the split-K slices of a gradient GEMM into dst (leading dimension ldc).
+__global__ void sum_slices_kernel(const float* __restrict__ part, int splits, int M, int N, float* __restrict__ dst,
+                                  int ldc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * N) return;
+    float t = 0.0f;
+    for (int z = 0; z < splits; ++z) t += part[(size_t)z * M * N + i];
+    dst[(size_t)(i / N) * ldc + i % N] = t;
+}
+
+// dZ = dH * (1 - H^2) and, per block of 64 rows, the partial bias gradient
+// (column sums of dZ) in bpart[block * 64 + unit].
 __global__ void tanh_back_kernel(const float* __restrict__ dH, const float* __restrict__ H, int B,
-                                 float* __restrict__ dZ, float* __restrict__ gbias) {
+                                 float* __restrict__ dZ, float* __restrict__ bpart) {
+    __shared__ float red[4][64];
     const int u = threadIdx.x & 63;          // blockDim = 256: 4 rows x 64 units per pass
     const int r0 = blockIdx.x * 64 + (threadIdx.x >> 6);
     float s = 0.0f;
@@ -195,11 +224,13 @@ __global__ void tanh_back_kernel(const float* __restrict__ dH, const float* __re
         dZ[i] = z;
         s += z;
     }
-    atomicAdd(gbias + u, s);
+    red[threadIdx.x >> 6][u] = s;
+    __syncthreads();
+    if (threadIdx.x < 64) bpart[blockIdx.x * 64 + u] = (red[0][u] + red[1][u]) + (red[2][u] + red[3][u]);
 }
 
-// dW1 = dZ1^T X (3 inputs): one block per hidden unit.
 __global__ void grad_w1_kernel(const float* __restrict__ dZ, const float* __restrict__ X, int B, float* __restrict__ grad) {
+    __shared__ float red[8][kNIn];
     const int u = blockIdx.x;
     float s[kNIn] = {0.0f, 0.0f, 0.0f};
     for (int r = threadIdx.x; r < B; r += blockDim.x) {
@@ -212,7 +243,13 @@ __global__ void grad_w1_kernel(const float* __restrict__ dZ, const float* __rest
         float v = s[c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(grad + kOffW1 + u * kNIn + c, v);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNIn) {
+        float t = 0.0f;
+        for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) t += red[wi][threadIdx.x];
+        grad[kOffW1 + u * kNIn + threadIdx.x] = t;
     }
 }
 
@@ -336,7 +373,13 @@ __global__ void gather_kernel(const float* __restrict__ X, const float* __restri
 struct Work {
     float *H1, *H2, *H3, *Y, *dY, *dH, *dZ;
     float* loss;
+    float* part;   // reduction scratch, work_part_floats(B)
 };
+
+int grad_splits(int B) { return std::max(1, B / 2048); }
+size_t work_part_floats(int B) {
+    return (size_t)grad_splits(B) * kHid * kHid + (size_t)((B + 63) / 64) * 64 + (size_t)((B + 255) / 256) * 4;
+}
 
 void forward(const float* X, int B, const float* pr, const Work& w, cudaStream_t s) {
     layer1_kernel<<<(unsigned)(((size_t)B * kHid + 255) / 256), 256, 0, s>>>(X, B, pr, w.H1);
@@ -347,20 +390,34 @@ void forward(const float* X, int B, const float* pr, const Work& w, cudaStream_t
 
 void backward(const float* X, const float* T, const float* Wt, int B, const float* pr, float* g, const Work& w,
               cudaStream_t s) {
-    const int splits = std::max(1, B / 2048);
-    loss_grad_kernel<<<(B + 255) / 256, 256, 0, s>>>(w.Y, T, Wt, B, w.dY, g, w.loss);
+    const int splits = grad_splits(B);
+    float* gpart = w.part;                                    // split-K slices of a weight gradient
+    float* bpart = gpart + (size_t)splits * kHid * kHid;      // per-block bias partials
+    float* lpart = bpart + (size_t)((B + 63) / 64) * 64;      // per-block loss and db4 partials
+    const int nb64 = (B + 63) / 64, nb256 = (B + 255) / 256;
+    auto wgrad = [&](const float* dOut, int n_out, const float* In, float* dst) {
+        gemm<true, true, true, true, 3>(dOut, n_out, In, kHid, gpart, kHid, n_out, kHid, B, nullptr, s, splits);
+        sum_slices_kernel<<<(n_out * kHid + 255) / 256, 256, 0, s>>>(gpart, splits, n_out, kHid, dst, kHid);
+    };
+    auto bgrad = [&](float* dst) { sum_rows_kernel<<<1, 64, 0, s>>>(bpart, nb64, 64, 64, dst); };
+    loss_grad_kernel<<<nb256, 256, 0, s>>>(w.Y, T, Wt, B, w.dY, lpart);
+    sum_rows_kernel<<<1, 32, 0, s>>>(lpart, nb256, 4, 1, w.loss);
+    sum_rows_kernel<<<1, 32, 0, s>>>(lpart + 1, nb256, 4, kNOut, g + kOffB4);
     // layer 4: dW4 = dY^T H3, dH3 = dY W4
-    gemm<true, true, true, true, 3>(w.dY, kNOutP, w.H3, kHid, g + kOffW4, kHid, kNOutP, kHid, B, nullptr, s, splits);
+    wgrad(w.dY, kNOutP, w.H3, g + kOffW4);
     gemm<false, true, true, false, 0>(w.dY, kNOutP, pr + kOffW4, kHid, w.dH, kHid, B, kHid, kNOutP, nullptr, s);
-    tanh_back_kernel<<<(B + 63) / 64, 256, 0, s>>>(w.dH, w.H3, B, w.dZ, g + kOffB3);
+    tanh_back_kernel<<<nb64, 256, 0, s>>>(w.dH, w.H3, B, w.dZ, bpart);
+    bgrad(g + kOffB3);
     // layer 3
-    gemm<true, true, true, true, 3>(w.dZ, kHid, w.H2, kHid, g + kOffW3, kHid, kHid, kHid, B, nullptr, s, splits);
+    wgrad(w.dZ, kHid, w.H2, g + kOffW3);
     gemm<false, true, true, false, 0>(w.dZ, kHid, pr + kOffW3, kHid, w.dH, kHid, B, kHid, kHid, nullptr, s);
-    tanh_back_kernel<<<(B + 63) / 64, 256, 0, s>>>(w.dH, w.H2, B, w.dZ, g + kOffB2);
+    tanh_back_kernel<<<nb64, 256, 0, s>>>(w.dH, w.H2, B, w.dZ, bpart);
+    bgrad(g + kOffB2);
     // layer 2
-    gemm<true, true, true, true, 3>(w.dZ, kHid, w.H1, kHid, g + kOffW2, kHid, kHid, kHid, B, nullptr, s, splits);
+    wgrad(w.dZ, kHid, w.H1, g + kOffW2);
     gemm<false, true, true, false, 0>(w.dZ, kHid, pr + kOffW2, kHid, w.dH, kHid, B, kHid, kHid, nullptr, s);
-    tanh_back_kernel<<<(B + 63) / 64, 256, 0, s>>>(w.dH, w.H1, B, w.dZ, g + kOffB1);
+    tanh_back_kernel<<<nb64, 256, 0, s>>>(w.dH, w.H1, B, w.dZ, bpart);
+    bgrad(g + kOffB1);
     // layer 1 (3 inputs)
     grad_w1_kernel<<<kHid, 256, 0, s>>>(w.dZ, X, B, g);
 }
@@ -400,8 +457,8 @@ extern "C" void cs_surrogate_config_default(cs_surrogate_config* c) {
     if (!c) return;
     c->n_train = 1 << 20;
     c->n_heldout = 1 << 16;
-    c->batch = 16384;
-    c->epochs = 800;
+    c->batch = 32768;
+    c->epochs = 1600;
     c->seed = 0;
     c->lr = 1e-2;
     c->lr_min = 1e-5;
@@ -456,13 +513,14 @@ extern "C" cs_status cs_surrogate_train(const cs_atmosphere* atm, const cs_surro
     w.Y = (float*)A((size_t)B * kNOutP * 4);
     w.dY = (float*)A((size_t)B * kNOutP * 4);
     w.loss = (float*)A(256);
+    w.part = (float*)A(work_part_floats(B) * 4);
     float* p = (float*)A(kNParams * 4);
     float* pr = (float*)A(kNParams * 4);
     float* g = (float*)A(kNParams * 4);
     float* m = (float*)A(kNParams * 4);
     float* v = (float*)A(kNParams * 4);
     if (!hth || !lam || !lab || !X || !T || !Xb || !Tb || !w.H1 || !w.H2 || !w.H3 || !w.dH || !w.dZ || !w.Y ||
-        !w.dY || !w.loss || !p || !pr || !g || !m || !v) {
+        !w.dY || !w.loss || !w.part || !p || !pr || !g || !m || !v) {
         cleanup();
         return CS_ERR_CUDA;
     }
@@ -714,10 +772,12 @@ extern "C" cs_status cs_mlp_loss_grad(const float* params, const float* x, const
     w.Y = A((size_t)B * kNOutP * 4);
     w.dY = A((size_t)B * kNOutP * 4);
     w.loss = A(256);
+    w.part = A(work_part_floats(B) * 4);
     auto cleanup = [&]() {
         for (void* b : bufs) cudaFree(b);
     };
-    if (!X || !T || !p || !pr || !g || !w.H1 || !w.H2 || !w.H3 || !w.dH || !w.dZ || !w.Y || !w.dY || !w.loss) {
+    if (!X || !T || !p || !pr || !g || !w.H1 || !w.H2 || !w.H3 || !w.dH || !w.dZ || !w.Y || !w.dY || !w.loss ||
+        !w.part) {
         cleanup();
         return CS_ERR_CUDA;
     }

@@ -36,9 +36,11 @@ constexpr int kQBits = 10;              // map entry: sub-step (10 bits) | bunch
 // and one round of sub-steps with its bunch map.
 struct TileSmem {
     float4 segA[kTile];   // Px, Py, Pz, 1 / (1 - Pz)
-    float4 segB[kTile];   // Hs_hi, Hs_lo (z0 - h_obs), L / K, 1 / (beta c)
-    float4 segC[kTile];   // ground intercept G in the frame, float-float x and y
-    float4 segD[kTile];   // G in histogram cells, float-float x and y
+    // planar | spherical shell
+    float4 segB[kTile];   // Hs_hi, Hs_lo (z0 - h_obs), L / K, 1 / (beta c) | Hs, tilt_z, L / K, 1 / (beta c)
+    float4 segC[kTile];   // ground intercept G, float-float x and y | start point (hi), radial P component
+    float4 segD[kTile];   // G in histogram cells, float-float x and y | start point (lo), 1 / r
+    float4 segE[kTile];   // spherical shell: local-vertical tilt at the start, v - z
     double t0[kTile];
     float g[kTile], z2[kTile];
     int shower[kTile];
@@ -98,6 +100,10 @@ __device__ __forceinline__ void emit_record(const OutParams& o, unsigned long lo
 
 // Stage 1 (Sec. 5.3.1): import one segment, filter it, fold its parameters
 // and compute its local origin.  Returns the number of sub-steps (0 if invalid).
+// Planar: the origin is the ground intercept of the segment's line (float-float).
+// Spherical shell: the start point (float-float), its altitude above h_obs,
+// the radial component of P, 1 / r and the tilt of the local vertical.
+template <bool SPH>
 __device__ __forceinline__ int import_segment(TileSmem& S, int t, const cs_segment* seg, const PropParams& pp,
                                               const AtmParams& ap, const DetParams& dp, unsigned int& invalid) {
     const double2* src = reinterpret_cast<const double2*>(seg);
@@ -119,6 +125,30 @@ __device__ __forceinline__ int import_segment(TileSmem& S, int t, const cs_segme
     const float Px = dir.x * inv_n, Py = dir.y * inv_n, Pz = dir.z * inv_n;
     const float L = dir.w;
     const int K = max(1, (int)ceilf(L / pp.s_max));
+    if (SPH) {
+        const float R = ap.R;
+        const float x_hi = (float)xy.x, x_lo = (float)(xy.x - (double)x_hi);
+        const float y_hi = (float)xy.y, y_lo = (float)(xy.y - (double)y_hi);
+        const float z_hi = (float)zt.x, z_lo = (float)(zt.x - (double)z_hi);
+        // altitude h = |S - c| - R = z + rho^2 / (|S - c| + z + R), c = (0, 0, -R), without cancellation
+        const float rho2 = x_hi * x_hi + y_hi * y_hi, a = z_hi + R;
+        const float rr = sqrtf(rho2 + a * a);
+        const float lift = rho2 / (rr + a);
+        const float Hs = (float)(zt.x - ap.h_obs) + lift;
+        const float inv_r = 1.0f / rr;
+        const float dvx = x_hi * inv_r, dvy = y_hi * inv_r, dvz = -lift * inv_r;   // v - z-hat
+        const float Pr = Px * dvx + Py * dvy + Pz * (1.0f + dvz);
+        S.segA[t] = make_float4(Px, Py, Pz, 1.0f / (1.0f - Pz));
+        S.segB[t] = make_float4(Hs, dvz, L / (float)K, rsqrtf(1.0f - g) * kInvC);
+        S.segC[t] = make_float4(x_hi, y_hi, z_hi, Pr);
+        S.segD[t] = make_float4(x_lo, y_lo, z_lo, inv_r);
+        S.t0[t] = zt.y;
+        S.g[t] = g;
+        S.z2[t] = z * z;
+        S.shower[t] = (int)shower;
+        S.bunch[t] = pp.shower_bunch ? __ldg(pp.shower_bunch + shower) : pp.bunch;
+        return K;
+    }
     // local origin: Hs = z0 - h_obs and G = S_xy - Hs P_xy / P_z in float-float
     const double Hs = zt.x - ap.h_obs;
     const float Hs_hi = (float)Hs, Hs_lo = (float)(Hs - (double)Hs_hi);
@@ -159,11 +189,17 @@ __device__ __forceinline__ int import_segment(TileSmem& S, int t, const cs_segme
 // Stage 2 (Eq. 2.2-2.5, Sec. 4.2.1): sub-step k of tile segment sg at local
 // slot q: angle and mean bunch count at the sub-step midpoint, stochastic
 // rounding with the sub-step's own draw.  Returns the bunch count.
+template <bool SPH>
 __device__ __forceinline__ int substep(TileSmem& S, int q, int sg, int k, long long base, const PropParams& pp,
                                        const AtmParams& ap) {
     const float4 B = S.segB[sg];
-    const float Pz = S.segA[sg].z;
-    const float dz_mid = B.x + (B.y + ((float)k + 0.5f) * B.z * Pz);
+    float dz_mid;
+    if (SPH) {   // altitude along the track: Hs + s Pr + s^2 (1 - Pr^2) / (2 r)
+        const float Pr = S.segC[sg].w, s_mid = ((float)k + 0.5f) * B.z;
+        dz_mid = B.x + s_mid * fmaf(s_mid * 0.5f * S.segD[sg].w, fmaf(-Pr, Pr, 1.0f), Pr);
+    } else {
+        dz_mid = B.x + (B.y + ((float)k + 0.5f) * B.z * S.segA[sg].z);
+    }
     const float d = delta_at(ap, dz_mid);
     const float g = S.g[sg];
     const float onepd = 1.0f + d;
@@ -187,12 +223,86 @@ struct Tally {
     unsigned int absorbed, hist, tel, upward;
 };
 
-// Stages 3-5 for one bunch: generation on the cone (Sec. 4.2), the upward
-// filter (Sec. 5.3.4), straight line (Eq. 3.3) plus the interpolation-tracing
-// correction (Sec. 4.4.1) or the surrogate network, transmission (Sec. 4.3.1)
-// and detection.  With SURR the whole warp must call (inactive lanes pass
-// active = false): the network runs warp-collectively on the tensor cores.
+// Telescopes: the sphere whose centre is closest to the arrival line, if
+// closer than its radius (ties: lowest index).  (ddx, ddy, ddz)(it) gives the
+// centre minus the ground point for telescope it.  Arrivals within the
+// hash's zenith range test the spheres listed for their grid cell (none
+// outside the box of all reach discs); steeper ones test every sphere.
+template <typename Delta>
+__device__ __forceinline__ int hit_telescope(const DetParams& dp, float x, float y, float ugx, float ugy, float ugz,
+                                             Delta delta) {
+    int tel = -1;
+    float best_d2 = 3.0e38f;
+    auto test = [&](int it) {
+        float ddx, ddy, ddz, r;
+        delta(it, ddx, ddy, ddz, r);
+        const float along = ddx * ugx + ddy * ugy + ddz * ugz;
+        const float d2 = ddx * ddx + ddy * ddy + ddz * ddz - along * along;
+        if (d2 < r * r && d2 < best_d2) {
+            best_d2 = d2;
+            tel = it;
+        }
+    };
+    if (ugx * ugx + ugy * ugy <= dp.hash_sin2_max) {
+        if (!(x >= dp.bx0 && x < dp.bx1 && y >= dp.by0 && y < dp.by1)) return -1;
+        const int cx = (int)((x - dp.gx0) * dp.inv_cell);
+        const int cy = (int)((y - dp.gy0) * dp.inv_cell);
+        if (cx >= 0 && cx < dp.gnx && cy >= 0 && cy < dp.gny) {
+            const int c = cy * dp.gnx + cx;
+            const int e0 = __ldg(dp.cell_start + c), e1 = __ldg(dp.cell_start + c + 1);
+            for (int e = e0; e < e1; ++e) test(__ldg(dp.cell_tel + e));
+        }
+    } else {
+        for (int it = 0; it < dp.n_tel; ++it) test(it);
+    }
+    return tel;
+}
+
+// The correction fields at (dz, tan^2 of the local zenith) and the
+// transmission: the network's outputs where it applies, else the bilinear
+// table lookup; (0, 0, 1) without tables.
 template <bool SURR>
+__device__ __forceinline__ void correction_fields(const AtmParams& ap, bool use_net, const float (&net)[3], float dz,
+                                                  float w, float inv_l, float inv_uz, float& GR, float& Gt,
+                                                  float& Tr) {
+    GR = 0.0f;
+    Gt = 0.0f;
+    Tr = 1.0f;
+    if (!ap.use_tables) return;
+    if (SURR && use_net) {
+        GR = net[0];
+        Gt = net[1];
+        Tr = fminf(ex2_approx(net[2] * (float)kLog2e), 1.0f);   // the network gives ln T
+    } else {
+        // bilinear in (h, tan^2 theta0) on cells stored as value + change
+        const float fh = dz * ap.tv.inv_dh, fw = w * ap.tv.inv_dw;
+        const int j = min((int)fh, ap.tv.nh - 1);
+        const int m = min((int)fw, ap.tv.nw - 2);
+        const float fj = fh - (float)j, gm = fw - (float)m;
+        const float4* row = ap.tv.tab + ((size_t)j * ap.tv.nw + m) * 2;
+        const float4 v0 = __ldg(row), s0 = __ldg(row + 1), v1 = __ldg(row + 2), s1 = __ldg(row + 3);
+        const float a0 = 1.0f - gm;
+        GR = a0 * fmaf(fj, s0.x, v0.x) + gm * fmaf(fj, s1.x, v1.x);
+        Gt = a0 * fmaf(fj, s0.y, v0.y) + gm * fmaf(fj, s1.y, v1.y);
+        if (ap.transmission) {
+            const float GX = a0 * fmaf(fj, s0.z, v0.z) + gm * fmaf(fj, s1.z, v1.z);
+            const float GA = a0 * fmaf(fj, s0.w, v0.w) + gm * fmaf(fj, s1.w, v1.w);
+            const float il2 = inv_l * inv_l;
+            const float kR = ap.kR0 * il2 * il2;
+            const float kA = ap.kA0 * ex2_approx(ap.aer_alpha * lg2_approx(ap.lamA_nm * inv_l));
+            Tr = ex2_approx(-(GX * kR + GA * kA) * inv_uz);
+        }
+    }
+    if (!ap.transmission) Tr = 1.0f;
+}
+
+// Stages 3-5 for one bunch: generation on the cone (Sec. 4.2), the upward
+// filter (Sec. 5.3.4), straight line (Eq. 3.3; on the sphere, the vacuum
+// line to the ground sphere) plus the interpolation-tracing correction
+// (Sec. 4.4.1) or the surrogate network, transmission (Sec. 4.3.1) and
+// detection.  With SURR the whole warp must call (inactive lanes pass
+// active = false): the network runs warp-collectively on the tensor cores.
+template <bool SURR, bool SPH>
 __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool active, long long base,
                                       const PropParams& pp, const AtmParams& ap, const DetParams& dp,
                                       const OutParams& op, const SurrogateView& sv, Tally& T, bool want_records) {
@@ -208,7 +318,6 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
     const unsigned int b = (unsigned int)S.bunch[sg];
     // translation to a random point of the sub-step (Fig. 4.2c)
     const float ell = ((float)k + u0) * B.z;
-    const float dz = B.x + (B.y + ell * Pz);
     // cone vector rotated into the track frame (Sec. 4.2): u = cos P + sin M e(phi),
     // M the 180-degree rotation about the bisector of (0,0,-1) and P
     float sphi, cphi;
@@ -218,10 +327,32 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
     const float mx = Px * ce - cphi, my = Py * ce - sphi, mz = (Pz - 1.0f) * ce;
     const float ct = Q.x, st = Q.y;
     const float ux = ct * Px + st * mx, uy = ct * Py + st * my, uz = ct * Pz + st * mz;
-    const float inv_uz = rcp_approx(-uz);
-    const float w = (ux * ux + uy * uy) * inv_uz * inv_uz;   // tan^2(theta0)
+    // height above the observation level and the local zenith
+    float dz, cos_z, sin2;
+    float4 Cc, Dd;
+    float dvx = 0.0f, dvy = 0.0f, dvz = 0.0f;
+    if (!SPH) {
+        dz = B.x + (B.y + ell * Pz);
+        cos_z = -uz;
+        sin2 = ux * ux + uy * uy;
+    } else {
+        Cc = S.segC[sg];
+        Dd = S.segD[sg];
+        // tilt of the local vertical at the start, v - z-hat = (x / r, y / r, B.y)
+        const float ex = Cc.x * Dd.w, ey = Cc.y * Dd.w, ez = B.y;
+        dz = B.x + ell * fmaf(ell * 0.5f * Dd.w, fmaf(-Cc.w, Cc.w, 1.0f), Cc.w);
+        const float f = ell * Dd.w;   // the local vertical turns by ell / r along the track
+        dvx = ex + f * (Px - Cc.w * ex);
+        dvy = ey + f * (Py - Cc.w * ey);
+        dvz = ez + f * (Pz - Cc.w * (1.0f + ez));
+        cos_z = -(uz + ux * dvx + uy * dvy + uz * dvz);
+        const float hx = ux + cos_z * dvx, hy = uy + cos_z * dvy, hz = uz + cos_z * (1.0f + dvz);
+        sin2 = hx * hx + hy * hy + hz * hz;
+    }
+    const float inv_uz = rcp_approx(cos_z);
+    const float w = sin2 * inv_uz * inv_uz;   // tan^2 of the local zenith
     int status = CS_ST_LANDED;
-    if (!(uz < 0.0f)) status = CS_ST_UPWARD;                 // discarded (Sec. 5.3.4)
+    if (!(cos_z > 0.0f)) status = CS_ST_UPWARD;              // discarded (Sec. 5.3.4)
     else if (dz < 0.0f) status = CS_ST_BELOW;
     else if (ap.use_tables && (w > ap.tv.w_max || dz >= ap.tv.dz_max)) status = CS_ST_DOMAIN;
 
@@ -229,10 +360,9 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
     float net[3] = {0.0f, 0.0f, 1.0f};
     bool use_net = false;
     if (SURR) {
-        const float mu = -uz;   // cos(theta0)
-        use_net = active && status == CS_ST_LANDED && in_surrogate_domain(sv, dz, mu);
+        use_net = active && status == CS_ST_LANDED && in_surrogate_domain(sv, dz, cos_z);
         const float x[3] = {use_net ? fmaf(sv.in_scale[0], height_coordinate(sv, dz), sv.in_shift[0]) : 0.0f,
-                            use_net ? fmaf(sv.in_scale[1], mu, sv.in_shift[1]) : 0.0f,
+                            use_net ? fmaf(sv.in_scale[1], cos_z, sv.in_shift[1]) : 0.0f,
                             use_net ? fmaf(sv.in_scale[2], inv_l, sv.in_shift[2]) : 0.0f};
         float y[3];
         if (sv.split) net32<true>(sv, x, y);
@@ -245,7 +375,7 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
     // ---- propagation and detection -----------------------------------------------
     int tel = -1, bin = -1;
     float x = 0.0f, y = 0.0f, t_rel = ell * B.w;
-    if (status == CS_ST_LANDED) {
+    if (status == CS_ST_LANDED && !SPH) {
         float rx, ry;
         if (Pz < -1e-3f) {
             // I - G = dz (P_xy / P_z - u_xy / u_z); the numerator is sin(theta) (P x m)
@@ -258,40 +388,13 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
             ry = ell * Py + dz * uy * inv_uz;
         }
         float path = dz * inv_uz;
-        float Tr = 1.0f;
-        if (ap.use_tables) {
-            float GR, Gt, GX = 0.0f, GA = 0.0f;
-            if (SURR && use_net) {
-                GR = net[0];
-                Gt = net[1];
-                Tr = fminf(ex2_approx(net[2] * (float)kLog2e), 1.0f);   // the network gives ln T
-            } else {
-                // bilinear in (h, tan^2 theta0) on cells stored as value + change
-                const float fh = dz * ap.tv.inv_dh, fw = w * ap.tv.inv_dw;
-                const int j = min((int)fh, ap.tv.nh - 1);
-                const int m = min((int)fw, ap.tv.nw - 2);
-                const float fj = fh - (float)j, gm = fw - (float)m;
-                const float4* row = ap.tv.tab + ((size_t)j * ap.tv.nw + m) * 2;
-                const float4 v0 = __ldg(row), s0 = __ldg(row + 1), v1 = __ldg(row + 2), s1 = __ldg(row + 3);
-                const float a0 = 1.0f - gm;
-                GR = a0 * fmaf(fj, s0.x, v0.x) + gm * fmaf(fj, s1.x, v1.x);
-                Gt = a0 * fmaf(fj, s0.y, v0.y) + gm * fmaf(fj, s1.y, v1.y);
-                GX = a0 * fmaf(fj, s0.z, v0.z) + gm * fmaf(fj, s1.z, v1.z);
-                GA = a0 * fmaf(fj, s0.w, v0.w) + gm * fmaf(fj, s1.w, v1.w);
-                if (ap.transmission) {
-                    const float il2 = inv_l * inv_l;
-                    const float kR = ap.kR0 * il2 * il2;
-                    const float kA = ap.kA0 * ex2_approx(ap.aer_alpha * lg2_approx(ap.lamA_nm * inv_l));
-                    Tr = ex2_approx(-(GX * kR + GA * kA) * inv_uz);
-                }
-            }
-            if (ap.refraction) {
-                const float c3 = GR * inv_uz * inv_uz * inv_uz;
-                rx = fmaf(c3, ux, rx);
-                ry = fmaf(c3, uy, ry);
-                path = fmaf(Gt, inv_uz, path);
-            }
-            if (!ap.transmission) Tr = 1.0f;
+        float GR, Gt, Tr;
+        correction_fields<SURR>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
+        if (ap.refraction) {
+            const float c3 = GR * inv_uz * inv_uz * inv_uz;
+            rx = fmaf(c3, ux, rx);
+            ry = fmaf(c3, uy, ry);
+            path = fmaf(Gt, inv_uz, path);
         }
         t_rel = fmaf(path, kInvC, t_rel);
         const float4 Cg = S.segC[sg];
@@ -315,8 +418,7 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
                     atomicAdd(op.hist + ((size_t)sh * dp.ny * dp.nx + bin), (unsigned long long)b);
                 }
             }
-            // telescopes: distance from the sphere centre to the arrival line below the radius
-            if (dp.n_tel > 0 && x >= dp.bx0 && x < dp.bx1 && y >= dp.by0 && y < dp.by1) {
+            if (dp.n_tel > 0) {
                 float ugx = ux, ugy = uy, ugz = uz;
                 if (ap.refraction) {   // n sin(theta) conserved, azimuth kept
                     const float sc = (1.0f + Q.z) / ap.n_obs;
@@ -325,31 +427,87 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
                     const float c2 = fmaxf(1.0f - (ugx * ugx + ugy * ugy), 1e-30f);
                     ugz = -c2 * rsqrtf(c2);
                 }
-                float best_d2 = 3.0e38f;
-                auto test = [&](int it) {
+                tel = hit_telescope(dp, x, y, ugx, ugy, ugz, [&](int it, float& ddx, float& ddy, float& ddz, float& r) {
                     const float4 T4 = __ldg(dp.tel + it);
                     const float2 TL = __ldg(dp.tel_lo + it);
-                    const float ddx = (T4.x - Cg.x) + ((TL.x - Cg.y) - rx);
-                    const float ddy = (T4.y - Cg.z) + ((TL.y - Cg.w) - ry);
-                    const float ddz = T4.z;
-                    const float along = ddx * ugx + ddy * ugy + ddz * ugz;
-                    const float d2 = ddx * ddx + ddy * ddy + ddz * ddz - along * along;
-                    if (d2 < T4.w * T4.w && d2 < best_d2) {
-                        best_d2 = d2;
-                        tel = it;
-                    }
-                };
-                if (ugx * ugx + ugy * ugy <= dp.hash_sin2_max) {
-                    const int cx = (int)((x - dp.gx0) * dp.inv_cell);
-                    const int cy = (int)((y - dp.gy0) * dp.inv_cell);
-                    if (cx >= 0 && cx < dp.gnx && cy >= 0 && cy < dp.gny) {
-                        const int c = cy * dp.gnx + cx;
-                        const int e0 = __ldg(dp.cell_start + c), e1 = __ldg(dp.cell_start + c + 1);
-                        for (int e = e0; e < e1; ++e) test(__ldg(dp.cell_tel + e));
-                    }
-                } else {
-                    for (int it = 0; it < dp.n_tel; ++it) test(it);
+                    ddx = (T4.x - Cg.x) + ((TL.x - Cg.y) - rx);
+                    ddy = (T4.y - Cg.z) + ((TL.y - Cg.w) - ry);
+                    ddz = T4.z;
+                    r = T4.w;
+                });
+                if (tel >= 0) {
+                    const size_t slot = (size_t)sh * dp.n_tel + tel;
+                    atomicAdd(op.tel_counts + slot, (unsigned long long)b);
+                    if (op.tel_time) atomicAdd(op.tel_time + slot, (double)b * (S.t0[sg] + (double)t_rel));
                 }
+            }
+        }
+    } else if (status == CS_ST_LANDED) {
+        float GR, Gt, Tr;
+        correction_fields<SURR>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
+        // vacuum straight line to the ground sphere r_g: length t with
+        // t (r_e cos + sqrt(r_e^2 cos^2 - D)) = D, D = r_e^2 - r_g^2 = dz (r_e + r_g)
+        const float rg = ap.rg, re = rg + dz;
+        const float D2 = dz * (rg + re);
+        const float disc = fmaxf(re * re * cos_z * cos_z - D2, 0.0f);
+        const float tt = D2 * rcp_approx(re * cos_z + sqrtf(disc));
+        const float h_obs_f = (float)ap.h_obs;
+        float Gx = Cc.x + (Dd.x + fmaf(ell, Px, tt * ux));
+        float Gy = Cc.y + (Dd.y + fmaf(ell, Py, tt * uy));
+        float Gz = Cc.z + (Dd.z + fmaf(ell, Pz, tt * uz));
+        // ground tangent in the plane of travel at the landing point
+        const float irg = 1.0f / rg;
+        const float gvx = Gx * irg, gvy = Gy * irg, gvz = (Gz - h_obs_f) * irg;   // v_G - z-hat
+        const float uvG = ux * gvx + uy * gvy + uz * (1.0f + gvz);
+        float tx = ux - uvG * gvx, ty = uy - uvG * gvy, tz = uz - uvG * (1.0f + gvz);
+        const float tn = rsqrtf(fmaxf(tx * tx + ty * ty + tz * tz, 1e-30f));
+        tx *= tn;
+        ty *= tn;
+        tz *= tn;
+        float path = tt;
+        if (ap.refraction) {   // arc-length correction along the ground, delay
+            const float dR = GR * inv_uz * inv_uz * inv_uz * sqrtf(sin2);
+            Gx = fmaf(dR, tx, Gx);
+            Gy = fmaf(dR, ty, Gy);
+            Gz = fmaf(dR, tz, Gz);
+            path = fmaf(Gt, inv_uz, path);
+        }
+        t_rel = fmaf(path, kInvC, t_rel);
+        // azimuthal-equidistant coordinates: r_g atan(rho / z_c) along (G_x, G_y)
+        const float zc = rg + (Gz - h_obs_f);
+        const float iz = 1.0f / zc;
+        const float X2 = (Gx * Gx + Gy * Gy) * iz * iz;
+        const float fac = rg * iz * fmaf(X2, fmaf(X2, 0.2f, -1.0f / 3.0f), 1.0f);
+        x = Gx * fac;
+        y = Gy * fac;
+        if (ap.transmission && !(u3 < Tr)) {
+            status = CS_ST_ABSORBED;
+        } else {
+            const int sh = S.shower[sg];
+            if (dp.nx > 0) {
+                const int ix = (int)floorf(((x - dp.hx0_hi) - dp.hx0_lo) * dp.inv_dx);
+                const int iy = (int)floorf(((y - dp.hy0_hi) - dp.hy0_lo) * dp.inv_dy);
+                if (ix >= 0 && ix < dp.nx && iy >= 0 && iy < dp.ny) {
+                    bin = iy * dp.nx + ix;
+                    atomicAdd(op.hist + ((size_t)sh * dp.ny * dp.nx + bin), (unsigned long long)b);
+                }
+            }
+            if (dp.n_tel > 0) {
+                float ugx = ux, ugy = uy, ugz = uz;
+                if (ap.refraction) {   // Bouguer: n r sin(psi) conserved in the plane of travel
+                    const float sin_g = (1.0f + Q.z) / ap.n_obs * re * irg * sqrtf(sin2);
+                    const float cos_g = sqrtf(fmaxf(1.0f - sin_g * sin_g, 0.0f));
+                    ugx = -cos_g * gvx + sin_g * tx;
+                    ugy = -cos_g * gvy + sin_g * ty;
+                    ugz = -cos_g * (1.0f + gvz) + sin_g * tz;
+                }
+                tel = hit_telescope(dp, x, y, ugx, ugy, ugz, [&](int it, float& ddx, float& ddy, float& ddz, float& r) {
+                    const float4 T3 = __ldg(dp.tel3 + it);
+                    ddx = T3.x - Gx;
+                    ddy = T3.y - Gy;
+                    ddz = T3.z - Gz;
+                    r = T3.w;
+                });
                 if (tel >= 0) {
                     const size_t slot = (size_t)sh * dp.n_tel + tel;
                     atomicAdd(op.tel_counts + slot, (unsigned long long)b);
@@ -365,7 +523,7 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
     if (want_records) emit_record(op, gid, k, i, x, y, t_rel, inv_l, tel, bin, status);
 }
 
-template <bool SURR, int MINB>
+template <bool SURR, bool SPH, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB)
 propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, const OutParams op,
                  unsigned int* tile_ctr, const SurrogateView sv) {
@@ -387,7 +545,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
         const long long base = tile * kTile;
 
         // ---- stage 1: import and filter (one segment per thread) -------------
-        const int Kt = base + t < pp.n ? import_segment(S, t, pp.segs + base + t, pp, ap, dp, invalid) : 0;
+        const int Kt = base + t < pp.n ? import_segment<SPH>(S, t, pp.segs + base + t, pp, ap, dp, invalid) : 0;
         int S_tot;
         const int offk = block_scan(Kt, S.wsum, buf, &S_tot);
         S.offK[t] = offk;
@@ -413,7 +571,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                 for (int q = q0; q < q1; ++q) {
                     const int qq = sub0 + q;
                     while (S.offK[sg + 1] <= qq) ++sg;   // next non-empty segment
-                    const int N = substep(S, q, sg, qq - S.offK[sg], base, pp, ap);
+                    const int N = substep<SPH>(S, q, sg, qq - S.offK[sg], base, pp, ap);
                     my_ph += N;
                     my_emit += (unsigned int)N * (unsigned int)S.bunch[sg];
                 }
@@ -438,8 +596,8 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                     const int p = pw + (t & 31);
                     const bool active = p < wn;
                     const unsigned int e = S.map[active ? p : pw];
-                    bunch<SURR>(S, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), active, base, pp, ap, dp,
-                                op, sv, T, want_records);
+                    bunch<SURR, SPH>(S, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), active, base, pp, ap,
+                                     dp, op, sv, T, want_records);
                 }
                 __syncthreads();
             }
@@ -468,18 +626,31 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
 }
 
 // Launches the exact-tracer or the surrogate instance of the kernel.
+// An atmosphere and a detector work together when they share the observation
+// level and the geometry (and, on the sphere, the Earth radius).
+bool compatible(const cs_atmosphere* atm, const cs_detector* det) {
+    const double tol = 1e-9 * fmax(1.0, fabs(atm->p.h_obs));
+    if (fabs(det->p.h_obs - atm->p.h_obs) > tol) return false;
+    if (det->p.spherical != atm->p.spherical) return false;
+    return !atm->p.spherical || fabs(det->p.R - atm->f64.R) <= 1e-9 * atm->f64.R;
+}
+
 cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp, const AtmParams& ap,
                         const DetParams& dp, const OutParams& op, unsigned int* ctr, const cs_surrogate* sur,
                         bool sur_one_block) {
     const size_t smem = sizeof(TileSmem);
-    if (sur) {
+    SurrogateView none;
+    memset(&none, 0, sizeof none);
+    const SurrogateView& sv = sur ? *surrogate_view(sur) : none;
+    if (ap.spherical) {
+        if (sur) propagate_kernel<true, true, 1><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
+        else propagate_kernel<false, true, 4><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
+    } else if (sur) {
         // 1 block per SM: the 255-register instance (no spills); else 2 blocks of 128 registers
-        if (sur_one_block) propagate_kernel<true, 1><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, *surrogate_view(sur));
-        else propagate_kernel<true, 2><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, *surrogate_view(sur));
+        if (sur_one_block) propagate_kernel<true, false, 1><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
+        else propagate_kernel<true, false, 2><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
     } else {
-        SurrogateView none;
-        memset(&none, 0, sizeof none);
-        propagate_kernel<false, 4><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, none);
+        propagate_kernel<false, false, 4><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
     }
     CS_CUDA_TRY(cudaGetLastError());
     return CS_OK;
@@ -487,9 +658,11 @@ cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp
 
 cs_status set_smem_attributes() {
     const int smem = (int)sizeof(TileSmem);
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     return CS_OK;
 }
 
@@ -601,7 +774,7 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
     if (det->p.nx > 0 && !out->hist) return CS_ERR_INVALID_ARG;
     if (det->p.n_tel > 0 && !out->tel_counts) return CS_ERR_INVALID_ARG;
     if (out->records && !out->record_count) return CS_ERR_INVALID_ARG;
-    if (fabs(det->p.h_obs - atm->p.h_obs) > 1e-9 * fmax(1.0, fabs(atm->p.h_obs))) return CS_ERR_INVALID_ARG;
+    if (!compatible(atm, det)) return CS_ERR_INVALID_ARG;
     if (n > (size_t)1 << 40) return CS_ERR_INVALID_ARG;
     cudaStream_t stream = (cudaStream_t)stream_;
     const DetParams& dp = det->p;
@@ -741,7 +914,7 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     if (det->p.nx > 0 && !out->hist) return CS_ERR_INVALID_ARG;
     if (det->p.n_tel > 0 && !out->tel_counts) return CS_ERR_INVALID_ARG;
     if (out->records && !out->record_count) return CS_ERR_INVALID_ARG;
-    if (fabs(det->p.h_obs - atm->p.h_obs) > 1e-9 * fmax(1.0, fabs(atm->p.h_obs))) return CS_ERR_INVALID_ARG;
+    if (!compatible(atm, det)) return CS_ERR_INVALID_ARG;
     // the counter is 32 bits wide: reject inputs with more tiles than it can count
     if ((n + kTile - 1) / kTile >= 0xFFFFFFFFull - 65536ull) return CS_ERR_INVALID_ARG;
     cudaStream_t stream = (cudaStream_t)stream_;
@@ -808,7 +981,7 @@ cs_status check_device_call(const cs_segment* segs, size_t n, const cs_atmospher
     if (det->p.nx > 0 && !out->hist) return CS_ERR_INVALID_ARG;
     if (det->p.n_tel > 0 && !out->tel_counts) return CS_ERR_INVALID_ARG;
     if (out->records && !out->record_count) return CS_ERR_INVALID_ARG;
-    if (fabs(det->p.h_obs - atm->p.h_obs) > 1e-9 * fmax(1.0, fabs(atm->p.h_obs))) return CS_ERR_INVALID_ARG;
+    if (!compatible(atm, det)) return CS_ERR_INVALID_ARG;
     if (n > (size_t)1 << 40) return CS_ERR_INVALID_ARG;
     return CS_OK;
 }
@@ -1037,6 +1210,103 @@ extern "C" cs_status cs_autotune_bunches(const cs_segment* segs, size_t n, const
         for (int i = 0; i < n_allowed; ++i)
             if (allowed[i] > pick && sqrt((double)allowed[i] / fmax(mean, 1e-300)) <= rel_noise) pick = allowed[i];
         shower_bunch[s] = pick;
+    }
+    return CS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Streaming: host segments in fixed-size chunks through two device staging
+// buffers on two streams, so the host-to-device copy of one chunk overlaps
+// the photon kernel of the previous one (data transfer and batching,
+// Sec. 5.1 and 5.4).  Buffer b is only ever used on stream b, so stream
+// order alone keeps a copy from overwriting segments a kernel still reads.
+// ---------------------------------------------------------------------------
+struct cs_streamer {
+    size_t chunk = 0;
+    cs_segment* d_buf[2] = {nullptr, nullptr};
+    cudaStream_t st[2] = {nullptr, nullptr};
+    cudaEvent_t ev_in = nullptr, ev_done[2] = {nullptr, nullptr};
+    int device = 0;
+};
+
+extern "C" void cs_streamer_destroy(cs_streamer* s) {
+    if (!s) return;
+    for (int b = 0; b < 2; ++b) {
+        if (s->st[b]) cudaStreamSynchronize(s->st[b]);
+        cudaFree(s->d_buf[b]);
+        if (s->st[b]) cudaStreamDestroy(s->st[b]);
+        if (s->ev_done[b]) cudaEventDestroy(s->ev_done[b]);
+    }
+    if (s->ev_in) cudaEventDestroy(s->ev_in);
+    delete s;
+}
+
+extern "C" cs_status cs_streamer_create(size_t chunk, cs_streamer** out) {
+    if (!out) return CS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (chunk < 1 || chunk > ((size_t)1 << 32)) return CS_ERR_INVALID_ARG;
+    cs_status st = check_device();
+    if (st != CS_OK) return st;
+    cs_streamer* s = new cs_streamer;
+    s->chunk = chunk;
+    cudaGetDevice(&s->device);
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaMalloc(&s->d_buf[b], chunk * sizeof(cs_segment));
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st[b], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_done[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        set_last_error("streamer create", e);
+        cs_streamer_destroy(s);
+        return CS_ERR_CUDA;
+    }
+    *out = s;
+    return CS_OK;
+}
+
+extern "C" cs_status cs_streamer_run(cs_streamer* s, const cs_segment* host_segs, size_t n, const cs_atmosphere* atm,
+                                     const cs_detector* det, uint64_t seed, const cs_opts* opts, cs_output* out,
+                                     void* stream_) {
+    if (!s) return CS_ERR_INVALID_ARG;
+    cs_opts o;
+    if (opts) o = *opts; else cs_opts_default(&o);
+    // the outputs are device memory (device_ptrs = 1); the segments are host memory
+    cs_status st = check_device_call(s->d_buf[0], n, atm, det, o, out);
+    if (st != CS_OK) return st;
+    if (n > 0 && !host_segs) return CS_ERR_INVALID_ARG;
+    int dev = 0;
+    CS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != s->device) return CS_ERR_INVALID_ARG;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    unsigned int grid = 0;
+    st = prepare_launch(std::min(n, s->chunk), o, &grid);
+    if (st != CS_OK) return st;
+    // zeroing (unless accumulating) on the caller's stream, then both streams wait for it
+    st = enqueue(nullptr, 0, atm, det, seed, nullptr, o, out, nullptr, grid, stream);
+    if (st != CS_OK) return st;
+    CS_CUDA_TRY(cudaEventRecord(s->ev_in, stream));
+    for (int b = 0; b < 2; ++b) CS_CUDA_TRY(cudaStreamWaitEvent(s->st[b], s->ev_in, 0));
+    cs_opts oc = o;
+    oc.accumulate = 1;
+    const size_t n_chunks = (n + s->chunk - 1) / s->chunk;
+    for (size_t c = 0; c < n_chunks; ++c) {
+        const int b = (int)(c & 1);
+        const size_t off = c * s->chunk, m = std::min(s->chunk, n - off);
+        CS_CUDA_TRY(cudaMemcpyAsync(s->d_buf[b], host_segs + off, m * sizeof(cs_segment), cudaMemcpyHostToDevice,
+                                    s->st[b]));
+        oc.seg_base = o.seg_base + off;
+        unsigned int* ctr = nullptr;
+        st = tile_counter(&ctr);
+        if (st != CS_OK) return st;
+        st = enqueue(s->d_buf[b], m, atm, det, seed, nullptr, oc, out, ctr, grid, s->st[b]);
+        if (st != CS_OK) return st;
+    }
+    // the caller's stream continues after both streams' last chunks
+    for (int b = 0; b < 2; ++b) {
+        CS_CUDA_TRY(cudaEventRecord(s->ev_done[b], s->st[b]));
+        CS_CUDA_TRY(cudaStreamWaitEvent(stream, s->ev_done[b], 0));
     }
     return CS_OK;
 }

@@ -92,6 +92,9 @@ __device__ void node_fields(const AtmF64& a, double h_e, bool below, double cos0
         if (a.lin_h1 > a.h_obs && a.lin_h1 < h_e) cuts[nc++] = a.lin_h1;
     }
     cuts[nc++] = h_e;
+    // spherical shell: r = R + h, Bouguer's invariant K = n_e r_e sin(psi0); the
+    // straight-line reference has K0 = r_e sin(psi0) and q0 = sqrt(r^2 - K0^2)
+    const double re = a.R + h_e, K0 = re * sin0;
     for (int piece = 0; piece + 1 < nc; ++piece) {
         const double lo = cuts[piece], hi = cuts[piece + 1];
         const int nsub = (int)ceil((hi - lo) / kSubMax);
@@ -103,18 +106,44 @@ __device__ void node_fields(const AtmF64& a, double h_e, bool below, double cos0
                 double d, rho;
                 delta_rho(a, h, false, &d, &rho);
                 const double n = 1.0 + d;
-                if (a.refraction) {
-                    const double q = sqrt(n * n - s * s);
-                    acc[0] += wt * (de - d) * (2.0 + de + d) / (q * (ne * cos0 + q));
-                    acc[1] += wt * (n * n * cos0 - q) / q;
-                    acc[2] += wt * 100.0 * rho * n / q;
-                    acc[3] += wt * exp(-h / a.H_A) * n / q;
+                if (!a.spherical) {
+                    if (a.refraction) {
+                        const double q = sqrt(n * n - s * s);
+                        acc[0] += wt * (de - d) * (2.0 + de + d) / (q * (ne * cos0 + q));
+                        acc[1] += wt * (n * n * cos0 - q) / q;
+                        acc[2] += wt * 100.0 * rho * n / q;
+                        acc[3] += wt * exp(-h / a.H_A) * n / q;
+                    } else {
+                        acc[2] += wt * 100.0 * rho;
+                        acc[3] += wt * exp(-h / a.H_A);
+                    }
                 } else {
-                    acc[2] += wt * 100.0 * rho;
-                    acc[3] += wt * exp(-h / a.H_A);
+                    const double r = a.R + h;
+                    const double q0 = sqrt(r * r - K0 * K0);
+                    if (a.refraction) {
+                        const double q = sqrt(n * n * r * r - ne * ne * K0 * K0);
+                        // central angle minus the straight line's, divided by sin(psi0):
+                        // K0 r (n_e^2 - n^2) / (q q0 (n_e q0 + q)) / sin(psi0)
+                        acc[0] += wt * re * r * (de - d) * (2.0 + de + d) / (q * q0 * (ne * q0 + q));
+                        acc[1] += wt * (n * n * r / q - r / q0);
+                        acc[2] += wt * 100.0 * rho * n * r / q;
+                        acc[3] += wt * exp(-h / a.H_A) * n * r / q;
+                    } else {
+                        acc[2] += wt * 100.0 * rho * r / q0;
+                        acc[3] += wt * exp(-h / a.H_A) * r / q0;
+                    }
                 }
             }
         }
+    }
+    if (a.spherical) {
+        // G_R = (arc length correction on the ground sphere) cos^3 / sin, G_t = c dt cos,
+        // G_X = X cos, G_A = A cos
+        out[0] = a.refraction ? (a.R + a.h_obs) * cos0 * cos0 * cos0 * acc[0] : 0.0;
+        out[1] = a.refraction ? cos0 * acc[1] : 0.0;
+        out[2] = cos0 * acc[2];
+        out[3] = cos0 * acc[3];
+        return;
     }
     if (a.refraction) {
         out[0] = cos0 * cos0 * acc[0];
@@ -210,6 +239,9 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
     a.kind = d->kind;
     a.h_obs = d->h_obs;
     a.refraction = d->refraction ? 1 : 0;
+    a.spherical = d->geometry == CS_GEOM_SPHERICAL ? 1 : 0;
+    a.R = d->earth_radius > 0.0 ? d->earth_radius : 6370000.0;
+    if (d->geometry != CS_GEOM_PLANAR && d->geometry != CS_GEOM_SPHERICAL) return CS_ERR_INVALID_ARG;
     a.H_A = d->aer_H > 0.0 ? d->aer_H : 1200.0;
     double table_top;
     if (d->kind == CS_ATM_LAYERED) {
@@ -262,6 +294,9 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
     h->lambda_max = d->lambda_max;
     AtmParams& p = h->p;
     p.kind = d->kind;
+    p.spherical = a.spherical;
+    p.R = (float)a.R;
+    p.rg = (float)(a.R + d->h_obs);
     p.n_layers = a.n_layers;
     p.refraction = a.refraction;
     p.transmission = d->transmission ? 1 : 0;

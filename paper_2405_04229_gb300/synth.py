@@ -14,6 +14,7 @@ Gaussian direction scatter about the shower axis.
 """
 from __future__ import annotations
 
+import functools
 import math
 
 import numpy as np
@@ -173,6 +174,50 @@ def uneven_showers(n_showers=64, seed=0, lo=4.0, hi=7.0, max_total=None):
     parts = [shower_segments(int(c), zen[i], azi[i], 1e12, seed, shower_id=i)
              for i, c in enumerate(counts)]
     return concat(parts), counts
+
+
+@functools.lru_cache(maxsize=2)
+def _inclined_base(n, seed, zenith_deg, azimuth_deg, E0_eV):
+    return shower_segments(n, zenith_deg, azimuth_deg, E0_eV, seed)
+
+
+def inclined_chunk(c, n=10_000_000, seed=0, zenith_deg=60.0, azimuth_deg=0.0, E0_eV=1e14, n_chunks=10,
+                   h_obs=2000.0):
+    """Chunk c of the large inclined shower (100 TeV-class, zenith 60 deg): one
+    seeded draw of n segments turned about the shower axis by 2 pi c / n_chunks.
+    The lateral and angular spreads are symmetric about the axis, so every
+    chunk is a sample of the same shower; its photons are keyed by the global
+    segment ids c n .. (c + 1) n - 1."""
+    b = _inclined_base(n, seed, zenith_deg, azimuth_deg, E0_eV)
+    th, ph = math.radians(zenith_deg), math.radians(azimuth_deg)
+    k = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+    a = 2.0 * math.pi * c / n_chunks
+    K = np.array([[0.0, -k[2], k[1]], [k[2], 0.0, -k[0]], [-k[1], k[0], 0.0]])
+    Rm = np.eye(3) + math.sin(a) * K + (1.0 - math.cos(a)) * (K @ K)   # Rodrigues
+    pos = np.stack([b["x0"], b["y0"], b["z0"] - h_obs], axis=1) @ Rm.T
+    d = np.stack([b["ux"], b["uy"], b["uz"]], axis=1).astype(np.float64) @ Rm.T
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    s = dict(b)
+    s["x0"], s["y0"], s["z0"] = pos[:, 0], pos[:, 1], pos[:, 2] + h_obs
+    s["ux"], s["uy"], s["uz"] = (d[:, i].astype(np.float32) for i in range(3))
+    return s
+
+
+def steep_arrival_segments(n, seed, zenith_deg=80.0, half=560.0, h_obs=2000.0):
+    """Segments 50-300 m above the ground moving at a fixed steep zenith (+x
+    azimuth), placed so their photons land over [-half, half)^2: arrivals far
+    beyond the telescope hash's zenith range, many near the array's edge."""
+    rng = np.random.default_rng([seed, 0x5EED, 0x57])
+    s = _empty(n)
+    th = math.radians(zenith_deg)
+    dz = rng.uniform(50.0, 300.0, n)
+    s["z0"] = h_obs + dz
+    s["x0"] = -dz * math.tan(th) + rng.uniform(-half, half, n)
+    s["y0"] = rng.uniform(-half, half, n)
+    s["ux"][:], s["uz"][:] = np.float32(math.sin(th)), np.float32(-math.cos(th))
+    s["length"][:] = 2.0
+    s["inv_gamma2"][:] = np.float32(1e-8)
+    return s
 
 
 def grid_telescopes(nx=10, ny=10, pitch=100.0, radius=6.0, h_obs=2000.0):

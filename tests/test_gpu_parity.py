@@ -256,3 +256,17 @@ def test_full_size_refraction_workload_sampled():
     orc = dict(records=np.concatenate(o_recs))
     st = PU.compare(g, orc, bunch=5, check_hist=False)
     assert st["matched"] > 2000
+
+
+def test_steep_arrivals_beyond_the_telescope_hash():
+    """Straight lines at zenith 80 deg (no table domain): arrivals steeper
+    than the telescope hash serves test every sphere, also outside the box of
+    the hash's reach discs."""
+    segs = synth.steep_arrival_segments(2000, seed=1)
+    tel = synth.grid_telescopes()
+    g, o = _run_both(segs, False, False, 1, tel=tel, seed=1)
+    st = PU.compare(g, o, bunch=1)
+    assert st["matched"] > 100000
+    assert int(g["counters"][B.CS_CNT_TEL]) > 5000
+    d = np.abs(g["tel_counts"].astype(np.int64) - o["tel_counts"].astype(np.int64)).sum()
+    assert d <= 2 * (st["tel_flips"] + st["status_flips"] + st["only_gpu"] + st["only_oracle"])

@@ -61,6 +61,17 @@ def test_training_gradients_match_oracle(B):
         assert rel <= 1e-2, (name, rel)
 
 
+def test_training_is_deterministic(B):
+    """Fixed-order reductions: two trainings from the same seed give the same bits."""
+    atm = B.Atmosphere(layered=synth.US_STANDARD, refraction=True, transmission=True)
+    a = B.Surrogate(atm, epochs=4, n_train=1 << 16, n_heldout=1 << 12)
+    b = B.Surrogate(atm, epochs=4, n_train=1 << 16, n_heldout=1 << 12)
+    pa, na = a.info()
+    pb, nb = b.info()
+    assert np.array_equal(pa, pb) and np.array_equal(na, nb)
+    assert a.stats["p99"] == b.stats["p99"]
+
+
 @pytest.fixture(scope="module")
 def trained(B):
     atm = B.Atmosphere(layered=synth.US_STANDARD, refraction=True, transmission=True)
