@@ -33,7 +33,7 @@ struct TableView {
 struct AtmParams {
     int kind;            // CS_ATM_*
     int spherical;       // 1: spherical shell (Earth centre at (0, 0, -R))
-    float R, rg;         // Earth radius and R + h_obs [m]
+    float R, rg, inv_rg; // Earth radius, r_g = R + h_obs [m], 1 / r_g
     int n_layers;
     int refraction;
     int transmission;
@@ -47,7 +47,9 @@ struct AtmParams {
     float lin_d0, lin_slope, lin_top_rel, lin_d1;   // linear kind, relative to h_obs
     float hom_delta;
     float n_obs;         // n(h_obs)
+    float inv_n_obs;
     double h_obs;
+    float h_obs_hi, h_obs_lo;   // h_obs as float-float
     float inv_l1_nm, dinv_l_nm;  // 1/lambda_min and 1/lambda_min - 1/lambda_max [1/nm]
     float ft;            // 2 pi alpha (1/lambda_min - 1/lambda_max) [1/m]
     // transmission: exponent in log2 units = (G_X kR + G_A kA) / |u_z|
@@ -71,11 +73,13 @@ struct DetParams {
     const float4* tel;    // {x_hi, y_hi, z - h_obs, radius}
     const float2* tel_lo; // {x_lo, y_lo}
     const float4* tel3;   // spherical: centre in frame coordinates and radius
-    // uniform grid hash over the telescopes' reach discs
-    float gx0, gy0, inv_cell;
+    // uniform grid hash over the telescopes' reach discs; the grid origin and
+    // the cell size are whole metres, so cell corners are exact in FP32
+    float gx0, gy0, cell, inv_cell;
     int gnx, gny;
     const int* cell_start;  // gnx * gny + 1
-    const int* cell_tel;
+    const int* cell_tel;    // telescope index of each cell entry (ascending within a cell)
+    const float4* cell_data;  // planar: {x - corner_x, y - corner_y, z - h_obs, radius}; spherical: tel3
     float hash_sin2_max;    // photons arriving steeper than this use the full list
     float bx0, bx1, by0, by1;  // bounding box of all reach discs
 };

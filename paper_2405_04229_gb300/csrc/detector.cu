@@ -5,6 +5,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -63,6 +64,7 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
     std::vector<float4> tel(d->n_tel), tel3(p.spherical ? d->n_tel : 0);
     std::vector<float2> tel_lo(d->n_tel);
     std::vector<int> cell_start(1, 0), cell_tel;
+    std::vector<float4> cell_data;
     if (d->n_tel > 0) {
         double reach_max = 0.0, x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
         std::vector<double> reach(d->n_tel);
@@ -86,7 +88,14 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
             x0 = fmin(x0, t[0] - reach[i]); x1 = fmax(x1, t[0] + reach[i]);
             y0 = fmin(y0, t[1] - reach[i]); y1 = fmax(y1, t[1] + reach[i]);
         }
-        double cell = fmax(2.0 * reach_max, 1.0);
+        // whole-metre origin and cell size: cell corners are exact in FP32
+        x0 = floor(x0);
+        y0 = floor(y0);
+        double cell = fmax(ceil(2.0 * reach_max), 1.0);
+        if (fabs(x0) > 8e6 || fabs(y0) > 8e6 || fabs(x1) > 8e6 || fabs(y1) > 8e6) {
+            delete h;
+            return CS_ERR_INVALID_ARG;
+        }
         int gnx = (int)ceil((x1 - x0) / cell), gny = (int)ceil((y1 - y0) / cell);
         while ((double)gnx * gny > 4e6) { cell *= 2.0; gnx = (int)ceil((x1 - x0) / cell); gny = (int)ceil((y1 - y0) / cell); }
         gnx = gnx < 1 ? 1 : gnx;
@@ -103,9 +112,20 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
         cell_start.assign((size_t)gnx * gny + 1, 0);
         for (size_t c = 0; c < lists.size(); ++c) cell_start[c + 1] = cell_start[c] + (int)lists[c].size();
         cell_tel.reserve(cell_start.back());
-        for (auto& l : lists) cell_tel.insert(cell_tel.end(), l.begin(), l.end());
+        cell_data.reserve(cell_start.back());
+        for (size_t c = 0; c < lists.size(); ++c) {
+            const double cx0 = x0 + (double)(c % gnx) * cell, cy0 = y0 + (double)(c / gnx) * cell;
+            for (int i : lists[c]) {
+                const double* t = d->tel_xyzr + 4 * i;
+                cell_tel.push_back(i);
+                cell_data.push_back(p.spherical ? tel3[i]
+                                                : make_float4((float)(t[0] - cx0), (float)(t[1] - cy0),
+                                                              (float)(t[2] - d->h_obs), (float)t[3]));
+            }
+        }
         p.gx0 = (float)x0;
         p.gy0 = (float)y0;
+        p.cell = (float)cell;
         p.inv_cell = (float)(1.0 / cell);
         p.gnx = gnx;
         p.gny = gny;
@@ -126,7 +146,8 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
     const size_t o_t3 = align_up(o_lo + tel_lo.size() * sizeof(float2));
     const size_t o_cs = align_up(o_t3 + tel3.size() * sizeof(float4));
     const size_t o_ct = align_up(o_cs + cell_start.size() * sizeof(int));
-    const size_t total = align_up(o_ct + (cell_tel.size() + 1) * sizeof(int));
+    const size_t o_cd = align_up(o_ct + (cell_tel.size() + 1) * sizeof(int));
+    const size_t total = align_up(o_cd + (cell_data.size() + 1) * sizeof(float4));
     cudaError_t e = cudaMalloc(&h->d_mem, total);
     if (e != cudaSuccess) { cs::set_last_error("detector alloc", e); delete h; return CS_ERR_CUDA; }
     char* base = (char*)h->d_mem;
@@ -136,6 +157,7 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
     if (!tel3.empty()) memcpy(host.data() + o_t3, tel3.data(), tel3.size() * sizeof(float4));
     memcpy(host.data() + o_cs, cell_start.data(), cell_start.size() * sizeof(int));
     if (!cell_tel.empty()) memcpy(host.data() + o_ct, cell_tel.data(), cell_tel.size() * sizeof(int));
+    if (!cell_data.empty()) memcpy(host.data() + o_cd, cell_data.data(), cell_data.size() * sizeof(float4));
     e = cudaMemcpy(h->d_mem, host.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cs::set_last_error("detector copy", e); cudaFree(h->d_mem); delete h; return CS_ERR_CUDA; }
     p.tel = (const float4*)(base + o_tel);
@@ -143,6 +165,7 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
     p.tel3 = p.spherical ? (const float4*)(base + o_t3) : nullptr;
     p.cell_start = (const int*)(base + o_cs);
     p.cell_tel = (const int*)(base + o_ct);
+    p.cell_data = (const float4*)(base + o_cd);
     *out = h;
     return CS_OK;
 }

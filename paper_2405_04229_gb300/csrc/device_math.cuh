@@ -40,6 +40,35 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
+// finiteness of a double from its exponent bits
+__device__ __forceinline__ bool finite_f64(double d) {
+    return ((unsigned long long)__double_as_longlong(d) & 0x7FF0000000000000ull) != 0x7FF0000000000000ull;
+}
+
+// hi = d rounded to the nearest float (ties to even), lo = d - hi rounded to
+// float: the float-float split of a double, taken from its bits with integer
+// operations (the FP64 pipe of this GPU is narrow).  The same values as
+// hi = (float)d, lo = (float)(d - (double)hi); |d| outside [2^-74, 2^127)
+// and non-finite values take that conversion path.
+__device__ __forceinline__ void split_f64(double d, float& hi, float& lo) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((u >> 52) & 0x7FF);
+    if (e < 949 || e > 1149) {
+        hi = (float)d;
+        lo = (float)(d - (double)hi);
+        return;
+    }
+    const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
+    const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+    const unsigned int mh = (unsigned int)(m >> 29), rem = (unsigned int)m & 0x1FFFFFFFu;
+    const unsigned int up = (rem > 0x10000000u || (rem == 0x10000000u && (mh & 1u))) ? 1u : 0u;
+    hi = __uint_as_float(sign | ((((unsigned int)(e - 1023 + 127)) << 23) + mh + up));
+    const int r = (int)rem - (up ? 0x20000000 : 0);
+    const float scale = __uint_as_float((unsigned int)(e - 1075 + 127) << 23);   // 2^(e - 1075)
+    const float l = __int2float_rn(r) * scale;
+    lo = sign ? -l : l;
+}
+
 // floor(s + t) for |t| below one ulp of s
 __device__ __forceinline__ int ff_floor(float s, float t) {
     const float f = floorf(s);

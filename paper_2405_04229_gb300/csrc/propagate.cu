@@ -27,7 +27,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kTile = 256;              // segments per tile, one per thread
-constexpr int kSubCap = 1024;           // sub-steps per round
+constexpr int kSubCap = 512;            // sub-steps per round
 constexpr int kMapCap = 2048;           // bunches per window of the bunch -> sub-step map
 constexpr int kKShift = 8;              // sub-step record: segment (8 bits) | k << 8
 constexpr int kQBits = 10;              // map entry: sub-step (10 bits) | bunch index << 10
@@ -40,7 +40,6 @@ struct TileSmem {
     float4 segB[kTile];   // Hs_hi, Hs_lo (z0 - h_obs), L / K, 1 / (beta c) | Hs, tilt_z, L / K, 1 / (beta c)
     float4 segC[kTile];   // ground intercept G, float-float x and y | start point (hi), radial P component
     float4 segD[kTile];   // G in histogram cells, float-float x and y | start point (lo), 1 / r
-    float4 segE[kTile];   // spherical shell: local-vertical tilt at the start, v - z
     double t0[kTile];
     float g[kTile], z2[kTile];
     int shower[kTile];
@@ -113,7 +112,7 @@ __device__ __forceinline__ int import_segment(TileSmem& S, int t, const cs_segme
     const float g = __uint_as_float(rest.x), z = __uint_as_float(rest.y);
     const unsigned int shower = rest.z;
     const float n2 = dir.x * dir.x + dir.y * dir.y + dir.z * dir.z;
-    const bool valid = isfinite(xy.x) && isfinite(xy.y) && isfinite(zt.x) && isfinite(zt.y) && isfinite(dir.x) &&
+    const bool valid = finite_f64(xy.x) && finite_f64(xy.y) && finite_f64(zt.x) && finite_f64(zt.y) && isfinite(dir.x) &&
                        isfinite(dir.y) && isfinite(dir.z) && isfinite(dir.w) && dir.w > 0.0f && g > 0.0f &&
                        g < 1.0f && isfinite(z) && dir.z < 0.99f && fabsf(n2 - 1.0f) <= 1e-4f &&
                        shower < (unsigned int)dp.n_showers;
@@ -125,16 +124,26 @@ __device__ __forceinline__ int import_segment(TileSmem& S, int t, const cs_segme
     const float Px = dir.x * inv_n, Py = dir.y * inv_n, Pz = dir.z * inv_n;
     const float L = dir.w;
     const int K = max(1, (int)ceilf(L / pp.s_max));
+    float x_hi, x_lo, y_hi, y_lo, z_hi, z_lo;
+    split_f64(xy.x, x_hi, x_lo);
+    split_f64(xy.y, y_hi, y_lo);
+    split_f64(zt.x, z_hi, z_lo);
+    // Hs = z0 - h_obs in float-float
+    float Hs_hi, Hs_lo;
+    {
+        float s, e;
+        two_sum(z_hi, -ap.h_obs_hi, s, e);
+        const float t = e + (z_lo - ap.h_obs_lo);
+        Hs_hi = s + t;
+        Hs_lo = t - (Hs_hi - s);
+    }
     if (SPH) {
         const float R = ap.R;
-        const float x_hi = (float)xy.x, x_lo = (float)(xy.x - (double)x_hi);
-        const float y_hi = (float)xy.y, y_lo = (float)(xy.y - (double)y_hi);
-        const float z_hi = (float)zt.x, z_lo = (float)(zt.x - (double)z_hi);
         // altitude h = |S - c| - R = z + rho^2 / (|S - c| + z + R), c = (0, 0, -R), without cancellation
         const float rho2 = x_hi * x_hi + y_hi * y_hi, a = z_hi + R;
         const float rr = sqrtf(rho2 + a * a);
         const float lift = rho2 / (rr + a);
-        const float Hs = (float)(zt.x - ap.h_obs) + lift;
+        const float Hs = Hs_hi + (Hs_lo + lift);
         const float inv_r = 1.0f / rr;
         const float dvx = x_hi * inv_r, dvy = y_hi * inv_r, dvz = -lift * inv_r;   // v - z-hat
         const float Pr = Px * dvx + Py * dvy + Pz * (1.0f + dvz);
@@ -149,11 +158,7 @@ __device__ __forceinline__ int import_segment(TileSmem& S, int t, const cs_segme
         S.bunch[t] = pp.shower_bunch ? __ldg(pp.shower_bunch + shower) : pp.bunch;
         return K;
     }
-    // local origin: Hs = z0 - h_obs and G = S_xy - Hs P_xy / P_z in float-float
-    const double Hs = zt.x - ap.h_obs;
-    const float Hs_hi = (float)Hs, Hs_lo = (float)(Hs - (double)Hs_hi);
-    const float x_hi = (float)xy.x, x_lo = (float)(xy.x - (double)x_hi);
-    const float y_hi = (float)xy.y, y_lo = (float)(xy.y - (double)y_hi);
+    // local origin: G = S_xy - Hs P_xy / P_z in float-float
     float Gxh = x_hi, Gxl = x_lo, Gyh = y_hi, Gyl = y_lo;
     if (Pz < -1e-3f) {
         const float sx = Px / Pz, sy = Py / Pz;                       // slopes, float-float via FMA remainder
@@ -206,7 +211,7 @@ __device__ __forceinline__ int substep(TileSmem& S, int q, int sg, int k, long l
     // 1 - 1/(beta n)^2 without forming 1/(beta n)^2 (cancellation-free)
     const float sin2 = (d * (2.0f + d) - onepd * onepd * g) * rcp_approx(onepd * onepd * (1.0f - g));
     float nbar = 0.0f;
-    if (sin2 > 0.0f) nbar = ap.ft * S.z2[sg] * sin2 * B.z / (float)S.bunch[sg];
+    if (sin2 > 0.0f) nbar = ap.ft * S.z2[sg] * sin2 * B.z * rcp_approx((float)S.bunch[sg]);
     const unsigned long long gid = pp.seg_base + (unsigned long long)(base + sg);
     const uint4 rc = philox((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0xFFFFFFFFu, pp.key0, pp.key1);
     const float uk = uniform24(rc.x);
@@ -224,38 +229,45 @@ struct Tally {
 };
 
 // Telescopes: the sphere whose centre is closest to the arrival line, if
-// closer than its radius (ties: lowest index).  (ddx, ddy, ddz)(it) gives the
-// centre minus the ground point for telescope it.  Arrivals within the
-// hash's zenith range test the spheres listed for their grid cell (none
-// outside the box of all reach discs); steeper ones test every sphere.
-template <typename Delta>
-__device__ __forceinline__ int hit_telescope(const DetParams& dp, float x, float y, float ugx, float ugy, float ugz,
-                                             Delta delta) {
-    int tel = -1;
+// closer than its radius (ties: lowest index).  Arrivals within the hash's
+// zenith range (`hashed`; the caller has checked the box of all reach discs)
+// test the entries of their grid cell: cell_delta(entry, corner_x, corner_y,
+// ddx, ddy, ddz) gives the centre minus the ground point.  Steeper arrivals
+// test every sphere through full_delta(index, ddx, ddy, ddz, radius).
+template <typename CellDelta, typename FullDelta>
+__device__ __forceinline__ int hit_telescope(const DetParams& dp, bool hashed, float x, float y, float ugx, float ugy,
+                                             float ugz, CellDelta cell_delta, FullDelta full_delta) {
+    int best = -1;
     float best_d2 = 3.0e38f;
-    auto test = [&](int it) {
-        float ddx, ddy, ddz, r;
-        delta(it, ddx, ddy, ddz, r);
+    auto test = [&](float ddx, float ddy, float ddz, float r, int id) {
         const float along = ddx * ugx + ddy * ugy + ddz * ugz;
         const float d2 = ddx * ddx + ddy * ddy + ddz * ddz - along * along;
         if (d2 < r * r && d2 < best_d2) {
             best_d2 = d2;
-            tel = it;
+            best = id;
         }
     };
-    if (ugx * ugx + ugy * ugy <= dp.hash_sin2_max) {
-        if (!(x >= dp.bx0 && x < dp.bx1 && y >= dp.by0 && y < dp.by1)) return -1;
+    if (hashed) {
         const int cx = (int)((x - dp.gx0) * dp.inv_cell);
         const int cy = (int)((y - dp.gy0) * dp.inv_cell);
-        if (cx >= 0 && cx < dp.gnx && cy >= 0 && cy < dp.gny) {
-            const int c = cy * dp.gnx + cx;
-            const int e0 = __ldg(dp.cell_start + c), e1 = __ldg(dp.cell_start + c + 1);
-            for (int e = e0; e < e1; ++e) test(__ldg(dp.cell_tel + e));
+        if (cx < 0 || cx >= dp.gnx || cy < 0 || cy >= dp.gny) return -1;
+        const int c = cy * dp.gnx + cx;
+        const float cx0 = fmaf((float)cx, dp.cell, dp.gx0), cy0 = fmaf((float)cy, dp.cell, dp.gy0);   // exact
+        const int e0 = __ldg(dp.cell_start + c), e1 = __ldg(dp.cell_start + c + 1);
+        for (int e = e0; e < e1; ++e) {
+            const float4 D = __ldg(dp.cell_data + e);
+            float ddx, ddy, ddz;
+            cell_delta(D, cx0, cy0, ddx, ddy, ddz);
+            test(ddx, ddy, ddz, D.w, e);
         }
-    } else {
-        for (int it = 0; it < dp.n_tel; ++it) test(it);
+        return best >= 0 ? __ldg(dp.cell_tel + best) : -1;
     }
-    return tel;
+    for (int it = 0; it < dp.n_tel; ++it) {
+        float ddx, ddy, ddz, r;
+        full_delta(it, ddx, ddy, ddz, r);
+        test(ddx, ddy, ddz, r, it);
+    }
+    return best;
 }
 
 // The correction fields at (dz, tan^2 of the local zenith) and the
@@ -419,22 +431,32 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
                 }
             }
             if (dp.n_tel > 0) {
-                float ugx = ux, ugy = uy, ugz = uz;
-                if (ap.refraction) {   // n sin(theta) conserved, azimuth kept
-                    const float sc = (1.0f + Q.z) / ap.n_obs;
-                    ugx = ux * sc;
-                    ugy = uy * sc;
-                    const float c2 = fmaxf(1.0f - (ugx * ugx + ugy * ugy), 1e-30f);
-                    ugz = -c2 * rsqrtf(c2);
+                // arrival direction: n sin(theta) conserved, azimuth kept
+                const float sc = ap.refraction ? (1.0f + Q.z) * ap.inv_n_obs : 1.0f;
+                const float s2 = (ux * ux + uy * uy) * (sc * sc);
+                const bool hashed = s2 <= dp.hash_sin2_max;
+                if (!hashed || (x >= dp.bx0 && x < dp.bx1 && y >= dp.by0 && y < dp.by1)) {
+                    float ugz = uz;
+                    if (ap.refraction) {
+                        const float c2 = fmaxf(1.0f - s2, 1e-30f);
+                        ugz = -c2 * rsqrtf(c2);
+                    }
+                    tel = hit_telescope(
+                        dp, hashed, x, y, ux * sc, uy * sc, ugz,
+                        [&](const float4& D, float cx0, float cy0, float& ddx, float& ddy, float& ddz) {
+                            ddx = D.x - ((Cg.x - cx0) + (Cg.y + rx));
+                            ddy = D.y - ((Cg.z - cy0) + (Cg.w + ry));
+                            ddz = D.z;
+                        },
+                        [&](int it, float& ddx, float& ddy, float& ddz, float& r) {
+                            const float4 T4 = __ldg(dp.tel + it);
+                            const float2 TL = __ldg(dp.tel_lo + it);
+                            ddx = (T4.x - Cg.x) + ((TL.x - Cg.y) - rx);
+                            ddy = (T4.y - Cg.z) + ((TL.y - Cg.w) - ry);
+                            ddz = T4.z;
+                            r = T4.w;
+                        });
                 }
-                tel = hit_telescope(dp, x, y, ugx, ugy, ugz, [&](int it, float& ddx, float& ddy, float& ddz, float& r) {
-                    const float4 T4 = __ldg(dp.tel + it);
-                    const float2 TL = __ldg(dp.tel_lo + it);
-                    ddx = (T4.x - Cg.x) + ((TL.x - Cg.y) - rx);
-                    ddy = (T4.y - Cg.z) + ((TL.y - Cg.w) - ry);
-                    ddz = T4.z;
-                    r = T4.w;
-                });
                 if (tel >= 0) {
                     const size_t slot = (size_t)sh * dp.n_tel + tel;
                     atomicAdd(op.tel_counts + slot, (unsigned long long)b);
@@ -456,7 +478,7 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
         float Gy = Cc.y + (Dd.y + fmaf(ell, Py, tt * uy));
         float Gz = Cc.z + (Dd.z + fmaf(ell, Pz, tt * uz));
         // ground tangent in the plane of travel at the landing point
-        const float irg = 1.0f / rg;
+        const float irg = ap.inv_rg;
         const float gvx = Gx * irg, gvy = Gy * irg, gvz = (Gz - h_obs_f) * irg;   // v_G - z-hat
         const float uvG = ux * gvx + uy * gvy + uz * (1.0f + gvz);
         float tx = ux - uvG * gvx, ty = uy - uvG * gvy, tz = uz - uvG * (1.0f + gvz);
@@ -495,19 +517,28 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
             if (dp.n_tel > 0) {
                 float ugx = ux, ugy = uy, ugz = uz;
                 if (ap.refraction) {   // Bouguer: n r sin(psi) conserved in the plane of travel
-                    const float sin_g = (1.0f + Q.z) / ap.n_obs * re * irg * sqrtf(sin2);
+                    const float sin_g = (1.0f + Q.z) * ap.inv_n_obs * re * irg * sqrtf(sin2);
                     const float cos_g = sqrtf(fmaxf(1.0f - sin_g * sin_g, 0.0f));
                     ugx = -cos_g * gvx + sin_g * tx;
                     ugy = -cos_g * gvy + sin_g * ty;
                     ugz = -cos_g * (1.0f + gvz) + sin_g * tz;
                 }
-                tel = hit_telescope(dp, x, y, ugx, ugy, ugz, [&](int it, float& ddx, float& ddy, float& ddz, float& r) {
-                    const float4 T3 = __ldg(dp.tel3 + it);
-                    ddx = T3.x - Gx;
-                    ddy = T3.y - Gy;
-                    ddz = T3.z - Gz;
-                    r = T3.w;
-                });
+                const bool hashed = ugx * ugx + ugy * ugy <= dp.hash_sin2_max;
+                if (!hashed || (x >= dp.bx0 && x < dp.bx1 && y >= dp.by0 && y < dp.by1)) {
+                    auto delta3 = [&](const float4& T3, float& ddx, float& ddy, float& ddz) {
+                        ddx = T3.x - Gx;
+                        ddy = T3.y - Gy;
+                        ddz = T3.z - Gz;
+                    };
+                    tel = hit_telescope(
+                        dp, hashed, x, y, ugx, ugy, ugz,
+                        [&](const float4& D, float, float, float& ddx, float& ddy, float& ddz) { delta3(D, ddx, ddy, ddz); },
+                        [&](int it, float& ddx, float& ddy, float& ddz, float& r) {
+                            const float4 T3 = __ldg(dp.tel3 + it);
+                            delta3(T3, ddx, ddy, ddz);
+                            r = T3.w;
+                        });
+                }
                 if (tel >= 0) {
                     const size_t slot = (size_t)sh * dp.n_tel + tel;
                     atomicAdd(op.tel_counts + slot, (unsigned long long)b);

@@ -297,6 +297,7 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
     p.spherical = a.spherical;
     p.R = (float)a.R;
     p.rg = (float)(a.R + d->h_obs);
+    p.inv_rg = (float)(1.0 / (a.R + d->h_obs));
     p.n_layers = a.n_layers;
     p.refraction = a.refraction;
     p.transmission = d->transmission ? 1 : 0;
@@ -330,6 +331,9 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
         p.hom_delta = (float)a.hom_delta;
         p.n_obs = (float)(1.0 + a.hom_delta);
     }
+    p.inv_n_obs = 1.0f / p.n_obs;
+    p.h_obs_hi = (float)d->h_obs;
+    p.h_obs_lo = (float)(d->h_obs - (double)p.h_obs_hi);
     const double l1_nm = d->lambda_min * 1e9, l2_nm = d->lambda_max * 1e9;
     p.inv_l1_nm = (float)(1.0 / l1_nm);
     p.dinv_l_nm = (float)(1.0 / l1_nm - 1.0 / l2_nm);
