@@ -24,7 +24,8 @@ _lib = None
 ST_LANDED, ST_UPWARD, ST_BELOW, ST_DOMAIN, ST_ABSORBED, ST_SUBSTEP_FLAG = range(6)
 FL_COUNT, FL_ABSORB, FL_HIST_EDGE, FL_TEL_EDGE, FL_DOMAIN, FL_BELOW, FL_UPWARD, FL_LAYER = (
     1, 2, 4, 8, 16, 32, 64, 128)
-ATM_LAYERED, ATM_LINEAR, ATM_HOMOGENEOUS = 0, 1, 2
+ATM_LAYERED, ATM_LINEAR, ATM_HOMOGENEOUS, ATM_TABLE = 0, 1, 2, 3
+RHO_REF = 1.225e-3   # [g/cm^3]: the table kind's density is RHO_REF (n - 1) / kappa
 
 
 def build(force: bool = False) -> str:
@@ -43,7 +44,9 @@ class Atm(C.Structure):
                 ("layer_h", C.c_double * 8), ("a", C.c_double * 8), ("b", C.c_double * 8),
                 ("c", C.c_double * 8), ("h_top", C.c_double), ("kappa", C.c_double),
                 ("lin_h0", C.c_double), ("lin_h1", C.c_double), ("lin_n0", C.c_double),
-                ("lin_n1", C.c_double), ("hom_delta", C.c_double)]
+                ("lin_n1", C.c_double), ("hom_delta", C.c_double),
+                ("n_nodes", C.c_int), ("pad2", C.c_int), ("node_h", C.c_double * 128),
+                ("node_d", C.c_double * 128), ("rho_ref", C.c_double)]
 
 
 class Config(C.Structure):
@@ -123,9 +126,18 @@ def lib():
 # ---------------------------------------------------------------------------
 # argument helpers
 # ---------------------------------------------------------------------------
-def make_atm(kind=ATM_LAYERED, layered=None, linear=None, hom_delta=0.0):
+def make_atm(kind=ATM_LAYERED, layered=None, linear=None, hom_delta=0.0, table=None, kappa=2.9e-4):
+    """table: dict(h=[...], delta=[...]) of n - 1 at ascending node heights (table kind)."""
     a = Atm()
     a.kind = kind
+    if kind == ATM_TABLE:
+        h, d = list(table["h"]), list(table["delta"])
+        assert 2 <= len(h) <= 128 and len(h) == len(d)
+        a.n_nodes = len(h)
+        for i in range(len(h)):
+            a.node_h[i], a.node_d[i] = h[i], d[i]
+        a.kappa, a.rho_ref, a.h_top = kappa, RHO_REF, h[-1]
+        return a
     if kind == ATM_LAYERED:
         p = layered
         n = len(p["layer_h"])
@@ -249,7 +261,7 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
         use_domain = bool(refraction or transmission)
     cfg.use_domain = int(use_domain)
     cfg.w_max = w_max if w_max is not None else float(np.tan(np.radians(75.0)) ** 2)
-    if atm.kind == ATM_LAYERED:
+    if atm.kind in (ATM_LAYERED, ATM_TABLE):
         cfg.h_dom_top = atm.h_top
     elif atm.kind == ATM_LINEAR:
         cfg.h_dom_top = atm.lin_h1

@@ -75,7 +75,8 @@ static double orc_uniform(uint32_t x) { return (double)(x >> 8) * (1.0 / 1677721
 /* ------------------------------------------------------------------ */
 /* Atmosphere (Sec. 3.3).                                             */
 /* ------------------------------------------------------------------ */
-enum { ORC_ATM_LAYERED = 0, ORC_ATM_LINEAR = 1, ORC_ATM_HOMOGENEOUS = 2 };
+enum { ORC_ATM_LAYERED = 0, ORC_ATM_LINEAR = 1, ORC_ATM_HOMOGENEOUS = 2, ORC_ATM_TABLE = 3 };
+#define ORC_MAX_NODES 128
 
 typedef struct {
     int kind;
@@ -89,7 +90,51 @@ typedef struct {
     double lin_h0, lin_h1; /* linear kind: n = n0 at h0 falling to n1 at h1        */
     double lin_n0, lin_n1;
     double hom_delta;      /* homogeneous kind: n - 1                              */
+    /* table kind (a user's n(h) table, Sec. 3.3): n - 1 at ascending node
+     * heights, log-linear between nodes (each interval one exponential), the
+     * first interval's law continued below the first node, vacuum at and
+     * above the last node (the top); density rho = rho_ref (n - 1) / kappa */
+    int n_nodes;
+    int pad2;
+    double node_h[ORC_MAX_NODES];
+    double node_d[ORC_MAX_NODES];
+    double rho_ref;        /* [g/cm^3] */
 } orc_atm;
+
+/* Table kind: the interval [node_h[i], node_h[i+1]) holding h (the first
+ * interval below the first node) and its exponential rate k = d ln(n-1)/dh. */
+static int orc_node_interval(const orc_atm* a, double h, double* k)
+{
+    int i = 0;
+    while (i + 2 < a->n_nodes && h >= a->node_h[i + 1]) ++i;
+    *k = log(a->node_d[i + 1] / a->node_d[i]) / (a->node_h[i + 1] - a->node_h[i]);
+    return i;
+}
+
+static double orc_table_delta(const orc_atm* a, double h)
+{
+    if (h >= a->node_h[a->n_nodes - 1]) return 0.0;
+    double k;
+    int i = orc_node_interval(a, h, &k);
+    return a->node_d[i] * exp(k * (h - a->node_h[i]));
+}
+
+/* Table kind: integral of n - 1 over [lo, hi] below the top, interval by interval. */
+static double orc_table_delta_integral(const orc_atm* a, double lo, double hi)
+{
+    double top = a->node_h[a->n_nodes - 1], sum = 0.0;
+    if (hi > top) hi = top;
+    for (int i = 0; i + 1 < a->n_nodes; ++i) {
+        double l0 = (i == 0) ? -1e30 : a->node_h[i];
+        double l1 = a->node_h[i + 1];
+        double p = fmax(lo, l0), q = fmin(hi, l1);
+        if (q <= p) continue;
+        double k = log(a->node_d[i + 1] / a->node_d[i]) / (a->node_h[i + 1] - a->node_h[i]);
+        double ep = exp(k * (p - a->node_h[i])), eq = exp(k * (q - a->node_h[i]));
+        sum += (k != 0.0) ? a->node_d[i] * (eq - ep) / k : a->node_d[i] * (q - p);
+    }
+    return sum;
+}
 
 static int orc_layer_of(const orc_atm* a, double h)
 {
@@ -101,6 +146,8 @@ static int orc_layer_of(const orc_atm* a, double h)
 /* Vertical column depth above h [g/cm^2]. */
 double orc_atm_T(const orc_atm* a, double h)
 {
+    if (a->kind == ORC_ATM_TABLE)
+        return 100.0 * a->rho_ref / a->kappa * orc_table_delta_integral(a, h, a->node_h[a->n_nodes - 1]);
     if (a->kind != ORC_ATM_LAYERED) return 0.0;
     if (h >= a->h_top) return 0.0;
     int i = orc_layer_of(a, h);
@@ -112,6 +159,7 @@ double orc_atm_T(const orc_atm* a, double h)
 /* Density rho = -dT/dh [g/cm^3]. */
 double orc_atm_rho(const orc_atm* a, double h)
 {
+    if (a->kind == ORC_ATM_TABLE) return a->rho_ref * orc_table_delta(a, h) / a->kappa;
     if (a->kind != ORC_ATM_LAYERED) return 0.0;
     if (h >= a->h_top) return 0.0;
     int i = orc_layer_of(a, h);
@@ -132,6 +180,7 @@ static double orc_T_layer(const orc_atm* a, int i, double h)
  * piecewise fit is continuous only to about 1e-3 g/cm^2 at the boundaries). */
 double orc_column(const orc_atm* a, double lo, double hi)
 {
+    if (a->kind == ORC_ATM_TABLE) return 100.0 * a->rho_ref / a->kappa * orc_table_delta_integral(a, lo, hi);
     if (a->kind != ORC_ATM_LAYERED) return 0.0;
     double X = 0.0;
     for (int i = 0; i < a->n_layers; ++i) {
@@ -151,6 +200,8 @@ double orc_atm_delta(const orc_atm* a, double h)
     switch (a->kind) {
     case ORC_ATM_LAYERED:
         return a->kappa * orc_atm_rho(a, h) / orc_rho0(a);
+    case ORC_ATM_TABLE:
+        return orc_table_delta(a, h);
     case ORC_ATM_LINEAR: {
         if (h >= a->lin_h1) return a->lin_n1 - 1.0;
         double f = (h - a->lin_h0) / (a->lin_h1 - a->lin_h0);
@@ -173,6 +224,9 @@ static int orc_breakpoints(const orc_atm* a, double lo, double hi, double* bp)
         if (a->h_top > lo && a->h_top < hi) bp[m++] = a->h_top;
     } else if (a->kind == ORC_ATM_LINEAR) {
         if (a->lin_h1 > lo && a->lin_h1 < hi) bp[m++] = a->lin_h1;
+    } else if (a->kind == ORC_ATM_TABLE) {
+        for (int i = 1; i < a->n_nodes; ++i)
+            if (a->node_h[i] > lo && a->node_h[i] < hi) bp[m++] = a->node_h[i];
     }
     return m;
 }
@@ -243,9 +297,9 @@ static double orc_integrate(const orc_atm* a, orc_fn f, const void* ctx, double 
                             double rtol)
 {
     orc_gl_init();
-    double bp[16];
+    double bp[ORC_MAX_NODES + 16];
     int m = orc_breakpoints(a, lo, hi, bp);
-    double edges[18];
+    double edges[ORC_MAX_NODES + 18];
     edges[0] = lo;
     for (int i = 0; i < m; ++i) edges[i + 1] = bp[i];
     edges[m + 1] = hi;
@@ -369,6 +423,33 @@ int orc_refract_closed(const orc_atm* a, double h_obs, double h_e, double theta0
         double G_hi = 0.5 * (n_hi * q_hi + s * s * log(n_hi + q_hi));
         out[1] = (G_lo - G_hi) / (c1 * ORC_C_LIGHT);
         out[2] = 0.0;
+        return 0;
+    }
+    if (a->kind == ORC_ATM_TABLE) {
+        /* each interval is an exponential layer with its own scale height */
+        double top = a->node_h[a->n_nodes - 1];
+        if (h_e >= top) return -1;
+        for (int i = 0; i + 1 < a->n_nodes; ++i) {
+            double lo = (i == 0) ? h_obs : fmax(h_obs, a->node_h[i]);
+            double hi = fmin(h_e, a->node_h[i + 1]);
+            if (hi <= lo) continue;
+            double k = log(a->node_d[i + 1] / a->node_d[i]) / (a->node_h[i + 1] - a->node_h[i]);
+            double n_lo = 1.0 + a->node_d[i] * exp(k * (lo - a->node_h[i]));
+            double n_hi = 1.0 + a->node_d[i] * exp(k * (hi - a->node_h[i]));
+            double q_lo = sqrt(n_lo * n_lo - s * s), q_hi = sqrt(n_hi * n_hi - s * s);
+            if (k == 0.0) {   /* constant n: a straight line */
+                R += (hi - lo) * s / q_lo;
+                T += (hi - lo) * n_lo * n_lo / q_lo / ORC_C_LIGHT;
+                X += 100.0 * a->rho_ref / a->kappa * (n_lo - 1.0) * (hi - lo) * n_lo / q_lo;
+                continue;
+            }
+            double H = -1.0 / k;
+            double F_lo = orc_F(n_lo, s), F_hi = orc_F(n_hi, s);
+            R += H * s * (F_lo - F_hi);
+            T += H / ORC_C_LIGHT * ((q_lo - q_hi) + (log(n_lo + q_lo) - log(n_hi + q_hi)) + (F_lo - F_hi));
+            X += 100.0 * H * (a->rho_ref / a->kappa) * (q_lo - q_hi);
+        }
+        out[0] = R; out[1] = T; out[2] = X;
         return 0;
     }
     /* layered */
