@@ -83,7 +83,11 @@ enum {
 enum {
     CS_ATM_LAYERED = 0,      /* CORSIKA-style layers: T(h) = a + b exp(-h/c), top layer linear */
     CS_ATM_LINEAR = 1,       /* n falls linearly from lin_n0 at lin_h0 to lin_n1 at lin_h1 (Sec. 6.3.1) */
-    CS_ATM_HOMOGENEOUS = 2   /* constant n = 1 + hom_delta (Sec. 3.3.1) */
+    CS_ATM_HOMOGENEOUS = 2,  /* constant n = 1 + hom_delta (Sec. 3.3.1) */
+    CS_ATM_TABLE = 3         /* a user's n(h) table (Sec. 3.3): n - 1 at ascending node heights,
+                                log-linear between nodes, the first interval's law below the first
+                                node, vacuum at and above the last node (the top); density
+                                1.225e-3 g/cm^3 * (n - 1) / kappa for the transmission stage */
 };
 
 typedef struct cs_atmosphere_desc {
@@ -109,6 +113,10 @@ typedef struct cs_atmosphere_desc {
     double table_dh;             /* 0 = default row spacing [m]; must divide the layer bottoms - h_obs */
     int geometry;                /* CS_GEOM_PLANAR or CS_GEOM_SPHERICAL */
     double earth_radius;         /* spherical: R_E [m]; 0 = 6,370 km */
+    int table_n;                 /* CS_ATM_TABLE: 2 .. 128 nodes */
+    const double* table_h;       /* CS_ATM_TABLE: node heights [m], strictly ascending; host, read during
+                                    the call only */
+    const double* table_delta;   /* CS_ATM_TABLE: n - 1 at the nodes, > 0 */
 } cs_atmosphere_desc;
 
 typedef struct cs_atmosphere cs_atmosphere;

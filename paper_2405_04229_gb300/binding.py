@@ -19,7 +19,7 @@ _lock = threading.Lock()
 _lib = None
 
 CS_OK, CS_ERR_INVALID_ARG, CS_ERR_CUDA, CS_ERR_CAPACITY, CS_ERR_TIMEOUT, CS_ERR_DOMAIN, CS_ERR_NO_DEVICE = range(7)
-CS_ATM_LAYERED, CS_ATM_LINEAR, CS_ATM_HOMOGENEOUS = 0, 1, 2
+CS_ATM_LAYERED, CS_ATM_LINEAR, CS_ATM_HOMOGENEOUS, CS_ATM_TABLE = 0, 1, 2, 3
 CS_GEOM_PLANAR, CS_GEOM_SPHERICAL = 0, 1
 (CS_CNT_EMITTED, CS_CNT_ABSORBED, CS_CNT_HIST, CS_CNT_TEL, CS_CNT_MISSED_HIST, CS_CNT_MISSED_TEL,
  CS_CNT_UPWARD, CS_CNT_INVALID_SEGMENTS) = range(8)
@@ -57,7 +57,8 @@ class cs_atmosphere_desc(C.Structure):
                 ("rayl_X0", C.c_double), ("rayl_lambda0", C.c_double),
                 ("aer_tau0", C.c_double), ("aer_lambda0", C.c_double), ("aer_alpha", C.c_double),
                 ("aer_H", C.c_double), ("theta_max", C.c_double), ("table_nw", C.c_int),
-                ("table_dh", C.c_double), ("geometry", C.c_int), ("earth_radius", C.c_double)]
+                ("table_dh", C.c_double), ("geometry", C.c_int), ("earth_radius", C.c_double),
+                ("table_n", C.c_int), ("table_h", C.POINTER(C.c_double)), ("table_delta", C.POINTER(C.c_double))]
 
 
 class cs_detector_desc(C.Structure):
@@ -301,7 +302,8 @@ class Atmosphere:
 
     def __init__(self, kind=CS_ATM_LAYERED, layered=None, linear=None, hom_delta=0.0, h_obs=2000.0,
                  lambda_nm=(300.0, 600.0), refraction=False, transmission=False, transmission_params=None,
-                 theta_max_deg=75.0, table_nw=0, table_dh=0.0, spherical=False, earth_radius=0.0):
+                 theta_max_deg=75.0, table_nw=0, table_dh=0.0, spherical=False, earth_radius=0.0, table=None,
+                 kappa=2.9e-4):
         d = cs_atmosphere_desc()
         d.kind = kind
         self._keep = []
@@ -312,6 +314,12 @@ class Atmosphere:
             d.n_layers = n
             d.layer_h, d.layer_a, d.layer_b, d.layer_c = (a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs)
             d.h_top, d.kappa = layered["h_top"], layered["kappa"]
+        elif kind == CS_ATM_TABLE:
+            arrs = [np.ascontiguousarray(table[k], np.float64) for k in ("h", "delta")]
+            self._keep += arrs
+            d.table_n = len(arrs[0])
+            d.table_h, d.table_delta = (a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs)
+            d.kappa = kappa
         elif kind == CS_ATM_LINEAR:
             d.lin_h0, d.lin_h1, d.lin_n0, d.lin_n1 = (linear[k] for k in ("lin_h0", "lin_h1", "lin_n0", "lin_n1"))
         else:

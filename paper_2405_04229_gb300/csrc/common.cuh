@@ -13,6 +13,8 @@ constexpr double kAlpha = 7.2973525693e-3;  // fine-structure constant
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kLog2e = 1.4426950408889634;
 constexpr int kMaxLayers = 8;
+constexpr int kMaxNodes = 128;     // tabulated atmosphere
+constexpr double kTableRhoRef = 1.225e-3;   // [g/cm^3]: density = kTableRhoRef (n - 1) / kappa
 
 // Correction table: per node two float4 {value at h_j from above, change to
 // h_j+1 from below}; the four fields are
@@ -46,6 +48,12 @@ struct AtmParams {
     float top_rel;       // vacuum above h_top - h_obs
     float lin_d0, lin_slope, lin_top_rel, lin_d1;   // linear kind, relative to h_obs
     float hom_delta;
+    // tabulated kind: interval i starts at node_lo[i] (relative to h_obs; the
+    // first also serves below it) with n - 1 = node_d[i] exp2(node_c2[i] (dz - node_lo[i]))
+    int n_nodes;
+    const float* node_lo;   // device: node_lo, node_d, node_c2 (n_nodes - 1 each)
+    const float* node_d;
+    const float* node_c2;
     float n_obs;         // n(h_obs)
     float inv_n_obs;
     double h_obs;
@@ -114,6 +122,8 @@ struct AtmF64 {
     int refraction;
     int spherical;          // 1: spherical shell, Earth radius R
     double R;
+    int n_nodes;            // tabulated kind: n - 1 log-linear between nodes
+    double node_h[kMaxNodes], node_d[kMaxNodes];
 };
 
 
@@ -136,6 +146,7 @@ cs_status exact_fields(const cs_atmosphere* atm, const double2* d_in, size_t n, 
 struct cs_atmosphere {
     cs::AtmParams p;
     float4* d_tab;         // device table (owned)
+    float* d_nodes;        // tabulated kind: interval laws (owned)
     double h0, dh, dw;
     int device;
     cs::AtmF64 f64;        // the FP64 description the tables were built from

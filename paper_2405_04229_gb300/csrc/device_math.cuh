@@ -137,6 +137,16 @@ __device__ __forceinline__ float delta_at(const AtmParams& a, float dz) {
         return a.lay_D[i] * exp2f(a.lay_c2[i] * dz);
     }
     if (a.kind == CS_ATM_LINEAR) return dz >= a.lin_top_rel ? a.lin_d1 : a.lin_d0 + a.lin_slope * dz;
+    if (a.kind == CS_ATM_TABLE) {
+        if (dz >= a.top_rel) return 0.0f;
+        int lo = 0, hi = a.n_nodes - 1;   // interval: largest i < n - 1 with node_lo[i] <= dz
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(a.node_lo + mid) <= dz) lo = mid;
+            else hi = mid;
+        }
+        return __ldg(a.node_d + lo) * exp2f(__ldg(a.node_c2 + lo) * (dz - __ldg(a.node_lo + lo)));
+    }
     return a.hom_delta;
 }
 

@@ -61,6 +61,15 @@ __device__ inline void delta_rho(const AtmF64& a, double h, bool below, double* 
                                          : a.lay_b[i] / a.lay_c[i] * exp(-h * 100.0 / a.lay_c[i]);
         *rho = r;
         *delta = a.kappa * r / a.rho0;
+    } else if (a.kind == CS_ATM_TABLE) {
+        const int n = a.n_nodes;
+        bool vac = below ? (h > a.node_h[n - 1]) : (h >= a.node_h[n - 1]);
+        if (vac) { *delta = 0.0; *rho = 0.0; return; }
+        int i = 0;
+        while (i + 2 < n && h >= a.node_h[i + 1]) ++i;
+        const double k = log(a.node_d[i + 1] / a.node_d[i]) / (a.node_h[i + 1] - a.node_h[i]);
+        *delta = a.node_d[i] * exp(k * (h - a.node_h[i]));
+        *rho = kTableRhoRef * *delta / a.kappa;
     } else if (a.kind == CS_ATM_LINEAR) {
         *rho = 0.0;
         bool above_top = below ? (h > a.lin_h1) : (h >= a.lin_h1);
@@ -90,6 +99,9 @@ __device__ void node_fields(const AtmF64& a, double h_e, bool below, double cos0
         if (a.h_top > a.h_obs && a.h_top < h_e) cuts[nc++] = a.h_top;
     } else if (a.kind == CS_ATM_LINEAR) {
         if (a.lin_h1 > a.h_obs && a.lin_h1 < h_e) cuts[nc++] = a.lin_h1;
+    } else if (a.kind == CS_ATM_TABLE) {
+        for (int k = 1; k < a.n_nodes; ++k)
+            if (a.node_h[k] > a.h_obs && a.node_h[k] < h_e) cuts[nc++] = a.node_h[k];
     }
     cuts[nc++] = h_e;
     // spherical shell: r = R + h, Bouguer's invariant K = n_e r_e sin(psi0); the
@@ -225,7 +237,7 @@ using namespace cs;
 extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosphere** out) {
     if (!d || !out) return CS_ERR_INVALID_ARG;
     *out = nullptr;
-    if (d->kind < CS_ATM_LAYERED || d->kind > CS_ATM_HOMOGENEOUS) return CS_ERR_INVALID_ARG;
+    if (d->kind < CS_ATM_LAYERED || d->kind > CS_ATM_TABLE) return CS_ERR_INVALID_ARG;
     if (!(d->lambda_min > 0.0) || !(d->lambda_max > d->lambda_min)) return CS_ERR_INVALID_ARG;
     if (!isfinite(d->h_obs)) return CS_ERR_INVALID_ARG;
     const double theta_max = d->theta_max > 0.0 ? d->theta_max : 75.0 * kPi / 180.0;
@@ -271,6 +283,19 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
         if (d->transmission) return CS_ERR_INVALID_ARG;   // no density for this kind
         table_top = a.lin_h1;
         if (!divides(a.lin_h1 - d->h_obs, dh)) return CS_ERR_INVALID_ARG;
+    } else if (d->kind == CS_ATM_TABLE) {
+        if (d->table_n < 2 || d->table_n > kMaxNodes || !d->table_h || !d->table_delta) return CS_ERR_INVALID_ARG;
+        a.n_nodes = d->table_n;
+        for (int i = 0; i < d->table_n; ++i) {
+            a.node_h[i] = d->table_h[i];
+            a.node_d[i] = d->table_delta[i];
+            if (!isfinite(a.node_h[i]) || !(a.node_d[i] > 0.0) || !isfinite(a.node_d[i])) return CS_ERR_INVALID_ARG;
+            if (i > 0 && !(a.node_h[i] > a.node_h[i - 1])) return CS_ERR_INVALID_ARG;
+        }
+        a.kappa = d->kappa > 0.0 ? d->kappa : 2.9e-4;
+        a.h_top = a.node_h[a.n_nodes - 1];
+        if (!(d->h_obs < a.h_top)) return CS_ERR_INVALID_ARG;
+        table_top = a.h_top;
     } else {
         a.hom_delta = d->hom_delta;
         if (!(a.hom_delta >= 0.0)) return CS_ERR_INVALID_ARG;
@@ -283,6 +308,25 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
     cs_atmosphere* h = new cs_atmosphere;
     memset(h, 0, sizeof *h);
     cudaGetDevice(&h->device);
+    if (d->kind == CS_ATM_TABLE) {   // interval laws for the FP32 hot path, relative to h_obs
+        const int m = a.n_nodes - 1;
+        std::vector<float> nodes(3 * (size_t)m);
+        for (int i = 0; i < m; ++i) {
+            const double k = log(a.node_d[i + 1] / a.node_d[i]) / (a.node_h[i + 1] - a.node_h[i]);
+            nodes[i] = (float)(a.node_h[i] - d->h_obs);
+            nodes[m + i] = (float)a.node_d[i];
+            nodes[2 * m + i] = (float)(k * kLog2e);
+        }
+        if (cudaMalloc(&h->d_nodes, nodes.size() * sizeof(float)) != cudaSuccess ||
+            cudaMemcpy(h->d_nodes, nodes.data(), nodes.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(h->d_nodes);
+            delete h;
+            return CS_ERR_CUDA;
+        }
+        h->p.node_lo = h->d_nodes;
+        h->p.node_d = h->d_nodes + m;
+        h->p.node_c2 = h->d_nodes + 2 * m;
+    }
     h->f64 = a;
     h->rayl_X0 = d->rayl_X0;
     h->rayl_lambda0 = d->rayl_lambda0;
@@ -327,6 +371,17 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
         p.lin_top_rel = (float)(a.lin_h1 - d->h_obs);
         p.lin_d1 = (float)(a.lin_n1 - 1.0);
         p.n_obs = 1.0f + p.lin_d0;
+    } else if (d->kind == CS_ATM_TABLE) {
+        p.n_nodes = a.n_nodes;
+        p.top_rel = (float)(a.h_top - d->h_obs);
+        double d_obs = 0.0;
+        {
+            int i = 0;
+            while (i + 2 < a.n_nodes && d->h_obs >= a.node_h[i + 1]) ++i;
+            const double k = log(a.node_d[i + 1] / a.node_d[i]) / (a.node_h[i + 1] - a.node_h[i]);
+            d_obs = a.node_d[i] * exp(k * (d->h_obs - a.node_h[i]));
+        }
+        p.n_obs = (float)(1.0 + d_obs);
     } else {
         p.hom_delta = (float)a.hom_delta;
         p.n_obs = (float)(1.0 + a.hom_delta);
@@ -340,6 +395,7 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
     p.ft = (float)(2.0 * kPi * kAlpha * (1.0 / d->lambda_min - 1.0 / d->lambda_max));
     if (p.transmission) {
         if (!(d->rayl_X0 > 0.0) || !(d->rayl_lambda0 > 0.0) || !(d->aer_lambda0 > 0.0)) {
+            cudaFree(h->d_nodes);
             delete h;
             return CS_ERR_INVALID_ARG;
         }
@@ -383,7 +439,7 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
     cudaError_t e = cudaSuccess;
     auto fail = [&](const char* where) {
         set_last_error(where, e);
-        cudaFree(dF); cudaFree(dFb); cudaFree(dslot); cudaFree(drows); cudaFree(h->d_tab);
+        cudaFree(dF); cudaFree(dFb); cudaFree(dslot); cudaFree(drows); cudaFree(h->d_tab); cudaFree(h->d_nodes);
         delete h;
         return CS_ERR_CUDA;
     };
@@ -423,6 +479,7 @@ cs_status exact_fields(const cs_atmosphere* atm, const double2* d_in, size_t n, 
 extern "C" void cs_atmosphere_destroy(cs_atmosphere* atm) {
     if (!atm) return;
     cudaFree(atm->d_tab);
+    cudaFree(atm->d_nodes);
     delete atm;
 }
 

@@ -34,6 +34,13 @@ US_STANDARD = dict(
     kappa=2.9e-4,
 )
 
+# A user's n(h) table (the tabulated atmosphere kind): nodes every 1.5-7 km to
+# 40 km with a falling profile, one rising and one constant interval.
+TABLE_PROFILE = dict(
+    h=[0.0, 1500.0, 3000.0, 4500.0, 7000.0, 9000.0, 12000.0, 15000.0, 20000.0, 26000.0, 33000.0, 40000.0],
+    delta=[2.9e-4, 2.5e-4, 2.15e-4, 2.2e-4, 1.6e-4, 1.6e-4, 1.0e-4, 6.4e-5, 3.1e-5, 1.2e-5, 4.0e-6, 1.5e-6],
+)
+
 # Linear test profile of the thesis's propagation cross-check (Sec. 6.3.1):
 # n = 1.5 at the ground falling linearly to 1.0 at 100 km.
 LINEAR_TEST = dict(lin_h0=0.0, lin_h1=100_000.0, lin_n0=1.5, lin_n1=1.0)

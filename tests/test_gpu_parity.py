@@ -270,3 +270,36 @@ def test_steep_arrivals_beyond_the_telescope_hash():
     assert int(g["counters"][B.CS_CNT_TEL]) > 5000
     d = np.abs(g["tel_counts"].astype(np.int64) - o["tel_counts"].astype(np.int64)).sum()
     assert d <= 2 * (st["tel_flips"] + st["status_flips"] + st["only_gpu"] + st["only_oracle"])
+
+
+def test_tabulated_atmosphere_table_builder_and_photons():
+    """A user's n(h) table (log-linear between nodes): the FP64 table builder
+    against the oracle's quadrature, and photon parity with refraction,
+    transmission and telescopes."""
+    C = 299792458.0
+    orc = oracle.make_atm(oracle.ATM_TABLE, table=synth.TABLE_PROFILE)
+    atm = B.Atmosphere(kind=B.CS_ATM_TABLE, table=synth.TABLE_PROFILE, refraction=True, transmission=True)
+    tab, info = atm.table()
+    rng = np.random.default_rng(9)
+    for _ in range(40):
+        j = int(rng.integers(0, info["nh"] - 1))
+        m = int(rng.integers(0, info["nw"]))
+        h_e = info["h0"] + j * info["dh"]
+        w = max(m * info["dw"], 1e-8)
+        th = math.atan(math.sqrt(w))
+        c, s = math.cos(th), math.sin(th)
+        q = oracle.refract_quad(orc, 2000.0, h_e, th, rtol=1e-13)
+        want = np.array([(q[0] - (h_e - 2000.0) * math.tan(th)) * c**3 / s,
+                         (q[1] * C - (h_e - 2000.0) / c) * c, q[2] * c, q[3] * c])
+        got = tab[j, m, 0].astype(np.float64)
+        scale = np.maximum(np.abs(want), [1e-3, 1e-3, 1e-2, 1e-2])
+        assert np.all(np.abs(got - want) <= 2e-6 * scale + 1e-9), (j, m, got, want)
+    segs = synth.refraction_showers(n_showers=1, per_shower=1500, seed=8)
+    tel = synth.grid_telescopes()
+    det = B.Detector(hist=HIST, tel=tel)
+    g = B.propagate_host(segs, atm, det, seed=3, bunch=4, records=True)
+    o = oracle.propagate(segs, orc, hist=HIST, tel=tel, bunch=4, refraction=True, transmission=True, seed=3)
+    st = PU.compare(g, o, bunch=4)
+    assert st["matched"] > 10000
+    PU.check_conservation(g["counters"])
+    assert g["counters"][B.CS_CNT_TEL] > 0 and g["counters"][B.CS_CNT_ABSORBED] > 0

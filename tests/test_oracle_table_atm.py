@@ -26,11 +26,7 @@ def _layer0_table(top=4000.0, step=250.0):
 
 
 def _rough_table():
-    """Nodes every 1-3 km to 40 km with a decreasing profile, one increasing
-    and one constant interval."""
-    h = [0.0, 1500.0, 3000.0, 4500.0, 7000.0, 9000.0, 12000.0, 15000.0, 20000.0, 26000.0, 33000.0, 40000.0]
-    d = [2.9e-4, 2.5e-4, 2.15e-4, 2.2e-4, 1.6e-4, 1.6e-4, 1.0e-4, 6.4e-5, 3.1e-5, 1.2e-5, 4.0e-6, 1.5e-6]
-    return dict(h=h, delta=d)
+    return synth.TABLE_PROFILE
 
 
 def test_nodes_and_log_linear_interpolation():
