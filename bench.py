@@ -127,7 +127,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_rate(segs, tel, hist, budget_s=12.0, chunk=250, bunch=5, seed=0):
+def cpu_oracle_rate(segs, tel, hist, budget_s=12.0, chunk=250, bunch=5, seed=0, threads=None):
     """The FP64 oracle as it stands, on the host cores, over a bounded prefix
     of every shower of the workload; returns (photons/s, threads, sample)."""
     import concurrent.futures as cf
@@ -138,7 +138,7 @@ def cpu_oracle_rate(segs, tel, hist, budget_s=12.0, chunk=250, bunch=5, seed=0):
     n = len(segs["z0"])
     n_showers = int(segs["shower_id"].max()) + 1
     per = n // n_showers
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     # interleave chunks across showers so the sample has every shower's shape
     starts = [s * per + j for j in range(0, per, chunk) for s in range(n_showers)]
     done_photons, done_segs = 0, 0
@@ -175,6 +175,32 @@ def cpu_oracle_rate(segs, tel, hist, budget_s=12.0, chunk=250, bunch=5, seed=0):
         done_segs, chunk, n_showers, dt)
 
 
+def cpu_model():
+    """The host CPU's model string (x86 'model name', else lscpu's 'Model name')."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def cpu_baseline_entry(segs, tel, hist):
+    """The oracle on all host cores (the reported value) and on one core."""
+    rate, cores, sample = cpu_oracle_rate(segs, tel, hist)
+    rate1, _, sample1 = cpu_oracle_rate(segs, tel, hist, budget_s=4.0, threads=1)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "single_core": {"value": rate1, "sample": sample1}, "cpu_model": cpu_model()}
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -186,7 +212,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "l2": "inputs re-read per chunk on the host"},
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -655,8 +682,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        rate, cores, sample = cpu_oracle_rate(segs, tel, hist)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = cpu_baseline_entry(segs, tel, hist)
 
     if rank == 0:
         line = {

@@ -707,6 +707,9 @@ __global__ void philox_kernel(const uint4* ctr, size_t n, uint32_t k0, uint32_t 
     }
 }
 
+// Host-pointer calls above 2 chunks of this many segments stream their input.
+constexpr size_t kHostChunk = (size_t)1 << 18;
+
 // Device buffers reused by host-pointer calls.
 struct HostWorkspace {
     std::mutex mu;
@@ -714,6 +717,7 @@ struct HostWorkspace {
     void* segs = nullptr; size_t segs_cap = 0;
     void* outs = nullptr; size_t outs_cap = 0;
     void* recs = nullptr; size_t recs_cap = 0;
+    cs_streamer* streamer = nullptr;   // large host inputs: chunks overlap copies and kernels
 };
 HostWorkspace g_ws;
 
@@ -828,12 +832,15 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
     if (g_ws.device != dev) {   // buffers of another device are not reused
         g_ws.segs = g_ws.outs = g_ws.recs = nullptr;
         g_ws.segs_cap = g_ws.outs_cap = g_ws.recs_cap = 0;
+        g_ws.streamer = nullptr;
         g_ws.device = dev;
     }
     const size_t hist_b = (size_t)dp.n_showers * dp.nx * dp.ny * 8, tel_b = (size_t)dp.n_showers * dp.n_tel * 8;
     const size_t o_hist = 0, o_tel = up256(hist_b), o_time = o_tel + up256(tel_b), o_cnt = o_time + up256(tel_b),
                  o_rc = o_cnt + 256, outs_b = o_rc + 256;
-    CS_CUDA_TRY(ensure(&g_ws.segs, &g_ws.segs_cap, std::max<size_t>(n, 1) * sizeof(cs_segment)));
+    // large inputs are streamed in chunks: the copy of one chunk overlaps the kernel of the previous
+    const bool chunked = n > 2 * kHostChunk;
+    if (!chunked) CS_CUDA_TRY(ensure(&g_ws.segs, &g_ws.segs_cap, std::max<size_t>(n, 1) * sizeof(cs_segment)));
     CS_CUDA_TRY(ensure(&g_ws.outs, &g_ws.outs_cap, outs_b));
     const size_t rec_b = out->records ? out->record_capacity * sizeof(cs_record) : 0;
     if (rec_b) CS_CUDA_TRY(ensure(&g_ws.recs, &g_ws.recs_cap, rec_b));
@@ -846,7 +853,8 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
     op.records = out->records ? (cs_record*)g_ws.recs : nullptr;
     op.record_capacity = out->records ? out->record_capacity : 0;
     op.record_count = (unsigned long long*)(ob + o_rc);
-    if (n) CS_CUDA_TRY(cudaMemcpyAsync(g_ws.segs, segs, n * sizeof(cs_segment), cudaMemcpyHostToDevice, stream));
+    if (n && !chunked)
+        CS_CUDA_TRY(cudaMemcpyAsync(g_ws.segs, segs, n * sizeof(cs_segment), cudaMemcpyHostToDevice, stream));
     if (o.accumulate) {   // bring the caller's running totals in
         if (op.hist) CS_CUDA_TRY(cudaMemcpyAsync(op.hist, out->hist, hist_b, cudaMemcpyHostToDevice, stream));
         if (op.tel_counts) CS_CUDA_TRY(cudaMemcpyAsync(op.tel_counts, out->tel_counts, tel_b, cudaMemcpyHostToDevice, stream));
@@ -854,7 +862,26 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
         CS_CUDA_TRY(cudaMemcpyAsync(op.counters, out->counters, CS_N_COUNTERS * 8, cudaMemcpyHostToDevice, stream));
         CS_CUDA_TRY(cudaMemsetAsync(op.record_count, 0, 8, stream));
     }
-    cs_status st = launch((const cs_segment*)g_ws.segs, n, atm, det, seed, o, op, stream);
+    cs_status st;
+    if (chunked) {
+        if (!g_ws.streamer) {
+            st = cs_streamer_create(kHostChunk, &g_ws.streamer);
+            if (st != CS_OK) return st;
+        }
+        cs_output dout;
+        dout.hist = (uint64_t*)op.hist;
+        dout.tel_counts = (uint64_t*)op.tel_counts;
+        dout.tel_time = op.tel_time;
+        dout.counters = (uint64_t*)op.counters;
+        dout.records = op.records;
+        dout.record_capacity = op.record_capacity;
+        dout.record_count = (uint64_t*)op.record_count;
+        cs_opts od = o;
+        od.device_ptrs = 1;
+        st = cs_streamer_run(g_ws.streamer, segs, n, atm, det, seed, &od, &dout, stream);
+    } else {
+        st = launch((const cs_segment*)g_ws.segs, n, atm, det, seed, o, op, stream);
+    }
     if (st != CS_OK) return st;
     if (op.hist) CS_CUDA_TRY(cudaMemcpyAsync(out->hist, op.hist, hist_b, cudaMemcpyDeviceToHost, stream));
     if (op.tel_counts) CS_CUDA_TRY(cudaMemcpyAsync(out->tel_counts, op.tel_counts, tel_b, cudaMemcpyDeviceToHost, stream));

@@ -303,3 +303,27 @@ def test_tabulated_atmosphere_table_builder_and_photons():
     assert st["matched"] > 10000
     PU.check_conservation(g["counters"])
     assert g["counters"][B.CS_CNT_TEL] > 0 and g["counters"][B.CS_CNT_ABSORBED] > 0
+
+
+def test_large_host_call_streams_and_equals_device_call():
+    """Host-pointer calls above two chunks of 2^18 segments stream their input
+    (copies overlap kernels); the integer outputs equal one device call."""
+    torch = pytest.importorskip("torch")
+    import ctypes as C
+    segs = synth.refraction_showers(n_showers=3, per_shower=200_000, seed=4)
+    arr = B.pack_segments(segs)
+    tel = synth.grid_telescopes()
+    atm = _atm(True, True)
+    det = B.Detector(n_showers=3, hist=HIST, tel=tel)
+    host = B.propagate_host(segs, atm, det, seed=6, bunch=5)
+    outs = B.DeviceOutputs(det)
+    d_segs = torch.from_numpy(arr.view(np.uint8)).cuda()
+    o = B.cs_opts_default()
+    o.bunch, o.device_ptrs = 5, 1
+    st = B.cs_propagate_ex(C.c_void_p(d_segs.data_ptr()), len(arr), atm.handle, det.handle, 6, o, outs.out,
+                           B.stream_ptr())
+    assert st == B.CS_OK
+    dev = outs.host()
+    for k in ("hist", "tel_counts", "counters"):
+        assert np.array_equal(host[k], dev[k]), k
+    np.testing.assert_allclose(host["tel_time"], dev["tel_time"], rtol=1e-12)
