@@ -641,7 +641,8 @@ def main():
                      "heldout_max": {"displacement_m": sur.stats["max"][0], "delay_s": sur.stats["max"][1],
                                      "transmission": sur.stats["max"][2]},
                      "train_seconds": round(train_s, 2), "train_steps": sur.stats["steps"],
-                     "network": "MLP 3-64-64-64-3 tanh, BF16 weights, FP32 accumulation (mma.sync m16n8k16)"}
+                     "network": "MLP 3-64-64-64-3 tanh, BF16 weights and split BF16 activations, FP32 accumulation in "
+                                "tensor memory (tcgen05.mma M=128 per warpgroup)"}
         sur.close()
 
     e2e = None

@@ -16,7 +16,7 @@
 #include <chrono>
 #include <vector>
 
-#include "mlp_common.cuh"
+#include "mlp_tc.cuh"
 
 struct cs_surrogate {
     float* d_p = nullptr;             // FP32 master parameters
@@ -430,18 +430,40 @@ cs_status alloc(void** p, size_t bytes) {
 // Evaluates the trained network through the photon kernel's warp-level
 // inference path on arbitrary (dz, cos(theta0), 1/lambda_nm) inputs.
 template <bool SPLIT>
-__global__ void eval_kernel(SurrogateView sv, const float4* __restrict__ in, size_t n, float4* __restrict__ out) {
-    const size_t base = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(size_t)31;
-    const size_t i = base + (threadIdx.x & 31);
-    float4 v = i < n ? in[i] : make_float4(0.f, 1.f, 3.0e-3f, 0.f);   // dz, cos(theta0), 1/lambda_nm
-    const float x[3] = {sv.in_scale[0] * height_coordinate(sv, v.x) + sv.in_shift[0],
-                        sv.in_scale[1] * v.y + sv.in_shift[1], sv.in_scale[2] * v.z + sv.in_shift[2]};
-    float y[3];
-    net32<SPLIT>(sv, x, y);
-    if (i < n) {
-        out[i] = make_float4(sv.out_half[0] * y[0] + sv.out_mid[0], sv.out_half[1] * y[1] + sv.out_mid[1],
-                             fminf(expf(sv.out_half[2] * y[2] + sv.out_mid[2]), 1.0f), 0.0f);
+__global__ void __launch_bounds__(256, 1)
+eval_kernel(SurrogateView sv, const float4* __restrict__ in, size_t n, float4* __restrict__ out) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TcSmem& T = *reinterpret_cast<TcSmem*>(smem_raw);
+    tc_setup(T, sv);
+    // every thread of the block takes the same number of 256-row rounds
+    for (size_t base = (size_t)blockIdx.x * 256; base < n; base += (size_t)gridDim.x * 256) {
+        const size_t i = base + threadIdx.x;
+        const float4 v = i < n ? in[i] : make_float4(0.f, 1.f, 3.0e-3f, 0.f);   // dz, cos(theta0), 1/lambda_nm
+        const float x[3] = {sv.in_scale[0] * height_coordinate(sv, v.x) + sv.in_shift[0],
+                            sv.in_scale[1] * v.y + sv.in_shift[1], sv.in_scale[2] * v.z + sv.in_shift[2]};
+        float y[3];
+        net128_tc<SPLIT>(sv, T, x, y);
+        if (i < n) {
+            out[i] = make_float4(sv.out_half[0] * y[0] + sv.out_mid[0], sv.out_half[1] * y[1] + sv.out_mid[1],
+                                 fminf(expf(sv.out_half[2] * y[2] + sv.out_mid[2]), 1.0f), 0.0f);
+        }
     }
+    tc_teardown(T);
+}
+
+// The network on n inputs through the tensor-core path, synchronously;
+// CS_ERR_TIMEOUT if a wait on the tensor cores ran out.
+cs_status run_eval(const SurrogateView& sv, const float4* d_in, size_t n, float4* d_out, cudaStream_t s) {
+    if (n == 0) return CS_OK;
+    const int smem = (int)sizeof(TcSmem);
+    CS_CUDA_TRY(cudaFuncSetAttribute(eval_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(eval_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)device_sm_count());
+    if (sv.split) eval_kernel<true><<<grid, 256, smem, s>>>(sv, d_in, n, d_out);
+    else eval_kernel<false><<<grid, 256, smem, s>>>(sv, d_in, n, d_out);
+    CS_CUDA_TRY(cudaGetLastError());
+    CS_CUDA_TRY(cudaStreamSynchronize(s));
+    return tc_take_timeout() ? CS_ERR_TIMEOUT : CS_OK;
 }
 
 }  // namespace
@@ -676,8 +698,12 @@ extern "C" cs_status cs_surrogate_train(const cs_atmosphere* atm, const cs_surro
     std::vector<float4> hout(nh);
     if (din && dout) {
         cudaMemcpy(din, hin.data(), nh * sizeof(float4), cudaMemcpyHostToDevice);
-        if (sv.split) eval_kernel<true><<<(unsigned)((nh + 127) / 128), 128, 0, s>>>(sv, din, nh, dout);
-        else eval_kernel<false><<<(unsigned)((nh + 127) / 128), 128, 0, s>>>(sv, din, nh, dout);
+        const cs_status ev = run_eval(sv, din, nh, dout, s);
+        if (ev != CS_OK) {
+            cleanup();
+            cs_surrogate_destroy(sg);
+            return ev;
+        }
         cudaMemcpy(hout.data(), dout, nh * sizeof(float4), cudaMemcpyDeviceToHost);
     }
     std::vector<double> er[3];
@@ -719,12 +745,7 @@ extern "C" cs_status cs_surrogate_eval(const cs_surrogate* s, const float* d_in,
                                        void* stream) {
     if (!s || (n && (!d_in || !d_out))) return CS_ERR_INVALID_ARG;
     if (((uintptr_t)d_in & 15) || ((uintptr_t)d_out & 15)) return CS_ERR_INVALID_ARG;
-    if (n == 0) return CS_OK;
-    const unsigned grid = (unsigned)((n + 127) / 128);
-    if (s->view.split) eval_kernel<true><<<grid, 128, 0, (cudaStream_t)stream>>>(s->view, (const float4*)d_in, n, (float4*)d_out);
-    else eval_kernel<false><<<grid, 128, 0, (cudaStream_t)stream>>>(s->view, (const float4*)d_in, n, (float4*)d_out);
-    CS_CUDA_TRY(cudaGetLastError());
-    return CS_OK;
+    return run_eval(s->view, (const float4*)d_in, n, (float4*)d_out, (cudaStream_t)stream);
 }
 
 extern "C" cs_status cs_surrogate_info(const cs_surrogate* s, float* params, size_t n_params, cs_surrogate_stats* st,

@@ -20,7 +20,7 @@
 #include <mutex>
 #include <vector>
 
-#include "mlp_common.cuh"
+#include "mlp_tc.cuh"
 
 namespace cs {
 namespace {
@@ -51,6 +51,10 @@ struct TileSmem {
     int wsum[2][kThreads / 32];   // double-buffered warp sums of the block scans
     int tile;
 };
+
+// The surrogate instances keep the tensor-core network's buffers after the tile.
+constexpr size_t kTcSmemOffset = (sizeof(TileSmem) + 127) & ~(size_t)127;
+constexpr size_t kSmemSurrogate = kTcSmemOffset + sizeof(TcSmem);
 
 // Exclusive block scan with one barrier; `buf` alternates between calls so a
 // scan never overwrites warp sums another warp may still be reading.
@@ -312,12 +316,13 @@ __device__ __forceinline__ void correction_fields(const AtmParams& ap, bool use_
 // filter (Sec. 5.3.4), straight line (Eq. 3.3; on the sphere, the vacuum
 // line to the ground sphere) plus the interpolation-tracing correction
 // (Sec. 4.4.1) or the surrogate network, transmission (Sec. 4.3.1) and
-// detection.  With SURR the whole warp must call (inactive lanes pass
-// active = false): the network runs warp-collectively on the tensor cores.
+// detection.  With SURR the whole warpgroup must call (inactive threads pass
+// active = false): the network runs on the tensor cores for 128 photons.
 template <bool SURR, bool SPH>
 __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool active, long long base,
                                       const PropParams& pp, const AtmParams& ap, const DetParams& dp,
-                                      const OutParams& op, const SurrogateView& sv, Tally& T, bool want_records) {
+                                      const OutParams& op, const SurrogateView& sv, TcSmem* tcs, Tally& T,
+                                      bool want_records) {
     // ---- generation ------------------------------------------------------------
     const float4 Q = S.sub[q];
     const int segk = __float_as_int(Q.w);
@@ -377,8 +382,8 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
                             use_net ? fmaf(sv.in_scale[1], cos_z, sv.in_shift[1]) : 0.0f,
                             use_net ? fmaf(sv.in_scale[2], inv_l, sv.in_shift[2]) : 0.0f};
         float y[3];
-        if (sv.split) net32<true>(sv, x, y);
-        else net32<false>(sv, x, y);
+        if (sv.split) net128_tc<true>(sv, *tcs, x, y);
+        else net128_tc<false>(sv, *tcs, x, y);
 #pragma unroll
         for (int c = 0; c < 3; ++c) net[c] = fmaf(sv.out_half[c], y[c], sv.out_mid[c]);
     }
@@ -558,10 +563,12 @@ template <bool SURR, bool SPH, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB)
 propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, const OutParams op,
                  unsigned int* tile_ctr, const SurrogateView sv) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
+    TcSmem* tcs = SURR ? reinterpret_cast<TcSmem*>(smem_raw + kTcSmemOffset) : nullptr;
     const int t = threadIdx.x;
     const bool want_records = op.records != nullptr;
+    if (SURR) tc_setup(*tcs, sv);
     const long long n_tiles = (pp.n + kTile - 1) / kTile;
     unsigned int emitted = 0, invalid = 0;
     Tally T = {0, 0, 0, 0};
@@ -622,18 +629,22 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                     off += N;
                 }
                 __syncthreads();
-                // whole warps iterate together (the surrogate path is warp-collective)
-                for (int pw = t & ~31; pw < wn; pw += kThreads) {
-                    const int p = pw + (t & 31);
+                // whole warps (warpgroups on the surrogate path, whose network is
+                // warpgroup-collective) iterate together
+                constexpr int kGroup = SURR ? 128 : 32;
+                for (int pw = t & ~(kGroup - 1); pw < wn; pw += kThreads) {
+                    const int p = pw + (t & (kGroup - 1));
                     const bool active = p < wn;
                     const unsigned int e = S.map[active ? p : pw];
                     bunch<SURR, SPH>(S, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), active, base, pp, ap,
-                                     dp, op, sv, T, want_records);
+                                     dp, op, sv, tcs, T, want_records);
                 }
                 __syncthreads();
             }
         }
     }
+
+    if (SURR) tc_teardown(*tcs);
 
     // ---- counter flush: missed = emitted - absorbed - detected.  A thread's
     // emitted bunches and the bunches it propagated are different sets, so the
@@ -667,9 +678,8 @@ bool compatible(const cs_atmosphere* atm, const cs_detector* det) {
 }
 
 cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp, const AtmParams& ap,
-                        const DetParams& dp, const OutParams& op, unsigned int* ctr, const cs_surrogate* sur,
-                        bool sur_one_block) {
-    const size_t smem = sizeof(TileSmem);
+                        const DetParams& dp, const OutParams& op, unsigned int* ctr, const cs_surrogate* sur) {
+    const size_t smem = sur ? kSmemSurrogate : sizeof(TileSmem);
     SurrogateView none;
     memset(&none, 0, sizeof none);
     const SurrogateView& sv = sur ? *surrogate_view(sur) : none;
@@ -677,9 +687,7 @@ cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp
         if (sur) propagate_kernel<true, true, 1><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
         else propagate_kernel<false, true, 4><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
     } else if (sur) {
-        // 1 block per SM: the 255-register instance (no spills); else 2 blocks of 128 registers
-        if (sur_one_block) propagate_kernel<true, false, 1><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
-        else propagate_kernel<true, false, 2><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
+        propagate_kernel<true, false, 1><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
     } else {
         propagate_kernel<false, false, 4><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
     }
@@ -688,16 +696,15 @@ cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp
 }
 
 cs_status set_smem_attributes() {
-    const int smem = (int)sizeof(TileSmem);
+    const int smem = (int)sizeof(TileSmem), smem_sur = (int)kSmemSurrogate;
     CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_sur));
     CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_sur));
     return CS_OK;
 }
 
-int default_blocks_per_sm(const cs_opts& o) { return o.blocks_per_sm > 0 ? o.blocks_per_sm : (o.surrogate ? 2 : 4); }
+int default_blocks_per_sm(const cs_opts& o) { return o.blocks_per_sm > 0 ? o.blocks_per_sm : (o.surrogate ? 1 : 4); }
 
 __global__ void philox_kernel(const uint4* ctr, size_t n, uint32_t k0, uint32_t k1, uint4* out) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -791,7 +798,7 @@ cs_status launch(const cs_segment* d_segs, size_t n, const cs_atmosphere* atm, c
     cs_status st = tile_counter(&ctr);
     if (st != CS_OK) return st;
     CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), stream));
-    return launch_kernel((unsigned)grid, stream, pp, atm->p, det->p, op, ctr, o.surrogate, per_sm <= 1);
+    return launch_kernel((unsigned)grid, stream, pp, atm->p, det->p, op, ctr, o.surrogate);
 }
 
 }  // namespace
@@ -1011,7 +1018,7 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     const long long grid = std::min<long long>(tiles, (long long)device_sm_count() * per_sm);
     // the array keeps the previous call's count: start this call's schedule at zero
     CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), stream));
-    return launch_kernel((unsigned)grid, stream, pp, atm->p, dp, op, ctr, o.surrogate, per_sm <= 1);
+    return launch_kernel((unsigned)grid, stream, pp, atm->p, dp, op, ctr, o.surrogate);
 }
 
 // ---------------------------------------------------------------------------
@@ -1087,7 +1094,7 @@ cs_status enqueue(const cs_segment* segs, size_t n, const cs_atmosphere* atm, co
     op.record_capacity = out->records ? out->record_capacity : 0;
     op.record_count = (unsigned long long*)out->record_count;
     CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), stream));
-    return launch_kernel(grid, stream, pp, atm->p, dp, op, ctr, o.surrogate, default_blocks_per_sm(o) <= 1);
+    return launch_kernel(grid, stream, pp, atm->p, dp, op, ctr, o.surrogate);
 }
 
 cs_status upload_bunches(const cs_detector* det, const int* shower_bunch, int** d_bunch) {
