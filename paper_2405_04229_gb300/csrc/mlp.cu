@@ -433,7 +433,7 @@ template <bool SPLIT>
 __global__ void __launch_bounds__(256, 1)
 eval_kernel(SurrogateView sv, const float4* __restrict__ in, size_t n, float4* __restrict__ out) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    TcSmem& T = *reinterpret_cast<TcSmem*>(smem_raw);
+    TcSmem<2>& T = *reinterpret_cast<TcSmem<2>*>(smem_raw);
     tc_setup(T, sv);
     // every thread of the block takes the same number of 256-row rounds
     for (size_t base = (size_t)blockIdx.x * 256; base < n; base += (size_t)gridDim.x * 256) {
@@ -455,7 +455,7 @@ eval_kernel(SurrogateView sv, const float4* __restrict__ in, size_t n, float4* _
 // CS_ERR_TIMEOUT if a wait on the tensor cores ran out.
 cs_status run_eval(const SurrogateView& sv, const float4* d_in, size_t n, float4* d_out, cudaStream_t s) {
     if (n == 0) return CS_OK;
-    const int smem = (int)sizeof(TcSmem);
+    const int smem = (int)sizeof(TcSmem<2>);
     CS_CUDA_TRY(cudaFuncSetAttribute(eval_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     CS_CUDA_TRY(cudaFuncSetAttribute(eval_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)device_sm_count());

@@ -17,17 +17,23 @@ constexpr int kTcATile = kTcRows * kHid * 2;         // one BF16 A tile: 16 KB
 constexpr int kTcW2 = 0, kTcW3 = kHid * kHid * 2, kTcW4 = 2 * kHid * kHid * 2;
 constexpr int kTcN4 = 16;                            // output layer padded to the smallest MMA width
 constexpr int kTcWBytes = kTcW4 + kTcN4 * kHid * 2;  // W2 | W3 | W4: 18 KB
-constexpr int kTcCols = 128;                         // tensor-memory columns per CTA: 64 per warpgroup
 constexpr int kTcSpin = 1 << 20;                     // polls of an MMA completion before giving up
 
-// Shared memory of the tensor-core network, per CTA of two warpgroups.
+// Shared memory of the tensor-core network, per CTA of NWG warpgroups; the
+// CTA holds NWG x 64 tensor-memory columns (64 FP32 accumulators per row).
+template <int NWG>
 struct TcSmem {
-    __align__(128) unsigned char a[2][2][kTcATile];  // [warpgroup][hi, lo] activations
-    __align__(128) unsigned char w[kTcWBytes];       // BF16 weights, core-matrix layout
-    unsigned long long mbar[2];                      // MMA completion, per warpgroup
+    static_assert(NWG == 2 || NWG == 4, "tensor-memory allocations are powers of two >= 32 columns");
+    static constexpr unsigned int kCols = 64 * NWG;
+    __align__(128) unsigned char a[NWG][2][kTcATile];  // [warpgroup][hi, lo] activations
+    __align__(128) unsigned char w[kTcWBytes];         // BF16 weights, core-matrix layout
+    float4 w1b[kHid];                                  // layer 1: {W1[u][0..2], b1[u]}
+    float4 b23[2][kHid / 4];                           // biases of layers 2 and 3
+    float b4[4];
+    unsigned long long mbar[NWG];                      // MMA completion, per warpgroup
     unsigned int tmem_base;
-    int abort[2];                                    // a wait ran out (per warpgroup)
-    unsigned int phase[2];                           // parity of the next completion
+    int abort[NWG];                                    // a wait ran out (per warpgroup)
+    unsigned int phase[NWG];                           // parity of the next completion
 };
 
 // Set when a tensor-core wait ran out (one flag per translation unit); read
@@ -141,20 +147,22 @@ __device__ __forceinline__ void tc_store8(unsigned char* a_hi, unsigned char* a_
 }
 
 // Per-CTA set-up (all threads): tensor memory, completion barriers, weights.
-__device__ __forceinline__ void tc_setup(TcSmem& T, const SurrogateView& sv) {
+template <int NWG>
+__device__ __forceinline__ void tc_setup(TcSmem<NWG>& T, const SurrogateView& sv) {
     const int t = threadIdx.x;
     if (t < 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&T.tmem_base)),
-                     "r"((uint32_t)kTcCols)
+                     "r"(TcSmem<NWG>::kCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (t == 0) {
-        mbar_init(smem_u32(&T.mbar[0]), 1);
-        mbar_init(smem_u32(&T.mbar[1]), 1);
+        for (int wg = 0; wg < NWG; ++wg) {
+            mbar_init(smem_u32(&T.mbar[wg]), 1);
+            T.abort[wg] = 0;
+            T.phase[wg] = 0;
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        T.abort[0] = T.abort[1] = 0;
-        T.phase[0] = T.phase[1] = 0;
     }
     // weights: global [n][k] rows of 64 BF16 -> core-matrix layout, 16 bytes at a time
     const uint4* src = reinterpret_cast<const uint4*>(sv.wb);
@@ -175,6 +183,12 @@ __device__ __forceinline__ void tc_setup(TcSmem& T, const SurrogateView& sv) {
         }
         *reinterpret_cast<uint4*>(T.w + dst) = v;
     }
+    const float* p = sv.p;
+    for (int u = t; u < kHid; u += blockDim.x)
+        T.w1b[u] = make_float4(p[kOffW1 + 3 * u], p[kOffW1 + 3 * u + 1], p[kOffW1 + 3 * u + 2], p[kOffB1 + u]);
+    for (int i = t; i < 2 * kHid; i += blockDim.x)
+        reinterpret_cast<float*>(T.b23)[i] = p[(i < kHid ? kOffB2 : kOffB3 - kHid) + i];
+    if (t < 4) T.b4[t] = t < kNOut ? p[kOffB4 + t] : 0.0f;
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -183,11 +197,12 @@ __device__ __forceinline__ void tc_setup(TcSmem& T, const SurrogateView& sv) {
 
 // Per-CTA tear-down (all threads): after a wait that ran out, give the
 // outstanding MMAs a bounded chance to finish; then free the tensor memory.
-__device__ __forceinline__ void tc_teardown(TcSmem& T) {
+template <int NWG>
+__device__ __forceinline__ void tc_teardown(TcSmem<NWG>& T) {
     tc_fence_before();
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int wg = 0; wg < 2; ++wg)
+        for (int wg = 0; wg < NWG; ++wg)
             if (T.abort[wg]) {
                 mbar_wait_bounded(smem_u32(&T.mbar[wg]), T.phase[wg]);
                 atomicOr(&g_tc_timeout, 1u);
@@ -196,7 +211,8 @@ __device__ __forceinline__ void tc_teardown(TcSmem& T) {
     __syncthreads();
     if (threadIdx.x < 32) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(T.tmem_base), "r"((uint32_t)kTcCols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(T.tmem_base),
+                     "r"(TcSmem<NWG>::kCols)
                      : "memory");
     }
 }
@@ -205,24 +221,21 @@ __device__ __forceinline__ void tc_teardown(TcSmem& T) {
 // warpgroup): normalised inputs x in, normalised outputs y out.  All 128
 // threads of the warpgroup call it together.  Returns false (outputs zero)
 // once a wait of this warpgroup has run out.
-template <bool SPLIT>
-__device__ __forceinline__ bool net128_tc(const SurrogateView& sv, TcSmem& T, const float (&x)[3], float (&y)[3]) {
-    const int wg = (threadIdx.x >> 7) & 1, row = threadIdx.x & 127;
+template <bool SPLIT, int NWG>
+__device__ __forceinline__ bool net128_tc(const SurrogateView& sv, TcSmem<NWG>& T, const float (&x)[3], float (&y)[3]) {
+    const int wg = threadIdx.x >> 7, row = threadIdx.x & 127;
     y[0] = y[1] = y[2] = 0.0f;
     if (T.abort[wg]) return false;   // uniform: set before one of this warpgroup's barriers
     unsigned char* a_hi = T.a[wg][0];
     unsigned char* a_lo = T.a[wg][1];
-    const float* p = sv.p;
     // layer 1 (3 inputs): FP32 on the CUDA cores
 #pragma unroll 1
     for (int g = 0; g < 8; ++g) {
         float h[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const int u = 8 * g + j;
-            h[j] = tanh_act(fmaf(__ldg(p + kOffW1 + 3 * u + 2), x[2],
-                                 fmaf(__ldg(p + kOffW1 + 3 * u + 1), x[1],
-                                      fmaf(__ldg(p + kOffW1 + 3 * u), x[0], __ldg(p + kOffB1 + u)))));
+            const float4 w = T.w1b[8 * g + j];
+            h[j] = tanh_act(fmaf(w.z, x[2], fmaf(w.y, x[1], fmaf(w.x, x[0], w.w))));
         }
         tc_store8<SPLIT>(a_hi, a_lo, row, g, h);
     }
@@ -256,16 +269,23 @@ __device__ __forceinline__ bool net128_tc(const SurrogateView& sv, TcSmem& T, co
         if (T.abort[wg]) return false;
         tc_fence_after();
         if (L < 2) {
-            const float* bias = p + (L == 0 ? kOffB2 : kOffB3);
+            const float4* bias = T.b23[L];
 #pragma unroll 1
             for (int c = 0; c < kHid / 16; ++c) {
                 float v[16];
                 tc_ld16(t_lane + (uint32_t)(16 * c), v);
                 float h0[8], h1[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    h0[j] = tanh_act(v[j] + __ldg(bias + 16 * c + j));
-                    h1[j] = tanh_act(v[8 + j] + __ldg(bias + 16 * c + 8 + j));
+                for (int q = 0; q < 2; ++q) {
+                    const float4 b0 = bias[4 * c + q], b1 = bias[4 * c + 2 + q];
+                    h0[4 * q + 0] = tanh_act(v[4 * q + 0] + b0.x);
+                    h0[4 * q + 1] = tanh_act(v[4 * q + 1] + b0.y);
+                    h0[4 * q + 2] = tanh_act(v[4 * q + 2] + b0.z);
+                    h0[4 * q + 3] = tanh_act(v[4 * q + 3] + b0.w);
+                    h1[4 * q + 0] = tanh_act(v[8 + 4 * q + 0] + b1.x);
+                    h1[4 * q + 1] = tanh_act(v[8 + 4 * q + 1] + b1.y);
+                    h1[4 * q + 2] = tanh_act(v[8 + 4 * q + 2] + b1.z);
+                    h1[4 * q + 3] = tanh_act(v[8 + 4 * q + 3] + b1.w);
                 }
                 tc_store8<SPLIT>(a_hi, a_lo, row, 2 * c, h0);
                 tc_store8<SPLIT>(a_hi, a_lo, row, 2 * c + 1, h1);
@@ -274,7 +294,7 @@ __device__ __forceinline__ bool net128_tc(const SurrogateView& sv, TcSmem& T, co
             float v[4];
             tc_ld4(t_lane, v);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) y[k] = v[k] + __ldg(p + kOffB4 + k);
+            for (int k = 0; k < 3; ++k) y[k] = v[k] + T.b4[k];
         }
     }
     tc_fence_before();   // these accumulator reads precede the next call's MMAs (its barrier)

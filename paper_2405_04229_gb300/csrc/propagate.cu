@@ -25,8 +25,10 @@
 namespace cs {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kTile = 256;              // segments per tile, one per thread
+constexpr int kThreads = 256;           // exact tracer: threads per block
+constexpr int kThreadsSur = 512;        // surrogate: four warpgroups per block
+constexpr int kMaxThreads = 512;
+constexpr int kTile = 256;              // segments per tile, one per thread (the first kTile threads)
 constexpr int kSubCap = 512;            // sub-steps per round
 constexpr int kMapCap = 2048;           // bunches per window of the bunch -> sub-step map
 constexpr int kKShift = 8;              // sub-step record: segment (8 bits) | k << 8
@@ -48,17 +50,18 @@ struct TileSmem {
     float4 sub[kSubCap];  // cos(theta), sin(theta), n - 1, segment | k << 8
     int nsub_ph[kSubCap]; // bunches of each sub-step
     unsigned int map[kMapCap];
-    int wsum[2][kThreads / 32];   // double-buffered warp sums of the block scans
+    int wsum[2][kMaxThreads / 32];   // double-buffered warp sums of the block scans
     int tile;
 };
 
 // The surrogate instances keep the tensor-core network's buffers after the tile.
 constexpr size_t kTcSmemOffset = (sizeof(TileSmem) + 127) & ~(size_t)127;
-constexpr size_t kSmemSurrogate = kTcSmemOffset + sizeof(TcSmem);
+constexpr size_t kSmemSurrogate = kTcSmemOffset + sizeof(TcSmem<kThreadsSur / 128>);
 
 // Exclusive block scan with one barrier; `buf` alternates between calls so a
 // scan never overwrites warp sums another warp may still be reading.
-__device__ __forceinline__ int block_scan(int v, int (*wsum)[kThreads / 32], int& buf, int* total) {
+template <int NT>
+__device__ __forceinline__ int block_scan(int v, int (*wsum)[kMaxThreads / 32], int& buf, int* total) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int x = v;
 #pragma unroll
@@ -72,7 +75,7 @@ __device__ __forceinline__ int block_scan(int v, int (*wsum)[kThreads / 32], int
     __syncthreads();
     int pre = 0, tot = 0;
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) {
+    for (int w = 0; w < NT / 32; ++w) {
         const int s = ws[w];
         pre += w < wid ? s : 0;
         tot += s;
@@ -321,8 +324,8 @@ __device__ __forceinline__ void correction_fields(const AtmParams& ap, bool use_
 template <bool SURR, bool SPH>
 __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool active, long long base,
                                       const PropParams& pp, const AtmParams& ap, const DetParams& dp,
-                                      const OutParams& op, const SurrogateView& sv, TcSmem* tcs, Tally& T,
-                                      bool want_records) {
+                                      const OutParams& op, const SurrogateView& sv, TcSmem<kThreadsSur / 128>* tcs,
+                                      Tally& T, bool want_records) {
     // ---- generation ------------------------------------------------------------
     const float4 Q = S.sub[q];
     const int segk = __float_as_int(Q.w);
@@ -559,13 +562,13 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
     if (want_records) emit_record(op, gid, k, i, x, y, t_rel, inv_l, tel, bin, status);
 }
 
-template <bool SURR, bool SPH, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB)
+template <bool SURR, bool SPH, int MINB, int NT = SURR ? kThreadsSur : kThreads>
+__global__ void __launch_bounds__(NT, MINB)
 propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, const OutParams op,
                  unsigned int* tile_ctr, const SurrogateView sv) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
-    TcSmem* tcs = SURR ? reinterpret_cast<TcSmem*>(smem_raw + kTcSmemOffset) : nullptr;
+    TcSmem<kThreadsSur / 128>* tcs = SURR ? reinterpret_cast<TcSmem<kThreadsSur / 128>*>(smem_raw + kTcSmemOffset) : nullptr;
     const int t = threadIdx.x;
     const bool want_records = op.records != nullptr;
     if (SURR) tc_setup(*tcs, sv);
@@ -583,17 +586,17 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
         const long long base = tile * kTile;
 
         // ---- stage 1: import and filter (one segment per thread) -------------
-        const int Kt = base + t < pp.n ? import_segment<SPH>(S, t, pp.segs + base + t, pp, ap, dp, invalid) : 0;
+        const int Kt = (t < kTile && base + t < pp.n) ? import_segment<SPH>(S, t, pp.segs + base + t, pp, ap, dp, invalid) : 0;
         int S_tot;
-        const int offk = block_scan(Kt, S.wsum, buf, &S_tot);
-        S.offK[t] = offk;
-        if (t == kThreads - 1) S.offK[kTile] = S_tot;
+        const int offk = block_scan<NT>(Kt, S.wsum, buf, &S_tot);
+        if (t < kTile) S.offK[t] = offk;
+        if (t == 0) S.offK[kTile] = S_tot;
         __syncthreads();
 
         for (int sub0 = 0; sub0 < S_tot; sub0 += kSubCap) {
             const int nsub = min(kSubCap, S_tot - sub0);
             // ---- stage 2: sub-step yields, a balanced run [q0, q1) per thread ---
-            const int per = (nsub + kThreads - 1) / kThreads;
+            const int per = (nsub + NT - 1) / NT;
             const int q0 = min(t * per, nsub), q1 = min(q0 + per, nsub);
             int my_ph = 0;
             unsigned int my_emit = 0;
@@ -615,7 +618,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                 }
             }
             int M;
-            const int ph0 = block_scan(my_ph, S.wsum, buf, &M);
+            const int ph0 = block_scan<NT>(my_ph, S.wsum, buf, &M);
             emitted += my_emit;
 
             // ---- stages 3-5 over windows of the bunch map ------------------------
@@ -632,7 +635,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                 // whole warps (warpgroups on the surrogate path, whose network is
                 // warpgroup-collective) iterate together
                 constexpr int kGroup = SURR ? 128 : 32;
-                for (int pw = t & ~(kGroup - 1); pw < wn; pw += kThreads) {
+                for (int pw = t & ~(kGroup - 1); pw < wn; pw += NT) {
                     const int p = pw + (t & (kGroup - 1));
                     const bool active = p < wn;
                     const unsigned int e = S.map[active ? p : pw];
@@ -684,10 +687,10 @@ cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp
     memset(&none, 0, sizeof none);
     const SurrogateView& sv = sur ? *surrogate_view(sur) : none;
     if (ap.spherical) {
-        if (sur) propagate_kernel<true, true, 1><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
+        if (sur) propagate_kernel<true, true, 1><<<grid, kThreadsSur, smem, stream>>>(pp, ap, dp, op, ctr, sv);
         else propagate_kernel<false, true, 4><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
     } else if (sur) {
-        propagate_kernel<true, false, 1><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
+        propagate_kernel<true, false, 1><<<grid, kThreadsSur, smem, stream>>>(pp, ap, dp, op, ctr, sv);
     } else {
         propagate_kernel<false, false, 4><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
     }
