@@ -235,6 +235,14 @@ struct Tally {
     unsigned int absorbed, hist, tel, upward;
 };
 
+// Histogram count: one 64-bit atomic per bunch.  (Warp aggregation -- lanes
+// adding to the same cell combining first -- measured 3 % slower: a warp's
+// bunches come from cones whose ground rings spread over hundreds of 1 m
+// cells, so lanes rarely share one.)
+__device__ __forceinline__ void hist_add(const OutParams& op, unsigned int key, unsigned int b) {
+    atomicAdd(op.hist + key, (unsigned long long)b);
+}
+
 // Telescopes: the sphere whose centre is closest to the arrival line, if
 // closer than its radius (ties: lowest index).  Arrivals within the hash's
 // zenith range (`hashed`; the caller has checked the box of all reach discs)
@@ -435,7 +443,7 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
                 const int iy = (int)floorf(D.z + fmaf(ry, dp.inv_dy, D.w));
                 if (ix >= 0 && ix < dp.nx && iy >= 0 && iy < dp.ny) {
                     bin = iy * dp.nx + ix;
-                    atomicAdd(op.hist + ((size_t)sh * dp.ny * dp.nx + bin), (unsigned long long)b);
+                    hist_add(op, (unsigned int)(sh * dp.ny * dp.nx + bin), b);
                 }
             }
             if (dp.n_tel > 0) {
@@ -519,7 +527,7 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
                 const int iy = (int)floorf(((y - dp.hy0_hi) - dp.hy0_lo) * dp.inv_dy);
                 if (ix >= 0 && ix < dp.nx && iy >= 0 && iy < dp.ny) {
                     bin = iy * dp.nx + ix;
-                    atomicAdd(op.hist + ((size_t)sh * dp.ny * dp.nx + bin), (unsigned long long)b);
+                    hist_add(op, (unsigned int)(sh * dp.ny * dp.nx + bin), b);
                 }
             }
             if (dp.n_tel > 0) {
