@@ -183,3 +183,29 @@ def test_spherical_steep_arrivals_beyond_the_telescope_hash():
     st = PU.compare(g, o, bunch=1)
     assert st["matched"] > 100000
     assert int(g["counters"][B.CS_CNT_TEL]) > 5000
+
+
+def test_spherical_surrogate_against_exact_tracer():
+    """The network trained on the spherical shell's exact fields (local zenith)
+    replaces the tables photon by photon within its stated bars."""
+    atm = _atm(True, True)
+    sur = B.Surrogate(atm)
+    s = sur.stats
+    assert s["p99"][0] <= 0.01 and s["p99"][1] <= 0.1e-9 and s["p99"][2] <= 1e-3, s
+    segs = synth.shower_segments(1500, 60.0, 30.0, 1e13, seed=21)
+    det = B.Detector(hist=HIST, tel=_tel(), spherical=True)
+    ex = B.propagate_host(segs, atm, det, seed=2, bunch=5, records=True)
+    sg = B.propagate_host(segs, atm, det, seed=2, bunch=5, records=True, surrogate=sur)
+    ke = PU._key(ex["records"]["seg"], ex["records"]["k"], ex["records"]["i"])
+    ks = PU._key(sg["records"]["seg"], sg["records"]["k"], sg["records"]["i"])
+    e, g = ex["records"][np.argsort(ke)], sg["records"][np.argsort(ks)]
+    assert np.array_equal(np.sort(ke), np.sort(ks))
+    both = (e["status"] == 0) & (g["status"] == 0)
+    assert both.sum() > 2000
+    dpos = np.hypot(e["x"][both] - g["x"][both], e["y"][both] - g["y"][both])
+    dt = np.abs(e["dt_ns"][both] - g["dt_ns"][both]) * 1e-9
+    # the network's bars plus the FP32 resolution of ~50 km paths
+    assert np.percentile(dpos, 99) <= 1.42 * 0.01 + BAND_POS and dpos.max() <= 1.42 * 0.06 + BAND_POS
+    assert np.percentile(dt, 99) <= 0.1e-9 + 1e-5 * 2e-4 and dt.max() <= 0.4e-9 + 1e-5 * 2e-4
+    assert (e["status"] != g["status"]).sum() <= 0.01 * len(e)
+    sur.close()
