@@ -329,11 +329,11 @@ __device__ __forceinline__ void correction_fields(const AtmParams& ap, bool use_
 // (Sec. 4.4.1) or the surrogate network, transmission (Sec. 4.3.1) and
 // detection.  With SURR the whole warpgroup must call (inactive threads pass
 // active = false): the network runs on the tensor cores for 128 photons.
-template <bool SURR, bool SPH>
+template <bool SURR, bool SPH, bool REC>
 __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool active, long long base,
                                       const PropParams& pp, const AtmParams& ap, const DetParams& dp,
                                       const OutParams& op, const SurrogateView& sv, TcSmem<kThreadsSur / 128>* tcs,
-                                      Tally& T, bool want_records) {
+                                      Tally& T) {
     // ---- generation ------------------------------------------------------------
     const float4 Q = S.sub[q];
     const int segk = __float_as_int(Q.w);
@@ -426,12 +426,15 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
         }
         t_rel = fmaf(path, kInvC, t_rel);
         const float4 Cg = S.segC[sg];
-        {
+        if (REC) {   // records carry the ground point to FP32 precision
             float s, e;
             two_sum(Cg.x, rx, s, e);
             x = s + (e + Cg.y);
             two_sum(Cg.z, ry, s, e);
             y = s + (e + Cg.w);
+        } else {     // the telescope hash only needs its cell
+            x = Cg.x + (Cg.y + rx);
+            y = Cg.z + (Cg.w + ry);
         }
         if (ap.transmission && !(u3 < Tr)) {
             status = CS_ST_ABSORBED;
@@ -567,10 +570,10 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
     T.upward += status == CS_ST_UPWARD ? b : 0;
     T.hist += bin >= 0 ? b : 0;
     T.tel += tel >= 0 ? b : 0;
-    if (want_records) emit_record(op, gid, k, i, x, y, t_rel, inv_l, tel, bin, status);
+    if (REC) emit_record(op, gid, k, i, x, y, t_rel, inv_l, tel, bin, status);
 }
 
-template <bool SURR, bool SPH, int MINB, int NT = SURR ? kThreadsSur : kThreads>
+template <bool SURR, bool SPH, int MINB, bool REC, int NT = SURR ? kThreadsSur : kThreads>
 __global__ void __launch_bounds__(NT, MINB)
 propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, const OutParams op,
                  unsigned int* tile_ctr, const SurrogateView sv) {
@@ -578,7 +581,6 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
     TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
     TcSmem<kThreadsSur / 128>* tcs = SURR ? reinterpret_cast<TcSmem<kThreadsSur / 128>*>(smem_raw + kTcSmemOffset) : nullptr;
     const int t = threadIdx.x;
-    const bool want_records = op.records != nullptr;
     if (SURR) tc_setup(*tcs, sv);
     const long long n_tiles = (pp.n + kTile - 1) / kTile;
     unsigned int emitted = 0, invalid = 0;
@@ -647,8 +649,8 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                     const int p = pw + (t & (kGroup - 1));
                     const bool active = p < wn;
                     const unsigned int e = S.map[active ? p : pw];
-                    bunch<SURR, SPH>(S, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), active, base, pp, ap,
-                                     dp, op, sv, tcs, T, want_records);
+                    bunch<SURR, SPH, REC>(S, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), active, base, pp,
+                                          ap, dp, op, sv, tcs, T);
                 }
                 __syncthreads();
             }
@@ -694,13 +696,16 @@ cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp
     SurrogateView none;
     memset(&none, 0, sizeof none);
     const SurrogateView& sv = sur ? *surrogate_view(sur) : none;
+    // instances: (network or tables) x (sphere or plane) x (records or throughput)
+    auto go = [&](auto kernel, int threads) { kernel<<<grid, threads, smem, stream>>>(pp, ap, dp, op, ctr, sv); };
+    const bool rec = op.records != nullptr;
     if (ap.spherical) {
-        if (sur) propagate_kernel<true, true, 1><<<grid, kThreadsSur, smem, stream>>>(pp, ap, dp, op, ctr, sv);
-        else propagate_kernel<false, true, 4><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
+        if (sur) rec ? go(propagate_kernel<true, true, 1, true>, kThreadsSur) : go(propagate_kernel<true, true, 1, false>, kThreadsSur);
+        else rec ? go(propagate_kernel<false, true, 4, true>, kThreads) : go(propagate_kernel<false, true, 4, false>, kThreads);
     } else if (sur) {
-        propagate_kernel<true, false, 1><<<grid, kThreadsSur, smem, stream>>>(pp, ap, dp, op, ctr, sv);
+        rec ? go(propagate_kernel<true, false, 1, true>, kThreadsSur) : go(propagate_kernel<true, false, 1, false>, kThreadsSur);
     } else {
-        propagate_kernel<false, false, 4><<<grid, kThreads, smem, stream>>>(pp, ap, dp, op, ctr, sv);
+        rec ? go(propagate_kernel<false, false, 4, true>, kThreads) : go(propagate_kernel<false, false, 4, false>, kThreads);
     }
     CS_CUDA_TRY(cudaGetLastError());
     return CS_OK;
@@ -708,10 +713,15 @@ cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp
 
 cs_status set_smem_attributes() {
     const int smem = (int)sizeof(TileSmem), smem_sur = (int)kSmemSurrogate;
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_sur));
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_sur));
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, false, 4, false>, attr, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, false, 4, true>, attr, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, true, 4, false>, attr, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, true, 4, true>, attr, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, false, 1, false>, attr, smem_sur));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, false, 1, true>, attr, smem_sur));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, true, 1, false>, attr, smem_sur));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, true, 1, true>, attr, smem_sur));
     return CS_OK;
 }
 
