@@ -201,6 +201,49 @@ def cpu_baseline_entry(segs, tel, hist):
             "single_core": {"value": rate1, "sample": sample1}, "cpu_model": cpu_model()}
 
 
+def cpu_baseline_sampled(segs, tel, hist, shower_bunch, budget_s=12.0, chunk=200, seed=0):
+    """The oracle on all host cores over seeded random chunks of an uneven batch
+    (each chunk with its shower's bunch size); photons/s of the sample."""
+    import concurrent.futures as cf
+
+    import oracle
+    from paper_2405_04229_gb300 import synth
+    atm = oracle.make_atm(oracle.ATM_LAYERED, layered=synth.US_STANDARD)
+    n = len(segs["z0"])
+    n_showers = int(segs["shower_id"].max()) + 1
+    rng = np.random.default_rng([seed, 0xC9])
+    starts = iter(rng.integers(0, max(1, n - chunk), 100000))
+    threads = os.cpu_count() or 1
+    photons, done = 0, 0
+    t0 = time.perf_counter()
+
+    def work(st):
+        sl = slice(int(st), min(int(st) + chunk, n))
+        sub = synth.take(segs, sl)
+        # one shower per call: the chunk's first shower and its bunch size
+        sid = sub["shower_id"] == sub["shower_id"][0]
+        sub = synth.take(sub, sid)
+        b = int(shower_bunch[int(sub["shower_id"][0])])
+        r = oracle.propagate(sub, atm, hist=hist, tel=tel, bunch=b, refraction=True, transmission=True, seed=seed,
+                             seg_base=int(st), n_showers=n_showers, records=False)
+        return int(r["counters"][0]), len(sub["z0"])
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        futs = {ex.submit(work, next(starts)) for _ in range(threads)}
+        while futs:
+            fin, futs = cf.wait(futs, return_when=cf.FIRST_COMPLETED)
+            for f in fin:
+                p, s_ = f.result()
+                photons += p
+                done += s_
+            if time.perf_counter() - t0 < budget_s:
+                for _ in fin:
+                    futs.add(ex.submit(work, next(starts)))
+    dt = time.perf_counter() - t0
+    return {"value": photons / dt, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": "%d segments in seeded random %d-segment chunks of the batch, %.1f s" % (done, chunk, dt)}
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -230,6 +273,7 @@ def run_batched(args):
     t0 = time.perf_counter()
     segs, counts = synth.uneven_showers(n_showers=64, seed=args.seed)
     gen_s = time.perf_counter() - t0
+    segs_all = segs
     n = len(segs["z0"])
     tel = synth.grid_telescopes(nx=20, ny=20, pitch=100.0)
     atm = B.Atmosphere(layered=synth.US_STANDARD, refraction=True, transmission=True)
@@ -264,6 +308,9 @@ def run_batched(args):
     B.cs_batch_destroy(batch)
     h = outs.host()
     per_shower_bunch = {int(b): int((sb == b).sum()) for b in np.unique(sb)}
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline_sampled(segs_all, tel, synth.histogram_400(), sb)
     line = {"metric": METRIC, "value": photons * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -272,7 +319,8 @@ def run_batched(args):
                        "segments": n, "photons_per_step": photons, "bunch_sizes": per_shower_bunch,
                        "blocks_per_sm": tune.blocks_per_sm, "tiling_ms": [round(tune.ms[i], 3) for i in range(4)],
                        "generation_s": round(gen_s, 1), "l2": "inputs (%.1f GB) larger than L2" % (arr.nbytes / 1e9)},
-            "counters": [int(x) for x in h["counters"]], "gpu_launches": args.steps, "clocks": clk.summary()}
+            "counters": [int(x) for x in h["counters"]], "cpu_baseline": cpu, "gpu_launches": args.steps,
+            "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 
