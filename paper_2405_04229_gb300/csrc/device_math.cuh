@@ -19,8 +19,10 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
             k0 += 0x9E3779B9u;
             k1 += 0xBB67AE85u;
         }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        // one 32 x 32 -> 64 multiply each (a single wide integer multiply-add)
+        const unsigned long long p0 = 0xD2511F53ull * c0, p1 = 0xCD9E8D57ull * c2;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
         const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
         c0 = n0;
         c1 = lo1;
@@ -112,14 +114,14 @@ __device__ __forceinline__ void sincos_2pi(float u, float& s, float& c) {
     const float q = rintf(v);
     const float x = (v - q) * 1.57079632679489662f;   // |x| <= pi/4
     const float x2 = x * x;
-    float sp = fmaf(x2, 2.75573192e-6f, -1.98412698e-4f);   //  1/9!, -1/7!
-    sp = fmaf(x2, sp, 8.33333333e-3f);                      //  1/5!
-    sp = fmaf(x2, sp, -1.66666667e-1f);                     // -1/3!
-    const float sx = fmaf(x * x2, sp, x);
-    float cp = fmaf(x2, 2.48015873e-5f, -1.38888889e-3f);   //  1/8!, -1/6!
-    cp = fmaf(x2, cp, 4.16666667e-2f);                      //  1/4!
-    cp = fmaf(x2, cp, -0.5f);                               // -1/2!
-    const float cx = fmaf(x2, cp, 1.0f);
+    // the sine (odd) and cosine (even) Horner chains side by side, two lanes per
+    // packed FP32 instruction: (1/9!, 1/8!), (-1/7!, -1/6!), (1/5!, 1/4!), (-1/3!, -1/2!)
+    const float2 xx = make_float2(x2, x2);
+    float2 p = __ffma2_rn(xx, make_float2(2.75573192e-6f, 2.48015873e-5f), make_float2(-1.98412698e-4f, -1.38888889e-3f));
+    p = __ffma2_rn(xx, p, make_float2(8.33333333e-3f, 4.16666667e-2f));
+    p = __ffma2_rn(xx, p, make_float2(-1.66666667e-1f, -0.5f));
+    const float2 r = __ffma2_rn(make_float2(x * x2, x2), p, make_float2(x, 1.0f));
+    const float sx = r.x, cx = r.y;
     const int qi = ((int)q) & 3;
     s = (qi == 0) ? sx : (qi == 1) ? cx : (qi == 2) ? -sx : -cx;
     c = (qi == 0) ? cx : (qi == 1) ? -sx : (qi == 2) ? -cx : sx;

@@ -309,11 +309,16 @@ __device__ __forceinline__ void correction_fields(const AtmParams& ap, bool use_
         const float4* row = ap.tv.tab + ((size_t)j * ap.tv.nw + m) * 2;
         const float4 v0 = __ldg(row), s0 = __ldg(row + 1), v1 = __ldg(row + 2), s1 = __ldg(row + 3);
         const float a0 = 1.0f - gm;
-        GR = a0 * fmaf(fj, s0.x, v0.x) + gm * fmaf(fj, s1.x, v1.x);
-        Gt = a0 * fmaf(fj, s0.y, v0.y) + gm * fmaf(fj, s1.y, v1.y);
+        // value + fj * change at both columns, then the column weights; two fields per packed instruction
+        const float2 ff = make_float2(fj, fj), aa = make_float2(a0, a0), gg = make_float2(gm, gm);
+        const float2 rt = __ffma2_rn(aa, __ffma2_rn(ff, make_float2(s0.x, s0.y), make_float2(v0.x, v0.y)),
+                                     __fmul2_rn(gg, __ffma2_rn(ff, make_float2(s1.x, s1.y), make_float2(v1.x, v1.y))));
+        GR = rt.x;
+        Gt = rt.y;
         if (ap.transmission) {
-            const float GX = a0 * fmaf(fj, s0.z, v0.z) + gm * fmaf(fj, s1.z, v1.z);
-            const float GA = a0 * fmaf(fj, s0.w, v0.w) + gm * fmaf(fj, s1.w, v1.w);
+            const float2 xa = __ffma2_rn(aa, __ffma2_rn(ff, make_float2(s0.z, s0.w), make_float2(v0.z, v0.w)),
+                                         __fmul2_rn(gg, __ffma2_rn(ff, make_float2(s1.z, s1.w), make_float2(v1.z, v1.w))));
+            const float GX = xa.x, GA = xa.y;
             const float il2 = inv_l * inv_l;
             const float kR = ap.kR0 * il2 * il2;
             const float kA = ap.kA0 * ex2_approx(ap.aer_alpha * lg2_approx(ap.lamA_nm * inv_l));
@@ -352,9 +357,12 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
     sincos_2pi(u1, sphi, cphi);
     const float inv_l = ap.inv_l1_nm - u2 * ap.dinv_l_nm;   // 1/lambda^2 spectrum
     const float ce = (Px * cphi + Py * sphi) * A.w;
-    const float mx = Px * ce - cphi, my = Py * ce - sphi, mz = (Pz - 1.0f) * ce;
     const float ct = Q.x, st = Q.y;
-    const float ux = ct * Px + st * mx, uy = ct * Py + st * my, uz = ct * Pz + st * mz;
+    // x and y components two lanes per packed FP32 instruction
+    const float2 mxy = __ffma2_rn(make_float2(Px, Py), make_float2(ce, ce), make_float2(-cphi, -sphi));
+    const float mz = (Pz - 1.0f) * ce;
+    const float2 uxy = __ffma2_rn(make_float2(ct, ct), make_float2(Px, Py), __fmul2_rn(make_float2(st, st), mxy));
+    const float ux = uxy.x, uy = uxy.y, uz = ct * Pz + st * mz;
     // height above the observation level and the local zenith
     float dz, cos_z, sin2;
     float4 Cc, Dd;
@@ -420,8 +428,9 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
         correction_fields<SURR>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
         if (ap.refraction) {
             const float c3 = GR * inv_uz * inv_uz * inv_uz;
-            rx = fmaf(c3, ux, rx);
-            ry = fmaf(c3, uy, ry);
+            const float2 r2 = __ffma2_rn(make_float2(c3, c3), uxy, make_float2(rx, ry));
+            rx = r2.x;
+            ry = r2.y;
             path = fmaf(Gt, inv_uz, path);
         }
         t_rel = fmaf(path, kInvC, t_rel);
