@@ -22,8 +22,9 @@ _lock = threading.Lock()
 _lib = None
 
 ST_LANDED, ST_UPWARD, ST_BELOW, ST_DOMAIN, ST_ABSORBED, ST_SUBSTEP_FLAG = range(6)
-FL_COUNT, FL_ABSORB, FL_HIST_EDGE, FL_TEL_EDGE, FL_DOMAIN, FL_BELOW, FL_UPWARD, FL_LAYER = (
-    1, 2, 4, 8, 16, 32, 64, 128)
+FL_COUNT, FL_ABSORB, FL_HIST_EDGE, FL_TEL_EDGE, FL_DOMAIN, FL_BELOW, FL_UPWARD, FL_LAYER, FL_LV1 = (
+    1, 2, 4, 8, 16, 32, 64, 128, 256)
+LV1_OFF, LV1_ARRAY_CENTRE, LV1_ARRAY_DISC, LV1_TELESCOPES = 0, 1, 2, 3
 ATM_LAYERED, ATM_LINEAR, ATM_HOMOGENEOUS, ATM_TABLE = 0, 1, 2, 3
 RHO_REF = 1.225e-3   # [g/cm^3]: the table kind's density is RHO_REF (n - 1) / kappa
 
@@ -62,7 +63,9 @@ class Config(C.Structure):
                 ("hist_dy", C.c_double), ("tel", C.POINTER(C.c_double)),
                 ("band_pos", C.c_double), ("band_count", C.c_double), ("band_T", C.c_double),
                 ("band_h", C.c_double), ("band_w", C.c_double), ("quad_rtol", C.c_double),
-                ("spherical", C.c_int), ("pad2", C.c_int), ("earth_radius", C.c_double)]
+                ("spherical", C.c_int), ("pad2", C.c_int), ("earth_radius", C.c_double),
+                ("lv1_metric", C.c_int), ("pad3", C.c_int), ("lv1_a", C.c_double), ("lv1_b", C.c_double),
+                ("lv1_centre", C.c_double * 3), ("lv1_radius", C.c_double), ("band_lv1", C.c_double)]
 
 
 SEGMENT_DTYPE = np.dtype([("x0", "<f8"), ("y0", "<f8"), ("z0", "<f8"), ("t0", "<f8"),
@@ -80,7 +83,8 @@ RECORD_DTYPE = np.dtype([("seg", "<u8"), ("k", "<u4"), ("i", "<u4"), ("x", "<f8"
 class Output(C.Structure):
     _fields_ = [("hist", C.POINTER(C.c_uint64)), ("tel_counts", C.POINTER(C.c_uint64)),
                 ("tel_time", C.POINTER(C.c_double)), ("counters", C.c_uint64 * 8),
-                ("records", C.c_void_p), ("capacity", C.c_size_t), ("count", C.c_size_t)]
+                ("records", C.c_void_p), ("capacity", C.c_size_t), ("count", C.c_size_t),
+                ("lv1_dropped", C.c_uint64)]
 
 
 def lib():
@@ -243,7 +247,8 @@ DEFAULT_BANDS = dict(band_pos=1e-4, band_count=1e-4, band_T=1e-5, band_h=1e-3, b
 def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, bunch=1,
               refraction=False, transmission=False, use_domain=None, w_max=None, seed=0,
               seg_base=0, n_showers=1, hist=None, tel=None, records=True, record_capacity=None,
-              transmission_params=None, bands=None, quad_rtol=1e-10, spherical=False, earth_radius=EARTH_RADIUS):
+              transmission_params=None, bands=None, quad_rtol=1e-10, spherical=False, earth_radius=EARTH_RADIUS,
+              lv1=None):
     """Run the oracle over ``segs`` (dict of columns or SEGMENT_DTYPE array).
 
     Returns a dict with hist [n_showers, ny, nx], tel_counts [n_showers, n_tel],
@@ -288,6 +293,11 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
         setattr(cfg, k, v)
     cfg.quad_rtol = quad_rtol
     cfg.spherical, cfg.earth_radius = int(spherical), earth_radius
+    if lv1:   # dict(metric, a, b, centre=(x, y, z), radius, band)
+        cfg.lv1_metric, cfg.lv1_a, cfg.lv1_b = lv1["metric"], lv1["a"], lv1["b"]
+        for i, v in enumerate(lv1.get("centre", (0.0, 0.0, h_obs))):
+            cfg.lv1_centre[i] = v
+        cfg.lv1_radius, cfg.band_lv1 = lv1.get("radius", 0.0), lv1.get("band", 1e-4)
 
     hist_out = np.zeros((n_showers, max(h["ny"], 0), max(h["nx"], 0)), np.uint64)
     tel_counts = np.zeros((n_showers, cfg.n_tel), np.uint64)
@@ -305,7 +315,8 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
     if rc != 0:
         raise RuntimeError("oracle failed: %d" % rc)
     res = dict(hist=hist_out, tel_counts=tel_counts, tel_time=tel_time,
-               counters=np.array(out.counters[:], np.uint64), n_records=int(out.count))
+               counters=np.array(out.counters[:], np.uint64), n_records=int(out.count),
+               lv1_dropped=int(out.lv1_dropped))
     if records:
         if out.count > cap:
             raise RuntimeError("record capacity %d too small (%d)" % (cap, out.count))

@@ -653,12 +653,21 @@ typedef struct {
     int spherical;             /* 1: spherical-shell atmosphere, Earth centre at (0, 0, -earth_radius) */
     int pad2;
     double earth_radius;
+    /* LV1 particle filter (Sec. 4.3.2, 6.2.1): a segment whose start lies y above
+     * h_obs and whose direction makes the angle x [deg] with the point of interest
+     * is dropped, before any photon is generated, when y >= a x^b */
+    int lv1_metric;            /* 0 off, 1 array centre, 2 disc of radius lv1_radius about it, 3 telescope spheres */
+    int pad3;
+    double lv1_a, lv1_b;
+    double lv1_centre[3];
+    double lv1_radius;
+    double band_lv1;           /* relative band of y about a x^b flagged for the parity comparison */
 } orc_config;
 
 enum { ORC_ST_LANDED = 0, ORC_ST_UPWARD = 1, ORC_ST_BELOW = 2, ORC_ST_DOMAIN = 3,
        ORC_ST_ABSORBED = 4, ORC_ST_SUBSTEP_FLAG = 5 };
 enum { ORC_FL_COUNT = 1, ORC_FL_ABSORB = 2, ORC_FL_HIST_EDGE = 4, ORC_FL_TEL_EDGE = 8,
-       ORC_FL_DOMAIN = 16, ORC_FL_BELOW = 32, ORC_FL_UPWARD = 64, ORC_FL_LAYER = 128 };
+       ORC_FL_DOMAIN = 16, ORC_FL_BELOW = 32, ORC_FL_UPWARD = 64, ORC_FL_LAYER = 128, ORC_FL_LV1 = 256 };
 
 typedef struct {
     uint64_t seg;
@@ -681,6 +690,7 @@ typedef struct {
     orc_record* records;
     size_t capacity;
     size_t count;
+    uint64_t lv1_dropped;      /* segments removed by the LV1 filter */
 } orc_output;
 
 static double orc_floor_dist(double v)     /* distance of v to the nearest integer */
@@ -709,6 +719,33 @@ static int orc_segment_valid(const orc_segment* s, int n_showers)
     return 1;
 }
 
+/* Angle [deg] between the unit direction P and the direction from S towards a
+ * sphere of radius r about C, less the sphere's angular radius (0 inside). */
+static double orc_angle_to_sphere(const double S[3], const double P[3], const double C[3], double r)
+{
+    double d[3] = { C[0] - S[0], C[1] - S[1], C[2] - S[2] };
+    double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (!(dn > r)) return 0.0;
+    double c = (P[0] * d[0] + P[1] * d[1] + P[2] * d[2]) / dn;
+    double a = acos(fmax(-1.0, fmin(1.0, c))) - asin(r / dn);
+    return fmax(a, 0.0) * 180.0 / ORC_PI;
+}
+
+/* The LV1 cut parameter x [deg] of a segment starting at S with direction P. */
+static double orc_lv1_x(const orc_config* cfg, const double S[3], const double P[3])
+{
+    if (cfg->lv1_metric == 1) return orc_angle_to_sphere(S, P, cfg->lv1_centre, 0.0);
+    if (cfg->lv1_metric == 2) return orc_angle_to_sphere(S, P, cfg->lv1_centre, cfg->lv1_radius);
+    double best = 180.0;
+    for (int it = 0; it < cfg->n_tel; ++it) {
+        const double* T4 = cfg->tel + 4 * it;
+        double Tc[3] = { T4[0], T4[1], T4[2] };
+        if (cfg->spherical) orc_ae_inverse(cfg->earth_radius, cfg->h_obs, T4[0], T4[1], T4[2] - cfg->h_obs, Tc);
+        best = fmin(best, orc_angle_to_sphere(S, P, Tc, T4[3]));
+    }
+    return best;
+}
+
 int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                   const orc_config* cfg, orc_output* out)
 {
@@ -734,6 +771,33 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
         const float Kf = ceilf(sg->length / (float)cfg->s_max);
         const int K = Kf < 1.0f ? 1 : (int)Kf;
         const int shower = (int)sg->shower_id;
+
+        /* LV1 particle filter (Sec. 4.3.2; the two-parameter cut of Sec. 6.2.1) */
+        int lv1_near = 0;
+        if (cfg->lv1_metric) {
+            const double S[3] = { sg->x0, sg->y0, sg->z0 };
+            double y = sg->z0 - cfg->h_obs;
+            if (cfg->spherical) {
+                double zr = sg->z0 + cfg->earth_radius;
+                y = sqrt(sg->x0 * sg->x0 + sg->y0 * sg->y0 + zr * zr) - cfg->earth_radius - cfg->h_obs;
+            }
+            double x = fmax(orc_lv1_x(cfg, S, P), 1e-3);
+            double thr = cfg->lv1_a * pow(x, cfg->lv1_b);
+            lv1_near = fabs(y - thr) < cfg->band_lv1 * fmax(fabs(thr), 1.0);
+            if (y >= thr) {
+                out->lv1_dropped++;
+                if (lv1_near) {   /* the kernel may keep it: its sub-steps may appear */
+                    for (int k = 0; k < K; ++k) {
+                        orc_record fr; memset(&fr, 0, sizeof fr);
+                        fr.seg = gid; fr.k = (uint32_t)k; fr.i = 0xFFFFFFFFu;
+                        fr.status = ORC_ST_SUBSTEP_FLAG; fr.flags = ORC_FL_COUNT | ORC_FL_LV1;
+                        fr.tel = -1; fr.bin = -1;
+                        orc_push(out, &fr);
+                    }
+                }
+                continue;
+            }
+        }
 
         /* Euler-Rodrigues rotation by 180 degrees about the bisector A of
          * D = (0,0,-1) and P: M = 2 A A^T - 1 (Sec. 4.2), A normalised. */
@@ -791,6 +855,7 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                 rec.tel = -1; rec.bin = -1; rec.nbar = nbar;
                 if (count_flag && i == N - 1) rec.flags |= ORC_FL_COUNT;
                 if (mid_layer_flag) rec.flags |= ORC_FL_LAYER;
+                if (lv1_near) rec.flags |= ORC_FL_COUNT | ORC_FL_LV1;   /* the kernel may drop the segment */
 
                 /* translation to a random point of the sub-step (Fig. 4.2c) */
                 double ell = (k + u0) / K * L;

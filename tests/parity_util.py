@@ -42,7 +42,7 @@ def compare(gpu, orc, bunch=1, shower_of_seg=None, pos_rel=POS_REL, t_rel=T_REL,
     only_g = np.setdiff1d(np.arange(len(g)), ig)
     only_o = np.setdiff1d(np.arange(len(o)), io)
     for j in only_o:
-        assert o["flags"][j] & oracle.FL_COUNT, "oracle bunch missing on the GPU: %r" % (o[j],)
+        assert o["flags"][j] & (oracle.FL_COUNT | oracle.FL_LV1), "oracle bunch missing on the GPU: %r" % (o[j],)
     for j in only_g:
         assert (int(g["seg"][j]), int(g["k"][j])) in flagged_sub, "extra GPU bunch: %r" % (g[j],)
 
