@@ -221,9 +221,33 @@ typedef struct cs_opts {
     int blocks_per_sm;       /* 0 = default */
     const cs_surrogate* surrogate;  /* NULL: exact tracer (tables); else the network replaces the
                                        refraction/time/transmission lookups inside its domain */
+    /* LV1 particle filter (Sec. 4.3.2, with the two-parameter cut of Sec. 6.2.1): a
+     * segment whose start lies y [m] above h_obs (on the sphere: altitude) and whose
+     * direction makes the angle x [deg] (clamped to >= 1e-3) with the point of
+     * interest is dropped before any photon is generated when y >= lv1_a x^lv1_b.
+     * The cut is fitted per detector (the package's lv1.fit_cut). */
+    int lv1_metric;          /* CS_LV1_OFF (default), CS_LV1_ARRAY_CENTRE, CS_LV1_ARRAY_DISC,
+                                CS_LV1_TELESCOPES */
+    double lv1_a, lv1_b;
+    double lv1_centre[3];    /* array centre in the frame [m] (centre and disc metrics) */
+    double lv1_radius;       /* disc radius [m] (disc metric) */
+    uint64_t* lv1_dropped;   /* NULL or one counter in the outputs' memory kind: dropped segments are
+                                added (zeroed first unless accumulate) */
 } cs_opts;
 
-/* Defaults: bunch 1, s_max 1 m, seg_base 0, host pointers, no accumulation. */
+/* The LV1 filter's point of interest: x is the angle from the segment's
+ * direction to the array centre, to a sphere of lv1_radius about it (0 inside),
+ * or the smallest such angle to the telescope spheres (a loop over all
+ * telescopes per segment: for arrays of up to a few hundred). */
+enum {
+    CS_LV1_OFF = 0,
+    CS_LV1_ARRAY_CENTRE = 1,
+    CS_LV1_ARRAY_DISC = 2,
+    CS_LV1_TELESCOPES = 3
+};
+
+/* Defaults: bunch 1, s_max 1 m, seg_base 0, host pointers, no accumulation, no
+ * LV1 filter. */
 void cs_opts_default(cs_opts* opts);
 
 /* Generates and propagates the photons of n segments (Sec. 5.3 pipeline).

@@ -21,6 +21,17 @@ _lib = None
 CS_OK, CS_ERR_INVALID_ARG, CS_ERR_CUDA, CS_ERR_CAPACITY, CS_ERR_TIMEOUT, CS_ERR_DOMAIN, CS_ERR_NO_DEVICE = range(7)
 CS_ATM_LAYERED, CS_ATM_LINEAR, CS_ATM_HOMOGENEOUS, CS_ATM_TABLE = 0, 1, 2, 3
 CS_GEOM_PLANAR, CS_GEOM_SPHERICAL = 0, 1
+CS_LV1_OFF, CS_LV1_ARRAY_CENTRE, CS_LV1_ARRAY_DISC, CS_LV1_TELESCOPES = 0, 1, 2, 3
+
+
+def set_lv1(o, lv1):
+    """Fill the LV1 filter fields of a cs_opts from dict(metric, a, b, centre, radius)."""
+    if not lv1:
+        return
+    o.lv1_metric, o.lv1_a, o.lv1_b = lv1["metric"], lv1["a"], lv1["b"]
+    for i, v in enumerate(lv1.get("centre", (0.0, 0.0, 0.0))):
+        o.lv1_centre[i] = v
+    o.lv1_radius = lv1.get("radius", 0.0)
 (CS_CNT_EMITTED, CS_CNT_ABSORBED, CS_CNT_HIST, CS_CNT_TEL, CS_CNT_MISSED_HIST, CS_CNT_MISSED_TEL,
  CS_CNT_UPWARD, CS_CNT_INVALID_SEGMENTS) = range(8)
 CS_N_COUNTERS = 8
@@ -96,7 +107,9 @@ N_MLP_PARAMS = 64 * 3 + 64 + 2 * (64 * 64 + 64) + 8 * 64 + 8
 class cs_opts(C.Structure):
     _fields_ = [("bunch", C.c_int), ("s_max", C.c_double), ("seg_base", C.c_uint64),
                 ("device_ptrs", C.c_int), ("accumulate", C.c_int), ("block_threads", C.c_int),
-                ("blocks_per_sm", C.c_int), ("surrogate", C.c_void_p)]
+                ("blocks_per_sm", C.c_int), ("surrogate", C.c_void_p),
+                ("lv1_metric", C.c_int), ("lv1_a", C.c_double), ("lv1_b", C.c_double),
+                ("lv1_centre", C.c_double * 3), ("lv1_radius", C.c_double), ("lv1_dropped", C.c_void_p)]
 
 
 def lib():
@@ -385,7 +398,7 @@ class Detector:
 
 
 def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=1.0, seg_base=0,
-                   records=False, record_capacity=None, blocks_per_sm=0, surrogate=None):
+                   records=False, record_capacity=None, blocks_per_sm=0, surrogate=None, lv1=None):
     """cs_propagate_ex with host numpy buffers; returns a dict of outputs."""
     arr = segs if isinstance(segs, np.ndarray) else pack_segments(segs)
     arr = np.ascontiguousarray(arr)
@@ -408,9 +421,14 @@ def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=
     o = cs_opts_default()
     o.bunch, o.s_max, o.seg_base, o.device_ptrs, o.blocks_per_sm = bunch, s_max, seg_base, 0, blocks_per_sm
     o.surrogate = surrogate.handle if surrogate is not None else None
+    dropped = np.zeros(1, np.uint64)
+    if lv1:
+        set_lv1(o, lv1)
+        o.lv1_dropped = dropped.ctypes.data
     st = cs_propagate_ex(_dptr(arr) if len(arr) else None, len(arr), atm.handle, det.handle, seed, o, out)
     _check(st, "cs_propagate_ex")
-    res = dict(hist=hist, tel_counts=tel_counts, tel_time=tel_time, counters=counters, n_records=int(rc[0]))
+    res = dict(hist=hist, tel_counts=tel_counts, tel_time=tel_time, counters=counters, n_records=int(rc[0]),
+               lv1_dropped=int(dropped[0]))
     if records:
         res["records"] = rec[: int(rc[0])]
     return res

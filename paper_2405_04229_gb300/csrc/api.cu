@@ -74,4 +74,10 @@ extern "C" void cs_opts_default(cs_opts* o) {
     o->block_threads = 0;
     o->blocks_per_sm = 0;
     o->surrogate = nullptr;
+    o->lv1_metric = CS_LV1_OFF;
+    o->lv1_a = 0.0;
+    o->lv1_b = 0.0;
+    o->lv1_centre[0] = o->lv1_centre[1] = o->lv1_centre[2] = 0.0;
+    o->lv1_radius = 0.0;
+    o->lv1_dropped = nullptr;
 }

@@ -110,6 +110,11 @@ struct PropParams {
     int bunch;                 // photons per bunch when shower_bunch is null
     const int* shower_bunch;   // per-shower bunch sizes (device), or null
     float s_max;
+    // LV1 particle filter: drop when y >= lv1_a x^lv1_b (x in degrees)
+    int lv1;                   // CS_LV1_*
+    float lv1_a, lv1_b, lv1_r;
+    float lv1_c[3];            // array centre, frame coordinates
+    unsigned long long* lv1_dropped;   // device counter or null
 };
 
 // The atmosphere in FP64, as the table builder integrates it.

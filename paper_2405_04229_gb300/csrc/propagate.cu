@@ -104,6 +104,45 @@ __device__ __forceinline__ void emit_record(const OutParams& o, unsigned long lo
     }
 }
 
+// Angle [deg] from the unit direction P to a sphere of radius r whose centre
+// lies at d from the segment start, less the sphere's angular radius (0 inside).
+__device__ __forceinline__ float angle_to_sphere(float Px, float Py, float Pz, float dx, float dy, float dz, float r) {
+    const float dn = sqrtf(dx * dx + dy * dy + dz * dz);
+    if (!(dn > r)) return 0.0f;
+    const float c = fminf(fmaxf((Px * dx + Py * dy + Pz * dz) / dn, -1.0f), 1.0f);
+    return fmaxf(acosf(c) - asinf(r / dn), 0.0f) * 57.29577951308232f;
+}
+
+// LV1 particle filter (Sec. 4.3.2; the cut of Sec. 6.2.1): true when the
+// segment starting at (x, y, z) (float-float; h its height above h_obs) with
+// direction P is dropped, i.e. h >= a x^b for the angle x to the point of
+// interest.
+template <bool SPH>
+__device__ __forceinline__ bool lv1_drop(const PropParams& pp, const DetParams& dp, float x_hi, float x_lo, float y_hi,
+                                         float y_lo, float z_hi, float z_lo, float h, float Px, float Py, float Pz) {
+    float x;
+    if (pp.lv1 != CS_LV1_TELESCOPES) {
+        const float dx = (pp.lv1_c[0] - x_hi) - x_lo, dy = (pp.lv1_c[1] - y_hi) - y_lo, dz = (pp.lv1_c[2] - z_hi) - z_lo;
+        x = angle_to_sphere(Px, Py, Pz, dx, dy, dz, pp.lv1 == CS_LV1_ARRAY_DISC ? pp.lv1_r : 0.0f);
+    } else {
+        x = 180.0f;
+        for (int it = 0; it < dp.n_tel; ++it) {
+            float dx, dy, dz, r;
+            if (SPH) {
+                const float4 T3 = __ldg(dp.tel3 + it);
+                dx = (T3.x - x_hi) - x_lo; dy = (T3.y - y_hi) - y_lo; dz = (T3.z - z_hi) - z_lo; r = T3.w;
+            } else {
+                const float4 T4 = __ldg(dp.tel + it);
+                const float2 TL = __ldg(dp.tel_lo + it);
+                dx = (T4.x - x_hi) + (TL.x - x_lo); dy = (T4.y - y_hi) + (TL.y - y_lo); dz = T4.z - h; r = T4.w;
+            }
+            x = fminf(x, angle_to_sphere(Px, Py, Pz, dx, dy, dz, r));
+        }
+    }
+    x = fmaxf(x, 1e-3f);
+    return h >= pp.lv1_a * exp2f(pp.lv1_b * log2f(x));
+}
+
 // Stage 1 (Sec. 5.3.1): import one segment, filter it, fold its parameters
 // and compute its local origin.  Returns the number of sub-steps (0 if invalid).
 // Planar: the origin is the ground intercept of the segment's line (float-float).
@@ -111,7 +150,8 @@ __device__ __forceinline__ void emit_record(const OutParams& o, unsigned long lo
 // the radial component of P, 1 / r and the tilt of the local vertical.
 template <bool SPH>
 __device__ __forceinline__ int import_segment(TileSmem& S, int t, const cs_segment* seg, const PropParams& pp,
-                                              const AtmParams& ap, const DetParams& dp, unsigned int& invalid) {
+                                              const AtmParams& ap, const DetParams& dp, unsigned int& invalid,
+                                              unsigned int& dropped) {
     const double2* src = reinterpret_cast<const double2*>(seg);
     const double2 xy = __ldg(src), zt = __ldg(src + 1);
     const float4 dir = __ldg(reinterpret_cast<const float4*>(src + 2));
@@ -151,6 +191,10 @@ __device__ __forceinline__ int import_segment(TileSmem& S, int t, const cs_segme
         const float rr = sqrtf(rho2 + a * a);
         const float lift = rho2 / (rr + a);
         const float Hs = Hs_hi + (Hs_lo + lift);
+        if (pp.lv1 && lv1_drop<true>(pp, dp, x_hi, x_lo, y_hi, y_lo, z_hi, z_lo, Hs, Px, Py, Pz)) {
+            dropped += 1;
+            return 0;
+        }
         const float inv_r = 1.0f / rr;
         const float dvx = x_hi * inv_r, dvy = y_hi * inv_r, dvz = -lift * inv_r;   // v - z-hat
         const float Pr = Px * dvx + Py * dvy + Pz * (1.0f + dvz);
@@ -164,6 +208,10 @@ __device__ __forceinline__ int import_segment(TileSmem& S, int t, const cs_segme
         S.shower[t] = (int)shower;
         S.bunch[t] = pp.shower_bunch ? __ldg(pp.shower_bunch + shower) : pp.bunch;
         return K;
+    }
+    if (pp.lv1 && lv1_drop<false>(pp, dp, x_hi, x_lo, y_hi, y_lo, z_hi, z_lo, Hs_hi + Hs_lo, Px, Py, Pz)) {
+        dropped += 1;
+        return 0;
     }
     // local origin: G = S_xy - Hs P_xy / P_z in float-float
     float Gxh = x_hi, Gxl = x_lo, Gyh = y_hi, Gyl = y_lo;
@@ -592,7 +640,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
     const int t = threadIdx.x;
     if (SURR) tc_setup(*tcs, sv);
     const long long n_tiles = (pp.n + kTile - 1) / kTile;
-    unsigned int emitted = 0, invalid = 0;
+    unsigned int emitted = 0, invalid = 0, dropped = 0;
     Tally T = {0, 0, 0, 0};
     int buf = 0;
 
@@ -605,7 +653,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
         const long long base = tile * kTile;
 
         // ---- stage 1: import and filter (one segment per thread) -------------
-        const int Kt = (t < kTile && base + t < pp.n) ? import_segment<SPH>(S, t, pp.segs + base + t, pp, ap, dp, invalid) : 0;
+        const int Kt = (t < kTile && base + t < pp.n) ? import_segment<SPH>(S, t, pp.segs + base + t, pp, ap, dp, invalid, dropped) : 0;
         int S_tot;
         const int offk = block_scan<NT>(Kt, S.wsum, buf, &S_tot);
         if (t < kTile) S.offK[t] = offk;
@@ -686,6 +734,12 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if ((t & 31) == 0 && x) atomicAdd(op.counters + c, (unsigned long long)(long long)x);
+    }
+    if (pp.lv1_dropped) {
+        unsigned int x = dropped;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((t & 31) == 0 && x) atomicAdd(pp.lv1_dropped, (unsigned long long)x);
     }
 }
 
@@ -795,6 +849,21 @@ cs_status tile_counter(unsigned int** out) {
     return CS_OK;
 }
 
+// The LV1 filter's parameters from the options (the counter as given: device memory here).
+void set_lv1(PropParams& pp, const cs_opts& o) {
+    pp.lv1 = o.lv1_metric;
+    pp.lv1_a = (float)o.lv1_a;
+    pp.lv1_b = (float)o.lv1_b;
+    pp.lv1_r = (float)o.lv1_radius;
+    for (int i = 0; i < 3; ++i) pp.lv1_c[i] = (float)o.lv1_centre[i];
+    pp.lv1_dropped = (unsigned long long*)o.lv1_dropped;
+}
+
+bool lv1_valid(const cs_opts& o) {
+    return o.lv1_metric >= CS_LV1_OFF && o.lv1_metric <= CS_LV1_TELESCOPES &&
+           (o.lv1_metric == CS_LV1_OFF || (isfinite(o.lv1_a) && isfinite(o.lv1_b) && o.lv1_radius >= 0.0));
+}
+
 cs_status launch(const cs_segment* d_segs, size_t n, const cs_atmosphere* atm, const cs_detector* det,
                  uint64_t seed, const cs_opts& o, const OutParams& op, cudaStream_t stream) {
     const DetParams& dp = det->p;
@@ -804,6 +873,7 @@ cs_status launch(const cs_segment* d_segs, size_t n, const cs_atmosphere* atm, c
         if (op.tel_time) CS_CUDA_TRY(cudaMemsetAsync(op.tel_time, 0, (size_t)dp.n_showers * dp.n_tel * 8, stream));
         CS_CUDA_TRY(cudaMemsetAsync(op.counters, 0, CS_N_COUNTERS * 8, stream));
         if (op.record_count) CS_CUDA_TRY(cudaMemsetAsync(op.record_count, 0, 8, stream));
+        if (o.lv1_dropped) CS_CUDA_TRY(cudaMemsetAsync(o.lv1_dropped, 0, 8, stream));
     }
     if (n == 0) return CS_OK;
     PropParams pp;
@@ -815,6 +885,7 @@ cs_status launch(const cs_segment* d_segs, size_t n, const cs_atmosphere* atm, c
     pp.bunch = o.bunch;
     pp.shower_bunch = nullptr;
     pp.s_max = (float)o.s_max;
+    set_lv1(pp, o);
     static bool attr_done = false;
     if (!attr_done) {
         cs_status sa = set_smem_attributes();
@@ -846,7 +917,7 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
     if (det->p.nx > 0 && !out->hist) return CS_ERR_INVALID_ARG;
     if (det->p.n_tel > 0 && !out->tel_counts) return CS_ERR_INVALID_ARG;
     if (out->records && !out->record_count) return CS_ERR_INVALID_ARG;
-    if (!compatible(atm, det)) return CS_ERR_INVALID_ARG;
+    if (!compatible(atm, det) || !lv1_valid(o)) return CS_ERR_INVALID_ARG;
     if (n > (size_t)1 << 40) return CS_ERR_INVALID_ARG;
     cudaStream_t stream = (cudaStream_t)stream_;
     const DetParams& dp = det->p;
@@ -890,6 +961,8 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
     op.records = out->records ? (cs_record*)g_ws.recs : nullptr;
     op.record_capacity = out->records ? out->record_capacity : 0;
     op.record_count = (unsigned long long*)(ob + o_rc);
+    uint64_t* host_dropped = o.lv1_dropped;   // a host counter: staged through the workspace
+    if (host_dropped) o.lv1_dropped = (uint64_t*)(ob + o_rc + 64);
     if (n && !chunked)
         CS_CUDA_TRY(cudaMemcpyAsync(g_ws.segs, segs, n * sizeof(cs_segment), cudaMemcpyHostToDevice, stream));
     if (o.accumulate) {   // bring the caller's running totals in
@@ -898,6 +971,7 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
         if (op.tel_time) CS_CUDA_TRY(cudaMemcpyAsync(op.tel_time, out->tel_time, tel_b, cudaMemcpyHostToDevice, stream));
         CS_CUDA_TRY(cudaMemcpyAsync(op.counters, out->counters, CS_N_COUNTERS * 8, cudaMemcpyHostToDevice, stream));
         CS_CUDA_TRY(cudaMemsetAsync(op.record_count, 0, 8, stream));
+        if (host_dropped) CS_CUDA_TRY(cudaMemcpyAsync(o.lv1_dropped, host_dropped, 8, cudaMemcpyHostToDevice, stream));
     }
     cs_status st;
     if (chunked) {
@@ -926,6 +1000,7 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
     CS_CUDA_TRY(cudaMemcpyAsync(out->counters, op.counters, CS_N_COUNTERS * 8, cudaMemcpyDeviceToHost, stream));
     unsigned long long produced = 0;
     CS_CUDA_TRY(cudaMemcpyAsync(&produced, op.record_count, 8, cudaMemcpyDeviceToHost, stream));
+    if (host_dropped) CS_CUDA_TRY(cudaMemcpyAsync(host_dropped, o.lv1_dropped, 8, cudaMemcpyDeviceToHost, stream));
     CS_CUDA_TRY(cudaStreamSynchronize(stream));
     if (out->record_count) *out->record_count = produced;
     if (out->records && produced) {
@@ -1009,7 +1084,7 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     if (det->p.nx > 0 && !out->hist) return CS_ERR_INVALID_ARG;
     if (det->p.n_tel > 0 && !out->tel_counts) return CS_ERR_INVALID_ARG;
     if (out->records && !out->record_count) return CS_ERR_INVALID_ARG;
-    if (!compatible(atm, det)) return CS_ERR_INVALID_ARG;
+    if (!compatible(atm, det) || !lv1_valid(o)) return CS_ERR_INVALID_ARG;
     // the counter is 32 bits wide: reject inputs with more tiles than it can count
     if ((n + kTile - 1) / kTile >= 0xFFFFFFFFull - 65536ull) return CS_ERR_INVALID_ARG;
     cudaStream_t stream = (cudaStream_t)stream_;
@@ -1034,6 +1109,7 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     pp.bunch = o.bunch;
     pp.shower_bunch = nullptr;
     pp.s_max = (float)o.s_max;
+    set_lv1(pp, o);
     OutParams op;
     op.hist = (unsigned long long*)out->hist;
     op.tel_counts = (unsigned long long*)out->tel_counts;
@@ -1076,7 +1152,7 @@ cs_status check_device_call(const cs_segment* segs, size_t n, const cs_atmospher
     if (det->p.nx > 0 && !out->hist) return CS_ERR_INVALID_ARG;
     if (det->p.n_tel > 0 && !out->tel_counts) return CS_ERR_INVALID_ARG;
     if (out->records && !out->record_count) return CS_ERR_INVALID_ARG;
-    if (!compatible(atm, det)) return CS_ERR_INVALID_ARG;
+    if (!compatible(atm, det) || !lv1_valid(o)) return CS_ERR_INVALID_ARG;
     if (n > (size_t)1 << 40) return CS_ERR_INVALID_ARG;
     return CS_OK;
 }
@@ -1104,6 +1180,7 @@ cs_status enqueue(const cs_segment* segs, size_t n, const cs_atmosphere* atm, co
         if (out->tel_time) CS_CUDA_TRY(cudaMemsetAsync(out->tel_time, 0, (size_t)dp.n_showers * dp.n_tel * 8, stream));
         CS_CUDA_TRY(cudaMemsetAsync(out->counters, 0, CS_N_COUNTERS * 8, stream));
         if (out->record_count) CS_CUDA_TRY(cudaMemsetAsync(out->record_count, 0, 8, stream));
+        if (o.lv1_dropped) CS_CUDA_TRY(cudaMemsetAsync(o.lv1_dropped, 0, 8, stream));
     }
     if (n == 0) return CS_OK;
     PropParams pp;
@@ -1115,6 +1192,7 @@ cs_status enqueue(const cs_segment* segs, size_t n, const cs_atmosphere* atm, co
     pp.bunch = o.bunch;
     pp.shower_bunch = d_bunch;
     pp.s_max = (float)o.s_max;
+    set_lv1(pp, o);
     OutParams op;
     op.hist = (unsigned long long*)out->hist;
     op.tel_counts = (unsigned long long*)out->tel_counts;
