@@ -416,6 +416,43 @@ def run_inclined(args):
         pass
     peak = B.cs_device_sm_count() * LANES_PER_SM * max_mhz * 1e6 / 1e12
     counters = [int(x) for x in outs.counters.cpu()]
+    tel_full = int(outs.tel_counts.sum().item())
+    hist_full = int(outs.hist.sum().item())
+
+    # LV1 particle filter (Sec. 4.3.2, 6.2.1): cut fitted on a labelled sample of chunk 0
+    lv1_res = None
+    if args.lv1:
+        from paper_2405_04229_gb300 import lv1 as L
+        n_lab = min(chunk, 1_000_000)
+        lab = synth.take(synth.inclined_chunk(0, n=chunk, seed=args.seed), slice(0, n_lab))
+        lab_out = B.DeviceOutputs(det, record_capacity=40 * n_lab)
+        ol = B.cs_opts_default()
+        ol.bunch, ol.device_ptrs = bunch, 1
+        st = B.cs_propagate_ex(C.c_void_p(base_ptr), n_lab, atm.handle, det.handle, args.seed, ol, lab_out.out, sp)
+        if st != B.CS_OK:
+            raise B.CSError(st, "cs_propagate_ex(labels)")
+        recs = lab_out.host()["records"]
+        keep = L.contributing(recs, n_lab, histogram=True)
+        centre, radius = (0.0, 0.0, 2000.0), 1000.0 * math.sqrt(2.0) + 30.0
+        x, y = L.cut_parameters(lab, B.CS_LV1_ARRAY_DISC, centre=centre, radius=radius)
+        cut = L.fit_cut(x, y, keep, margin=1.2)
+        del lab_out
+        dropped = torch.zeros(1, dtype=torch.int64, device=dev)
+        B.set_lv1(o, dict(metric=B.CS_LV1_ARRAY_DISC, a=cut["a"], b=cut["b"], centre=centre, radius=radius))
+        o.lv1_dropped = dropped.data_ptr()
+        step()
+        torch.cuda.synchronize()
+        f_photons = int(outs.counters[0].item())
+        f_ms = timed(args.steps, step)
+        lv1_res = {"metric": "disc about the array centre", "radius_m": radius, "a": cut["a"], "b": cut["b"],
+                   "label_sample_segments": n_lab, "removed_in_sample": cut["removed"],
+                   "dropped_segments_fraction": int(dropped.item()) / n, "ms_per_step": f_ms / args.steps,
+                   "photons_per_s": f_photons * args.steps / (f_ms / 1e3),
+                   "equivalent_photons_per_s": photons * args.steps / (f_ms / 1e3),
+                   "speedup": ms / f_ms,
+                   "telescope_count_retention": int(outs.tel_counts.sum().item()) / max(tel_full, 1),
+                   "histogram_count_retention": int(outs.hist.sum().item()) / max(hist_full, 1)}
+        o.lv1_metric, o.lv1_dropped = B.CS_LV1_OFF, None
 
     # end to end: pinned host segments streamed through the library's two-stream
     # double buffer, outputs read back every step
@@ -490,7 +527,7 @@ def run_inclined(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": None,
                          "note": "per chunk launch; spherical lane-op count per bunch %d" % OPS_PER_BUNCH_SPHERICAL},
-            "kernel_ms": k_ms, "cpu_baseline": cpu, "surrogate": surrogate, "e2e": e2e,
+            "kernel_ms": k_ms, "cpu_baseline": cpu, "surrogate": surrogate, "e2e": e2e, "lv1_filter": lv1_res,
             "gpu_launches": args.steps * n_chunks, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
@@ -541,6 +578,7 @@ def main():
     ap.add_argument("--config", default="refraction", choices=["refraction", "batched", "inclined"])
     ap.add_argument("--chunk", type=int, default=10_000_000)
     ap.add_argument("--chunks", type=int, default=10)
+    ap.add_argument("--lv1", action="store_true", help="inclined: also time the LV1 particle filter")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--per-shower", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -54,7 +54,7 @@ def contributing(records, n_segments, seg_base=0, histogram=False):
 def fit_cut(x, y, keep, margin=1.1, b_grid=None):
     """The cut y >= a x^b removing the most segments while keeping every
     segment marked in `keep` (with a margin on a).  Returns dict(a, b, removed)."""
-    b_grid = np.linspace(-4.0, 2.0, 121) if b_grid is None else b_grid
+    b_grid = np.linspace(-10.0, 2.0, 241) if b_grid is None else b_grid
     lx, ly = np.log(x), np.log(np.maximum(y, 1e-3))
     best = dict(a=np.inf, b=0.0, removed=0.0)
     for b in b_grid:
