@@ -51,17 +51,19 @@ def kernel_sources_hash():
     return h.hexdigest()[:16]
 
 
-def kernel_traffic():
-    """DRAM bytes per launch from the committed ncu capture, or None when the
-    kernel sources changed since it was taken."""
+def kernel_profile():
+    """Per-launch DRAM traffic and pipe utilisation of the photon kernel from the
+    committed ncu captures, or None when the kernel sources changed since they
+    were taken."""
     try:
         kv = dict(l.strip().split("=", 1) for l in open(os.path.join(ROOT, "profiles", "propagate_kernel_traffic.txt"))
                   if "=" in l and not l.startswith("#"))
         if kv.get("kernel_sources_sha256") == kernel_sources_hash():
-            return float(kv["bytes_per_launch"])
+            pipes = {k[len("pipe_"):]: float(v) for k, v in kv.items() if k.startswith("pipe_")}
+            return float(kv["bytes_per_launch"]), pipes or None
     except (OSError, ValueError, KeyError):
         pass
-    return None
+    return None, None
 
 
 def env_rank():
@@ -697,7 +699,7 @@ def main():
         pass
     n_sm = B.cs_device_sm_count()
     peak = n_sm * LANES_PER_SM * max_mhz * 1e6 / 1e12
-    traffic = kernel_traffic()
+    traffic, pipes = kernel_profile()
 
     # the surrogate form: the network replaces the table lookups inside its domain
     surrogate = None
@@ -782,8 +784,10 @@ def main():
             "bunches_per_s": value / bunch,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "ncu_pipes_pct": pipes,
                          "note": "FP32/INT lane ops of the method per launch / kernel time; peak = SMs x 128 lanes "
-                                 "x max SM clock"},
+                                 "x max SM clock; ncu_pipes_pct: issue-slot and busiest-pipe utilisation of the "
+                                 "same kernel from the committed capture (2.5e6-segment case)"},
             "kernel_ms": k_ms,
             "cpu_baseline": cpu,
             "surrogate": surrogate,
