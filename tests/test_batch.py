@@ -108,3 +108,56 @@ def test_tiling_autotune(env):
     assert 1 <= r.blocks_per_sm <= 4 and r.n_tried == 4
     assert all(r.ms[i] > 0 for i in range(4))
     assert r.ms[r.blocks_per_sm - 1] == min(r.ms[i] for i in range(4))
+
+
+def test_batched_at_scale_sampled():
+    """64 uneven showers (8e6 segments) in the benchmark's launch form --
+    autotuned tiling, one graph-captured persistent launch, per-shower bunch
+    sizes (10, every eighth shower 5, so that every bunch fits the record
+    buffer) -- with records; 150 sampled segments photon by photon against the
+    oracle, every record against the aggregates."""
+    torch = pytest.importorskip("torch")
+    from paper_2405_04229_gb300 import binding as B
+    segs, counts = synth.uneven_showers(n_showers=64, seed=9, max_total=8_000_000)
+    n = len(segs["z0"])
+    tel = synth.grid_telescopes(nx=20, ny=20, pitch=100.0)
+    atm = B.Atmosphere(layered=synth.US_STANDARD, refraction=True, transmission=True)
+    det = B.Detector(n_showers=64, hist=synth.histogram_400(), tel=tel)
+    d_segs = torch.from_numpy(B.pack_segments(segs).view(np.uint8)).cuda()
+    segp = C.c_void_p(d_segs.data_ptr())
+    tune_out = B.DeviceOutputs(det)
+    sb = np.where(np.arange(64) % 8 == 0, 5, 10).astype(np.int32)
+    o = _opts(B)
+    o.blocks_per_sm = B.cs_autotune_tiling(segp, n, atm.handle, det.handle, 2, sb, o, tune_out.out,
+                                           B.stream_ptr()).blocks_per_sm
+    del tune_out
+    outs = B.DeviceOutputs(det, record_capacity=80_000_000)
+    batch = B.cs_batch_create(segp, n, atm.handle, det.handle, 2, sb, o, outs.out)
+    try:
+        assert B.cs_batch_launch(batch, B.stream_ptr()) == B.CS_OK
+        g = outs.host()
+    finally:
+        B.cs_batch_destroy(batch)
+    PU.check_conservation(g["counters"])
+    rec = g["records"]
+    assert g["n_records"] == len(rec)
+    sid = segs["shower_id"][rec["seg"].astype(np.int64)]
+    assert int(g["counters"][0]) == int(sb[sid].astype(np.int64).sum())
+    h = np.zeros((64, 400 * 400), np.int64)
+    m = rec["bin"] >= 0
+    np.add.at(h, (sid[m], rec["bin"][m]), sb[sid[m]])
+    assert np.array_equal(h.reshape(64, 400, 400), g["hist"].astype(np.int64))
+    rng = np.random.default_rng(4)
+    sample = np.sort(rng.choice(n, 150, replace=False))
+    ORC = oracle.make_atm(oracle.ATM_LAYERED, layered=synth.US_STANDARD)
+    o_recs = []
+    for s in sample:
+        sh = int(segs["shower_id"][s])
+        r = oracle.propagate(synth.take(segs, slice(int(s), int(s) + 1)), ORC, hist=synth.histogram_400(), tel=tel,
+                             bunch=int(sb[sh]), refraction=True, transmission=True, seed=2, seg_base=int(s),
+                             n_showers=64)
+        o_recs.append(r["records"])
+    sel = np.isin(rec["seg"], sample)
+    st = PU.compare(dict(records=rec[sel], n_records=int(sel.sum())), dict(records=np.concatenate(o_recs)),
+                    check_hist=False)
+    assert st["matched"] > 100
