@@ -65,7 +65,9 @@ class Config(C.Structure):
                 ("band_h", C.c_double), ("band_w", C.c_double), ("quad_rtol", C.c_double),
                 ("spherical", C.c_int), ("pad2", C.c_int), ("earth_radius", C.c_double),
                 ("lv1_metric", C.c_int), ("pad3", C.c_int), ("lv1_a", C.c_double), ("lv1_b", C.c_double),
-                ("lv1_centre", C.c_double * 3), ("lv1_radius", C.c_double), ("band_lv1", C.c_double)]
+                ("lv1_centre", C.c_double * 3), ("lv1_radius", C.c_double), ("band_lv1", C.c_double),
+                ("mirror_d", C.c_double), ("focal_f", C.c_double), ("camera_r", C.c_double),
+                ("point_zenith", C.c_double), ("point_azimuth", C.c_double), ("cam_n", C.c_int), ("pad4", C.c_int)]
 
 
 SEGMENT_DTYPE = np.dtype([("x0", "<f8"), ("y0", "<f8"), ("z0", "<f8"), ("t0", "<f8"),
@@ -77,14 +79,14 @@ RECORD_DTYPE = np.dtype([("seg", "<u8"), ("k", "<u4"), ("i", "<u4"), ("x", "<f8"
                          ("dt", "<f8"), ("lam", "<f8"), ("ex", "<f8"), ("ey", "<f8"), ("h_e", "<f8"),
                          ("ux", "<f8"), ("uy", "<f8"), ("uz", "<f8"), ("theta0", "<f8"),
                          ("T", "<f8"), ("nbar", "<f8"), ("status", "<i4"), ("tel", "<i4"),
-                         ("bin", "<i4"), ("flags", "<u4")])
+                         ("bin", "<i4"), ("flags", "<u4"), ("pix", "<i4"), ("pad", "<i4")])
 
 
 class Output(C.Structure):
     _fields_ = [("hist", C.POINTER(C.c_uint64)), ("tel_counts", C.POINTER(C.c_uint64)),
                 ("tel_time", C.POINTER(C.c_double)), ("counters", C.c_uint64 * 8),
                 ("records", C.c_void_p), ("capacity", C.c_size_t), ("count", C.c_size_t),
-                ("lv1_dropped", C.c_uint64)]
+                ("lv1_dropped", C.c_uint64), ("camera", C.POINTER(C.c_uint64))]
 
 
 def lib():
@@ -232,6 +234,18 @@ def ae_inverse(x, y, dz=0.0, h_obs=2000.0, R=EARTH_RADIUS):
     return np.array(out[:])
 
 
+def camera_trace(centre, ground, u, optics):
+    """(pixel or -1, camera-plane point) of the ray ground + t u through the
+    telescope whose sphere is centred at `centre`."""
+    cfg = Config()
+    for k in ("mirror_d", "focal_f", "camera_r", "point_zenith", "point_azimuth", "cam_n"):
+        setattr(cfg, k, optics[k])
+    xy = (C.c_double * 2)()
+    d3 = C.c_double * 3
+    pix = lib().orc_camera_trace(C.byref(cfg), d3(*centre), d3(*ground), d3(*u), xy)
+    return int(pix), np.array(xy[:])
+
+
 def pack_segments(cols) -> np.ndarray:
     n = len(cols["z0"])
     a = np.zeros(n, SEGMENT_DTYPE)
@@ -248,7 +262,7 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
               refraction=False, transmission=False, use_domain=None, w_max=None, seed=0,
               seg_base=0, n_showers=1, hist=None, tel=None, records=True, record_capacity=None,
               transmission_params=None, bands=None, quad_rtol=1e-10, spherical=False, earth_radius=EARTH_RADIUS,
-              lv1=None):
+              lv1=None, optics=None):
     """Run the oracle over ``segs`` (dict of columns or SEGMENT_DTYPE array).
 
     Returns a dict with hist [n_showers, ny, nx], tel_counts [n_showers, n_tel],
@@ -298,11 +312,18 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
         for i, v in enumerate(lv1.get("centre", (0.0, 0.0, h_obs))):
             cfg.lv1_centre[i] = v
         cfg.lv1_radius, cfg.band_lv1 = lv1.get("radius", 0.0), lv1.get("band", 1e-4)
+    if optics:   # dict(mirror_d, focal_f, camera_r, point_zenith, point_azimuth [rad], cam_n)
+        for k in ("mirror_d", "focal_f", "camera_r", "point_zenith", "point_azimuth", "cam_n"):
+            setattr(cfg, k, optics[k])
 
     hist_out = np.zeros((n_showers, max(h["ny"], 0), max(h["nx"], 0)), np.uint64)
     tel_counts = np.zeros((n_showers, cfg.n_tel), np.uint64)
     tel_time = np.zeros((n_showers, cfg.n_tel), np.float64)
     out = Output()
+    cam = None
+    if optics:
+        cam = np.zeros((n_showers, cfg.n_tel, optics["cam_n"], optics["cam_n"]), np.uint64)
+        out.camera = cam.ctypes.data_as(C.POINTER(C.c_uint64))
     out.hist = hist_out.ctypes.data_as(C.POINTER(C.c_uint64))
     out.tel_counts = tel_counts.ctypes.data_as(C.POINTER(C.c_uint64))
     out.tel_time = tel_time.ctypes.data_as(C.POINTER(C.c_double))
@@ -316,7 +337,7 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
         raise RuntimeError("oracle failed: %d" % rc)
     res = dict(hist=hist_out, tel_counts=tel_counts, tel_time=tel_time,
                counters=np.array(out.counters[:], np.uint64), n_records=int(out.count),
-               lv1_dropped=int(out.lv1_dropped))
+               lv1_dropped=int(out.lv1_dropped), camera=cam)
     if records:
         if out.count > cap:
             raise RuntimeError("record capacity %d too small (%d)" % (cap, out.count))

@@ -662,6 +662,13 @@ typedef struct {
     double lv1_centre[3];
     double lv1_radius;
     double band_lv1;           /* relative band of y about a x^b flagged for the parity comparison */
+    /* last-mile optics (Sec. 6.4): each telescope a parabolic mirror (diameter mirror_d,
+     * focal length focal_f, vertex focal_f / 2 behind the sphere centre along the optical
+     * axis pointing at (point_zenith, point_azimuth)), a flat camera disc of radius
+     * camera_r at the focus that also shadows the mirror, cam_n x cam_n pixels */
+    double mirror_d, focal_f, camera_r, point_zenith, point_azimuth;
+    int cam_n;
+    int pad4;
 } orc_config;
 
 enum { ORC_ST_LANDED = 0, ORC_ST_UPWARD = 1, ORC_ST_BELOW = 2, ORC_ST_DOMAIN = 3,
@@ -680,6 +687,8 @@ typedef struct {
     double theta0, T, nbar;
     int32_t status, tel, bin;
     uint32_t flags;
+    int32_t pix;               /* camera pixel iy * cam_n + ix, or -1 */
+    int32_t pad;
 } orc_record;
 
 typedef struct {
@@ -691,6 +700,7 @@ typedef struct {
     size_t capacity;
     size_t count;
     uint64_t lv1_dropped;      /* segments removed by the LV1 filter */
+    uint64_t* camera;          /* n_showers x n_tel x cam_n x cam_n (photons), or NULL */
 } orc_output;
 
 static double orc_floor_dist(double v)     /* distance of v to the nearest integer */
@@ -717,6 +727,97 @@ static int orc_segment_valid(const orc_segment* s, int n_showers)
     if (fabs(n2 - 1.0) > 1e-4) return 0;
     if ((int64_t)s->shower_id >= n_showers) return 0;
     return 1;
+}
+
+/* Last-mile ray tracing through one telescope (Sec. 6.4).  The photon line
+ * G + t u (G on the ground, u its arrival direction) is followed in the
+ * telescope's frame (e1, e2, a; origin the mirror vertex V = C - f/2 a): it
+ * must cross the camera plane z' = f outside the camera disc (else the camera
+ * shadows it), meet the paraboloid z' = (x'^2 + y'^2) / (4 f) inside the
+ * aperture, reflect about the surface normal (x', y', -2 f) and reach the
+ * camera plane inside the disc.  Returns the pixel iy * n + ix or -1; sets
+ * *edge when a decision lies within `band` [m] of a rim or a pixel edge. */
+static int orc_camera_pixel_xy(const orc_config* cfg, const double C[3], const double G[3], const double u[3],
+                               double band, int* edge, double xy[2]);
+
+static int orc_camera_pixel(const orc_config* cfg, const double C[3], const double G[3], const double u[3],
+                            double band, int* edge)
+{
+    double xy[2];
+    return orc_camera_pixel_xy(cfg, C, G, u, band, edge, xy);
+}
+
+/* For the pins: the pixel (or -1) and the camera-plane point of one ray. */
+int orc_camera_trace(const orc_config* cfg, const double C[3], const double G[3], const double u[3], double xy[2])
+{
+    int edge = 0;
+    return orc_camera_pixel_xy(cfg, C, G, u, 0.0, &edge, xy);
+}
+
+static int orc_camera_pixel_xy(const orc_config* cfg, const double C[3], const double G[3], const double u[3],
+                               double band, int* edge, double xy[2])
+{
+    const double f = cfg->focal_f, R = cfg->camera_r, rd = 0.5 * cfg->mirror_d;
+    const double th = cfg->point_zenith, ph = cfg->point_azimuth;
+    const double a[3] = { sin(th) * cos(ph), sin(th) * sin(ph), cos(th) };
+    double e1[3] = { a[1], -a[0], 0.0 };                 /* a x z-hat */
+    double n1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1]);
+    if (n1 < 1e-12) { e1[0] = 1.0; e1[1] = 0.0; } else { e1[0] /= n1; e1[1] /= n1; }
+    const double e2[3] = { a[1] * e1[2] - a[2] * e1[1], a[2] * e1[0] - a[0] * e1[2], a[0] * e1[1] - a[1] * e1[0] };
+    double q[3], p[3], d[3];
+    for (int c = 0; c < 3; ++c) q[c] = G[c] - (C[c] - 0.5 * f * a[c]);
+    p[0] = q[0] * e1[0] + q[1] * e1[1] + q[2] * e1[2];
+    p[1] = q[0] * e2[0] + q[1] * e2[1] + q[2] * e2[2];
+    p[2] = q[0] * a[0] + q[1] * a[1] + q[2] * a[2];
+    d[0] = u[0] * e1[0] + u[1] * e1[1] + u[2] * e1[2];
+    d[1] = u[0] * e2[0] + u[1] * e2[1] + u[2] * e2[2];
+    d[2] = u[0] * a[0] + u[1] * a[1] + u[2] * a[2];
+    if (!(d[2] < 0.0)) return -1;                        /* travelling away from the mirror */
+    /* the camera's shadow */
+    double tc = (f - p[2]) / d[2];
+    double rc = hypot(p[0] + tc * d[0], p[1] + tc * d[1]);
+    if (fabs(rc - R) < band) *edge = 1;
+    if (rc < R) return -1;
+    /* the mirror: F(t) = A t^2 + B t + Cq = r'^2 - 4 f z' is negative inside the
+     * bowl; a ray travelling down leaves the bowl through the mirror at the
+     * larger root (the smaller one is an entry through the wall far above) */
+    double A = d[0] * d[0] + d[1] * d[1];
+    double B = 2.0 * (p[0] * d[0] + p[1] * d[1]) - 4.0 * f * d[2];
+    double Cq = p[0] * p[0] + p[1] * p[1] - 4.0 * f * p[2];
+    double t;
+    if (A < 1e-300) t = -Cq / B;
+    else {
+        double disc = B * B - 4.0 * A * Cq;
+        if (disc < 0.0) return -1;
+        double qq = -0.5 * (B + (B >= 0.0 ? sqrt(disc) : -sqrt(disc)));
+        double t1 = qq / A, t2 = Cq / qq;
+        t = fmax(t1, t2);
+    }
+    double m[3] = { p[0] + t * d[0], p[1] + t * d[1], p[2] + t * d[2] };
+    double rm = hypot(m[0], m[1]);
+    if (fabs(rm - rd) < band) *edge = 1;
+    if (rm > rd) return -1;
+    /* reflection */
+    double N[3] = { m[0], m[1], -2.0 * f };
+    double nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    for (int c = 0; c < 3; ++c) N[c] /= nn;
+    double dn = d[0] * N[0] + d[1] * N[1] + d[2] * N[2];
+    double r[3] = { d[0] - 2.0 * dn * N[0], d[1] - 2.0 * dn * N[1], d[2] - 2.0 * dn * N[2] };
+    if (!(r[2] > 0.0)) return -1;
+    double t2c = (f - m[2]) / r[2];
+    double xq = m[0] + t2c * r[0], yq = m[1] + t2c * r[1];
+    xy[0] = xq; xy[1] = yq;
+    double rq = hypot(xq, yq);
+    if (fabs(rq - R) < band) *edge = 1;
+    if (rq > R) return -1;
+    const int n = cfg->cam_n;
+    double fx = (xq + R) / (2.0 * R) * n, fy = (yq + R) / (2.0 * R) * n;
+    double pitch = 2.0 * R / n;
+    if (orc_floor_dist(fx) * pitch < band || orc_floor_dist(fy) * pitch < band) *edge = 1;
+    int ix = (int)floor(fx), iy = (int)floor(fy);
+    ix = ix < 0 ? 0 : (ix >= n ? n - 1 : ix);
+    iy = iy < 0 ? 0 : (iy >= n ? n - 1 : iy);
+    return iy * n + ix;
 }
 
 /* Angle [deg] between the unit direction P and the direction from S towards a
@@ -791,7 +892,7 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                         orc_record fr; memset(&fr, 0, sizeof fr);
                         fr.seg = gid; fr.k = (uint32_t)k; fr.i = 0xFFFFFFFFu;
                         fr.status = ORC_ST_SUBSTEP_FLAG; fr.flags = ORC_FL_COUNT | ORC_FL_LV1;
-                        fr.tel = -1; fr.bin = -1;
+                        fr.tel = -1; fr.bin = -1; fr.pix = -1;
                         orc_push(out, &fr);
                     }
                 }
@@ -837,7 +938,7 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                 orc_record fr; memset(&fr, 0, sizeof fr);
                 fr.seg = gid; fr.k = (uint32_t)k; fr.i = 0xFFFFFFFFu;
                 fr.status = ORC_ST_SUBSTEP_FLAG; fr.nbar = nbar; fr.flags = ORC_FL_COUNT;
-                fr.tel = -1; fr.bin = -1;
+                fr.tel = -1; fr.bin = -1; fr.pix = -1;
                 orc_push(out, &fr);
             }
             if (N == 0) continue;
@@ -851,6 +952,7 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                 double u2 = orc_uniform(r4[2]), u3 = orc_uniform(r4[3]);
 
                 orc_record rec; memset(&rec, 0, sizeof rec);
+                rec.pix = -1;
                 rec.seg = gid; rec.k = (uint32_t)k; rec.i = (uint32_t)i;
                 rec.tel = -1; rec.bin = -1; rec.nbar = nbar;
                 if (count_flag && i == N - 1) rec.flags |= ORC_FL_COUNT;
@@ -1005,6 +1107,17 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                         if (best >= 0 && fabs(dist - best_d) < cfg->band_pos) rec.flags |= ORC_FL_TEL_EDGE;
                         if (best < 0 || dist < best_d) { best = it; best_d = dist; }
                     }
+                }
+                rec.pix = -1;
+                if (best >= 0 && cfg->cam_n > 0) {
+                    const double* T4 = cfg->tel + 4 * best;
+                    double Tc[3] = { T4[0], T4[1], T4[2] };
+                    if (cfg->spherical) orc_ae_inverse(R, cfg->h_obs, T4[0], T4[1], T4[2] - cfg->h_obs, Tc);
+                    int edge = 0;
+                    rec.pix = orc_camera_pixel(cfg, Tc, G3, ug, cfg->band_pos, &edge);
+                    if (edge) rec.flags |= ORC_FL_TEL_EDGE;
+                    if (rec.pix >= 0 && out->camera)
+                        out->camera[((size_t)shower * cfg->n_tel + best) * cfg->cam_n * cfg->cam_n + rec.pix] += cfg->bunch;
                 }
                 if (best >= 0) {
                     rec.tel = best;

@@ -1,0 +1,79 @@
+"""Pins of the oracle's last-mile ray tracing (Sec. 6.4): a parabolic mirror
+images rays parallel to its axis onto the focus, tilted rays about f tan(a)
+off centre, the camera shadows the rays that meet it first, and the aperture
+and camera rims bound the hits."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_04229_gb300 import synth
+
+OPT = dict(mirror_d=7.0, focal_f=8.0, camera_r=0.5, point_zenith=math.radians(20.0),
+           point_azimuth=math.radians(30.0), cam_n=41)
+C0 = np.array([100.0, -50.0, 2000.0])
+
+
+def _frame():
+    th, ph = OPT["point_zenith"], OPT["point_azimuth"]
+    a = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+    e1 = np.cross(a, [0.0, 0.0, 1.0])
+    e1 /= np.linalg.norm(e1)
+    return a, e1, np.cross(a, e1)
+
+
+def _ray(rho, phi, tilt=0.0, tilt_dir=0.0):
+    """A ray that crosses the aperture plane at (rho, phi) from the axis,
+    tilted by `tilt` from the axis towards `tilt_dir`."""
+    a, e1, e2 = _frame()
+    w = -a * math.cos(tilt) + math.sin(tilt) * (math.cos(tilt_dir) * e1 + math.sin(tilt_dir) * e2)
+    V = C0 - 0.5 * OPT["focal_f"] * a
+    P = V + rho * (math.cos(phi) * e1 + math.sin(phi) * e2)   # a point on the ray in the vertex plane
+    return P, w
+
+
+@pytest.mark.parametrize("rho", [0.6, 1.3, 2.2, 3.4])
+@pytest.mark.parametrize("phi", [0.0, 1.1, 2.9, 4.4])
+def test_rays_parallel_to_the_axis_meet_at_the_focus(rho, phi):
+    P, w = _ray(rho, phi)
+    pix, xy = oracle.camera_trace(C0, P, w, OPT)
+    assert pix >= 0
+    assert np.hypot(*xy) < 1e-9
+    n = OPT["cam_n"]
+    assert pix == (n // 2) * n + n // 2          # the centre pixel (odd n: the focus is its centre)
+
+
+def test_tilted_rays_land_at_f_tan_alpha():
+    f = OPT["focal_f"]
+    for tilt in (0.005, 0.01, 0.02):
+        for tdir in (0.0, 1.0, 2.5):
+            pts = [oracle.camera_trace(C0, *_ray(rho, phi, tilt, tdir), OPT)[1]
+                   for rho in (0.7, 1.0) for phi in np.linspace(0, 2 * math.pi, 8, endpoint=False)]
+            c = np.mean(pts, axis=0)
+            assert np.hypot(*c) == pytest.approx(f * math.tan(tilt), rel=0.03)
+            # a source on the -t side of the axis (the ray travels towards +t) images on the +t side
+            assert np.dot(c, [math.cos(tdir), math.sin(tdir)]) > 0.99 * np.hypot(*c)
+
+
+def test_camera_shadow_and_rims():
+    assert oracle.camera_trace(C0, *_ray(0.3, 0.7), OPT)[0] == -1          # meets the camera first
+    assert oracle.camera_trace(C0, *_ray(3.6, 0.7), OPT)[0] == -1          # outside the aperture
+    assert oracle.camera_trace(C0, *_ray(3.4, 0.7), OPT)[0] >= 0
+    assert oracle.camera_trace(C0, *_ray(2.0, 0.7, 0.08), OPT)[0] == -1    # image beyond the camera rim
+    P, w = _ray(2.0, 0.7)
+    assert oracle.camera_trace(C0, P, -w, OPT)[0] == -1                     # travelling away from the mirror
+
+
+def test_propagation_camera_images_equal_the_records():
+    segs = synth.shower_segments(1200, 20.0, 30.0, 1e12, seed=4)
+    tel = synth.grid_telescopes(nx=4, ny=4, pitch=60.0)
+    r = oracle.propagate(segs, oracle.make_atm(oracle.ATM_LAYERED, layered=synth.US_STANDARD), tel=tel, bunch=2,
+                         refraction=True, transmission=True, seed=1, optics=OPT)
+    rec = r["records"]
+    hit = (rec["status"] == oracle.ST_LANDED) & (rec["tel"] >= 0) & (rec["pix"] >= 0)
+    assert hit.sum() > 20
+    img = np.zeros_like(r["camera"])
+    np.add.at(img.reshape(1, len(tel), -1), (0, rec["tel"][hit], rec["pix"][hit]), 2)
+    assert np.array_equal(img, r["camera"])
+    assert (rec["pix"][rec["tel"] < 0] == -1).all()
