@@ -586,6 +586,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-optics", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -632,9 +633,9 @@ def main():
     o = B.cs_opts_default()
     o.bunch, o.device_ptrs, o.seg_base = bunch, 1, seg_base
 
-    def step(accumulate=0):
+    def step(accumulate=0, det_=det):
         o.accumulate = accumulate
-        st = B.cs_propagate_ex(C.c_void_p(d_segs.data_ptr()), n, atm.handle, det.handle, args.seed, o, out, sp)
+        st = B.cs_propagate_ex(C.c_void_p(d_segs.data_ptr()), n, atm.handle, det_.handle, args.seed, o, out, sp)
         if st != B.CS_OK:
             raise B.CSError(st, "cs_propagate_ex")
 
@@ -733,6 +734,33 @@ def main():
                                 "tensor memory (tcgen05.mma M=128 per warpgroup)"}
         sur.close()
 
+    optics = None
+    if not args.no_optics:
+        # last-mile ray tracing (Sec. 6.4): every telescope a 7 m parabolic mirror (f = 8 m) pointing
+        # along the showers with a 1 m camera of 41 x 41 pixels; the same step with the trace on
+        opt = dict(mirror_d=7.0, focal_f=8.0, camera_r=0.5, point_zenith=math.radians(20.0), point_azimuth=0.0,
+                   cam_n=41)
+        det_o = B.Detector(n_showers=10, hist=hist, tel=tel, optics=opt)
+        cam_t = torch.zeros((10, tel.shape[0], 41, 41), dtype=torch.int64, device=dev)
+        out.camera = cam_t.data_ptr()
+        for _ in range(3):
+            step(det_=det_o)
+        torch.cuda.synchronize()
+        o_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for a, b_ in o_ev:
+            flush.zero_()
+            a.record(stream)
+            step(det_=det_o)
+            b_.record(stream)
+        torch.cuda.synchronize()
+        o_ms = sum(a.elapsed_time(b_) for a, b_ in o_ev) / args.steps
+        optics = {"value": int(cnt[0].item()) / (o_ms / 1e3), "unit": UNIT, "ms_per_step": o_ms,
+                  "time_vs_without": o_ms / (ms_max / args.steps),
+                  "camera_photons": int(cam_t.sum().item()), "telescope_photons": int(tel_c.sum().item()),
+                  "optics": "7 m parabolic mirror, f 8 m, 1 m camera, 41 x 41 pixels, pointing zenith 20 deg"}
+        out.camera = None
+        det_o.close()
+
     e2e = None
     if not args.no_e2e:
         # end to end through the host-pointer call: pinned segments in, outputs out
@@ -791,6 +819,7 @@ def main():
             "kernel_ms": k_ms,
             "cpu_baseline": cpu,
             "surrogate": surrogate,
+            "optics": optics,
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": sm_clk,

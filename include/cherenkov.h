@@ -160,6 +160,16 @@ typedef struct cs_detector_desc {
                                     telescope z is the height above the ground sphere plus h_obs; must
                                     match the atmosphere */
     double earth_radius;         /* spherical: R_E [m]; 0 = 6,370 km */
+    /* Last-mile optics (Sec. 6.4), cam_n > 0 to enable: every telescope is a parabolic mirror of
+     * diameter mirror_d and focal length focal_f whose vertex lies focal_f / 2 behind the sphere
+     * centre along the optical axis (pointing at zenith point_zenith, azimuth point_azimuth [rad],
+     * frame coordinates), with a flat camera disc of radius camera_r at the focus that also shadows
+     * the mirror; photons reaching the camera are binned into cam_n x cam_n square pixels over the
+     * camera's square (pixel iy * cam_n + ix, x along a x z-hat, y along a x x).  Every sphere must
+     * hold its instrument: radius >= sqrt((mirror_d / 2)^2 + (focal_f / 2)^2). */
+    double mirror_d, focal_f, camera_r;
+    double point_zenith, point_azimuth;
+    int cam_n;
 } cs_detector_desc;
 
 typedef struct cs_detector cs_detector;
@@ -195,7 +205,7 @@ typedef struct cs_record {
     int32_t tel;         /* telescope hit or -1 */
     int32_t bin;         /* histogram cell iy * nx + ix or -1 */
     uint32_t status;     /* CS_ST_* */
-    uint32_t reserved;
+    int32_t pix;         /* camera pixel iy * cam_n + ix of the telescope hit, or -1 */
 } cs_record;
 
 typedef struct cs_output {
@@ -207,6 +217,8 @@ typedef struct cs_output {
     cs_record* records;      /* NULL: throughput mode (no per-bunch output) */
     uint64_t record_capacity;
     uint64_t* record_count;  /* 1 element: records produced (may exceed the capacity) */
+    uint64_t* camera;        /* n_showers x n_tel x cam_n x cam_n camera images (photons), or NULL;
+                                required when the detector has optics */
 } cs_output;
 
 typedef struct cs_surrogate cs_surrogate;

@@ -53,7 +53,7 @@ SEGMENT_DTYPE = np.dtype([("x0", "<f8"), ("y0", "<f8"), ("z0", "<f8"), ("t0", "<
                           ("flags", "<u4")])
 RECORD_DTYPE = np.dtype([("seg", "<u8"), ("k", "<u4"), ("i", "<u4"), ("x", "<f4"), ("y", "<f4"),
                          ("dt_ns", "<f4"), ("lambda_nm", "<f4"), ("tel", "<i4"), ("bin", "<i4"),
-                         ("status", "<u4"), ("reserved", "<u4")])
+                         ("status", "<u4"), ("pix", "<i4")])
 
 
 class cs_atmosphere_desc(C.Structure):
@@ -76,13 +76,18 @@ class cs_detector_desc(C.Structure):
     _fields_ = [("n_showers", C.c_int), ("h_obs", C.c_double), ("hist_nx", C.c_int), ("hist_ny", C.c_int),
                 ("hist_x0", C.c_double), ("hist_y0", C.c_double), ("hist_dx", C.c_double),
                 ("hist_dy", C.c_double), ("n_tel", C.c_int), ("tel_xyzr", C.POINTER(C.c_double)),
-                ("geometry", C.c_int), ("earth_radius", C.c_double)]
+                ("geometry", C.c_int), ("earth_radius", C.c_double),
+                ("mirror_d", C.c_double), ("focal_f", C.c_double), ("camera_r", C.c_double),
+                ("point_zenith", C.c_double), ("point_azimuth", C.c_double), ("cam_n", C.c_int)]
+
+
+OPTICS_KEYS = ("mirror_d", "focal_f", "camera_r", "point_zenith", "point_azimuth", "cam_n")
 
 
 class cs_output(C.Structure):
     _fields_ = [("hist", C.c_void_p), ("tel_counts", C.c_void_p), ("tel_time", C.c_void_p),
                 ("counters", C.c_void_p), ("records", C.c_void_p), ("record_capacity", C.c_uint64),
-                ("record_count", C.c_void_p)]
+                ("record_count", C.c_void_p), ("camera", C.c_void_p)]
 
 
 class cs_tune_result(C.Structure):
@@ -371,9 +376,15 @@ class Atmosphere:
 class Detector:
     """Owns a cs_detector handle."""
 
-    def __init__(self, n_showers=1, h_obs=2000.0, hist=None, tel=None, spherical=False, earth_radius=0.0):
+    def __init__(self, n_showers=1, h_obs=2000.0, hist=None, tel=None, spherical=False, earth_radius=0.0,
+                 optics=None):
+        """optics: dict(mirror_d, focal_f, camera_r, point_zenith, point_azimuth [rad], cam_n)
+        for the last-mile ray tracing into per-telescope camera images."""
         d = cs_detector_desc()
         d.n_showers, d.h_obs = n_showers, h_obs
+        if optics:
+            for k in OPTICS_KEYS:
+                setattr(d, k, optics[k])
         d.geometry, d.earth_radius = (CS_GEOM_SPHERICAL if spherical else CS_GEOM_PLANAR), earth_radius
         if hist:
             d.hist_nx, d.hist_ny = hist["nx"], hist["ny"]
@@ -382,6 +393,7 @@ class Detector:
         d.n_tel = self.tel.shape[0]
         d.tel_xyzr = self.tel.ctypes.data_as(C.POINTER(C.c_double))
         self.n_showers, self.nx, self.ny, self.n_tel = n_showers, d.hist_nx, d.hist_ny, d.n_tel
+        self.cam_n = d.cam_n if d.n_tel else 0
         self.desc = d
         self.handle = cs_detector_create(d)
 
@@ -413,6 +425,8 @@ def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=
     out.tel_time = _dptr(tel_time) if det.n_tel else None
     out.counters = _dptr(counters)
     out.record_count = _dptr(rc)
+    camera = np.zeros((det.n_showers, det.n_tel, det.cam_n, det.cam_n), np.uint64)
+    out.camera = _dptr(camera) if det.cam_n else None
     rec = None
     if records:
         cap = record_capacity if record_capacity is not None else max(1024, 120 * len(arr))
@@ -428,7 +442,7 @@ def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=
     st = cs_propagate_ex(_dptr(arr) if len(arr) else None, len(arr), atm.handle, det.handle, seed, o, out)
     _check(st, "cs_propagate_ex")
     res = dict(hist=hist, tel_counts=tel_counts, tel_time=tel_time, counters=counters, n_records=int(rc[0]),
-               lv1_dropped=int(dropped[0]))
+               lv1_dropped=int(dropped[0]), camera=camera)
     if records:
         res["records"] = rec[: int(rc[0])]
     return res
@@ -461,6 +475,8 @@ class DeviceOutputs:
         self.record_count = torch.zeros(1, dtype=torch.int64, device=d)
         self.records = torch.zeros(record_capacity * RECORD_DTYPE.itemsize, dtype=torch.uint8, device=d) \
             if record_capacity else None
+        self.camera = torch.zeros((det.n_showers, det.n_tel, det.cam_n, det.cam_n), dtype=torch.int64, device=d) \
+            if det.cam_n else None
         o = cs_output()
         o.hist = self.hist.data_ptr() if det.nx else None
         o.tel_counts = self.tel_counts.data_ptr() if det.n_tel else None
@@ -469,6 +485,7 @@ class DeviceOutputs:
         o.record_count = self.record_count.data_ptr()
         if record_capacity:
             o.records, o.record_capacity = self.records.data_ptr(), record_capacity
+        o.camera = self.camera.data_ptr() if self.camera is not None else None
         self.out = o
 
     def host(self):
@@ -476,6 +493,8 @@ class DeviceOutputs:
         r = dict(hist=self.hist.cpu().numpy().astype(np.uint64), tel_counts=self.tel_counts.cpu().numpy().astype(np.uint64),
                  tel_time=self.tel_time.cpu().numpy(), counters=self.counters.cpu().numpy().astype(np.uint64),
                  n_records=int(self.record_count.item()))
+        if self.camera is not None:
+            r["camera"] = self.camera.cpu().numpy().astype(np.uint64)
         if self.records is not None:
             n = min(r["n_records"], self.out.record_capacity)
             r["records"] = self.records[: n * RECORD_DTYPE.itemsize].cpu().numpy().view(RECORD_DTYPE)

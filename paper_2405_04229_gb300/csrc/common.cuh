@@ -90,6 +90,11 @@ struct DetParams {
     const float4* cell_data;  // planar: {x - corner_x, y - corner_y, z - h_obs, radius}; spherical: tel3
     float hash_sin2_max;    // photons arriving steeper than this use the full list
     float bx0, bx1, by0, by1;  // bounding box of all reach discs
+    // last-mile optics: mirror focal length, (aperture radius)^2, camera radius,
+    // pixels per metre on the camera, and the telescope frame (axis a, e1 = a x z-hat, e2 = a x e1)
+    int cam_n;
+    float cam_f, cam_rd2, cam_r, cam_scale;
+    float ax, ay, az, e1x, e1y, e1z, e2x, e2y, e2z;
 };
 
 struct OutParams {
@@ -100,6 +105,7 @@ struct OutParams {
     cs_record* records;
     unsigned long long record_capacity;
     unsigned long long* record_count;
+    unsigned long long* camera;   // n_showers x n_tel x cam_n^2, or null
 };
 
 struct PropParams {

@@ -38,6 +38,17 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
         const double* t = d->tel_xyzr + 4 * i;
         if (!isfinite(t[0]) || !isfinite(t[1]) || !isfinite(t[2]) || !(t[3] > 0.0)) return CS_ERR_INVALID_ARG;
     }
+    if (d->cam_n < 0 || d->cam_n > 4096) return CS_ERR_INVALID_ARG;
+    if (d->cam_n > 0) {   // the optics: positive sizes, and every sphere must hold its instrument
+        if (!(d->mirror_d > 0.0) || !(d->focal_f > 0.0) || !(d->camera_r > 0.0) || !isfinite(d->mirror_d) ||
+            !isfinite(d->focal_f) || !isfinite(d->camera_r) || !isfinite(d->point_zenith) ||
+            !isfinite(d->point_azimuth))
+            return CS_ERR_INVALID_ARG;
+        const double hold = sqrt(0.25 * d->mirror_d * d->mirror_d + 0.25 * d->focal_f * d->focal_f);
+        for (int i = 0; i < d->n_tel; ++i)
+            if (d->tel_xyzr[4 * i + 3] < hold) return CS_ERR_INVALID_ARG;
+        if ((double)d->n_showers * d->n_tel * d->cam_n * d->cam_n > 4e9) return CS_ERR_INVALID_ARG;
+    }
     cs_status st = cs::check_device();
     if (st != CS_OK) return st;
 
@@ -59,6 +70,23 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
         p.inv_dy = (float)(1.0 / d->hist_dy);
     }
     p.n_tel = d->n_tel;
+    p.cam_n = d->n_tel > 0 ? d->cam_n : 0;
+    if (p.cam_n > 0) {
+        // telescope frame: axis a towards the pointing, e1 = a x z-hat (x-hat at zenith), e2 = a x e1
+        const double th = d->point_zenith, ph = d->point_azimuth;
+        const double a[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
+        double e1[3] = {a[1], -a[0], 0.0};
+        const double n1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1]);
+        if (n1 < 1e-12) { e1[0] = 1.0; e1[1] = 0.0; } else { e1[0] /= n1; e1[1] /= n1; }
+        const double e2[3] = {a[1] * e1[2] - a[2] * e1[1], a[2] * e1[0] - a[0] * e1[2], a[0] * e1[1] - a[1] * e1[0]};
+        p.ax = (float)a[0]; p.ay = (float)a[1]; p.az = (float)a[2];
+        p.e1x = (float)e1[0]; p.e1y = (float)e1[1]; p.e1z = (float)e1[2];
+        p.e2x = (float)e2[0]; p.e2y = (float)e2[1]; p.e2z = (float)e2[2];
+        p.cam_f = (float)d->focal_f;
+        p.cam_rd2 = (float)(0.25 * d->mirror_d * d->mirror_d);
+        p.cam_r = (float)d->camera_r;
+        p.cam_scale = (float)(d->cam_n / (2.0 * d->camera_r));
+    }
 
     // host-side layout: tel float4, tel_lo float2, tel3 float4, cell_start, cell_tel
     std::vector<float4> tel(d->n_tel), tel3(p.spherical ? d->n_tel : 0);

@@ -85,7 +85,8 @@ __device__ __forceinline__ int block_scan(int v, int (*wsum)[kMaxThreads / 32], 
 }
 
 __device__ __forceinline__ void emit_record(const OutParams& o, unsigned long long seg, int k, int i, float x,
-                                            float y, float t_rel, float inv_l, int tel, int bin, int status) {
+                                            float y, float t_rel, float inv_l, int tel, int bin, int status,
+                                            int pix) {
     const unsigned long long slot = atomicAdd(o.record_count, 1ULL);
     if (slot < o.record_capacity) {
         cs_record r;
@@ -99,7 +100,7 @@ __device__ __forceinline__ void emit_record(const OutParams& o, unsigned long lo
         r.tel = tel;
         r.bin = bin;
         r.status = (uint32_t)status;
-        r.reserved = 0;
+        r.pix = pix;
         o.records[slot] = r;
     }
 }
@@ -333,6 +334,61 @@ __device__ __forceinline__ int hit_telescope(const DetParams& dp, bool hashed, f
     return best;
 }
 
+// Last-mile ray tracing (Sec. 6.4) through the telescope whose sphere centre
+// lies at dd from the ground point, for the arrival direction u, in the
+// telescope's frame (e1, e2, a) with the origin at the mirror vertex
+// C - f/2 a.  The ray starts at its closest approach to the centre (the same
+// line as from the ground point, better conditioned in FP32).  It must pass
+// the camera plane z' = f outside the camera disc (else the camera shadows
+// it), leave the bowl z' < r'^2 / (4 f) through the paraboloid inside the
+// aperture -- the larger root of r'^2 - 4 f z' = 0 along the line, the
+// smaller being an entry through the wall far above --, reflect about the
+// surface normal (x', y', -2 f) and reach the camera plane inside the disc.
+// Returns the pixel iy * cam_n + ix or -1.
+__device__ __noinline__ int camera_pixel(const DetParams& dp, float ddx, float ddy, float ddz, float ux, float uy,
+                                         float uz) {
+    const float f = dp.cam_f, R = dp.cam_r;
+    const float along = ddx * ux + ddy * uy + ddz * uz;
+    const float hf = 0.5f * f;
+    const float qx = fmaf(along, ux, fmaf(hf, dp.ax, -ddx));
+    const float qy = fmaf(along, uy, fmaf(hf, dp.ay, -ddy));
+    const float qz = fmaf(along, uz, fmaf(hf, dp.az, -ddz));
+    const float p0 = qx * dp.e1x + qy * dp.e1y + qz * dp.e1z;
+    const float p1 = qx * dp.e2x + qy * dp.e2y + qz * dp.e2z;
+    const float p2 = qx * dp.ax + qy * dp.ay + qz * dp.az;
+    const float d0 = ux * dp.e1x + uy * dp.e1y + uz * dp.e1z;
+    const float d1 = ux * dp.e2x + uy * dp.e2y + uz * dp.e2z;
+    const float d2 = ux * dp.ax + uy * dp.ay + uz * dp.az;
+    if (!(d2 < 0.0f)) return -1;   // travelling away from the mirror
+    const float tc = (f - p2) / d2;
+    const float cx = fmaf(tc, d0, p0), cy = fmaf(tc, d1, p1);
+    if (cx * cx + cy * cy < R * R) return -1;   // the camera's shadow
+    const float A = d0 * d0 + d1 * d1;
+    const float B = 2.0f * (p0 * d0 + p1 * d1) - 4.0f * f * d2;
+    const float Cq = p0 * p0 + p1 * p1 - 4.0f * f * p2;
+    const float disc = B * B - 4.0f * A * Cq;
+    if (!(disc >= 0.0f)) return -1;
+    // roots qq / A and Cq / qq without cancellation; A = 0 (a ray along the
+    // axis, B > 0) leaves the finite root Cq / qq = -Cq / B
+    const float qq = -0.5f * (B + copysignf(sqrtf(disc), B));
+    const float t = fmaxf(qq / A, Cq / qq);
+    if (!isfinite(t)) return -1;
+    const float mx = fmaf(t, d0, p0), my = fmaf(t, d1, p1), mz = fmaf(t, d2, p2);
+    const float rm2 = mx * mx + my * my;
+    if (rm2 > dp.cam_rd2) return -1;   // outside the aperture
+    const float nz = -2.0f * f;
+    const float k = 2.0f * (d0 * mx + d1 * my + d2 * nz) / (rm2 + nz * nz);
+    const float r0 = d0 - k * mx, r1 = d1 - k * my, r2 = d2 - k * nz;
+    if (!(r2 > 0.0f)) return -1;
+    const float sc = (f - mz) / r2;
+    const float xq = fmaf(sc, r0, mx), yq = fmaf(sc, r1, my);
+    if (xq * xq + yq * yq > R * R) return -1;   // beyond the camera's rim
+    const int n = dp.cam_n;
+    const int ix = min(max((int)floorf((xq + R) * dp.cam_scale), 0), n - 1);
+    const int iy = min(max((int)floorf((yq + R) * dp.cam_scale), 0), n - 1);
+    return iy * n + ix;
+}
+
 // The correction fields at (dz, tan^2 of the local zenith) and the
 // transmission: the network's outputs where it applies, else the bilinear
 // table lookup; (0, 0, 1) without tables.
@@ -457,7 +513,7 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
     if (!active) return;
 
     // ---- propagation and detection -----------------------------------------------
-    int tel = -1, bin = -1;
+    int tel = -1, bin = -1, pix = -1;
     float x = 0.0f, y = 0.0f, t_rel = ell * B.w;
     if (status == CS_ST_LANDED && !SPH) {
         float rx, ry;
@@ -532,11 +588,18 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
                             ddz = T4.z;
                             r = T4.w;
                         });
+                    if (tel >= 0 && dp.cam_n > 0) {
+                        const float4 T4 = __ldg(dp.tel + tel);
+                        const float2 TL = __ldg(dp.tel_lo + tel);
+                        pix = camera_pixel(dp, (T4.x - Cg.x) + ((TL.x - Cg.y) - rx),
+                                           (T4.y - Cg.z) + ((TL.y - Cg.w) - ry), T4.z, ux * sc, uy * sc, ugz);
+                    }
                 }
                 if (tel >= 0) {
                     const size_t slot = (size_t)sh * dp.n_tel + tel;
                     atomicAdd(op.tel_counts + slot, (unsigned long long)b);
                     if (op.tel_time) atomicAdd(op.tel_time + slot, (double)b * (S.t0[sg] + (double)t_rel));
+                    if (pix >= 0) atomicAdd(op.camera + (slot * dp.cam_n * dp.cam_n + pix), (unsigned long long)b);
                 }
             }
         }
@@ -614,11 +677,16 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
                             delta3(T3, ddx, ddy, ddz);
                             r = T3.w;
                         });
+                    if (tel >= 0 && dp.cam_n > 0) {
+                        const float4 T3 = __ldg(dp.tel3 + tel);
+                        pix = camera_pixel(dp, T3.x - Gx, T3.y - Gy, T3.z - Gz, ugx, ugy, ugz);
+                    }
                 }
                 if (tel >= 0) {
                     const size_t slot = (size_t)sh * dp.n_tel + tel;
                     atomicAdd(op.tel_counts + slot, (unsigned long long)b);
                     if (op.tel_time) atomicAdd(op.tel_time + slot, (double)b * (S.t0[sg] + (double)t_rel));
+                    if (pix >= 0) atomicAdd(op.camera + (slot * dp.cam_n * dp.cam_n + pix), (unsigned long long)b);
                 }
             }
         }
@@ -627,7 +695,7 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
     T.upward += status == CS_ST_UPWARD ? b : 0;
     T.hist += bin >= 0 ? b : 0;
     T.tel += tel >= 0 ? b : 0;
-    if (REC) emit_record(op, gid, k, i, x, y, t_rel, inv_l, tel, bin, status);
+    if (REC) emit_record(op, gid, k, i, x, y, t_rel, inv_l, tel, bin, status, pix);
 }
 
 template <bool SURR, bool SPH, int MINB, bool REC, int NT = SURR ? kThreadsSur : kThreads>
@@ -864,16 +932,49 @@ bool lv1_valid(const cs_opts& o) {
            (o.lv1_metric == CS_LV1_OFF || (isfinite(o.lv1_a) && isfinite(o.lv1_b) && o.lv1_radius >= 0.0));
 }
 
+size_t camera_bytes(const DetParams& dp) { return (size_t)dp.n_showers * dp.n_tel * dp.cam_n * dp.cam_n * 8; }
+
+// The caller's device outputs as the kernel sees them.
+OutParams out_params(const cs_output* out) {
+    OutParams op;
+    op.hist = (unsigned long long*)out->hist;
+    op.tel_counts = (unsigned long long*)out->tel_counts;
+    op.tel_time = out->tel_time;
+    op.counters = (unsigned long long*)out->counters;
+    op.records = out->records;
+    op.record_capacity = out->records ? out->record_capacity : 0;
+    op.record_count = (unsigned long long*)out->record_count;
+    op.camera = (unsigned long long*)out->camera;
+    return op;
+}
+
+// The outputs a call that does not accumulate starts from: zero.
+cs_status zero_outputs(const DetParams& dp, const OutParams& op, uint64_t* lv1_dropped, cudaStream_t stream) {
+    if (op.hist) CS_CUDA_TRY(cudaMemsetAsync(op.hist, 0, (size_t)dp.n_showers * dp.nx * dp.ny * 8, stream));
+    if (op.tel_counts) CS_CUDA_TRY(cudaMemsetAsync(op.tel_counts, 0, (size_t)dp.n_showers * dp.n_tel * 8, stream));
+    if (op.tel_time) CS_CUDA_TRY(cudaMemsetAsync(op.tel_time, 0, (size_t)dp.n_showers * dp.n_tel * 8, stream));
+    if (op.camera && dp.cam_n > 0) CS_CUDA_TRY(cudaMemsetAsync(op.camera, 0, camera_bytes(dp), stream));
+    CS_CUDA_TRY(cudaMemsetAsync(op.counters, 0, CS_N_COUNTERS * 8, stream));
+    if (op.record_count) CS_CUDA_TRY(cudaMemsetAsync(op.record_count, 0, 8, stream));
+    if (lv1_dropped) CS_CUDA_TRY(cudaMemsetAsync(lv1_dropped, 0, 8, stream));
+    return CS_OK;
+}
+
+// Output pointers every call needs for its detector.
+bool outputs_complete(const cs_detector* det, const cs_output* out) {
+    if (det->p.nx > 0 && !out->hist) return false;
+    if (det->p.n_tel > 0 && !out->tel_counts) return false;
+    if (det->p.cam_n > 0 && !out->camera) return false;
+    if (out->records && !out->record_count) return false;
+    return true;
+}
+
 cs_status launch(const cs_segment* d_segs, size_t n, const cs_atmosphere* atm, const cs_detector* det,
                  uint64_t seed, const cs_opts& o, const OutParams& op, cudaStream_t stream) {
     const DetParams& dp = det->p;
     if (!o.accumulate) {
-        if (op.hist) CS_CUDA_TRY(cudaMemsetAsync(op.hist, 0, (size_t)dp.n_showers * dp.nx * dp.ny * 8, stream));
-        if (op.tel_counts) CS_CUDA_TRY(cudaMemsetAsync(op.tel_counts, 0, (size_t)dp.n_showers * dp.n_tel * 8, stream));
-        if (op.tel_time) CS_CUDA_TRY(cudaMemsetAsync(op.tel_time, 0, (size_t)dp.n_showers * dp.n_tel * 8, stream));
-        CS_CUDA_TRY(cudaMemsetAsync(op.counters, 0, CS_N_COUNTERS * 8, stream));
-        if (op.record_count) CS_CUDA_TRY(cudaMemsetAsync(op.record_count, 0, 8, stream));
-        if (o.lv1_dropped) CS_CUDA_TRY(cudaMemsetAsync(o.lv1_dropped, 0, 8, stream));
+        cs_status z = zero_outputs(dp, op, o.lv1_dropped, stream);
+        if (z != CS_OK) return z;
     }
     if (n == 0) return CS_OK;
     PropParams pp;
@@ -914,24 +1015,14 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
     cs_opts o;
     if (opts) o = *opts; else cs_opts_default(&o);
     if (o.bunch < 1 || !(o.s_max > 0.0) || (n > 0 && !segs)) return CS_ERR_INVALID_ARG;
-    if (det->p.nx > 0 && !out->hist) return CS_ERR_INVALID_ARG;
-    if (det->p.n_tel > 0 && !out->tel_counts) return CS_ERR_INVALID_ARG;
-    if (out->records && !out->record_count) return CS_ERR_INVALID_ARG;
+    if (!outputs_complete(det, out)) return CS_ERR_INVALID_ARG;
     if (!compatible(atm, det) || !lv1_valid(o)) return CS_ERR_INVALID_ARG;
     if (n > (size_t)1 << 40) return CS_ERR_INVALID_ARG;
     cudaStream_t stream = (cudaStream_t)stream_;
     const DetParams& dp = det->p;
     if (o.device_ptrs) {
         if (((uintptr_t)segs & 15) != 0) return CS_ERR_INVALID_ARG;
-        OutParams op;
-        op.hist = (unsigned long long*)out->hist;
-        op.tel_counts = (unsigned long long*)out->tel_counts;
-        op.tel_time = out->tel_time;
-        op.counters = (unsigned long long*)out->counters;
-        op.records = out->records;
-        op.record_capacity = out->records ? out->record_capacity : 0;
-        op.record_count = (unsigned long long*)out->record_count;
-        return launch(segs, n, atm, det, seed, o, op, stream);
+        return launch(segs, n, atm, det, seed, o, out_params(out), stream);
     }
     // host pointers: stage through the workspace
     std::lock_guard<std::mutex> lock(g_ws.mu);
@@ -944,8 +1035,9 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
         g_ws.device = dev;
     }
     const size_t hist_b = (size_t)dp.n_showers * dp.nx * dp.ny * 8, tel_b = (size_t)dp.n_showers * dp.n_tel * 8;
-    const size_t o_hist = 0, o_tel = up256(hist_b), o_time = o_tel + up256(tel_b), o_cnt = o_time + up256(tel_b),
-                 o_rc = o_cnt + 256, outs_b = o_rc + 256;
+    const size_t cam_b = camera_bytes(dp);
+    const size_t o_hist = 0, o_tel = up256(hist_b), o_time = o_tel + up256(tel_b), o_cam = o_time + up256(tel_b),
+                 o_cnt = o_cam + up256(cam_b), o_rc = o_cnt + 256, outs_b = o_rc + 256;
     // large inputs are streamed in chunks: the copy of one chunk overlaps the kernel of the previous
     const bool chunked = n > 2 * kHostChunk;
     if (!chunked) CS_CUDA_TRY(ensure(&g_ws.segs, &g_ws.segs_cap, std::max<size_t>(n, 1) * sizeof(cs_segment)));
@@ -961,6 +1053,7 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
     op.records = out->records ? (cs_record*)g_ws.recs : nullptr;
     op.record_capacity = out->records ? out->record_capacity : 0;
     op.record_count = (unsigned long long*)(ob + o_rc);
+    op.camera = cam_b ? (unsigned long long*)(ob + o_cam) : nullptr;
     uint64_t* host_dropped = o.lv1_dropped;   // a host counter: staged through the workspace
     if (host_dropped) o.lv1_dropped = (uint64_t*)(ob + o_rc + 64);
     if (n && !chunked)
@@ -969,6 +1062,7 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
         if (op.hist) CS_CUDA_TRY(cudaMemcpyAsync(op.hist, out->hist, hist_b, cudaMemcpyHostToDevice, stream));
         if (op.tel_counts) CS_CUDA_TRY(cudaMemcpyAsync(op.tel_counts, out->tel_counts, tel_b, cudaMemcpyHostToDevice, stream));
         if (op.tel_time) CS_CUDA_TRY(cudaMemcpyAsync(op.tel_time, out->tel_time, tel_b, cudaMemcpyHostToDevice, stream));
+        if (op.camera) CS_CUDA_TRY(cudaMemcpyAsync(op.camera, out->camera, cam_b, cudaMemcpyHostToDevice, stream));
         CS_CUDA_TRY(cudaMemcpyAsync(op.counters, out->counters, CS_N_COUNTERS * 8, cudaMemcpyHostToDevice, stream));
         CS_CUDA_TRY(cudaMemsetAsync(op.record_count, 0, 8, stream));
         if (host_dropped) CS_CUDA_TRY(cudaMemcpyAsync(o.lv1_dropped, host_dropped, 8, cudaMemcpyHostToDevice, stream));
@@ -987,6 +1081,7 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
         dout.records = op.records;
         dout.record_capacity = op.record_capacity;
         dout.record_count = (uint64_t*)op.record_count;
+        dout.camera = (uint64_t*)op.camera;
         cs_opts od = o;
         od.device_ptrs = 1;
         st = cs_streamer_run(g_ws.streamer, segs, n, atm, det, seed, &od, &dout, stream);
@@ -997,6 +1092,7 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
     if (op.hist) CS_CUDA_TRY(cudaMemcpyAsync(out->hist, op.hist, hist_b, cudaMemcpyDeviceToHost, stream));
     if (op.tel_counts) CS_CUDA_TRY(cudaMemcpyAsync(out->tel_counts, op.tel_counts, tel_b, cudaMemcpyDeviceToHost, stream));
     if (op.tel_time) CS_CUDA_TRY(cudaMemcpyAsync(out->tel_time, op.tel_time, tel_b, cudaMemcpyDeviceToHost, stream));
+    if (op.camera) CS_CUDA_TRY(cudaMemcpyAsync(out->camera, op.camera, cam_b, cudaMemcpyDeviceToHost, stream));
     CS_CUDA_TRY(cudaMemcpyAsync(out->counters, op.counters, CS_N_COUNTERS * 8, cudaMemcpyDeviceToHost, stream));
     unsigned long long produced = 0;
     CS_CUDA_TRY(cudaMemcpyAsync(&produced, op.record_count, 8, cudaMemcpyDeviceToHost, stream));
@@ -1082,8 +1178,7 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     if (!o.device_ptrs) return CS_ERR_INVALID_ARG;           // host buffers would need staging memory
     if (((uintptr_t)segs & 15) != 0) return CS_ERR_INVALID_ARG;
     if (det->p.nx > 0 && !out->hist) return CS_ERR_INVALID_ARG;
-    if (det->p.n_tel > 0 && !out->tel_counts) return CS_ERR_INVALID_ARG;
-    if (out->records && !out->record_count) return CS_ERR_INVALID_ARG;
+    if (!outputs_complete(det, out)) return CS_ERR_INVALID_ARG;
     if (!compatible(atm, det) || !lv1_valid(o)) return CS_ERR_INVALID_ARG;
     // the counter is 32 bits wide: reject inputs with more tiles than it can count
     if ((n + kTile - 1) / kTile >= 0xFFFFFFFFull - 65536ull) return CS_ERR_INVALID_ARG;
@@ -1092,13 +1187,8 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     unsigned int* ctr = nullptr;
     cs_status st = noalloc_scratch(&ctr);
     if (st != CS_OK) return st;
-    if (!o.accumulate) {
-        if (out->hist) CS_CUDA_TRY(cudaMemsetAsync(out->hist, 0, (size_t)dp.n_showers * dp.nx * dp.ny * 8, stream));
-        if (out->tel_counts) CS_CUDA_TRY(cudaMemsetAsync(out->tel_counts, 0, (size_t)dp.n_showers * dp.n_tel * 8, stream));
-        if (out->tel_time) CS_CUDA_TRY(cudaMemsetAsync(out->tel_time, 0, (size_t)dp.n_showers * dp.n_tel * 8, stream));
-        CS_CUDA_TRY(cudaMemsetAsync(out->counters, 0, CS_N_COUNTERS * 8, stream));
-        if (out->record_count) CS_CUDA_TRY(cudaMemsetAsync(out->record_count, 0, 8, stream));
-    }
+    const OutParams op = out_params(out);
+    if (!o.accumulate && (st = zero_outputs(dp, op, o.lv1_dropped, stream)) != CS_OK) return st;
     if (n == 0) return CS_OK;
     PropParams pp;
     pp.segs = segs;
@@ -1110,14 +1200,6 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     pp.shower_bunch = nullptr;
     pp.s_max = (float)o.s_max;
     set_lv1(pp, o);
-    OutParams op;
-    op.hist = (unsigned long long*)out->hist;
-    op.tel_counts = (unsigned long long*)out->tel_counts;
-    op.tel_time = out->tel_time;
-    op.counters = (unsigned long long*)out->counters;
-    op.records = out->records;
-    op.record_capacity = out->records ? out->record_capacity : 0;
-    op.record_count = (unsigned long long*)out->record_count;
     if ((st = set_smem_attributes()) != CS_OK) return st;
     const int per_sm = default_blocks_per_sm(o);
     const long long tiles = ((long long)n + kTile - 1) / kTile;
@@ -1149,9 +1231,7 @@ cs_status check_device_call(const cs_segment* segs, size_t n, const cs_atmospher
     if (!atm || !det || !out || !out->counters) return CS_ERR_INVALID_ARG;
     if (o.bunch < 1 || !(o.s_max > 0.0) || (n > 0 && !segs) || !o.device_ptrs) return CS_ERR_INVALID_ARG;
     if (((uintptr_t)segs & 15) != 0) return CS_ERR_INVALID_ARG;
-    if (det->p.nx > 0 && !out->hist) return CS_ERR_INVALID_ARG;
-    if (det->p.n_tel > 0 && !out->tel_counts) return CS_ERR_INVALID_ARG;
-    if (out->records && !out->record_count) return CS_ERR_INVALID_ARG;
+    if (!outputs_complete(det, out)) return CS_ERR_INVALID_ARG;
     if (!compatible(atm, det) || !lv1_valid(o)) return CS_ERR_INVALID_ARG;
     if (n > (size_t)1 << 40) return CS_ERR_INVALID_ARG;
     return CS_OK;
@@ -1174,13 +1254,10 @@ cs_status enqueue(const cs_segment* segs, size_t n, const cs_atmosphere* atm, co
                   uint64_t seed, const int* d_bunch, const cs_opts& o, const cs_output* out, unsigned int* ctr,
                   unsigned int grid, cudaStream_t stream) {
     const DetParams& dp = det->p;
+    const OutParams op = out_params(out);
     if (!o.accumulate) {
-        if (out->hist) CS_CUDA_TRY(cudaMemsetAsync(out->hist, 0, (size_t)dp.n_showers * dp.nx * dp.ny * 8, stream));
-        if (out->tel_counts) CS_CUDA_TRY(cudaMemsetAsync(out->tel_counts, 0, (size_t)dp.n_showers * dp.n_tel * 8, stream));
-        if (out->tel_time) CS_CUDA_TRY(cudaMemsetAsync(out->tel_time, 0, (size_t)dp.n_showers * dp.n_tel * 8, stream));
-        CS_CUDA_TRY(cudaMemsetAsync(out->counters, 0, CS_N_COUNTERS * 8, stream));
-        if (out->record_count) CS_CUDA_TRY(cudaMemsetAsync(out->record_count, 0, 8, stream));
-        if (o.lv1_dropped) CS_CUDA_TRY(cudaMemsetAsync(o.lv1_dropped, 0, 8, stream));
+        cs_status z = zero_outputs(dp, op, o.lv1_dropped, stream);
+        if (z != CS_OK) return z;
     }
     if (n == 0) return CS_OK;
     PropParams pp;
@@ -1193,14 +1270,6 @@ cs_status enqueue(const cs_segment* segs, size_t n, const cs_atmosphere* atm, co
     pp.shower_bunch = d_bunch;
     pp.s_max = (float)o.s_max;
     set_lv1(pp, o);
-    OutParams op;
-    op.hist = (unsigned long long*)out->hist;
-    op.tel_counts = (unsigned long long*)out->tel_counts;
-    op.tel_time = out->tel_time;
-    op.counters = (unsigned long long*)out->counters;
-    op.records = out->records;
-    op.record_capacity = out->records ? out->record_capacity : 0;
-    op.record_count = (unsigned long long*)out->record_count;
     CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), stream));
     return launch_kernel(grid, stream, pp, atm->p, dp, op, ctr, o.surrogate);
 }

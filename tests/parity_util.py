@@ -72,6 +72,9 @@ def compare(gpu, orc, bunch=1, shower_of_seg=None, pos_rel=POS_REL, t_rel=T_REL,
     assert not bin_bad.any(), "bin mismatch outside the edge band: %r / %r" % (G[bin_bad][:3], O[bin_bad][:3])
     tel_bad = landed & (G["tel"] != O["tel"]) & ((fl & (oracle.FL_TEL_EDGE | oracle.FL_LAYER)) == 0)
     assert not tel_bad.any(), "telescope mismatch outside the edge band: %r / %r" % (G[tel_bad][:3], O[tel_bad][:3])
+    # camera pixels (-1 on both sides without optics); rim and pixel edges carry the telescope flag
+    pix_bad = landed & (G["pix"] != O["pix"]) & ((fl & (oracle.FL_TEL_EDGE | oracle.FL_LAYER)) == 0)
+    assert not pix_bad.any(), "camera pixel mismatch outside the edge band: %r / %r" % (G[pix_bad][:3], O[pix_bad][:3])
 
     # aggregates equal the records they summarise (the GPU's counts are its records')
     if check_hist and "hist" in gpu and gpu["hist"].size:
@@ -81,11 +84,21 @@ def compare(gpu, orc, bunch=1, shower_of_seg=None, pos_rel=POS_REL, t_rel=T_REL,
         showers = np.zeros(m.sum(), np.int64) if sh is None else np.asarray(sh, np.int64)[g["seg"][m].astype(np.int64)]
         np.add.at(h.reshape(h.shape[0], -1), (showers, g["bin"][m]), bunch)
         assert np.array_equal(h, gpu["hist"]), "GPU histogram differs from its records"
+    cam = gpu.get("camera")
+    if check_hist and cam is not None and cam.size:
+        c = np.zeros_like(cam)
+        m = g["pix"] >= 0
+        sh = shower_of_seg
+        showers = np.zeros(m.sum(), np.int64) if sh is None else np.asarray(sh, np.int64)[g["seg"][m].astype(np.int64)]
+        np.add.at(c.reshape(cam.shape[0], cam.shape[1], -1), (showers, g["tel"][m], g["pix"][m]), bunch)
+        assert np.array_equal(c, cam), "GPU camera images differ from their records"
     n_diff_bins = int(((G["bin"] != O["bin"]) & landed).sum())
     n_diff_tel = int(((G["tel"] != O["tel"]) & landed).sum())
     return dict(matched=len(common), flagged=int((fl != 0).sum()), only_gpu=len(only_g), only_oracle=len(only_o),
                 max_pos_rel=max_pos, max_t_rel=max_t, max_abs_pos=float(abs_pos[prop].max(initial=0.0)),
-                status_flips=int((~same_status).sum()), bin_flips=n_diff_bins, tel_flips=n_diff_tel)
+                status_flips=int((~same_status).sum()), bin_flips=n_diff_bins, tel_flips=n_diff_tel,
+                pix_flips=int(((G["pix"] != O["pix"]) & landed).sum()),
+                pix_hits=int((landed & (G["pix"] >= 0) & (G["pix"] == O["pix"]) & (fl == 0)).sum()))
 
 
 def check_conservation(c):
