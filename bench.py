@@ -46,7 +46,7 @@ LANES_PER_SM = 128
 def kernel_sources_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("propagate.cu", "device_math.cuh", "common.cuh", "mlp_common.cuh"):
+    for f in ("propagate.cu", "device_math.cuh", "common.cuh", "mlp_common.cuh", "mlp_tc.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2405_04229_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
