@@ -21,9 +21,10 @@ _LIB = os.path.join(_LIB_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-ST_LANDED, ST_UPWARD, ST_BELOW, ST_DOMAIN, ST_ABSORBED, ST_SUBSTEP_FLAG = range(6)
-FL_COUNT, FL_ABSORB, FL_HIST_EDGE, FL_TEL_EDGE, FL_DOMAIN, FL_BELOW, FL_UPWARD, FL_LAYER, FL_LV1 = (
-    1, 2, 4, 8, 16, 32, 64, 128, 256)
+ST_LANDED, ST_UPWARD, ST_BELOW, ST_DOMAIN, ST_ABSORBED, ST_LV3 = range(6)
+ST_SUBSTEP_FLAG = 15
+FL_COUNT, FL_ABSORB, FL_HIST_EDGE, FL_TEL_EDGE, FL_DOMAIN, FL_BELOW, FL_UPWARD, FL_LAYER, FL_LV1, FL_LV3 = (
+    1, 2, 4, 8, 16, 32, 64, 128, 256, 512)
 LV1_OFF, LV1_ARRAY_CENTRE, LV1_ARRAY_DISC, LV1_TELESCOPES = 0, 1, 2, 3
 ATM_LAYERED, ATM_LINEAR, ATM_HOMOGENEOUS, ATM_TABLE = 0, 1, 2, 3
 RHO_REF = 1.225e-3   # [g/cm^3]: the table kind's density is RHO_REF (n - 1) / kappa
@@ -67,7 +68,9 @@ class Config(C.Structure):
                 ("lv1_metric", C.c_int), ("pad3", C.c_int), ("lv1_a", C.c_double), ("lv1_b", C.c_double),
                 ("lv1_centre", C.c_double * 3), ("lv1_radius", C.c_double), ("band_lv1", C.c_double),
                 ("mirror_d", C.c_double), ("focal_f", C.c_double), ("camera_r", C.c_double),
-                ("point_zenith", C.c_double), ("point_azimuth", C.c_double), ("cam_n", C.c_int), ("pad4", C.c_int)]
+                ("point_zenith", C.c_double), ("point_azimuth", C.c_double), ("cam_n", C.c_int), ("pad4", C.c_int),
+                ("lv3", C.c_int), ("pad5", C.c_int), ("lv3_centre", C.c_double * 3), ("lv3_radius", C.c_double),
+                ("lv3_margin", C.c_double)]
 
 
 SEGMENT_DTYPE = np.dtype([("x0", "<f8"), ("y0", "<f8"), ("z0", "<f8"), ("t0", "<f8"),
@@ -262,7 +265,7 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
               refraction=False, transmission=False, use_domain=None, w_max=None, seed=0,
               seg_base=0, n_showers=1, hist=None, tel=None, records=True, record_capacity=None,
               transmission_params=None, bands=None, quad_rtol=1e-10, spherical=False, earth_radius=EARTH_RADIUS,
-              lv1=None, optics=None):
+              lv1=None, optics=None, lv3=None):
     """Run the oracle over ``segs`` (dict of columns or SEGMENT_DTYPE array).
 
     Returns a dict with hist [n_showers, ny, nx], tel_counts [n_showers, n_tel],
@@ -312,6 +315,11 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
         for i, v in enumerate(lv1.get("centre", (0.0, 0.0, h_obs))):
             cfg.lv1_centre[i] = v
         cfg.lv1_radius, cfg.band_lv1 = lv1.get("radius", 0.0), lv1.get("band", 1e-4)
+    if lv3:   # dict(centre=(x, y, z), radius, margin)
+        cfg.lv3 = 1
+        for i, v in enumerate(lv3.get("centre", (0.0, 0.0, h_obs))):
+            cfg.lv3_centre[i] = v
+        cfg.lv3_radius, cfg.lv3_margin = lv3["radius"], lv3.get("margin", 0.0)
     if optics:   # dict(mirror_d, focal_f, camera_r, point_zenith, point_azimuth [rad], cam_n)
         for k in ("mirror_d", "focal_f", "camera_r", "point_zenith", "point_azimuth", "cam_n"):
             setattr(cfg, k, optics[k])

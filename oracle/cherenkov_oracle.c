@@ -669,12 +669,20 @@ typedef struct {
     double mirror_d, focal_f, camera_r, point_zenith, point_azimuth;
     int cam_n;
     int pad4;
+    /* LV3 photon pre-filter (Sec. 4.3.4, 6.2.2): before the refraction correction a
+     * photon is dropped when its vacuum straight line lands farther than
+     * lv3_radius + lv3_margin from lv3_centre (3-D distance in the frame) */
+    int lv3;
+    int pad5;
+    double lv3_centre[3];
+    double lv3_radius, lv3_margin;
 } orc_config;
 
 enum { ORC_ST_LANDED = 0, ORC_ST_UPWARD = 1, ORC_ST_BELOW = 2, ORC_ST_DOMAIN = 3,
-       ORC_ST_ABSORBED = 4, ORC_ST_SUBSTEP_FLAG = 5 };
+       ORC_ST_ABSORBED = 4, ORC_ST_LV3 = 5, ORC_ST_SUBSTEP_FLAG = 15 };
 enum { ORC_FL_COUNT = 1, ORC_FL_ABSORB = 2, ORC_FL_HIST_EDGE = 4, ORC_FL_TEL_EDGE = 8,
-       ORC_FL_DOMAIN = 16, ORC_FL_BELOW = 32, ORC_FL_UPWARD = 64, ORC_FL_LAYER = 128, ORC_FL_LV1 = 256 };
+       ORC_FL_DOMAIN = 16, ORC_FL_BELOW = 32, ORC_FL_UPWARD = 64, ORC_FL_LAYER = 128, ORC_FL_LV1 = 256,
+       ORC_FL_LV3 = 512 };
 
 typedef struct {
     uint64_t seg;
@@ -1020,6 +1028,34 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                     orc_push(out, &rec);
                     continue;
                 }
+                /* LV3 photon pre-filter (Sec. 4.3.4, 6.2.2): the vacuum straight line's
+                 * landing point S decides, before any correction is looked up */
+                if (cfg->lv3) {
+                    double S[3];
+                    if (!cfg->spherical) {
+                        const double t = (h_e - cfg->h_obs) / cos_z;
+                        S[0] = E[0] + t * u[0]; S[1] = E[1] + t * u[1]; S[2] = cfg->h_obs;
+                    } else {   /* first crossing of |E + t u - (0, 0, -R)| = R + h_obs */
+                        const double d[3] = { E[0], E[1], E[2] + R }, rg = R + cfg->h_obs;
+                        const double b = d[0] * u[0] + d[1] * u[1] + d[2] * u[2];
+                        const double c = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] - rg * rg;
+                        const double disc = b * b - c;
+                        if (disc < 0.0) rec.flags |= ORC_FL_LV3;   /* the line passes over the ground */
+                        const double t = -b - sqrt(fmax(disc, 0.0));
+                        for (int c3 = 0; c3 < 3; ++c3) S[c3] = E[c3] + t * u[c3];
+                    }
+                    const double dx = S[0] - cfg->lv3_centre[0], dy = S[1] - cfg->lv3_centre[1],
+                                 dz = S[2] - cfg->lv3_centre[2];
+                    const double dist = sqrt(dx * dx + dy * dy + dz * dz), lim = cfg->lv3_radius + cfg->lv3_margin;
+                    if (fabs(dist - lim) < cfg->band_pos) rec.flags |= ORC_FL_LV3;
+                    if (dist > lim) {
+                        rec.status = ORC_ST_LV3;
+                        out->counters[4] += cfg->bunch; out->counters[5] += cfg->bunch;
+                        orc_push(out, &rec);
+                        continue;
+                    }
+                }
+
                 /* horizontal unit of u in the local frame (the plane of travel) */
                 double hv[3] = { u[0] + cos_z * vloc[0], u[1] + cos_z * vloc[1], u[2] + cos_z * vloc[2] };
                 double hn = sqrt(hv[0] * hv[0] + hv[1] * hv[1] + hv[2] * hv[2]);
