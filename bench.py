@@ -420,6 +420,7 @@ def run_inclined(args):
     counters = [int(x) for x in outs.counters.cpu()]
     tel_full = int(outs.tel_counts.sum().item())
     hist_full = int(outs.hist.sum().item())
+    tel_ref, hist_ref = outs.tel_counts.clone(), outs.hist.clone()
 
     # LV1 particle filter (Sec. 4.3.2, 6.2.1): cut fitted on a labelled sample of chunk 0
     lv1_res = None
@@ -455,6 +456,51 @@ def run_inclined(args):
                    "telescope_count_retention": int(outs.tel_counts.sum().item()) / max(tel_full, 1),
                    "histogram_count_retention": int(outs.hist.sum().item()) / max(hist_full, 1)}
         o.lv1_metric, o.lv1_dropped = B.CS_LV1_OFF, None
+
+    # LV3 photon pre-filter (Sec. 4.3.4, 6.2.2): photons whose straight line lands outside
+    # the disc holding the array and the histogram, widened by a margin for the refraction
+    # correction, skip the lookups, the transmission and the detection.  The margin is the
+    # largest correction displacement seen on a sample (same photons with refraction on and
+    # off) with 50 % headroom; the detector counts over the whole workload must not change.
+    lv3_res = None
+    if args.lv3:
+        n_lab = min(chunk, 200_000)
+        atm_line = B.Atmosphere(layered=synth.US_STANDARD, refraction=False, transmission=True, spherical=True)
+        ol = B.cs_opts_default()
+        ol.bunch, ol.device_ptrs = bunch, 1
+        recs = []
+        for a in (atm, atm_line):
+            lab_out = B.DeviceOutputs(det, record_capacity=60 * n_lab)
+            st = B.cs_propagate_ex(C.c_void_p(base_ptr), n_lab, a.handle, det.handle, args.seed, ol, lab_out.out, sp)
+            if st != B.CS_OK:
+                raise B.CSError(st, "cs_propagate_ex(sample)")
+            recs.append(lab_out.host()["records"])
+            del lab_out
+        atm_line.close()
+        key = [(r["seg"].astype(np.int64) << 24) | (r["k"].astype(np.int64) << 12) | r["i"].astype(np.int64)
+               for r in recs]
+        _, ia, ib = np.intersect1d(key[0], key[1], assume_unique=True, return_indices=True)
+        ra, rb = recs[0][ia], recs[1][ib]
+        both = np.isin(ra["status"], [B.CS_ST_LANDED, B.CS_ST_ABSORBED]) & \
+            np.isin(rb["status"], [B.CS_ST_LANDED, B.CS_ST_ABSORBED])
+        shift = float(np.hypot(ra["x"].astype(np.float64) - rb["x"], ra["y"].astype(np.float64) - rb["y"])[both].max())
+        radius, margin = 1000.0 * math.sqrt(2.0) + 6.0, 1.5 * shift + 1.0
+        straight = np.hypot(rb["x"].astype(np.float64), rb["y"].astype(np.float64))
+        B.set_lv3(o, dict(centre=(0.0, 0.0, 2000.0), radius=radius, margin=margin))
+        step()
+        torch.cuda.synchronize()
+        f_ms = timed(args.steps, step)
+        lv3_res = {"metric": "straight-line landing point against a disc about the array centre",
+                   "radius_m": radius, "margin_m": margin, "largest_correction_shift_m": shift,
+                   "sample_segments": n_lab,
+                   "dropped_photon_fraction_in_sample": float(((straight > radius + margin) & both).sum()) /
+                   max(int(np.isin(rb["status"], [B.CS_ST_LANDED, B.CS_ST_ABSORBED]).sum()), 1),
+                   "ms_per_step": f_ms / args.steps,
+                   "equivalent_photons_per_s": photons * args.steps / (f_ms / 1e3),
+                   "speedup": ms / f_ms,
+                   "telescope_counts_unchanged": bool(torch.equal(outs.tel_counts, tel_ref)),
+                   "histogram_counts_unchanged": bool(torch.equal(outs.hist, hist_ref))}
+        o.lv3 = 0
 
     # end to end: pinned host segments streamed through the library's two-stream
     # double buffer, outputs read back every step
@@ -529,7 +575,7 @@ def run_inclined(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": None,
                          "note": "per chunk launch; spherical lane-op count per bunch %d" % OPS_PER_BUNCH_SPHERICAL},
-            "kernel_ms": k_ms, "cpu_baseline": cpu, "surrogate": surrogate, "e2e": e2e, "lv1_filter": lv1_res,
+            "kernel_ms": k_ms, "cpu_baseline": cpu, "surrogate": surrogate, "e2e": e2e, "lv1_filter": lv1_res, "lv3_filter": lv3_res,
             "gpu_launches": args.steps * n_chunks, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
@@ -581,6 +627,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=10_000_000)
     ap.add_argument("--chunks", type=int, default=10)
     ap.add_argument("--lv1", action="store_true", help="inclined: also time the LV1 particle filter")
+    ap.add_argument("--lv3", action="store_true", help="inclined: also time the LV3 photon pre-filter")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--per-shower", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -191,7 +191,7 @@ enum {
 };
 /* Conservation: emitted = absorbed + hist + missed_hist = absorbed + tel + missed_tel. */
 
-enum { CS_ST_LANDED = 0, CS_ST_UPWARD = 1, CS_ST_BELOW = 2, CS_ST_DOMAIN = 3, CS_ST_ABSORBED = 4 };
+enum { CS_ST_LANDED = 0, CS_ST_UPWARD = 1, CS_ST_BELOW = 2, CS_ST_DOMAIN = 3, CS_ST_ABSORBED = 4, CS_ST_LV3 = 5 };
 
 /* Optional per-bunch record (parity mode), 48 bytes.  Records are written in
  * no particular order; (seg, k, i) identifies a bunch uniquely. */
@@ -245,6 +245,16 @@ typedef struct cs_opts {
     double lv1_radius;       /* disc radius [m] (disc metric) */
     uint64_t* lv1_dropped;   /* NULL or one counter in the outputs' memory kind: dropped segments are
                                 added (zeroed first unless accumulate) */
+    /* LV3 photon pre-filter (Sec. 4.3.4, 6.2.2): after the straight line and before the
+     * refraction correction, a photon whose vacuum straight line lands farther than
+     * lv3_radius + lv3_margin from lv3_centre (3-D distance, frame coordinates; on the
+     * plane the landing point lies at h_obs) is dropped: status CS_ST_LV3, counted as
+     * missed by the histogram and the telescopes, no lookup, transmission or detection.
+     * Detector counts are unchanged when the disc holds the histogram and the telescope
+     * spheres and the margin covers the largest correction displacement. */
+    int lv3;                 /* 0 (default) off, 1 on */
+    double lv3_centre[3];
+    double lv3_radius, lv3_margin;   /* >= 0 [m] */
 } cs_opts;
 
 /* The LV1 filter's point of interest: x is the angle from the segment's

@@ -32,10 +32,20 @@ def set_lv1(o, lv1):
     for i, v in enumerate(lv1.get("centre", (0.0, 0.0, 0.0))):
         o.lv1_centre[i] = v
     o.lv1_radius = lv1.get("radius", 0.0)
+
+
+def set_lv3(o, lv3):
+    """Fill the LV3 photon pre-filter fields of a cs_opts from dict(centre, radius, margin)."""
+    if not lv3:
+        return
+    o.lv3 = 1
+    for i, v in enumerate(lv3["centre"]):
+        o.lv3_centre[i] = v
+    o.lv3_radius, o.lv3_margin = lv3["radius"], lv3.get("margin", 0.0)
 (CS_CNT_EMITTED, CS_CNT_ABSORBED, CS_CNT_HIST, CS_CNT_TEL, CS_CNT_MISSED_HIST, CS_CNT_MISSED_TEL,
  CS_CNT_UPWARD, CS_CNT_INVALID_SEGMENTS) = range(8)
 CS_N_COUNTERS = 8
-CS_ST_LANDED, CS_ST_UPWARD, CS_ST_BELOW, CS_ST_DOMAIN, CS_ST_ABSORBED = range(5)
+CS_ST_LANDED, CS_ST_UPWARD, CS_ST_BELOW, CS_ST_DOMAIN, CS_ST_ABSORBED, CS_ST_LV3 = range(6)
 
 
 class CSError(RuntimeError):
@@ -114,7 +124,9 @@ class cs_opts(C.Structure):
                 ("device_ptrs", C.c_int), ("accumulate", C.c_int), ("block_threads", C.c_int),
                 ("blocks_per_sm", C.c_int), ("surrogate", C.c_void_p),
                 ("lv1_metric", C.c_int), ("lv1_a", C.c_double), ("lv1_b", C.c_double),
-                ("lv1_centre", C.c_double * 3), ("lv1_radius", C.c_double), ("lv1_dropped", C.c_void_p)]
+                ("lv1_centre", C.c_double * 3), ("lv1_radius", C.c_double), ("lv1_dropped", C.c_void_p),
+                ("lv3", C.c_int), ("lv3_centre", C.c_double * 3), ("lv3_radius", C.c_double),
+                ("lv3_margin", C.c_double)]
 
 
 def lib():
@@ -410,7 +422,7 @@ class Detector:
 
 
 def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=1.0, seg_base=0,
-                   records=False, record_capacity=None, blocks_per_sm=0, surrogate=None, lv1=None):
+                   records=False, record_capacity=None, blocks_per_sm=0, surrogate=None, lv1=None, lv3=None):
     """cs_propagate_ex with host numpy buffers; returns a dict of outputs."""
     arr = segs if isinstance(segs, np.ndarray) else pack_segments(segs)
     arr = np.ascontiguousarray(arr)
@@ -439,6 +451,7 @@ def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=
     if lv1:
         set_lv1(o, lv1)
         o.lv1_dropped = dropped.ctypes.data
+    set_lv3(o, lv3)
     st = cs_propagate_ex(_dptr(arr) if len(arr) else None, len(arr), atm.handle, det.handle, seed, o, out)
     _check(st, "cs_propagate_ex")
     res = dict(hist=hist, tel_counts=tel_counts, tel_time=tel_time, counters=counters, n_records=int(rc[0]),
@@ -525,13 +538,14 @@ class Streamer:
         self.handle, self.chunk = h, chunk
 
     def run(self, host_segs_ptr, n, atm, det, out, seed=0, bunch=1, s_max=1.0, seg_base=0, accumulate=False,
-            surrogate=None, stream=None):
+            surrogate=None, stream=None, lv3=None):
         """host_segs_ptr: address of n packed segments in host memory; out: a
         cs_output of device pointers.  Enqueues on `stream` (default: torch's)."""
         o = cs_opts_default()
         o.bunch, o.s_max, o.seg_base, o.device_ptrs, o.accumulate = bunch, s_max, seg_base, 1, int(accumulate)
         if surrogate is not None:
             o.surrogate = surrogate.handle
+        set_lv3(o, lv3)
         _check(lib().cs_streamer_run(self.handle, C.c_void_p(host_segs_ptr), n, atm.handle, det.handle, seed,
                                      C.byref(o), C.byref(out), stream if stream is not None else stream_ptr()),
                "cs_streamer_run")

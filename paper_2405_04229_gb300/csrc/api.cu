@@ -80,4 +80,7 @@ extern "C" void cs_opts_default(cs_opts* o) {
     o->lv1_centre[0] = o->lv1_centre[1] = o->lv1_centre[2] = 0.0;
     o->lv1_radius = 0.0;
     o->lv1_dropped = nullptr;
+    o->lv3 = 0;
+    o->lv3_centre[0] = o->lv3_centre[1] = o->lv3_centre[2] = 0.0;
+    o->lv3_radius = o->lv3_margin = 0.0;
 }

@@ -121,6 +121,11 @@ struct PropParams {
     float lv1_a, lv1_b, lv1_r;
     float lv1_c[3];            // array centre, frame coordinates
     unsigned long long* lv1_dropped;   // device counter or null
+    // LV3 photon pre-filter: drop when the straight line lands farther than
+    // sqrt(lv3_r2) from lv3_c (planar: lv3_dz2 = (h_obs - centre z)^2)
+    int lv3;
+    float lv3_c[3];
+    float lv3_r2, lv3_dz2;
 };
 
 // The atmosphere in FP64, as the table builder integrates it.

@@ -515,8 +515,8 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
     // ---- propagation and detection -----------------------------------------------
     int tel = -1, bin = -1, pix = -1;
     float x = 0.0f, y = 0.0f, t_rel = ell * B.w;
+    float rx = 0.0f, ry = 0.0f;
     if (status == CS_ST_LANDED && !SPH) {
-        float rx, ry;
         if (Pz < -1e-3f) {
             // I - G = dz (P_xy / P_z - u_xy / u_z); the numerator is sin(theta) (P x m)
             const float pmx = Pz * sphi - ce * Py, pmy = ce * Px - Pz * cphi;
@@ -527,6 +527,13 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
             rx = ell * Px + dz * ux * inv_uz;
             ry = ell * Py + dz * uy * inv_uz;
         }
+        if (pp.lv3) {   // LV3 photon pre-filter (Sec. 4.3.4): the straight line's landing point
+            const float4 Cg = S.segC[sg];
+            const float sx = (Cg.x - pp.lv3_c[0]) + (Cg.y + rx), sy = (Cg.z - pp.lv3_c[1]) + (Cg.w + ry);
+            if (fmaf(sx, sx, fmaf(sy, sy, pp.lv3_dz2)) > pp.lv3_r2) status = CS_ST_LV3;
+        }
+    }
+    if (status == CS_ST_LANDED && !SPH) {
         float path = dz * inv_uz;
         float GR, Gt, Tr;
         correction_fields<SURR>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
@@ -604,8 +611,6 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
             }
         }
     } else if (status == CS_ST_LANDED) {
-        float GR, Gt, Tr;
-        correction_fields<SURR>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
         // vacuum straight line to the ground sphere r_g: length t with
         // t (r_e cos + sqrt(r_e^2 cos^2 - D)) = D, D = r_e^2 - r_g^2 = dz (r_e + r_g)
         const float rg = ap.rg, re = rg + dz;
@@ -616,77 +621,85 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
         float Gx = Cc.x + (Dd.x + fmaf(ell, Px, tt * ux));
         float Gy = Cc.y + (Dd.y + fmaf(ell, Py, tt * uy));
         float Gz = Cc.z + (Dd.z + fmaf(ell, Pz, tt * uz));
-        // ground tangent in the plane of travel at the landing point
-        const float irg = ap.inv_rg;
-        const float gvx = Gx * irg, gvy = Gy * irg, gvz = (Gz - h_obs_f) * irg;   // v_G - z-hat
-        const float uvG = ux * gvx + uy * gvy + uz * (1.0f + gvz);
-        float tx = ux - uvG * gvx, ty = uy - uvG * gvy, tz = uz - uvG * (1.0f + gvz);
-        const float tn = rsqrtf(fmaxf(tx * tx + ty * ty + tz * tz, 1e-30f));
-        tx *= tn;
-        ty *= tn;
-        tz *= tn;
-        float path = tt;
-        if (ap.refraction) {   // arc-length correction along the ground, delay
-            const float dR = GR * inv_uz * inv_uz * inv_uz * sqrtf(sin2);
-            Gx = fmaf(dR, tx, Gx);
-            Gy = fmaf(dR, ty, Gy);
-            Gz = fmaf(dR, tz, Gz);
-            path = fmaf(Gt, inv_uz, path);
+        if (pp.lv3) {   // LV3 photon pre-filter (Sec. 4.3.4): the straight line's landing point
+            const float sx = Gx - pp.lv3_c[0], sy = Gy - pp.lv3_c[1], sz = Gz - pp.lv3_c[2];
+            if (fmaf(sx, sx, fmaf(sy, sy, sz * sz)) > pp.lv3_r2) status = CS_ST_LV3;
         }
-        t_rel = fmaf(path, kInvC, t_rel);
-        // azimuthal-equidistant coordinates: r_g atan(rho / z_c) along (G_x, G_y)
-        const float zc = rg + (Gz - h_obs_f);
-        const float iz = 1.0f / zc;
-        const float X2 = (Gx * Gx + Gy * Gy) * iz * iz;
-        const float fac = rg * iz * fmaf(X2, fmaf(X2, 0.2f, -1.0f / 3.0f), 1.0f);
-        x = Gx * fac;
-        y = Gy * fac;
-        if (ap.transmission && !(u3 < Tr)) {
-            status = CS_ST_ABSORBED;
-        } else {
-            const int sh = S.shower[sg];
-            if (dp.nx > 0) {
-                const int ix = (int)floorf(((x - dp.hx0_hi) - dp.hx0_lo) * dp.inv_dx);
-                const int iy = (int)floorf(((y - dp.hy0_hi) - dp.hy0_lo) * dp.inv_dy);
-                if (ix >= 0 && ix < dp.nx && iy >= 0 && iy < dp.ny) {
-                    bin = iy * dp.nx + ix;
-                    hist_add(op, (unsigned int)(sh * dp.ny * dp.nx + bin), b);
-                }
+        if (status == CS_ST_LANDED) {
+            float GR, Gt, Tr;
+            correction_fields<SURR>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
+            // ground tangent in the plane of travel at the landing point
+            const float irg = ap.inv_rg;
+            const float gvx = Gx * irg, gvy = Gy * irg, gvz = (Gz - h_obs_f) * irg;   // v_G - z-hat
+            const float uvG = ux * gvx + uy * gvy + uz * (1.0f + gvz);
+            float tx = ux - uvG * gvx, ty = uy - uvG * gvy, tz = uz - uvG * (1.0f + gvz);
+            const float tn = rsqrtf(fmaxf(tx * tx + ty * ty + tz * tz, 1e-30f));
+            tx *= tn;
+            ty *= tn;
+            tz *= tn;
+            float path = tt;
+            if (ap.refraction) {   // arc-length correction along the ground, delay
+                const float dR = GR * inv_uz * inv_uz * inv_uz * sqrtf(sin2);
+                Gx = fmaf(dR, tx, Gx);
+                Gy = fmaf(dR, ty, Gy);
+                Gz = fmaf(dR, tz, Gz);
+                path = fmaf(Gt, inv_uz, path);
             }
-            if (dp.n_tel > 0) {
-                float ugx = ux, ugy = uy, ugz = uz;
-                if (ap.refraction) {   // Bouguer: n r sin(psi) conserved in the plane of travel
-                    const float sin_g = (1.0f + Q.z) * ap.inv_n_obs * re * irg * sqrtf(sin2);
-                    const float cos_g = sqrtf(fmaxf(1.0f - sin_g * sin_g, 0.0f));
-                    ugx = -cos_g * gvx + sin_g * tx;
-                    ugy = -cos_g * gvy + sin_g * ty;
-                    ugz = -cos_g * (1.0f + gvz) + sin_g * tz;
-                }
-                const bool hashed = ugx * ugx + ugy * ugy <= dp.hash_sin2_max;
-                if (!hashed || (x >= dp.bx0 && x < dp.bx1 && y >= dp.by0 && y < dp.by1)) {
-                    auto delta3 = [&](const float4& T3, float& ddx, float& ddy, float& ddz) {
-                        ddx = T3.x - Gx;
-                        ddy = T3.y - Gy;
-                        ddz = T3.z - Gz;
-                    };
-                    tel = hit_telescope(
-                        dp, hashed, x, y, ugx, ugy, ugz,
-                        [&](const float4& D, float, float, float& ddx, float& ddy, float& ddz) { delta3(D, ddx, ddy, ddz); },
-                        [&](int it, float& ddx, float& ddy, float& ddz, float& r) {
-                            const float4 T3 = __ldg(dp.tel3 + it);
-                            delta3(T3, ddx, ddy, ddz);
-                            r = T3.w;
-                        });
-                    if (tel >= 0 && dp.cam_n > 0) {
-                        const float4 T3 = __ldg(dp.tel3 + tel);
-                        pix = camera_pixel(dp, T3.x - Gx, T3.y - Gy, T3.z - Gz, ugx, ugy, ugz);
+            t_rel = fmaf(path, kInvC, t_rel);
+            // azimuthal-equidistant coordinates: r_g atan(rho / z_c) along (G_x, G_y)
+            const float zc = rg + (Gz - h_obs_f);
+            const float iz = 1.0f / zc;
+            const float X2 = (Gx * Gx + Gy * Gy) * iz * iz;
+            const float fac = rg * iz * fmaf(X2, fmaf(X2, 0.2f, -1.0f / 3.0f), 1.0f);
+            x = Gx * fac;
+            y = Gy * fac;
+            if (ap.transmission && !(u3 < Tr)) {
+                status = CS_ST_ABSORBED;
+            } else {
+                const int sh = S.shower[sg];
+                if (dp.nx > 0) {
+                    const int ix = (int)floorf(((x - dp.hx0_hi) - dp.hx0_lo) * dp.inv_dx);
+                    const int iy = (int)floorf(((y - dp.hy0_hi) - dp.hy0_lo) * dp.inv_dy);
+                    if (ix >= 0 && ix < dp.nx && iy >= 0 && iy < dp.ny) {
+                        bin = iy * dp.nx + ix;
+                        hist_add(op, (unsigned int)(sh * dp.ny * dp.nx + bin), b);
                     }
                 }
-                if (tel >= 0) {
-                    const size_t slot = (size_t)sh * dp.n_tel + tel;
-                    atomicAdd(op.tel_counts + slot, (unsigned long long)b);
-                    if (op.tel_time) atomicAdd(op.tel_time + slot, (double)b * (S.t0[sg] + (double)t_rel));
-                    if (pix >= 0) atomicAdd(op.camera + (slot * dp.cam_n * dp.cam_n + pix), (unsigned long long)b);
+                if (dp.n_tel > 0) {
+                    float ugx = ux, ugy = uy, ugz = uz;
+                    if (ap.refraction) {   // Bouguer: n r sin(psi) conserved in the plane of travel
+                        const float sin_g = (1.0f + Q.z) * ap.inv_n_obs * re * irg * sqrtf(sin2);
+                        const float cos_g = sqrtf(fmaxf(1.0f - sin_g * sin_g, 0.0f));
+                        ugx = -cos_g * gvx + sin_g * tx;
+                        ugy = -cos_g * gvy + sin_g * ty;
+                        ugz = -cos_g * (1.0f + gvz) + sin_g * tz;
+                    }
+                    const bool hashed = ugx * ugx + ugy * ugy <= dp.hash_sin2_max;
+                    if (!hashed || (x >= dp.bx0 && x < dp.bx1 && y >= dp.by0 && y < dp.by1)) {
+                        auto delta3 = [&](const float4& T3, float& ddx, float& ddy, float& ddz) {
+                            ddx = T3.x - Gx;
+                            ddy = T3.y - Gy;
+                            ddz = T3.z - Gz;
+                        };
+                        tel = hit_telescope(
+                            dp, hashed, x, y, ugx, ugy, ugz,
+                            [&](const float4& D, float, float, float& ddx, float& ddy, float& ddz) { delta3(D, ddx, ddy, ddz); },
+                            [&](int it, float& ddx, float& ddy, float& ddz, float& r) {
+                                const float4 T3 = __ldg(dp.tel3 + it);
+                                delta3(T3, ddx, ddy, ddz);
+                                r = T3.w;
+                            });
+                        if (tel >= 0 && dp.cam_n > 0) {
+                            const float4 T3 = __ldg(dp.tel3 + tel);
+                            pix = camera_pixel(dp, T3.x - Gx, T3.y - Gy, T3.z - Gz, ugx, ugy, ugz);
+                        }
+                    }
+                    if (tel >= 0) {
+                        const size_t slot = (size_t)sh * dp.n_tel + tel;
+                        atomicAdd(op.tel_counts + slot, (unsigned long long)b);
+                        if (op.tel_time) atomicAdd(op.tel_time + slot, (double)b * (S.t0[sg] + (double)t_rel));
+                        if (pix >= 0) atomicAdd(op.camera + (slot * dp.cam_n * dp.cam_n + pix), (unsigned long long)b);
+                    }
                 }
             }
         }
@@ -918,7 +931,12 @@ cs_status tile_counter(unsigned int** out) {
 }
 
 // The LV1 filter's parameters from the options (the counter as given: device memory here).
-void set_lv1(PropParams& pp, const cs_opts& o) {
+void set_filters(PropParams& pp, const cs_opts& o, const DetParams& dp) {
+    pp.lv3 = o.lv3 ? 1 : 0;
+    for (int i = 0; i < 3; ++i) pp.lv3_c[i] = (float)o.lv3_centre[i];
+    const double lim = o.lv3_radius + o.lv3_margin;
+    pp.lv3_r2 = (float)(lim * lim);
+    pp.lv3_dz2 = (float)((dp.h_obs - o.lv3_centre[2]) * (dp.h_obs - o.lv3_centre[2]));
     pp.lv1 = o.lv1_metric;
     pp.lv1_a = (float)o.lv1_a;
     pp.lv1_b = (float)o.lv1_b;
@@ -927,7 +945,10 @@ void set_lv1(PropParams& pp, const cs_opts& o) {
     pp.lv1_dropped = (unsigned long long*)o.lv1_dropped;
 }
 
-bool lv1_valid(const cs_opts& o) {
+bool filters_valid(const cs_opts& o) {
+    if (o.lv3 && !(o.lv3_radius >= 0.0 && o.lv3_margin >= 0.0 && isfinite(o.lv3_radius + o.lv3_margin) &&
+                   isfinite(o.lv3_centre[0]) && isfinite(o.lv3_centre[1]) && isfinite(o.lv3_centre[2])))
+        return false;
     return o.lv1_metric >= CS_LV1_OFF && o.lv1_metric <= CS_LV1_TELESCOPES &&
            (o.lv1_metric == CS_LV1_OFF || (isfinite(o.lv1_a) && isfinite(o.lv1_b) && o.lv1_radius >= 0.0));
 }
@@ -986,7 +1007,7 @@ cs_status launch(const cs_segment* d_segs, size_t n, const cs_atmosphere* atm, c
     pp.bunch = o.bunch;
     pp.shower_bunch = nullptr;
     pp.s_max = (float)o.s_max;
-    set_lv1(pp, o);
+    set_filters(pp, o, det->p);
     static bool attr_done = false;
     if (!attr_done) {
         cs_status sa = set_smem_attributes();
@@ -1016,7 +1037,7 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
     if (opts) o = *opts; else cs_opts_default(&o);
     if (o.bunch < 1 || !(o.s_max > 0.0) || (n > 0 && !segs)) return CS_ERR_INVALID_ARG;
     if (!outputs_complete(det, out)) return CS_ERR_INVALID_ARG;
-    if (!compatible(atm, det) || !lv1_valid(o)) return CS_ERR_INVALID_ARG;
+    if (!compatible(atm, det) || !filters_valid(o)) return CS_ERR_INVALID_ARG;
     if (n > (size_t)1 << 40) return CS_ERR_INVALID_ARG;
     cudaStream_t stream = (cudaStream_t)stream_;
     const DetParams& dp = det->p;
@@ -1179,7 +1200,7 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     if (((uintptr_t)segs & 15) != 0) return CS_ERR_INVALID_ARG;
     if (det->p.nx > 0 && !out->hist) return CS_ERR_INVALID_ARG;
     if (!outputs_complete(det, out)) return CS_ERR_INVALID_ARG;
-    if (!compatible(atm, det) || !lv1_valid(o)) return CS_ERR_INVALID_ARG;
+    if (!compatible(atm, det) || !filters_valid(o)) return CS_ERR_INVALID_ARG;
     // the counter is 32 bits wide: reject inputs with more tiles than it can count
     if ((n + kTile - 1) / kTile >= 0xFFFFFFFFull - 65536ull) return CS_ERR_INVALID_ARG;
     cudaStream_t stream = (cudaStream_t)stream_;
@@ -1199,7 +1220,7 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     pp.bunch = o.bunch;
     pp.shower_bunch = nullptr;
     pp.s_max = (float)o.s_max;
-    set_lv1(pp, o);
+    set_filters(pp, o, det->p);
     if ((st = set_smem_attributes()) != CS_OK) return st;
     const int per_sm = default_blocks_per_sm(o);
     const long long tiles = ((long long)n + kTile - 1) / kTile;
@@ -1232,7 +1253,7 @@ cs_status check_device_call(const cs_segment* segs, size_t n, const cs_atmospher
     if (o.bunch < 1 || !(o.s_max > 0.0) || (n > 0 && !segs) || !o.device_ptrs) return CS_ERR_INVALID_ARG;
     if (((uintptr_t)segs & 15) != 0) return CS_ERR_INVALID_ARG;
     if (!outputs_complete(det, out)) return CS_ERR_INVALID_ARG;
-    if (!compatible(atm, det) || !lv1_valid(o)) return CS_ERR_INVALID_ARG;
+    if (!compatible(atm, det) || !filters_valid(o)) return CS_ERR_INVALID_ARG;
     if (n > (size_t)1 << 40) return CS_ERR_INVALID_ARG;
     return CS_OK;
 }
@@ -1269,7 +1290,7 @@ cs_status enqueue(const cs_segment* segs, size_t n, const cs_atmosphere* atm, co
     pp.bunch = o.bunch;
     pp.shower_bunch = d_bunch;
     pp.s_max = (float)o.s_max;
-    set_lv1(pp, o);
+    set_filters(pp, o, det->p);
     CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), stream));
     return launch_kernel(grid, stream, pp, atm->p, dp, op, ctr, o.surrogate);
 }

@@ -48,7 +48,8 @@ def compare(gpu, orc, bunch=1, shower_of_seg=None, pos_rel=POS_REL, t_rel=T_REL,
 
     G, O = g[ig], o[io]
     fl = O["flags"]
-    status_flags = oracle.FL_ABSORB | oracle.FL_DOMAIN | oracle.FL_BELOW | oracle.FL_UPWARD | oracle.FL_LAYER
+    status_flags = (oracle.FL_ABSORB | oracle.FL_DOMAIN | oracle.FL_BELOW | oracle.FL_UPWARD | oracle.FL_LAYER |
+                    oracle.FL_LV3)
     same_status = G["status"].astype(np.int64) == O["status"].astype(np.int64)
     bad = ~same_status & ((fl & status_flags) == 0)
     assert not bad.any(), "status mismatch: gpu %r oracle %r" % (G[bad][:3], O[bad][:3])
