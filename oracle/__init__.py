@@ -70,7 +70,7 @@ class Config(C.Structure):
                 ("mirror_d", C.c_double), ("focal_f", C.c_double), ("camera_r", C.c_double),
                 ("point_zenith", C.c_double), ("point_azimuth", C.c_double), ("cam_n", C.c_int), ("pad4", C.c_int),
                 ("lv3", C.c_int), ("pad5", C.c_int), ("lv3_centre", C.c_double * 3), ("lv3_radius", C.c_double),
-                ("lv3_margin", C.c_double)]
+                ("lv3_margin", C.c_double), ("tracer", C.c_int), ("pad6", C.c_int), ("tracer_dh", C.c_double)]
 
 
 SEGMENT_DTYPE = np.dtype([("x0", "<f8"), ("y0", "<f8"), ("z0", "<f8"), ("t0", "<f8"),
@@ -111,6 +111,7 @@ def lib():
             L.orc_refract_closed.argtypes = [C.POINTER(Atm), d, d, d, dp]
             L.orc_refract_closed.restype = C.c_int
             L.orc_snell_stepper.argtypes = [C.POINTER(Atm), d, d, d, d, dp]
+            L.orc_snell_path.argtypes = [C.POINTER(Atm), d, d, d, d, d, dp]
             L.orc_sph_path.argtypes = [C.POINTER(Atm), d, d, d, d, d, C.c_int, d, dp]
             L.orc_ae_inverse.argtypes = [d, d, d, d, d, dp]
             L.orc_propagate.argtypes = [C.c_void_p, C.c_size_t, C.POINTER(Atm), C.POINTER(Config),
@@ -215,6 +216,13 @@ def refract_closed(atm, h_obs, h_e, theta0):
     return np.array(out[:])
 
 
+def snell_path(atm, h_obs, h_e, theta0, dh, H_A=1200.0):
+    """{R, t_path, X_slant, A_slant} of the Snell vector stepper."""
+    out = (C.c_double * 4)()
+    lib().orc_snell_path(C.byref(atm), h_obs, h_e, theta0, dh, H_A, out)
+    return np.array(out[:])
+
+
 def snell_stepper(atm, h_obs, h_e, theta0, dh):
     out = (C.c_double * 2)()
     lib().orc_snell_stepper(C.byref(atm), h_obs, h_e, theta0, dh, out)
@@ -265,7 +273,7 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
               refraction=False, transmission=False, use_domain=None, w_max=None, seed=0,
               seg_base=0, n_showers=1, hist=None, tel=None, records=True, record_capacity=None,
               transmission_params=None, bands=None, quad_rtol=1e-10, spherical=False, earth_radius=EARTH_RADIUS,
-              lv1=None, optics=None, lv3=None):
+              lv1=None, optics=None, lv3=None, snell_dh=None):
     """Run the oracle over ``segs`` (dict of columns or SEGMENT_DTYPE array).
 
     Returns a dict with hist [n_showers, ny, nx], tel_counts [n_showers, n_tel],
@@ -315,6 +323,8 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
         for i, v in enumerate(lv1.get("centre", (0.0, 0.0, h_obs))):
             cfg.lv1_centre[i] = v
         cfg.lv1_radius, cfg.band_lv1 = lv1.get("radius", 0.0), lv1.get("band", 1e-4)
+    if snell_dh:   # refraction by the Snell vector stepper through slabs <= snell_dh [m]
+        cfg.tracer, cfg.tracer_dh = 1, snell_dh
     if lv3:   # dict(centre=(x, y, z), radius, margin)
         cfg.lv3 = 1
         for i, v in enumerate(lv3.get("centre", (0.0, 0.0, h_obs))):

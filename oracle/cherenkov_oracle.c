@@ -484,26 +484,32 @@ int orc_refract_closed(const orc_atm* a, double h_obs, double h_e, double theta0
 
 /* ------------------------------------------------------------------ */
 /* The thesis's numerical tracer: Snell's law in vector form at the   */
-/* boundaries of homogeneous slabs of thickness dh (Eq. 3.15).        */
-/* out = {R, t_path}.                                                 */
+/* boundaries of homogeneous slabs (Eq. 3.15).  The height range is   */
+/* cut into the fewest equal slabs no thicker than dh; slab j holds   */
+/* the index at its middle height; the photon crosses it straight and */
+/* refracts at its lower boundary.                                    */
+/* out = {R, t_path, X_slant [g/cm^2], A_slant [m]}.                  */
 /* ------------------------------------------------------------------ */
-void orc_snell_stepper(const orc_atm* a, double h_obs, double h_e, double theta0, double dh,
-                       double out[2])
+void orc_snell_path(const orc_atm* a, double h_obs, double h_e, double theta0, double dh, double H_A,
+                    double out[4])
 {
     /* 2-D: direction (horizontal, vertical); N = (0, -1) is the downward normal */
     double dir_x = sin(theta0), dir_z = -cos(theta0);
-    double h = h_e, x = 0.0, t = 0.0;
+    double x = 0.0, t = 0.0, X = 0.0, A = 0.0;
     int nsteps = (int)ceil((h_e - h_obs) / dh - 1e-9);
+    if (nsteps < 1) nsteps = 1;
     double step = (h_e - h_obs) / nsteps;
     double n1 = orc_n(a, h_e - 0.5 * step);
     for (int j = 0; j < nsteps; ++j) {
         /* straight through slab j with index n1 */
+        const double h_mid = h_e - (j + 0.5) * step;
         double path = step / (-dir_z);
         x += path * dir_x;
         t += path * n1 / ORC_C_LIGHT;
-        h -= step;
+        X += 100.0 * orc_atm_rho(a, h_mid) * path;
+        A += exp(-h_mid / H_A) * path;
         if (j + 1 == nsteps) break;
-        double n2 = orc_n(a, h - 0.5 * step);
+        double n2 = orc_n(a, h_mid - step);
         /* optical vectors A' = n A; A2' = A1' + (sqrt(n2^2 - n1^2 + n1^2 cos^2 a1) - n1 cos a1) N */
         double cos_a1 = -dir_z;                       /* A1 . N with N = (0, -1) */
         double c = sqrt(n2 * n2 - n1 * n1 + n1 * n1 * cos_a1 * cos_a1) - n1 * cos_a1;
@@ -511,7 +517,16 @@ void orc_snell_stepper(const orc_atm* a, double h_obs, double h_e, double theta0
         dir_x = Ax / n2; dir_z = Az / n2;
         n1 = n2;
     }
-    out[0] = x; out[1] = t;
+    out[0] = x; out[1] = t; out[2] = X; out[3] = A;
+}
+
+/* {R, t_path} of the stepper (the pins' entry point). */
+void orc_snell_stepper(const orc_atm* a, double h_obs, double h_e, double theta0, double dh,
+                       double out[2])
+{
+    double o4[4];
+    orc_snell_path(a, h_obs, h_e, theta0, dh, 1200.0, o4);
+    out[0] = o4[0]; out[1] = o4[1];
 }
 
 /* ------------------------------------------------------------------ */
@@ -676,6 +691,11 @@ typedef struct {
     int pad5;
     double lv3_centre[3];
     double lv3_radius, lv3_margin;
+    /* propagation method with refraction on: 0 the exact path (quadrature), 1 the Snell
+     * vector stepper (Sec. 3.4.2, Eq. 3.15) through slabs no thicker than tracer_dh */
+    int tracer;
+    int pad6;
+    double tracer_dh;
 } orc_config;
 
 enum { ORC_ST_LANDED = 0, ORC_ST_UPWARD = 1, ORC_ST_BELOW = 2, ORC_ST_DOMAIN = 3,
@@ -1064,8 +1084,28 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
 
                 double path[4], G3[3], ug[3], gx, gy;
                 if (!cfg->spherical) {
-                    if (cfg->refraction) orc_refract_quad(atm, cfg->h_obs, h_e, theta0, cfg->aer_H, cfg->quad_rtol, path);
-                    else orc_straight(atm, cfg->h_obs, h_e, theta0, cfg->aer_H, path);
+                    if (cfg->refraction && cfg->tracer == 1) {
+                        orc_snell_path(atm, cfg->h_obs, h_e, theta0, cfg->tracer_dh, cfg->aer_H, path);
+                        /* the slab count and the slab holding a jump of n are decisions too */
+                        const double q = (h_e - cfg->h_obs) / cfg->tracer_dh;
+                        if (fabs(q - nearbyint(q)) < 1e-3) rec.flags |= ORC_FL_LAYER;
+                        int ns = (int)ceil(q - 1e-9); if (ns < 1) ns = 1;
+                        const double step = (h_e - cfg->h_obs) / ns;
+                        double jumps[9]; int nj = 0;
+                        if (atm->kind == ORC_ATM_LAYERED) {
+                            for (int li = 1; li < atm->n_layers; ++li) jumps[nj++] = atm->layer_h[li];
+                            jumps[nj++] = atm->h_top;
+                        }
+                        for (int k2 = 0; k2 < nj; ++k2) {
+                            if (!(jumps[k2] > cfg->h_obs && jumps[k2] < h_e)) continue;
+                            const double f = (h_e - jumps[k2]) / step - 0.5;   /* midpoints at integer f */
+                            if (fabs(f - nearbyint(f)) * step < 0.01) rec.flags |= ORC_FL_LAYER;
+                        }
+                    } else if (cfg->refraction) {
+                        orc_refract_quad(atm, cfg->h_obs, h_e, theta0, cfg->aer_H, cfg->quad_rtol, path);
+                    } else {
+                        orc_straight(atm, cfg->h_obs, h_e, theta0, cfg->aer_H, path);
+                    }
                     /* ground point: E_xy + R along the horizontal unit of u */
                     gx = E[0] + path[0] * hv[0];
                     gy = E[1] + path[0] * hv[1];
