@@ -634,6 +634,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-optics", action="store_true")
+    ap.add_argument("--no-snell", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -808,6 +809,30 @@ def main():
         out.camera = None
         det_o.close()
 
+    snell = None
+    if not args.no_snell:
+        # the general-atmosphere fallback: every photon traced through 10 m slabs with the
+        # Snell vector stepper (Sec. 3.4.2, Eq. 3.15) instead of the table lookup; the thesis
+        # times this method per photon on one CPU core (Table 4.2: 0.157 ms at 0 deg, 10 m steps)
+        o.tracer, o.tracer_dh = B.CS_TRACER_SNELL, 10.0
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        k_snell = max(3, args.steps // 50)
+        sn_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k_snell)]
+        for a, b_ in sn_ev:
+            flush.zero_()
+            a.record(stream)
+            step()
+            b_.record(stream)
+        torch.cuda.synchronize()
+        sn_ms = sum(a.elapsed_time(b_) for a, b_ in sn_ev) / k_snell
+        o.tracer = B.CS_TRACER_TABLES
+        snell = {"value": int(cnt[0].item()) / (sn_ms / 1e3), "unit": UNIT, "ms_per_step": sn_ms, "steps": k_snell,
+                 "time_vs_tables": sn_ms / (ms_max / args.steps),
+                 "bunches_per_s": int(cnt[0].item()) / bunch / (sn_ms / 1e3),
+                 "method": "Snell vector stepper, slabs <= 10 m, FP32, one traced path per bunch"}
+
     e2e = None
     if not args.no_e2e:
         # end to end through the host-pointer call: pinned segments in, outputs out
@@ -867,6 +892,7 @@ def main():
             "cpu_baseline": cpu,
             "surrogate": surrogate,
             "optics": optics,
+            "snell_tracer": snell,
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": sm_clk,

@@ -255,7 +255,18 @@ typedef struct cs_opts {
     int lv3;                 /* 0 (default) off, 1 on */
     double lv3_centre[3];
     double lv3_radius, lv3_margin;   /* >= 0 [m] */
+    /* Propagation method when the atmosphere refracts: CS_TRACER_TABLES (default) looks
+     * the correction up in the FP64-built tables (interpolation tracing, Sec. 4.4.1);
+     * CS_TRACER_SNELL traces every photon through homogeneous slabs of thickness
+     * <= tracer_dh [m] with Snell's law in vector form (Sec. 3.4.2, Eq. 3.15) and
+     * accumulates its delay and slant columns on the way (the general-atmosphere
+     * fallback; planar atmospheres, exact path only: CS_ERR_INVALID_ARG with a
+     * spherical atmosphere or a surrogate). */
+    int tracer;
+    double tracer_dh;
 } cs_opts;
+
+enum { CS_TRACER_TABLES = 0, CS_TRACER_SNELL = 1 };
 
 /* The LV1 filter's point of interest: x is the angle from the segment's
  * direction to the array centre, to a sphere of lv1_radius about it (0 inside),
@@ -269,7 +280,7 @@ enum {
 };
 
 /* Defaults: bunch 1, s_max 1 m, seg_base 0, host pointers, no accumulation, no
- * LV1 filter. */
+ * LV1 or LV3 filter, the table tracer (tracer_dh 10 m for the Snell stepper). */
 void cs_opts_default(cs_opts* opts);
 
 /* Generates and propagates the photons of n segments (Sec. 5.3 pipeline).

@@ -126,7 +126,10 @@ class cs_opts(C.Structure):
                 ("lv1_metric", C.c_int), ("lv1_a", C.c_double), ("lv1_b", C.c_double),
                 ("lv1_centre", C.c_double * 3), ("lv1_radius", C.c_double), ("lv1_dropped", C.c_void_p),
                 ("lv3", C.c_int), ("lv3_centre", C.c_double * 3), ("lv3_radius", C.c_double),
-                ("lv3_margin", C.c_double)]
+                ("lv3_margin", C.c_double), ("tracer", C.c_int), ("tracer_dh", C.c_double)]
+
+
+CS_TRACER_TABLES, CS_TRACER_SNELL = 0, 1
 
 
 def lib():
@@ -422,7 +425,8 @@ class Detector:
 
 
 def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=1.0, seg_base=0,
-                   records=False, record_capacity=None, blocks_per_sm=0, surrogate=None, lv1=None, lv3=None):
+                   records=False, record_capacity=None, blocks_per_sm=0, surrogate=None, lv1=None, lv3=None,
+                   snell_dh=None):
     """cs_propagate_ex with host numpy buffers; returns a dict of outputs."""
     arr = segs if isinstance(segs, np.ndarray) else pack_segments(segs)
     arr = np.ascontiguousarray(arr)
@@ -452,6 +456,8 @@ def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=
         set_lv1(o, lv1)
         o.lv1_dropped = dropped.ctypes.data
     set_lv3(o, lv3)
+    if snell_dh:   # the Snell vector stepper through slabs <= snell_dh [m] instead of the tables
+        o.tracer, o.tracer_dh = CS_TRACER_SNELL, snell_dh
     st = cs_propagate_ex(_dptr(arr) if len(arr) else None, len(arr), atm.handle, det.handle, seed, o, out)
     _check(st, "cs_propagate_ex")
     res = dict(hist=hist, tel_counts=tel_counts, tel_time=tel_time, counters=counters, n_records=int(rc[0]),

@@ -83,4 +83,6 @@ extern "C" void cs_opts_default(cs_opts* o) {
     o->lv3 = 0;
     o->lv3_centre[0] = o->lv3_centre[1] = o->lv3_centre[2] = 0.0;
     o->lv3_radius = o->lv3_margin = 0.0;
+    o->tracer = CS_TRACER_TABLES;
+    o->tracer_dh = 10.0;
 }

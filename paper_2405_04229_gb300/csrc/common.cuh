@@ -63,6 +63,9 @@ struct AtmParams {
     // transmission: exponent in log2 units = (G_X kR + G_A kA) / |u_z|
     float kR0;           // log2(e) lambda0_R^4 / X0_R [nm^4 cm^2/g]
     float kA0;           // log2(e) tau0 / H_A [1/m]
+    // the Snell stepper's slant columns: X [g/cm^2] per metre = rho_per_delta * delta,
+    // exp(-h / H_A) = aer_hobs * exp2(aer_c2 * dz)
+    float rho_per_delta, aer_hobs, aer_c2;
     float lamA_nm;       // aerosol reference wavelength [nm]
     float aer_alpha;
     TableView tv;
@@ -126,6 +129,9 @@ struct PropParams {
     int lv3;
     float lv3_c[3];
     float lv3_r2, lv3_dz2;
+    // Snell vector stepper instead of the tables: slabs no thicker than snell_dh
+    int snell;
+    float snell_dh;
 };
 
 // The atmosphere in FP64, as the table builder integrates it.

@@ -389,6 +389,41 @@ __device__ __noinline__ int camera_pixel(const DetParams& dp, float ddx, float d
     return iy * n + ix;
 }
 
+// Snell's law in vector form through homogeneous slabs (Sec. 3.4.2, Eq. 3.15),
+// the general-atmosphere tracer.  The height dz above the observation level is
+// cut into the fewest equal slabs no thicker than dh; slab j holds the index
+// at its middle height and is crossed straight.  At a planar boundary Eq. 3.15
+// adds c N to the optical vector A' = n A, so the horizontal part n sin(a)
+// never changes and the normal part becomes A'_j = sqrt(A'_0^2 + D_j) with
+// D_j = n_j^2 - n_0^2 = (d_j - d_0)(2 + d_j + d_0): the same algebra, written
+// so that FP32 resolves changes of 1e-8 per slab.  (A'_j^2 <= 0, a total
+// reflection that no atmosphere denser below produces, is clamped.)
+// Returns {(R - R_straight) / sin(theta0), c t_path, X_slant [g/cm^2], A_slant [m]}.
+__device__ __noinline__ float4 snell_path(const AtmParams& ap, float dz, float cos0, float dh) {
+    const int ns = max(1, (int)ceilf(dz / dh));
+    const float step = dz / (float)ns;
+    const float d0 = delta_at(ap, dz - 0.5f * step);
+    const float A0 = (1.0f + d0) * cos0;
+    const float inv0 = 1.0f / A0;
+    const float t0 = (1.0f + d0) * (1.0f + d0) * inv0;   // c t per metre of height in slab 0
+    float sR = 0.0f, sT = 0.0f, sX = 0.0f, sA = 0.0f;
+    for (int j = 0; j < ns; ++j) {
+        const float h = dz - ((float)j + 0.5f) * step;
+        const float dj = j == 0 ? d0 : delta_at(ap, h);
+        const float D = (dj - d0) * (2.0f + dj + d0);
+        const float Aj2 = fmaxf(fmaf(A0, A0, D), 1e-12f);
+        const float inv = rsqrtf(Aj2);         // 1 / A'_j
+        const float Aj = Aj2 * inv;
+        const float g = (1.0f + dj) * inv;     // path length per metre of height
+        sR -= D * inv * inv0 / (Aj + A0);      // 1 / A'_j - 1 / A'_0 without cancellation
+        sT += fmaf(1.0f + dj, g, -t0);         // the delay relative to slab 0's, summed small
+        sX = fmaf(dj, g, sX);
+        sA = fmaf(ex2_approx(ap.aer_c2 * h), g, sA);
+    }
+    return make_float4((1.0f + d0) * step * sR, fmaf(step, sT, dz * t0), ap.rho_per_delta * step * sX,
+                       ap.aer_hobs * step * sA);
+}
+
 // The correction fields at (dz, tan^2 of the local zenith) and the
 // transmission: the network's outputs where it applies, else the bilinear
 // table lookup; (0, 0, 1) without tables.
@@ -536,13 +571,27 @@ __device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool acti
     if (status == CS_ST_LANDED && !SPH) {
         float path = dz * inv_uz;
         float GR, Gt, Tr;
-        correction_fields<SURR>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
-        if (ap.refraction) {
-            const float c3 = GR * inv_uz * inv_uz * inv_uz;
-            const float2 r2 = __ffma2_rn(make_float2(c3, c3), uxy, make_float2(rx, ry));
+        if (!SURR && pp.snell && ap.refraction) {   // the per-photon stepper instead of the tables
+            const float4 sp = snell_path(ap, dz, cos_z, pp.snell_dh);
+            const float2 r2 = __ffma2_rn(make_float2(sp.x, sp.x), uxy, make_float2(rx, ry));
             rx = r2.x;
             ry = r2.y;
-            path = fmaf(Gt, inv_uz, path);
+            path = sp.y;
+            Tr = 1.0f;
+            if (ap.transmission) {
+                const float il2 = inv_l * inv_l;
+                const float kA = ap.kA0 * ex2_approx(ap.aer_alpha * lg2_approx(ap.lamA_nm * inv_l));
+                Tr = ex2_approx(-(sp.z * (ap.kR0 * il2 * il2) + sp.w * kA));
+            }
+        } else {
+            correction_fields<SURR>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
+            if (ap.refraction) {
+                const float c3 = GR * inv_uz * inv_uz * inv_uz;
+                const float2 r2 = __ffma2_rn(make_float2(c3, c3), uxy, make_float2(rx, ry));
+                rx = r2.x;
+                ry = r2.y;
+                path = fmaf(Gt, inv_uz, path);
+            }
         }
         t_rel = fmaf(path, kInvC, t_rel);
         const float4 Cg = S.segC[sg];
@@ -937,6 +986,8 @@ void set_filters(PropParams& pp, const cs_opts& o, const DetParams& dp) {
     const double lim = o.lv3_radius + o.lv3_margin;
     pp.lv3_r2 = (float)(lim * lim);
     pp.lv3_dz2 = (float)((dp.h_obs - o.lv3_centre[2]) * (dp.h_obs - o.lv3_centre[2]));
+    pp.snell = o.tracer == CS_TRACER_SNELL ? 1 : 0;
+    pp.snell_dh = (float)o.tracer_dh;
     pp.lv1 = o.lv1_metric;
     pp.lv1_a = (float)o.lv1_a;
     pp.lv1_b = (float)o.lv1_b;
@@ -945,7 +996,11 @@ void set_filters(PropParams& pp, const cs_opts& o, const DetParams& dp) {
     pp.lv1_dropped = (unsigned long long*)o.lv1_dropped;
 }
 
-bool filters_valid(const cs_opts& o) {
+bool filters_valid(const cs_opts& o, const cs_atmosphere* atm) {
+    if (o.tracer != CS_TRACER_TABLES &&
+        (o.tracer != CS_TRACER_SNELL || !(o.tracer_dh >= 0.01) || !isfinite(o.tracer_dh) || o.surrogate ||
+         atm->p.spherical))
+        return false;
     if (o.lv3 && !(o.lv3_radius >= 0.0 && o.lv3_margin >= 0.0 && isfinite(o.lv3_radius + o.lv3_margin) &&
                    isfinite(o.lv3_centre[0]) && isfinite(o.lv3_centre[1]) && isfinite(o.lv3_centre[2])))
         return false;
@@ -1037,7 +1092,7 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
     if (opts) o = *opts; else cs_opts_default(&o);
     if (o.bunch < 1 || !(o.s_max > 0.0) || (n > 0 && !segs)) return CS_ERR_INVALID_ARG;
     if (!outputs_complete(det, out)) return CS_ERR_INVALID_ARG;
-    if (!compatible(atm, det) || !filters_valid(o)) return CS_ERR_INVALID_ARG;
+    if (!compatible(atm, det) || !filters_valid(o, atm)) return CS_ERR_INVALID_ARG;
     if (n > (size_t)1 << 40) return CS_ERR_INVALID_ARG;
     cudaStream_t stream = (cudaStream_t)stream_;
     const DetParams& dp = det->p;
@@ -1200,7 +1255,7 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     if (((uintptr_t)segs & 15) != 0) return CS_ERR_INVALID_ARG;
     if (det->p.nx > 0 && !out->hist) return CS_ERR_INVALID_ARG;
     if (!outputs_complete(det, out)) return CS_ERR_INVALID_ARG;
-    if (!compatible(atm, det) || !filters_valid(o)) return CS_ERR_INVALID_ARG;
+    if (!compatible(atm, det) || !filters_valid(o, atm)) return CS_ERR_INVALID_ARG;
     // the counter is 32 bits wide: reject inputs with more tiles than it can count
     if ((n + kTile - 1) / kTile >= 0xFFFFFFFFull - 65536ull) return CS_ERR_INVALID_ARG;
     cudaStream_t stream = (cudaStream_t)stream_;
@@ -1253,7 +1308,7 @@ cs_status check_device_call(const cs_segment* segs, size_t n, const cs_atmospher
     if (o.bunch < 1 || !(o.s_max > 0.0) || (n > 0 && !segs) || !o.device_ptrs) return CS_ERR_INVALID_ARG;
     if (((uintptr_t)segs & 15) != 0) return CS_ERR_INVALID_ARG;
     if (!outputs_complete(det, out)) return CS_ERR_INVALID_ARG;
-    if (!compatible(atm, det) || !filters_valid(o)) return CS_ERR_INVALID_ARG;
+    if (!compatible(atm, det) || !filters_valid(o, atm)) return CS_ERR_INVALID_ARG;
     if (n > (size_t)1 << 40) return CS_ERR_INVALID_ARG;
     return CS_OK;
 }

@@ -402,6 +402,11 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
         const double lR = d->rayl_lambda0 * 1e9;
         p.kR0 = (float)(kLog2e * lR * lR * lR * lR / d->rayl_X0);
         p.kA0 = (float)(kLog2e * d->aer_tau0 / a.H_A);
+        p.rho_per_delta = a.kind == CS_ATM_LAYERED ? (float)(100.0 * a.rho0 / a.kappa)
+                        : a.kind == CS_ATM_TABLE   ? (float)(100.0 * kTableRhoRef / a.kappa)
+                                                   : 0.0f;
+        p.aer_hobs = (float)exp(-d->h_obs / a.H_A);
+        p.aer_c2 = (float)(-kLog2e / a.H_A);
         p.lamA_nm = (float)(d->aer_lambda0 * 1e9);
         p.aer_alpha = (float)d->aer_alpha;
     }
