@@ -75,7 +75,7 @@ def test_stepper_rejects_what_it_does_not_cover():
     sph = B.Atmosphere(layered=synth.US_STANDARD, refraction=True, transmission=False, spherical=True)
     with pytest.raises(RuntimeError):
         B.propagate_host(segs, sph, B.Detector(hist=HIST, spherical=True), seed=1, snell_dh=10.0)
-    sur = B.Surrogate(atm, epochs=1, n_train=1 << 14, n_heldout=1 << 12)
+    sur = B.Surrogate(atm, epochs=1, n_train=1 << 16, n_heldout=1 << 12)
     with pytest.raises(RuntimeError):
         B.propagate_host(segs, atm, det, seed=1, snell_dh=10.0, surrogate=sur)
     sur.close()
