@@ -415,10 +415,12 @@ __device__ __noinline__ float4 snell_path(const AtmParams& ap, float dz, float c
         const float inv = rsqrtf(Aj2);         // 1 / A'_j
         const float Aj = Aj2 * inv;
         const float g = (1.0f + dj) * inv;     // path length per metre of height
-        sR -= D * inv * inv0 / (Aj + A0);      // 1 / A'_j - 1 / A'_0 without cancellation
+        sR -= D * inv * inv0 * rcp_approx(Aj + A0);   // 1 / A'_j - 1 / A'_0 without cancellation
         sT += fmaf(1.0f + dj, g, -t0);         // the delay relative to slab 0's, summed small
-        sX = fmaf(dj, g, sX);
-        sA = fmaf(ex2_approx(ap.aer_c2 * h), g, sA);
+        if (ap.transmission) {
+            sX = fmaf(dj, g, sX);
+            sA = fmaf(ex2_approx(ap.aer_c2 * h), g, sA);
+        }
     }
     return make_float4((1.0f + d0) * step * sR, fmaf(step, sT, dz * t0), ap.rho_per_delta * step * sX,
                        ap.aer_hobs * step * sA);
