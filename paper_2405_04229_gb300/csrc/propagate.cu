@@ -54,6 +54,27 @@ struct TileSmem {
     int tile;
 };
 
+// The exact-tracer instances run their warps independently: each warp takes
+// tiles of 32 segments from the work counter and keeps its own segment,
+// sub-step and bunch-map buffers, so no block-wide barrier ever holds a warp
+// (the surrogate's warpgroups, whose tensor-core network is collective, keep
+// the block-wide tile above).
+constexpr int kWTile = 32;              // segments per warp tile
+constexpr int kWSubCap = 96;            // sub-steps per warp round
+constexpr int kWMapCap = 384;           // bunches per warp map window
+struct WarpSmem {
+    float4 segA[kWTile], segB[kWTile], segC[kWTile], segD[kWTile];   // as in TileSmem
+    double t0[kWTile];
+    float g[kWTile], z2[kWTile];
+    int shower[kWTile];
+    int bunch[kWTile];
+    int offK[kWTile + 1];
+    float4 sub[kWSubCap];
+    int nsub_ph[kWSubCap];
+    unsigned int map[kWMapCap];
+};
+constexpr size_t kSmemExact = (kThreads / 32) * sizeof(WarpSmem);
+
 // The surrogate instances keep the tensor-core network's buffers after the tile.
 constexpr size_t kTcSmemOffset = (sizeof(TileSmem) + 127) & ~(size_t)127;
 constexpr size_t kSmemSurrogate = kTcSmemOffset + sizeof(TcSmem<kThreadsSur / 128>);
@@ -149,8 +170,8 @@ __device__ __forceinline__ bool lv1_drop(const PropParams& pp, const DetParams& 
 // Planar: the origin is the ground intercept of the segment's line (float-float).
 // Spherical shell: the start point (float-float), its altitude above h_obs,
 // the radial component of P, 1 / r and the tilt of the local vertical.
-template <bool SPH>
-__device__ __forceinline__ int import_segment(TileSmem& S, int t, const cs_segment* seg, const PropParams& pp,
+template <bool SPH, typename SM>
+__device__ __forceinline__ int import_segment(SM& S, int t, const cs_segment* seg, const PropParams& pp,
                                               const AtmParams& ap, const DetParams& dp, unsigned int& invalid,
                                               unsigned int& dropped) {
     const double2* src = reinterpret_cast<const double2*>(seg);
@@ -250,8 +271,8 @@ __device__ __forceinline__ int import_segment(TileSmem& S, int t, const cs_segme
 // Stage 2 (Eq. 2.2-2.5, Sec. 4.2.1): sub-step k of tile segment sg at local
 // slot q: angle and mean bunch count at the sub-step midpoint, stochastic
 // rounding with the sub-step's own draw.  Returns the bunch count.
-template <bool SPH>
-__device__ __forceinline__ int substep(TileSmem& S, int q, int sg, int k, long long base, const PropParams& pp,
+template <bool SPH, typename SM>
+__device__ __forceinline__ int substep(SM& S, int q, int sg, int k, long long base, const PropParams& pp,
                                        const AtmParams& ap) {
     const float4 B = S.segB[sg];
     float dz_mid;
@@ -475,8 +496,8 @@ __device__ __forceinline__ void correction_fields(const AtmParams& ap, bool use_
 // (Sec. 4.4.1) or the surrogate network, transmission (Sec. 4.3.1) and
 // detection.  With SURR the whole warpgroup must call (inactive threads pass
 // active = false): the network runs on the tensor cores for 128 photons.
-template <bool SURR, bool SPH, bool REC>
-__device__ __forceinline__ void bunch(const TileSmem& S, int q, int i, bool active, long long base,
+template <bool SURR, bool SPH, bool REC, typename SM>
+__device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, long long base,
                                       const PropParams& pp, const AtmParams& ap, const DetParams& dp,
                                       const OutParams& op, const SurrogateView& sv, TcSmem<kThreadsSur / 128>* tcs,
                                       Tally& T) {
@@ -776,74 +797,155 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
     Tally T = {0, 0, 0, 0};
     int buf = 0;
 
-    for (;;) {
-        // dynamic tile scheduling: blocks that finish early take more tiles
-        if (t == 0) S.tile = (int)atomicAdd(tile_ctr, 1u);
-        __syncthreads();
-        const long long tile = S.tile;
-        if (tile >= n_tiles) break;
-        const long long base = tile * kTile;
-
-        // ---- stage 1: import and filter (one segment per thread) -------------
-        const int Kt = (t < kTile && base + t < pp.n) ? import_segment<SPH>(S, t, pp.segs + base + t, pp, ap, dp, invalid, dropped) : 0;
-        int S_tot;
-        const int offk = block_scan<NT>(Kt, S.wsum, buf, &S_tot);
-        if (t < kTile) S.offK[t] = offk;
-        if (t == 0) S.offK[kTile] = S_tot;
-        __syncthreads();
-
-        for (int sub0 = 0; sub0 < S_tot; sub0 += kSubCap) {
-            const int nsub = min(kSubCap, S_tot - sub0);
-            // ---- stage 2: sub-step yields, a balanced run [q0, q1) per thread ---
-            const int per = (nsub + NT - 1) / NT;
-            const int q0 = min(t * per, nsub), q1 = min(q0 + per, nsub);
-            int my_ph = 0;
-            unsigned int my_emit = 0;
-            if (q0 < q1) {
-                int lo = 0, hi = kTile;   // offK[lo] <= sub0 + q0 < offK[lo + 1]
-                const int first = sub0 + q0;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (S.offK[mid] <= first) lo = mid;
-                    else hi = mid;
-                }
-                int sg = lo;
-                for (int q = q0; q < q1; ++q) {
-                    const int qq = sub0 + q;
-                    while (S.offK[sg + 1] <= qq) ++sg;   // next non-empty segment
-                    const int N = substep<SPH>(S, q, sg, qq - S.offK[sg], base, pp, ap);
-                    my_ph += N;
-                    my_emit += (unsigned int)N * (unsigned int)S.bunch[sg];
-                }
+    if constexpr (!SURR) {
+        // ---- warps on their own: tiles of 32 segments, warp scans, no block barrier
+        WarpSmem& W = reinterpret_cast<WarpSmem*>(smem_raw)[t >> 5];
+        const int lane = t & 31;
+        const long long n_wtiles = (pp.n + kWTile - 1) / kWTile;
+        for (;;) {
+            unsigned int wt = 0;
+            if (lane == 0) wt = atomicAdd(tile_ctr, 1u);
+            const long long tile = (long long)__shfl_sync(0xffffffffu, wt, 0);
+            if (tile >= n_wtiles) break;
+            const long long base = tile * kWTile;
+            const int Kt = base + lane < pp.n
+                               ? import_segment<SPH>(W, lane, pp.segs + base + lane, pp, ap, dp, invalid, dropped)
+                               : 0;
+            int incl = Kt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
-            int M;
-            const int ph0 = block_scan<NT>(my_ph, S.wsum, buf, &M);
-            emitted += my_emit;
-
-            // ---- stages 3-5 over windows of the bunch map ------------------------
-            for (int p0 = 0; p0 < M; p0 += kMapCap) {
-                const int wn = min(kMapCap, M - p0);
-                int off = ph0;
-                for (int q = q0; q < q1; ++q) {   // owners write their bunches' entries
-                    const int N = S.nsub_ph[q];
-                    const int a = max(off, p0), b = min(off + N, p0 + wn);
-                    for (int p = a; p < b; ++p) S.map[p - p0] = (unsigned int)q | ((unsigned int)(p - off) << kQBits);
-                    off += N;
+            const int S_tot = __shfl_sync(0xffffffffu, incl, 31);
+            W.offK[lane] = incl - Kt;
+            if (lane == 31) W.offK[kWTile] = S_tot;
+            __syncwarp();
+            for (int sub0 = 0; sub0 < S_tot; sub0 += kWSubCap) {
+                const int nsub = min(kWSubCap, S_tot - sub0);
+                // sub-step yields: a balanced run [q0, q1) per lane
+                const int per = (nsub + 31) >> 5;
+                const int q0 = min(lane * per, nsub), q1 = min(q0 + per, nsub);
+                int my_ph = 0;
+                unsigned int my_emit = 0;
+                if (q0 < q1) {
+                    int lo = 0, hi = kWTile;   // offK[lo] <= sub0 + q0 < offK[lo + 1]
+                    const int first = sub0 + q0;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (W.offK[mid] <= first) lo = mid;
+                        else hi = mid;
+                    }
+                    int sg = lo;
+                    for (int q = q0; q < q1; ++q) {
+                        const int qq = sub0 + q;
+                        while (W.offK[sg + 1] <= qq) ++sg;   // next non-empty segment
+                        const int N = substep<SPH>(W, q, sg, qq - W.offK[sg], base, pp, ap);
+                        my_ph += N;
+                        my_emit += (unsigned int)N * (unsigned int)W.bunch[sg];
+                    }
                 }
-                __syncthreads();
-                // whole warps (warpgroups on the surrogate path, whose network is
-                // warpgroup-collective) iterate together
-                constexpr int kGroup = SURR ? 128 : 32;
-                for (int pw = t & ~(kGroup - 1); pw < wn; pw += NT) {
-                    const int p = pw + (t & (kGroup - 1));
-                    const bool active = p < wn;
-                    const unsigned int e = S.map[active ? p : pw];
-                    bunch<SURR, SPH, REC>(S, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), active, base, pp,
-                                          ap, dp, op, sv, tcs, T);
+                emitted += my_emit;
+                int ph_incl = my_ph;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, ph_incl, o);
+                    if (lane >= o) ph_incl += y;
                 }
-                __syncthreads();
+                const int M = __shfl_sync(0xffffffffu, ph_incl, 31);
+                const int ph0 = ph_incl - my_ph;
+                __syncwarp();
+                // bunches over windows of the warp's bunch -> sub-step map
+                for (int p0 = 0; p0 < M; p0 += kWMapCap) {
+                    const int wn = min(kWMapCap, M - p0);
+                    int off = ph0;
+                    for (int q = q0; q < q1; ++q) {
+                        const int N = W.nsub_ph[q];
+                        const int a = max(off, p0), b = min(off + N, p0 + wn);
+                        for (int p = a; p < b; ++p) W.map[p - p0] = (unsigned int)q | ((unsigned int)(p - off) << kQBits);
+                        off += N;
+                    }
+                    __syncwarp();
+                    for (int p = lane; p < wn; p += 32) {
+                        const unsigned int e = W.map[p];
+                        bunch<false, SPH, REC>(W, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), true, base,
+                                               pp, ap, dp, op, sv, tcs, T);
+                    }
+                    __syncwarp();
+                }
             }
         }
+    } else {
+        for (;;) {
+            // dynamic tile scheduling: blocks that finish early take more tiles
+            if (t == 0) S.tile = (int)atomicAdd(tile_ctr, 1u);
+            __syncthreads();
+            const long long tile = S.tile;
+            if (tile >= n_tiles) break;
+            const long long base = tile * kTile;
+
+            // ---- stage 1: import and filter (one segment per thread) -------------
+            const int Kt = (t < kTile && base + t < pp.n) ? import_segment<SPH>(S, t, pp.segs + base + t, pp, ap, dp, invalid, dropped) : 0;
+            int S_tot;
+            const int offk = block_scan<NT>(Kt, S.wsum, buf, &S_tot);
+            if (t < kTile) S.offK[t] = offk;
+            if (t == 0) S.offK[kTile] = S_tot;
+            __syncthreads();
+
+            for (int sub0 = 0; sub0 < S_tot; sub0 += kSubCap) {
+                const int nsub = min(kSubCap, S_tot - sub0);
+                // ---- stage 2: sub-step yields, a balanced run [q0, q1) per thread ---
+                const int per = (nsub + NT - 1) / NT;
+                const int q0 = min(t * per, nsub), q1 = min(q0 + per, nsub);
+                int my_ph = 0;
+                unsigned int my_emit = 0;
+                if (q0 < q1) {
+                    int lo = 0, hi = kTile;   // offK[lo] <= sub0 + q0 < offK[lo + 1]
+                    const int first = sub0 + q0;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (S.offK[mid] <= first) lo = mid;
+                        else hi = mid;
+                    }
+                    int sg = lo;
+                    for (int q = q0; q < q1; ++q) {
+                        const int qq = sub0 + q;
+                        while (S.offK[sg + 1] <= qq) ++sg;   // next non-empty segment
+                        const int N = substep<SPH>(S, q, sg, qq - S.offK[sg], base, pp, ap);
+                        my_ph += N;
+                        my_emit += (unsigned int)N * (unsigned int)S.bunch[sg];
+                    }
+                }
+                int M;
+                const int ph0 = block_scan<NT>(my_ph, S.wsum, buf, &M);
+                emitted += my_emit;
+
+                // ---- stages 3-5 over windows of the bunch map ------------------------
+                for (int p0 = 0; p0 < M; p0 += kMapCap) {
+                    const int wn = min(kMapCap, M - p0);
+                    int off = ph0;
+                    for (int q = q0; q < q1; ++q) {   // owners write their bunches' entries
+                        const int N = S.nsub_ph[q];
+                        const int a = max(off, p0), b = min(off + N, p0 + wn);
+                        for (int p = a; p < b; ++p) S.map[p - p0] = (unsigned int)q | ((unsigned int)(p - off) << kQBits);
+                        off += N;
+                    }
+                    __syncthreads();
+                    // whole warps (warpgroups on the surrogate path, whose network is
+                    // warpgroup-collective) iterate together
+                    constexpr int kGroup = SURR ? 128 : 32;
+                    for (int pw = t & ~(kGroup - 1); pw < wn; pw += NT) {
+                        const int p = pw + (t & (kGroup - 1));
+                        const bool active = p < wn;
+                        const unsigned int e = S.map[active ? p : pw];
+                        bunch<SURR, SPH, REC>(S, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), active, base, pp,
+                                              ap, dp, op, sv, tcs, T);
+                    }
+                    __syncthreads();
+                }
+            }
+        }
+
     }
 
     if (SURR) tc_teardown(*tcs);
@@ -887,7 +989,7 @@ bool compatible(const cs_atmosphere* atm, const cs_detector* det) {
 
 cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp, const AtmParams& ap,
                         const DetParams& dp, const OutParams& op, unsigned int* ctr, const cs_surrogate* sur) {
-    const size_t smem = sur ? kSmemSurrogate : sizeof(TileSmem);
+    const size_t smem = sur ? kSmemSurrogate : kSmemExact;
     SurrogateView none;
     memset(&none, 0, sizeof none);
     const SurrogateView& sv = sur ? *surrogate_view(sur) : none;
@@ -907,7 +1009,7 @@ cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp
 }
 
 cs_status set_smem_attributes() {
-    const int smem = (int)sizeof(TileSmem), smem_sur = (int)kSmemSurrogate;
+    const int smem = (int)kSmemExact, smem_sur = (int)kSmemSurrogate;
     const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
     CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, false, 4, false>, attr, smem));
     CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, false, 4, true>, attr, smem));
@@ -1219,7 +1321,7 @@ namespace cs {
 namespace {
 
 // One 32-bit tile counter per call, padded to one 256-byte line.  A call can
-// schedule at most 2^32 - 1 tiles of kTile segments.
+// schedule at most 2^32 - 1 tiles (of kWTile segments per warp, or kTile per block).
 constexpr int kNoAllocScratchWords = 64;
 static __device__ __align__(256) unsigned int g_noalloc_scratch[kNoAllocScratchWords];
 
@@ -1259,7 +1361,7 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     if (!outputs_complete(det, out)) return CS_ERR_INVALID_ARG;
     if (!compatible(atm, det) || !filters_valid(o, atm)) return CS_ERR_INVALID_ARG;
     // the counter is 32 bits wide: reject inputs with more tiles than it can count
-    if ((n + kTile - 1) / kTile >= 0xFFFFFFFFull - 65536ull) return CS_ERR_INVALID_ARG;
+    if ((n + kWTile - 1) / kWTile >= 0xFFFFFFFFull - 65536ull) return CS_ERR_INVALID_ARG;
     cudaStream_t stream = (cudaStream_t)stream_;
     const DetParams& dp = det->p;
     unsigned int* ctr = nullptr;
