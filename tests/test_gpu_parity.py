@@ -112,7 +112,7 @@ def test_straight_line_with_transmission_and_inclined_showers():
 
 
 def test_ragged_sizes_and_tiles():
-    for n in (1, 255, 257, 513):
+    for n in (1, 31, 33, 255, 257, 513):
         segs = synth.tiny_vertical_segments(n, seed=n)
         g, o = _run_both(segs, True, False, 1)
         PU.compare(g, o, bunch=1)
@@ -132,6 +132,17 @@ def test_long_segments_exercise_substep_rounds():
     segs["length"][:] = np.float32(37.5)        # 38 sub-steps each, 11,400 per tile
     g, o = _run_both(segs, True, True, 10)
     PU.compare(g, o, bunch=10)
+    PU.check_conservation(g["counters"])
+
+
+def test_many_bunches_exercise_map_windows():
+    """Bunches of one photon from long segments: a warp's sub-step round holds
+    far more bunches than one window of its bunch map."""
+    segs = synth.tiny_vertical_segments(150, seed=9)
+    segs["length"][:] = np.float32(12.0)
+    g, o = _run_both(segs, True, True, 1)
+    st = PU.compare(g, o, bunch=1)
+    assert st["matched"] > 15000
     PU.check_conservation(g["counters"])
 
 
