@@ -70,7 +70,9 @@ class Config(C.Structure):
                 ("mirror_d", C.c_double), ("focal_f", C.c_double), ("camera_r", C.c_double),
                 ("point_zenith", C.c_double), ("point_azimuth", C.c_double), ("cam_n", C.c_int), ("pad4", C.c_int),
                 ("lv3", C.c_int), ("pad5", C.c_int), ("lv3_centre", C.c_double * 3), ("lv3_radius", C.c_double),
-                ("lv3_margin", C.c_double), ("tracer", C.c_int), ("pad6", C.c_int), ("tracer_dh", C.c_double)]
+                ("lv3_margin", C.c_double), ("tracer", C.c_int), ("pad6", C.c_int), ("tracer_dh", C.c_double),
+                ("emission", C.c_int), ("fl_n_lines", C.c_int), ("fl_lines_nm", C.c_double * 8),
+                ("fl_yield", C.c_double * 8), ("fl_dedx", C.c_double)]
 
 
 SEGMENT_DTYPE = np.dtype([("x0", "<f8"), ("y0", "<f8"), ("z0", "<f8"), ("t0", "<f8"),
@@ -273,7 +275,7 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
               refraction=False, transmission=False, use_domain=None, w_max=None, seed=0,
               seg_base=0, n_showers=1, hist=None, tel=None, records=True, record_capacity=None,
               transmission_params=None, bands=None, quad_rtol=1e-10, spherical=False, earth_radius=EARTH_RADIUS,
-              lv1=None, optics=None, lv3=None, snell_dh=None):
+              lv1=None, optics=None, lv3=None, snell_dh=None, fluorescence=None):
     """Run the oracle over ``segs`` (dict of columns or SEGMENT_DTYPE array).
 
     Returns a dict with hist [n_showers, ny, nx], tel_counts [n_showers, n_tel],
@@ -323,6 +325,13 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
         for i, v in enumerate(lv1.get("centre", (0.0, 0.0, h_obs))):
             cfg.lv1_centre[i] = v
         cfg.lv1_radius, cfg.band_lv1 = lv1.get("radius", 0.0), lv1.get("band", 1e-4)
+    if fluorescence:   # dict(half=bool, lines_nm, yield_per_mev, dedx): isotropic line emission
+        cfg.emission = 2 if fluorescence.get("half") else 1
+        lines, ys = fluorescence["lines_nm"], fluorescence["yield_per_mev"]
+        cfg.fl_n_lines = len(lines)
+        for j, (l, y) in enumerate(zip(lines, ys)):
+            cfg.fl_lines_nm[j], cfg.fl_yield[j] = l, y
+        cfg.fl_dedx = fluorescence["dedx"]
     if snell_dh:   # refraction by the Snell vector stepper through slabs <= snell_dh [m]
         cfg.tracer, cfg.tracer_dh = 1, snell_dh
     if lv3:   # dict(centre=(x, y, z), radius, margin)

@@ -696,6 +696,14 @@ typedef struct {
     int tracer;
     int pad6;
     double tracer_dh;
+    /* emission (Sec. 2.2.2, 4.2.2): 0 Cherenkov; 1 fluorescence, isotropic; 2 fluorescence into
+     * the downward half sphere with half the photons.  Fluorescence yield (Eq. 2.6) per metre:
+     * z^2 fl_dedx [MeV cm^2/g] rho [g/cm^3] 100 sum_l fl_yield[l] [photons/MeV], lines fl_lines_nm */
+    int emission;
+    int fl_n_lines;
+    double fl_lines_nm[8];
+    double fl_yield[8];
+    double fl_dedx;
 } orc_config;
 
 enum { ORC_ST_LANDED = 0, ORC_ST_UPWARD = 1, ORC_ST_BELOW = 2, ORC_ST_DOMAIN = 3,
@@ -955,6 +963,12 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                     if (fabs(h_mid - atm->layer_h[li]) < cfg->band_h) mid_layer_flag = 1;
             double sin2 = 1.0 - 1.0 / (beta * beta * n_k * n_k);    /* Eq. 2.3 */
             double nbar = sin2 > 0.0 ? ft * z * z * sin2 * (L / K) / b : 0.0;  /* threshold */
+            if (cfg->emission) {   /* fluorescence (Eq. 2.6): deposited energy times the lines' yields */
+                double ysum = 0.0;
+                for (int l = 0; l < cfg->fl_n_lines; ++l) ysum += cfg->fl_yield[l];
+                nbar = z * z * cfg->fl_dedx * orc_atm_rho(atm, h_mid) * 100.0 * ysum * (L / K) / b;
+                if (cfg->emission == 2) nbar *= 0.5;
+            }
             uint32_t ctr_c[4] = { (uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0xFFFFFFFFu };
             uint32_t rc[4];
             orc_philox4x32_10(ctr_c, key, rc);
@@ -998,6 +1012,26 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                 double p[3] = { cos(phi) * sin_t, sin(phi) * sin_t, -cos_t };
                 double u[3];
                 for (int r = 0; r < 3; ++r) u[r] = M[r][0] * p[0] + M[r][1] * p[1] + M[r][2] * p[2];
+                if (cfg->emission) {
+                    /* fluorescence (Sec. 4.2.2): isotropic, cos(zenith) uniform over the sphere
+                     * or the downward half sphere; the line from a second draw, its 24-bit
+                     * integer against the lines' cumulative shares in units of 2^-24 */
+                    const double c = cfg->emission == 2 ? u2 - 1.0 : 2.0 * u2 - 1.0;
+                    const double sc = sqrt(fmax(1.0 - c * c, 0.0));
+                    u[0] = sc * cos(phi); u[1] = sc * sin(phi); u[2] = c;
+                    uint32_t ctr2[4] = { (uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, (uint32_t)i | 0x80000000u };
+                    uint32_t r2[4];
+                    orc_philox4x32_10(ctr2, key, r2);
+                    double ysum = 0.0, cum = 0.0;
+                    for (int l = 0; l < cfg->fl_n_lines; ++l) ysum += cfg->fl_yield[l];
+                    const uint32_t v = r2[0] >> 8;
+                    int line = cfg->fl_n_lines - 1;
+                    for (int l = 0; l + 1 < cfg->fl_n_lines; ++l) {
+                        cum += cfg->fl_yield[l];
+                        if (v < (uint32_t)floor(cum / ysum * 16777216.0)) { line = l; break; }
+                    }
+                    rec.lambda = cfg->fl_lines_nm[line] * 1e-9;
+                }
                 rec.ux = u[0]; rec.uy = u[1]; rec.uz = u[2];
                 out->counters[0] += (uint64_t)cfg->bunch;
 

@@ -25,6 +25,13 @@ C_LIGHT = 299_792_458.0
 # T(h) = a + b exp(-h/c) for the four lower layers, T(h) = a - b h / c in the
 # top layer.  T in g/cm^2, c in cm, layer bottoms in m.  The thesis names the
 # US standard atmosphere (Sec. 4.3.1) but prints no parameters.
+# Synthetic stand-in for a nitrogen fluorescence line list (the measured yields with their
+# pressure, temperature and humidity dependence are not available here): five lines of the
+# near-UV bands with round yields in photons per MeV deposited, and a minimum-ionising
+# energy loss of 2.2 MeV cm^2/g.
+FLUORESCENCE = dict(lines_nm=[316.0, 337.0, 358.0, 380.0, 391.0],
+                    yield_per_mev=[2.0, 5.0, 4.0, 1.5, 1.5], dedx=2.2)
+
 US_STANDARD = dict(
     layer_h=[0.0, 4000.0, 10000.0, 40000.0, 100000.0],
     a=[-186.555305, -94.919, 0.61289, 0.0, 0.01128292],
