@@ -264,7 +264,22 @@ typedef struct cs_opts {
      * spherical atmosphere or a surrogate). */
     int tracer;
     double tracer_dh;
+    /* Emission (Sec. 2.2.2, 4.2.2): CS_EMIT_CHERENKOV (default), or nitrogen fluorescence,
+     * isotropic (CS_EMIT_FLUORESCENCE) or into the downward half sphere with half the photons
+     * (CS_EMIT_FLUORESCENCE_HALF).  Fluorescence yield (Eq. 2.6) per metre of track:
+     * z^2 fl_dedx [MeV cm^2/g] rho(h) [g/cm^3] 100 sum_l fl_yield_per_mev[l], rho from the
+     * atmosphere's density law (zero for the linear and homogeneous kinds); each bunch takes
+     * line l with probability fl_yield_per_mev[l] / sum (up to 8 lines, fl_lines_nm [nm]).
+     * Every propagation method, filter and detector applies, except the LV1 cut
+     * (CS_ERR_INVALID_ARG): isotropic light cannot be filtered by direction. */
+    int emission;
+    int fl_n_lines;
+    const double* fl_lines_nm;
+    const double* fl_yield_per_mev;
+    double fl_dedx;
 } cs_opts;
+
+enum { CS_EMIT_CHERENKOV = 0, CS_EMIT_FLUORESCENCE = 1, CS_EMIT_FLUORESCENCE_HALF = 2 };
 
 enum { CS_TRACER_TABLES = 0, CS_TRACER_SNELL = 1 };
 

@@ -126,10 +126,27 @@ class cs_opts(C.Structure):
                 ("lv1_metric", C.c_int), ("lv1_a", C.c_double), ("lv1_b", C.c_double),
                 ("lv1_centre", C.c_double * 3), ("lv1_radius", C.c_double), ("lv1_dropped", C.c_void_p),
                 ("lv3", C.c_int), ("lv3_centre", C.c_double * 3), ("lv3_radius", C.c_double),
-                ("lv3_margin", C.c_double), ("tracer", C.c_int), ("tracer_dh", C.c_double)]
+                ("lv3_margin", C.c_double), ("tracer", C.c_int), ("tracer_dh", C.c_double),
+                ("emission", C.c_int), ("fl_n_lines", C.c_int), ("fl_lines_nm", C.c_void_p),
+                ("fl_yield_per_mev", C.c_void_p), ("fl_dedx", C.c_double)]
 
 
 CS_TRACER_TABLES, CS_TRACER_SNELL = 0, 1
+CS_EMIT_CHERENKOV, CS_EMIT_FLUORESCENCE, CS_EMIT_FLUORESCENCE_HALF = 0, 1, 2
+
+
+def set_fluorescence(o, fl):
+    """Fill the emission fields of a cs_opts from dict(lines_nm, yield_per_mev, dedx, half);
+    returns the arrays the struct points to (keep them alive for the call)."""
+    if not fl:
+        return None
+    lines = np.ascontiguousarray(fl["lines_nm"], np.float64)
+    ys = np.ascontiguousarray(fl["yield_per_mev"], np.float64)
+    o.emission = CS_EMIT_FLUORESCENCE_HALF if fl.get("half") else CS_EMIT_FLUORESCENCE
+    o.fl_n_lines = len(lines)
+    o.fl_lines_nm, o.fl_yield_per_mev = lines.ctypes.data, ys.ctypes.data
+    o.fl_dedx = fl.get("dedx", 2.2)
+    return lines, ys
 
 
 def lib():
@@ -426,7 +443,7 @@ class Detector:
 
 def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=1.0, seg_base=0,
                    records=False, record_capacity=None, blocks_per_sm=0, surrogate=None, lv1=None, lv3=None,
-                   snell_dh=None):
+                   snell_dh=None, fluorescence=None):
     """cs_propagate_ex with host numpy buffers; returns a dict of outputs."""
     arr = segs if isinstance(segs, np.ndarray) else pack_segments(segs)
     arr = np.ascontiguousarray(arr)
@@ -458,6 +475,7 @@ def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=
     set_lv3(o, lv3)
     if snell_dh:   # the Snell vector stepper through slabs <= snell_dh [m] instead of the tables
         o.tracer, o.tracer_dh = CS_TRACER_SNELL, snell_dh
+    keep = set_fluorescence(o, fluorescence)   # noqa: F841 (the arrays must outlive the call)
     st = cs_propagate_ex(_dptr(arr) if len(arr) else None, len(arr), atm.handle, det.handle, seed, o, out)
     _check(st, "cs_propagate_ex")
     res = dict(hist=hist, tel_counts=tel_counts, tel_time=tel_time, counters=counters, n_records=int(rc[0]),

@@ -85,4 +85,9 @@ extern "C" void cs_opts_default(cs_opts* o) {
     o->lv3_radius = o->lv3_margin = 0.0;
     o->tracer = CS_TRACER_TABLES;
     o->tracer_dh = 10.0;
+    o->emission = CS_EMIT_CHERENKOV;
+    o->fl_n_lines = 0;
+    o->fl_lines_nm = nullptr;
+    o->fl_yield_per_mev = nullptr;
+    o->fl_dedx = 2.2;
 }

@@ -132,6 +132,13 @@ struct PropParams {
     // Snell vector stepper instead of the tables: slabs no thicker than snell_dh
     int snell;
     float snell_dh;
+    // fluorescence (CS_EMIT_*): mean bunches per metre = fl_yd z^2 delta(h) / b; line l
+    // (1 / lambda in fl_inv_l) when the second draw's 24 bits are below fl_thr[l]
+    int emission;
+    int fl_n;
+    float fl_yd;
+    float fl_inv_l[8];
+    uint32_t fl_thr[8];
 };
 
 // The atmosphere in FP64, as the table builder integrates it.

@@ -170,7 +170,7 @@ __device__ __forceinline__ bool lv1_drop(const PropParams& pp, const DetParams& 
 // Planar: the origin is the ground intercept of the segment's line (float-float).
 // Spherical shell: the start point (float-float), its altitude above h_obs,
 // the radial component of P, 1 / r and the tilt of the local vertical.
-template <bool SPH, typename SM>
+template <bool SPH, bool FL, typename SM>
 __device__ __forceinline__ int import_segment(SM& S, int t, const cs_segment* seg, const PropParams& pp,
                                               const AtmParams& ap, const DetParams& dp, unsigned int& invalid,
                                               unsigned int& dropped) {
@@ -235,9 +235,10 @@ __device__ __forceinline__ int import_segment(SM& S, int t, const cs_segment* se
         dropped += 1;
         return 0;
     }
-    // local origin: G = S_xy - Hs P_xy / P_z in float-float
+    // local origin: G = S_xy - Hs P_xy / P_z in float-float (isotropic fluorescence keeps the
+    // start point: its photons land anywhere, not near the track's own ground point)
     float Gxh = x_hi, Gxl = x_lo, Gyh = y_hi, Gyl = y_lo;
-    if (Pz < -1e-3f) {
+    if (Pz < -1e-3f && !FL) {
         const float sx = Px / Pz, sy = Py / Pz;                       // slopes, float-float via FMA remainder
         const float sx_l = fmaf(-sx, Pz, Px) / Pz, sy_l = fmaf(-sy, Pz, Py) / Pz;
         const float px = Hs_hi * sx, py = Hs_hi * sy;
@@ -268,10 +269,23 @@ __device__ __forceinline__ int import_segment(SM& S, int t, const cs_segment* se
     return K;
 }
 
+// Fluorescence line of bunch (segment, k, i): a second Philox draw, its 24-bit
+// integer against the lines' cumulative yield shares in units of 2^-24.
+__device__ __forceinline__ float fluorescence_line(const PropParams& pp, uint32_t g_lo, uint32_t g_hi, uint32_t k,
+                                                  uint32_t i) {
+    const PropParams& fp = pp;
+    const uint4 r = philox(g_lo, g_hi, k, i | 0x80000000u, pp.key0, pp.key1);
+    const uint32_t v = r.x >> 8;
+    int line = fp.fl_n - 1;
+    for (int l = fp.fl_n - 2; l >= 0; --l)
+        if (v < fp.fl_thr[l]) line = l;
+    return fp.fl_inv_l[line];
+}
+
 // Stage 2 (Eq. 2.2-2.5, Sec. 4.2.1): sub-step k of tile segment sg at local
 // slot q: angle and mean bunch count at the sub-step midpoint, stochastic
 // rounding with the sub-step's own draw.  Returns the bunch count.
-template <bool SPH, typename SM>
+template <bool SPH, bool FL, typename SM>
 __device__ __forceinline__ int substep(SM& S, int q, int sg, int k, long long base, const PropParams& pp,
                                        const AtmParams& ap) {
     const float4 B = S.segB[sg];
@@ -288,7 +302,8 @@ __device__ __forceinline__ int substep(SM& S, int q, int sg, int k, long long ba
     // 1 - 1/(beta n)^2 without forming 1/(beta n)^2 (cancellation-free)
     const float sin2 = (d * (2.0f + d) - onepd * onepd * g) * rcp_approx(onepd * onepd * (1.0f - g));
     float nbar = 0.0f;
-    if (sin2 > 0.0f) nbar = ap.ft * S.z2[sg] * sin2 * B.z * rcp_approx((float)S.bunch[sg]);
+    if constexpr (FL) nbar = pp.fl_yd * S.z2[sg] * d * B.z * rcp_approx((float)S.bunch[sg]);   // Eq. 2.6
+    else if (sin2 > 0.0f) nbar = ap.ft * S.z2[sg] * sin2 * B.z * rcp_approx((float)S.bunch[sg]);
     const unsigned long long gid = pp.seg_base + (unsigned long long)(base + sg);
     const uint4 rc = philox((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0xFFFFFFFFu, pp.key0, pp.key1);
     const float uk = uniform24(rc.x);
@@ -496,7 +511,7 @@ __device__ __forceinline__ void correction_fields(const AtmParams& ap, bool use_
 // (Sec. 4.4.1) or the surrogate network, transmission (Sec. 4.3.1) and
 // detection.  With SURR the whole warpgroup must call (inactive threads pass
 // active = false): the network runs on the tensor cores for 128 photons.
-template <bool SURR, bool SPH, bool REC, typename SM>
+template <bool SURR, bool SPH, bool REC, bool FL, typename SM>
 __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, long long base,
                                       const PropParams& pp, const AtmParams& ap, const DetParams& dp,
                                       const OutParams& op, const SurrogateView& sv, TcSmem<kThreadsSur / 128>* tcs,
@@ -517,14 +532,26 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
     // M the 180-degree rotation about the bisector of (0,0,-1) and P
     float sphi, cphi;
     sincos_2pi(u1, sphi, cphi);
-    const float inv_l = ap.inv_l1_nm - u2 * ap.dinv_l_nm;   // 1/lambda^2 spectrum
+    const float inv_l_c = ap.inv_l1_nm - u2 * ap.dinv_l_nm;   // 1/lambda^2 spectrum
     const float ce = (Px * cphi + Py * sphi) * A.w;
     const float ct = Q.x, st = Q.y;
     // x and y components two lanes per packed FP32 instruction
     const float2 mxy = __ffma2_rn(make_float2(Px, Py), make_float2(ce, ce), make_float2(-cphi, -sphi));
     const float mz = (Pz - 1.0f) * ce;
-    const float2 uxy = __ffma2_rn(make_float2(ct, ct), make_float2(Px, Py), __fmul2_rn(make_float2(st, st), mxy));
-    const float ux = uxy.x, uy = uxy.y, uz = ct * Pz + st * mz;
+    const float2 uxy_c = __ffma2_rn(make_float2(ct, ct), make_float2(Px, Py), __fmul2_rn(make_float2(st, st), mxy));
+    const float uz_c = ct * Pz + st * mz;
+    float2 uxy_f = uxy_c;
+    float uz_f = uz_c, inv_l_f = inv_l_c;
+    if constexpr (FL) {   // fluorescence (Sec. 4.2.2): isotropic, the line from a second draw
+        const float c = pp.emission == CS_EMIT_FLUORESCENCE_HALF ? u2 - 1.0f : fmaf(2.0f, u2, -1.0f);
+        const float sn = sqrtf(fmaxf(fmaf(-c, c, 1.0f), 0.0f));
+        uxy_f = make_float2(sn * cphi, sn * sphi);
+        uz_f = c;
+        inv_l_f = fluorescence_line(pp, (uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, (uint32_t)i);
+    }
+    const float2 uxy = FL ? uxy_f : uxy_c;
+    const float uz = FL ? uz_f : uz_c, inv_l = FL ? inv_l_f : inv_l_c;
+    const float ux = uxy.x, uy = uxy.y;
     // height above the observation level and the local zenith
     float dz, cos_z, sin2;
     float4 Cc, Dd;
@@ -575,7 +602,7 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
     float x = 0.0f, y = 0.0f, t_rel = ell * B.w;
     float rx = 0.0f, ry = 0.0f;
     if (status == CS_ST_LANDED && !SPH) {
-        if (Pz < -1e-3f) {
+        if (Pz < -1e-3f && !FL) {
             // I - G = dz (P_xy / P_z - u_xy / u_z); the numerator is sin(theta) (P x m)
             const float pmx = Pz * sphi - ce * Py, pmy = ce * Px - Pz * cphi;
             const float fac = dz * st * rcp_approx(Pz * uz);
@@ -783,7 +810,7 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
     if (REC) emit_record(op, gid, k, i, x, y, t_rel, inv_l, tel, bin, status, pix);
 }
 
-template <bool SURR, bool SPH, int MINB, bool REC, int NT = SURR ? kThreadsSur : kThreads>
+template <bool SURR, bool SPH, int MINB, bool REC, bool FL = false, int NT = SURR ? kThreadsSur : kThreads>
 __global__ void __launch_bounds__(NT, MINB)
 propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, const OutParams op,
                  unsigned int* tile_ctr, const SurrogateView sv) {
@@ -809,7 +836,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
             if (tile >= n_wtiles) break;
             const long long base = tile * kWTile;
             const int Kt = base + lane < pp.n
-                               ? import_segment<SPH>(W, lane, pp.segs + base + lane, pp, ap, dp, invalid, dropped)
+                               ? import_segment<SPH, FL>(W, lane, pp.segs + base + lane, pp, ap, dp, invalid, dropped)
                                : 0;
             int incl = Kt;
 #pragma unroll
@@ -840,7 +867,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                     for (int q = q0; q < q1; ++q) {
                         const int qq = sub0 + q;
                         while (W.offK[sg + 1] <= qq) ++sg;   // next non-empty segment
-                        const int N = substep<SPH>(W, q, sg, qq - W.offK[sg], base, pp, ap);
+                        const int N = substep<SPH, FL>(W, q, sg, qq - W.offK[sg], base, pp, ap);
                         my_ph += N;
                         my_emit += (unsigned int)N * (unsigned int)W.bunch[sg];
                     }
@@ -868,7 +895,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                     __syncwarp();
                     for (int p = lane; p < wn; p += 32) {
                         const unsigned int e = W.map[p];
-                        bunch<false, SPH, REC>(W, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), true, base,
+                        bunch<false, SPH, REC, FL>(W, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), true, base,
                                                pp, ap, dp, op, sv, tcs, T);
                     }
                     __syncwarp();
@@ -885,7 +912,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
             const long long base = tile * kTile;
 
             // ---- stage 1: import and filter (one segment per thread) -------------
-            const int Kt = (t < kTile && base + t < pp.n) ? import_segment<SPH>(S, t, pp.segs + base + t, pp, ap, dp, invalid, dropped) : 0;
+            const int Kt = (t < kTile && base + t < pp.n) ? import_segment<SPH, FL>(S, t, pp.segs + base + t, pp, ap, dp, invalid, dropped) : 0;
             int S_tot;
             const int offk = block_scan<NT>(Kt, S.wsum, buf, &S_tot);
             if (t < kTile) S.offK[t] = offk;
@@ -911,7 +938,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                     for (int q = q0; q < q1; ++q) {
                         const int qq = sub0 + q;
                         while (S.offK[sg + 1] <= qq) ++sg;   // next non-empty segment
-                        const int N = substep<SPH>(S, q, sg, qq - S.offK[sg], base, pp, ap);
+                        const int N = substep<SPH, FL>(S, q, sg, qq - S.offK[sg], base, pp, ap);
                         my_ph += N;
                         my_emit += (unsigned int)N * (unsigned int)S.bunch[sg];
                     }
@@ -938,7 +965,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                         const int p = pw + (t & (kGroup - 1));
                         const bool active = p < wn;
                         const unsigned int e = S.map[active ? p : pw];
-                        bunch<SURR, SPH, REC>(S, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), active, base, pp,
+                        bunch<SURR, SPH, REC, FL>(S, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), active, base, pp,
                                               ap, dp, op, sv, tcs, T);
                     }
                     __syncthreads();
@@ -996,7 +1023,12 @@ cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp
     // instances: (network or tables) x (sphere or plane) x (records or throughput)
     auto go = [&](auto kernel, int threads) { kernel<<<grid, threads, smem, stream>>>(pp, ap, dp, op, ctr, sv); };
     const bool rec = op.records != nullptr;
-    if (ap.spherical) {
+    if (pp.emission) {   // fluorescence: the exact tracer's own instances
+        if (ap.spherical)
+            rec ? go(propagate_kernel<false, true, 4, true, true>, kThreads) : go(propagate_kernel<false, true, 4, false, true>, kThreads);
+        else
+            rec ? go(propagate_kernel<false, false, 4, true, true>, kThreads) : go(propagate_kernel<false, false, 4, false, true>, kThreads);
+    } else if (ap.spherical) {
         if (sur) rec ? go(propagate_kernel<true, true, 1, true>, kThreadsSur) : go(propagate_kernel<true, true, 1, false>, kThreadsSur);
         else rec ? go(propagate_kernel<false, true, 4, true>, kThreads) : go(propagate_kernel<false, true, 4, false>, kThreads);
     } else if (sur) {
@@ -1015,6 +1047,10 @@ cs_status set_smem_attributes() {
     CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, false, 4, true>, attr, smem));
     CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, true, 4, false>, attr, smem));
     CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, true, 4, true>, attr, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, false, 4, false, true>, attr, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, false, 4, true, true>, attr, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, true, 4, false, true>, attr, smem));
+    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, true, 4, true, true>, attr, smem));
     CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, false, 1, false>, attr, smem_sur));
     CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, false, 1, true>, attr, smem_sur));
     CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, true, 1, false>, attr, smem_sur));
@@ -1084,7 +1120,21 @@ cs_status tile_counter(unsigned int** out) {
 }
 
 // The LV1 filter's parameters from the options (the counter as given: device memory here).
-void set_filters(PropParams& pp, const cs_opts& o, const DetParams& dp) {
+void set_filters(PropParams& pp, const cs_opts& o, const DetParams& dp, const AtmParams& ap) {
+    pp.emission = o.emission;
+    pp.fl_n = 0;
+    pp.fl_yd = 0.0f;
+    if (o.emission) {   // Eq. 2.6: z^2 dE/dX rho sum(yields), rho = rho_per_delta delta / 100 [g/cm^3]
+        double ysum = 0.0, cum = 0.0;
+        for (int l = 0; l < o.fl_n_lines; ++l) ysum += o.fl_yield_per_mev[l];
+        pp.fl_n = o.fl_n_lines;
+        for (int l = 0; l < o.fl_n_lines; ++l) {
+            cum += o.fl_yield_per_mev[l];
+            pp.fl_inv_l[l] = (float)(1.0 / o.fl_lines_nm[l]);
+            pp.fl_thr[l] = l + 1 < o.fl_n_lines ? (uint32_t)floor(cum / ysum * 16777216.0) : 16777216u;
+        }
+        pp.fl_yd = (float)(o.fl_dedx * ysum * ap.rho_per_delta * (o.emission == CS_EMIT_FLUORESCENCE_HALF ? 0.5 : 1.0));
+    }
     pp.lv3 = o.lv3 ? 1 : 0;
     for (int i = 0; i < 3; ++i) pp.lv3_c[i] = (float)o.lv3_centre[i];
     const double lim = o.lv3_radius + o.lv3_margin;
@@ -1101,6 +1151,20 @@ void set_filters(PropParams& pp, const cs_opts& o, const DetParams& dp) {
 }
 
 bool filters_valid(const cs_opts& o, const cs_atmosphere* atm) {
+    if (o.emission < CS_EMIT_CHERENKOV || o.emission > CS_EMIT_FLUORESCENCE_HALF) return false;
+    if (o.emission) {   // a line list, and no LV1 cut: isotropic light is not filtered (Sec. 4.3.2)
+        if (o.fl_n_lines < 1 || o.fl_n_lines > 8 || !o.fl_lines_nm || !o.fl_yield_per_mev ||
+            !(o.fl_dedx >= 0.0) || !isfinite(o.fl_dedx) || o.lv1_metric != CS_LV1_OFF || o.surrogate)
+            return false;
+        double ysum = 0.0;
+        for (int l = 0; l < o.fl_n_lines; ++l) {
+            if (!(o.fl_lines_nm[l] > 0.0) || !isfinite(o.fl_lines_nm[l]) || !(o.fl_yield_per_mev[l] >= 0.0) ||
+                !isfinite(o.fl_yield_per_mev[l]))
+                return false;
+            ysum += o.fl_yield_per_mev[l];
+        }
+        if (!(ysum > 0.0)) return false;
+    }
     if (o.tracer != CS_TRACER_TABLES &&
         (o.tracer != CS_TRACER_SNELL || !(o.tracer_dh >= 0.01) || !isfinite(o.tracer_dh) || o.surrogate ||
          atm->p.spherical))
@@ -1166,7 +1230,7 @@ cs_status launch(const cs_segment* d_segs, size_t n, const cs_atmosphere* atm, c
     pp.bunch = o.bunch;
     pp.shower_bunch = nullptr;
     pp.s_max = (float)o.s_max;
-    set_filters(pp, o, det->p);
+    set_filters(pp, o, det->p, atm->p);
     static bool attr_done = false;
     if (!attr_done) {
         cs_status sa = set_smem_attributes();
@@ -1379,7 +1443,7 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     pp.bunch = o.bunch;
     pp.shower_bunch = nullptr;
     pp.s_max = (float)o.s_max;
-    set_filters(pp, o, det->p);
+    set_filters(pp, o, det->p, atm->p);
     if ((st = set_smem_attributes()) != CS_OK) return st;
     const int per_sm = default_blocks_per_sm(o);
     const long long tiles = ((long long)n + kTile - 1) / kTile;
@@ -1449,7 +1513,7 @@ cs_status enqueue(const cs_segment* segs, size_t n, const cs_atmosphere* atm, co
     pp.bunch = o.bunch;
     pp.shower_bunch = d_bunch;
     pp.s_max = (float)o.s_max;
-    set_filters(pp, o, det->p);
+    set_filters(pp, o, det->p, atm->p);
     CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), stream));
     return launch_kernel(grid, stream, pp, atm->p, dp, op, ctr, o.surrogate);
 }

@@ -393,6 +393,10 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
     p.inv_l1_nm = (float)(1.0 / l1_nm);
     p.dinv_l_nm = (float)(1.0 / l1_nm - 1.0 / l2_nm);
     p.ft = (float)(2.0 * kPi * kAlpha * (1.0 / d->lambda_min - 1.0 / d->lambda_max));
+    // density per unit n - 1, in g/cm^2 per metre: the stepper's columns and the fluorescence yield
+    p.rho_per_delta = a.kind == CS_ATM_LAYERED ? (float)(100.0 * a.rho0 / a.kappa)
+                    : a.kind == CS_ATM_TABLE   ? (float)(100.0 * kTableRhoRef / a.kappa)
+                                               : 0.0f;
     if (p.transmission) {
         if (!(d->rayl_X0 > 0.0) || !(d->rayl_lambda0 > 0.0) || !(d->aer_lambda0 > 0.0)) {
             cudaFree(h->d_nodes);
@@ -402,9 +406,6 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
         const double lR = d->rayl_lambda0 * 1e9;
         p.kR0 = (float)(kLog2e * lR * lR * lR * lR / d->rayl_X0);
         p.kA0 = (float)(kLog2e * d->aer_tau0 / a.H_A);
-        p.rho_per_delta = a.kind == CS_ATM_LAYERED ? (float)(100.0 * a.rho0 / a.kappa)
-                        : a.kind == CS_ATM_TABLE   ? (float)(100.0 * kTableRhoRef / a.kappa)
-                                                   : 0.0f;
         p.aer_hobs = (float)exp(-d->h_obs / a.H_A);
         p.aer_c2 = (float)(-kLog2e / a.H_A);
         p.lamA_nm = (float)(d->aer_lambda0 * 1e9);
