@@ -140,7 +140,7 @@ def test_many_bunches_exercise_map_windows():
     far more bunches than one window of its bunch map."""
     segs = synth.tiny_vertical_segments(150, seed=9)
     segs["length"][:] = np.float32(12.0)
-    g, o = _run_both(segs, True, True, 1)
+    g, o = _run_both(segs, True, True, 1, record_capacity=200_000)
     st = PU.compare(g, o, bunch=1)
     assert st["matched"] > 15000
     PU.check_conservation(g["counters"])
