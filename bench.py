@@ -635,6 +635,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-optics", action="store_true")
     ap.add_argument("--no-snell", action="store_true")
+    ap.add_argument("--no-fluorescence", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -833,6 +834,29 @@ def main():
                  "bunches_per_s": int(cnt[0].item()) / bunch / (sn_ms / 1e3),
                  "method": "Snell vector stepper, slabs <= 10 m, FP32, one traced path per bunch"}
 
+    fluor = None
+    if not args.no_fluorescence:
+        # the second emission workload: nitrogen fluorescence (Eq. 2.6, Sec. 4.2.2) from the same
+        # segments, isotropic into the downward half sphere, synthetic five-line list
+        keep = B.set_fluorescence(o, dict(synth.FLUORESCENCE, half=True))   # noqa: F841
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        k_fl = max(3, args.steps // 10)
+        fl_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k_fl)]
+        for a, b_ in fl_ev:
+            flush.zero_()
+            a.record(stream)
+            step()
+            b_.record(stream)
+        torch.cuda.synchronize()
+        fl_ms = sum(a.elapsed_time(b_) for a, b_ in fl_ev) / k_fl
+        fl_photons = int(cnt[0].item())
+        o.emission = B.CS_EMIT_CHERENKOV
+        fluor = {"value": fl_photons / (fl_ms / 1e3), "unit": UNIT, "ms_per_step": fl_ms, "steps": k_fl,
+                 "photons_per_step": fl_photons, "bunches_per_s": fl_photons / bunch / (fl_ms / 1e3),
+                 "emission": "nitrogen fluorescence, downward half sphere, 5 synthetic lines, dE/dX 2.2 MeV cm^2/g"}
+
     e2e = None
     if not args.no_e2e:
         # end to end through the host-pointer call: pinned segments in, outputs out
@@ -893,6 +917,7 @@ def main():
             "surrogate": surrogate,
             "optics": optics,
             "snell_tracer": snell,
+            "fluorescence": fluor,
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": sm_clk,
