@@ -114,6 +114,7 @@ def lib():
             L.orc_refract_closed.restype = C.c_int
             L.orc_snell_stepper.argtypes = [C.POINTER(Atm), d, d, d, d, dp]
             L.orc_snell_path.argtypes = [C.POINTER(Atm), d, d, d, d, d, dp]
+            L.orc_snell_path_sph.argtypes = [C.POINTER(Atm), d, d, d, d, d, d, dp]
             L.orc_sph_path.argtypes = [C.POINTER(Atm), d, d, d, d, d, C.c_int, d, dp]
             L.orc_ae_inverse.argtypes = [d, d, d, d, d, dp]
             L.orc_propagate.argtypes = [C.c_void_p, C.c_size_t, C.POINTER(Atm), C.POINTER(Config),
@@ -222,6 +223,13 @@ def snell_path(atm, h_obs, h_e, theta0, dh, H_A=1200.0):
     """{R, t_path, X_slant, A_slant} of the Snell vector stepper."""
     out = (C.c_double * 4)()
     lib().orc_snell_path(C.byref(atm), h_obs, h_e, theta0, dh, H_A, out)
+    return np.array(out[:])
+
+
+def snell_path_sph(atm, h_obs, h_e, psi0, dh, R=None, H_A=1200.0):
+    """{central angle, t_path, X_slant, A_slant} of the stepper on the spherical shell."""
+    out = (C.c_double * 4)()
+    lib().orc_snell_path_sph(C.byref(atm), EARTH_RADIUS if R is None else R, h_obs, h_e, psi0, dh, H_A, out)
     return np.array(out[:])
 
 

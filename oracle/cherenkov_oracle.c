@@ -520,6 +520,47 @@ void orc_snell_path(const orc_atm* a, double h_obs, double h_e, double theta0, d
     out[0] = x; out[1] = t; out[2] = X; out[3] = A;
 }
 
+/* The same stepper on the spherical shell: shells of equal thickness <= dh in
+ * altitude, each holding n at its middle altitude; inside a shell the photon
+ * runs straight to the next inner sphere, where Eq. 3.15 refracts it about the
+ * radial normal.  Worked in the plane of travel: p = (x, y) with the Earth's
+ * centre at the origin and the emission point at (0, R + h_e); direction at
+ * local zenith psi0 towards +x.  out = {central angle, t_path, X_slant, A_slant}. */
+void orc_snell_path_sph(const orc_atm* a, double R, double h_obs, double h_e, double psi0, double dh, double H_A,
+                        double out[4])
+{
+    double px = 0.0, py = R + h_e;
+    double dx = sin(psi0), dy = -cos(psi0);
+    double t = 0.0, X = 0.0, A = 0.0;
+    int nsteps = (int)ceil((h_e - h_obs) / dh - 1e-9);
+    if (nsteps < 1) nsteps = 1;
+    const double step = (h_e - h_obs) / nsteps;
+    double n1 = orc_n(a, h_e - 0.5 * step);
+    for (int j = 0; j < nsteps; ++j) {
+        const double h_mid = h_e - (j + 0.5) * step;
+        const double r_in = R + h_e - (j + 1) * step;
+        /* first crossing of |p + s d| = r_in: s^2 + 2 (p.d) s + |p|^2 - r_in^2 = 0 */
+        const double pd = px * dx + py * dy, c = px * px + py * py - r_in * r_in;
+        const double disc = pd * pd - c;
+        const double sq = sqrt(fmax(disc, 0.0));
+        const double sl = c / (-pd + sq);           /* the smaller root, without cancellation */
+        px += sl * dx; py += sl * dy;
+        t += sl * n1 / ORC_C_LIGHT;
+        X += 100.0 * orc_atm_rho(a, h_mid) * sl;
+        A += exp(-h_mid / H_A) * sl;
+        if (j + 1 == nsteps) break;
+        const double n2 = orc_n(a, h_mid - step);
+        /* Eq. 3.15 with N the inward normal at the crossing */
+        const double r = sqrt(px * px + py * py), Nx = -px / r, Ny = -py / r;
+        const double cos_a1 = dx * Nx + dy * Ny;
+        const double cc = sqrt(n2 * n2 - n1 * n1 + n1 * n1 * cos_a1 * cos_a1) - n1 * cos_a1;
+        const double Ax = n1 * dx + cc * Nx, Ay = n1 * dy + cc * Ny;
+        dx = Ax / n2; dy = Ay / n2;
+        n1 = n2;
+    }
+    out[0] = atan2(px, py); out[1] = t; out[2] = X; out[3] = A;
+}
+
 /* {R, t_path} of the stepper (the pins' entry point). */
 void orc_snell_stepper(const orc_atm* a, double h_obs, double h_e, double theta0, double dh,
                        double out[2])
@@ -1152,7 +1193,23 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                 } else {
                     /* the path stays in the plane (centre, E, u): rotate the vertical by the
                      * central angle Phi towards hv; Bouguer's invariant gives the arrival zenith */
-                    orc_sph_path(atm, R, cfg->h_obs, h_e, theta0, cfg->aer_H, cfg->refraction, cfg->quad_rtol, path);
+                    if (cfg->refraction && cfg->tracer == 1) {
+                        orc_snell_path_sph(atm, R, cfg->h_obs, h_e, theta0, cfg->tracer_dh, cfg->aer_H, path);
+                        const double q = (h_e - cfg->h_obs) / cfg->tracer_dh;
+                        if (fabs(q - nearbyint(q)) < 1e-3) rec.flags |= ORC_FL_LAYER;
+                        int ns = (int)ceil(q - 1e-9); if (ns < 1) ns = 1;
+                        const double step = (h_e - cfg->h_obs) / ns;
+                        if (atm->kind == ORC_ATM_LAYERED) {
+                            for (int li = 1; li <= atm->n_layers; ++li) {
+                                const double hb = li < atm->n_layers ? atm->layer_h[li] : atm->h_top;
+                                if (!(hb > cfg->h_obs && hb < h_e)) continue;
+                                const double f = (h_e - hb) / step - 0.5;
+                                if (fabs(f - nearbyint(f)) * step < 0.01) rec.flags |= ORC_FL_LAYER;
+                            }
+                        }
+                    } else {
+                        orc_sph_path(atm, R, cfg->h_obs, h_e, theta0, cfg->aer_H, cfg->refraction, cfg->quad_rtol, path);
+                    }
                     const double rg = R + cfg->h_obs, Phi = path[0];
                     double vG[3], hG[3];
                     for (int c = 0; c < 3; ++c) {

@@ -75,3 +75,48 @@ def test_pipeline_stepper_lands_where_the_exact_path_does():
     assert (err <= 2e-3 * shift + 1e-6).all(), float((err / np.maximum(shift, 1e-9)).max())
     dt = np.abs(ex["dt"] - st["dt"])[m] / ex["dt"][m]
     assert dt.max() < 1e-7
+
+
+# ---- the spherical shell ----------------------------------------------------
+@pytest.mark.parametrize("deg", [30.0, 60.0, 75.0])
+def test_shell_stepper_converges_to_the_bouguer_quadrature(deg):
+    th = math.radians(deg)
+    q = oracle.sph_path(LAY, 2000.0, 15000.0, th, rtol=1e-12)
+    errs = np.array([np.abs(oracle.snell_path_sph(LAY, 2000.0, 15000.0, th, dh) - q) / np.abs(q)
+                     for dh in (20.0, 2.0, 0.2)])
+    assert (errs[2] < 2e-8).all(), errs
+    assert (errs[1] < errs[0]).all() and (errs[2][:2] < errs[1][:2]).all()
+
+
+def test_shell_stepper_vertical_equals_the_slab_stepper():
+    """Straight down, shells and slabs are the same layers."""
+    s = oracle.snell_path_sph(LAY, 2000.0, 12000.0, 0.0, 7.0)
+    p = oracle.snell_path(LAY, 2000.0, 12000.0, 0.0, 7.0)
+    assert s[0] == 0.0
+    np.testing.assert_allclose(s[1:], p[1:], rtol=1e-12)
+
+
+def test_shell_stepper_in_a_homogeneous_medium_is_the_straight_line():
+    hom = oracle.make_atm(oracle.ATM_HOMOGENEOUS, hom_delta=3e-4)
+    for deg in (20.0, 70.0):
+        th = math.radians(deg)
+        s = oracle.snell_path_sph(hom, 2000.0, 9000.0, th, 5.0)
+        line = oracle.sph_path(hom, 2000.0, 9000.0, th, refraction=False)
+        assert abs(s[0] - line[0]) < 1e-10 * max(line[0], 1e-3)   # FP64 with r^2 ~ 4e13 m^2
+        assert abs(s[1] - (1 + 3e-4) * line[1]) < 1e-10 * s[1]
+
+
+def test_pipeline_shell_stepper_lands_where_the_exact_path_does():
+    segs = synth.shower_segments(300, 60.0, 20.0, 1e13, seed=5)
+    kw = dict(bunch=2, refraction=True, transmission=False, seed=4, spherical=True)
+    ex = oracle.propagate(segs, LAY, **kw)["records"]
+    st = oracle.propagate(segs, LAY, snell_dh=1.0, **kw)["records"]
+    assert np.array_equal(ex["seg"], st["seg"]) and np.array_equal(ex["status"], st["status"])
+    m = ex["status"] == oracle.ST_LANDED
+    assert m.sum() > 3000
+    line = oracle.propagate(segs, LAY, bunch=2, refraction=False, transmission=False, use_domain=True, seed=4,
+                            spherical=True)["records"]
+    shift = np.hypot(ex["x"] - line["x"], ex["y"] - line["y"])[m]
+    err = np.hypot(ex["x"] - st["x"], ex["y"] - st["y"])[m]
+    assert shift.max() > 1.0
+    assert (err <= 1e-3 * shift + 1e-4).all(), float((err / np.maximum(shift, 1e-9)).max())
