@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <functional>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "mlp_tc.cuh"
@@ -462,6 +463,46 @@ __device__ __noinline__ float4 snell_path(const AtmParams& ap, float dz, float c
                        ap.aer_hobs * step * sA);
 }
 
+// The same stepper on the spherical shell: shells of equal thickness <= dh in
+// altitude; inside a shell the photon runs straight to the next inner sphere,
+// where Eq. 3.15 refracts it about the radial normal.  A straight line keeps
+// its impact parameter r sin(psi), and Eq. 3.15 at a spherical boundary keeps
+// n r sin(psi), so in shell j the photon runs with impact parameter
+// b_j = K / n_j, K = n_0 r_e sin(psi_0) (the same algebra in FP32-stable
+// scalar form).  A chord from r_out to r_in = r_out - step with impact
+// parameter b has length step (r_out + r_in) / (q_out + q_in), q = sqrt(r^2 -
+// b^2), and sweeps the central angle asin(b t / (r_in r_out)); the straight
+// line (b_0 = r_e sin(psi_0)) is walked through the same shells and the
+// differences are summed.  Returns {arc-length correction along the ground
+// r_g (Phi - Phi_line) [m], c t_path - straight length [m], X_slant, A_slant}.
+__device__ __noinline__ float4 snell_path_sph(const AtmParams& ap, float dz, float sin2, float dh) {
+    const int ns = max(1, (int)ceilf(dz / dh));
+    const float step = dz / (float)ns;
+    const float d0 = delta_at(ap, dz - 0.5f * step);
+    const float re = ap.rg + dz;
+    const float b0 = re * sqrtf(sin2);
+    float sPhi = 0.0f, sT = 0.0f, sX = 0.0f, sA = 0.0f;
+    for (int j = 0; j < ns; ++j) {
+        const float h = dz - ((float)j + 0.5f) * step;
+        const float dj = j == 0 ? d0 : delta_at(ap, h);
+        const float r_out = re - (float)j * step, r_in = r_out - step;
+        const float rs = fmaf(-2.0f * (float)j - 1.0f, step, 2.0f * re);   // r_out + r_in
+        const float b = b0 + b0 * (d0 - dj) * rcp_approx(1.0f + dj);
+        const float q_out = sqrtf((r_out - b) * (r_out + b)), q_in = sqrtf((r_in - b) * (r_in + b));
+        const float p_out = sqrtf((r_out - b0) * (r_out + b0)), p_in = sqrtf((r_in - b0) * (r_in + b0));
+        const float t = step * rs * rcp_approx(q_out + q_in);
+        const float t0 = step * rs * rcp_approx(p_out + p_in);
+        const float irr = rcp_approx(r_in * r_out);
+        sPhi += (b * t - b0 * t0) * irr;
+        sT += fmaf(dj, t, t - t0);
+        if (ap.transmission) {
+            sX = fmaf(dj, t, sX);
+            sA = fmaf(ex2_approx(ap.aer_c2 * h), t, sA);
+        }
+    }
+    return make_float4(ap.rg * sPhi, sT, ap.rho_per_delta * sX, ap.aer_hobs * sA);
+}
+
 // The correction fields at (dz, tan^2 of the local zenith) and the
 // transmission: the network's outputs where it applies, else the bilinear
 // table lookup; (0, 0, 1) without tables.
@@ -511,7 +552,7 @@ __device__ __forceinline__ void correction_fields(const AtmParams& ap, bool use_
 // (Sec. 4.4.1) or the surrogate network, transmission (Sec. 4.3.1) and
 // detection.  With SURR the whole warpgroup must call (inactive threads pass
 // active = false): the network runs on the tensor cores for 128 photons.
-template <bool SURR, bool SPH, bool REC, bool FL, typename SM>
+template <bool SURR, bool SPH, bool REC, bool FL, bool TR, typename SM>
 __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, long long base,
                                       const PropParams& pp, const AtmParams& ap, const DetParams& dp,
                                       const OutParams& op, const SurrogateView& sv, TcSmem<kThreadsSur / 128>* tcs,
@@ -621,7 +662,7 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
     if (status == CS_ST_LANDED && !SPH) {
         float path = dz * inv_uz;
         float GR, Gt, Tr;
-        if (!SURR && pp.snell && ap.refraction) {   // the per-photon stepper instead of the tables
+        if (TR && ap.refraction) {   // the per-photon stepper instead of the tables
             const float4 sp = snell_path(ap, dz, cos_z, pp.snell_dh);
             const float2 r2 = __ffma2_rn(make_float2(sp.x, sp.x), uxy, make_float2(rx, ry));
             rx = r2.x;
@@ -726,7 +767,20 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
         }
         if (status == CS_ST_LANDED) {
             float GR, Gt, Tr;
-            correction_fields<SURR>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
+            const bool stepper = TR && ap.refraction;
+            if (stepper) {   // the per-photon stepper instead of the tables
+                const float4 sp = snell_path_sph(ap, dz, sin2, pp.snell_dh);
+                GR = sp.x;   // here the arc-length correction itself
+                Gt = sp.y;   // and the delay as a length
+                Tr = 1.0f;
+                if (ap.transmission) {
+                    const float il2 = inv_l * inv_l;
+                    const float kA = ap.kA0 * ex2_approx(ap.aer_alpha * lg2_approx(ap.lamA_nm * inv_l));
+                    Tr = ex2_approx(-(sp.z * (ap.kR0 * il2 * il2) + sp.w * kA));
+                }
+            } else {
+                correction_fields<SURR>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
+            }
             // ground tangent in the plane of travel at the landing point
             const float irg = ap.inv_rg;
             const float gvx = Gx * irg, gvy = Gy * irg, gvz = (Gz - h_obs_f) * irg;   // v_G - z-hat
@@ -738,11 +792,11 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
             tz *= tn;
             float path = tt;
             if (ap.refraction) {   // arc-length correction along the ground, delay
-                const float dR = GR * inv_uz * inv_uz * inv_uz * sqrtf(sin2);
+                const float dR = stepper ? GR : GR * inv_uz * inv_uz * inv_uz * sqrtf(sin2);
                 Gx = fmaf(dR, tx, Gx);
                 Gy = fmaf(dR, ty, Gy);
                 Gz = fmaf(dR, tz, Gz);
-                path = fmaf(Gt, inv_uz, path);
+                path = stepper ? path + Gt : fmaf(Gt, inv_uz, path);
             }
             t_rel = fmaf(path, kInvC, t_rel);
             // azimuthal-equidistant coordinates: r_g atan(rho / z_c) along (G_x, G_y)
@@ -810,7 +864,8 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
     if (REC) emit_record(op, gid, k, i, x, y, t_rel, inv_l, tel, bin, status, pix);
 }
 
-template <bool SURR, bool SPH, int MINB, bool REC, bool FL = false, int NT = SURR ? kThreadsSur : kThreads>
+template <bool SURR, bool SPH, int MINB, bool REC, bool FL = false, bool TR = false,
+          int NT = SURR ? kThreadsSur : kThreads>
 __global__ void __launch_bounds__(NT, MINB)
 propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, const OutParams op,
                  unsigned int* tile_ctr, const SurrogateView sv) {
@@ -895,7 +950,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                     __syncwarp();
                     for (int p = lane; p < wn; p += 32) {
                         const unsigned int e = W.map[p];
-                        bunch<false, SPH, REC, FL>(W, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), true, base,
+                        bunch<false, SPH, REC, FL, TR>(W, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), true, base,
                                                pp, ap, dp, op, sv, tcs, T);
                     }
                     __syncwarp();
@@ -965,7 +1020,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                         const int p = pw + (t & (kGroup - 1));
                         const bool active = p < wn;
                         const unsigned int e = S.map[active ? p : pw];
-                        bunch<SURR, SPH, REC, FL>(S, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), active, base, pp,
+                        bunch<SURR, SPH, REC, FL, TR>(S, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), active, base, pp,
                                               ap, dp, op, sv, tcs, T);
                     }
                     __syncthreads();
@@ -1023,34 +1078,46 @@ cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp
     // instances: (network or tables) x (sphere or plane) x (records or throughput)
     auto go = [&](auto kernel, int threads) { kernel<<<grid, threads, smem, stream>>>(pp, ap, dp, op, ctr, sv); };
     const bool rec = op.records != nullptr;
-    if (pp.emission) {   // fluorescence: the exact tracer's own instances
-        if (ap.spherical)
-            rec ? go(propagate_kernel<false, true, 4, true, true>, kThreads) : go(propagate_kernel<false, true, 4, false, true>, kThreads);
-        else
-            rec ? go(propagate_kernel<false, false, 4, true, true>, kThreads) : go(propagate_kernel<false, false, 4, false, true>, kThreads);
+    // the exact tracer's instances: emission (Cherenkov or fluorescence) x tracer (tables or stepper)
+    auto exact = [&](auto sph, auto fl, auto tr) {
+        constexpr bool S = decltype(sph)::value, F = decltype(fl)::value, T = decltype(tr)::value;
+        rec ? go(propagate_kernel<false, S, 4, true, F, T>, kThreads) : go(propagate_kernel<false, S, 4, false, F, T>, kThreads);
+    };
+    using t_ = std::true_type;
+    using f_ = std::false_type;
+    const bool fl = pp.emission != 0, tr = pp.snell != 0;
+    if (sur) {
+        if (ap.spherical) rec ? go(propagate_kernel<true, true, 1, true>, kThreadsSur) : go(propagate_kernel<true, true, 1, false>, kThreadsSur);
+        else rec ? go(propagate_kernel<true, false, 1, true>, kThreadsSur) : go(propagate_kernel<true, false, 1, false>, kThreadsSur);
     } else if (ap.spherical) {
-        if (sur) rec ? go(propagate_kernel<true, true, 1, true>, kThreadsSur) : go(propagate_kernel<true, true, 1, false>, kThreadsSur);
-        else rec ? go(propagate_kernel<false, true, 4, true>, kThreads) : go(propagate_kernel<false, true, 4, false>, kThreads);
-    } else if (sur) {
-        rec ? go(propagate_kernel<true, false, 1, true>, kThreadsSur) : go(propagate_kernel<true, false, 1, false>, kThreadsSur);
+        if (fl) tr ? exact(t_{}, t_{}, t_{}) : exact(t_{}, t_{}, f_{});
+        else tr ? exact(t_{}, f_{}, t_{}) : exact(t_{}, f_{}, f_{});
     } else {
-        rec ? go(propagate_kernel<false, false, 4, true>, kThreads) : go(propagate_kernel<false, false, 4, false>, kThreads);
+        if (fl) tr ? exact(f_{}, t_{}, t_{}) : exact(f_{}, t_{}, f_{});
+        else tr ? exact(f_{}, f_{}, t_{}) : exact(f_{}, f_{}, f_{});
     }
     CS_CUDA_TRY(cudaGetLastError());
     return CS_OK;
 }
 
+template <bool S, bool F, bool T>
+cudaError_t set_exact_smem(int smem) {
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(propagate_kernel<false, S, 4, false, F, T>, attr, smem);
+    return e != cudaSuccess ? e : cudaFuncSetAttribute(propagate_kernel<false, S, 4, true, F, T>, attr, smem);
+}
+
 cs_status set_smem_attributes() {
     const int smem = (int)kSmemExact, smem_sur = (int)kSmemSurrogate;
     const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, false, 4, false>, attr, smem));
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, false, 4, true>, attr, smem));
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, true, 4, false>, attr, smem));
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, true, 4, true>, attr, smem));
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, false, 4, false, true>, attr, smem));
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, false, 4, true, true>, attr, smem));
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, true, 4, false, true>, attr, smem));
-    CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<false, true, 4, true, true>, attr, smem));
+    CS_CUDA_TRY((set_exact_smem<false, false, false>(smem)));
+    CS_CUDA_TRY((set_exact_smem<false, false, true>(smem)));
+    CS_CUDA_TRY((set_exact_smem<false, true, false>(smem)));
+    CS_CUDA_TRY((set_exact_smem<false, true, true>(smem)));
+    CS_CUDA_TRY((set_exact_smem<true, false, false>(smem)));
+    CS_CUDA_TRY((set_exact_smem<true, false, true>(smem)));
+    CS_CUDA_TRY((set_exact_smem<true, true, false>(smem)));
+    CS_CUDA_TRY((set_exact_smem<true, true, true>(smem)));
     CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, false, 1, false>, attr, smem_sur));
     CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, false, 1, true>, attr, smem_sur));
     CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, true, 1, false>, attr, smem_sur));
@@ -1166,8 +1233,7 @@ bool filters_valid(const cs_opts& o, const cs_atmosphere* atm) {
         if (!(ysum > 0.0)) return false;
     }
     if (o.tracer != CS_TRACER_TABLES &&
-        (o.tracer != CS_TRACER_SNELL || !(o.tracer_dh >= 0.01) || !isfinite(o.tracer_dh) || o.surrogate ||
-         atm->p.spherical))
+        (o.tracer != CS_TRACER_SNELL || !(o.tracer_dh >= 0.01) || !isfinite(o.tracer_dh) || o.surrogate))
         return false;
     if (o.lv3 && !(o.lv3_radius >= 0.0 && o.lv3_margin >= 0.0 && isfinite(o.lv3_radius + o.lv3_margin) &&
                    isfinite(o.lv3_centre[0]) && isfinite(o.lv3_centre[1]) && isfinite(o.lv3_centre[2])))

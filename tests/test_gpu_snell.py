@@ -43,6 +43,22 @@ def test_stepper_parity(kind, dh):
     assert g["counters"][B.CS_CNT_ABSORBED] > 0
 
 
+def test_shell_stepper_parity():
+    """The spherical shell: the kernel's invariant form of Eq. 3.15 against the
+    oracle's vector steps about the radial normal, over the same shells."""
+    segs = synth.shower_segments(1200, 60.0, 10.0, 1e13, seed=13)
+    tel = synth.poisson_disk_telescopes(n=300, half=250.0, seed=1)
+    atm = B.Atmosphere(layered=synth.US_STANDARD, refraction=True, transmission=True, spherical=True)
+    det = B.Detector(hist=HIST, tel=tel, spherical=True)
+    orc = oracle.make_atm(oracle.ATM_LAYERED, layered=synth.US_STANDARD)
+    g = B.propagate_host(segs, atm, det, seed=3, bunch=3, records=True, snell_dh=10.0)
+    o = oracle.propagate(segs, orc, hist=HIST, tel=tel, bunch=3, refraction=True, transmission=True, seed=3,
+                         spherical=True, snell_dh=10.0, bands=dict(band_pos=0.03))
+    st = PU.compare(g, o, bunch=3)
+    assert st["matched"] > 5000
+    PU.check_conservation(g["counters"])
+
+
 def test_stepper_and_tables_agree_up_to_the_discretisation():
     segs = synth.shower_segments(2000, 35.0, 50.0, 1e12, seed=12)
     atm = B.Atmosphere(layered=synth.US_STANDARD, refraction=True, transmission=False)
@@ -72,9 +88,6 @@ def test_stepper_rejects_what_it_does_not_cover():
     atm = B.Atmosphere(layered=synth.US_STANDARD, refraction=True, transmission=False)
     with pytest.raises(RuntimeError):
         B.propagate_host(segs, atm, det, seed=1, snell_dh=1e-4)      # slabs thinner than 1 cm
-    sph = B.Atmosphere(layered=synth.US_STANDARD, refraction=True, transmission=False, spherical=True)
-    with pytest.raises(RuntimeError):
-        B.propagate_host(segs, sph, B.Detector(hist=HIST, spherical=True), seed=1, snell_dh=10.0)
     sur = B.Surrogate(atm, epochs=1, n_train=1 << 16, n_heldout=1 << 12)
     with pytest.raises(RuntimeError):
         B.propagate_host(segs, atm, det, seed=1, snell_dh=10.0, surrogate=sur)
