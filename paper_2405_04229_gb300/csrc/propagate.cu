@@ -61,8 +61,8 @@ struct TileSmem {
 // (the surrogate's warpgroups, whose tensor-core network is collective, keep
 // the block-wide tile above).
 constexpr int kWTile = 32;              // segments per warp tile
-constexpr int kWSubCap = 96;            // sub-steps per warp round
-constexpr int kWMapCap = 384;           // bunches per warp map window
+constexpr int kWSubCap = 128;           // sub-steps per warp round
+constexpr int kWMapCap = 256;           // bunches per warp map window
 struct WarpSmem {
     float4 segA[kWTile], segB[kWTile], segC[kWTile], segD[kWTile];   // as in TileSmem
     double t0[kWTile];
