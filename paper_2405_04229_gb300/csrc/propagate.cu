@@ -70,6 +70,7 @@ struct WarpSmem {
     int shower[kWTile];
     int bunch[kWTile];
     int offK[kWTile + 1];
+    int perm[kWTile];      // tile slot of the i-th segment in processing order
     float4 sub[kWSubCap];
     int nsub_ph[kWSubCap];
     unsigned int map[kWMapCap];
@@ -890,9 +891,54 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
             const long long tile = (long long)__shfl_sync(0xffffffffu, wt, 0);
             if (tile >= n_wtiles) break;
             const long long base = tile * kWTile;
-            const int Kt = base + lane < pp.n
-                               ? import_segment<SPH, FL>(W, lane, pp.segs + base + lane, pp, ap, dp, invalid, dropped)
-                               : 0;
+            const int Kt0 = base + lane < pp.n
+                                ? import_segment<SPH, FL>(W, lane, pp.segs + base + lane, pp, ap, dp, invalid, dropped)
+                                : 0;
+            // With the LV3 pre-filter on, the warp takes its segments in order of their
+            // ground footprint's distance from the filter's centre, so that the bunches of
+            // a warp round tend to land on the same side of the disc and whole rounds skip
+            // the correction (the draws stay keyed by the segments' own indices).
+            int slot = lane;
+            if (pp.lv3) {
+                float key = 3.0e38f;   // empty slots last
+                if (Kt0 > 0) {
+                    const float4 A = W.segA[lane], C = W.segC[lane];
+                    float gx, gy;
+                    if (SPH) {   // start point carried along P to the observation level
+                        const float f = fmaxf(W.segB[lane].x, 0.0f) * rcp_approx(fmaxf(-C.w, 0.05f));
+                        gx = fmaf(f, A.x, C.x);
+                        gy = fmaf(f, A.y, C.y);
+                    } else if (FL) {   // fluorescence keeps the start point as the origin
+                        const float f = fmaxf(W.segB[lane].x, 0.0f) * rcp_approx(fmaxf(-A.z, 0.05f));
+                        gx = fmaf(f, A.x, C.x);
+                        gy = fmaf(f, A.y, C.z);
+                    } else {     // the ground intercept
+                        gx = C.x;
+                        gy = C.z;
+                    }
+                    gx -= pp.lv3_c[0];
+                    gy -= pp.lv3_c[1];
+                    key = fmaf(gx, gx, gy * gy);
+                }
+                // bitonic sort of (key, slot) across the warp, ascending
+#pragma unroll
+                for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+                    for (int j = k >> 1; j > 0; j >>= 1) {
+                        const float ok = __shfl_xor_sync(0xffffffffu, key, j);
+                        const int os = __shfl_xor_sync(0xffffffffu, slot, j);
+                        const bool other_less = ok < key || (ok == key && os < slot);
+                        // the lower lane of an ascending pair keeps the smaller entry
+                        const bool want_less = ((lane & k) == 0) == ((lane & j) == 0);
+                        if (other_less == want_less && os != slot) {
+                            key = ok;
+                            slot = os;
+                        }
+                    }
+                }
+            }
+            const int Kt = __shfl_sync(0xffffffffu, Kt0, slot);
+            W.perm[lane] = slot;
             int incl = Kt;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -918,11 +964,12 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                         if (W.offK[mid] <= first) lo = mid;
                         else hi = mid;
                     }
-                    int sg = lo;
+                    int si = lo;
                     for (int q = q0; q < q1; ++q) {
                         const int qq = sub0 + q;
-                        while (W.offK[sg + 1] <= qq) ++sg;   // next non-empty segment
-                        const int N = substep<SPH, FL>(W, q, sg, qq - W.offK[sg], base, pp, ap);
+                        while (W.offK[si + 1] <= qq) ++si;   // next non-empty segment
+                        const int sg = W.perm[si];
+                        const int N = substep<SPH, FL>(W, q, sg, qq - W.offK[si], base, pp, ap);
                         my_ph += N;
                         my_emit += (unsigned int)N * (unsigned int)W.bunch[sg];
                     }
