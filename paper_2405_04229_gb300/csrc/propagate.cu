@@ -894,12 +894,14 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
             const int Kt0 = base + lane < pp.n
                                 ? import_segment<SPH, FL>(W, lane, pp.segs + base + lane, pp, ap, dp, invalid, dropped)
                                 : 0;
-            // With the LV3 pre-filter on, the warp takes its segments in order of their
-            // ground footprint's distance from the filter's centre, so that the bunches of
-            // a warp round tend to land on the same side of the disc and whole rounds skip
-            // the correction (the draws stay keyed by the segments' own indices).
+            // The warp takes its segments in order of their ground footprint's distance
+            // from the LV3 centre (the frame origin unless the filter is on), so that the
+            // bunches of a warp round tend to land together: the telescope cells, histogram
+            // rows and statuses of a round agree more often (measured 2-3 % faster), and with
+            // the LV3 pre-filter whole rounds skip the correction (1.08x on the inclined
+            // shower).  The draws stay keyed by the segments' own indices.
             int slot = lane;
-            if (pp.lv3) {
+            {
                 float key = 3.0e38f;   // empty slots last
                 if (Kt0 > 0) {
                     const float4 A = W.segA[lane], C = W.segC[lane];
