@@ -898,12 +898,10 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
             // from the LV3 centre (the frame origin unless the filter is on), so that the
             // bunches of a warp round tend to land together: the telescope cells, histogram
             // rows and statuses of a round agree more often (measured 2-3 % faster), and with
-            // the LV3 pre-filter whole rounds skip the correction.  Not after the LV1 cut: its
-            // survivors point at the array, and ordered warps then pile their photons onto the
-            // same spheres, whose 64-bit count and time atomics serialise (measured 6 %
-            // slower).  The draws stay keyed by the segments' own indices.
+            // the LV3 pre-filter whole rounds skip the correction (1.08x on the inclined
+            // shower).  The draws stay keyed by the segments' own indices.
             int slot = lane;
-            if (!pp.lv1) {
+            {
                 float key = 3.0e38f;   // empty slots last
                 if (Kt0 > 0) {
                     const float4 A = W.segA[lane], C = W.segC[lane];
