@@ -257,11 +257,11 @@ typedef struct cs_opts {
     double lv3_radius, lv3_margin;   /* >= 0 [m] */
     /* Propagation method when the atmosphere refracts: CS_TRACER_TABLES (default) looks
      * the correction up in the FP64-built tables (interpolation tracing, Sec. 4.4.1);
-     * CS_TRACER_SNELL traces every photon through homogeneous slabs of thickness
-     * <= tracer_dh [m] with Snell's law in vector form (Sec. 3.4.2, Eq. 3.15) and
-     * accumulates its delay and slant columns on the way (the general-atmosphere
-     * fallback; planar atmospheres, exact path only: CS_ERR_INVALID_ARG with a
-     * spherical atmosphere or a surrogate). */
+     * CS_TRACER_SNELL traces every photon through homogeneous slabs (on the spherical
+     * shell: shells) of thickness <= tracer_dh [m], >= 0.01 m, with Snell's law in vector
+     * form (Sec. 3.4.2, Eq. 3.15) and accumulates its delay and slant columns on the way
+     * (the general-atmosphere fallback; the exact path only: CS_ERR_INVALID_ARG with a
+     * surrogate).  Ignored when the atmosphere does not refract. */
     int tracer;
     double tracer_dh;
     /* Emission (Sec. 2.2.2, 4.2.2): CS_EMIT_CHERENKOV (default), or nitrogen fluorescence,
