@@ -16,6 +16,10 @@
  *   absorption           Sec. 4.3.1
  *   correction tables    Sec. 4.4.1 ("interpolation tracing")
  *   GPU pipeline         Sec. 5.3 (import, generate, filter, propagate, store)
+ *   Snell vector stepper Sec. 3.4.2, Eq. 3.15 (the general-atmosphere tracer)
+ *   fluorescence         Sec. 2.2.2, Eq. 2.6 and Sec. 4.2.2
+ *   LV1 / LV3 filters    Sec. 4.3.2, 4.3.4 and 6.2
+ *   mirror and camera    Sec. 6.4 (last-mile ray tracing)
  *
  * Conventions.  Lengths in metres, times in seconds, heights above sea level
  * on the z axis, the detector frame's origin at the array centre.  All calls
