@@ -139,6 +139,7 @@ struct PropParams {
     float fl_yd;
     float fl_inv_l[8];
     uint32_t fl_thr[8];
+    uint32_t rk[20];   // Philox key schedule: round r uses rk[2r], rk[2r + 1]
 };
 
 // The atmosphere in FP64, as the table builder integrates it.

@@ -276,7 +276,7 @@ __device__ __forceinline__ int import_segment(SM& S, int t, const cs_segment* se
 __device__ __forceinline__ float fluorescence_line(const PropParams& pp, uint32_t g_lo, uint32_t g_hi, uint32_t k,
                                                   uint32_t i) {
     const PropParams& fp = pp;
-    const uint4 r = philox(g_lo, g_hi, k, i | 0x80000000u, pp.key0, pp.key1);
+    const uint4 r = philox_rk(g_lo, g_hi, k, i | 0x80000000u, pp.rk);
     const uint32_t v = r.x >> 8;
     int line = fp.fl_n - 1;
     for (int l = fp.fl_n - 2; l >= 0; --l)
@@ -307,7 +307,7 @@ __device__ __forceinline__ int substep(SM& S, int q, int sg, int k, long long ba
     if constexpr (FL) nbar = pp.fl_yd * S.z2[sg] * d * B.z * rcp_approx((float)S.bunch[sg]);   // Eq. 2.6
     else if (sin2 > 0.0f) nbar = ap.ft * S.z2[sg] * sin2 * B.z * rcp_approx((float)S.bunch[sg]);
     const unsigned long long gid = pp.seg_base + (unsigned long long)(base + sg);
-    const uint4 rc = philox((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0xFFFFFFFFu, pp.key0, pp.key1);
+    const uint4 rc = philox_rk((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0xFFFFFFFFu, pp.rk);
     const float uk = uniform24(rc.x);
     const float fl = floorf(nbar);
     const int N = (int)fl + (uk < nbar - fl ? 1 : 0);
@@ -563,7 +563,7 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
     const int segk = __float_as_int(Q.w);
     const int sg = segk & ((1 << kKShift) - 1), k = segk >> kKShift;
     const unsigned long long gid = pp.seg_base + (unsigned long long)(base + sg);
-    const uint4 r4 = philox((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, (uint32_t)i, pp.key0, pp.key1);
+    const uint4 r4 = philox_rk((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, (uint32_t)i, pp.rk);
     const float u0 = uniform24(r4.x), u1 = uniform24(r4.y), u2 = uniform24(r4.z), u3 = uniform24(r4.w);
     const float4 A = S.segA[sg], B = S.segB[sg];
     const float Px = A.x, Py = A.y, Pz = A.z;
@@ -1237,6 +1237,13 @@ cs_status tile_counter(unsigned int** out) {
 
 // The LV1 filter's parameters from the options (the counter as given: device memory here).
 void set_filters(PropParams& pp, const cs_opts& o, const DetParams& dp, const AtmParams& ap) {
+    uint32_t k0 = pp.key0, k1 = pp.key1;   // the Philox key schedule, once per call
+    for (int r = 0; r < 10; ++r) {
+        pp.rk[2 * r] = k0;
+        pp.rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
     pp.emission = o.emission;
     pp.fl_n = 0;
     pp.fl_yd = 0.0f;
