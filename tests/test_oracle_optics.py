@@ -77,3 +77,54 @@ def test_propagation_camera_images_equal_the_records():
     np.add.at(img.reshape(1, len(tel), -1), (0, rec["tel"][hit], rec["pix"][hit]), 2)
     assert np.array_equal(img, r["camera"])
     assert (rec["pix"][rec["tel"] < 0] == -1).all()
+
+
+def _march(P, w):
+    """Independent trace: the ray P + t w in the telescope frame, the mirror
+    found by bisection on r^2 - 4 f z along the ray below the camera plane."""
+    f, R, rd = OPT["focal_f"], OPT["camera_r"], OPT["mirror_d"] / 2
+    a, e1, e2 = _frame()
+    V = C0 - 0.5 * f * a
+    M = np.stack([e1, e2, a])
+    p, d = M @ (P - V), M @ w
+    if d[2] >= 0:
+        return None
+    tc = (f - p[2]) / d[2]
+    if np.hypot(*(p[:2] + tc * d[:2])) < R:
+        return None
+    F = lambda t: (p[0] + t * d[0]) ** 2 + (p[1] + t * d[1]) ** 2 - 4 * f * (p[2] + t * d[2])
+    lo, hi = tc, tc + 4 * f / -d[2]          # inside the bowl at the camera plane, below the vertex later
+    if not (F(lo) < 0 < F(hi)):
+        return None
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if F(mid) < 0 else (lo, mid)
+    m = p + 0.5 * (lo + hi) * d
+    if np.hypot(m[0], m[1]) > rd:
+        return None
+    n = np.array([m[0], m[1], -2 * f]) / np.linalg.norm([m[0], m[1], -2 * f])
+    r = d - 2 * np.dot(d, n) * n
+    q = m + (f - m[2]) / r[2] * r
+    return q[:2] if np.hypot(*q[:2]) <= R else None
+
+
+def test_camera_points_match_an_independent_ray_march():
+    rng = np.random.default_rng(11)
+    hits = 0
+    for _ in range(300):
+        rho, phi = rng.uniform(0.0, 3.6), rng.uniform(0, 2 * math.pi)
+        tilt, tdir = abs(rng.normal(0.0, 0.02)), rng.uniform(0, 2 * math.pi)
+        P, w = _ray(rho, phi, tilt, tdir)
+        P = P - 30.0 * w                           # start well before the instrument
+        pix, xy = oracle.camera_trace(C0, P, w, OPT)
+        ref = _march(P, w)
+        if ref is None:
+            assert pix == -1
+            continue
+        hits += 1
+        assert pix >= 0
+        assert np.allclose(xy, ref, atol=1e-9)
+        n = OPT["cam_n"]
+        ix, iy = (int(math.floor((v + OPT["camera_r"]) / (2 * OPT["camera_r"]) * n)) for v in ref)
+        assert pix == min(max(iy, 0), n - 1) * n + min(max(ix, 0), n - 1)
+    assert hits > 150
