@@ -24,6 +24,15 @@
  *   absorption            Sec. 2.3.2 and Sec. 4.3.1 (survival test r < p)
  *   correction target     Sec. 4.4.1 (the exact path that the correction
  *                         tables approximate)
+ *   spherical shell       Sec. 3.3.4 (Bouguer's invariant n r sin(psi),
+ *                         azimuthal-equidistant ground coordinates)
+ *   tabulated atmosphere  Sec. 3.3 (a user's n(h) table, log-linear)
+ *   Snell stepper as a    Sec. 3.4.2 on slabs and on spherical shells, with
+ *   propagation method    delay and slant columns
+ *   fluorescence          Sec. 2.2.2, Eq. 2.6 and Sec. 4.2.2 (isotropic or
+ *                         half-sphere line emission)
+ *   LV1 / LV3 filters     Sec. 4.3.2, 4.3.4, 6.2.1, 6.2.2
+ *   mirror and camera     Sec. 6.4 (last-mile ray tracing)
  *
  * Where the thesis is silent the oracle takes the documented readings
  * (layer parameters, transmission constants, stochastic rounding of the
