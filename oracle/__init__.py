@@ -21,10 +21,11 @@ _LIB = os.path.join(_LIB_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-ST_LANDED, ST_UPWARD, ST_BELOW, ST_DOMAIN, ST_ABSORBED, ST_LV3 = range(6)
+ST_LANDED, ST_UPWARD, ST_BELOW, ST_NO_GROUND, ST_ABSORBED, ST_LV3 = range(6)
 ST_SUBSTEP_FLAG = 15
-FL_COUNT, FL_ABSORB, FL_HIST_EDGE, FL_TEL_EDGE, FL_DOMAIN, FL_BELOW, FL_UPWARD, FL_LAYER, FL_LV1, FL_LV3 = (
+FL_COUNT, FL_ABSORB, FL_HIST_EDGE, FL_TEL_EDGE, FL_GROUND, FL_BELOW, FL_UPWARD, FL_LAYER, FL_LV1, FL_LV3 = (
     1, 2, 4, 8, 16, 32, 64, 128, 256, 512)
+FL_SEGMENT = 1024   # the segment's sub-step count is a rounding decision: all its bunches are undetermined
 LV1_OFF, LV1_ARRAY_CENTRE, LV1_ARRAY_DISC, LV1_TELESCOPES = 0, 1, 2, 3
 ATM_LAYERED, ATM_LINEAR, ATM_HOMOGENEOUS, ATM_TABLE = 0, 1, 2, 3
 RHO_REF = 1.225e-3   # [g/cm^3]: the table kind's density is RHO_REF (n - 1) / kappa
@@ -54,8 +55,7 @@ class Atm(C.Structure):
 class Config(C.Structure):
     _fields_ = [("h_obs", C.c_double), ("lambda1", C.c_double), ("lambda2", C.c_double),
                 ("s_max", C.c_double), ("bunch", C.c_int), ("refraction", C.c_int),
-                ("transmission", C.c_int), ("use_domain", C.c_int), ("w_max", C.c_double),
-                ("h_dom_top", C.c_double),
+                ("transmission", C.c_int), ("pad0", C.c_int),
                 ("rayl_X0", C.c_double), ("rayl_lambda0", C.c_double),
                 ("aer_tau0", C.c_double), ("aer_lambda0", C.c_double), ("aer_alpha", C.c_double),
                 ("aer_H", C.c_double), ("seed", C.c_uint64), ("seg_base", C.c_uint64),
@@ -280,7 +280,7 @@ DEFAULT_BANDS = dict(band_pos=1e-4, band_count=1e-4, band_T=1e-5, band_h=1e-3, b
 
 
 def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, bunch=1,
-              refraction=False, transmission=False, use_domain=None, w_max=None, seed=0,
+              refraction=False, transmission=False, seed=0,
               seg_base=0, n_showers=1, hist=None, tel=None, records=True, record_capacity=None,
               transmission_params=None, bands=None, quad_rtol=1e-10, spherical=False, earth_radius=EARTH_RADIUS,
               lv1=None, optics=None, lv3=None, snell_dh=None, fluorescence=None):
@@ -297,16 +297,6 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
     cfg.lambda1, cfg.lambda2 = lambda_nm[0] * 1e-9, lambda_nm[1] * 1e-9
     cfg.s_max, cfg.bunch = s_max, bunch
     cfg.refraction, cfg.transmission = int(refraction), int(transmission)
-    if use_domain is None:
-        use_domain = bool(refraction or transmission)
-    cfg.use_domain = int(use_domain)
-    cfg.w_max = w_max if w_max is not None else float(np.tan(np.radians(75.0)) ** 2)
-    if atm.kind in (ATM_LAYERED, ATM_TABLE):
-        cfg.h_dom_top = atm.h_top
-    elif atm.kind == ATM_LINEAR:
-        cfg.h_dom_top = atm.lin_h1
-    else:
-        cfg.h_dom_top = h_obs + 1e5
     tp = dict(rayl_X0=2974.0, rayl_lambda0=400e-9, aer_tau0=0.05, aer_lambda0=350e-9,
               aer_alpha=1.3, aer_H=1200.0)
     if transmission_params:

@@ -699,10 +699,6 @@ typedef struct {
     int bunch;
     int refraction;            /* 0: straight line, 1: exact planar refraction */
     int transmission;          /* 0: off, 1: Rayleigh + aerosol */
-    int use_domain;            /* 1: photons with tan^2(theta0) > w_max or emitted at or above
-                                  h_dom_top are out of the correction tables' domain */
-    double w_max;
-    double h_dom_top;
     double rayl_X0, rayl_lambda0;                 /* X_R(l) = X0 (l / l0)^4          */
     double aer_tau0, aer_lambda0, aer_alpha, aer_H; /* tau_A(l) = tau0 (l / l0)^-alpha */
     uint64_t seed;
@@ -756,11 +752,18 @@ typedef struct {
     double fl_dedx;
 } orc_config;
 
-enum { ORC_ST_LANDED = 0, ORC_ST_UPWARD = 1, ORC_ST_BELOW = 2, ORC_ST_DOMAIN = 3,
+/* ORC_ST_NO_GROUND: a descending photon whose path never meets the observation level
+ * (on the spherical shell it passes over the ground sphere and leaves the atmosphere;
+ * in the plane, a profile whose index drops below the Snell invariant reflects it) */
+enum { ORC_ST_LANDED = 0, ORC_ST_UPWARD = 1, ORC_ST_BELOW = 2, ORC_ST_NO_GROUND = 3,
        ORC_ST_ABSORBED = 4, ORC_ST_LV3 = 5, ORC_ST_SUBSTEP_FLAG = 15 };
+/* ORC_FL_SEGMENT: the segment's sub-step count K = ceil(L / s_max) lies within rounding
+ * of a whole number, so an FP32 evaluation may take the other count and every bunch of
+ * the segment is undetermined; ORC_FL_GROUND: the photon lies within the band of the
+ * condition that decides whether its path meets the observation level */
 enum { ORC_FL_COUNT = 1, ORC_FL_ABSORB = 2, ORC_FL_HIST_EDGE = 4, ORC_FL_TEL_EDGE = 8,
-       ORC_FL_DOMAIN = 16, ORC_FL_BELOW = 32, ORC_FL_UPWARD = 64, ORC_FL_LAYER = 128, ORC_FL_LV1 = 256,
-       ORC_FL_LV3 = 512 };
+       ORC_FL_GROUND = 16, ORC_FL_BELOW = 32, ORC_FL_UPWARD = 64, ORC_FL_LAYER = 128, ORC_FL_LV1 = 256,
+       ORC_FL_LV3 = 512, ORC_FL_SEGMENT = 1024 };
 
 typedef struct {
     uint64_t seg;
@@ -933,6 +936,40 @@ static double orc_lv1_x(const orc_config* cfg, const double S[3], const double P
     return best;
 }
 
+/* Relative margin by which a descending photon emitted at h_e with (local)
+ * zenith sine sin_z clears the turning-point condition: the smallest of
+ * (n(h) r(h) - K) / K over [h_obs, h_e], with K = n(h_e) r(h_e) sin_z and
+ * r = R + h on the spherical shell (r = 1 in the plane; n = 1 for the straight
+ * line).  Within each piece between breakpoints n(h) is monotone (exponential,
+ * linear or constant) and, on the shell, n r grows with r wherever
+ * (n - 1) < H / r (the scale height over the radius, ~1e-3 against n - 1 <
+ * 3e-4 here), so the smallest value lies at a piece end; both one-sided limits
+ * are taken at a breakpoint.  Positive: the path reaches the ground. */
+static double orc_reach_margin(const orc_atm* a, const orc_config* cfg, double h_e, double sin_z)
+{
+    const int refr = cfg->refraction;
+    const double R = cfg->earth_radius;
+    double rr_e = cfg->spherical ? R + h_e : 1.0;
+    const double K = (refr ? orc_n(a, h_e) : 1.0) * rr_e * sin_z;
+    if (!(K > 0.0)) return 1.0;
+    double hs[ORC_MAX_NODES + 20];
+    int m = 0;
+    hs[m++] = cfg->h_obs;
+    double bp[ORC_MAX_NODES + 16];
+    int nb = refr ? orc_breakpoints(a, cfg->h_obs, h_e, bp) : 0;
+    for (int i = 0; i < nb; ++i) {
+        hs[m++] = bp[i];
+        hs[m++] = bp[i] - 1e-9 * fmax(1.0, fabs(bp[i]));   /* the limit from below */
+    }
+    double best = 1e300;
+    for (int i = 0; i < m; ++i) {
+        const double r = cfg->spherical ? R + hs[i] : 1.0;
+        const double v = ((refr ? orc_n(a, hs[i]) : 1.0) * r - K) / K;
+        if (v < best) best = v;
+    }
+    return best;
+}
+
 int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                   const orc_config* cfg, orc_output* out)
 {
@@ -943,7 +980,6 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
     const double b = (double)cfg->bunch;
     const uint32_t key[2] = { (uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32) };
     const double n_obs = orc_n(atm, cfg->h_obs);
-    const int use_tables = cfg->use_domain;
 
     for (size_t is = 0; is < n_segs; ++is) {
         const orc_segment* sg = &segs[is];
@@ -954,10 +990,20 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
         const double P[3] = { sg->ux / un, sg->uy / un, sg->uz / un };
         const double L = sg->length, g = sg->inv_gamma2, z = sg->charge;
         const double beta = sqrt(1.0 - g);
-        /* the integer K is decided in FP32 (the kernel's precision) */
-        const float Kf = ceilf(sg->length / (float)cfg->s_max);
-        const int K = Kf < 1.0f ? 1 : (int)Kf;
+        /* Sub-stepping (Sec. 4.2.1): K = ceil(L / s_max) sub-steps of equal length.
+         * Where L / s_max lies within rounding of a whole number the count itself is
+         * a rounding decision; the whole segment is then flagged. */
+        const double Lq = L / cfg->s_max;
+        const int K = Lq <= 1.0 ? 1 : (int)ceil(Lq);
+        const int seg_flag = fabs(Lq - nearbyint(Lq)) < 1e-6 * fmax(1.0, Lq) ? ORC_FL_SEGMENT : 0;
         const int shower = (int)sg->shower_id;
+        if (seg_flag) {
+            orc_record fr; memset(&fr, 0, sizeof fr);
+            fr.seg = gid; fr.k = 0xFFFFFFFFu; fr.i = 0xFFFFFFFFu;
+            fr.status = ORC_ST_SUBSTEP_FLAG; fr.flags = ORC_FL_SEGMENT;
+            fr.tel = -1; fr.bin = -1; fr.pix = -1;
+            orc_push(out, &fr);
+        }
 
         /* LV1 particle filter (Sec. 4.3.2; the two-parameter cut of Sec. 6.2.1) */
         int lv1_near = 0;
@@ -1047,6 +1093,7 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                 rec.pix = -1;
                 rec.seg = gid; rec.k = (uint32_t)k; rec.i = (uint32_t)i;
                 rec.tel = -1; rec.bin = -1; rec.nbar = nbar;
+                rec.flags |= seg_flag;
                 if (count_flag && i == N - 1) rec.flags |= ORC_FL_COUNT;
                 if (mid_layer_flag) rec.flags |= ORC_FL_LAYER;
                 if (lv1_near) rec.flags |= ORC_FL_COUNT | ORC_FL_LV1;   /* the kernel may drop the segment */
@@ -1103,7 +1150,7 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
 
                 if (fabs(cos_z) < cfg->band_w) rec.flags |= ORC_FL_UPWARD;
                 if (fabs(h_e - cfg->h_obs) < cfg->band_h) rec.flags |= ORC_FL_BELOW;
-                if (use_tables && atm->kind == ORC_ATM_LAYERED) {
+                if ((cfg->refraction || cfg->transmission) && atm->kind == ORC_ATM_LAYERED) {
                     for (int li = 1; li < atm->n_layers; ++li)
                         if (fabs(h_e - atm->layer_h[li]) < cfg->band_h) rec.flags |= ORC_FL_LAYER;
                 }
@@ -1123,14 +1170,18 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                 double theta0 = acos(cos_z);
                 rec.theta0 = theta0;
                 double sin_z = sin(theta0);
-                double w = sin_z * sin_z / (cos_z * cos_z);   /* tan^2 of the local zenith */
-                if (use_tables && fabs(w - cfg->w_max) < cfg->band_w * cfg->w_max) rec.flags |= ORC_FL_DOMAIN;
-                if (use_tables && fabs(h_e - cfg->h_dom_top) < cfg->band_h) rec.flags |= ORC_FL_DOMAIN;
-                if (use_tables && (w > cfg->w_max || h_e >= cfg->h_dom_top)) {
-                    rec.status = ORC_ST_DOMAIN;
-                    out->counters[4] += cfg->bunch; out->counters[5] += cfg->bunch;
-                    orc_push(out, &rec);
-                    continue;
+                /* Does the path meet the observation level?  Along the exact path the
+                 * invariant (Eq. 3.17; Bouguer's n r sin(psi) on the shell) must stay below
+                 * n (h) (n r) all the way down; the straight line of Eq. 3.3 is the n = 1 case. */
+                {
+                    double margin = orc_reach_margin(atm, cfg, h_e, sin_z);
+                    if (fabs(margin) < cfg->band_w) rec.flags |= ORC_FL_GROUND;
+                    if (!(margin > 0.0)) {
+                        rec.status = ORC_ST_NO_GROUND;
+                        out->counters[4] += cfg->bunch; out->counters[5] += cfg->bunch;
+                        orc_push(out, &rec);
+                        continue;
+                    }
                 }
                 /* LV3 photon pre-filter (Sec. 4.3.4, 6.2.2): the vacuum straight line's
                  * landing point S decides, before any correction is looked up */

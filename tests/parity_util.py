@@ -5,7 +5,9 @@ follow the method's parity rules: per-photon positions and times agree to a
 relative 1e-5 (positions relative to the horizontal displacement from the
 emission point, floor 1 m); counts are bit-exact except bunches the oracle
 flags as lying within an edge band (bin or sphere edge, count-rounding,
-absorption or domain threshold, layer boundary).
+absorption threshold, the condition for reaching the ground, layer
+boundary).  A segment whose sub-step count is itself a rounding decision is
+left out as a whole.
 """
 import numpy as np
 
@@ -29,12 +31,18 @@ def compare(gpu, orc, bunch=1, shower_of_seg=None, pos_rel=POS_REL, t_rel=T_REL,
     times max(1 m, the horizontal displacement from the emission point), or to
     pos_abs [m] where the FP32 resolution of far-out frame coordinates is the
     floor (isotropic emission on the spherical shell)."""
-    g = gpu["records"]
+    g = g_all = gpu["records"]
     assert gpu["n_records"] == len(g), "GPU record capacity exceeded"
     o_all = orc["records"]
     sub = o_all[o_all["status"] == oracle.ST_SUBSTEP_FLAG]
     o = o_all[o_all["status"] != oracle.ST_SUBSTEP_FLAG]
     flagged_sub = set(zip(sub["seg"].tolist(), sub["k"].tolist()))
+    # segments whose sub-step count K = ceil(L / s_max) is a rounding decision: every
+    # bunch of them may differ, so they take no part in the per-photon comparison
+    seg_out = np.unique(sub["seg"][(sub["flags"] & oracle.FL_SEGMENT) != 0])
+    n_seg_out = int(np.isin(g["seg"], seg_out).sum())
+    g = g[~np.isin(g["seg"], seg_out)]
+    o = o[~np.isin(o["seg"], seg_out)]
 
     kg, ko = _key(g["seg"], g["k"], g["i"]), _key(o["seg"], o["k"], o["i"])
     assert len(np.unique(kg)) == len(kg), "duplicate GPU records"
@@ -51,7 +59,7 @@ def compare(gpu, orc, bunch=1, shower_of_seg=None, pos_rel=POS_REL, t_rel=T_REL,
 
     G, O = g[ig], o[io]
     fl = O["flags"]
-    status_flags = (oracle.FL_ABSORB | oracle.FL_DOMAIN | oracle.FL_BELOW | oracle.FL_UPWARD | oracle.FL_LAYER |
+    status_flags = (oracle.FL_ABSORB | oracle.FL_GROUND | oracle.FL_BELOW | oracle.FL_UPWARD | oracle.FL_LAYER |
                     oracle.FL_LV3)
     same_status = G["status"].astype(np.int64) == O["status"].astype(np.int64)
     bad = ~same_status & ((fl & status_flags) == 0)
@@ -83,22 +91,23 @@ def compare(gpu, orc, bunch=1, shower_of_seg=None, pos_rel=POS_REL, t_rel=T_REL,
     # aggregates equal the records they summarise (the GPU's counts are its records')
     if check_hist and "hist" in gpu and gpu["hist"].size:
         h = np.zeros_like(gpu["hist"])
-        m = g["bin"] >= 0
+        m = g_all["bin"] >= 0
         sh = shower_of_seg
-        showers = np.zeros(m.sum(), np.int64) if sh is None else np.asarray(sh, np.int64)[g["seg"][m].astype(np.int64)]
-        np.add.at(h.reshape(h.shape[0], -1), (showers, g["bin"][m]), bunch)
+        showers = np.zeros(m.sum(), np.int64) if sh is None else np.asarray(sh, np.int64)[g_all["seg"][m].astype(np.int64)]
+        np.add.at(h.reshape(h.shape[0], -1), (showers, g_all["bin"][m]), bunch)
         assert np.array_equal(h, gpu["hist"]), "GPU histogram differs from its records"
     cam = gpu.get("camera")
     if check_hist and cam is not None and cam.size:
         c = np.zeros_like(cam)
-        m = g["pix"] >= 0
+        m = g_all["pix"] >= 0
         sh = shower_of_seg
-        showers = np.zeros(m.sum(), np.int64) if sh is None else np.asarray(sh, np.int64)[g["seg"][m].astype(np.int64)]
-        np.add.at(c.reshape(cam.shape[0], cam.shape[1], -1), (showers, g["tel"][m], g["pix"][m]), bunch)
+        showers = np.zeros(m.sum(), np.int64) if sh is None else np.asarray(sh, np.int64)[g_all["seg"][m].astype(np.int64)]
+        np.add.at(c.reshape(cam.shape[0], cam.shape[1], -1), (showers, g_all["tel"][m], g_all["pix"][m]), bunch)
         assert np.array_equal(c, cam), "GPU camera images differ from their records"
     n_diff_bins = int(((G["bin"] != O["bin"]) & landed).sum())
     n_diff_tel = int(((G["tel"] != O["tel"]) & landed).sum())
     return dict(matched=len(common), flagged=int((fl != 0).sum()), only_gpu=len(only_g), only_oracle=len(only_o),
+                segments_out=len(seg_out), gpu_bunches_out=n_seg_out,
                 max_pos_rel=max_pos, max_t_rel=max_t, max_abs_pos=float(abs_pos[prop].max(initial=0.0)),
                 status_flips=int((~same_status).sum()), bin_flips=n_diff_bins, tel_flips=n_diff_tel,
                 pix_flips=int(((G["pix"] != O["pix"]) & landed).sum()),

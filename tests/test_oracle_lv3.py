@@ -30,7 +30,7 @@ def _real(r):
 
 def _run(segs, refr, lv3=None, spherical=False, **kw):
     return oracle.propagate(segs, ATM, hist=HIST, tel=TEL, bunch=2, refraction=refr, transmission=refr,
-                            use_domain=True, seed=3, lv3=lv3, spherical=spherical, **kw)
+                            seed=3, lv3=lv3, spherical=spherical, **kw)
 
 
 def _paired(a, b):

@@ -67,7 +67,7 @@ def test_pipeline_stepper_lands_where_the_exact_path_does():
     assert np.array_equal(ex["seg"], st["seg"]) and np.array_equal(ex["status"], st["status"])
     m = ex["status"] == oracle.ST_LANDED
     assert m.sum() > 5000
-    line = oracle.propagate(segs, LAY, bunch=2, refraction=False, transmission=False, use_domain=True,
+    line = oracle.propagate(segs, LAY, bunch=2, refraction=False, transmission=False,
                             seed=4)["records"]
     shift = np.hypot(ex["x"] - line["x"], ex["y"] - line["y"])[m]   # the refraction correction
     err = np.hypot(ex["x"] - st["x"], ex["y"] - st["y"])[m]
@@ -114,7 +114,7 @@ def test_pipeline_shell_stepper_lands_where_the_exact_path_does():
     assert np.array_equal(ex["seg"], st["seg"]) and np.array_equal(ex["status"], st["status"])
     m = ex["status"] == oracle.ST_LANDED
     assert m.sum() > 3000
-    line = oracle.propagate(segs, LAY, bunch=2, refraction=False, transmission=False, use_domain=True, seed=4,
+    line = oracle.propagate(segs, LAY, bunch=2, refraction=False, transmission=False, seed=4,
                             spherical=True)["records"]
     shift = np.hypot(ex["x"] - line["x"], ex["y"] - line["y"])[m]
     err = np.hypot(ex["x"] - st["x"], ex["y"] - st["y"])[m]
