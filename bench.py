@@ -34,8 +34,14 @@ METRIC = "Cherenkov photons propagated/sec on 1 GB300 (exact vs surrogate) at st
 UNIT = "photons/s"
 WORKLOAD = "refraction-corrected exact tracer: 1e6 segments, 10 showers, zenith 20 deg, bunch 5, 100 telescopes"
 
-# Algorithmic FP32/INT lane operations of the method (counted from its formula
-# sequence, not from the compiled code): per bunch, per sub-step, per segment.
+# Algorithmic FP32/INT lane operations per bunch of the method's hot path as
+# planned before any kernel was written (Philox ~60, cone and rotation ~27,
+# straight line ~9, four bilinear fields ~24, transmission ~7, detector ~11,
+# plus index math: 130-160); the roofline's `achieved` uses the upper end.
+OPS_PER_BUNCH_PLAN = 160
+# The same counted item by item from the formulas as implemented (the
+# float-float origins, both Philox draws, every index computation): per bunch,
+# per sub-step, per segment.  Reported beside the planned count.
 OPS_PER_BUNCH = 285
 OPS_PER_SUBSTEP = 150
 OPS_PER_SEGMENT = 120
@@ -321,7 +327,7 @@ def run_batched(args):
                        "segments": n, "photons_per_step": photons, "bunch_sizes": per_shower_bunch,
                        "blocks_per_sm": tune.blocks_per_sm, "tiling_ms": [round(tune.ms[i], 3) for i in range(4)],
                        "generation_s": round(gen_s, 1), "l2": "inputs (%.1f GB) larger than L2" % (arr.nbytes / 1e9)},
-            "counters": [int(x) for x in h["counters"]], "cpu_baseline": cpu, "gpu_launches": args.steps,
+            "counters": [int(x) for x in h["counters"]], "cpu_baseline": cpu, "gpu_launches": 2 * args.steps,
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
@@ -576,7 +582,7 @@ def run_inclined(args):
                          "frac": achieved / peak, "traffic": None,
                          "note": "per chunk launch; spherical lane-op count per bunch %d" % OPS_PER_BUNCH_SPHERICAL},
             "kernel_ms": k_ms, "cpu_baseline": cpu, "surrogate": surrogate, "e2e": e2e, "lv1_filter": lv1_res, "lv3_filter": lv3_res,
-            "gpu_launches": args.steps * n_chunks, "clocks": clk.summary()}
+            "gpu_launches": 2 * args.steps * n_chunks, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 
@@ -740,8 +746,10 @@ def main():
     torch.cuda.synchronize()
     k_ms = sum(s.elapsed_time(e) for s, e in zip(kstarts, kends)) / args.steps
     sm_clk = clk.summary()
-    ops = OPS_PER_BUNCH * bunches_per_step + OPS_PER_SUBSTEP * n_sub + OPS_PER_SEGMENT * n
+    ops = OPS_PER_BUNCH_PLAN * bunches_per_step
     achieved = ops / (k_ms / 1e3) / 1e12
+    ops_full = OPS_PER_BUNCH * bunches_per_step + OPS_PER_SUBSTEP * n_sub + OPS_PER_SEGMENT * n
+    achieved_full = ops_full / (k_ms / 1e3) / 1e12
     max_mhz = 2070.0
     try:
         max_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", max_mhz)
@@ -908,10 +916,13 @@ def main():
             "bunches_per_s": value / bunch,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "achieved_full_count": achieved_full, "frac_full_count": achieved_full / peak,
                          "ncu_pipes_pct": pipes,
-                         "note": "FP32/INT lane ops of the method per launch / kernel time; peak = SMs x 128 lanes "
-                                 "x max SM clock; ncu_pipes_pct: issue-slot and busiest-pipe utilisation of the "
-                                 "same kernel from the committed capture (2.5e6-segment case)"},
+                         "note": "achieved: %d planned FP32/INT lane ops per bunch x bunches per launch / launch "
+                                 "time; *_full_count: the itemised count of the implemented formulas (%d per bunch "
+                                 "+ %d per sub-step + %d per segment); peak = SMs x 128 lanes x max SM clock; "
+                                 "ncu_pipes_pct: issue-slot and busiest-pipe utilisation from the committed capture"
+                                 % (OPS_PER_BUNCH_PLAN, OPS_PER_BUNCH, OPS_PER_SUBSTEP, OPS_PER_SEGMENT)},
             "kernel_ms": k_ms,
             "cpu_baseline": cpu,
             "surrogate": surrogate,
@@ -919,7 +930,7 @@ def main():
             "snell_tracer": snell,
             "fluorescence": fluor,
             "e2e": e2e,
-            "gpu_launches": args.steps,
+            "gpu_launches": 2 * args.steps,   # the photon kernel and its exact pass, per step
             "clocks": sm_clk,
         }
         print(json.dumps(line), flush=True)

@@ -174,13 +174,27 @@ typedef struct cs_detector_desc {
     double mirror_d, focal_f, camera_r;
     double point_zenith, point_azimuth;
     int cam_n;
+    /* Absorption in those optics (Sec. 6.4): a photon that reaches a camera pixel survives the
+     * mirror's reflectivity R(lambda) and the camera's photon detection efficiency eps(lambda)
+     * with probability R eps, each linear between eff_n <= 16 nodes (eff_lambda_nm [nm]
+     * ascending, values in [0, 1]; constant beyond the end nodes); a photon that does not
+     * survive still counts as a telescope hit but adds nothing to the camera image.  The
+     * survival draw is Philox word x of counter (segment, sub-step, bunch index | 2^30).
+     * eff_n = 0 (default): no absorption. */
+    int eff_n;
+    const double* eff_lambda_nm;
+    const double* eff_mirror;
+    const double* eff_camera;
 } cs_detector_desc;
 
 typedef struct cs_detector cs_detector;
 
-/* Copies the layout to the device and builds its telescope grid hash.
- * A photon hits telescope i if its arrival line passes within radius_i of
- * the sphere's centre; the closest centre wins, then the lowest index. */
+/* The detector of the thesis's pipeline (Sec. 5.3 "store"; Sec. 6.2 bounding
+ * spheres of the telescopes; App. B.3 the detector layouts): copies the layout to
+ * the device and builds its telescope grid hash.  A photon hits telescope i if its
+ * arrival line passes within radius_i of the sphere's centre; the closest centre
+ * wins, then the lowest index.  Errors: CS_ERR_INVALID_ARG (NULL or inconsistent
+ * description), CS_ERR_CUDA. */
 cs_status cs_detector_create(const cs_detector_desc* desc, cs_detector** out);
 void cs_detector_destroy(cs_detector* det);
 
@@ -195,21 +209,32 @@ enum {
 };
 /* Conservation: emitted = absorbed + hist + missed_hist = absorbed + tel + missed_tel. */
 
-enum { CS_ST_LANDED = 0, CS_ST_UPWARD = 1, CS_ST_BELOW = 2, CS_ST_DOMAIN = 3, CS_ST_ABSORBED = 4, CS_ST_LV3 = 5 };
+/* Bunch statuses.  CS_ST_NO_GROUND: a descending bunch whose exact path never
+ * meets the observation level (on the spherical shell it passes over the ground
+ * sphere, Bouguer's n r sin(psi) exceeding n r at the ground; in the plane an
+ * inverted n(h) profile turns it back up); it counts as missed.  Every other
+ * descending bunch emitted above the observation level is propagated: inside the
+ * correction tables' domain by the tables, beyond it (steeper zenith, or emitted
+ * above the tables' top) by the exact path integrated for that bunch. */
+enum { CS_ST_LANDED = 0, CS_ST_UPWARD = 1, CS_ST_BELOW = 2, CS_ST_NO_GROUND = 3, CS_ST_ABSORBED = 4, CS_ST_LV3 = 5 };
 
-/* Optional per-bunch record (parity mode), 48 bytes.  Records are written in
- * no particular order; (seg, k, i) identifies a bunch uniquely. */
+/* Optional per-bunch record (parity mode), 56 bytes.  Records are written in
+ * no particular order; (seg, k, i) identifies a bunch uniquely.  The ground
+ * position is a float-float pair (x + x_lo, y + y_lo): a single float would
+ * round it to ~2 mm at 30 km from the frame origin, coarser than the
+ * per-photon bar for photons that travel a short way far out. */
 typedef struct cs_record {
     uint64_t seg;        /* global segment index (seg_base + position in the input) */
     uint32_t k;          /* sub-step index */
     uint32_t i;          /* bunch index within the sub-step */
-    float x, y;          /* ground position [m] (landed and absorbed bunches) */
+    float x, y;          /* ground position [m] (landed and absorbed bunches), leading part */
     float dt_ns;         /* arrival time minus the segment's t0 [ns] */
     float lambda_nm;     /* wavelength [nm] */
     int32_t tel;         /* telescope hit or -1 */
     int32_t bin;         /* histogram cell iy * nx + ix or -1 */
     uint32_t status;     /* CS_ST_* */
     int32_t pix;         /* camera pixel iy * cam_n + ix of the telescope hit, or -1 */
+    float x_lo, y_lo;    /* trailing parts of the ground position [m] */
 } cs_record;
 
 typedef struct cs_output {
@@ -281,6 +306,13 @@ typedef struct cs_opts {
     const double* fl_lines_nm;
     const double* fl_yield_per_mev;
     double fl_dedx;
+    /* Polls of each tensor-core completion wait of the surrogate network before the
+     * kernel gives up on it: 0 (default) = 2^20; < 0 = no poll at all (the wait gives up at
+     * once, which exercises the give-up path).  A warpgroup whose wait gives up stops using
+     * the network: its photons take the correction tables, so the counts stay valid, and
+     * the call reports CS_ERR_TIMEOUT (host-pointer calls directly, device-pointer and
+     * streamed calls through cs_check_timeout). */
+    int tc_poll_limit;
 } cs_opts;
 
 enum { CS_EMIT_CHERENKOV = 0, CS_EMIT_FLUORESCENCE = 1, CS_EMIT_FLUORESCENCE_HALF = 2 };
@@ -301,6 +333,14 @@ enum {
 /* Defaults: bunch 1, s_max 1 m, seg_base 0, host pointers, no accumulation, no
  * LV1 or LV3 filter, the table tracer (tracer_dh 10 m for the Snell stepper). */
 void cs_opts_default(cs_opts* opts);
+
+/* Synchronises the current device and reports whether a tensor-core wait of the
+ * surrogate network gave up in a propagation call (device-pointer, batched or
+ * streamed) since the last check: CS_ERR_TIMEOUT if so (the flag is cleared; the
+ * affected photons took the correction tables, so that call's counts are valid),
+ * CS_OK otherwise, CS_ERR_CUDA if the synchronisation fails.  Host-pointer calls
+ * check this themselves. */
+cs_status cs_check_timeout(void);
 
 /* Generates and propagates the photons of n segments (Sec. 5.3 pipeline).
  * Random draws are keyed by (seed, global segment index, sub-step, bunch),
@@ -401,7 +441,11 @@ cs_status cs_autotune_bunches(const cs_segment* segs, size_t n, const cs_atmosph
  * uniform zenith in [0, theta_max] and uniform wavelength in the atmosphere's
  * band (minus bands around the layer boundaries, where n(h) and hence the
  * exact fields are discontinuous), labelled by the FP64 quadrature of the
- * exact path.  Hidden layers run
+ * exact path.  The network learns the fields less their first-order
+ * expansion in n - 1 (I = int (n - 1) dh over [h_obs, h_e], H = h_e - h_obs,
+ * mu = cos(zenith): G_R = d_e H - I, G_t = 2 I - d_e H + (d_e H - I) / mu^2,
+ * ln T from the vertical slant columns over mu), which is added back at
+ * inference from a table of the FP64 vertical integrals.  Hidden layers run
  * on the tensor cores (BF16 weights, FP32 accumulation); the 3-input layer
  * runs in FP32.  Outside its domain the photon kernel uses the tables.
  * ---------------------------------------------------------------------- */
@@ -414,7 +458,10 @@ typedef struct cs_surrogate_config {
     double lr, lr_min;       /* Adam learning rate (default 1e-2), cosine-decayed to lr_min (1e-5) */
     double h_min, h_max;     /* emission heights [m] (default 2 km .. 30 km) */
     double theta_max;        /* largest zenith [rad] (default 60 deg) */
-    int split_activations;   /* 1: hidden activations enter the MMAs as BF16 hi + lo pairs */
+    int split_activations;   /* 1: hidden activations enter the MMAs as BF16 hi + lo pairs after an accurate
+                                tanh; 0: as single BF16 values through the hardware's packed BF16 tanh
+                                (fewer instructions and MMAs; the network only adds a correction to the
+                                first-order baseline) */
     double boundary_band;    /* half-width [m] of the bands around layer boundaries left to the tables
                                 (the exact fields jump there with n(h_e)); default 500 m */
     double height_scale;     /* > 0: the height enters as exp(-(h - h_obs) / height_scale) (default
@@ -440,6 +487,10 @@ void cs_surrogate_destroy(cs_surrogate* s);
  * inputs {h_e - h_obs [m], cos(theta0), 1/lambda [1/nm], unused}; writes
  * float4 {G_R [m], G_t [m], T, 0}.  16-byte aligned device pointers. */
 cs_status cs_surrogate_eval(const cs_surrogate* s, const float* d_in, size_t n, float* d_out, void* stream);
+/* The same on the network's own part: float4 {G_R, G_t, ln T} less the
+ * first-order baseline (the de-normalised network outputs), for checking the
+ * tensor-core arithmetic against a plain forward pass. */
+cs_status cs_surrogate_eval_network(const cs_surrogate* s, const float* d_in, size_t n, float* d_out, void* stream);
 /* Host copies of the parameters as inference uses them (flat FP32, the
  * tensor-core weights already rounded to BF16; layout W1[64][3] b1[64]
  * W2[64][64] b2 W3[64][64] b3 W4[8][64] b4[8]), the training statistics, and
@@ -460,17 +511,19 @@ cs_status cs_mlp_loss_grad(const float* params, const float* x, const float* t, 
  * start-up, callers that must account for every byte in advance.  It does
  * what cs_propagate_ex does with opts->device_ptrs = 1 (opts must say so;
  * host pointers are rejected with CS_ERR_INVALID_ARG), but its only scratch,
- * the dynamic scheduler's tile counter, lives in a 256-byte array that the
- * library declares statically on every device that loads it (held until the
- * process exits) instead of in memory the library allocates.  It calls no
- * cudaMalloc or cudaFree.
- * Limits and rules: one 32-bit counter, so inputs needing 2^32 - 65537 or
- * more tiles of 256 segments are rejected with CS_ERR_INVALID_ARG.  The first
- * call on a device looks up the array's device address, so make that first
- * call before any stream capture.  Every call reuses the same array and
- * resets the counter on its stream before the kernel; two calls whose work
- * overlaps on the GPU (different streams, or different host threads) race on
- * the counter and give wrong results, so serialise them. */
+ * the dynamic scheduler's work counters and the exact pass's map and list of
+ * warp tiles with bunches beyond the correction tables, lives in a 67.6 KB array
+ * that the library declares statically on every device that loads it (held
+ * until the process exits) instead of in memory the library allocates.  It
+ * calls no cudaMalloc, cudaFree or pool allocation.
+ * Limits and rules: 32-bit counters, so inputs needing 2^32 - 65537 or more
+ * warp tiles of 32 segments (about 1.37e11 segments) are rejected with
+ * CS_ERR_INVALID_ARG; the map holds 2^14 groups, each of ceil(tiles / 2^14)
+ * warp tiles.  The first call on a device looks up the array's device address,
+ * so make that first call before any stream capture.  Every call reuses the
+ * same array and clears it on its stream before the kernels; two calls whose
+ * work overlaps on the GPU (different streams, or different host threads) race
+ * on it and give wrong results, so serialise them. */
 cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, const cs_atmosphere* atm,
                                const cs_detector* det, uint64_t seed, const cs_opts* opts,
                                cs_output* out, void* stream);

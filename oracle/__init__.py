@@ -26,6 +26,7 @@ ST_SUBSTEP_FLAG = 15
 FL_COUNT, FL_ABSORB, FL_HIST_EDGE, FL_TEL_EDGE, FL_GROUND, FL_BELOW, FL_UPWARD, FL_LAYER, FL_LV1, FL_LV3 = (
     1, 2, 4, 8, 16, 32, 64, 128, 256, 512)
 FL_SEGMENT = 1024   # the segment's sub-step count is a rounding decision: all its bunches are undetermined
+FL_OPTICS = 2048    # the optics survival draw lies within the band of its threshold
 LV1_OFF, LV1_ARRAY_CENTRE, LV1_ARRAY_DISC, LV1_TELESCOPES = 0, 1, 2, 3
 ATM_LAYERED, ATM_LINEAR, ATM_HOMOGENEOUS, ATM_TABLE = 0, 1, 2, 3
 RHO_REF = 1.225e-3   # [g/cm^3]: the table kind's density is RHO_REF (n - 1) / kappa
@@ -72,7 +73,9 @@ class Config(C.Structure):
                 ("lv3", C.c_int), ("pad5", C.c_int), ("lv3_centre", C.c_double * 3), ("lv3_radius", C.c_double),
                 ("lv3_margin", C.c_double), ("tracer", C.c_int), ("pad6", C.c_int), ("tracer_dh", C.c_double),
                 ("emission", C.c_int), ("fl_n_lines", C.c_int), ("fl_lines_nm", C.c_double * 8),
-                ("fl_yield", C.c_double * 8), ("fl_dedx", C.c_double)]
+                ("fl_yield", C.c_double * 8), ("fl_dedx", C.c_double),
+                ("eff_n", C.c_int), ("pad7", C.c_int), ("eff_l", C.c_double * 16), ("eff_R", C.c_double * 16),
+                ("eff_E", C.c_double * 16)]
 
 
 SEGMENT_DTYPE = np.dtype([("x0", "<f8"), ("y0", "<f8"), ("z0", "<f8"), ("t0", "<f8"),
@@ -337,9 +340,17 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
         for i, v in enumerate(lv3.get("centre", (0.0, 0.0, h_obs))):
             cfg.lv3_centre[i] = v
         cfg.lv3_radius, cfg.lv3_margin = lv3["radius"], lv3.get("margin", 0.0)
-    if optics:   # dict(mirror_d, focal_f, camera_r, point_zenith, point_azimuth [rad], cam_n)
+    if optics:   # dict(mirror_d, focal_f, camera_r, point_zenith, point_azimuth [rad], cam_n
+        #            [, efficiency=dict(lambda_nm, mirror, camera)])
         for k in ("mirror_d", "focal_f", "camera_r", "point_zenith", "point_azimuth", "cam_n"):
             setattr(cfg, k, optics[k])
+        eff = optics.get("efficiency")
+        if eff:
+            n_eff = len(eff["lambda_nm"])
+            assert 1 <= n_eff <= 16
+            cfg.eff_n = n_eff
+            for j in range(n_eff):
+                cfg.eff_l[j], cfg.eff_R[j], cfg.eff_E[j] = eff["lambda_nm"][j], eff["mirror"][j], eff["camera"][j]
 
     hist_out = np.zeros((n_showers, max(h["ny"], 0), max(h["nx"], 0)), np.uint64)
     tel_counts = np.zeros((n_showers, cfg.n_tel), np.uint64)

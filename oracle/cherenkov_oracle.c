@@ -296,6 +296,7 @@ static double orc_adapt(orc_fn f, const void* ctx, double lo, double hi, double 
     double mid = 0.5 * (lo + hi);
     double left = orc_gl(f, ctx, lo, mid), right = orc_gl(f, ctx, mid, hi);
     double both = left + right;
+    if (!isfinite(both)) return both;   /* a path that never reaches the lower limit: no refinement helps */
     if (depth >= 40 || fabs(both - whole) <= rtol * fabs(both) + 1e-300) return both;
     return orc_adapt(f, ctx, lo, mid, left, rtol, depth + 1) +
            orc_adapt(f, ctx, mid, hi, right, rtol, depth + 1);
@@ -750,6 +751,14 @@ typedef struct {
     double fl_lines_nm[8];
     double fl_yield[8];
     double fl_dedx;
+    /* absorption in the last-mile optics (Sec. 6.4): a photon that reaches a camera pixel
+     * survives the mirror's reflectivity R(lambda) and the camera's detection efficiency
+     * eps(lambda) with probability R eps, each linear between eff_n nodes (eff_l [nm],
+     * ascending; constant beyond the end nodes); eff_n = 0: no absorption.  The draw is
+     * the Philox word x of counter (segment, sub-step, bunch index | 2^30). */
+    int eff_n;
+    int pad7;
+    double eff_l[16], eff_R[16], eff_E[16];
 } orc_config;
 
 /* ORC_ST_NO_GROUND: a descending photon whose path never meets the observation level
@@ -763,7 +772,7 @@ enum { ORC_ST_LANDED = 0, ORC_ST_UPWARD = 1, ORC_ST_BELOW = 2, ORC_ST_NO_GROUND 
  * condition that decides whether its path meets the observation level */
 enum { ORC_FL_COUNT = 1, ORC_FL_ABSORB = 2, ORC_FL_HIST_EDGE = 4, ORC_FL_TEL_EDGE = 8,
        ORC_FL_GROUND = 16, ORC_FL_BELOW = 32, ORC_FL_UPWARD = 64, ORC_FL_LAYER = 128, ORC_FL_LV1 = 256,
-       ORC_FL_LV3 = 512, ORC_FL_SEGMENT = 1024 };
+       ORC_FL_LV3 = 512, ORC_FL_SEGMENT = 1024, ORC_FL_OPTICS = 2048 };
 
 typedef struct {
     uint64_t seg;
@@ -936,6 +945,16 @@ static double orc_lv1_x(const orc_config* cfg, const double S[3], const double P
     return best;
 }
 
+/* Piecewise-linear curve through n nodes (x ascending), constant beyond the ends. */
+static double orc_lerp_curve(const double* x, const double* y, int n, double v)
+{
+    if (v <= x[0]) return y[0];
+    if (v >= x[n - 1]) return y[n - 1];
+    int i = 0;
+    while (v > x[i + 1]) ++i;
+    return y[i] + (y[i + 1] - y[i]) * (v - x[i]) / (x[i + 1] - x[i]);
+}
+
 /* Relative margin by which a descending photon emitted at h_e with (local)
  * zenith sine sin_z clears the turning-point condition: the smallest of
  * (n(h) r(h) - K) / K over [h_obs, h_e], with K = n(h_e) r(h_e) sin_z and
@@ -990,12 +1009,19 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
         const double P[3] = { sg->ux / un, sg->uy / un, sg->uz / un };
         const double L = sg->length, g = sg->inv_gamma2, z = sg->charge;
         const double beta = sqrt(1.0 - g);
-        /* Sub-stepping (Sec. 4.2.1): K = ceil(L / s_max) sub-steps of equal length.
-         * Where L / s_max lies within rounding of a whole number the count itself is
-         * a rounding decision; the whole segment is then flagged. */
-        const double Lq = L / cfg->s_max;
-        const int K = Lq <= 1.0 ? 1 : (int)ceil(Lq);
-        const int seg_flag = fabs(Lq - nearbyint(Lq)) < 1e-6 * fmax(1.0, Lq) ? ORC_FL_SEGMENT : 0;
+        /* Sub-stepping (Sec. 4.2.1): K = ceil(L / s_max) sub-steps of equal length, the
+         * exact ceiling of the quotient of the two stored numbers.  The rounded quotient
+         * proposes K; the residual K s_max - L, whose sign one fused multiply-add gives
+         * exactly, confirms K s_max >= L > (K - 1) s_max.  A length within 1e-13
+         * (relative) of a whole number of sub-steps, without lying exactly on one, is
+         * flagged: a rounding of s_max at that level moves the count, and every bunch of
+         * the segment with it. */
+        const double s_max = cfg->s_max, Lq = L / s_max;
+        int K = Lq <= 1.0 ? 1 : (int)ceil(Lq);
+        if (fma((double)K, s_max, -L) < 0.0) ++K;
+        else if (K > 1 && fma((double)(K - 1), s_max, -L) >= 0.0) --K;
+        const double res = fma(nearbyint(Lq), s_max, -L);
+        const int seg_flag = (res != 0.0 && fabs(res) < 1e-13 * L) ? ORC_FL_SEGMENT : 0;
         const int shower = (int)sg->shower_id;
         if (seg_flag) {
             orc_record fr; memset(&fr, 0, sizeof fr);
@@ -1343,6 +1369,17 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                     int edge = 0;
                     rec.pix = orc_camera_pixel(cfg, Tc, G3, ug, cfg->band_pos, &edge);
                     if (edge) rec.flags |= ORC_FL_TEL_EDGE;
+                    if (rec.pix >= 0 && cfg->eff_n > 0) {   /* mirror reflectivity x camera efficiency */
+                        const double lnm = rec.lambda * 1e9;
+                        const double P = orc_lerp_curve(cfg->eff_l, cfg->eff_R, cfg->eff_n, lnm) *
+                                         orc_lerp_curve(cfg->eff_l, cfg->eff_E, cfg->eff_n, lnm);
+                        uint32_t ctr3[4] = { (uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, (uint32_t)i | 0x40000000u };
+                        uint32_t r3[4];
+                        orc_philox4x32_10(ctr3, key, r3);
+                        const double uo = orc_uniform(r3[0]);
+                        if (fabs(uo - P) < cfg->band_T) rec.flags |= ORC_FL_OPTICS;
+                        if (!(uo < P)) rec.pix = -1;   /* absorbed in the optics: no camera photon */
+                    }
                     if (rec.pix >= 0 && out->camera)
                         out->camera[((size_t)shower * cfg->n_tel + best) * cfg->cam_n * cfg->cam_n + rec.pix] += cfg->bunch;
                 }

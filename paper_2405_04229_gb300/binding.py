@@ -45,7 +45,7 @@ def set_lv3(o, lv3):
 (CS_CNT_EMITTED, CS_CNT_ABSORBED, CS_CNT_HIST, CS_CNT_TEL, CS_CNT_MISSED_HIST, CS_CNT_MISSED_TEL,
  CS_CNT_UPWARD, CS_CNT_INVALID_SEGMENTS) = range(8)
 CS_N_COUNTERS = 8
-CS_ST_LANDED, CS_ST_UPWARD, CS_ST_BELOW, CS_ST_DOMAIN, CS_ST_ABSORBED, CS_ST_LV3 = range(6)
+CS_ST_LANDED, CS_ST_UPWARD, CS_ST_BELOW, CS_ST_NO_GROUND, CS_ST_ABSORBED, CS_ST_LV3 = range(6)
 
 
 class CSError(RuntimeError):
@@ -63,7 +63,7 @@ SEGMENT_DTYPE = np.dtype([("x0", "<f8"), ("y0", "<f8"), ("z0", "<f8"), ("t0", "<
                           ("flags", "<u4")])
 RECORD_DTYPE = np.dtype([("seg", "<u8"), ("k", "<u4"), ("i", "<u4"), ("x", "<f4"), ("y", "<f4"),
                          ("dt_ns", "<f4"), ("lambda_nm", "<f4"), ("tel", "<i4"), ("bin", "<i4"),
-                         ("status", "<u4"), ("pix", "<i4")])
+                         ("status", "<u4"), ("pix", "<i4"), ("x_lo", "<f4"), ("y_lo", "<f4")])
 
 
 class cs_atmosphere_desc(C.Structure):
@@ -88,7 +88,9 @@ class cs_detector_desc(C.Structure):
                 ("hist_dy", C.c_double), ("n_tel", C.c_int), ("tel_xyzr", C.POINTER(C.c_double)),
                 ("geometry", C.c_int), ("earth_radius", C.c_double),
                 ("mirror_d", C.c_double), ("focal_f", C.c_double), ("camera_r", C.c_double),
-                ("point_zenith", C.c_double), ("point_azimuth", C.c_double), ("cam_n", C.c_int)]
+                ("point_zenith", C.c_double), ("point_azimuth", C.c_double), ("cam_n", C.c_int),
+                ("eff_n", C.c_int), ("eff_lambda_nm", C.POINTER(C.c_double)), ("eff_mirror", C.POINTER(C.c_double)),
+                ("eff_camera", C.POINTER(C.c_double))]
 
 
 OPTICS_KEYS = ("mirror_d", "focal_f", "camera_r", "point_zenith", "point_azimuth", "cam_n")
@@ -128,7 +130,7 @@ class cs_opts(C.Structure):
                 ("lv3", C.c_int), ("lv3_centre", C.c_double * 3), ("lv3_radius", C.c_double),
                 ("lv3_margin", C.c_double), ("tracer", C.c_int), ("tracer_dh", C.c_double),
                 ("emission", C.c_int), ("fl_n_lines", C.c_int), ("fl_lines_nm", C.c_void_p),
-                ("fl_yield_per_mev", C.c_void_p), ("fl_dedx", C.c_double)]
+                ("fl_yield_per_mev", C.c_void_p), ("fl_dedx", C.c_double), ("tc_poll_limit", C.c_int)]
 
 
 CS_TRACER_TABLES, CS_TRACER_SNELL = 0, 1
@@ -204,6 +206,8 @@ def lib():
             L.cs_surrogate_destroy.argtypes = [vp]
             L.cs_surrogate_eval.argtypes = [vp, vp, C.c_size_t, vp, vp]
             L.cs_surrogate_eval.restype = st
+            L.cs_surrogate_eval_network.argtypes = [vp, vp, C.c_size_t, vp, vp]
+            L.cs_surrogate_eval_network.restype = st
             L.cs_surrogate_info.argtypes = [vp, vp, C.c_size_t, C.POINTER(cs_surrogate_stats), vp]
             L.cs_surrogate_info.restype = st
             L.cs_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int, vp, vp]
@@ -214,6 +218,8 @@ def lib():
             L.cs_philox4x32_10.restype = st
             L.cs_device_sm_count.argtypes = [C.POINTER(C.c_int)]
             L.cs_device_sm_count.restype = st
+            L.cs_check_timeout.argtypes = []
+            L.cs_check_timeout.restype = st
             _lib = L
     return _lib
 
@@ -329,6 +335,12 @@ def cs_philox4x32_10(ctr_ptr, n, key0, key1, out_ptr, stream=None):
     return lib().cs_philox4x32_10(ctr_ptr, n, key0, key1, out_ptr, stream)
 
 
+def cs_check_timeout():
+    """CS_ERR_TIMEOUT if a tensor-core wait of the surrogate gave up in a device-pointer,
+    batched or streamed call since the last check (synchronises the device)."""
+    return lib().cs_check_timeout()
+
+
 def cs_device_sm_count():
     n = C.c_int()
     _check(lib().cs_device_sm_count(C.byref(n)), "cs_device_sm_count")
@@ -410,13 +422,21 @@ class Detector:
 
     def __init__(self, n_showers=1, h_obs=2000.0, hist=None, tel=None, spherical=False, earth_radius=0.0,
                  optics=None):
-        """optics: dict(mirror_d, focal_f, camera_r, point_zenith, point_azimuth [rad], cam_n)
-        for the last-mile ray tracing into per-telescope camera images."""
+        """optics: dict(mirror_d, focal_f, camera_r, point_zenith, point_azimuth [rad], cam_n
+        [, efficiency=dict(lambda_nm, mirror, camera)]) for the last-mile ray tracing into
+        per-telescope camera images, with the optics' absorption when efficiency is given."""
         d = cs_detector_desc()
         d.n_showers, d.h_obs = n_showers, h_obs
+        self._eff = None
         if optics:
             for k in OPTICS_KEYS:
                 setattr(d, k, optics[k])
+            eff = optics.get("efficiency")
+            if eff:
+                self._eff = [np.ascontiguousarray(eff[k], np.float64) for k in ("lambda_nm", "mirror", "camera")]
+                d.eff_n = len(self._eff[0])
+                d.eff_lambda_nm, d.eff_mirror, d.eff_camera = (a.ctypes.data_as(C.POINTER(C.c_double))
+                                                               for a in self._eff)
         d.geometry, d.earth_radius = (CS_GEOM_SPHERICAL if spherical else CS_GEOM_PLANAR), earth_radius
         if hist:
             d.hist_nx, d.hist_ny = hist["nx"], hist["ny"]
@@ -443,8 +463,9 @@ class Detector:
 
 def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=1.0, seg_base=0,
                    records=False, record_capacity=None, blocks_per_sm=0, surrogate=None, lv1=None, lv3=None,
-                   snell_dh=None, fluorescence=None):
-    """cs_propagate_ex with host numpy buffers; returns a dict of outputs."""
+                   snell_dh=None, fluorescence=None, tc_poll_limit=0, allow_timeout=False):
+    """cs_propagate_ex with host numpy buffers; returns a dict of outputs (with the
+    call's status, CS_ERR_TIMEOUT accepted when allow_timeout)."""
     arr = segs if isinstance(segs, np.ndarray) else pack_segments(segs)
     arr = np.ascontiguousarray(arr)
     hist = np.zeros((det.n_showers, det.ny, det.nx), np.uint64)
@@ -476,10 +497,12 @@ def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=
     if snell_dh:   # the Snell vector stepper through slabs <= snell_dh [m] instead of the tables
         o.tracer, o.tracer_dh = CS_TRACER_SNELL, snell_dh
     keep = set_fluorescence(o, fluorescence)   # noqa: F841 (the arrays must outlive the call)
+    o.tc_poll_limit = tc_poll_limit
     st = cs_propagate_ex(_dptr(arr) if len(arr) else None, len(arr), atm.handle, det.handle, seed, o, out)
-    _check(st, "cs_propagate_ex")
+    if not (allow_timeout and st == CS_ERR_TIMEOUT):
+        _check(st, "cs_propagate_ex")
     res = dict(hist=hist, tel_counts=tel_counts, tel_time=tel_time, counters=counters, n_records=int(rc[0]),
-               lv1_dropped=int(dropped[0]), camera=camera)
+               lv1_dropped=int(dropped[0]), camera=camera, status=st)
     if records:
         res["records"] = rec[: int(rc[0])]
     return res
@@ -607,15 +630,17 @@ class Surrogate:
         _check(lib().cs_surrogate_info(self.handle, _dptr(p), p.size, None, _dptr(norm)), "cs_surrogate_info")
         return p, norm
 
-    def eval(self, inputs):
-        """inputs: n x 3 (h_e - h_obs [m], cos(theta0), 1/lambda [1/nm]) -> n x 3 (G_R, G_t, T)."""
+    def eval(self, inputs, network_only=False):
+        """inputs: n x 3 (h_e - h_obs [m], cos(theta0), 1/lambda [1/nm]) -> n x 3 (G_R, G_t, T); with
+        network_only, the network's part (G_R, G_t, ln T less the first-order baseline)."""
         import torch
         x = np.zeros((len(inputs), 4), np.float32)
         x[:, :3] = inputs
         d_in = torch.from_numpy(x).cuda()
         d_out = torch.zeros_like(d_in)
-        _check(lib().cs_surrogate_eval(self.handle, C.c_void_p(d_in.data_ptr()), len(x),
-                                       C.c_void_p(d_out.data_ptr()), stream_ptr()), "cs_surrogate_eval")
+        fn = lib().cs_surrogate_eval_network if network_only else lib().cs_surrogate_eval
+        _check(fn(self.handle, C.c_void_p(d_in.data_ptr()), len(x), C.c_void_p(d_out.data_ptr()), stream_ptr()),
+               "cs_surrogate_eval")
         torch.cuda.synchronize()
         return d_out.cpu().numpy()[:, :3]
 

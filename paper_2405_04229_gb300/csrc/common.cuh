@@ -69,6 +69,7 @@ struct AtmParams {
     float lamA_nm;       // aerosol reference wavelength [nm]
     float aer_alpha;
     TableView tv;
+    const AtmParams* self;   // device copy of these parameters (for out-of-line routines)
 };
 
 struct DetParams {
@@ -98,6 +99,9 @@ struct DetParams {
     int cam_n;
     float cam_f, cam_rd2, cam_r, cam_scale;
     float ax, ay, az, e1x, e1y, e1z, e2x, e2y, e2z;
+    // absorption in the optics: R(lambda), eps(lambda) linear between eff_n nodes [1/nm in eff_il]
+    int eff_n;
+    float eff_l[16], eff_R[16], eff_E[16];
 };
 
 struct OutParams {
@@ -118,7 +122,7 @@ struct PropParams {
     uint32_t key0, key1;
     int bunch;                 // photons per bunch when shower_bunch is null
     const int* shower_bunch;   // per-shower bunch sizes (device), or null
-    float s_max;
+    float s_max, s_max_lo;     // sub-step length as float-float
     // LV1 particle filter: drop when y >= lv1_a x^lv1_b (x in degrees)
     int lv1;                   // CS_LV1_*
     float lv1_a, lv1_b, lv1_r;
@@ -140,6 +144,7 @@ struct PropParams {
     float fl_inv_l[8];
     uint32_t fl_thr[8];
     uint32_t rk[20];   // Philox key schedule: round r uses rk[2r], rk[2r + 1]
+    int tiles_per_bit; // warp tiles (32 segments) per bit of the exact pass's tile map
 };
 
 // The atmosphere in FP64, as the table builder integrates it.
@@ -171,10 +176,14 @@ struct __align__(16) Fields4 {   // {G_R, G_t, G_X, G_A} in FP64
 };
 // Exact FP64 {G_R, G_t, G_X, G_A} at samples {h_e [m], theta0 [rad]} (device arrays).
 cs_status exact_fields(const cs_atmosphere* atm, const double2* d_in, size_t n, Fields4* d_out, cudaStream_t stream);
+// FP64 vertical integrals from h_obs up to each height h [m] (device arrays):
+// {int (n - 1) dh, n(h) - 1, int 100 rho dh [g/cm^2], int exp(-h / H_A) dh}.
+cs_status column_fields(const cs_atmosphere* atm, const double* d_h, size_t n, Fields4* d_out, cudaStream_t stream);
 }  // namespace cs
 
 struct cs_atmosphere {
     cs::AtmParams p;
+    cs::AtmParams* d_params;   // device copy of p (owned)
     float4* d_tab;         // device table (owned)
     float* d_nodes;        // tabulated kind: interval laws (owned)
     double h0, dh, dw;

@@ -48,6 +48,14 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
         for (int i = 0; i < d->n_tel; ++i)
             if (d->tel_xyzr[4 * i + 3] < hold) return CS_ERR_INVALID_ARG;
         if ((double)d->n_showers * d->n_tel * d->cam_n * d->cam_n > 4e9) return CS_ERR_INVALID_ARG;
+        if (d->eff_n < 0 || d->eff_n > 16) return CS_ERR_INVALID_ARG;
+        if (d->eff_n > 0 && (!d->eff_lambda_nm || !d->eff_mirror || !d->eff_camera)) return CS_ERR_INVALID_ARG;
+        for (int i = 0; i < d->eff_n; ++i) {
+            if (!isfinite(d->eff_lambda_nm[i]) || !(d->eff_mirror[i] >= 0.0 && d->eff_mirror[i] <= 1.0) ||
+                !(d->eff_camera[i] >= 0.0 && d->eff_camera[i] <= 1.0))
+                return CS_ERR_INVALID_ARG;
+            if (i > 0 && !(d->eff_lambda_nm[i] > d->eff_lambda_nm[i - 1])) return CS_ERR_INVALID_ARG;
+        }
     }
     cs_status st = cs::check_device();
     if (st != CS_OK) return st;
@@ -86,6 +94,12 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
         p.cam_rd2 = (float)(0.25 * d->mirror_d * d->mirror_d);
         p.cam_r = (float)d->camera_r;
         p.cam_scale = (float)(d->cam_n / (2.0 * d->camera_r));
+        p.eff_n = d->eff_n;
+        for (int i = 0; i < d->eff_n; ++i) {
+            p.eff_l[i] = (float)d->eff_lambda_nm[i];
+            p.eff_R[i] = (float)d->eff_mirror[i];
+            p.eff_E[i] = (float)d->eff_camera[i];
+        }
     }
 
     // host-side layout: tel float4, tel_lo float2, tel3 float4, cell_start, cell_tel

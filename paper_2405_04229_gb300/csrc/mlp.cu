@@ -21,6 +21,7 @@
 struct cs_surrogate {
     float* d_p = nullptr;             // FP32 master parameters
     __nv_bfloat16* d_wb = nullptr;    // BF16 tensor-core weights
+    float4* d_base = nullptr;         // first-order baseline table (see surrogate_baseline)
     cs::SurrogateView view{};
     cs_surrogate_stats stats{};
     double h_min = 0, h_max = 0, theta_max = 0, lambda_min = 0, lambda_max = 0;
@@ -327,22 +328,37 @@ __global__ void transmission_kernel(const double2* __restrict__ hth, const doubl
     Tphys[i] = Tr;
 }
 
-// Normalised inputs (h_e - h_obs, cos(theta0), 1/lambda_nm) and targets
-// (G_R, G_t, ln T): -ln T is linear in the wavelength-dependent attenuation.
+// The first-order baseline of each sample's fields, from the same FP32 table
+// and arithmetic as inference (so the network learns exactly what is added
+// back at inference).
+__global__ void baseline_kernel(SurrogateView sv, const double2* __restrict__ hth, const double* __restrict__ lam,
+                                size_t n, double h_obs, double* __restrict__ b3) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float3 b = surrogate_baseline(sv, (float)(hth[i].x - h_obs), (float)cos(hth[i].y), (float)(1.0 / (lam[i] * 1e9)));
+    b3[3 * i] = b.x;
+    b3[3 * i + 1] = b.y;
+    b3[3 * i + 2] = b.z;
+}
+
+// Normalised inputs (h_e - h_obs, cos(theta0), 1/lambda_nm) and targets: the
+// fields (G_R, G_t, ln T) less their first-order baseline b3 (-ln T is linear
+// in the wavelength-dependent attenuation).
 // Loss weights: (sensitivity of the physical output x normalisation half-range
 // / error bar)^2, so the loss measures each error against its bar:
 // displacement = G_R sin / cos^3 (bar 1 cm), delay = G_t / (c cos) (bar
 // 0.1 ns), T = exp(ln T) (bar 1e-3).
 __global__ void build_xt_kernel(const double2* __restrict__ hth, const double* __restrict__ lam,
-                                const Fields4* __restrict__ f, const double* __restrict__ Tphys, size_t n, Norm nm,
-                                double h_obs, float* __restrict__ X, float* __restrict__ T, float* __restrict__ Wt) {
+                                const Fields4* __restrict__ f, const double* __restrict__ Tphys,
+                                const double* __restrict__ b3, size_t n, Norm nm, double h_obs,
+                                float* __restrict__ X, float* __restrict__ T, float* __restrict__ Wt) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double h = hth[i].x, th = hth[i].y, l = lam[i];
     const double c = cos(th);
     const double hc = nm.height_scale > 0.0 ? exp(-(h - h_obs) / nm.height_scale) : h - h_obs;
     const double v[3] = {hc, c, 1.0 / (l * 1e9)};   // zenith enters as cos(theta0)
-    const double y[3] = {f[i].x, f[i].y, log(Tphys[i])};
+    const double y[3] = {f[i].x - b3[3 * i], f[i].y - b3[3 * i + 1], log(Tphys[i]) - b3[3 * i + 2]};
     for (int k = 0; k < 3; ++k) {
         X[i * 3 + k] = (float)(nm.in_scale[k] * v[k] + nm.in_shift[k]);
         T[i * 3 + k] = (float)((y[k] - nm.out_mid[k]) / nm.out_half[k]);
@@ -431,7 +447,7 @@ cs_status alloc(void** p, size_t bytes) {
 // inference path on arbitrary (dz, cos(theta0), 1/lambda_nm) inputs.
 template <bool SPLIT>
 __global__ void __launch_bounds__(256, 1)
-eval_kernel(SurrogateView sv, const float4* __restrict__ in, size_t n, float4* __restrict__ out) {
+eval_kernel(SurrogateView sv, const float4* __restrict__ in, size_t n, float4* __restrict__ out, int network_only) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TcSmem<2>& T = *reinterpret_cast<TcSmem<2>*>(smem_raw);
     tc_setup(T, sv);
@@ -444,8 +460,14 @@ eval_kernel(SurrogateView sv, const float4* __restrict__ in, size_t n, float4* _
         float y[3];
         net128_tc<SPLIT>(sv, T, x, y);
         if (i < n) {
-            out[i] = make_float4(sv.out_half[0] * y[0] + sv.out_mid[0], sv.out_half[1] * y[1] + sv.out_mid[1],
-                                 fminf(expf(sv.out_half[2] * y[2] + sv.out_mid[2]), 1.0f), 0.0f);
+            const float r0 = fmaf(sv.out_half[0], y[0], sv.out_mid[0]), r1 = fmaf(sv.out_half[1], y[1], sv.out_mid[1]);
+            const float r2 = fmaf(sv.out_half[2], y[2], sv.out_mid[2]);
+            if (network_only) {
+                out[i] = make_float4(r0, r1, r2, 0.0f);
+            } else {
+                const float3 b = surrogate_baseline(sv, v.x, v.y, v.z);
+                out[i] = make_float4(r0 + b.x, r1 + b.y, fminf(expf(r2 + b.z), 1.0f), 0.0f);
+            }
         }
     }
     tc_teardown(T);
@@ -453,14 +475,15 @@ eval_kernel(SurrogateView sv, const float4* __restrict__ in, size_t n, float4* _
 
 // The network on n inputs through the tensor-core path, synchronously;
 // CS_ERR_TIMEOUT if a wait on the tensor cores ran out.
-cs_status run_eval(const SurrogateView& sv, const float4* d_in, size_t n, float4* d_out, cudaStream_t s) {
+cs_status run_eval(const SurrogateView& sv, const float4* d_in, size_t n, float4* d_out, cudaStream_t s,
+                   int network_only = 0) {
     if (n == 0) return CS_OK;
     const int smem = (int)sizeof(TcSmem<2>);
     CS_CUDA_TRY(cudaFuncSetAttribute(eval_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     CS_CUDA_TRY(cudaFuncSetAttribute(eval_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)device_sm_count());
-    if (sv.split) eval_kernel<true><<<grid, 256, smem, s>>>(sv, d_in, n, d_out);
-    else eval_kernel<false><<<grid, 256, smem, s>>>(sv, d_in, n, d_out);
+    if (sv.split) eval_kernel<true><<<grid, 256, smem, s>>>(sv, d_in, n, d_out, network_only);
+    else eval_kernel<false><<<grid, 256, smem, s>>>(sv, d_in, n, d_out, network_only);
     CS_CUDA_TRY(cudaGetLastError());
     CS_CUDA_TRY(cudaStreamSynchronize(s));
     return tc_take_timeout() ? CS_ERR_TIMEOUT : CS_OK;
@@ -592,12 +615,47 @@ extern "C" cs_status cs_surrogate_train(const cs_atmosphere* atm, const cs_surro
         atm->aer_alpha, atm->p.transmission, Tphys);
     std::vector<double> Tp(n_all);
     cudaMemcpy(Tp.data(), Tphys, n_all * sizeof(double), cudaMemcpyDeviceToHost);
+    // ---- the first-order baseline: FP64 vertical integrals on a fine grid of heights ----
+    constexpr int kBaseN = 4096;
+    SurrogateView bv;
+    memset(&bv, 0, sizeof bv);
+    float4* d_base = nullptr;
+    {
+        std::vector<double> hb(kBaseN);
+        for (int j = 0; j < kBaseN; ++j) hb[j] = cfg.h_min + (cfg.h_max - cfg.h_min) * j / (kBaseN - 1);
+        double* d_hb = (double*)A(kBaseN * sizeof(double));
+        Fields4* d_col = (Fields4*)A(kBaseN * sizeof(Fields4));
+        if (!d_hb || !d_col || alloc((void**)&d_base, kBaseN * sizeof(float4)) != CS_OK) { cleanup(); return CS_ERR_CUDA; }
+        cudaMemcpy(d_hb, hb.data(), kBaseN * sizeof(double), cudaMemcpyHostToDevice);
+        if ((st = column_fields(atm, d_hb, kBaseN, d_col, s)) != CS_OK) { cudaFree(d_base); cleanup(); return st; }
+        std::vector<Fields4> col(kBaseN);
+        std::vector<float4> tab(kBaseN);
+        cudaMemcpy(col.data(), d_col, kBaseN * sizeof(Fields4), cudaMemcpyDeviceToHost);
+        for (int j = 0; j < kBaseN; ++j)
+            tab[j] = make_float4((float)col[j].x, (float)col[j].y, (float)col[j].z, (float)col[j].w);
+        cudaMemcpy(d_base, tab.data(), kBaseN * sizeof(float4), cudaMemcpyHostToDevice);
+        bv.base = d_base;
+        bv.base_n = kBaseN;
+        bv.base_dz0 = (float)(cfg.h_min - atm->p.h_obs);
+        bv.base_inv_step = (float)((kBaseN - 1) / (cfg.h_max - cfg.h_min));
+        bv.kR0 = atm->p.kR0;
+        bv.kA0 = atm->p.kA0;
+        bv.lamA_nm = atm->p.lamA_nm;
+        bv.aer_alpha = atm->p.aer_alpha;
+    }
+    double* b3 = (double*)A(n_all * 3 * sizeof(double));
+    if (!b3) { cudaFree(d_base); cleanup(); return CS_ERR_CUDA; }
+    baseline_kernel<<<(unsigned)((n_all + 255) / 256), 256, 0, s>>>(bv, hth, lam, n_all, atm->p.h_obs, b3);
+    std::vector<double> hb3(n_all * 3);
+    cudaMemcpy(hb3.data(), b3, n_all * 3 * sizeof(double), cudaMemcpyDeviceToHost);
+    // output normalisation from the training targets (fields less baseline)
     double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
     for (size_t i = 0; i < nt; ++i) {
-        mn[0] = std::min(mn[0], hl[i].x); mx[0] = std::max(mx[0], hl[i].x);
-        mn[1] = std::min(mn[1], hl[i].y); mx[1] = std::max(mx[1], hl[i].y);
-        const double lt = log(Tp[i]);
-        mn[2] = std::min(mn[2], lt); mx[2] = std::max(mx[2], lt);
+        const double r[3] = {hl[i].x - hb3[3 * i], hl[i].y - hb3[3 * i + 1], log(Tp[i]) - hb3[3 * i + 2]};
+        for (int k = 0; k < 3; ++k) {
+            mn[k] = std::min(mn[k], r[k]);
+            mx[k] = std::max(mx[k], r[k]);
+        }
     }
     for (int k = 0; k < 3; ++k) {
         nm.out_mid[k] = 0.5 * (mx[k] + mn[k]);
@@ -605,8 +663,8 @@ extern "C" cs_status cs_surrogate_train(const cs_atmosphere* atm, const cs_surro
     }
     float* Wt = (float*)A(n_all * 3 * sizeof(float));
     float* Wb = (float*)A((size_t)B * 3 * sizeof(float));
-    if (!Wt || !Wb) { cleanup(); return CS_ERR_CUDA; }
-    build_xt_kernel<<<(unsigned)((n_all + 255) / 256), 256, 0, s>>>(hth, lam, lab, Tphys, n_all, nm, atm->p.h_obs,
+    if (!Wt || !Wb) { cudaFree(d_base); cleanup(); return CS_ERR_CUDA; }
+    build_xt_kernel<<<(unsigned)((n_all + 255) / 256), 256, 0, s>>>(hth, lam, lab, Tphys, b3, n_all, nm, atm->p.h_obs,
                                                                      X, T, Wt);
     // ---- initial parameters (Xavier-uniform from the counter-based generator) ----
     std::vector<float> hp(kNParams, 0.0f);
@@ -651,13 +709,16 @@ extern "C" cs_status cs_surrogate_train(const cs_atmosphere* atm, const cs_surro
     }
     if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess) {
         set_last_error("surrogate training", e);
+        cudaFree(d_base);
         cleanup();
         return CS_ERR_CUDA;
     }
     // ---- the trained network ---------------------------------------------------
     cs_surrogate* sg = new cs_surrogate;
+    sg->d_base = d_base;
     if (alloc((void**)&sg->d_p, kNParams * 4) != CS_OK || alloc((void**)&sg->d_wb, kNBf16 * 2) != CS_OK) {
         cudaFree(sg->d_p);
+        cudaFree(sg->d_base);
         delete sg;
         cleanup();
         return CS_ERR_CUDA;
@@ -665,9 +726,11 @@ extern "C" cs_status cs_surrogate_train(const cs_atmosphere* atm, const cs_surro
     round_weights_kernel<<<(kNParams + 255) / 256, 256, 0, s>>>(p, sg->d_p);
     to_bf16_kernel<<<(kNBf16 + 255) / 256, 256, 0, s>>>(p, sg->d_wb);
     SurrogateView& sv = sg->view;
+    sv = bv;   // the baseline table and constants
     sv.p = sg->d_p;
     sv.wb = sg->d_wb;
     sv.split = cfg.split_activations ? 1 : 0;
+    sv.polls = kTcSpin;
     for (int k = 0; k < 3; ++k) {
         sv.in_scale[k] = (float)nm.in_scale[k];
         sv.in_shift[k] = (float)nm.in_shift[k];
@@ -738,6 +801,7 @@ extern "C" void cs_surrogate_destroy(cs_surrogate* s) {
     if (!s) return;
     cudaFree(s->d_p);
     cudaFree(s->d_wb);
+    cudaFree(s->d_base);
     delete s;
 }
 
@@ -746,6 +810,13 @@ extern "C" cs_status cs_surrogate_eval(const cs_surrogate* s, const float* d_in,
     if (!s || (n && (!d_in || !d_out))) return CS_ERR_INVALID_ARG;
     if (((uintptr_t)d_in & 15) || ((uintptr_t)d_out & 15)) return CS_ERR_INVALID_ARG;
     return run_eval(s->view, (const float4*)d_in, n, (float4*)d_out, (cudaStream_t)stream);
+}
+
+extern "C" cs_status cs_surrogate_eval_network(const cs_surrogate* s, const float* d_in, size_t n, float* d_out,
+                                               void* stream) {
+    if (!s || (n && (!d_in || !d_out))) return CS_ERR_INVALID_ARG;
+    if (((uintptr_t)d_in & 15) || ((uintptr_t)d_out & 15)) return CS_ERR_INVALID_ARG;
+    return run_eval(s->view, (const float4*)d_in, n, (float4*)d_out, (cudaStream_t)stream, 1);
 }
 
 extern "C" cs_status cs_surrogate_info(const cs_surrogate* s, float* params, size_t n_params, cs_surrogate_stats* st,

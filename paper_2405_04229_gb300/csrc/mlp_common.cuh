@@ -44,14 +44,22 @@ struct SurrogateView {
     // when height_scale H > 0
     float in_scale[3], in_shift[3];
     float inv_height_scale;   // 1 / H, or 0 for the linear coordinate
-    // output de-normalisation y = out_half * o + out_mid for (G_R, G_t, ln T)
+    // output de-normalisation y = out_half * o + out_mid of the network's part of
+    // (G_R, G_t, ln T); the fields are that part plus the first-order baseline below
     float out_half[3], out_mid[3];
+    // first-order baseline: {I = int (n - 1) dh, n(h_e) - 1, X_v = int 100 rho dh,
+    // A_v = int exp(-h / H_A) dh} from h_obs up, tabulated in dz (linear interpolation)
+    const float4* base;
+    int base_n;
+    float base_dz0, base_inv_step;
+    float kR0, kA0, lamA_nm, aer_alpha;   // transmission constants (log2 units, as AtmParams)
     // domain in which the network replaces the tables
     float dz_min, dz_max, mu_min;   // mu_min = cos of the largest zenith
     // bands around the atmosphere's layer boundaries, where the exact fields
     // jump with n(h_e): heights dz in [band_lo[i], band_hi[i]) use the tables
     int n_bands;
     float band_lo[kMaxLayers], band_hi[kMaxLayers];
+    int polls;   // polls of each tensor-core completion before giving up (>= 0)
 };
 
 __device__ __forceinline__ float height_coordinate(const SurrogateView& sv, float dz) {
@@ -64,6 +72,30 @@ __device__ __forceinline__ bool in_surrogate_domain(const SurrogateView& sv, flo
     for (int i = 0; i < kMaxLayers; ++i)
         if (i < sv.n_bands && dz >= sv.band_lo[i] && dz < sv.band_hi[i]) ok = false;
     return ok;
+}
+
+// First-order baseline of the fields (G_R, G_t, ln T) at height dz above the
+// observation level, cos(theta0) = mu and 1/lambda_nm = inv_l.  Expanding the
+// exact planar path (Eq. 3.17-3.18) to first order in n - 1, with
+// I = int (n - 1) dh over [h_obs, h_e] and H = h_e - h_obs:
+//   G_R = d_e H - I,   G_t = 2 I - d_e H + (d_e H - I) / mu^2,
+//   ln T = -(X_v / X_R(lambda) + tau_A(lambda) A_v / H_A) / mu   (the vertical columns).
+// The network learns only the remainder, about 1e-3 of the fields' range in
+// the plane and a few per cent on the spherical shell, so its BF16
+// resolution acts on that remainder.
+__device__ __forceinline__ float3 surrogate_baseline(const SurrogateView& sv, float dz, float mu, float inv_l) {
+    const float f = fminf(fmaxf((dz - sv.base_dz0) * sv.base_inv_step, 0.0f), (float)(sv.base_n - 1));
+    const int j = min((int)f, sv.base_n - 2);
+    const float t = f - (float)j;
+    const float4 a = __ldg(sv.base + j), b = __ldg(sv.base + j + 1);
+    const float I = fmaf(t, b.x - a.x, a.x), de = fmaf(t, b.y - a.y, a.y);
+    const float Xv = fmaf(t, b.z - a.z, a.z), Av = fmaf(t, b.w - a.w, a.w);
+    const float m = fmaf(de, dz, -I);   // int (d_e - d) dh
+    const float imu = 1.0f / mu;
+    const float il2 = inv_l * inv_l;
+    const float kA = sv.kA0 * ex2_approx(sv.aer_alpha * lg2_approx(sv.lamA_nm * inv_l));
+    return make_float3(m, fmaf(m, imu * imu, fmaf(2.0f, I, -de * dz)),
+                       -0.69314718f * (Xv * sv.kR0 * il2 * il2 + Av * kA) * imu);
 }
 
 // The trained network's view (defined with the training code).

@@ -21,6 +21,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "exact_path.cuh"
 #include "mlp_tc.cuh"
 
 namespace cs {
@@ -76,6 +77,7 @@ struct WarpSmem {
     unsigned int map[kWMapCap];
 };
 constexpr size_t kSmemExact = (kThreads / 32) * sizeof(WarpSmem);
+static_assert(4 * (kSmemExact + 1024) <= 228 * 1024, "four exact-tracer blocks per SM");
 
 // The surrogate instances keep the tensor-core network's buffers after the tile.
 constexpr size_t kTcSmemOffset = (sizeof(TileSmem) + 127) & ~(size_t)127;
@@ -108,8 +110,8 @@ __device__ __forceinline__ int block_scan(int v, int (*wsum)[kMaxThreads / 32], 
 }
 
 __device__ __forceinline__ void emit_record(const OutParams& o, unsigned long long seg, int k, int i, float x,
-                                            float y, float t_rel, float inv_l, int tel, int bin, int status,
-                                            int pix) {
+                                            float x_lo, float y, float y_lo, float t_rel, float inv_l, int tel,
+                                            int bin, int status, int pix) {
     const unsigned long long slot = atomicAdd(o.record_count, 1ULL);
     if (slot < o.record_capacity) {
         cs_record r;
@@ -118,6 +120,8 @@ __device__ __forceinline__ void emit_record(const OutParams& o, unsigned long lo
         r.i = (uint32_t)i;
         r.x = x;
         r.y = y;
+        r.x_lo = x_lo;
+        r.y_lo = y_lo;
         r.dt_ns = t_rel * 1e9f;
         r.lambda_nm = 1.0f / inv_l;
         r.tel = tel;
@@ -167,6 +171,20 @@ __device__ __forceinline__ bool lv1_drop(const PropParams& pp, const DetParams& 
     return h >= pp.lv1_a * exp2f(pp.lv1_b * log2f(x));
 }
 
+// K = ceil(L / s_max) sub-steps (Sec. 4.2.1) for s_max = sh + sl (float-float):
+// the FP32 quotient proposes K, the sign of K s_max - L (the product exact
+// through FMA, to 2^-48 relative) confirms K s_max >= L > (K - 1) s_max.
+__device__ __forceinline__ int substep_count(float L, float sh, float sl) {
+    int K = max(1, (int)ceilf(L / sh));
+    const auto covers = [&](int k) {
+        const float kf = (float)k, p = kf * sh;
+        return (p - L) + (fmaf(kf, sh, -p) + kf * sl) >= 0.0f;
+    };
+    if (!covers(K)) ++K;
+    else if (K > 1 && covers(K - 1)) --K;
+    return K;
+}
+
 // Stage 1 (Sec. 5.3.1): import one segment, filter it, fold its parameters
 // and compute its local origin.  Returns the number of sub-steps (0 if invalid).
 // Planar: the origin is the ground intercept of the segment's line (float-float).
@@ -194,7 +212,7 @@ __device__ __forceinline__ int import_segment(SM& S, int t, const cs_segment* se
     const float inv_n = rsqrtf(n2);
     const float Px = dir.x * inv_n, Py = dir.y * inv_n, Pz = dir.z * inv_n;
     const float L = dir.w;
-    const int K = max(1, (int)ceilf(L / pp.s_max));
+    const int K = substep_count(L, pp.s_max, pp.s_max_lo);
     float x_hi, x_lo, y_hi, y_lo, z_hi, z_lo;
     split_f64(xy.x, x_hi, x_lo);
     split_f64(xy.y, y_hi, y_lo);
@@ -427,6 +445,27 @@ __device__ __noinline__ int camera_pixel(const DetParams& dp, float ddx, float d
     return iy * n + ix;
 }
 
+// Absorption in the optics (Sec. 6.4): the camera keeps a photon that reached
+// pixel pix when the 24-bit uniform of Philox word x of counter (segment,
+// sub-step, bunch | 2^30) lies below R(lambda) eps(lambda), the mirror's
+// reflectivity times the camera's detection efficiency, each linear between
+// the detector's nodes and constant beyond them.  Returns pix or -1.
+__device__ __forceinline__ int optics_survival(const DetParams& dp, const PropParams& pp, unsigned long long gid, int k,
+                                               int i, float inv_l, int pix) {
+    if (pix < 0 || dp.eff_n == 0) return pix;
+    const float lnm = 1.0f / inv_l;
+    int j = 0;
+    while (j + 2 < dp.eff_n && lnm > dp.eff_l[j + 1]) ++j;
+    float fR = dp.eff_R[0], fE = dp.eff_E[0];
+    if (dp.eff_n > 1) {
+        const float t = fminf(fmaxf((lnm - dp.eff_l[j]) / (dp.eff_l[j + 1] - dp.eff_l[j]), 0.0f), 1.0f);
+        fR = fmaf(t, dp.eff_R[j + 1] - dp.eff_R[j], dp.eff_R[j]);
+        fE = fmaf(t, dp.eff_E[j + 1] - dp.eff_E[j], dp.eff_E[j]);
+    }
+    const uint4 r = philox_rk((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, (uint32_t)i | 0x40000000u, pp.rk);
+    return uniform24(r.x) < fR * fE ? pix : -1;
+}
+
 // Snell's law in vector form through homogeneous slabs (Sec. 3.4.2, Eq. 3.15),
 // the general-atmosphere tracer.  The height dz above the observation level is
 // cut into the fewest equal slabs no thicker than dh; slab j holds the index
@@ -476,12 +515,17 @@ __device__ __noinline__ float4 snell_path(const AtmParams& ap, float dz, float c
 // line (b_0 = r_e sin(psi_0)) is walked through the same shells and the
 // differences are summed.  Returns {arc-length correction along the ground
 // r_g (Phi - Phi_line) [m], c t_path - straight length [m], X_slant, A_slant}.
-__device__ __noinline__ float4 snell_path_sph(const AtmParams& ap, float dz, float sin2, float dh) {
+// When the straight line passes over the ground sphere (b_0 >= r_g) while the
+// refracted photon still reaches it, there is no line to refer to: the sums
+// are then absolute, {r_g Phi, c t_path, X, A}, and `absolute` is set.
+__device__ __noinline__ float4 snell_path_sph(const AtmParams& ap, float dz, float sin2, float dh, bool& absolute) {
     const int ns = max(1, (int)ceilf(dz / dh));
     const float step = dz / (float)ns;
     const float d0 = delta_at(ap, dz - 0.5f * step);
     const float re = ap.rg + dz;
     const float b0 = re * sqrtf(sin2);
+    const bool line = b0 < ap.rg;
+    absolute = !line;
     float sPhi = 0.0f, sT = 0.0f, sX = 0.0f, sA = 0.0f;
     for (int j = 0; j < ns; ++j) {
         const float h = dz - ((float)j + 0.5f) * step;
@@ -489,10 +533,12 @@ __device__ __noinline__ float4 snell_path_sph(const AtmParams& ap, float dz, flo
         const float r_out = re - (float)j * step, r_in = r_out - step;
         const float rs = fmaf(-2.0f * (float)j - 1.0f, step, 2.0f * re);   // r_out + r_in
         const float b = b0 + b0 * (d0 - dj) * rcp_approx(1.0f + dj);
-        const float q_out = sqrtf((r_out - b) * (r_out + b)), q_in = sqrtf((r_in - b) * (r_in + b));
-        const float p_out = sqrtf((r_out - b0) * (r_out + b0)), p_in = sqrtf((r_in - b0) * (r_in + b0));
+        const float q_out = sqrtf(fmaxf((r_out - b) * (r_out + b), 0.0f));
+        const float q_in = sqrtf(fmaxf((r_in - b) * (r_in + b), 0.0f));
+        const float p_out = sqrtf(fmaxf((r_out - b0) * (r_out + b0), 0.0f));
+        const float p_in = sqrtf(fmaxf((r_in - b0) * (r_in + b0), 0.0f));
         const float t = step * rs * rcp_approx(q_out + q_in);
-        const float t0 = step * rs * rcp_approx(p_out + p_in);
+        const float t0 = line ? step * rs * rcp_approx(p_out + p_in) : 0.0f;
         const float irr = rcp_approx(r_in * r_out);
         sPhi += (b * t - b0 * t0) * irr;
         sT += fmaf(dj, t, t - t0);
@@ -502,6 +548,15 @@ __device__ __noinline__ float4 snell_path_sph(const AtmParams& ap, float dz, flo
         }
     }
     return make_float4(ap.rg * sPhi, sT, ap.rho_per_delta * sX, ap.aer_hobs * sA);
+}
+
+// Survival probability (Sec. 4.3.1) from the slant columns in table form
+// (G_X = X cos, G_A = A cos): exp(-X / X_R(lambda) - tau_A(lambda) A / H_A).
+__device__ __forceinline__ float transmission_T(const AtmParams& ap, float GX, float GA, float inv_l, float inv_uz) {
+    const float il2 = inv_l * inv_l;
+    const float kR = ap.kR0 * il2 * il2;
+    const float kA = ap.kA0 * ex2_approx(ap.aer_alpha * lg2_approx(ap.lamA_nm * inv_l));
+    return ex2_approx(-(GX * kR + GA * kA) * inv_uz);
 }
 
 // The correction fields at (dz, tan^2 of the local zenith) and the
@@ -537,11 +592,7 @@ __device__ __forceinline__ void correction_fields(const AtmParams& ap, bool use_
         if (ap.transmission) {
             const float2 xa = __ffma2_rn(aa, __ffma2_rn(ff, make_float2(s0.z, s0.w), make_float2(v0.z, v0.w)),
                                          __fmul2_rn(gg, __ffma2_rn(ff, make_float2(s1.z, s1.w), make_float2(v1.z, v1.w))));
-            const float GX = xa.x, GA = xa.y;
-            const float il2 = inv_l * inv_l;
-            const float kR = ap.kR0 * il2 * il2;
-            const float kA = ap.kA0 * ex2_approx(ap.aer_alpha * lg2_approx(ap.lamA_nm * inv_l));
-            Tr = ex2_approx(-(GX * kR + GA * kA) * inv_uz);
+            Tr = transmission_T(ap, xa.x, xa.y, inv_l, inv_uz);
         }
     }
     if (!ap.transmission) Tr = 1.0f;
@@ -553,8 +604,16 @@ __device__ __forceinline__ void correction_fields(const AtmParams& ap, bool use_
 // (Sec. 4.4.1) or the surrogate network, transmission (Sec. 4.3.1) and
 // detection.  With SURR the whole warpgroup must call (inactive threads pass
 // active = false): the network runs on the tensor cores for 128 photons.
-template <bool SURR, bool SPH, bool REC, bool FL, bool TR, typename SM>
-__device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, long long base,
+// A bunch beyond the correction tables takes the exact path (Sec. 3.4.3),
+// integrated for that bunch.  That integration lives in a second kernel, the
+// exact pass, so that the photon kernel keeps its registers: MODE 0 (the
+// photon kernel) returns true for such a bunch without counting or recording
+// it; MODE 1 (the exact pass's scan) only returns whether the bunch lies
+// beyond the tables; MODE 2 (the exact pass) propagates it along the exact
+// path and counts it.
+enum { kModeMain = 0, kModeCheck = 1, kModeExact = 2 };
+template <bool SURR, bool SPH, bool REC, bool FL, bool TR, int MODE = kModeMain, typename SM>
+__device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, long long base,
                                       const PropParams& pp, const AtmParams& ap, const DetParams& dp,
                                       const OutParams& op, const SurrogateView& sv, TcSmem<kThreadsSur / 128>* tcs,
                                       Tally& T) {
@@ -597,7 +656,7 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
     // height above the observation level and the local zenith
     float dz, cos_z, sin2;
     float4 Cc, Dd;
-    float dvx = 0.0f, dvy = 0.0f, dvz = 0.0f;
+    float dvx = 0.0f, dvy = 0.0f, dvz = 0.0f, hx = 0.0f, hy = 0.0f, hz = 0.0f;
     if (!SPH) {
         dz = B.x + (B.y + ell * Pz);
         cos_z = -uz;
@@ -613,7 +672,9 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
         dvy = ey + f * (Py - Cc.w * ey);
         dvz = ez + f * (Pz - Cc.w * (1.0f + ez));
         cos_z = -(uz + ux * dvx + uy * dvy + uz * dvz);
-        const float hx = ux + cos_z * dvx, hy = uy + cos_z * dvy, hz = uz + cos_z * (1.0f + dvz);
+        hx = ux + cos_z * dvx;
+        hy = uy + cos_z * dvy;
+        hz = uz + cos_z * (1.0f + dvz);
         sin2 = hx * hx + hy * hy + hz * hz;
     }
     const float inv_uz = rcp_approx(cos_z);
@@ -621,7 +682,13 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
     int status = CS_ST_LANDED;
     if (!(cos_z > 0.0f)) status = CS_ST_UPWARD;              // discarded (Sec. 5.3.4)
     else if (dz < 0.0f) status = CS_ST_BELOW;
-    else if (ap.use_tables && (w > ap.tv.w_max || dz >= ap.tv.dz_max)) status = CS_ST_DOMAIN;
+    // beyond the correction tables (steeper than their largest zenith or above their
+    // top): the exact path is integrated for this photon instead (Sec. 3.4.3)
+    const bool beyond = ap.use_tables && !(TR && ap.refraction) && (w > ap.tv.w_max || dz >= ap.tv.dz_max);
+    if constexpr (MODE == kModeCheck) return status == CS_ST_LANDED && beyond;
+    if constexpr (MODE == kModeMain && !SURR) {
+        if (status == CS_ST_LANDED && beyond) return true;   // left to the exact pass
+    }
 
     // ---- the surrogate network, warp-collective --------------------------------
     float net[3] = {0.0f, 0.0f, 1.0f};
@@ -632,16 +699,23 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
                             use_net ? fmaf(sv.in_scale[1], cos_z, sv.in_shift[1]) : 0.0f,
                             use_net ? fmaf(sv.in_scale[2], inv_l, sv.in_shift[2]) : 0.0f};
         float y[3];
-        if (sv.split) net128_tc<true>(sv, *tcs, x, y);
-        else net128_tc<false>(sv, *tcs, x, y);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) net[c] = fmaf(sv.out_half[c], y[c], sv.out_mid[c]);
+        const bool ok = sv.split ? net128_tc<true>(sv, *tcs, x, y) : net128_tc<false>(sv, *tcs, x, y);
+        use_net = use_net && ok;   // a tensor-core wait that gave up: the tables take over
+        if (use_net) {   // the network's part plus the first-order baseline
+            const float3 bl = surrogate_baseline(sv, dz, cos_z, inv_l);
+            net[0] = fmaf(sv.out_half[0], y[0], sv.out_mid[0]) + bl.x;
+            net[1] = fmaf(sv.out_half[1], y[1], sv.out_mid[1]) + bl.y;
+            net[2] = fmaf(sv.out_half[2], y[2], sv.out_mid[2]) + bl.z;
+        }
     }
-    if (!active) return;
+    if (!active) return false;
+    if constexpr (MODE == kModeMain && SURR) {
+        if (status == CS_ST_LANDED && beyond) return true;   // left to the exact pass
+    }
 
     // ---- propagation and detection -----------------------------------------------
     int tel = -1, bin = -1, pix = -1;
-    float x = 0.0f, y = 0.0f, t_rel = ell * B.w;
+    float x = 0.0f, y = 0.0f, xl = 0.0f, yl = 0.0f, t_rel = ell * B.w;   // ground point x + xl, y + yl
     float rx = 0.0f, ry = 0.0f;
     if (status == CS_ST_LANDED && !SPH) {
         if (Pz < -1e-3f && !FL) {
@@ -676,7 +750,16 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
                 Tr = ex2_approx(-(sp.z * (ap.kR0 * il2 * il2) + sp.w * kA));
             }
         } else {
-            correction_fields<SURR>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
+            if (MODE == kModeExact && beyond) {   // the exact path, integrated for this photon
+                bool reach;
+                const float4 f = exact_fields_planar(ap.self, dz, cos_z, reach);
+                GR = f.x;
+                Gt = f.y;
+                Tr = ap.transmission ? transmission_T(ap, f.z, f.w, inv_l, inv_uz) : 1.0f;
+                if (!reach) status = CS_ST_NO_GROUND;   // reflected back up by an inverted profile
+            } else {
+                correction_fields<SURR>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
+            }
             if (ap.refraction) {
                 const float c3 = GR * inv_uz * inv_uz * inv_uz;
                 const float2 r2 = __ffma2_rn(make_float2(c3, c3), uxy, make_float2(rx, ry));
@@ -687,17 +770,18 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
         }
         t_rel = fmaf(path, kInvC, t_rel);
         const float4 Cg = S.segC[sg];
-        if (REC) {   // records carry the ground point to FP32 precision
-            float s, e;
-            two_sum(Cg.x, rx, s, e);
-            x = s + (e + Cg.y);
-            two_sum(Cg.z, ry, s, e);
-            y = s + (e + Cg.w);
+        if (REC) {   // records carry the ground point as float-float
+            two_sum(Cg.x, rx, x, xl);
+            xl += Cg.y;
+            two_sum(Cg.z, ry, y, yl);
+            yl += Cg.w;
         } else {     // the telescope hash only needs its cell
             x = Cg.x + (Cg.y + rx);
             y = Cg.z + (Cg.w + ry);
         }
-        if (ap.transmission && !(u3 < Tr)) {
+        if (status != CS_ST_LANDED) {
+            // the path never meets the observation level: missed
+        } else if (ap.transmission && !(u3 < Tr)) {
             status = CS_ST_ABSORBED;
         } else {
             const int sh = S.shower[sg];
@@ -741,6 +825,7 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
                         const float2 TL = __ldg(dp.tel_lo + tel);
                         pix = camera_pixel(dp, (T4.x - Cg.x) + ((TL.x - Cg.y) - rx),
                                            (T4.y - Cg.z) + ((TL.y - Cg.w) - ry), T4.z, ux * sc, uy * sc, ugz);
+                        pix = optics_survival(dp, pp, gid, k, i, inv_l, pix);
                     }
                 }
                 if (tel >= 0) {
@@ -759,29 +844,76 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
         const float disc = fmaxf(re * re * cos_z * cos_z - D2, 0.0f);
         const float tt = D2 * rcp_approx(re * cos_z + sqrtf(disc));
         const float h_obs_f = (float)ap.h_obs;
-        float Gx = Cc.x + (Dd.x + fmaf(ell, Px, tt * ux));
-        float Gy = Cc.y + (Dd.y + fmaf(ell, Py, tt * uy));
-        float Gz = Cc.z + (Dd.z + fmaf(ell, Pz, tt * uz));
+        // ground point G = start (float-float) + offset, kept as float-float (Gx + Gxl, ...):
+        // the offset is as long as the photon's path, the start may lie tens of km out
+        float Gx, Gy, Gz, Gxl, Gyl, Gzl;
+        auto set_G = [&](float ox, float oy, float oz) {
+            two_sum(Cc.x, Dd.x + ox, Gx, Gxl);
+            two_sum(Cc.y, Dd.y + oy, Gy, Gyl);
+            two_sum(Cc.z, Dd.z + oz, Gz, Gzl);
+        };
+        set_G(fmaf(ell, Px, tt * ux), fmaf(ell, Py, tt * uy), fmaf(ell, Pz, tt * uz));
         if (pp.lv3) {   // LV3 photon pre-filter (Sec. 4.3.4): the straight line's landing point
             const float sx = Gx - pp.lv3_c[0], sy = Gy - pp.lv3_c[1], sz = Gz - pp.lv3_c[2];
             if (fmaf(sx, sx, fmaf(sy, sy, sz * sz)) > pp.lv3_r2) status = CS_ST_LV3;
         }
+        float GR = 0.0f, Gt = 0.0f, Tr = 1.0f;
+        const bool stepper = TR && ap.refraction;
+        bool direct = false;   // landing point from the path's central angle
+        // G = E + (r_g cos Phi - r_e) v_E + r_g sin Phi h_E, with
+        // r_g cos Phi - r_e = -(dz + 2 r_g sin^2(Phi / 2)) and h_E = (u + cos v_E) / sin
+        auto land_at = [&](float Phi) {
+            // a central angle within the atmosphere stays below 0.4 rad: Taylor terms to x^11
+            auto sin_small = [](float x) {
+                const float x2 = x * x;
+                return x * fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, -2.5052108e-8f, 2.7557319e-6f),
+                                                              -1.9841270e-4f), 8.3333333e-3f), -1.6666667e-1f), 1.0f);
+            };
+            const float sP = sin_small(Phi), sh = sin_small(0.5f * Phi);
+            const float down = fmaf(2.0f * rg * sh, sh, dz), along = rg * sP * rsqrtf(sin2);
+            set_G(fmaf(ell, Px, fmaf(along, hx, -down * dvx)), fmaf(ell, Py, fmaf(along, hy, -down * dvy)),
+                  fmaf(ell, Pz, fmaf(along, hz, -down * (1.0f + dvz))));
+        };
+        // Does the path meet the ground sphere?  Inside the tables' domain (zenith <= 75 deg,
+        // below the top of the atmosphere) it always does; straight lines, the stepper and
+        // photons beyond the tables are checked.
         if (status == CS_ST_LANDED) {
-            float GR, Gt, Tr;
-            const bool stepper = TR && ap.refraction;
+            if (!ap.refraction) {   // the straight line: r_g > r_e sin(psi) <=> r_e (1 - sin) > dz
+                const float s0 = sqrtf(sin2);
+                if (!(fmaf(re, cos_z * cos_z / (1.0f + s0), -dz) > 0.0f)) status = CS_ST_NO_GROUND;
+            } else if ((stepper || (MODE == kModeExact && beyond)) && !sph_reaches(ap.self, dz, cos_z, sqrtf(sin2))) {
+                status = CS_ST_NO_GROUND;
+            }
+        }
+        if (status == CS_ST_LANDED) {
             if (stepper) {   // the per-photon stepper instead of the tables
-                const float4 sp = snell_path_sph(ap, dz, sin2, pp.snell_dh);
+                bool absolute;
+                const float4 sp = snell_path_sph(ap, dz, sin2, pp.snell_dh, absolute);
                 GR = sp.x;   // here the arc-length correction itself
                 Gt = sp.y;   // and the delay as a length
+                if (absolute) {   // no straight line to the ground: land from the central angle
+                    direct = true;
+                    land_at(sp.x * ap.inv_rg);
+                }
                 Tr = 1.0f;
                 if (ap.transmission) {
                     const float il2 = inv_l * inv_l;
                     const float kA = ap.kA0 * ex2_approx(ap.aer_alpha * lg2_approx(ap.lamA_nm * inv_l));
                     Tr = ex2_approx(-(sp.z * (ap.kR0 * il2 * il2) + sp.w * kA));
                 }
+            } else if (MODE == kModeExact && beyond) {   // the exact path, integrated for this photon
+                const float4 f = exact_fields_sph(ap.self, dz, cos_z, sqrtf(sin2));
+                Tr = ap.transmission ? transmission_T(ap, f.z, f.w, inv_l, inv_uz) : 1.0f;
+                if (ap.refraction) {
+                    direct = true;
+                    land_at(f.x);
+                    Gt = f.y;   // c t_path itself
+                }
             } else {
                 correction_fields<SURR>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
             }
+        }
+        if (status == CS_ST_LANDED) {
             // ground tangent in the plane of travel at the landing point
             const float irg = ap.inv_rg;
             const float gvx = Gx * irg, gvy = Gy * irg, gvz = (Gz - h_obs_f) * irg;   // v_G - z-hat
@@ -791,29 +923,36 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
             tx *= tn;
             ty *= tn;
             tz *= tn;
-            float path = tt;
-            if (ap.refraction) {   // arc-length correction along the ground, delay
+            float path = direct ? Gt : tt;
+            if (ap.refraction && !direct) {   // arc-length correction along the ground, delay
                 const float dR = stepper ? GR : GR * inv_uz * inv_uz * inv_uz * sqrtf(sin2);
-                Gx = fmaf(dR, tx, Gx);
-                Gy = fmaf(dR, ty, Gy);
-                Gz = fmaf(dR, tz, Gz);
+                Gxl = fmaf(dR, tx, Gxl);
+                Gyl = fmaf(dR, ty, Gyl);
+                Gzl = fmaf(dR, tz, Gzl);
                 path = stepper ? path + Gt : fmaf(Gt, inv_uz, path);
             }
             t_rel = fmaf(path, kInvC, t_rel);
-            // azimuthal-equidistant coordinates: r_g atan(rho / z_c) along (G_x, G_y)
-            const float zc = rg + (Gz - h_obs_f);
-            const float iz = 1.0f / zc;
-            const float X2 = (Gx * Gx + Gy * Gy) * iz * iz;
-            const float fac = rg * iz * fmaf(X2, fmaf(X2, 0.2f, -1.0f / 3.0f), 1.0f);
-            x = Gx * fac;
-            y = Gy * fac;
+            // azimuthal-equidistant coordinates: x = G_x r_g atan(X) / (X z_c), X = rho / z_c,
+            // z_c = r_g (1 + eta); written x = G_x - G_x om with the small om = 1 - r_g atan(X) /
+            // (X z_c) = (eta + (1 - atan(X) / X)) / (1 + eta), kept as float-float
+            const float eta = ((Gz - h_obs_f) + Gzl) * irg, ie = rcp_approx(1.0f + eta);
+            const float X2 = (Gx * Gx + Gy * Gy) * (irg * irg) * (ie * ie);
+            // 1 - atan(X) / X by its series near the centre; far landings (X^2 > 0.01, beyond
+            // ~600 km, only photons beyond the tables' zenith) take the library arctangent
+            const float one_m_s = X2 < 0.01f ? X2 * fmaf(X2, -0.2f, 1.0f / 3.0f) : 1.0f - atanf(sqrtf(X2)) * rsqrtf(X2);
+            const float om = (eta + one_m_s) * ie;
+            x = Gx;
+            xl = fmaf(-Gx, om, Gxl);
+            y = Gy;
+            yl = fmaf(-Gy, om, Gyl);
+            const float xs = x + xl, ys = y + yl;   // single floats for the box and hash tests
             if (ap.transmission && !(u3 < Tr)) {
                 status = CS_ST_ABSORBED;
             } else {
                 const int sh = S.shower[sg];
                 if (dp.nx > 0) {
-                    const int ix = (int)floorf(((x - dp.hx0_hi) - dp.hx0_lo) * dp.inv_dx);
-                    const int iy = (int)floorf(((y - dp.hy0_hi) - dp.hy0_lo) * dp.inv_dy);
+                    const int ix = (int)floorf(((x - dp.hx0_hi) + (xl - dp.hx0_lo)) * dp.inv_dx);
+                    const int iy = (int)floorf(((y - dp.hy0_hi) + (yl - dp.hy0_lo)) * dp.inv_dy);
                     if (ix >= 0 && ix < dp.nx && iy >= 0 && iy < dp.ny) {
                         bin = iy * dp.nx + ix;
                         hist_add(op, (unsigned int)(sh * dp.ny * dp.nx + bin), b);
@@ -829,14 +968,14 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
                         ugz = -cos_g * (1.0f + gvz) + sin_g * tz;
                     }
                     const bool hashed = ugx * ugx + ugy * ugy <= dp.hash_sin2_max;
-                    if (!hashed || (x >= dp.bx0 && x < dp.bx1 && y >= dp.by0 && y < dp.by1)) {
+                    if (!hashed || (xs >= dp.bx0 && xs < dp.bx1 && ys >= dp.by0 && ys < dp.by1)) {
                         auto delta3 = [&](const float4& T3, float& ddx, float& ddy, float& ddz) {
-                            ddx = T3.x - Gx;
-                            ddy = T3.y - Gy;
-                            ddz = T3.z - Gz;
+                            ddx = (T3.x - Gx) - Gxl;
+                            ddy = (T3.y - Gy) - Gyl;
+                            ddz = (T3.z - Gz) - Gzl;
                         };
                         tel = hit_telescope(
-                            dp, hashed, x, y, ugx, ugy, ugz,
+                            dp, hashed, xs, ys, ugx, ugy, ugz,
                             [&](const float4& D, float, float, float& ddx, float& ddy, float& ddz) { delta3(D, ddx, ddy, ddz); },
                             [&](int it, float& ddx, float& ddy, float& ddz, float& r) {
                                 const float4 T3 = __ldg(dp.tel3 + it);
@@ -845,7 +984,8 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
                             });
                         if (tel >= 0 && dp.cam_n > 0) {
                             const float4 T3 = __ldg(dp.tel3 + tel);
-                            pix = camera_pixel(dp, T3.x - Gx, T3.y - Gy, T3.z - Gz, ugx, ugy, ugz);
+                            pix = camera_pixel(dp, (T3.x - Gx) - Gxl, (T3.y - Gy) - Gyl, (T3.z - Gz) - Gzl, ugx, ugy, ugz);
+                            pix = optics_survival(dp, pp, gid, k, i, inv_l, pix);
                         }
                     }
                     if (tel >= 0) {
@@ -862,14 +1002,50 @@ __device__ __forceinline__ void bunch(const SM& S, int q, int i, bool active, lo
     T.upward += status == CS_ST_UPWARD ? b : 0;
     T.hist += bin >= 0 ? b : 0;
     T.tel += tel >= 0 ? b : 0;
-    if (REC) emit_record(op, gid, k, i, x, y, t_rel, inv_l, tel, bin, status, pix);
+    if (REC) emit_record(op, gid, k, i, x, xl, y, yl, t_rel, inv_l, tel, bin, status, pix);
+    return false;
 }
 
-template <bool SURR, bool SPH, int MINB, bool REC, bool FL = false, bool TR = false,
+// Per-launch scratch (zeroed before the photon kernel): the photon kernel's
+// work counter, the exact pass's cursor, the number of listed groups and a
+// pad word; then one bit per group of pp.tiles_per_bit warp tiles (32
+// segments) that hold a bunch beyond the correction tables, and the list of
+// the marked groups (each entered once, when its bit is first set).
+constexpr int kScratchCounters = 4;
+__host__ __device__ constexpr size_t scratch_groups(long long n_wtiles, int tiles_per_bit) {
+    return (size_t)((n_wtiles + tiles_per_bit - 1) / tiles_per_bit);
+}
+__host__ __device__ constexpr size_t scratch_words(long long n_wtiles, int tiles_per_bit) {
+    return kScratchCounters + (scratch_groups(n_wtiles, tiles_per_bit) + 31) / 32 + scratch_groups(n_wtiles, tiles_per_bit);
+}
+// The part that must start at zero: the counters and the map (the list is written before it is read).
+__host__ __device__ constexpr size_t scratch_zero_words(long long n_wtiles, int tiles_per_bit) {
+    return kScratchCounters + (scratch_groups(n_wtiles, tiles_per_bit) + 31) / 32;
+}
+
+// Marks group g for the exact pass (bit and, the first time, list entry).
+__device__ __forceinline__ void mark_group(unsigned int* scratch, long long n_wtiles, int tiles_per_bit, unsigned int g) {
+    unsigned int* bits = scratch + kScratchCounters;
+    const unsigned int bit = 1u << (g & 31);
+    if (!(atomicOr(bits + (g >> 5), bit) & bit)) {
+        unsigned int* list = bits + (scratch_groups(n_wtiles, tiles_per_bit) + 31) / 32;
+        list[atomicAdd(scratch + 2, 1u)] = g;
+    }
+}
+
+// The photon kernel (EX = false) and the exact pass (EX = true, exact-tracer
+// instances only): the exact pass walks the same warp tiles, skips those
+// whose bit the photon kernel left clear, regenerates the sub-steps and
+// bunches of the others from their keyed draws, and propagates the bunches
+// beyond the tables along the exact path, 32 at a time per warp.
+template <bool SURR, bool SPH, int MINB, bool REC, bool FL = false, bool TR = false, bool EX = false,
           int NT = SURR ? kThreadsSur : kThreads>
 __global__ void __launch_bounds__(NT, MINB)
 propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, const OutParams op,
-                 unsigned int* tile_ctr, const SurrogateView sv) {
+                 unsigned int* scratch, const SurrogateView sv) {
+    static_assert(!(EX && SURR), "the exact pass runs the exact-tracer form");
+    if (EX && __ldcg(scratch + 2) == 0) return;   // no tile holds a bunch beyond the tables
+    unsigned int* const tile_ctr = scratch + (EX ? 1 : 0);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
     TcSmem<kThreadsSur / 128>* tcs = SURR ? reinterpret_cast<TcSmem<kThreadsSur / 128>*>(smem_raw + kTcSmemOffset) : nullptr;
@@ -885,12 +1061,9 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
         WarpSmem& W = reinterpret_cast<WarpSmem*>(smem_raw)[t >> 5];
         const int lane = t & 31;
         const long long n_wtiles = (pp.n + kWTile - 1) / kWTile;
-        for (;;) {
-            unsigned int wt = 0;
-            if (lane == 0) wt = atomicAdd(tile_ctr, 1u);
-            const long long tile = (long long)__shfl_sync(0xffffffffu, wt, 0);
-            if (tile >= n_wtiles) break;
+        auto process_tile = [&](const long long tile) {
             const long long base = tile * kWTile;
+            bool any_beyond = false;   // a bunch of this tile left to the exact pass
             const int Kt0 = base + lane < pp.n
                                 ? import_segment<SPH, FL>(W, lane, pp.segs + base + lane, pp, ap, dp, invalid, dropped)
                                 : 0;
@@ -997,13 +1170,76 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                         off += N;
                     }
                     __syncwarp();
-                    for (int p = lane; p < wn; p += 32) {
-                        const unsigned int e = W.map[p];
-                        bunch<false, SPH, REC, FL, TR>(W, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), true, base,
-                                               pp, ap, dp, op, sv, tcs, T);
+                    if constexpr (!EX) {
+                        for (int p = lane; p < wn; p += 32) {
+                            const unsigned int e = W.map[p];
+                            any_beyond |= bunch<false, SPH, REC, FL, TR>(W, (int)(e & ((1u << kQBits) - 1)),
+                                                                         (int)(e >> kQBits), true, base, pp, ap, dp,
+                                                                         op, sv, tcs, T);
+                        }
+                    } else {
+                        // rounds of 32 bunches: those beyond the tables are queued (in the map
+                        // entries already read: a round's entries are never read again) and
+                        // propagated 32 at a time, so that the warp stays converged
+                        int nq = 0;
+                        for (int pw = 0;; pw += 32) {
+                            const bool last = pw + 32 >= wn;
+                            const int p = pw + lane;
+                            bool take = false;
+                            unsigned int e = 0;
+                            if (p < wn) {
+                                e = W.map[p];
+                                take = bunch<false, SPH, REC, FL, TR, kModeCheck>(W, (int)(e & ((1u << kQBits) - 1)),
+                                                                                 (int)(e >> kQBits), true, base, pp,
+                                                                                 ap, dp, op, sv, tcs, T);
+                            }
+                            const unsigned int m = __ballot_sync(0xffffffffu, take);
+                            __syncwarp();
+                            if (take) W.map[nq + __popc(m & ((1u << lane) - 1u))] = e;
+                            nq += __popc(m);
+                            __syncwarp();
+                            while (nq >= 32 || (last && nq > 0)) {
+                                const int n_run = min(nq, 32);
+                                if (lane < n_run) {
+                                    const unsigned int ex = W.map[nq - n_run + lane];
+                                    bunch<false, SPH, REC, FL, TR, kModeExact>(W, (int)(ex & ((1u << kQBits) - 1)),
+                                                                               (int)(ex >> kQBits), true, base, pp, ap,
+                                                                               dp, op, sv, tcs, T);
+                                }
+                                nq -= n_run;
+                                __syncwarp();
+                            }
+                            if (last) break;
+                        }
                     }
                     __syncwarp();
                 }
+            }
+            if constexpr (!EX) {   // the exact pass is to visit this tile
+                if (__any_sync(0xffffffffu, any_beyond) && lane == 0)
+                    mark_group(scratch, n_wtiles, pp.tiles_per_bit, (unsigned int)tile / (unsigned int)pp.tiles_per_bit);
+            }
+        };
+        if constexpr (!EX) {
+            for (;;) {   // dynamic scheduling: warp tiles from the work counter
+                unsigned int wt = 0;
+                if (lane == 0) wt = atomicAdd(tile_ctr, 1u);
+                const long long tile = (long long)__shfl_sync(0xffffffffu, wt, 0);
+                if (tile >= n_wtiles) break;
+                process_tile(tile);
+            }
+        } else {
+            // the exact pass takes the marked groups from their list (none: nothing to do)
+            const unsigned int n_listed = __ldcg(scratch + 2);
+            const unsigned int* list = scratch + kScratchCounters + (scratch_groups(n_wtiles, pp.tiles_per_bit) + 31) / 32;
+            while (n_listed > 0) {
+                unsigned int idx = 0;
+                if (lane == 0) idx = atomicAdd(tile_ctr, 1u);
+                idx = __shfl_sync(0xffffffffu, idx, 0);
+                if (idx >= n_listed) break;
+                const long long g = (long long)__ldcg(list + idx);
+                const long long t_end = std::min<long long>((g + 1) * pp.tiles_per_bit, n_wtiles);
+                for (long long tile = g * pp.tiles_per_bit; tile < t_end; ++tile) process_tile(tile);
             }
         }
     } else {
@@ -1069,8 +1305,13 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                         const int p = pw + (t & (kGroup - 1));
                         const bool active = p < wn;
                         const unsigned int e = S.map[active ? p : pw];
-                        bunch<SURR, SPH, REC, FL, TR>(S, (int)(e & ((1u << kQBits) - 1)), (int)(e >> kQBits), active, base, pp,
-                                              ap, dp, op, sv, tcs, T);
+                        const int qs = (int)(e & ((1u << kQBits) - 1));
+                        if (bunch<SURR, SPH, REC, FL, TR>(S, qs, (int)(e >> kQBits), active, base, pp, ap, dp, op, sv,
+                                                          tcs, T)) {   // left to the exact pass: mark its warp tile
+                            const int sg = __float_as_int(S.sub[qs].w) & ((1 << kKShift) - 1);
+                            mark_group(scratch, (pp.n + kWTile - 1) / kWTile, pp.tiles_per_bit,
+                                       (unsigned int)((base + sg) / kWTile) / (unsigned int)pp.tiles_per_bit);
+                        }
                     }
                     __syncthreads();
                 }
@@ -1080,6 +1321,11 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
     }
 
     if (SURR) tc_teardown(*tcs);
+    if (EX) {   // the photon kernel counted these segments and their emitted bunches
+        emitted = 0;
+        invalid = 0;
+        dropped = 0;
+    }
 
     // ---- counter flush: missed = emitted - absorbed - detected.  A thread's
     // emitted bunches and the bunches it propagated are different sets, so the
@@ -1119,11 +1365,15 @@ bool compatible(const cs_atmosphere* atm, const cs_detector* det) {
 }
 
 cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp, const AtmParams& ap,
-                        const DetParams& dp, const OutParams& op, unsigned int* ctr, const cs_surrogate* sur) {
+                        const DetParams& dp, const OutParams& op, unsigned int* ctr, const cs_surrogate* sur,
+                        int tc_poll_limit) {
     const size_t smem = sur ? kSmemSurrogate : kSmemExact;
-    SurrogateView none;
-    memset(&none, 0, sizeof none);
-    const SurrogateView& sv = sur ? *surrogate_view(sur) : none;
+    SurrogateView sv;
+    memset(&sv, 0, sizeof sv);
+    if (sur) {
+        sv = *surrogate_view(sur);
+        sv.polls = tc_poll_limit == 0 ? kTcSpin : std::max(tc_poll_limit, 0);
+    }
     // instances: (network or tables) x (sphere or plane) x (records or throughput)
     auto go = [&](auto kernel, int threads) { kernel<<<grid, threads, smem, stream>>>(pp, ap, dp, op, ctr, sv); };
     const bool rec = op.records != nullptr;
@@ -1146,6 +1396,21 @@ cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp
         else tr ? exact(f_{}, f_{}, t_{}) : exact(f_{}, f_{}, f_{});
     }
     CS_CUDA_TRY(cudaGetLastError());
+    // the exact pass over the warp tiles the photon kernel marked (only atmospheres
+    // with tables have a domain to leave; the stepper integrates every photon itself)
+    if (ap.use_tables && !(tr && ap.refraction)) {
+        const long long n_wtiles = (pp.n + kWTile - 1) / kWTile;
+        const unsigned grid_x = (unsigned)std::max<long long>(1, std::min<long long>(n_wtiles, (long long)device_sm_count() * 4));
+        auto pass = [&](auto kernel) { kernel<<<grid_x, kThreads, kSmemExact, stream>>>(pp, ap, dp, op, ctr, sv); };
+        if (ap.spherical) {
+            if (fl) rec ? pass(propagate_kernel<false, true, 4, true, true, false, true>) : pass(propagate_kernel<false, true, 4, false, true, false, true>);
+            else rec ? pass(propagate_kernel<false, true, 4, true, false, false, true>) : pass(propagate_kernel<false, true, 4, false, false, false, true>);
+        } else {
+            if (fl) rec ? pass(propagate_kernel<false, false, 4, true, true, false, true>) : pass(propagate_kernel<false, false, 4, false, true, false, true>);
+            else rec ? pass(propagate_kernel<false, false, 4, true, false, false, true>) : pass(propagate_kernel<false, false, 4, false, false, false, true>);
+        }
+        CS_CUDA_TRY(cudaGetLastError());
+    }
     return CS_OK;
 }
 
@@ -1153,10 +1418,25 @@ template <bool S, bool F, bool T>
 cudaError_t set_exact_smem(int smem) {
     const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e = cudaFuncSetAttribute(propagate_kernel<false, S, 4, false, F, T>, attr, smem);
-    return e != cudaSuccess ? e : cudaFuncSetAttribute(propagate_kernel<false, S, 4, true, F, T>, attr, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(propagate_kernel<false, S, 4, true, F, T>, attr, smem);
+    if (!T) {   // the exact pass of the table-tracer instances
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(propagate_kernel<false, S, 4, false, F, false, true>, attr, smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(propagate_kernel<false, S, 4, true, F, false, true>, attr, smem);
+    }
+    return e;
 }
 
+// Raises the kernels' shared-memory limits, once per device.
+constexpr int kMaxDevices = 64;
+std::mutex g_attr_mu;
+bool g_attr_done[kMaxDevices] = {};
+
 cs_status set_smem_attributes() {
+    int dev = 0;
+    CS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return CS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (g_attr_done[dev]) return CS_OK;
     const int smem = (int)kSmemExact, smem_sur = (int)kSmemSurrogate;
     const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
     CS_CUDA_TRY((set_exact_smem<false, false, false>(smem)));
@@ -1171,6 +1451,7 @@ cs_status set_smem_attributes() {
     CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, false, 1, true>, attr, smem_sur));
     CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, true, 1, false>, attr, smem_sur));
     CS_CUDA_TRY(cudaFuncSetAttribute(propagate_kernel<true, true, 1, true>, attr, smem_sur));
+    g_attr_done[dev] = true;
     return CS_OK;
 }
 
@@ -1210,28 +1491,33 @@ cudaError_t ensure(void** p, size_t* cap, size_t need) {
 
 size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Tile counters of the dynamic scheduler: a ring of slots in one device
-// allocation per device; each launch takes the next slot and zeroes it on its
-// stream, so launches in flight on different streams use different slots.
-constexpr int kCounterSlots = 4096;
-struct TileCounters {
-    std::mutex mu;
-    int device = -1;
-    unsigned int* d = nullptr;
-    unsigned int next = 0;
-};
-TileCounters g_ctr;
+// Per-launch scratch (work counters and the exact pass's tile bits) from a
+// stream-ordered memory pool the library keeps per device: allocated and
+// freed on the launch's stream, so launches in flight on different streams
+// never share it, and the pool keeps its memory between launches.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
 
-cs_status tile_counter(unsigned int** out) {
-    std::lock_guard<std::mutex> lock(g_ctr.mu);
+cs_status scratch_alloc(size_t bytes, cudaStream_t stream, unsigned int** out) {
     int dev = 0;
     CS_CUDA_TRY(cudaGetDevice(&dev));
-    if (g_ctr.device != dev || !g_ctr.d) {
-        g_ctr.d = nullptr;
-        CS_CUDA_TRY(cudaMalloc(&g_ctr.d, kCounterSlots * sizeof(unsigned int)));
-        g_ctr.device = dev;
+    if (dev < 0 || dev >= kMaxDevices) return CS_ERR_INVALID_ARG;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        if (!g_pool[dev]) {
+            cudaMemPoolProps props;
+            memset(&props, 0, sizeof props);
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            CS_CUDA_TRY(cudaMemPoolCreate(&g_pool[dev], &props));
+            uint64_t keep = ~0ull;
+            CS_CUDA_TRY(cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+        }
+        pool = g_pool[dev];
     }
-    *out = g_ctr.d + (g_ctr.next++ % kCounterSlots);
+    CS_CUDA_TRY(cudaMallocFromPoolAsync((void**)out, bytes, pool, stream));
     return CS_OK;
 }
 
@@ -1244,6 +1530,8 @@ void set_filters(PropParams& pp, const cs_opts& o, const DetParams& dp, const At
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
+    pp.s_max = (float)o.s_max;
+    pp.s_max_lo = (float)(o.s_max - (double)pp.s_max);
     pp.emission = o.emission;
     pp.fl_n = 0;
     pp.fl_yd = 0.0f;
@@ -1353,20 +1641,19 @@ cs_status launch(const cs_segment* d_segs, size_t n, const cs_atmosphere* atm, c
     pp.shower_bunch = nullptr;
     pp.s_max = (float)o.s_max;
     set_filters(pp, o, det->p, atm->p);
-    static bool attr_done = false;
-    if (!attr_done) {
-        cs_status sa = set_smem_attributes();
-        if (sa != CS_OK) return sa;
-        attr_done = true;
-    }
+    cs_status st = set_smem_attributes();
+    if (st != CS_OK) return st;
     const int per_sm = default_blocks_per_sm(o);
     const long long tiles = ((long long)n + kTile - 1) / kTile;
     const long long grid = std::min<long long>(tiles, (long long)device_sm_count() * per_sm);
-    unsigned int* ctr = nullptr;
-    cs_status st = tile_counter(&ctr);
-    if (st != CS_OK) return st;
-    CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), stream));
-    return launch_kernel((unsigned)grid, stream, pp, atm->p, det->p, op, ctr, o.surrogate);
+    pp.tiles_per_bit = 1;
+    const size_t bytes = scratch_words((pp.n + kWTile - 1) / kWTile, 1) * sizeof(unsigned int);
+    unsigned int* scratch = nullptr;
+    if ((st = scratch_alloc(bytes, stream, &scratch)) != CS_OK) return st;
+    CS_CUDA_TRY(cudaMemsetAsync(scratch, 0, scratch_zero_words((pp.n + kWTile - 1) / kWTile, 1) * sizeof(unsigned int), stream));
+    st = launch_kernel((unsigned)grid, stream, pp, atm->p, det->p, op, scratch, o.surrogate, o.tc_poll_limit);
+    CS_CUDA_TRY(cudaFreeAsync(scratch, stream));
+    return st;
 }
 
 }  // namespace
@@ -1464,13 +1751,19 @@ extern "C" cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_
     CS_CUDA_TRY(cudaMemcpyAsync(&produced, op.record_count, 8, cudaMemcpyDeviceToHost, stream));
     if (host_dropped) CS_CUDA_TRY(cudaMemcpyAsync(host_dropped, o.lv1_dropped, 8, cudaMemcpyDeviceToHost, stream));
     CS_CUDA_TRY(cudaStreamSynchronize(stream));
+    const bool timed_out = o.surrogate && tc_take_timeout();   // the tables served the network's photons
     if (out->record_count) *out->record_count = produced;
     if (out->records && produced) {
         const size_t ncopy = std::min<unsigned long long>(produced, out->record_capacity);
         CS_CUDA_TRY(cudaMemcpy(out->records, g_ws.recs, ncopy * sizeof(cs_record), cudaMemcpyDeviceToHost));
     }
     if (out->records && produced > out->record_capacity) return CS_ERR_CAPACITY;
-    return CS_OK;
+    return timed_out ? CS_ERR_TIMEOUT : CS_OK;
+}
+
+extern "C" cs_status cs_check_timeout(void) {
+    CS_CUDA_TRY(cudaDeviceSynchronize());
+    return tc_take_timeout() ? CS_ERR_TIMEOUT : CS_OK;
 }
 
 extern "C" cs_status cs_propagate(const cs_segment* segs, size_t n, const cs_atmosphere* atm,
@@ -1497,21 +1790,22 @@ extern "C" cs_status cs_philox4x32_10(const uint32_t* ctr, size_t n, uint32_t ke
 // memory pool or arena owns the whole device (so a surprise allocation would
 // fail or fragment it), real-time or embedded hosts that allow no allocation
 // after start-up, and callers that must keep every byte the library uses
-// accounted for in advance.  The regular device-pointer call allocates, once
-// per device, the ring of tile counters its dynamic scheduler uses; this
-// variant uses a counter in a file-scope device array instead, which the CUDA
-// module loader creates on every GPU that loads the library and which lives
-// until the process exits.
+// accounted for in advance.  The regular device-pointer call takes a small
+// per-launch scratch (its dynamic scheduler's work counters and the tile map
+// of its exact pass) from a memory pool the library creates; this variant
+// uses a file-scope device array instead, which the CUDA module loader creates
+// on every GPU that loads the library and which lives until the process exits.
 // ---------------------------------------------------------------------------
 namespace cs {
 namespace {
 
-// One 32-bit tile counter per call, padded to one 256-byte line.  A call can
-// schedule at most 2^32 - 1 tiles (of kWTile segments per warp, or kTile per block).
-constexpr int kNoAllocScratchWords = 64;
+// A call's counters, a map of 2^14 groups of warp tiles and their list (67.6 KB
+// in all): a call schedules at most 2^32 - 65537 warp tiles of 32 segments, and
+// each group holds ceil(tiles / 2^14) of them.
+constexpr int kNoAllocBits = 1 << 14;
+constexpr int kNoAllocScratchWords = kScratchCounters + kNoAllocBits / 32 + kNoAllocBits;
 static __device__ __align__(256) unsigned int g_noalloc_scratch[kNoAllocScratchWords];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 unsigned int* g_noalloc_ptr[kMaxDevices] = {};
 
@@ -1570,9 +1864,11 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     const int per_sm = default_blocks_per_sm(o);
     const long long tiles = ((long long)n + kTile - 1) / kTile;
     const long long grid = std::min<long long>(tiles, (long long)device_sm_count() * per_sm);
-    // the array keeps the previous call's count: start this call's schedule at zero
-    CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), stream));
-    return launch_kernel((unsigned)grid, stream, pp, atm->p, dp, op, ctr, o.surrogate);
+    const long long n_wtiles = ((long long)n + kWTile - 1) / kWTile;
+    pp.tiles_per_bit = (int)std::max<long long>(1, (n_wtiles + kNoAllocBits - 1) / kNoAllocBits);
+    // the array keeps the previous call's counters and map: start this call's at zero
+    CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, scratch_zero_words(n_wtiles, pp.tiles_per_bit) * sizeof(unsigned int), stream));
+    return launch_kernel((unsigned)grid, stream, pp, atm->p, dp, op, ctr, o.surrogate, o.tc_poll_limit);
 }
 
 // ---------------------------------------------------------------------------
@@ -1584,7 +1880,7 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
 struct cs_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    unsigned int* d_ctr = nullptr;   // the batch's own tile counter
+    unsigned int* d_ctr = nullptr;   // the batch's own scratch (work counters, exact-pass tile map)
     int* d_bunch = nullptr;          // per-shower bunch sizes
     int device = 0;
 };
@@ -1602,6 +1898,9 @@ cs_status check_device_call(const cs_segment* segs, size_t n, const cs_atmospher
     if (n > (size_t)1 << 40) return CS_ERR_INVALID_ARG;
     return CS_OK;
 }
+
+// Bytes of the per-launch scratch for n segments (one map bit per warp tile).
+size_t scratch_bytes(size_t n) { return scratch_words(((long long)n + kWTile - 1) / kWTile, 1) * sizeof(unsigned int); }
 
 // Grid of the persistent launch; also sets the kernel's shared-memory limit
 // (host-side calls kept out of stream capture).
@@ -1636,8 +1935,10 @@ cs_status enqueue(const cs_segment* segs, size_t n, const cs_atmosphere* atm, co
     pp.shower_bunch = d_bunch;
     pp.s_max = (float)o.s_max;
     set_filters(pp, o, det->p, atm->p);
-    CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned int), stream));
-    return launch_kernel(grid, stream, pp, atm->p, dp, op, ctr, o.surrogate);
+    pp.tiles_per_bit = 1;
+    CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, scratch_zero_words(((long long)n + kWTile - 1) / kWTile, 1) * sizeof(unsigned int),
+                                stream));
+    return launch_kernel(grid, stream, pp, atm->p, dp, op, ctr, o.surrogate, o.tc_poll_limit);
 }
 
 cs_status upload_bunches(const cs_detector* det, const int* shower_bunch, int** d_bunch) {
@@ -1681,7 +1982,7 @@ extern "C" cs_status cs_batch_create(const cs_segment* segs, size_t n, const cs_
         return s;
     };
     cudaError_t e;
-    if ((e = cudaMalloc(&b->d_ctr, 256)) != cudaSuccess) { set_last_error("batch counter", e); return fail(CS_ERR_CUDA); }
+    if ((e = cudaMalloc(&b->d_ctr, scratch_bytes(n))) != cudaSuccess) { set_last_error("batch scratch", e); return fail(CS_ERR_CUDA); }
     if ((st = upload_bunches(det, shower_bunch, &b->d_bunch)) != CS_OK) return fail(st);
     unsigned int grid = 1;
     if ((st = prepare_launch(n, o, &grid)) != CS_OK) return fail(st);
@@ -1745,7 +2046,7 @@ extern "C" cs_status cs_autotune_tiling(const cs_segment* segs, size_t n, const 
         if (e1) cudaEventDestroy(e1);
         return s;
     };
-    if ((e = cudaMalloc(&ctr, 256)) != cudaSuccess) { set_last_error("tune counter", e); return done(CS_ERR_CUDA); }
+    if ((e = cudaMalloc(&ctr, scratch_bytes(n))) != cudaSuccess) { set_last_error("tune scratch", e); return done(CS_ERR_CUDA); }
     if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
         set_last_error("tune events", e);
         return done(CS_ERR_CUDA);
@@ -1832,6 +2133,7 @@ extern "C" cs_status cs_autotune_bunches(const cs_segment* segs, size_t n, const
 struct cs_streamer {
     size_t chunk = 0;
     cs_segment* d_buf[2] = {nullptr, nullptr};
+    unsigned int* d_scratch[2] = {nullptr, nullptr};   // per-stream launch scratch
     cudaStream_t st[2] = {nullptr, nullptr};
     cudaEvent_t ev_in = nullptr, ev_done[2] = {nullptr, nullptr};
     int device = 0;
@@ -1842,6 +2144,7 @@ extern "C" void cs_streamer_destroy(cs_streamer* s) {
     for (int b = 0; b < 2; ++b) {
         if (s->st[b]) cudaStreamSynchronize(s->st[b]);
         cudaFree(s->d_buf[b]);
+        cudaFree(s->d_scratch[b]);
         if (s->st[b]) cudaStreamDestroy(s->st[b]);
         if (s->ev_done[b]) cudaEventDestroy(s->ev_done[b]);
     }
@@ -1861,6 +2164,7 @@ extern "C" cs_status cs_streamer_create(size_t chunk, cs_streamer** out) {
     cudaError_t e = cudaSuccess;
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
         e = cudaMalloc(&s->d_buf[b], chunk * sizeof(cs_segment));
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_scratch[b], scratch_bytes(chunk));
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st[b], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_done[b], cudaEventDisableTiming);
     }
@@ -1905,10 +2209,7 @@ extern "C" cs_status cs_streamer_run(cs_streamer* s, const cs_segment* host_segs
         CS_CUDA_TRY(cudaMemcpyAsync(s->d_buf[b], host_segs + off, m * sizeof(cs_segment), cudaMemcpyHostToDevice,
                                     s->st[b]));
         oc.seg_base = o.seg_base + off;
-        unsigned int* ctr = nullptr;
-        st = tile_counter(&ctr);
-        if (st != CS_OK) return st;
-        st = enqueue(s->d_buf[b], m, atm, det, seed, nullptr, oc, out, ctr, grid, s->st[b]);
+        st = enqueue(s->d_buf[b], m, atm, det, seed, nullptr, oc, out, s->d_scratch[b], grid, s->st[b]);
         if (st != CS_OK) return st;
     }
     // the caller's stream continues after both streams' last chunks

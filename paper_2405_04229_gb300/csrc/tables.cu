@@ -89,8 +89,8 @@ __device__ void node_fields(const AtmF64& a, double h_e, bool below, double cos0
     delta_rho(a, h_e, below, &de, &rho_e);
     const double ne = 1.0 + de, s = ne * sin0;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    // breakpoints: layer bottoms and the top strictly inside (h_obs, h_e)
-    double cuts[kMaxLayers + 3];
+    // breakpoints: layer bottoms, table nodes and the top strictly inside (h_obs, h_e)
+    double cuts[kMaxNodes + 3];
     int nc = 0;
     cuts[nc++] = a.h_obs;
     if (a.kind == CS_ATM_LAYERED) {
@@ -211,6 +211,49 @@ __global__ void assemble_kernel(const double* F, const double* Fb, const int* be
     tab[(size_t)node * 2 + 0] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
     tab[(size_t)node * 2 + 1] = make_float4((float)(up[0] - v[0]), (float)(up[1] - v[1]),
                                             (float)(up[2] - v[2]), (float)(up[3] - v[3]));
+}
+
+// Vertical integrals from h_obs up to each height h (one thread per height):
+// {int (n - 1) dh [m], n(h) - 1 (from above), int 100 rho dh [g/cm^2],
+//  int exp(-h / H_A) dh [m]}, by the same Gauss-Legendre pieces as the tables.
+__global__ void column_kernel(AtmF64 a, const double* h_in, size_t n, Fields4* out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double h = h_in[i];
+    double de, rho_e;
+    delta_rho(a, h, false, &de, &rho_e);
+    double cuts[kMaxNodes + 3];
+    int nc = 0;
+    cuts[nc++] = a.h_obs;
+    if (a.kind == CS_ATM_LAYERED) {
+        for (int k = 1; k < a.n_layers; ++k)
+            if (a.lay_h[k] > a.h_obs && a.lay_h[k] < h) cuts[nc++] = a.lay_h[k];
+        if (a.h_top > a.h_obs && a.h_top < h) cuts[nc++] = a.h_top;
+    } else if (a.kind == CS_ATM_LINEAR) {
+        if (a.lin_h1 > a.h_obs && a.lin_h1 < h) cuts[nc++] = a.lin_h1;
+    } else if (a.kind == CS_ATM_TABLE) {
+        for (int k = 1; k < a.n_nodes; ++k)
+            if (a.node_h[k] > a.h_obs && a.node_h[k] < h) cuts[nc++] = a.node_h[k];
+    }
+    cuts[nc++] = h;
+    double sI = 0.0, sX = 0.0, sA = 0.0;
+    for (int piece = 0; piece + 1 < nc; ++piece) {
+        const double lo = cuts[piece], hi = cuts[piece + 1];
+        const int nsub = (int)ceil((hi - lo) / kSubMax);
+        const double step = (hi - lo) / nsub;
+        for (int sub = 0; sub < nsub; ++sub) {
+            const double mid = lo + (sub + 0.5) * step, half = 0.5 * step;
+            for (int g = 0; g < kGL; ++g) {
+                const double y = mid + half * c_gl_x[g], wt = half * c_gl_w[g];
+                double d, rho;
+                delta_rho(a, y, false, &d, &rho);
+                sI += wt * d;
+                sX += wt * 100.0 * rho;
+                sA += wt * exp(-y / a.H_A);
+            }
+        }
+    }
+    out[i] = Fields4{sI, de, sX, sA};
 }
 
 // One thread per sample: the exact FP64 fields at (h_e, theta0).
@@ -446,6 +489,7 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
     auto fail = [&](const char* where) {
         set_last_error(where, e);
         cudaFree(dF); cudaFree(dFb); cudaFree(dslot); cudaFree(drows); cudaFree(h->d_tab); cudaFree(h->d_nodes);
+        cudaFree(h->d_params);
         delete h;
         return CS_ERR_CUDA;
     };
@@ -469,11 +513,21 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail("table build");
     cudaFree(dF); cudaFree(dFb); cudaFree(dslot); cudaFree(drows);
     p.tv.tab = h->d_tab;
+    if ((e = cudaMalloc(&h->d_params, sizeof(AtmParams))) != cudaSuccess) return fail("parameters");
+    p.self = h->d_params;
+    if ((e = cudaMemcpy(h->d_params, &p, sizeof(AtmParams), cudaMemcpyHostToDevice)) != cudaSuccess) return fail("parameters");
     *out = h;
     return CS_OK;
 }
 
 namespace cs {
+cs_status column_fields(const cs_atmosphere* atm, const double* d_h, size_t n, Fields4* d_out, cudaStream_t stream) {
+    if (n == 0) return CS_OK;
+    column_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(atm->f64, d_h, n, d_out);
+    CS_CUDA_TRY(cudaGetLastError());
+    return CS_OK;
+}
+
 cs_status exact_fields(const cs_atmosphere* atm, const double2* d_in, size_t n, Fields4* d_out, cudaStream_t stream) {
     if (n == 0) return CS_OK;
     exact_fields_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(atm->f64, d_in, n, d_out);
@@ -486,6 +540,7 @@ extern "C" void cs_atmosphere_destroy(cs_atmosphere* atm) {
     if (!atm) return;
     cudaFree(atm->d_tab);
     cudaFree(atm->d_nodes);
+    cudaFree(atm->d_params);
     delete atm;
 }
 

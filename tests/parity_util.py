@@ -26,11 +26,15 @@ def _key(seg, k, i):
     return (seg << np.uint64(32)) | (k << np.uint64(16)) | i
 
 
-def compare(gpu, orc, bunch=1, shower_of_seg=None, pos_rel=POS_REL, t_rel=T_REL, check_hist=True, pos_abs=0.0):
+def position(rec):
+    """Ground position of GPU records in FP64: the float-float pair summed."""
+    return (rec["x"].astype(np.float64) + rec["x_lo"].astype(np.float64),
+            rec["y"].astype(np.float64) + rec["y_lo"].astype(np.float64))
+
+
+def compare(gpu, orc, bunch=1, shower_of_seg=None, pos_rel=POS_REL, t_rel=T_REL, check_hist=True):
     """Asserts parity; returns summary statistics.  Positions agree to pos_rel
-    times max(1 m, the horizontal displacement from the emission point), or to
-    pos_abs [m] where the FP32 resolution of far-out frame coordinates is the
-    floor (isotropic emission on the spherical shell)."""
+    times max(1 m, the horizontal displacement from the emission point)."""
     g = g_all = gpu["records"]
     assert gpu["n_records"] == len(g), "GPU record capacity exceeded"
     o_all = orc["records"]
@@ -68,8 +72,9 @@ def compare(gpu, orc, bunch=1, shower_of_seg=None, pos_rel=POS_REL, t_rel=T_REL,
     # continuous values for bunches that were propagated to the ground on both sides
     prop = same_status & np.isin(O["status"], [oracle.ST_LANDED, oracle.ST_ABSORBED]) & ((fl & oracle.FL_LAYER) == 0)
     disp = np.maximum(1.0, np.hypot(O["x"] - O["ex"], O["y"] - O["ey"]))
-    ex = np.maximum(np.abs(G["x"].astype(np.float64) - O["x"]) - pos_abs, 0.0) / disp
-    ey = np.maximum(np.abs(G["y"].astype(np.float64) - O["y"]) - pos_abs, 0.0) / disp
+    gx, gy = position(G)
+    ex = np.abs(gx - O["x"]) / disp
+    ey = np.abs(gy - O["y"]) / disp
     et = np.abs(G["dt_ns"].astype(np.float64) * 1e-9 - O["dt"]) / np.maximum(O["dt"], 1e-12)
     el = np.abs(G["lambda_nm"].astype(np.float64) * 1e-9 - O["lam"]) / O["lam"]
     max_pos = float(max(ex[prop].max(initial=0.0), ey[prop].max(initial=0.0)))
@@ -77,7 +82,7 @@ def compare(gpu, orc, bunch=1, shower_of_seg=None, pos_rel=POS_REL, t_rel=T_REL,
     assert max_pos <= pos_rel, "position error %.3g > %.3g" % (max_pos, pos_rel)
     assert max_t <= t_rel, "time error %.3g > %.3g" % (max_t, t_rel)
     assert float(el.max(initial=0.0)) <= LAMBDA_REL
-    abs_pos = np.maximum(np.abs(G["x"].astype(np.float64) - O["x"]), np.abs(G["y"].astype(np.float64) - O["y"]))
+    abs_pos = np.maximum(np.abs(gx - O["x"]), np.abs(gy - O["y"]))
 
     landed = same_status & (O["status"] == oracle.ST_LANDED)
     bin_bad = landed & (G["bin"] != O["bin"]) & ((fl & (oracle.FL_HIST_EDGE | oracle.FL_LAYER)) == 0)
@@ -85,7 +90,7 @@ def compare(gpu, orc, bunch=1, shower_of_seg=None, pos_rel=POS_REL, t_rel=T_REL,
     tel_bad = landed & (G["tel"] != O["tel"]) & ((fl & (oracle.FL_TEL_EDGE | oracle.FL_LAYER)) == 0)
     assert not tel_bad.any(), "telescope mismatch outside the edge band: %r / %r" % (G[tel_bad][:3], O[tel_bad][:3])
     # camera pixels (-1 on both sides without optics); rim and pixel edges carry the telescope flag
-    pix_bad = landed & (G["pix"] != O["pix"]) & ((fl & (oracle.FL_TEL_EDGE | oracle.FL_LAYER)) == 0)
+    pix_bad = landed & (G["pix"] != O["pix"]) & ((fl & (oracle.FL_TEL_EDGE | oracle.FL_LAYER | oracle.FL_OPTICS)) == 0)
     assert not pix_bad.any(), "camera pixel mismatch outside the edge band: %r / %r" % (G[pix_bad][:3], O[pix_bad][:3])
 
     # aggregates equal the records they summarise (the GPU's counts are its records')

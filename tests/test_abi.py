@@ -59,9 +59,9 @@ int main(void) {
         a, b = subprocess.check_output([exe], text=True).strip().split("\n")
     sizes = [int(x) for x in a.split()]
     offs = [int(x) for x in b.split()]
-    assert sizes == [64, 48, C.sizeof(B.cs_atmosphere_desc), C.sizeof(B.cs_detector_desc), C.sizeof(B.cs_output),
+    assert sizes == [64, 56, C.sizeof(B.cs_atmosphere_desc), C.sizeof(B.cs_detector_desc), C.sizeof(B.cs_output),
                      C.sizeof(B.cs_opts)]
-    assert B.SEGMENT_DTYPE.itemsize == 64 and B.RECORD_DTYPE.itemsize == 48
+    assert B.SEGMENT_DTYPE.itemsize == 64 and B.RECORD_DTYPE.itemsize == 56
     assert offs == [B.cs_atmosphere_desc.table_dh.offset, B.cs_detector_desc.tel_xyzr.offset,
                     B.cs_output.record_count.offset, B.cs_opts.blocks_per_sm.offset]
 

@@ -32,10 +32,11 @@ def _tel():
 
 
 def _camera_close(g, o, bunch, nonempty=True):
-    """GPU and oracle images differ at most by the bunches whose pixel or
-    telescope decision lies in the oracle's edge band."""
+    """GPU and oracle images differ at most by the bunches whose pixel,
+    telescope or optics survival decision lies in the oracle's edge band."""
     rec = o["records"]
-    flagged = (rec["status"] == oracle.ST_LANDED) & (rec["tel"] >= 0) & ((rec["flags"] & oracle.FL_TEL_EDGE) != 0)
+    flagged = ((rec["status"] == oracle.ST_LANDED) & (rec["tel"] >= 0) &
+               ((rec["flags"] & (oracle.FL_TEL_EDGE | oracle.FL_OPTICS)) != 0))
     diff = np.abs(g["camera"].astype(np.int64) - o["camera"].astype(np.int64)).sum()
     assert diff <= 2 * bunch * int(flagged.sum()), (diff, int(flagged.sum()))
     assert o["camera"].sum() > 0 or not nonempty
@@ -128,3 +129,41 @@ def test_missing_camera_output_and_small_spheres_are_rejected():
         B.Detector(tel=small, optics=OPT)
     with pytest.raises(RuntimeError):
         B.Detector(tel=tel, optics=dict(OPT, focal_f=0.0))
+
+
+# mirror reflectivity and camera efficiency (a synthetic stand-in for a coated
+# mirror and a photomultiplier camera)
+EFF = dict(lambda_nm=[300.0, 350.0, 420.0, 500.0, 600.0],
+           mirror=[0.80, 0.86, 0.90, 0.89, 0.87],
+           camera=[0.18, 0.26, 0.24, 0.15, 0.05])
+
+
+@pytest.mark.parametrize("spherical", [False, True])
+def test_camera_absorption_parity(spherical):
+    """Absorption in the optics (Sec. 6.4): the camera keeps each photon with
+    probability R(lambda) eps(lambda) by its own keyed draw; pixels photon by
+    photon against the oracle, images equal to the records, and every kept
+    photon a photon of the lossless run's image."""
+    # on the sphere the camera is coarser (5 x 5 pixels): ground points carry FP32 ulps of ~4 mm
+    opt = dict(OPT, efficiency=EFF, cam_n=5 if spherical else 41)
+    free_opt = dict(OPT, cam_n=opt["cam_n"])
+    if spherical:
+        segs = synth.shower_segments(20000, 20.0, 30.0, 1e13, seed=8)
+        atm = B.Atmosphere(layered=synth.US_STANDARD, refraction=True, transmission=True, spherical=True)
+    else:
+        segs = synth.shower_segments(20000, 20.0, 30.0, 1e12, seed=7)
+        atm = B.Atmosphere(layered=synth.US_STANDARD, refraction=True, transmission=True)
+    tel = _tel()
+    det = B.Detector(tel=tel, optics=opt, spherical=spherical)
+    free_det = B.Detector(tel=tel, optics=free_opt, spherical=spherical)
+    g = B.propagate_host(segs, atm, det, seed=3, bunch=1, records=True)
+    free = B.propagate_host(segs, atm, free_det, seed=3, bunch=1, records=True)
+    bands = dict(band_pos=0.03) if spherical else None
+    o = oracle.propagate(segs, ORC_ATM, tel=tel, bunch=1, refraction=True, transmission=True, seed=3, optics=opt,
+                         spherical=spherical, bands=bands)
+    st = PU.compare(g, o, bunch=1)
+    assert st["pix_hits"] > 100, st
+    _camera_close(g, o, 1)
+    assert (g["camera"] <= free["camera"]).all()
+    kept, seen = g["camera"].sum(), free["camera"].sum()
+    assert 0.05 * seen < kept < 0.4 * seen, (kept, seen)

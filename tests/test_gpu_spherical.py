@@ -155,7 +155,7 @@ def test_inclined_full_size_streamed_sampled():
     PU.check_conservation(c)
     nrec = int(outs.record_count.item())
     assert nrec <= cap and int(c[0]) == 10 * nrec
-    recs = outs.records[: nrec * 48].view(torch.int64).view(nrec, 6)
+    recs = outs.records[: nrec * B.RECORD_DTYPE.itemsize].view(torch.int64).view(nrec, B.RECORD_DTYPE.itemsize // 8)
     rng = np.random.default_rng(21)
     sample = np.sort(rng.choice(2 * chunk, 150, replace=False))
     gids = torch.from_numpy((sample + 3 * chunk).astype(np.int64)).cuda()
@@ -191,7 +191,8 @@ def test_spherical_surrogate_against_exact_tracer():
     atm = _atm(True, True)
     sur = B.Surrogate(atm)
     s = sur.stats
-    assert s["p99"][0] <= 0.01 and s["p99"][1] <= 0.1e-9 and s["p99"][2] <= 1e-3, s
+    for k, bar in enumerate((0.01, 0.1e-9, 1e-3)):
+        assert s["p99"][k] <= bar and s["max"][k] <= bar, s
     segs = synth.shower_segments(1500, 60.0, 30.0, 1e13, seed=21)
     det = B.Detector(hist=HIST, tel=_tel(), spherical=True)
     ex = B.propagate_host(segs, atm, det, seed=2, bunch=5, records=True)
@@ -202,10 +203,40 @@ def test_spherical_surrogate_against_exact_tracer():
     assert np.array_equal(np.sort(ke), np.sort(ks))
     both = (e["status"] == 0) & (g["status"] == 0)
     assert both.sum() > 2000
-    dpos = np.hypot(e["x"][both] - g["x"][both], e["y"][both] - g["y"][both])
+    ex_, ey_ = PU.position(e[both])
+    gx_, gy_ = PU.position(g[both])
+    dpos = np.hypot(ex_ - gx_, ey_ - gy_)
     dt = np.abs(e["dt_ns"][both] - g["dt_ns"][both]) * 1e-9
     # the network's bars plus the FP32 resolution of ~50 km paths
-    assert np.percentile(dpos, 99) <= 1.42 * 0.01 + BAND_POS and dpos.max() <= 1.42 * 0.06 + BAND_POS
-    assert np.percentile(dt, 99) <= 0.1e-9 + 1e-5 * 2e-4 and dt.max() <= 0.4e-9 + 1e-5 * 2e-4
+    assert dpos.max() <= 0.01 + BAND_POS
+    assert dt.max() <= 0.1e-9 + 1e-5 * 2e-4
     assert (e["status"] != g["status"]).sum() <= 0.01 * len(e)
     sur.close()
+
+
+@pytest.mark.parametrize("refr", [True, False])
+def test_spherical_beyond_the_tables_and_past_the_ground(refr):
+    """Near-horizontal photons on the spherical shell: beyond the tables'
+    zenith they take the exact Bouguer path integrated per photon; those
+    whose path passes over the ground sphere are missed on both sides."""
+    rng = np.random.default_rng(21)
+    n = 500
+    s = synth._empty(n)
+    th = np.radians(rng.uniform(80.0, 89.6, n))
+    az = rng.uniform(0.0, 2 * np.pi, n)
+    s["z0"] = rng.uniform(2100.0, 9000.0, n)
+    s["x0"] = rng.uniform(-3000.0, 3000.0, n)
+    s["y0"] = rng.uniform(-3000.0, 3000.0, n)
+    s["ux"] = (np.sin(th) * np.cos(az)).astype(np.float32)
+    s["uy"] = (np.sin(th) * np.sin(az)).astype(np.float32)
+    s["uz"] = (-np.cos(th)).astype(np.float32)
+    s["length"][:] = np.float32(2.0)
+    s["inv_gamma2"][:] = np.float32(1e-8)
+    s["charge"][:] = 1.0
+    g, o = _run_both(s, refr, True, 2, tel=_tel(), seed=8)
+    st = PU.compare(g, o, bunch=2)
+    rec = o["records"]
+    assert (rec["status"] == oracle.ST_NO_GROUND).sum() > 200
+    assert ((rec["status"] == oracle.ST_LANDED) & (np.degrees(rec["theta0"]) > 76.0)).sum() > 2000
+    assert st["matched"] > 5000
+    PU.check_conservation(g["counters"])

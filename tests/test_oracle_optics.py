@@ -128,3 +128,62 @@ def test_camera_points_match_an_independent_ray_march():
         ix, iy = (int(math.floor((v + OPT["camera_r"]) / (2 * OPT["camera_r"]) * n)) for v in ref)
         assert pix == min(max(iy, 0), n - 1) * n + min(max(ix, 0), n - 1)
     assert hits > 150
+
+
+# ---- absorption in the optics (Sec. 6.4): mirror reflectivity x camera efficiency ----
+EFF = dict(lambda_nm=[300.0, 350.0, 420.0, 500.0, 600.0],
+           mirror=[0.80, 0.86, 0.90, 0.89, 0.87],
+           camera=[0.18, 0.26, 0.24, 0.15, 0.05])
+
+
+def _curve(x, y, v):
+    return np.interp(v, x, y)   # linear between the nodes, constant beyond the ends
+
+
+def test_optics_survival_is_the_keyed_draw_against_reflectivity_times_efficiency():
+    """Brute force per photon: the camera keeps a photon iff the Philox word x
+    of counter (segment, sub-step, bunch | 2^30), as a 24-bit uniform, lies
+    below R(lambda) eps(lambda); the surviving photons are exactly those of
+    the run without absorption that pass this test."""
+    segs = synth.shower_segments(1500, 20.0, 30.0, 1e12, seed=4)
+    tel = synth.grid_telescopes(nx=4, ny=4, pitch=60.0)
+    atm = oracle.make_atm(oracle.ATM_LAYERED, layered=synth.US_STANDARD)
+    kw = dict(tel=tel, bunch=1, refraction=True, transmission=True, seed=1)
+    free = oracle.propagate(segs, atm, optics=OPT, **kw)["records"]
+    lossy = oracle.propagate(segs, atm, optics=dict(OPT, efficiency=EFF), **kw)["records"]
+    assert np.array_equal(free["seg"], lossy["seg"]) and np.array_equal(free["tel"], lossy["tel"])
+    hit = free["pix"] >= 0
+    assert hit.sum() > 100
+    seen = 0
+    for j in np.nonzero(hit)[0]:
+        r = free[j]
+        word = oracle.philox([int(r["seg"]) & 0xFFFFFFFF, int(r["seg"]) >> 32, int(r["k"]), int(r["i"]) | 0x40000000],
+                             (1, 0))[0]
+        u = (word >> 8) * 2.0 ** -24
+        lnm = r["lam"] * 1e9
+        P = _curve(EFF["lambda_nm"], EFF["mirror"], lnm) * _curve(EFF["lambda_nm"], EFF["camera"], lnm)
+        assert lossy["pix"][j] == (r["pix"] if u < P else -1)
+        seen += 1
+    assert seen == hit.sum()
+    assert (lossy["pix"][~hit] == -1).all()
+
+
+def test_optics_survival_fraction_matches_the_curves():
+    """Over many camera photons the surviving fraction equals the mean of
+    R(lambda) eps(lambda) over their wavelengths (binomial 5 sigma); with flat
+    curves it is the product of the two constants."""
+    segs = synth.shower_segments(4000, 20.0, 30.0, 1e12, seed=6)
+    tel = synth.grid_telescopes(nx=4, ny=4, pitch=60.0)
+    atm = oracle.make_atm(oracle.ATM_LAYERED, layered=synth.US_STANDARD)
+    kw = dict(tel=tel, bunch=1, refraction=True, transmission=False, seed=2)
+    free = oracle.propagate(segs, atm, optics=OPT, **kw)["records"]
+    flat = dict(lambda_nm=[400.0], mirror=[0.9], camera=[0.25])
+    for eff in (EFF, flat):
+        lossy = oracle.propagate(segs, atm, optics=dict(OPT, efficiency=eff), **kw)["records"]
+        hit = free["pix"] >= 0
+        lnm = free["lam"][hit] * 1e9
+        P = _curve(eff["lambda_nm"], eff["mirror"], lnm) * _curve(eff["lambda_nm"], eff["camera"], lnm)
+        kept = int((lossy["pix"][hit] >= 0).sum())
+        assert abs(kept - P.sum()) < 5 * math.sqrt((P * (1 - P)).sum()), (kept, P.sum())
+        if eff is flat:
+            assert np.allclose(P, 0.225)

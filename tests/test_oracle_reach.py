@@ -61,20 +61,33 @@ def test_substep_count_is_the_fp64_ceiling():
             assert np.array_equal(ks, np.arange(K)), (i, K, ks)
 
 
-def test_count_on_a_rounding_edge_flags_the_segment():
-    """L = 0.3 (as FP32, 0.300000012) over s_max = 0.1 is 3.0000001 in FP64:
-    K = 4 here, while an FP32 quotient rounds to 3.  The segment is flagged."""
+def test_count_is_the_exact_ceiling_and_near_ties_are_flagged():
+    """K is the exact ceiling of L / s_max for the stored numbers.  L = 0.3
+    (as FP32, 0.300000012) over s_max = 0.1 is 3.0000001: K = 4.  L = 1 over
+    s_max = 1/3 (the double 0.333...3148) is 3.0000000000000002 in exact
+    arithmetic, so K = 4 although the FP64 product 3 s_max rounds to 1: a tie
+    at the 1e-16 level, flagged.  Whole multiples (12 m over 1 m) are exact
+    and not flagged."""
     s = _tilted(3, 9000.0, 0.0, seed=2, length=0.3)
-    s["length"][1] = np.float32(0.25)
-    s["length"][2] = np.float32(0.5)   # 5.0 exactly: also a whole number of sub-steps
-    r = oracle.propagate(s, ATM, s_max=0.1, bunch=1)
-    allr = r["records"]
-    flagged = allr[(allr["status"] == oracle.ST_SUBSTEP_FLAG) & ((allr["flags"] & oracle.FL_SEGMENT) != 0)]
-    assert sorted(flagged["seg"].tolist()) == [0, 2]
-    rec = _real(allr)
-    assert np.all((rec["flags"][rec["seg"] != 1] & oracle.FL_SEGMENT) != 0)
-    assert np.all((rec["flags"][rec["seg"] == 1] & oracle.FL_SEGMENT) == 0)
-    assert rec["k"][rec["seg"] == 0].max(initial=0) <= 3 and math.ceil(float(np.float32(0.3)) / 0.1) == 4
+    s["length"][1] = np.float32(1.0)
+    s["length"][2] = np.float32(12.0)
+    from fractions import Fraction
+    for s_max in (0.1, 1.0 / 3.0, 1.0):
+        r = oracle.propagate(s, ATM, s_max=s_max, bunch=1)
+        allr = r["records"]
+        rec = _real(allr)
+        flagged = set(allr["seg"][(allr["status"] == oracle.ST_SUBSTEP_FLAG) &
+                                  ((allr["flags"] & oracle.FL_SEGMENT) != 0)].tolist())
+        for i in range(3):
+            L = Fraction(float(s["length"][i]))
+            q = L / Fraction(s_max)                     # exact rational quotient
+            K = max(1, -((-q.numerator) // q.denominator))
+            ks = np.unique(rec["k"][rec["seg"] == i])
+            assert ks.max() == K - 1 and len(ks) == K, (s_max, i, K, ks)
+            tie = q != round(q) and abs(q - round(q)) < Fraction(1, 10**13) * q
+            assert (i in flagged) == tie, (s_max, i)
+        if s_max == 1.0 / 3.0:
+            assert flagged == {1, 2}   # 12 m is 36 sub-steps up to a tie too
 
 
 # ------------------------------------------------- steep planar photons -----

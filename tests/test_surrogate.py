@@ -89,23 +89,64 @@ def test_inference_kernel_matches_oracle_forward(B, trained):
     mu = rng.uniform(norm[14], 1.0, n)
     il = rng.uniform(1 / 600.0, 1 / 300.0, n)
     raw = np.stack([dz, mu, il], 1)
-    got = sur.eval(raw)
+    got = sur.eval(raw, network_only=True)
     hc = np.exp(-dz / sur.cfg.height_scale) if sur.cfg.height_scale > 0 else dz
     xn = np.stack([hc, mu, il], 1) * norm[0:3] + norm[3:6]
     y = oracle.mlp_forward(flat, xn)
     want = y * norm[6:9] + norm[9:12]
-    want[:, 2] = np.minimum(np.exp(want[:, 2]), 1.0)   # the network's third output is ln T
     # split BF16 activations: the kernel reproduces the FP64 forward of its own weights
-    scale = np.stack([np.full(n, norm[6]), np.full(n, norm[7]), norm[8] * want[:, 2]], 1)
-    err = np.abs(got - want) / scale
+    err = np.abs(got - want) / norm[6:9]
     assert err.max() < 2e-4, err.max(axis=0)
 
 
+def _column(h, h_obs=2000.0):
+    """int (n - 1) dh over [h_obs, h] by scipy's quadrature of the oracle's n(h)."""
+    from scipy import integrate
+    edges = [h_obs] + [b for b in (4000.0, 10000.0, 40000.0, 100000.0) if h_obs < b < h] + [h]
+    return sum(integrate.quad(lambda x: oracle.atm_delta(ORC_ATM, x), a, b, epsabs=0, epsrel=1e-11)[0]
+               for a, b in zip(edges, edges[1:]))
+
+
+def test_first_order_baseline_is_the_expansion_in_n_minus_1(B, trained):
+    """What inference adds to the network: the exact path expanded to first
+    order in n - 1, from vertical integrals computed here independently (scipy
+    quadrature of the oracle's n(h), the oracle's column depth, the aerosol
+    closed form); and that expansion is already within a few per mille of the
+    exact fields (pinned against the oracle's quadrature)."""
+    atm, sur = trained
+    rng = np.random.default_rng(3)
+    pts = []
+    while len(pts) < 60:
+        h = rng.uniform(2000.0, 30000.0)
+        if abs(h - 4000.0) >= 500.0 and abs(h - 10000.0) >= 500.0:
+            pts.append((h, math.radians(rng.uniform(0.0, 60.0)), rng.uniform(300e-9, 600e-9)))
+    raw = np.array([(h - 2000.0, math.cos(th), 1e-9 / lam) for h, th, lam in pts])
+    full = sur.eval(raw).astype(np.float64)
+    net = sur.eval(raw, network_only=True).astype(np.float64)
+    for (h, th, lam), f, r in zip(pts, full, net):
+        I, de, H, mu = _column(h), oracle.atm_delta(ORC_ATM, h), h - 2000.0, math.cos(th)
+        bR = de * H - I
+        bt = 2 * I - de * H + (de * H - I) / mu**2
+        Xv = oracle.column(ORC_ATM, 2000.0, h)
+        Av = 1200.0 * (math.exp(-2000.0 / 1200.0) - math.exp(-h / 1200.0))
+        blnT = -(Xv / (2974.0 * (lam / 400e-9) ** 4) + 0.05 * (lam / 350e-9) ** -1.3 * Av / 1200.0) / mu
+        assert abs((f[0] - r[0]) - bR) <= 2e-6 * max(1.0, abs(de * H)), (h, f[0] - r[0], bR)
+        assert abs((f[1] - r[1]) - bt) <= 2e-6 * max(1.0, abs(de * H)) / mu**2, (h, f[1] - r[1], bt)
+        if f[2] < 1.0:
+            assert abs((math.log(f[2]) - r[2]) - blnT) <= 2e-6 * max(1.0, abs(blnT)), (h, blnT)
+        # the expansion against the exact path (oracle quadrature): within 2e-3 in G_R and G_t
+        q = oracle.refract_quad(ORC_ATM, 2000.0, h, th)
+        if th > 1e-3:
+            GR = (q[0] - H * math.tan(th)) * mu**3 / math.sin(th)
+            assert abs(GR - bR) <= 2e-3, (h, th, GR, bR)
+        Gt = (q[1] * CL - H / mu) * mu
+        assert abs(Gt - bt) <= 5e-3, (h, th, Gt, bt)
+
+
 # the stated error of the trained network (held-out 2^16 samples against the
-# FP64 exact path): the 99th percentile meets the 1 cm / 0.1 ns / 1e-3 bar;
-# the maximum, set by the BF16 weight resolution, is stated separately
+# FP64 exact path): the 99th percentile and the maximum both meet the
+# 1 cm / 0.1 ns / 1e-3 bar
 BAR = (0.01, 0.1e-9, 1e-3)
-MAX_STATED = (0.06, 0.4e-9, 6e-3)
 
 
 def test_trained_network_error_bar(B, trained):
@@ -113,7 +154,7 @@ def test_trained_network_error_bar(B, trained):
     s = sur.stats
     for k in range(3):
         assert s["p99"][k] <= BAR[k], s
-        assert s["max"][k] <= MAX_STATED[k], s
+        assert s["max"][k] <= BAR[k], s
 
 
 def test_trained_network_against_oracle_quadrature(B, trained):
@@ -140,8 +181,17 @@ def test_trained_network_against_oracle_quadrature(B, trained):
                      abs(g[2] - T)))
     errs = np.array(errs)
     for k in range(3):
-        assert np.mean(errs[:, k] <= BAR[k]) >= 0.97, k
-        assert errs[:, k].max() <= MAX_STATED[k], k
+        assert errs[:, k].max() <= BAR[k], (k, errs[:, k].max())
+    # what the network adds to the first-order expansion it is trained on top of:
+    # the expansion alone (the network's part removed) errs by several times more
+    net = sur.eval(raw, network_only=True)
+    base_err = []
+    for (h, th, lam), g, r in zip(pts, got, net):
+        q = oracle.refract_quad(ORC_ATM, 2000.0, h, th)
+        c, sn = math.cos(th), math.sin(th)
+        dR = q[0] - (h - 2000.0) * math.tan(th)
+        base_err.append(abs((g[0] - r[0]) * sn / c**3 - dR))
+    assert max(base_err) > 5 * errs[:, 0].max(), (max(base_err), errs[:, 0].max())
 
 
 def test_propagation_with_surrogate(B, trained):
@@ -161,10 +211,12 @@ def test_propagation_with_surrogate(B, trained):
     s = sg["records"][np.argsort(ks)]
     both = (e["status"] == 0) & (s["status"] == 0)
     assert both.sum() > 3000
-    dpos = np.hypot(e["x"][both] - s["x"][both], e["y"][both] - s["y"][both])
+    (ex_, ey_), (sx_, sy_) = PU.position(e[both]), PU.position(s[both])
+    dpos = np.hypot(ex_ - sx_, ey_ - sy_)
     dt = np.abs(e["dt_ns"][both] - s["dt_ns"][both]) * 1e-9
-    assert np.percentile(dpos, 99) <= 1.42 * BAR[0] and dpos.max() <= 1.42 * MAX_STATED[0]
-    assert np.percentile(dt, 99) <= BAR[1] + 1e-5 * 4e-5 and dt.max() <= MAX_STATED[1] + 1e-5 * 4e-5
+    # both propagate from the same FP32 origin; the tables' own interpolation error is < 1e-5 m
+    assert dpos.max() <= BAR[0]
+    assert dt.max() <= BAR[1] + 1e-5 * 4e-5
     # status flips only from the transmission test near threshold
     flips = (e["status"] != s["status"]).sum()
     assert flips <= 0.01 * len(e)
@@ -176,12 +228,13 @@ def test_propagation_with_surrogate(B, trained):
     common, i_s, i_o = np.intersect1d(ks[np.argsort(ks)], ko, return_indices=True)
     S, O = s[i_s], orec[i_o]
     m = S["status"] == 0
-    d = np.hypot(S["x"][m] - O["x"][m], S["y"][m] - O["y"][m])
+    sx_, sy_ = PU.position(S[m])
+    d = np.hypot(sx_ - O["x"][m], sy_ - O["y"][m])
     disp = np.maximum(1.0, np.hypot(O["x"][m] - O["ex"][m], O["y"][m] - O["ey"][m]))
     tol = 1e-5 * disp + 1e-4
-    assert np.mean(d <= 1.42 * BAR[0] + tol) >= 0.99 and np.all(d <= 1.42 * MAX_STATED[0] + tol)
+    assert np.all(d <= BAR[0] + tol)
     dto = np.abs(S["dt_ns"][m] * 1e-9 - O["dt"][m])
-    assert np.mean(dto <= BAR[1] + 1e-5 * O["dt"][m]) >= 0.99 and np.all(dto <= MAX_STATED[1] + 1e-5 * O["dt"][m])
+    assert np.all(dto <= BAR[1] + 1e-5 * O["dt"][m])
 
 
 def test_network_gain_over_propagation_without_it(B, trained):
@@ -203,11 +256,12 @@ def test_network_gain_over_propagation_without_it(B, trained):
     assert len(ex) == len(sg) == len(st)
     m = (ex["status"] == 0) & (sg["status"] == 0) & (st["status"] == 0)
     assert m.sum() > 3000
-    d_net = np.hypot(sg["x"][m] - ex["x"][m], sg["y"][m] - ex["y"][m])
-    d_line = np.hypot(st["x"][m] - ex["x"][m], st["y"][m] - ex["y"][m])
+    (gx_, gy_), (ex_, ey_), (lx_, ly_) = PU.position(sg[m]), PU.position(ex[m]), PU.position(st[m])
+    d_net = np.hypot(gx_ - ex_, gy_ - ey_)
+    d_line = np.hypot(lx_ - ex_, ly_ - ey_)
     t_net = np.abs(sg["dt_ns"][m] - ex["dt_ns"][m])
     t_line = np.abs(st["dt_ns"][m] - ex["dt_ns"][m])
-    assert np.percentile(d_net, 99) <= 1.42 * BAR[0]
+    assert d_net.max() <= BAR[0]
     assert np.percentile(t_net, 99) * 1e-9 <= BAR[1] + 4e-14 * 1e5
     assert np.median(d_line) > 10 * np.percentile(d_net, 99)
     assert np.median(t_line) > 10 * np.percentile(t_net, 99)
