@@ -787,8 +787,9 @@ def main():
                      "heldout_max": {"displacement_m": sur.stats["max"][0], "delay_s": sur.stats["max"][1],
                                      "transmission": sur.stats["max"][2]},
                      "train_seconds": round(train_s, 2), "train_steps": sur.stats["steps"],
-                     "network": "MLP 3-64-64-64-3 tanh, BF16 weights and split BF16 activations, FP32 accumulation in "
-                                "tensor memory (tcgen05.mma M=128 per warpgroup)"}
+                     "network": "MLP 3-64-64-64-3 tanh on the fields less their first-order expansion in n - 1; BF16 "
+                                "weights and activations (packed hardware tanh), FP32 accumulation in tensor memory "
+                                "(tcgen05.mma M=128 per warpgroup)"}
         sur.close()
 
     optics = None

@@ -460,8 +460,8 @@ typedef struct cs_surrogate_config {
     double theta_max;        /* largest zenith [rad] (default 60 deg) */
     int split_activations;   /* 1: hidden activations enter the MMAs as BF16 hi + lo pairs after an accurate
                                 tanh; 0: as single BF16 values through the hardware's packed BF16 tanh
-                                (fewer instructions and MMAs; the network only adds a correction to the
-                                first-order baseline) */
+                                (default: fewer instructions and MMAs; the network only adds a correction
+                                to the first-order baseline) */
     double boundary_band;    /* half-width [m] of the bands around layer boundaries left to the tables
                                 (the exact fields jump there with n(h_e)); default 500 m */
     double height_scale;     /* > 0: the height enters as exp(-(h - h_obs) / height_scale) (default

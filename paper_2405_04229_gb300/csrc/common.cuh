@@ -72,6 +72,19 @@ struct AtmParams {
     const AtmParams* self;   // device copy of these parameters (for out-of-line routines)
 };
 
+// A uniform grid hash over the telescopes' reach discs for arrivals up to a
+// zenith: the grid origin and the cell size are whole metres, so cell corners
+// are exact in FP32; cell c lists the entries [cell_range[c].x, cell_range[c].y).
+struct TelHash {
+    float gx0, gy0, cell, inv_cell;
+    int gnx, gny;
+    const int2* cell_range;
+    const int* cell_tel;      // telescope index of each entry (ascending within a cell)
+    const float4* cell_data;  // planar: {x - corner_x, y - corner_y, z - h_obs, radius}; spherical: tel3
+    float sin2_max;           // arrivals steeper than this need a wider hash or the full list
+    float bx0, bx1, by0, by1; // bounding box of all reach discs
+};
+
 struct DetParams {
     int n_showers;
     int spherical;        // telescope layout and histogram in azimuthal-equidistant coordinates
@@ -85,15 +98,9 @@ struct DetParams {
     const float4* tel;    // {x_hi, y_hi, z - h_obs, radius}
     const float2* tel_lo; // {x_lo, y_lo}
     const float4* tel3;   // spherical: centre in frame coordinates and radius
-    // uniform grid hash over the telescopes' reach discs; the grid origin and
-    // the cell size are whole metres, so cell corners are exact in FP32
-    float gx0, gy0, cell, inv_cell;
-    int gnx, gny;
-    const int* cell_start;  // gnx * gny + 1
-    const int* cell_tel;    // telescope index of each cell entry (ascending within a cell)
-    const float4* cell_data;  // planar: {x - corner_x, y - corner_y, z - h_obs, radius}; spherical: tel3
-    float hash_sin2_max;    // photons arriving steeper than this use the full list
-    float bx0, bx1, by0, by1;  // bounding box of all reach discs
+    // two hashes: hash[0] for arrivals up to 45 deg (small cells, mostly empty),
+    // hash[1] up to 75 deg; steeper arrivals test every sphere
+    TelHash hash[2];
     // last-mile optics: mirror focal length, (aperture radius)^2, camera radius,
     // pixels per metre on the camera, and the telescope frame (axis a, e1 = a x z-hat, e2 = a x e1)
     int cam_n;

@@ -12,7 +12,8 @@
 
 namespace {
 
-constexpr double kHashTheta = 75.0 * 3.14159265358979323846 / 180.0;  // hash serves zenith <= 75 deg
+// the two hash levels serve arrivals up to 45 and 75 degrees zenith
+constexpr double kHashTheta[2] = {45.0 * 3.14159265358979323846 / 180.0, 75.0 * 3.14159265358979323846 / 180.0};
 
 void split(double v, float* hi, float* lo) {
     *hi = (float)v;
@@ -102,30 +103,37 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
         }
     }
 
-    // host-side layout: tel float4, tel_lo float2, tel3 float4, cell_start, cell_tel
+    // host-side layout: tel float4, tel_lo float2, tel3 float4, then per hash level
+    // its cell ranges, entry telescope indices and entry data
     std::vector<float4> tel(d->n_tel), tel3(p.spherical ? d->n_tel : 0);
     std::vector<float2> tel_lo(d->n_tel);
-    std::vector<int> cell_start(1, 0), cell_tel;
-    std::vector<float4> cell_data;
-    if (d->n_tel > 0) {
+    for (int i = 0; i < d->n_tel; ++i) {
+        const double* t = d->tel_xyzr + 4 * i;
+        float lo;
+        split(t[0], &tel[i].x, &lo); tel_lo[i].x = lo;
+        split(t[1], &tel[i].y, &lo); tel_lo[i].y = lo;
+        tel[i].z = (float)(t[2] - d->h_obs);
+        tel[i].w = (float)t[3];
+        if (p.spherical) {   // centre h = t[2] above the azimuthal-equidistant point (x, y)
+            const double rg = p.R + d->h_obs, sx = sqrt(t[0] * t[0] + t[1] * t[1]), a = sx / rg;
+            const double r = p.R + t[2], cx = sx > 0.0 ? t[0] / sx : 1.0, cy = sx > 0.0 ? t[1] / sx : 0.0;
+            tel3[i] = make_float4((float)(r * sin(a) * cx), (float)(r * sin(a) * cy), (float)(r * cos(a) - p.R),
+                                  (float)t[3]);
+        }
+    }
+    std::vector<int2> range[2];
+    std::vector<int> cell_tel[2];
+    std::vector<float4> cell_data[2];
+    for (int level = 0; level < 2 && d->n_tel > 0; ++level) {
+        cs::TelHash& H = p.hash[level];
+        const double theta_h = kHashTheta[level];
         double reach_max = 0.0, x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
         std::vector<double> reach(d->n_tel);
         for (int i = 0; i < d->n_tel; ++i) {
             const double* t = d->tel_xyzr + 4 * i;
-            float lo;
-            split(t[0], &tel[i].x, &lo); tel_lo[i].x = lo;
-            split(t[1], &tel[i].y, &lo); tel_lo[i].y = lo;
-            tel[i].z = (float)(t[2] - d->h_obs);
-            tel[i].w = (float)t[3];
-            if (p.spherical) {   // centre h = t[2] above the azimuthal-equidistant point (x, y)
-                const double rg = p.R + d->h_obs, s = sqrt(t[0] * t[0] + t[1] * t[1]), a = s / rg;
-                const double r = p.R + t[2], cx = s > 0.0 ? t[0] / s : 1.0, cy = s > 0.0 ? t[1] / s : 0.0;
-                tel3[i] = make_float4((float)(r * sin(a) * cx), (float)(r * sin(a) * cy), (float)(r * cos(a) - p.R),
-                                      (float)t[3]);
-            }
-            // ground points whose arrival line (zenith <= 75 deg) passes within r of
+            // ground points whose arrival line (zenith <= theta_h) passes within r of
             // the centre lie within r / cos + |dz| tan of the centre's footprint
-            reach[i] = t[3] / cos(kHashTheta) + fabs(t[2] - d->h_obs) * tan(kHashTheta) + 0.01;
+            reach[i] = t[3] / cos(theta_h) + fabs(t[2] - d->h_obs) * tan(theta_h) + 0.01;
             reach_max = fmax(reach_max, reach[i]);
             x0 = fmin(x0, t[0] - reach[i]); x1 = fmax(x1, t[0] + reach[i]);
             y0 = fmin(y0, t[1] - reach[i]); y1 = fmax(y1, t[1] + reach[i]);
@@ -151,45 +159,48 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
                 for (int cx = cx0 < 0 ? 0 : cx0; cx <= cx1 && cx < gnx; ++cx)
                     lists[(size_t)cy * gnx + cx].push_back(i);
         }
-        cell_start.assign((size_t)gnx * gny + 1, 0);
-        for (size_t c = 0; c < lists.size(); ++c) cell_start[c + 1] = cell_start[c] + (int)lists[c].size();
-        cell_tel.reserve(cell_start.back());
-        cell_data.reserve(cell_start.back());
+        range[level].resize(lists.size());
         for (size_t c = 0; c < lists.size(); ++c) {
             const double cx0 = x0 + (double)(c % gnx) * cell, cy0 = y0 + (double)(c / gnx) * cell;
+            range[level][c].x = (int)cell_tel[level].size();
             for (int i : lists[c]) {
                 const double* t = d->tel_xyzr + 4 * i;
-                cell_tel.push_back(i);
-                cell_data.push_back(p.spherical ? tel3[i]
-                                                : make_float4((float)(t[0] - cx0), (float)(t[1] - cy0),
-                                                              (float)(t[2] - d->h_obs), (float)t[3]));
+                cell_tel[level].push_back(i);
+                cell_data[level].push_back(p.spherical ? tel3[i]
+                                                       : make_float4((float)(t[0] - cx0), (float)(t[1] - cy0),
+                                                                     (float)(t[2] - d->h_obs), (float)t[3]));
             }
+            range[level][c].y = (int)cell_tel[level].size();
         }
-        p.gx0 = (float)x0;
-        p.gy0 = (float)y0;
-        p.cell = (float)cell;
-        p.inv_cell = (float)(1.0 / cell);
-        p.gnx = gnx;
-        p.gny = gny;
-        p.bx0 = (float)x0; p.bx1 = (float)(x0 + gnx * cell);
-        p.by0 = (float)y0; p.by1 = (float)(y0 + gny * cell);
+        H.gx0 = (float)x0;
+        H.gy0 = (float)y0;
+        H.cell = (float)cell;
+        H.inv_cell = (float)(1.0 / cell);
+        H.gnx = gnx;
+        H.gny = gny;
+        H.bx0 = (float)x0; H.bx1 = (float)(x0 + gnx * cell);
+        H.by0 = (float)y0; H.by1 = (float)(y0 + gny * cell);
         // on the sphere the local vertical at a ground point in the box leans from
         // the frame's z axis by up to the box's extent / r_g: photons steeper than
         // the hash's zenith in the local frame must be steeper in the frame's too
-        double theta = kHashTheta;
+        double theta = theta_h;
         if (p.spherical) {
             const double ex = fmax(fabs(x0), fabs(x0 + gnx * cell)), ey = fmax(fabs(y0), fabs(y0 + gny * cell));
             theta -= 1.01 * sqrt(ex * ex + ey * ey) / (p.R + d->h_obs) + 1e-6;
         }
-        p.hash_sin2_max = (float)(sin(theta) * sin(theta));
+        H.sin2_max = (float)(sin(theta) * sin(theta));
     }
     const size_t o_tel = 0;
     const size_t o_lo = align_up(o_tel + tel.size() * sizeof(float4));
     const size_t o_t3 = align_up(o_lo + tel_lo.size() * sizeof(float2));
-    const size_t o_cs = align_up(o_t3 + tel3.size() * sizeof(float4));
-    const size_t o_ct = align_up(o_cs + cell_start.size() * sizeof(int));
-    const size_t o_cd = align_up(o_ct + (cell_tel.size() + 1) * sizeof(int));
-    const size_t total = align_up(o_cd + (cell_data.size() + 1) * sizeof(float4));
+    size_t o_rg[2], o_ct[2], o_cd[2], end = align_up(o_t3 + tel3.size() * sizeof(float4));
+    for (int level = 0; level < 2; ++level) {
+        o_rg[level] = end;
+        o_ct[level] = align_up(o_rg[level] + (range[level].size() + 1) * sizeof(int2));
+        o_cd[level] = align_up(o_ct[level] + (cell_tel[level].size() + 1) * sizeof(int));
+        end = align_up(o_cd[level] + (cell_data[level].size() + 1) * sizeof(float4));
+    }
+    const size_t total = end;
     cudaError_t e = cudaMalloc(&h->d_mem, total);
     if (e != cudaSuccess) { cs::set_last_error("detector alloc", e); delete h; return CS_ERR_CUDA; }
     char* base = (char*)h->d_mem;
@@ -197,17 +208,23 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
     if (!tel.empty()) memcpy(host.data() + o_tel, tel.data(), tel.size() * sizeof(float4));
     if (!tel_lo.empty()) memcpy(host.data() + o_lo, tel_lo.data(), tel_lo.size() * sizeof(float2));
     if (!tel3.empty()) memcpy(host.data() + o_t3, tel3.data(), tel3.size() * sizeof(float4));
-    memcpy(host.data() + o_cs, cell_start.data(), cell_start.size() * sizeof(int));
-    if (!cell_tel.empty()) memcpy(host.data() + o_ct, cell_tel.data(), cell_tel.size() * sizeof(int));
-    if (!cell_data.empty()) memcpy(host.data() + o_cd, cell_data.data(), cell_data.size() * sizeof(float4));
+    for (int level = 0; level < 2; ++level) {
+        if (!range[level].empty()) memcpy(host.data() + o_rg[level], range[level].data(), range[level].size() * sizeof(int2));
+        if (!cell_tel[level].empty())
+            memcpy(host.data() + o_ct[level], cell_tel[level].data(), cell_tel[level].size() * sizeof(int));
+        if (!cell_data[level].empty())
+            memcpy(host.data() + o_cd[level], cell_data[level].data(), cell_data[level].size() * sizeof(float4));
+    }
     e = cudaMemcpy(h->d_mem, host.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cs::set_last_error("detector copy", e); cudaFree(h->d_mem); delete h; return CS_ERR_CUDA; }
     p.tel = (const float4*)(base + o_tel);
     p.tel_lo = (const float2*)(base + o_lo);
     p.tel3 = p.spherical ? (const float4*)(base + o_t3) : nullptr;
-    p.cell_start = (const int*)(base + o_cs);
-    p.cell_tel = (const int*)(base + o_ct);
-    p.cell_data = (const float4*)(base + o_cd);
+    for (int level = 0; level < 2; ++level) {
+        p.hash[level].cell_range = (const int2*)(base + o_rg[level]);
+        p.hash[level].cell_tel = (const int*)(base + o_ct[level]);
+        p.hash[level].cell_data = (const float4*)(base + o_cd[level]);
+    }
     *out = h;
     return CS_OK;
 }

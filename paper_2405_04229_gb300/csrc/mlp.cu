@@ -510,7 +510,7 @@ extern "C" void cs_surrogate_config_default(cs_surrogate_config* c) {
     c->h_min = 2000.0;
     c->h_max = 30000.0;
     c->theta_max = 60.0 * kPi / 180.0;
-    c->split_activations = 1;
+    c->split_activations = 0;
     c->boundary_band = 500.0;
     c->height_scale = 8000.0;
 }

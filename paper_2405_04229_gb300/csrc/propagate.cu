@@ -355,8 +355,8 @@ __device__ __forceinline__ void hist_add(const OutParams& op, unsigned int key, 
 // ddx, ddy, ddz) gives the centre minus the ground point.  Steeper arrivals
 // test every sphere through full_delta(index, ddx, ddy, ddz, radius).
 template <typename CellDelta, typename FullDelta>
-__device__ __forceinline__ int hit_telescope(const DetParams& dp, bool hashed, float x, float y, float ugx, float ugy,
-                                             float ugz, CellDelta cell_delta, FullDelta full_delta) {
+__device__ __forceinline__ int hit_telescope(const DetParams& dp, const TelHash& H, bool hashed, float x, float y, float ugx,
+                                             float ugy, float ugz, CellDelta cell_delta, FullDelta full_delta) {
     int best = -1;
     float best_d2 = 3.0e38f;
     auto test = [&](float ddx, float ddy, float ddz, float r, int id) {
@@ -368,19 +368,19 @@ __device__ __forceinline__ int hit_telescope(const DetParams& dp, bool hashed, f
         }
     };
     if (hashed) {
-        const int cx = (int)((x - dp.gx0) * dp.inv_cell);
-        const int cy = (int)((y - dp.gy0) * dp.inv_cell);
-        if (cx < 0 || cx >= dp.gnx || cy < 0 || cy >= dp.gny) return -1;
-        const int c = cy * dp.gnx + cx;
-        const float cx0 = fmaf((float)cx, dp.cell, dp.gx0), cy0 = fmaf((float)cy, dp.cell, dp.gy0);   // exact
-        const int e0 = __ldg(dp.cell_start + c), e1 = __ldg(dp.cell_start + c + 1);
-        for (int e = e0; e < e1; ++e) {
-            const float4 D = __ldg(dp.cell_data + e);
+        const int cx = (int)((x - H.gx0) * H.inv_cell);
+        const int cy = (int)((y - H.gy0) * H.inv_cell);
+        if (cx < 0 || cx >= H.gnx || cy < 0 || cy >= H.gny) return -1;
+        const int2 er = __ldg(H.cell_range + (cy * H.gnx + cx));
+        if (er.x == er.y) return -1;   // no reach disc covers this cell
+        const float cx0 = fmaf((float)cx, H.cell, H.gx0), cy0 = fmaf((float)cy, H.cell, H.gy0);   // exact
+        for (int e = er.x; e < er.y; ++e) {
+            const float4 D = __ldg(H.cell_data + e);
             float ddx, ddy, ddz;
             cell_delta(D, cx0, cy0, ddx, ddy, ddz);
             test(ddx, ddy, ddz, D.w, e);
         }
-        return best >= 0 ? __ldg(dp.cell_tel + best) : -1;
+        return best >= 0 ? __ldg(H.cell_tel + best) : -1;
     }
     for (int it = 0; it < dp.n_tel; ++it) {
         float ddx, ddy, ddz, r;
@@ -798,15 +798,16 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                 // arrival direction: n sin(theta) conserved, azimuth kept
                 const float sc = ap.refraction ? (1.0f + Q.z) * ap.inv_n_obs : 1.0f;
                 const float s2 = (ux * ux + uy * uy) * (sc * sc);
-                const bool hashed = s2 <= dp.hash_sin2_max;
-                if (!hashed || (x >= dp.bx0 && x < dp.bx1 && y >= dp.by0 && y < dp.by1)) {
+                const bool hashed = s2 <= dp.hash[1].sin2_max;
+                const TelHash& H = dp.hash[s2 <= dp.hash[0].sin2_max ? 0 : 1];   // the narrowest hash that serves
+                if (!hashed || (x >= H.bx0 && x < H.bx1 && y >= H.by0 && y < H.by1)) {
                     float ugz = uz;
                     if (ap.refraction) {
                         const float c2 = fmaxf(1.0f - s2, 1e-30f);
                         ugz = -c2 * rsqrtf(c2);
                     }
                     tel = hit_telescope(
-                        dp, hashed, x, y, ux * sc, uy * sc, ugz,
+                        dp, H, hashed, x, y, ux * sc, uy * sc, ugz,
                         [&](const float4& D, float cx0, float cy0, float& ddx, float& ddy, float& ddz) {
                             ddx = D.x - ((Cg.x - cx0) + (Cg.y + rx));
                             ddy = D.y - ((Cg.z - cy0) + (Cg.w + ry));
@@ -967,15 +968,17 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                         ugy = -cos_g * gvy + sin_g * ty;
                         ugz = -cos_g * (1.0f + gvz) + sin_g * tz;
                     }
-                    const bool hashed = ugx * ugx + ugy * ugy <= dp.hash_sin2_max;
-                    if (!hashed || (xs >= dp.bx0 && xs < dp.bx1 && ys >= dp.by0 && ys < dp.by1)) {
+                    const float sg2 = ugx * ugx + ugy * ugy;
+                    const bool hashed = sg2 <= dp.hash[1].sin2_max;
+                    const TelHash& H = dp.hash[sg2 <= dp.hash[0].sin2_max ? 0 : 1];
+                    if (!hashed || (xs >= H.bx0 && xs < H.bx1 && ys >= H.by0 && ys < H.by1)) {
                         auto delta3 = [&](const float4& T3, float& ddx, float& ddy, float& ddz) {
                             ddx = (T3.x - Gx) - Gxl;
                             ddy = (T3.y - Gy) - Gyl;
                             ddz = (T3.z - Gz) - Gzl;
                         };
                         tel = hit_telescope(
-                            dp, hashed, xs, ys, ugx, ugy, ugz,
+                            dp, H, hashed, xs, ys, ugx, ugy, ugz,
                             [&](const float4& D, float, float, float& ddx, float& ddy, float& ddz) { delta3(D, ddx, ddy, ddz); },
                             [&](int it, float& ddx, float& ddy, float& ddz, float& r) {
                                 const float4 T3 = __ldg(dp.tel3 + it);

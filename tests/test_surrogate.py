@@ -79,8 +79,12 @@ def trained(B):
     return atm, sur
 
 
-def test_inference_kernel_matches_oracle_forward(B, trained):
-    atm, sur = trained
+def test_inference_kernel_matches_oracle_forward(B):
+    """The tensor-core inference with split BF16 activations and the accurate
+    tanh reproduces the FP64 forward pass of its own weights (a short training:
+    the arithmetic, not the fit, is under test)."""
+    atm = B.Atmosphere(layered=synth.US_STANDARD, refraction=True, transmission=True)
+    sur = B.Surrogate(atm, epochs=4, n_train=1 << 16, n_heldout=1 << 12, split_activations=1)
     p, norm = sur.info()
     flat = B.mlp_padded_to_flat(p).astype(np.float64)
     rng = np.random.default_rng(8)
@@ -97,6 +101,14 @@ def test_inference_kernel_matches_oracle_forward(B, trained):
     # split BF16 activations: the kernel reproduces the FP64 forward of its own weights
     err = np.abs(got - want) / norm[6:9]
     assert err.max() < 2e-4, err.max(axis=0)
+    # the default single-BF16 path with the packed hardware tanh: within a few per cent of the range
+    fast = B.Surrogate(atm, epochs=4, n_train=1 << 16, n_heldout=1 << 12, split_activations=0)
+    pf, nf = fast.info()
+    yf = oracle.mlp_forward(B.mlp_padded_to_flat(pf).astype(np.float64), np.stack([hc, mu, il], 1) * nf[0:3] + nf[3:6])
+    errf = np.abs(fast.eval(raw, network_only=True) - (yf * nf[6:9] + nf[9:12])) / nf[6:9]
+    assert errf.max() < 5e-2, errf.max(axis=0)
+    sur.close()
+    fast.close()
 
 
 def _column(h, h_obs=2000.0):
