@@ -65,7 +65,7 @@ class Config(C.Structure):
                 ("hist_dy", C.c_double), ("tel", C.POINTER(C.c_double)),
                 ("band_pos", C.c_double), ("band_count", C.c_double), ("band_T", C.c_double),
                 ("band_h", C.c_double), ("band_w", C.c_double), ("quad_rtol", C.c_double),
-                ("spherical", C.c_int), ("pad2", C.c_int), ("earth_radius", C.c_double),
+                ("spherical", C.c_int), ("cylindrical", C.c_int), ("earth_radius", C.c_double),
                 ("lv1_metric", C.c_int), ("pad3", C.c_int), ("lv1_a", C.c_double), ("lv1_b", C.c_double),
                 ("lv1_centre", C.c_double * 3), ("lv1_radius", C.c_double), ("band_lv1", C.c_double),
                 ("mirror_d", C.c_double), ("focal_f", C.c_double), ("camera_r", C.c_double),
@@ -120,6 +120,10 @@ def lib():
             L.orc_snell_path_sph.argtypes = [C.POINTER(Atm), d, d, d, d, d, d, dp]
             L.orc_sph_path.argtypes = [C.POINTER(Atm), d, d, d, d, d, C.c_int, d, dp]
             L.orc_ae_inverse.argtypes = [d, d, d, d, d, dp]
+            L.orc_cyl_path.argtypes = [C.POINTER(Atm), d, d, d, d, d, d, C.c_int, d, dp]
+            L.orc_snell_path_cyl.argtypes = [C.POINTER(Atm), d, d, d, d, d, d, d, d, C.c_int, dp]
+            L.orc_cyl_reach_margin.argtypes = [C.POINTER(Atm), C.c_int, d, d, d, d, d]
+            L.orc_cyl_reach_margin.restype = d
             L.orc_propagate.argtypes = [C.c_void_p, C.c_size_t, C.POINTER(Atm), C.POINTER(Config),
                                         C.POINTER(Output)]
             L.orc_propagate.restype = C.c_int
@@ -252,6 +256,26 @@ def sph_path(atm, h_obs, h_e, psi0, refraction=True, R=EARTH_RADIUS, H_A=1200.0,
     return np.array(out[:])
 
 
+def cyl_path(atm, h_obs, h_e, u_a, u_chi, refraction=True, R=EARTH_RADIUS, H_A=1200.0, rtol=1e-12):
+    """{chi swept, t_path, axial drift, X_slant, A_slant} in the cylindrical atmosphere
+    for a photon at altitude h_e with direction components u_a (axial) and u_chi >= 0
+    (transverse tangent)."""
+    out = (C.c_double * 5)()
+    lib().orc_cyl_path(C.byref(atm), R, h_obs, h_e, u_a, u_chi, H_A, int(refraction), rtol, out)
+    return np.array(out[:])
+
+
+def snell_path_cyl(atm, h_obs, h_e, u_chi, u_rho, u_a, dh, refraction=True, R=EARTH_RADIUS, H_A=1200.0):
+    """The three-dimensional Snell stepper through the cylindrical atmosphere."""
+    out = (C.c_double * 5)()
+    lib().orc_snell_path_cyl(C.byref(atm), R, h_obs, h_e, u_chi, u_rho, u_a, dh, H_A, int(refraction), out)
+    return np.array(out[:])
+
+
+def cyl_reach_margin(atm, h_obs, h_e, u_a, u_chi, refraction=True, R=EARTH_RADIUS):
+    return lib().orc_cyl_reach_margin(C.byref(atm), int(refraction), R, h_obs, h_e, u_a, u_chi)
+
+
 def ae_inverse(x, y, dz=0.0, h_obs=2000.0, R=EARTH_RADIUS):
     out = (C.c_double * 3)()
     lib().orc_ae_inverse(R, h_obs, x, y, dz, out)
@@ -286,7 +310,7 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
               refraction=False, transmission=False, seed=0,
               seg_base=0, n_showers=1, hist=None, tel=None, records=True, record_capacity=None,
               transmission_params=None, bands=None, quad_rtol=1e-10, spherical=False, earth_radius=EARTH_RADIUS,
-              lv1=None, optics=None, lv3=None, snell_dh=None, fluorescence=None):
+              lv1=None, optics=None, lv3=None, snell_dh=None, fluorescence=None, cylindrical=False):
     """Run the oracle over ``segs`` (dict of columns or SEGMENT_DTYPE array).
 
     Returns a dict with hist [n_showers, ny, nx], tel_counts [n_showers, n_tel],
@@ -320,7 +344,8 @@ def propagate(segs, atm, *, h_obs=2000.0, lambda_nm=(300.0, 600.0), s_max=1.0, b
     for k, v in b.items():
         setattr(cfg, k, v)
     cfg.quad_rtol = quad_rtol
-    cfg.spherical, cfg.earth_radius = int(spherical), earth_radius
+    cfg.spherical, cfg.earth_radius = int(spherical or cylindrical), earth_radius
+    cfg.cylindrical = int(cylindrical)
     if lv1:   # dict(metric, a, b, centre=(x, y, z), radius, band)
         cfg.lv1_metric, cfg.lv1_a, cfg.lv1_b = lv1["metric"], lv1["a"], lv1["b"]
         for i, v in enumerate(lv1.get("centre", (0.0, 0.0, h_obs))):

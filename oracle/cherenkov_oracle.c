@@ -26,6 +26,8 @@
  *                         tables approximate)
  *   spherical shell       Sec. 3.3.4 (Bouguer's invariant n r sin(psi),
  *                         azimuthal-equidistant ground coordinates)
+ *   cylindrical model     Sec. 3.3.3 (coaxial cylinders per photon, the
+ *                         axial and angular invariants, unrolled ground)
  *   tabulated atmosphere  Sec. 3.3 (a user's n(h) table, log-linear)
  *   Snell stepper as a    Sec. 3.4.2 on slabs and on spherical shells, with
  *   propagation method    delay and slant columns
@@ -680,6 +682,176 @@ void orc_ae_inverse(double R, double h_obs, double x, double y, double dz, doubl
 }
 
 /* ------------------------------------------------------------------ */
+/* Cylindrical atmosphere (Sec. 3.3.3).  The model adds to the         */
+/* altitude the horizontal distance d of the emission point E from the */
+/* array centre: the index gradient leans from the vertical by the     */
+/* angle chi_E, tan(chi_E) = d / (R + z_E), inside the vertical plane   */
+/* through the centre and E, and keeps that plane's azimuth along the  */
+/* whole path.  Reading: n depends on the distance rho from the        */
+/* horizontal axis through the Earth's centre normal to that plane     */
+/* (altitude rho - R), i.e. the atmosphere is a set of coaxial         */
+/* cylinders chosen per photon.  With e_r the horizontal unit from the */
+/* centre towards E's foot (the x axis when d = 0) and e_a = z x e_r   */
+/* along the axis, two invariants follow from the symmetry:            */
+/*   n u_a = A            (translation along the axis),               */
+/*   n rho u_chi = L      (rotation about it),                         */
+/* u_chi the component along the transverse tangent e_chi.  The path's */
+/* projection on the transverse plane is the ray of the planar index   */
+/* N = sqrt(n^2 - A^2) with Bouguer's N rho sin(psi) = L, and per      */
+/* unit of altitude it sweeps   dchi = L / (rho q),                     */
+/* runs the length   ds = n rho / q   and drifts   da = A rho / q       */
+/* along the axis, q = sqrt(N^2 rho^2 - L^2).  The ground is the       */
+/* cylinder rho = R + h_obs, unrolled onto the plane of the array: its */
+/* point (chi, a) has the coordinates (R + h_obs) chi e_r + a e_a, and */
+/* a direction keeps its components along the unrolled e_chi, e_a and  */
+/* the normal.  With u_a = 0 the photon stays in the plane through the */
+/* Earth's centre and the model is the spherical shell's.              */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const orc_atm* atm;
+    double A, L, R, H_A;       /* L >= 0 */
+    int refraction;            /* 0: n = 1 in the geometry (the straight line) */
+} orc_cctx;
+
+static double orc_cq(const orc_cctx* c, double h, double* n_out, double* r_out)
+{
+    double n = c->refraction ? orc_n(c->atm, h) : 1.0, r = c->R + h;
+    *n_out = n; *r_out = r;
+    return sqrt((n * n - c->A * c->A) * r * r - c->L * c->L);
+}
+static double orc_cChi(double h, const void* p)
+{
+    const orc_cctx* c = (const orc_cctx*)p; double n, r; double q = orc_cq(c, h, &n, &r);
+    return c->L / (r * q);
+}
+static double orc_cT(double h, const void* p)
+{
+    const orc_cctx* c = (const orc_cctx*)p; double n, r; double q = orc_cq(c, h, &n, &r);
+    return n * n * r / q / ORC_C_LIGHT;
+}
+static double orc_cAx(double h, const void* p)
+{
+    const orc_cctx* c = (const orc_cctx*)p; double n, r; double q = orc_cq(c, h, &n, &r);
+    return c->A * r / q;
+}
+static double orc_cX(double h, const void* p)
+{
+    const orc_cctx* c = (const orc_cctx*)p; double n, r; double q = orc_cq(c, h, &n, &r);
+    return 100.0 * orc_atm_rho(c->atm, h) * n * r / q;
+}
+static double orc_cAer(double h, const void* p)
+{
+    const orc_cctx* c = (const orc_cctx*)p; double n, r; double q = orc_cq(c, h, &n, &r);
+    return exp(-h / c->H_A) * n * r / q;
+}
+
+/* out = {chi swept [rad], t_path [s], axial drift [m], X_slant [g/cm^2], A_slant [m]}
+ * for a photon at altitude h_e whose direction has the component u_a along the
+ * axis and u_chi >= 0 along the transverse tangent (the rest points down the
+ * radius); refraction = 0 gives the vacuum straight line. */
+void orc_cyl_path(const orc_atm* a, double R, double h_obs, double h_e, double u_a, double u_chi, double H_A,
+                  int refraction, double rtol, double out[5])
+{
+    const double n_e = refraction ? orc_n(a, h_e) : 1.0;
+    orc_cctx c = { a, n_e * u_a, n_e * (R + h_e) * u_chi, R, H_A, refraction };
+    out[0] = orc_integrate(a, orc_cChi, &c, h_obs, h_e, rtol);
+    out[1] = orc_integrate(a, orc_cT, &c, h_obs, h_e, rtol);
+    out[2] = orc_integrate(a, orc_cAx, &c, h_obs, h_e, rtol);
+    out[3] = orc_integrate(a, orc_cX, &c, h_obs, h_e, rtol);
+    out[4] = orc_integrate(a, orc_cAer, &c, h_obs, h_e, rtol);
+}
+
+/* The Snell stepper (Sec. 3.4.2, Eq. 3.15) in the cylindrical atmosphere, in
+ * three dimensions: shells between coaxial cylinders of equal thickness
+ * <= dh in altitude, each holding n at its middle altitude; inside a shell
+ * the photon runs straight to the next inner cylinder, where Eq. 3.15
+ * refracts it about the inward normal (towards the axis, no axial part).
+ * Coordinates: transverse (x, y) with the axis at the origin and E at
+ * (0, R + h_e), axial a; direction (u_chi, u_rho, u_a), u_rho < 0.
+ * out = {chi swept, t_path, axial drift, X_slant, A_slant}. */
+void orc_snell_path_cyl(const orc_atm* a, double R, double h_obs, double h_e, double u_chi, double u_rho,
+                        double u_a, double dh, double H_A, int refraction, double out[5])
+{
+    double px = 0.0, py = R + h_e, pa = 0.0;
+    double dx = u_chi, dy = u_rho, da = u_a;
+    double t = 0.0, X = 0.0, A = 0.0;
+    int nsteps = (int)ceil((h_e - h_obs) / dh - 1e-9);
+    if (nsteps < 1) nsteps = 1;
+    const double step = (h_e - h_obs) / nsteps;
+    double n1 = refraction ? orc_n(a, h_e - 0.5 * step) : 1.0;
+    for (int j = 0; j < nsteps; ++j) {
+        const double h_mid = h_e - (j + 0.5) * step;
+        const double r_in = R + h_e - (j + 1) * step;
+        /* first crossing of |(px, py) + s (dx, dy)| = r_in */
+        const double tt = dx * dx + dy * dy, pd = px * dx + py * dy, c = px * px + py * py - r_in * r_in;
+        const double disc = pd * pd - tt * c;
+        const double sl = c / (-pd + sqrt(fmax(disc, 0.0)));   /* the smaller root, without cancellation */
+        px += sl * dx; py += sl * dy; pa += sl * da;
+        t += sl * n1 / ORC_C_LIGHT;
+        X += 100.0 * orc_atm_rho(a, h_mid) * sl;
+        A += exp(-h_mid / H_A) * sl;
+        if (j + 1 == nsteps) break;
+        const double n2 = refraction ? orc_n(a, h_mid - step) : 1.0;
+        const double r = sqrt(px * px + py * py), Nx = -px / r, Ny = -py / r;   /* inward normal */
+        const double cos_a1 = dx * Nx + dy * Ny;
+        const double cc = sqrt(n2 * n2 - n1 * n1 + n1 * n1 * cos_a1 * cos_a1) - n1 * cos_a1;
+        dx = (n1 * dx + cc * Nx) / n2;
+        dy = (n1 * dy + cc * Ny) / n2;
+        da = n1 * da / n2;
+        n1 = n2;
+    }
+    out[0] = atan2(px, py); out[1] = t; out[2] = pa; out[3] = X; out[4] = A;
+}
+
+/* Reach condition in the cylindrical atmosphere: the smallest value of
+ * (N rho - L) / L over [h_obs, h_e], N = sqrt(n^2 - A^2) (n = 1 for the
+ * straight line).  Within a piece between breakpoints phi = (n^2 - A^2) rho^2
+ * has at most one turning point and it is a minimum only if phi' rises through
+ * zero (on exponential pieces phi'/(2 rho) = n^2 - A^2 + n n' rho grows with
+ * rho; on linear and constant ones it does not), so phi is unimodal there and a
+ * golden-section search finds its smallest value, ends included.  Positive:
+ * the path reaches the ground. */
+static double orc_cyl_phi(const orc_atm* a, int refr, double R, double A, double h)
+{
+    const double n = refr ? orc_n(a, h) : 1.0, r = R + h;
+    return (n * n - A * A) * r * r;
+}
+double orc_cyl_reach_margin(const orc_atm* a, int refr, double R, double h_obs, double h_e, double u_a, double u_chi)
+{
+    const double n_e = refr ? orc_n(a, h_e) : 1.0;
+    const double A = n_e * u_a, L = n_e * (R + h_e) * fabs(u_chi);
+    if (!(L > 0.0)) return 1.0;
+    double edges[ORC_MAX_NODES + 18];
+    int m = 0;
+    edges[m++] = h_obs;
+    double bp[ORC_MAX_NODES + 16];
+    const int nb = refr ? orc_breakpoints(a, h_obs, h_e, bp) : 0;
+    for (int i = 0; i < nb; ++i) edges[m++] = bp[i];
+    edges[m++] = h_e;
+    const double g = 0.5 * (sqrt(5.0) - 1.0);
+    double best = 1e300;
+    for (int p = 0; p + 1 < m; ++p) {
+        /* the piece's interior, 1e-9 relative inside its ends (the one-sided limits) */
+        double lo = edges[p], hi = edges[p + 1];
+        const double eps = 1e-9 * fmax(1.0, fmax(fabs(lo), fabs(hi)));
+        if (p > 0) lo += eps;
+        hi -= eps;
+        if (!(hi > lo)) continue;
+        double v = fmin(orc_cyl_phi(a, refr, R, A, lo), orc_cyl_phi(a, refr, R, A, hi));
+        double x1 = hi - g * (hi - lo), x2 = lo + g * (hi - lo);
+        double f1 = orc_cyl_phi(a, refr, R, A, x1), f2 = orc_cyl_phi(a, refr, R, A, x2);
+        for (int it = 0; it < 200 && hi - lo > 1e-7; ++it) {
+            if (f1 < f2) { hi = x2; x2 = x1; f2 = f1; x1 = hi - g * (hi - lo); f1 = orc_cyl_phi(a, refr, R, A, x1); }
+            else { lo = x1; x1 = x2; f1 = f2; x2 = lo + g * (hi - lo); f2 = orc_cyl_phi(a, refr, R, A, x2); }
+        }
+        v = fmin(v, fmin(f1, f2));
+        const double m_ = (sqrt(fmax(v, 0.0)) - L) / L;
+        if (m_ < best) best = m_;
+    }
+    return best;
+}
+
+/* ------------------------------------------------------------------ */
 /* Full photon generation and propagation.                            */
 /* ------------------------------------------------------------------ */
 typedef struct {               /* input segment, 64 bytes */
@@ -713,7 +885,8 @@ typedef struct {
     double band_pos, band_count, band_T, band_h, band_w;
     double quad_rtol;
     int spherical;             /* 1: spherical-shell atmosphere, Earth centre at (0, 0, -earth_radius) */
-    int pad2;
+    int cylindrical;           /* 1 (with spherical = 1): the cylindrical atmosphere of Sec. 3.3.3, ground
+                                * and detector in the unrolled ground cylinder's coordinates */
     double earth_radius;
     /* LV1 particle filter (Sec. 4.3.2, 6.2.1): a segment whose start lies y above
      * h_obs and whose direction makes the angle x [deg] with the point of interest
@@ -999,6 +1172,9 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
     const double b = (double)cfg->bunch;
     const uint32_t key[2] = { (uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32) };
     const double n_obs = orc_n(atm, cfg->h_obs);
+    /* the cylinders are laid out per photon from the spherical frame; the LV3 filter's
+     * straight-line landing point is defined on the plane and the sphere only */
+    if (cfg->cylindrical && (!cfg->spherical || cfg->lv3)) return 2;
 
     for (size_t is = 0; is < n_segs; ++is) {
         const orc_segment* sg = &segs[is];
@@ -1196,11 +1372,26 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                 double theta0 = acos(cos_z);
                 rec.theta0 = theta0;
                 double sin_z = sin(theta0);
+                /* cylindrical atmosphere: the photon's axis frame (e_r towards E's foot,
+                 * e_a = z x e_r, e_chi the transverse tangent at E) and its components */
+                double c_er[3] = { 1.0, 0.0, 0.0 }, c_ea[3] = { 0.0, 1.0, 0.0 }, c_ua = 0.0, c_uchi = 0.0;
+                if (cfg->cylindrical) {
+                    const double dE = sqrt(E[0] * E[0] + E[1] * E[1]);
+                    if (dE > 0.0) { c_er[0] = E[0] / dE; c_er[1] = E[1] / dE; }
+                    c_ea[0] = -c_er[1]; c_ea[1] = c_er[0];
+                    /* vloc = sin(chi_E) e_r + cos(chi_E) z, e_chi = cos(chi_E) e_r - sin(chi_E) z */
+                    const double s_chi = vloc[0] * c_er[0] + vloc[1] * c_er[1], c_chi = vloc[2];
+                    c_ua = u[0] * c_ea[0] + u[1] * c_ea[1];
+                    c_uchi = c_chi * (u[0] * c_er[0] + u[1] * c_er[1]) - s_chi * u[2];
+                }
                 /* Does the path meet the observation level?  Along the exact path the
-                 * invariant (Eq. 3.17; Bouguer's n r sin(psi) on the shell) must stay below
-                 * n (h) (n r) all the way down; the straight line of Eq. 3.3 is the n = 1 case. */
+                 * invariant (Eq. 3.17; Bouguer's n r sin(psi) on the shell; in the cylinders
+                 * N rho sin(psi) with N = sqrt(n^2 - A^2)) must stay below n (h) (n r, N rho)
+                 * all the way down; the straight line of Eq. 3.3 is the n = 1 case. */
                 {
-                    double margin = orc_reach_margin(atm, cfg, h_e, sin_z);
+                    double margin = cfg->cylindrical
+                                    ? orc_cyl_reach_margin(atm, cfg->refraction, R, cfg->h_obs, h_e, c_ua, c_uchi)
+                                    : orc_reach_margin(atm, cfg, h_e, sin_z);
                     if (fabs(margin) < cfg->band_w) rec.flags |= ORC_FL_GROUND;
                     if (!(margin > 0.0)) {
                         rec.status = ORC_ST_NO_GROUND;
@@ -1276,6 +1467,41 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                         double sg_ = orc_n(atm, h_e) * sin_z / n_obs, cg = sqrt(1.0 - sg_ * sg_);
                         ug[0] = sg_ * hv[0]; ug[1] = sg_ * hv[1]; ug[2] = -cg;
                     } else { ug[0] = u[0]; ug[1] = u[1]; ug[2] = u[2]; }
+                } else if (cfg->cylindrical) {
+                    /* the transverse path sweeps chi, the axial drift follows from A; both are
+                     * laid out on the unrolled ground cylinder, where the arrival direction keeps
+                     * its components along e_chi, e_a and the normal */
+                    double cp[5];
+                    if (cfg->refraction && cfg->tracer == 1) {
+                        orc_snell_path_cyl(atm, R, cfg->h_obs, h_e, fabs(c_uchi), -cos_z, c_ua, cfg->tracer_dh, cfg->aer_H,
+                                           1, cp);
+                        const double q = (h_e - cfg->h_obs) / cfg->tracer_dh;
+                        if (fabs(q - nearbyint(q)) < 1e-3) rec.flags |= ORC_FL_LAYER;
+                        int ns = (int)ceil(q - 1e-9); if (ns < 1) ns = 1;
+                        const double step = (h_e - cfg->h_obs) / ns;
+                        if (atm->kind == ORC_ATM_LAYERED) {
+                            for (int li = 1; li <= atm->n_layers; ++li) {
+                                const double hb = li < atm->n_layers ? atm->layer_h[li] : atm->h_top;
+                                if (!(hb > cfg->h_obs && hb < h_e)) continue;
+                                const double f = (h_e - hb) / step - 0.5;
+                                if (fabs(f - nearbyint(f)) * step < 0.01) rec.flags |= ORC_FL_LAYER;
+                            }
+                        }
+                    } else {
+                        orc_cyl_path(atm, R, cfg->h_obs, h_e, c_ua, fabs(c_uchi), cfg->aer_H, cfg->refraction,
+                                     cfg->quad_rtol, cp);
+                    }
+                    const double rg = R + cfg->h_obs, chi_E = atan2(sqrt(E[0] * E[0] + E[1] * E[1]), E[2] + R);
+                    const double chi_g = chi_E + (c_uchi < 0.0 ? -cp[0] : cp[0]);
+                    gx = rg * chi_g * c_er[0] + cp[2] * c_ea[0];
+                    gy = rg * chi_g * c_er[1] + cp[2] * c_ea[1];
+                    G3[0] = gx; G3[1] = gy; G3[2] = cfg->h_obs;
+                    path[0] = cp[0]; path[1] = cp[1]; path[2] = cp[3]; path[3] = cp[4];
+                    const double n_e = cfg->refraction ? orc_n(atm, h_e) : 1.0, n_g = cfg->refraction ? n_obs : 1.0;
+                    const double ga = n_e * c_ua / n_g, gchi = n_e * (R + h_e) * c_uchi / (n_g * rg);
+                    const double grho = -sqrt(fmax(1.0 - ga * ga - gchi * gchi, 0.0));
+                    for (int c = 0; c < 2; ++c) ug[c] = gchi * c_er[c] + ga * c_ea[c];
+                    ug[2] = grho;
                 } else {
                     /* the path stays in the plane (centre, E, u): rotate the vertical by the
                      * central angle Phi towards hv; Bouguer's invariant gives the arrival zenith */
@@ -1350,7 +1576,7 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                 for (int it = 0; it < cfg->n_tel; ++it) {
                     const double* T4 = cfg->tel + 4 * it;
                     double Tc[3] = { T4[0], T4[1], T4[2] };
-                    if (cfg->spherical) orc_ae_inverse(R, cfg->h_obs, T4[0], T4[1], T4[2] - cfg->h_obs, Tc);
+                    if (cfg->spherical && !cfg->cylindrical) orc_ae_inverse(R, cfg->h_obs, T4[0], T4[1], T4[2] - cfg->h_obs, Tc);
                     double d0 = Tc[0] - G3[0], d1 = Tc[1] - G3[1], d2 = Tc[2] - G3[2];
                     double along = d0 * ug[0] + d1 * ug[1] + d2 * ug[2];
                     double dist2 = d0 * d0 + d1 * d1 + d2 * d2 - along * along;
@@ -1365,7 +1591,7 @@ int orc_propagate(const orc_segment* segs, size_t n_segs, const orc_atm* atm,
                 if (best >= 0 && cfg->cam_n > 0) {
                     const double* T4 = cfg->tel + 4 * best;
                     double Tc[3] = { T4[0], T4[1], T4[2] };
-                    if (cfg->spherical) orc_ae_inverse(R, cfg->h_obs, T4[0], T4[1], T4[2] - cfg->h_obs, Tc);
+                    if (cfg->spherical && !cfg->cylindrical) orc_ae_inverse(R, cfg->h_obs, T4[0], T4[1], T4[2] - cfg->h_obs, Tc);
                     int edge = 0;
                     rec.pix = orc_camera_pixel(cfg, Tc, G3, ug, cfg->band_pos, &edge);
                     if (edge) rec.flags |= ORC_FL_TEL_EDGE;
