@@ -80,8 +80,21 @@ typedef struct cs_segment {
  * ---------------------------------------------------------------------- */
 enum {
     CS_GEOM_PLANAR = 0,      /* n depends on z only, ground is the plane z = h_obs (Sec. 3.3.2) */
-    CS_GEOM_SPHERICAL = 1    /* n depends on the altitude |x - c| - R_E, c = (0, 0, -R_E); the ground is the
+    CS_GEOM_SPHERICAL = 1,   /* n depends on the altitude |x - c| - R_E, c = (0, 0, -R_E); the ground is the
                                 sphere of radius R_E + h_obs (Sec. 3.3.4) */
+    CS_GEOM_CYLINDRICAL = 2  /* Sec. 3.3.3: the index gradient leans in zenith only, inside the vertical
+                                plane through the array centre and the emission point E.  Per photon the
+                                atmosphere is a set of cylinders coaxial with the horizontal line through
+                                c normal to that plane (e_a = z x e_r, e_r the horizontal unit from the
+                                centre towards E's foot, the x axis when E lies above the centre); n
+                                depends on the distance rho from that axis (altitude rho - R_E).  The
+                                ground is the cylinder rho = R_E + h_obs, unrolled onto the array's plane:
+                                its point at angle chi from the centre's vertical and axial offset a has
+                                the coordinates (R_E + h_obs) chi e_r + a e_a, and arrival directions keep
+                                their components along the unrolled tangent, axis and normal.  Traced by
+                                the Snell stepper only (cs_opts.tracer = CS_TRACER_SNELL; the correction
+                                tables serve the plane and the sphere), without the LV1/LV3 filters or a
+                                surrogate; the detector must use this geometry too */
 };
 
 enum {
@@ -111,12 +124,13 @@ typedef struct cs_atmosphere_desc {
     int transmission;            /* 0: off; 1: Rayleigh + exponential aerosol survival test */
     double rayl_X0, rayl_lambda0;    /* Rayleigh length X_R = X0 (lambda / lambda0)^4 [g/cm^2] */
     double aer_tau0, aer_lambda0, aer_alpha, aer_H;  /* aerosol depth tau0 (lambda/lambda0)^-alpha per scale height aer_H [m] */
-    double theta_max;            /* table domain: photons steeper than this zenith [rad] are "out of
-                                    domain" (missed) when refraction or transmission is on; 0 = 75 deg */
+    double theta_max;            /* table domain: largest tabulated zenith [rad]; steeper photons (and
+                                    photons emitted above the table top) take the exact path, integrated
+                                    per photon by the exact pass; 0 = 75 deg */
     int table_nw;                /* 0 = default number of tan^2(theta) columns */
     double table_dh;             /* 0 = default row spacing [m]; must divide the layer bottoms - h_obs */
-    int geometry;                /* CS_GEOM_PLANAR or CS_GEOM_SPHERICAL */
-    double earth_radius;         /* spherical: R_E [m]; 0 = 6,370 km */
+    int geometry;                /* CS_GEOM_PLANAR, CS_GEOM_SPHERICAL or CS_GEOM_CYLINDRICAL */
+    double earth_radius;         /* spherical, cylindrical: R_E [m]; 0 = 6,370 km */
     int table_n;                 /* CS_ATM_TABLE: 2 .. 128 nodes */
     const double* table_h;       /* CS_ATM_TABLE: node heights [m], strictly ascending; host, read during
                                     the call only */
@@ -161,9 +175,11 @@ typedef struct cs_detector_desc {
     const double* tel_xyzr;      /* host, n_tel x {x, y, z, radius} [m] */
     int geometry;                /* CS_GEOM_SPHERICAL: histogram and telescope (x, y) are azimuthal-
                                     equidistant ground coordinates about the array centre (0, 0, h_obs),
-                                    telescope z is the height above the ground sphere plus h_obs; must
-                                    match the atmosphere */
-    double earth_radius;         /* spherical: R_E [m]; 0 = 6,370 km */
+                                    telescope z is the height above the ground sphere plus h_obs;
+                                    CS_GEOM_CYLINDRICAL: (x, y) are the unrolled ground cylinder's
+                                    coordinates and z the height above it plus h_obs, every photon tested
+                                    in its own cylinder's unrolled frame; must match the atmosphere */
+    double earth_radius;         /* spherical, cylindrical: R_E [m]; 0 = 6,370 km */
     /* Last-mile optics (Sec. 6.4), cam_n > 0 to enable: every telescope is a parabolic mirror of
      * diameter mirror_d and focal length focal_f whose vertex lies focal_f / 2 behind the sphere
      * centre along the optical axis (pointing at zenith point_zenith, azimuth point_azimuth [rad],
@@ -287,10 +303,12 @@ typedef struct cs_opts {
     /* Propagation method when the atmosphere refracts: CS_TRACER_TABLES (default) looks
      * the correction up in the FP64-built tables (interpolation tracing, Sec. 4.4.1);
      * CS_TRACER_SNELL traces every photon through homogeneous slabs (on the spherical
-     * shell: shells) of thickness <= tracer_dh [m], >= 0.01 m, with Snell's law in vector
-     * form (Sec. 3.4.2, Eq. 3.15) and accumulates its delay and slant columns on the way
-     * (the general-atmosphere fallback; the exact path only: CS_ERR_INVALID_ARG with a
-     * surrogate).  Ignored when the atmosphere does not refract. */
+     * shell: shells; in the cylindrical atmosphere: coaxial cylinders) of thickness
+     * <= tracer_dh [m], >= 0.01 m, with Snell's law in vector form (Sec. 3.4.2, Eq. 3.15)
+     * and accumulates its delay and slant columns on the way (the general-atmosphere
+     * fallback; the exact path only: CS_ERR_INVALID_ARG with a surrogate).  Ignored when
+     * the atmosphere does not refract, except in the cylindrical atmosphere, which it
+     * traces always (with n = 1 in the geometry when refraction is off). */
     int tracer;
     double tracer_dh;
     /* Emission (Sec. 2.2.2, 4.2.2): CS_EMIT_CHERENKOV (default), or nitrogen fluorescence,

@@ -20,7 +20,7 @@ _lib = None
 
 CS_OK, CS_ERR_INVALID_ARG, CS_ERR_CUDA, CS_ERR_CAPACITY, CS_ERR_TIMEOUT, CS_ERR_DOMAIN, CS_ERR_NO_DEVICE = range(7)
 CS_ATM_LAYERED, CS_ATM_LINEAR, CS_ATM_HOMOGENEOUS, CS_ATM_TABLE = 0, 1, 2, 3
-CS_GEOM_PLANAR, CS_GEOM_SPHERICAL = 0, 1
+CS_GEOM_PLANAR, CS_GEOM_SPHERICAL, CS_GEOM_CYLINDRICAL = 0, 1, 2
 CS_LV1_OFF, CS_LV1_ARRAY_CENTRE, CS_LV1_ARRAY_DISC, CS_LV1_TELESCOPES = 0, 1, 2, 3
 
 
@@ -359,13 +359,17 @@ def pack_segments(cols) -> np.ndarray:
     return a
 
 
+def _geometry(spherical, cylindrical):
+    return CS_GEOM_CYLINDRICAL if cylindrical else CS_GEOM_SPHERICAL if spherical else CS_GEOM_PLANAR
+
+
 class Atmosphere:
     """Owns a cs_atmosphere handle."""
 
     def __init__(self, kind=CS_ATM_LAYERED, layered=None, linear=None, hom_delta=0.0, h_obs=2000.0,
                  lambda_nm=(300.0, 600.0), refraction=False, transmission=False, transmission_params=None,
                  theta_max_deg=75.0, table_nw=0, table_dh=0.0, spherical=False, earth_radius=0.0, table=None,
-                 kappa=2.9e-4):
+                 kappa=2.9e-4, cylindrical=False):
         d = cs_atmosphere_desc()
         d.kind = kind
         self._keep = []
@@ -397,7 +401,7 @@ class Atmosphere:
             setattr(d, k, v)
         d.theta_max = math.radians(theta_max_deg)
         d.table_nw, d.table_dh = table_nw, table_dh
-        d.geometry, d.earth_radius = (CS_GEOM_SPHERICAL if spherical else CS_GEOM_PLANAR), earth_radius
+        d.geometry, d.earth_radius = _geometry(spherical, cylindrical), earth_radius
         self.desc = d
         self.h_obs = h_obs
         self.handle = cs_atmosphere_create(d)
@@ -421,7 +425,7 @@ class Detector:
     """Owns a cs_detector handle."""
 
     def __init__(self, n_showers=1, h_obs=2000.0, hist=None, tel=None, spherical=False, earth_radius=0.0,
-                 optics=None):
+                 optics=None, cylindrical=False):
         """optics: dict(mirror_d, focal_f, camera_r, point_zenith, point_azimuth [rad], cam_n
         [, efficiency=dict(lambda_nm, mirror, camera)]) for the last-mile ray tracing into
         per-telescope camera images, with the optics' absorption when efficiency is given."""
@@ -437,7 +441,7 @@ class Detector:
                 d.eff_n = len(self._eff[0])
                 d.eff_lambda_nm, d.eff_mirror, d.eff_camera = (a.ctypes.data_as(C.POINTER(C.c_double))
                                                                for a in self._eff)
-        d.geometry, d.earth_radius = (CS_GEOM_SPHERICAL if spherical else CS_GEOM_PLANAR), earth_radius
+        d.geometry, d.earth_radius = _geometry(spherical, cylindrical), earth_radius
         if hist:
             d.hist_nx, d.hist_ny = hist["nx"], hist["ny"]
             d.hist_x0, d.hist_y0, d.hist_dx, d.hist_dy = hist["x0"], hist["y0"], hist["dx"], hist["dy"]

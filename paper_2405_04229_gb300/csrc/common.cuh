@@ -34,7 +34,8 @@ struct TableView {
 // Everything a kernel needs about the atmosphere, passed by value.
 struct AtmParams {
     int kind;            // CS_ATM_*
-    int spherical;       // 1: spherical shell (Earth centre at (0, 0, -R))
+    int spherical;       // 1: spherical shell (Earth centre at (0, 0, -R)); also set for the cylinders
+    int cylindrical;     // 1: coaxial cylinders per photon (traced by the stepper only)
     float R, rg, inv_rg; // Earth radius, r_g = R + h_obs [m], 1 / r_g
     int n_layers;
     int refraction;
@@ -88,6 +89,7 @@ struct TelHash {
 struct DetParams {
     int n_showers;
     int spherical;        // telescope layout and histogram in azimuthal-equidistant coordinates
+    int cylindrical;      // layout and histogram on the unrolled ground cylinder (flat data, like the plane's)
     double R;
     float h_obs_f;        // observation level the telescopes were placed for
     double h_obs;

@@ -32,8 +32,9 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
     if (d->hist_nx > 0 && (!(d->hist_dx > 0.0) || !(d->hist_dy > 0.0))) return CS_ERR_INVALID_ARG;
     if ((double)d->hist_nx * d->hist_ny * d->n_showers > 4e9) return CS_ERR_INVALID_ARG;
     if (d->n_tel < 0 || (d->n_tel > 0 && !d->tel_xyzr)) return CS_ERR_INVALID_ARG;
-    if (d->geometry != CS_GEOM_PLANAR && d->geometry != CS_GEOM_SPHERICAL) return CS_ERR_INVALID_ARG;
-    if (d->geometry == CS_GEOM_SPHERICAL && (d->earth_radius < 0.0 || !isfinite(d->earth_radius)))
+    if (d->geometry != CS_GEOM_PLANAR && d->geometry != CS_GEOM_SPHERICAL && d->geometry != CS_GEOM_CYLINDRICAL)
+        return CS_ERR_INVALID_ARG;
+    if (d->geometry != CS_GEOM_PLANAR && (d->earth_radius < 0.0 || !isfinite(d->earth_radius)))
         return CS_ERR_INVALID_ARG;
     for (int i = 0; i < d->n_tel; ++i) {
         const double* t = d->tel_xyzr + 4 * i;
@@ -67,6 +68,7 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
     cs::DetParams& p = h->p;
     p.n_showers = d->n_showers;
     p.spherical = d->geometry == CS_GEOM_SPHERICAL ? 1 : 0;
+    p.cylindrical = d->geometry == CS_GEOM_CYLINDRICAL ? 1 : 0;
     p.R = d->earth_radius > 0.0 ? d->earth_radius : 6370000.0;
     p.h_obs = d->h_obs;
     p.h_obs_f = (float)d->h_obs;

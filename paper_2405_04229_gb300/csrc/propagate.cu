@@ -550,6 +550,86 @@ __device__ __noinline__ float4 snell_path_sph(const AtmParams& ap, float dz, flo
     return make_float4(ap.rg * sPhi, sT, ap.rho_per_delta * sX, ap.aer_hobs * sA);
 }
 
+// The stepper in the cylindrical atmosphere (Sec. 3.3.3): shells between
+// coaxial cylinders of equal thickness <= dh in altitude, each holding n at its
+// middle altitude.  Eq. 3.15 at a cylinder changes only the optical vector's
+// part along the inward normal, so its parts along the axis (A = n u_a) and
+// along the transverse tangent (L = n rho u_chi) keep the values they take in
+// the first shell, and in shell j the transverse track is the straight chord
+// with impact parameter b_j = L / N_j, N_j^2 = n_j^2 - A^2 (the vector form's
+// algebra in scalar form).  A chord from rho_out to rho_in = rho_out - step
+// has the transverse length sigma = step (rho_out + rho_in) / (q_out + q_in),
+// q = sqrt(rho^2 - b^2), sweeps b sigma / (rho_in rho_out) radians (the sine of
+// the angle; they differ by < 1e-15 here), runs sigma n_j / N_j of path and
+// drifts sigma A / N_j along the axis.  FP32 cannot form rho - b directly
+// (rho ~ 6.4e6 m carries 0.5 m ulps, and grazing photons keep rho - b within a
+// few hundred metres), so with e = n^2 - 1, D = rho_e - rho and u_chi^2 +
+// cos^2 = 1 - u_a^2 = T the two are written cancellation-free:
+//   N_j^2 = T (1 + e_0) + (e_j - e_0),
+//   (rho N_j)^2 - L^2 = (1 + e_0) (rho^2 cos^2 - u_chi^2 D (2 rho_e - D)) + rho^2 (e_j - e_0),
+// in units of rho_e^2, e_j - e_0 = (d_j - d_0)(2 + d_j + d_0).  The long sums
+// are compensated.  Arguments: altitude dz above the observation level, u_a,
+// |u_chi| and cos(zenith) at the emission point.  Returns false when a chord
+// turns before its inner cylinder: the photon never meets the ground.
+struct CylPath {
+    float chi;     // angle swept about the axis [rad]
+    float axial;   // drift along the axis [m]
+    float ct;      // c t_path [m]
+    float X, A;    // slant columns [g/cm^2], [m]
+};
+__device__ __noinline__ bool snell_path_cyl(const AtmParams& ap, float dz, float ua, float uchi, float cz, float dh,
+                                            CylPath& out) {
+    const int ns = max(1, (int)ceilf(dz / dh));
+    const float step = dz / (float)ns;
+    const bool refr = ap.refraction != 0;
+    const float d0 = refr ? delta_at(ap, dz - 0.5f * step) : 0.0f;   // the first shell's n - 1
+    const float e0 = d0 * (2.0f + d0);
+    const float re = ap.rg + dz, ire = 1.0f / re, st = step * ire;
+    const float T = fmaf(uchi, uchi, cz * cz);            // 1 - u_a^2 from the other two parts
+    const float c2 = cz * cz, w2 = uchi * uchi;
+    const float Lr = (1.0f + d0) * uchi, Aax = (1.0f + d0) * ua;   // L / rho_e and A
+    float sChi = 0.0f, cChi = 0.0f, sAx = 0.0f, cAx = 0.0f, sCt = 0.0f, cCt = 0.0f, sX = 0.0f, sA = 0.0f;
+    auto acc = [](float& s, float& c, float v) {
+        float t, e;
+        two_sum(s, v, t, e);
+        s = t;
+        c += e;
+    };
+    // (rho N)^2 - L^2 in units of rho_e^2 at depth d = D / rho_e (x = rho / rho_e = 1 - d)
+    auto num = [&](float d, float de_) {
+        const float x = 1.0f - d;
+        return fmaf(1.0f + e0, fmaf(x * x, c2, -w2 * d * (2.0f - d)), x * x * de_);
+    };
+    bool reach = true;
+    for (int j = 0; j < ns; ++j) {
+        const float h = dz - ((float)j + 0.5f) * step;
+        const float dc = (refr || ap.transmission) ? delta_at(ap, h) : 0.0f;   // the shell's n - 1
+        const float dj = refr ? dc : 0.0f;                                      // in the geometry
+        const float de_ = (dj - d0) * (2.0f + dj + d0);                          // e_j - e_0
+        const float iN = rsqrtf(fmaxf(fmaf(T, 1.0f + e0, de_), 1e-30f));
+        const float n_in = num((float)(j + 1) * st, de_);
+        reach = reach && n_in > 0.0f;
+        const float q_out = sqrtf(fmaxf(num((float)j * st, de_), 0.0f)) * iN;   // q / rho_e
+        const float q_in = sqrtf(fmaxf(n_in, 0.0f)) * iN;
+        const float xo = 1.0f - (float)j * st, xi = xo - st;
+        const float sig = step * (xo + xi) * rcp_approx(q_out + q_in);   // transverse chord [m]
+        const float s3 = sig * (1.0f + dj) * iN;                          // the chord in three dimensions
+        acc(sChi, cChi, Lr * iN * sig * ire * rcp_approx(xi * xo));
+        acc(sAx, cAx, sig * Aax * iN);
+        acc(sCt, cCt, s3 * (1.0f + dj));
+        if (ap.transmission) {
+            sX = fmaf(dc, s3, sX);
+            sA = fmaf(ex2_approx(ap.aer_c2 * h), s3, sA);
+        }
+    }
+    out.chi = sChi + cChi;
+    out.axial = sAx + cAx;
+    out.ct = sCt + cCt;
+    out.X = ap.rho_per_delta * sX;
+    out.A = ap.aer_hobs * sA;
+    return reach;
+}
+
 // Survival probability (Sec. 4.3.1) from the slant columns in table form
 // (G_X = X cos, G_A = A cos): exp(-X / X_R(lambda) - tau_A(lambda) A / H_A).
 __device__ __forceinline__ float transmission_T(const AtmParams& ap, float GX, float GA, float inv_l, float inv_uz) {
@@ -826,6 +906,103 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                         const float2 TL = __ldg(dp.tel_lo + tel);
                         pix = camera_pixel(dp, (T4.x - Cg.x) + ((TL.x - Cg.y) - rx),
                                            (T4.y - Cg.z) + ((TL.y - Cg.w) - ry), T4.z, ux * sc, uy * sc, ugz);
+                        pix = optics_survival(dp, pp, gid, k, i, inv_l, pix);
+                    }
+                }
+                if (tel >= 0) {
+                    const size_t slot = (size_t)sh * dp.n_tel + tel;
+                    atomicAdd(op.tel_counts + slot, (unsigned long long)b);
+                    if (op.tel_time) atomicAdd(op.tel_time + slot, (double)b * (S.t0[sg] + (double)t_rel));
+                    if (pix >= 0) atomicAdd(op.camera + (slot * dp.cam_n * dp.cam_n + pix), (unsigned long long)b);
+                }
+            }
+        }
+    } else if (TR && ap.cylindrical && status == CS_ST_LANDED) {
+        // the cylindrical atmosphere (Sec. 3.3.3): emission point E = start + ell P in
+        // float-float, e_r the horizontal unit towards its foot, e_a = z x e_r the axis
+        float Ex, Exl, Ey, Eyl;
+        two_sum(Cc.x, fmaf(ell, Px, Dd.x), Ex, Exl);
+        two_sum(Cc.y, fmaf(ell, Py, Dd.y), Ey, Eyl);
+        const float dE2 = Ex * Ex + Ey * Ey;
+        float erx = 1.0f, ery = 0.0f;
+        if (dE2 > 0.0f) {
+            const float id = rsqrtf(dE2);
+            erx = Ex * id;
+            ery = Ey * id;
+        }
+        // the local vertical v = sin(chi_E) e_r + cos(chi_E) z; u's parts along the axis
+        // and along the transverse tangent e_chi = cos(chi_E) e_r - sin(chi_E) z
+        const float s_chi = dvx * erx + dvy * ery, c_chi = 1.0f + dvz;
+        const float ua = uy * erx - ux * ery;
+        const float uchi = c_chi * (ux * erx + uy * ery) - s_chi * uz;
+        CylPath cp;
+        if (!snell_path_cyl(ap, dz, ua, fabsf(uchi), cos_z, pp.snell_dh, cp)) status = CS_ST_NO_GROUND;
+        // ground point on the unrolled cylinder: E's footprint r_g chi_E e_r (the
+        // azimuthal-equidistant point of E, x = E_x - E_x om as on the sphere) plus the
+        // sweep along e_r and the drift along e_a
+        const float irg = ap.inv_rg, rg = ap.rg, h_obs_f = (float)ap.h_obs;
+        const float eta = ((Cc.z - h_obs_f) + (Dd.z + ell * Pz)) * irg, ie = rcp_approx(1.0f + eta);
+        const float X2 = dE2 * (irg * irg) * (ie * ie);
+        const float one_m_s = X2 < 0.01f ? X2 * fmaf(X2, -0.2f, 1.0f / 3.0f) : 1.0f - atanf(sqrtf(X2)) * rsqrtf(X2);
+        const float om = (eta + one_m_s) * ie;
+        const float dr = copysignf(cp.chi, uchi) * rg, da = cp.axial;
+        x = Ex;
+        xl = fmaf(-Ex, om, Exl) + fmaf(dr, erx, -da * ery);
+        y = Ey;
+        yl = fmaf(-Ey, om, Eyl) + fmaf(dr, ery, da * erx);
+        two_sum(x, xl, x, xl);
+        two_sum(y, yl, y, yl);
+        t_rel = fmaf(cp.ct, kInvC, t_rel);
+        float Tr = 1.0f;
+        if (ap.transmission) {
+            const float il2 = inv_l * inv_l;
+            const float kA = ap.kA0 * ex2_approx(ap.aer_alpha * lg2_approx(ap.lamA_nm * inv_l));
+            Tr = ex2_approx(-(cp.X * (ap.kR0 * il2 * il2) + cp.A * kA));
+        }
+        if (status != CS_ST_LANDED) {
+            // turned above the ground: missed
+        } else if (ap.transmission && !(u3 < Tr)) {
+            status = CS_ST_ABSORBED;
+        } else {
+            const int sh = S.shower[sg];
+            if (dp.nx > 0) {
+                const int ix = (int)floorf(((x - dp.hx0_hi) + (xl - dp.hx0_lo)) * dp.inv_dx);
+                const int iy = (int)floorf(((y - dp.hy0_hi) + (yl - dp.hy0_lo)) * dp.inv_dy);
+                if (ix >= 0 && ix < dp.nx && iy >= 0 && iy < dp.ny) {
+                    bin = iy * dp.nx + ix;
+                    hist_add(op, (unsigned int)(sh * dp.ny * dp.nx + bin), b);
+                }
+            }
+            if (dp.n_tel > 0) {
+                // arrival direction in the unrolled frame: n u_a and n rho u_chi conserved
+                const float ratio = ap.refraction ? (1.0f + delta_at(ap, dz)) * ap.inv_n_obs : 1.0f;   // n_e / n_g
+                const float uga = ratio * ua, ugc = ratio * fmaf(dz, irg, 1.0f) * uchi;
+                const float ugz = -sqrtf(fmaxf(1.0f - uga * uga - ugc * ugc, 0.0f));
+                const float ugx = ugc * erx - uga * ery, ugy = ugc * ery + uga * erx;
+                const float xs = x + xl, ys = y + yl;
+                const float sg2 = ugx * ugx + ugy * ugy;
+                const bool hashed = sg2 <= dp.hash[1].sin2_max;
+                const TelHash& H = dp.hash[sg2 <= dp.hash[0].sin2_max ? 0 : 1];
+                if (!hashed || (xs >= H.bx0 && xs < H.bx1 && ys >= H.by0 && ys < H.by1)) {
+                    tel = hit_telescope(
+                        dp, H, hashed, xs, ys, ugx, ugy, ugz,
+                        [&](const float4& D, float cx0, float cy0, float& ddx, float& ddy, float& ddz) {
+                            ddx = D.x - ((x - cx0) + xl);
+                            ddy = D.y - ((y - cy0) + yl);
+                            ddz = D.z;
+                        },
+                        [&](int it, float& ddx, float& ddy, float& ddz, float& r) {
+                            const float4 T4 = __ldg(dp.tel + it);
+                            const float2 TL = __ldg(dp.tel_lo + it);
+                            ddx = (T4.x - x) + (TL.x - xl);
+                            ddy = (T4.y - y) + (TL.y - yl);
+                            ddz = T4.z;
+                            r = T4.w;
+                        });
+                    if (tel >= 0 && dp.cam_n > 0) {
+                        const float4 T4 = __ldg(dp.tel + tel);
+                        const float2 TL = __ldg(dp.tel_lo + tel);
+                        pix = camera_pixel(dp, (T4.x - x) + (TL.x - xl), (T4.y - y) + (TL.y - yl), T4.z, ugx, ugy, ugz);
                         pix = optics_survival(dp, pp, gid, k, i, inv_l, pix);
                     }
                 }
@@ -1359,11 +1536,12 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
 
 // Launches the exact-tracer or the surrogate instance of the kernel.
 // An atmosphere and a detector work together when they share the observation
-// level and the geometry (and, on the sphere, the Earth radius).
+// level and the geometry (and, on the sphere and the cylinders, the Earth radius).
 bool compatible(const cs_atmosphere* atm, const cs_detector* det) {
     const double tol = 1e-9 * fmax(1.0, fabs(atm->p.h_obs));
     if (fabs(det->p.h_obs - atm->p.h_obs) > tol) return false;
-    if (det->p.spherical != atm->p.spherical) return false;
+    if (det->p.cylindrical != atm->p.cylindrical) return false;
+    if (!atm->p.cylindrical && det->p.spherical != atm->p.spherical) return false;
     return !atm->p.spherical || fabs(det->p.R - atm->f64.R) <= 1e-9 * atm->f64.R;
 }
 
@@ -1581,6 +1759,10 @@ bool filters_valid(const cs_opts& o, const cs_atmosphere* atm) {
     }
     if (o.tracer != CS_TRACER_TABLES &&
         (o.tracer != CS_TRACER_SNELL || !(o.tracer_dh >= 0.01) || !isfinite(o.tracer_dh) || o.surrogate))
+        return false;
+    // the cylinders: the stepper only, no filters (their geometry is the plane's or the sphere's), no network
+    if (atm->p.cylindrical &&
+        (o.tracer != CS_TRACER_SNELL || o.lv3 || o.lv1_metric != CS_LV1_OFF || o.surrogate))
         return false;
     if (o.lv3 && !(o.lv3_radius >= 0.0 && o.lv3_margin >= 0.0 && isfinite(o.lv3_radius + o.lv3_margin) &&
                    isfinite(o.lv3_centre[0]) && isfinite(o.lv3_centre[1]) && isfinite(o.lv3_centre[2])))

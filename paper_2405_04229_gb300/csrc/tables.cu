@@ -294,9 +294,11 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
     a.kind = d->kind;
     a.h_obs = d->h_obs;
     a.refraction = d->refraction ? 1 : 0;
-    a.spherical = d->geometry == CS_GEOM_SPHERICAL ? 1 : 0;
+    // the cylinders keep the sphere's frame (altitude of the emission point, local vertical)
+    a.spherical = d->geometry == CS_GEOM_SPHERICAL || d->geometry == CS_GEOM_CYLINDRICAL ? 1 : 0;
     a.R = d->earth_radius > 0.0 ? d->earth_radius : 6370000.0;
-    if (d->geometry != CS_GEOM_PLANAR && d->geometry != CS_GEOM_SPHERICAL) return CS_ERR_INVALID_ARG;
+    if (d->geometry != CS_GEOM_PLANAR && d->geometry != CS_GEOM_SPHERICAL && d->geometry != CS_GEOM_CYLINDRICAL)
+        return CS_ERR_INVALID_ARG;
     a.H_A = d->aer_H > 0.0 ? d->aer_H : 1200.0;
     double table_top;
     if (d->kind == CS_ATM_LAYERED) {
@@ -382,13 +384,15 @@ extern "C" cs_status cs_atmosphere_create(const cs_atmosphere_desc* d, cs_atmosp
     AtmParams& p = h->p;
     p.kind = d->kind;
     p.spherical = a.spherical;
+    p.cylindrical = d->geometry == CS_GEOM_CYLINDRICAL ? 1 : 0;
     p.R = (float)a.R;
     p.rg = (float)(a.R + d->h_obs);
     p.inv_rg = (float)(1.0 / (a.R + d->h_obs));
     p.n_layers = a.n_layers;
     p.refraction = a.refraction;
     p.transmission = d->transmission ? 1 : 0;
-    p.use_tables = (p.refraction || p.transmission) ? 1 : 0;
+    // the cylinders' stepper integrates every photon's fields itself
+    p.use_tables = (p.refraction || p.transmission) && !p.cylindrical ? 1 : 0;
     p.h_obs = d->h_obs;
     if (d->kind == CS_ATM_LAYERED) {
         for (int i = 0; i < a.n_layers; ++i) {
