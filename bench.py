@@ -329,6 +329,8 @@ def run_batched(args):
                        "generation_s": round(gen_s, 1), "l2": "inputs (%.1f GB) larger than L2" % (arr.nbytes / 1e9)},
             "counters": [int(x) for x in h["counters"]], "cpu_baseline": cpu, "gpu_launches": 2 * args.steps,
             "clocks": clk.summary()}
+    if getattr(args, "quiet", False):
+        return line
     print(json.dumps(line), flush=True)
 
 
@@ -583,6 +585,8 @@ def run_inclined(args):
                          "note": "per chunk launch; spherical lane-op count per bunch %d" % OPS_PER_BUNCH_SPHERICAL},
             "kernel_ms": k_ms, "cpu_baseline": cpu, "surrogate": surrogate, "e2e": e2e, "lv1_filter": lv1_res, "lv3_filter": lv3_res,
             "gpu_launches": 2 * args.steps * n_chunks, "clocks": clk.summary()}
+    if getattr(args, "quiet", False):
+        return line
     print(json.dumps(line), flush=True)
 
 
@@ -623,6 +627,63 @@ def cpu_oracle_rate_sph(segs, tel, hist, bunch, seed, budget_s=12.0, chunk=200):
     return photons / dt, threads, "first %d segments of chunk 0 (%d-segment pieces), %.1f s" % (done, chunk, dt)
 
 
+def run_tiny(steps=20, warmup=5, seed=0):
+    """The plain method at its smallest: 1,000 electron tracks from 8-12 km, straight
+    lines, bunch 1, the 400 x 400 histogram (launch-bound: a few thousand photons)."""
+    import torch
+    from paper_2405_04229_gb300 import binding as B
+    from paper_2405_04229_gb300 import synth
+    segs = synth.tiny_vertical_segments(1000, seed=seed)
+    arr = B.pack_segments(segs)
+    atm = B.Atmosphere(layered=synth.US_STANDARD, refraction=False, transmission=False)
+    det = B.Detector(n_showers=1, hist=synth.histogram_400())
+    outs = B.DeviceOutputs(det)
+    d = torch.from_numpy(arr.view(np.uint8)).cuda()
+    stream = torch.cuda.current_stream()
+    sp = C.c_void_p(stream.cuda_stream)
+    o = B.cs_opts_default()
+    o.bunch, o.device_ptrs = 1, 1
+
+    def step():
+        st = B.cs_propagate_ex(C.c_void_p(d.data_ptr()), len(arr), atm.handle, det.handle, seed, o, outs.out, sp)
+        if st != B.CS_OK:
+            raise B.CSError(st, "cs_propagate_ex(tiny)")
+
+    for _ in range(max(3, warmup)):
+        step()
+    torch.cuda.synchronize()
+    photons = int(outs.counters[0].item())
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b_ in ev:
+        a.record(stream)
+        step()
+        b_.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b_) for a, b_ in ev) / steps
+    h = outs.host()
+    res = {"value": photons / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "photons_per_step": photons, "histogram_photons": int(h["hist"].sum()),
+           "workload": "1,000 tracks 8-12 km, straight lines, bunch 1, 400 x 400 histogram (launch-bound)"}
+    atm.close()
+    det.close()
+    return res
+
+
+def extra_configs(args):
+    """The other configurations as keys of the default line: the tiny straight-line
+    case, the batched uneven showers (full size, one graph-captured launch) and the
+    large inclined shower (full size, 10 chunks, with the LV1 and LV3 filters)."""
+    sub = dict(seed=args.seed, warmup=3, steps=3, quiet=True, no_cpu_baseline=True)
+    out = {"c1_tiny": run_tiny(seed=args.seed)}
+    b = run_batched(argparse.Namespace(**sub))
+    out["c3_batched"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "steps", "config", "gpu_launches", "clocks")}
+    i = run_inclined(argparse.Namespace(**sub, chunk=args.chunk, chunks=args.chunks, lv1=True, lv3=True,
+                                        no_e2e=False, no_surrogate=True))
+    out["c5_inclined"] = {k: i[k] for k in ("value", "unit", "ms_per_step", "steps", "kernel_ms", "roofline", "e2e",
+                                            "lv1_filter", "lv3_filter", "config", "gpu_launches", "clocks")}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -642,6 +703,8 @@ def main():
     ap.add_argument("--no-optics", action="store_true")
     ap.add_argument("--no-snell", action="store_true")
     ap.add_argument("--no-fluorescence", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="leave out the tiny, batched and inclined configurations' keys")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -906,6 +969,10 @@ def main():
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline_entry(segs, tel, hist)
 
+    configs = None
+    if world == 1 and not args.no_configs:
+        configs = extra_configs(args)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -934,6 +1001,8 @@ def main():
             "gpu_launches": 2 * args.steps,   # the photon kernel and its exact pass, per step
             "clocks": sm_clk,
         }
+        if configs:
+            line.update(configs)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -378,8 +378,9 @@ cs_status cs_propagate_ex(const cs_segment* segs, size_t n, const cs_atmosphere*
 
 /* ------------------------------------------------------------------------
  * Batched uneven showers: many showers of uneven size in one persistent
- * launch (blocks take tiles of 256 segments from a work counter until the
- * batch is done), captured once into a CUDA graph and replayed.  The thesis
+ * launch (warps take tiles of 32 segments -- blocks tiles of 256 with the
+ * surrogate -- from a work counter until the batch is done), captured once
+ * into a CUDA graph and replayed.  The thesis
  * batches tens of thousands of tracks per kernel call (Sec. 5.1, 5.4).
  * ---------------------------------------------------------------------- */
 typedef struct cs_batch cs_batch;

@@ -31,115 +31,190 @@ namespace cs {
 namespace {
 
 // ---------------------------------------------------------------------------
-// Generic tensor-core GEMM: C[M x N] (op)= A[M x K] B[K x N].
+// Generic tensor-core GEMM on tcgen05: C[M x N] (op)= A[M x K] B[K x N].
 //   A_KM: A is stored [K][M] (else [M][K]);  B_KN: B is stored [K][N] (else [N][K]).
 //   SPLIT_A / SPLIT_B: the FP32 operand is staged as a BF16 hi + lo pair and
 //   the products hi*hi + lo*hi (+ hi*lo) are accumulated.
 //   EPI: 0 store, 1 store tanh(C + bias[n]), 2 store C + bias[n], 3 store the
 //   partial product of K slice z = blockIdx.z at C + z M ldc (summed in a
 //   fixed order afterwards, so training is deterministic).
-// One 64 x 64 output tile per block of 4 warps (32 x 32 each); K in chunks of
-// 32 staged through shared memory; blockIdx.z splits K for EPI 3.
+// One 128 x 64 output tile per block of 128 threads: the threads stage 64-wide
+// K chunks of A and B as BF16 into shared memory in the no-swizzle K-major
+// core-matrix layout, one thread issues single-CTA tcgen05.mma.kind::f16
+// (M = 128, N = 64, four K = 16 steps per chunk, FP32 accumulators in 64
+// tensor-memory columns) and commits to an mbarrier that every thread waits
+// on (bounded) before the chunk's buffers are refilled; the epilogue reads
+// the accumulators back with tcgen05.ld, warp w holding rows 32w .. 32w + 31.
+// blockIdx.z splits K for EPI 3.  A wait that runs out sets the unit's
+// time-out flag, and the block stops issuing, waits once more (bounded) for
+// its MMAs and frees its tensor memory.
 // ---------------------------------------------------------------------------
+constexpr int kGmM = 128, kGmN = 64, kGmK = 64;
+constexpr int kGmATile = kGmM * kGmK * 2, kGmBTile = kGmN * kGmK * 2;   // 16 KB, 8 KB
+constexpr int kGmSmem = 2 * kGmATile + 2 * kGmBTile;                    // hi and lo of both operands
+
+// Eight FP32 values as BF16 into a core-matrix row of 16 bytes (and the lo parts).
+template <bool SPLIT>
+__device__ __forceinline__ void gm_store8(unsigned char* hi, unsigned char* lo, int off, const float (&v)[8]) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat16 a = __float2bfloat16_rn(v[2 * j]), b = __float2bfloat16_rn(v[2 * j + 1]);
+        h[j] = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+        if (SPLIT) {
+            const __nv_bfloat16 c = __float2bfloat16_rn(v[2 * j] - __bfloat162float(a));
+            const __nv_bfloat16 d = __float2bfloat16_rn(v[2 * j + 1] - __bfloat162float(b));
+            l[j] = (uint32_t)__bfloat16_as_ushort(c) | ((uint32_t)__bfloat16_as_ushort(d) << 16);
+        }
+    }
+    *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    if (SPLIT) *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Eight consecutive K values of row r of an operand (zero beyond rows or kend).
+template <bool KMAJOR_STORE>
+__device__ __forceinline__ void gm_load8(const float* __restrict__ X, int ld, int r, int rows, int k, int kend,
+                                         float (&v)[8]) {
+    if (r >= rows) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = 0.0f;
+        return;
+    }
+    if (!KMAJOR_STORE && k + 8 <= kend && ((ld | k) & 3) == 0) {   // row-major: two float4 loads
+        const float4 a = __ldg(reinterpret_cast<const float4*>(X + (size_t)r * ld + k));
+        const float4 b = __ldg(reinterpret_cast<const float4*>(X + (size_t)r * ld + k + 4));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        v[j] = k + j < kend ? (KMAJOR_STORE ? __ldg(X + (size_t)(k + j) * ld + r) : __ldg(X + (size_t)r * ld + k + j)) : 0.0f;
+}
+
 template <bool A_KM, bool B_KN, bool SPLIT_A, bool SPLIT_B, int EPI>
 __global__ void __launch_bounds__(128) gemm_kernel(const float* __restrict__ A, int lda, const float* __restrict__ B,
                                                    int ldb, float* __restrict__ Cm, int ldc, int M, int N, int K,
                                                    int kchunk, const float* __restrict__ bias) {
-    __shared__ __align__(16) __nv_bfloat16 Ah[64][40], Al[64][40], Bh[64][40], Bl[64][40];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, q = lane & 3;
-    const int m_blk = blockIdx.y * 64, n_blk = blockIdx.x * 64;
+    extern __shared__ __align__(128) unsigned char gsm[];
+    unsigned char* a_hi = gsm;
+    unsigned char* a_lo = gsm + kGmATile;
+    unsigned char* b_hi = gsm + 2 * kGmATile;
+    unsigned char* b_lo = gsm + 2 * kGmATile + kGmBTile;
+    __shared__ unsigned long long mbar;
+    __shared__ unsigned int tmem_base;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m_blk = blockIdx.y * kGmM, n_blk = blockIdx.x * kGmN;
     const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
-
-    for (int k0 = kbeg; k0 < kend; k0 += 32) {
-        for (int idx = tid; idx < 64 * 32; idx += 128) {
-            int m, k;
-            if (A_KM) { k = idx >> 6; m = idx & 63; } else { m = idx >> 5; k = idx & 31; }
-            const int gm = m_blk + m, gk = k0 + k;
-            const float v = (gm < M && gk < kend) ? (A_KM ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk]) : 0.0f;
-            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-            Ah[m][k] = hi;
-            if (SPLIT_A) Al[m][k] = __float2bfloat16_rn(v - __bfloat162float(hi));
-        }
-        for (int idx = tid; idx < 64 * 32; idx += 128) {
-            int n, k;
-            if (B_KN) { k = idx >> 6; n = idx & 63; } else { n = idx >> 5; k = idx & 31; }
-            const int gn = n_blk + n, gk = k0 + k;
-            const float v = (gn < N && gk < kend) ? (B_KN ? B[(size_t)gk * ldb + gn] : B[(size_t)gn * ldb + gk]) : 0.0f;
-            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-            Bh[n][k] = hi;
-            if (SPLIT_B) Bl[n][k] = __float2bfloat16_rn(v - __bfloat162float(hi));
-        }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < 32; ks += 16) {
-            uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi) {
-                const int r0 = wm + mi * 16 + g;
-                ah[mi][0] = *reinterpret_cast<const uint32_t*>(&Ah[r0][ks + 2 * q]);
-                ah[mi][1] = *reinterpret_cast<const uint32_t*>(&Ah[r0 + 8][ks + 2 * q]);
-                ah[mi][2] = *reinterpret_cast<const uint32_t*>(&Ah[r0][ks + 8 + 2 * q]);
-                ah[mi][3] = *reinterpret_cast<const uint32_t*>(&Ah[r0 + 8][ks + 8 + 2 * q]);
-                if (SPLIT_A) {
-                    al[mi][0] = *reinterpret_cast<const uint32_t*>(&Al[r0][ks + 2 * q]);
-                    al[mi][1] = *reinterpret_cast<const uint32_t*>(&Al[r0 + 8][ks + 2 * q]);
-                    al[mi][2] = *reinterpret_cast<const uint32_t*>(&Al[r0][ks + 8 + 2 * q]);
-                    al[mi][3] = *reinterpret_cast<const uint32_t*>(&Al[r0 + 8][ks + 8 + 2 * q]);
-                }
-            }
-#pragma unroll
-            for (int ni = 0; ni < 4; ++ni) {
-                const int c0 = wn + ni * 8 + g;
-                bh[ni][0] = *reinterpret_cast<const uint32_t*>(&Bh[c0][ks + 2 * q]);
-                bh[ni][1] = *reinterpret_cast<const uint32_t*>(&Bh[c0][ks + 8 + 2 * q]);
-                if (SPLIT_B) {
-                    bl[ni][0] = *reinterpret_cast<const uint32_t*>(&Bl[c0][ks + 2 * q]);
-                    bl[ni][1] = *reinterpret_cast<const uint32_t*>(&Bl[c0][ks + 8 + 2 * q]);
-                }
-            }
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni) {
-                    mma_16816(acc[mi][ni], ah[mi][0], ah[mi][1], ah[mi][2], ah[mi][3], bh[ni][0], bh[ni][1]);
-                    if (SPLIT_A) mma_16816(acc[mi][ni], al[mi][0], al[mi][1], al[mi][2], al[mi][3], bh[ni][0], bh[ni][1]);
-                    if (SPLIT_B) mma_16816(acc[mi][ni], ah[mi][0], ah[mi][1], ah[mi][2], ah[mi][3], bl[ni][0], bl[ni][1]);
-                }
-        }
-        __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(kGmN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    if (tid == 0) {
+        mbar_init(smem_u32(&mbar), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t d_tmem = tmem_base, mb = smem_u32(&mbar);
+    constexpr uint32_t idesc = tc_idesc(kGmN);
+    uint32_t phase = 0;
+    bool first = true;
+    for (int k0 = kbeg; k0 < kend; k0 += kGmK) {
+        // A: 128 rows x 8 K groups, B: 64 rows x 8 K groups, 8 values per unit
+        for (int u = tid; u < kGmM * (kGmK / 8); u += 128) {
+            const int r = A_KM ? (u % kGmM) : (u / (kGmK / 8)), g = A_KM ? (u / kGmM) : (u % (kGmK / 8));
+            float v[8];
+            gm_load8<A_KM>(A, lda, m_blk + r, M, k0 + 8 * g, kend, v);
+            gm_store8<SPLIT_A>(a_hi, a_lo, tc_off(r, 8 * g, kGmM), v);
+        }
+        for (int u = tid; u < kGmN * (kGmK / 8); u += 128) {
+            const int r = B_KN ? (u % kGmN) : (u / (kGmK / 8)), g = B_KN ? (u / kGmN) : (u % (kGmK / 8));
+            float v[8];
+            gm_load8<B_KN>(B, ldb, n_blk + r, N, k0 + 8 * g, kend, v);
+            gm_store8<SPLIT_B>(b_hi, b_lo, tc_off(r, 8 * g, kGmN), v);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int row = m_blk + wm + mi * 16 + g + (r >= 2 ? 8 : 0);
-                const int col = n_blk + wn + ni * 8 + 2 * q + (r & 1);
-                if (row >= M || col >= N) continue;
-                const float v = acc[mi][ni][r];
-                float* dst = Cm + (size_t)row * ldc + col;
-                if (EPI == 0) *dst = v;
-                else if (EPI == 1) *dst = tanh_act(v + bias[col]);
-                else if (EPI == 2) *dst = v + bias[col];
-                else dst[(size_t)blockIdx.z * M * ldc] = v;
+            for (int st = 0; st < kGmK / 16; ++st) {   // K = 16 per MMA: two K groups
+                const uint64_t da = tc_desc(ah + (uint32_t)st * 2 * kGmM * 16, kGmM * 16, 128);
+                const uint64_t db = tc_desc(bh + (uint32_t)st * 2 * kGmN * 16, kGmN * 16, 128);
+                tc_mma(d_tmem, da, db, idesc, first && st == 0 ? 0u : 1u);
+                if (SPLIT_A) tc_mma(d_tmem, tc_desc(al + (uint32_t)st * 2 * kGmM * 16, kGmM * 16, 128), db, idesc, 1u);
+                if (SPLIT_B) tc_mma(d_tmem, da, tc_desc(bl + (uint32_t)st * 2 * kGmN * 16, kGmN * 16, 128), idesc, 1u);
             }
+            tc_commit(mb);
+        }
+        first = false;
+        const bool done = mbar_wait_bounded(mb, phase);
+        if (!done) abort_flag = 1;
+        __syncthreads();   // every thread has seen the completion (or the give-up) before refilling
+        if (abort_flag) break;
+        phase ^= 1u;
+        tc_fence_after();
+    }
+    if (abort_flag) {   // leave the accumulators alone; let the MMAs in flight finish
+        if (tid == 0) {
+            mbar_wait_bounded(mb, phase);
+            atomicOr(&g_tc_timeout, 1u);
+        }
+    } else if (kbeg < kend) {
+        const uint32_t t_lane = d_tmem + ((uint32_t)(warp * 32) << 16);
+        const int row = m_blk + warp * 32 + lane;
+#pragma unroll 1
+        for (int c = 0; c < kGmN / 16; ++c) {
+            float v[16];
+            tc_ld16(t_lane + (uint32_t)(16 * c), v);
+            if (row >= M) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = n_blk + 16 * c + j;
+                if (col >= N) continue;
+                float* dst = Cm + (size_t)row * ldc + col;
+                if (EPI == 0) *dst = v[j];
+                else if (EPI == 1) *dst = tanh_act(v[j] + bias[col]);
+                else if (EPI == 2) *dst = v[j] + bias[col];
+                else dst[(size_t)blockIdx.z * M * ldc] = v[j];
+            }
+        }
+    } else if (EPI == 3) {   // an empty K slice contributes zeros
+        for (int i = tid; i < kGmM * kGmN; i += 128) {
+            const int row = m_blk + i / kGmN, col = n_blk + i % kGmN;
+            if (row < M && col < N) Cm[(size_t)blockIdx.z * M * ldc + (size_t)row * ldc + col] = 0.0f;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kGmN) : "memory");
+    }
 }
 
 template <bool A_KM, bool B_KN, bool SA, bool SB, int EPI>
 void gemm(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int M, int N, int K,
           const float* bias, cudaStream_t s, int splits = 1) {
+    // 48 KB of operand tiles (and a few bytes of static shared memory): at most four blocks
+    // per SM, 256 of the 512 tensor-memory columns
+    static int attr_device = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != attr_device) {
+        cudaFuncSetAttribute(gemm_kernel<A_KM, B_KN, SA, SB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGmSmem);
+        attr_device = dev;
+    }
     const int kchunk = ((K + splits - 1) / splits + 31) / 32 * 32;
-    dim3 grid((N + 63) / 64, (M + 63) / 64, (K + kchunk - 1) / kchunk);
-    gemm_kernel<A_KM, B_KN, SA, SB, EPI><<<grid, 128, 0, s>>>(A, lda, B, ldb, C, ldc, M, N, K, kchunk, bias);
+    dim3 grid((N + kGmN - 1) / kGmN, (M + kGmM - 1) / kGmM, (K + kchunk - 1) / kchunk);
+    gemm_kernel<A_KM, B_KN, SA, SB, EPI><<<grid, 128, kGmSmem, s>>>(A, lda, B, ldb, C, ldc, M, N, K, kchunk, bias);
 }
 
 // Layer 1 (3 inputs) on the CUDA cores: H1 = tanh(X W1^T + b1).

@@ -1,7 +1,6 @@
 // The refraction surrogate network: 3 -> 64 -> 64 -> 64 -> 3 with tanh,
 // BF16 weights on the tensor cores with FP32 accumulation.  Shared by the
-// training translation unit (warp-level mma.sync GEMMs) and the inference
-// (tcgen05, mlp_tc.cuh).
+// training translation unit and the inference (both on tcgen05, mlp_tc.cuh).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -104,16 +103,6 @@ const SurrogateView* surrogate_view(const cs_surrogate* s);
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&v);
-}
-
-// D += A B for one m16n8k16 tile (BF16 inputs, FP32 accumulation).
-__device__ __forceinline__ void mma_16816(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                          uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
 // tanh(x) = 1 - 2 / (exp(2x) + 1) from ex2 and rcp approximations: absolute
