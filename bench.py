@@ -549,7 +549,7 @@ def run_inclined(args):
     surrogate = None
     if not args.no_surrogate:
         t_tr = time.perf_counter()
-        sur = B.Surrogate(atm)
+        sur = B.Surrogate(atm, **({"epochs": args.surrogate_epochs} if args.surrogate_epochs else {}))
         train_s = time.perf_counter() - t_tr
         o.surrogate = sur.handle
         step()
@@ -700,6 +700,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--surrogate-epochs", type=int, default=0,
+                    help="train the surrogate for this many epochs (0: the library's default); a short "
+                         "training serves profiling runs of the surrogate kernel")
     ap.add_argument("--no-optics", action="store_true")
     ap.add_argument("--no-snell", action="store_true")
     ap.add_argument("--no-fluorescence", action="store_true")
@@ -826,7 +829,7 @@ def main():
     surrogate = None
     if not args.no_surrogate:
         t_tr = time.perf_counter()
-        sur = B.Surrogate(atm)
+        sur = B.Surrogate(atm, **({"epochs": args.surrogate_epochs} if args.surrogate_epochs else {}))
         train_s = time.perf_counter() - t_tr
         o.surrogate = sur.handle
         for _ in range(3):

@@ -149,11 +149,16 @@ __device__ __forceinline__ void sincos_2pi(float u, float& s, float& c) {
 __device__ __forceinline__ float delta_at(const AtmParams& a, float dz) {
     if (a.kind == CS_ATM_LAYERED) {
         if (dz >= a.top_rel) return 0.0f;
-        int i = 0;
+        // the layer's constants picked by selects over the unrolled layers (constant
+        // operands, no indexed parameter loads)
+        float D = a.lay_D[0], c2 = a.lay_c2[0];
 #pragma unroll
         for (int k = 1; k < kMaxLayers; ++k)
-            if (k < a.n_layers && dz >= a.lay_lo[k]) i = k;
-        return a.lay_D[i] * exp2f(a.lay_c2[i] * dz);
+            if (k < a.n_layers && dz >= a.lay_lo[k]) {
+                D = a.lay_D[k];
+                c2 = a.lay_c2[k];
+            }
+        return D * exp2f(c2 * dz);
     }
     if (a.kind == CS_ATM_LINEAR) return dz >= a.lin_top_rel ? a.lin_d1 : a.lin_d0 + a.lin_slope * dz;
     if (a.kind == CS_ATM_TABLE) {

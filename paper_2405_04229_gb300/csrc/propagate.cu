@@ -878,8 +878,10 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                 // arrival direction: n sin(theta) conserved, azimuth kept
                 const float sc = ap.refraction ? (1.0f + Q.z) * ap.inv_n_obs : 1.0f;
                 const float s2 = (ux * ux + uy * uy) * (sc * sc);
-                const bool hashed = s2 <= dp.hash[1].sin2_max;
-                const TelHash& H = dp.hash[s2 <= dp.hash[0].sin2_max ? 0 : 1];   // the narrowest hash that serves
+                // the narrowest hash that serves; when every active lane's arrival fits the
+                // first, its fields are constant operands (no indexed parameter loads)
+                const bool lvl0 = s2 <= dp.hash[0].sin2_max;
+                auto detect = [&](const TelHash& H, const bool hashed) {
                 if (!hashed || (x >= H.bx0 && x < H.bx1 && y >= H.by0 && y < H.by1)) {
                     float ugz = uz;
                     if (ap.refraction) {
@@ -909,6 +911,9 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                         pix = optics_survival(dp, pp, gid, k, i, inv_l, pix);
                     }
                 }
+                };
+                if (__all_sync(__activemask(), lvl0)) detect(dp.hash[0], true);
+                else detect(dp.hash[lvl0 ? 0 : 1], s2 <= dp.hash[1].sin2_max);
                 if (tel >= 0) {
                     const size_t slot = (size_t)sh * dp.n_tel + tel;
                     atomicAdd(op.tel_counts + slot, (unsigned long long)b);
@@ -981,8 +986,8 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                 const float ugx = ugc * erx - uga * ery, ugy = ugc * ery + uga * erx;
                 const float xs = x + xl, ys = y + yl;
                 const float sg2 = ugx * ugx + ugy * ugy;
-                const bool hashed = sg2 <= dp.hash[1].sin2_max;
-                const TelHash& H = dp.hash[sg2 <= dp.hash[0].sin2_max ? 0 : 1];
+                const bool lvl0 = sg2 <= dp.hash[0].sin2_max;
+                auto detect = [&](const TelHash& H, const bool hashed) {
                 if (!hashed || (xs >= H.bx0 && xs < H.bx1 && ys >= H.by0 && ys < H.by1)) {
                     tel = hit_telescope(
                         dp, H, hashed, xs, ys, ugx, ugy, ugz,
@@ -1006,6 +1011,9 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                         pix = optics_survival(dp, pp, gid, k, i, inv_l, pix);
                     }
                 }
+                };
+                if (__all_sync(__activemask(), lvl0)) detect(dp.hash[0], true);
+                else detect(dp.hash[lvl0 ? 0 : 1], sg2 <= dp.hash[1].sin2_max);
                 if (tel >= 0) {
                     const size_t slot = (size_t)sh * dp.n_tel + tel;
                     atomicAdd(op.tel_counts + slot, (unsigned long long)b);
@@ -1146,8 +1154,8 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                         ugz = -cos_g * (1.0f + gvz) + sin_g * tz;
                     }
                     const float sg2 = ugx * ugx + ugy * ugy;
-                    const bool hashed = sg2 <= dp.hash[1].sin2_max;
-                    const TelHash& H = dp.hash[sg2 <= dp.hash[0].sin2_max ? 0 : 1];
+                    const bool lvl0 = sg2 <= dp.hash[0].sin2_max;
+                    auto detect = [&](const TelHash& H, const bool hashed) {
                     if (!hashed || (xs >= H.bx0 && xs < H.bx1 && ys >= H.by0 && ys < H.by1)) {
                         auto delta3 = [&](const float4& T3, float& ddx, float& ddy, float& ddz) {
                             ddx = (T3.x - Gx) - Gxl;
@@ -1168,6 +1176,9 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                             pix = optics_survival(dp, pp, gid, k, i, inv_l, pix);
                         }
                     }
+                    };
+                    if (__all_sync(__activemask(), lvl0)) detect(dp.hash[0], true);
+                    else detect(dp.hash[lvl0 ? 0 : 1], sg2 <= dp.hash[1].sin2_max);
                     if (tel >= 0) {
                         const size_t slot = (size_t)sh * dp.n_tel + tel;
                         atomicAdd(op.tel_counts + slot, (unsigned long long)b);
@@ -1275,22 +1286,21 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                     gy -= pp.lv3_c[1];
                     key = fmaf(gx, gx, gy * gy);
                 }
-                // bitonic sort of (key, slot) across the warp, ascending
+                // bitonic sort across the warp, ascending, of one 32-bit word per lane: the
+                // key's bits (a non-negative float orders as an unsigned integer) with its low
+                // five bits replaced by the slot, so that words are distinct and carry the slot
+                unsigned int word = (__float_as_uint(key) & ~31u) | (unsigned int)lane;
 #pragma unroll
                 for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
                     for (int j = k >> 1; j > 0; j >>= 1) {
-                        const float ok = __shfl_xor_sync(0xffffffffu, key, j);
-                        const int os = __shfl_xor_sync(0xffffffffu, slot, j);
-                        const bool other_less = ok < key || (ok == key && os < slot);
+                        const unsigned int other = __shfl_xor_sync(0xffffffffu, word, j);
                         // the lower lane of an ascending pair keeps the smaller entry
                         const bool want_less = ((lane & k) == 0) == ((lane & j) == 0);
-                        if (other_less == want_less && os != slot) {
-                            key = ok;
-                            slot = os;
-                        }
+                        if ((other < word) == want_less) word = other;
                     }
                 }
+                slot = (int)(word & 31u);
             }
             const int Kt = __shfl_sync(0xffffffffu, Kt0, slot);
             W.perm[lane] = slot;
