@@ -330,10 +330,16 @@ __global__ void grad_w1_kernel(const float* __restrict__ dZ, const float* __rest
 }
 
 // Adam (bias-corrected) on the FP32 masters; keeps the padding at zero.
+// The step's learning rate and bias corrections come from the per-step
+// schedule {lr, 1 - 0.9^step, 1 - 0.999^step} at the device step counter, so
+// that one captured graph serves every step.
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                            float* __restrict__ v, float lr, float c1, float c2) {
+                            float* __restrict__ v, const float4* __restrict__ sched,
+                            const unsigned int* __restrict__ step_ctr) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= kNParams) return;
+    const float4 sc = sched[*step_ctr];
+    const float lr = sc.x, c1 = sc.y, c2 = sc.z;
     if ((i >= kOffW4 + kNOut * kHid && i < kOffB4) || i >= kOffB4 + kNOut) return;   // padding
     const float gi = g[i];
     const float mi = 0.9f * m[i] + 0.1f * gi, vi = 0.999f * v[i] + 0.001f * gi * gi;
@@ -448,9 +454,11 @@ __global__ void build_xt_kernel(const double2* __restrict__ hth, const double* _
 
 __global__ void gather_kernel(const float* __restrict__ X, const float* __restrict__ T,
                               const float* __restrict__ Wt, size_t n, int B, uint32_t key0, uint32_t key1,
-                              uint32_t step, float* __restrict__ Xb, float* __restrict__ Tb, float* __restrict__ Wb) {
+                              const unsigned int* __restrict__ step_ctr, float* __restrict__ Xb,
+                              float* __restrict__ Tb, float* __restrict__ Wb) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B) return;
+    const uint32_t step = *step_ctr + 1u;   // steps count from 1
     const uint4 r = philox((uint32_t)i, step, 0xB47Cu, 0u, key0, key1);
     const size_t j = (size_t)(((unsigned long long)r.x * (unsigned long long)n) >> 32);
     for (int k = 0; k < 3; ++k) {
@@ -459,6 +467,9 @@ __global__ void gather_kernel(const float* __restrict__ X, const float* __restri
         Wb[i * 3 + k] = Wt[j * 3 + k];
     }
 }
+
+// Advances the device step counter after a training step.
+__global__ void step_advance_kernel(unsigned int* step_ctr) { *step_ctr += 1u; }
 
 // One forward + backward pass of a batch; gradients accumulate into g.
 struct Work {
@@ -763,26 +774,80 @@ extern "C" cs_status cs_surrogate_train(const cs_atmosphere* atm, const cs_surro
     cudaMemset(m, 0, kNParams * 4);
     cudaMemset(v, 0, kNParams * 4);
     // ---- training -----------------------------------------------------------
+    // A training step is ~20 short launches (the GEMMs of a 32768-row batch take microseconds), so
+    // the steps run as captured CUDA graphs: the step's draws, learning rate and bias corrections
+    // are read on the device from a step counter and a per-step schedule, and the first step runs
+    // eagerly (it also sets the GEMMs' shared-memory attributes outside the capture).
     const int steps_per_epoch = (int)(nt / B);
     const int total = steps_per_epoch * cfg.epochs;
     double last_loss = 0.0;
-    for (int step = 1; step <= total; ++step) {
-        const double lr = cfg.lr_min + 0.5 * (cfg.lr - cfg.lr_min) * (1.0 + cos(kPi * (step - 1) / total));
-        gather_kernel<<<(B + 255) / 256, 256, 0, s>>>(X, T, Wt, nt, B, k0, k1, (uint32_t)step, Xb, Tb, Wb);
-        round_weights_kernel<<<(kNParams + 255) / 256, 256, 0, s>>>(p, pr);
-        cudaMemsetAsync(g, 0, kNParams * 4, s);
-        cudaMemsetAsync(w.loss, 0, 4, s);
-        forward(Xb, B, pr, w, s);
-        backward(Xb, Tb, Wb, B, pr, g, w, s);
-        const float c1 = (float)(1.0 - pow(0.9, step)), c2 = (float)(1.0 - pow(0.999, step));
-        adam_kernel<<<(kNParams + 255) / 256, 256, 0, s>>>(p, g, m, v, (float)lr, c1, c2);
-        if (step == total) {
+    {
+        std::vector<float4> hs((size_t)total);
+        for (int step = 1; step <= total; ++step) {
+            const double lr = cfg.lr_min + 0.5 * (cfg.lr - cfg.lr_min) * (1.0 + cos(kPi * (step - 1) / total));
+            hs[step - 1] = make_float4((float)lr, (float)(1.0 - pow(0.9, step)), (float)(1.0 - pow(0.999, step)), 0.0f);
+        }
+        float4* sched = (float4*)A(hs.size() * sizeof(float4));
+        unsigned int* step_ctr = (unsigned int*)A(sizeof(unsigned int));
+        if (!sched || !step_ctr) { cudaFree(d_base); cleanup(); return CS_ERR_CUDA; }
+        cudaMemcpy(sched, hs.data(), hs.size() * sizeof(float4), cudaMemcpyHostToDevice);
+        cudaMemset(step_ctr, 0, sizeof(unsigned int));
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+            set_last_error("surrogate training set-up", e);
+            cudaFree(d_base);
+            cleanup();
+            return CS_ERR_CUDA;
+        }
+        cudaStream_t ts = nullptr;
+        cudaGraph_t graphs[2] = {nullptr, nullptr};
+        cudaGraphExec_t execs[2] = {nullptr, nullptr};
+        auto enqueue_step = [&]() {
+            gather_kernel<<<(B + 255) / 256, 256, 0, ts>>>(X, T, Wt, nt, B, k0, k1, step_ctr, Xb, Tb, Wb);
+            round_weights_kernel<<<(kNParams + 255) / 256, 256, 0, ts>>>(p, pr);
+            cudaMemsetAsync(g, 0, kNParams * 4, ts);
+            cudaMemsetAsync(w.loss, 0, 4, ts);
+            forward(Xb, B, pr, w, ts);
+            backward(Xb, Tb, Wb, B, pr, g, w, ts);
+            adam_kernel<<<(kNParams + 255) / 256, 256, 0, ts>>>(p, g, m, v, sched, step_ctr);
+            step_advance_kernel<<<1, 1, 0, ts>>>(step_ctr);
+        };
+        constexpr int kStepsPerGraph = 16;
+        const int n_graph = std::min(kStepsPerGraph, std::max(total - 1, 1));
+        e = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
+        if (e == cudaSuccess) {
+            enqueue_step();   // step 1
+            e = cudaGetLastError();
+        }
+        // graph 0: n_graph steps; graph 1: one step (the remainder)
+        for (int gi = 0; gi < 2 && e == cudaSuccess && total > 1; ++gi) {
+            if ((e = cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
+            for (int k = 0; k < (gi == 0 ? n_graph : 1); ++k) enqueue_step();
+            const cudaError_t ec = cudaStreamEndCapture(ts, &graphs[gi]);
+            if ((e = cudaGetLastError()) != cudaSuccess || (e = ec) != cudaSuccess) break;
+            e = cudaGraphInstantiate(&execs[gi], graphs[gi], 0);
+        }
+        int done = 1;
+        while (e == cudaSuccess && total - done >= n_graph && total > 1) {
+            e = cudaGraphLaunch(execs[0], ts);
+            done += n_graph;
+        }
+        while (e == cudaSuccess && done < total) {
+            e = cudaGraphLaunch(execs[1], ts);
+            done += 1;
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ts);
+        if (e == cudaSuccess) {
             float l = 0.0f;
-            cudaMemcpy(&l, w.loss, 4, cudaMemcpyDeviceToHost);
+            e = cudaMemcpy(&l, w.loss, 4, cudaMemcpyDeviceToHost);   // the last step's loss
             last_loss = l;
         }
+        for (int gi = 0; gi < 2; ++gi) {
+            if (execs[gi]) cudaGraphExecDestroy(execs[gi]);
+            if (graphs[gi]) cudaGraphDestroy(graphs[gi]);
+        }
+        if (ts) cudaStreamDestroy(ts);
     }
-    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess) {
+    if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess) {
         set_last_error("surrogate training", e);
         cudaFree(d_base);
         cleanup();

@@ -27,7 +27,8 @@ struct TcSmem {
     static constexpr unsigned int kCols = 64 * NWG;
     __align__(128) unsigned char a[NWG][2][kTcATile];  // [warpgroup][hi, lo] activations
     __align__(128) unsigned char w[kTcWBytes];         // BF16 weights, core-matrix layout
-    float4 w1b[kHid];                                  // layer 1: {W1[u][0..2], b1[u]}
+    float4 w1p[kHid / 2][2];                           // layer 1, units 2i and 2i + 1 side by side:
+                                                       // {W1[.][0], W1[.][1]}, {W1[.][2], b1[.]}
     float4 b23[2][kHid / 4];                           // biases of layers 2 and 3
     float b4[4];
     unsigned long long mbar[NWG];                      // MMA completion, per warpgroup
@@ -202,8 +203,11 @@ __device__ __forceinline__ void tc_setup(TcSmem<NWG>& T, const SurrogateView& sv
         *reinterpret_cast<uint4*>(T.w + dst) = v;
     }
     const float* p = sv.p;
-    for (int u = t; u < kHid; u += blockDim.x)
-        T.w1b[u] = make_float4(p[kOffW1 + 3 * u], p[kOffW1 + 3 * u + 1], p[kOffW1 + 3 * u + 2], p[kOffB1 + u]);
+    for (int i = t; i < kHid / 2; i += blockDim.x) {
+        const int u = 2 * i, v = u + 1;
+        T.w1p[i][0] = make_float4(p[kOffW1 + 3 * u], p[kOffW1 + 3 * v], p[kOffW1 + 3 * u + 1], p[kOffW1 + 3 * v + 1]);
+        T.w1p[i][1] = make_float4(p[kOffW1 + 3 * u + 2], p[kOffW1 + 3 * v + 2], p[kOffB1 + u], p[kOffB1 + v]);
+    }
     for (int i = t; i < 2 * kHid; i += blockDim.x)
         reinterpret_cast<float*>(T.b23)[i] = p[(i < kHid ? kOffB2 : kOffB3 - kHid) + i];
     if (t < 4) T.b4[t] = t < kNOut ? p[kOffB4 + t] : 0.0f;
@@ -250,11 +254,20 @@ __device__ __forceinline__ bool net128_tc(const SurrogateView& sv, TcSmem<NWG>& 
 #pragma unroll 1
     for (int g = 0; g < 8; ++g) {
         float h[8];
+        // two units per packed FP32 instruction (the same fused operations in the same order)
+        const float2 x0 = make_float2(x[0], x[0]), x1 = make_float2(x[1], x[1]), x2 = make_float2(x[2], x[2]);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float4 w = T.w1b[8 * g + j];
-            h[j] = fmaf(w.z, x[2], fmaf(w.y, x[1], fmaf(w.x, x[0], w.w)));
-            if (SPLIT) h[j] = tanh_act(h[j]);
+        for (int j = 0; j < 8; j += 2) {
+            const float4 wa = T.w1p[(8 * g + j) >> 1][0], wb = T.w1p[(8 * g + j) >> 1][1];
+            float2 z = __ffma2_rn(make_float2(wa.x, wa.y), x0, make_float2(wb.z, wb.w));
+            z = __ffma2_rn(make_float2(wa.z, wa.w), x1, z);
+            z = __ffma2_rn(make_float2(wb.x, wb.y), x2, z);
+            h[j] = z.x;
+            h[j + 1] = z.y;
+        }
+        if (SPLIT) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) h[j] = tanh_act(h[j]);
         }
         if (SPLIT) tc_store8<true>(a_hi, a_lo, row, g, h);
         else tc_tanh_store8(a_hi, row, g, h);
@@ -296,16 +309,21 @@ __device__ __forceinline__ bool net128_tc(const SurrogateView& sv, TcSmem<NWG>& 
                 tc_ld16(t_lane + (uint32_t)(16 * c), v);
                 float h0[8], h1[8];
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
+                for (int q = 0; q < 2; ++q) {   // bias adds two per packed FP32 instruction
                     const float4 b0 = bias[4 * c + q], b1 = bias[4 * c + 2 + q];
-                    h0[4 * q + 0] = v[4 * q + 0] + b0.x;
-                    h0[4 * q + 1] = v[4 * q + 1] + b0.y;
-                    h0[4 * q + 2] = v[4 * q + 2] + b0.z;
-                    h0[4 * q + 3] = v[4 * q + 3] + b0.w;
-                    h1[4 * q + 0] = v[8 + 4 * q + 0] + b1.x;
-                    h1[4 * q + 1] = v[8 + 4 * q + 1] + b1.y;
-                    h1[4 * q + 2] = v[8 + 4 * q + 2] + b1.z;
-                    h1[4 * q + 3] = v[8 + 4 * q + 3] + b1.w;
+                    float2 z;
+                    z = __fadd2_rn(make_float2(v[4 * q + 0], v[4 * q + 1]), make_float2(b0.x, b0.y));
+                    h0[4 * q + 0] = z.x;
+                    h0[4 * q + 1] = z.y;
+                    z = __fadd2_rn(make_float2(v[4 * q + 2], v[4 * q + 3]), make_float2(b0.z, b0.w));
+                    h0[4 * q + 2] = z.x;
+                    h0[4 * q + 3] = z.y;
+                    z = __fadd2_rn(make_float2(v[8 + 4 * q + 0], v[8 + 4 * q + 1]), make_float2(b1.x, b1.y));
+                    h1[4 * q + 0] = z.x;
+                    h1[4 * q + 1] = z.y;
+                    z = __fadd2_rn(make_float2(v[8 + 4 * q + 2], v[8 + 4 * q + 3]), make_float2(b1.z, b1.w));
+                    h1[4 * q + 2] = z.x;
+                    h1[4 * q + 3] = z.y;
                 }
                 if (SPLIT) {
 #pragma unroll

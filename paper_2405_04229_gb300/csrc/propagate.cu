@@ -642,14 +642,14 @@ __device__ __forceinline__ float transmission_T(const AtmParams& ap, float GX, f
 // The correction fields at (dz, tan^2 of the local zenith) and the
 // transmission: the network's outputs where it applies, else the bilinear
 // table lookup; (0, 0, 1) without tables.
-template <bool SURR>
+template <bool SURR, bool FIX = false>
 __device__ __forceinline__ void correction_fields(const AtmParams& ap, bool use_net, const float (&net)[3], float dz,
                                                   float w, float inv_l, float inv_uz, float& GR, float& Gt,
                                                   float& Tr) {
     GR = 0.0f;
     Gt = 0.0f;
     Tr = 1.0f;
-    if (!ap.use_tables) return;
+    if (!(FIX || ap.use_tables)) return;
     if (SURR && use_net) {
         GR = net[0];
         Gt = net[1];
@@ -669,13 +669,13 @@ __device__ __forceinline__ void correction_fields(const AtmParams& ap, bool use_
                                      __fmul2_rn(gg, __ffma2_rn(ff, make_float2(s1.x, s1.y), make_float2(v1.x, v1.y))));
         GR = rt.x;
         Gt = rt.y;
-        if (ap.transmission) {
+        if (FIX || ap.transmission) {
             const float2 xa = __ffma2_rn(aa, __ffma2_rn(ff, make_float2(s0.z, s0.w), make_float2(v0.z, v0.w)),
                                          __fmul2_rn(gg, __ffma2_rn(ff, make_float2(s1.z, s1.w), make_float2(v1.z, v1.w))));
             Tr = transmission_T(ap, xa.x, xa.y, inv_l, inv_uz);
         }
     }
-    if (!ap.transmission) Tr = 1.0f;
+    if (!(FIX || ap.transmission)) Tr = 1.0f;
 }
 
 // Stages 3-5 for one bunch: generation on the cone (Sec. 4.2), the upward
@@ -692,11 +692,18 @@ __device__ __forceinline__ void correction_fields(const AtmParams& ap, bool use_
 // beyond the tables; MODE 2 (the exact pass) propagates it along the exact
 // path and counts it.
 enum { kModeMain = 0, kModeCheck = 1, kModeExact = 2 };
-template <bool SURR, bool SPH, bool REC, bool FL, bool TR, int MODE = kModeMain, typename SM>
+template <bool SURR, bool SPH, bool REC, bool FL, bool TR, int MODE = kModeMain, bool FIX = false, typename SM>
 __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, long long base,
                                       const PropParams& pp, const AtmParams& ap, const DetParams& dp,
                                       const OutParams& op, const SurrogateView& sv, TcSmem<kThreadsSur / 128>* tcs,
                                       Tally& T) {
+    // The launch configuration; FIX instances are launched only for the standard one (refraction,
+    // transmission and tables on; histogram, telescopes and time sums on; no LV3 filter and no
+    // camera optics), where these are compile-time constants instead of parameter tests.
+    static_assert(!(FIX && (SURR || FL || TR || MODE != kModeMain)), "the fixed configuration is the exact tracer's");
+    const bool c_refr = FIX || ap.refraction, c_trans = FIX || ap.transmission, c_tables = FIX || ap.use_tables;
+    const bool c_lv3 = !FIX && pp.lv3, c_cam = !FIX && dp.cam_n > 0, c_hist = FIX || dp.nx > 0;
+    const bool c_tel = FIX || dp.n_tel > 0, c_time = FIX || op.tel_time != nullptr;
     // ---- generation ------------------------------------------------------------
     const float4 Q = S.sub[q];
     const int segk = __float_as_int(Q.w);
@@ -764,7 +771,7 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
     else if (dz < 0.0f) status = CS_ST_BELOW;
     // beyond the correction tables (steeper than their largest zenith or above their
     // top): the exact path is integrated for this photon instead (Sec. 3.4.3)
-    const bool beyond = ap.use_tables && !(TR && ap.refraction) && (w > ap.tv.w_max || dz >= ap.tv.dz_max);
+    const bool beyond = c_tables && !(TR && c_refr) && (w > ap.tv.w_max || dz >= ap.tv.dz_max);
     if constexpr (MODE == kModeCheck) return status == CS_ST_LANDED && beyond;
     if constexpr (MODE == kModeMain && !SURR) {
         if (status == CS_ST_LANDED && beyond) return true;   // left to the exact pass
@@ -808,7 +815,7 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
             rx = ell * Px + dz * ux * inv_uz;
             ry = ell * Py + dz * uy * inv_uz;
         }
-        if (pp.lv3) {   // LV3 photon pre-filter (Sec. 4.3.4): the straight line's landing point
+        if (c_lv3) {   // LV3 photon pre-filter (Sec. 4.3.4): the straight line's landing point
             const float4 Cg = S.segC[sg];
             const float sx = (Cg.x - pp.lv3_c[0]) + (Cg.y + rx), sy = (Cg.z - pp.lv3_c[1]) + (Cg.w + ry);
             if (fmaf(sx, sx, fmaf(sy, sy, pp.lv3_dz2)) > pp.lv3_r2) status = CS_ST_LV3;
@@ -817,14 +824,14 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
     if (status == CS_ST_LANDED && !SPH) {
         float path = dz * inv_uz;
         float GR, Gt, Tr;
-        if (TR && ap.refraction) {   // the per-photon stepper instead of the tables
+        if (TR && c_refr) {   // the per-photon stepper instead of the tables
             const float4 sp = snell_path(ap, dz, cos_z, pp.snell_dh);
             const float2 r2 = __ffma2_rn(make_float2(sp.x, sp.x), uxy, make_float2(rx, ry));
             rx = r2.x;
             ry = r2.y;
             path = sp.y;
             Tr = 1.0f;
-            if (ap.transmission) {
+            if (c_trans) {
                 const float il2 = inv_l * inv_l;
                 const float kA = ap.kA0 * ex2_approx(ap.aer_alpha * lg2_approx(ap.lamA_nm * inv_l));
                 Tr = ex2_approx(-(sp.z * (ap.kR0 * il2 * il2) + sp.w * kA));
@@ -835,12 +842,12 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                 const float4 f = exact_fields_planar(ap.self, dz, cos_z, reach);
                 GR = f.x;
                 Gt = f.y;
-                Tr = ap.transmission ? transmission_T(ap, f.z, f.w, inv_l, inv_uz) : 1.0f;
+                Tr = c_trans ? transmission_T(ap, f.z, f.w, inv_l, inv_uz) : 1.0f;
                 if (!reach) status = CS_ST_NO_GROUND;   // reflected back up by an inverted profile
             } else {
-                correction_fields<SURR>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
+                correction_fields<SURR, FIX>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
             }
-            if (ap.refraction) {
+            if (c_refr) {
                 const float c3 = GR * inv_uz * inv_uz * inv_uz;
                 const float2 r2 = __ffma2_rn(make_float2(c3, c3), uxy, make_float2(rx, ry));
                 rx = r2.x;
@@ -861,11 +868,11 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
         }
         if (status != CS_ST_LANDED) {
             // the path never meets the observation level: missed
-        } else if (ap.transmission && !(u3 < Tr)) {
+        } else if (c_trans && !(u3 < Tr)) {
             status = CS_ST_ABSORBED;
         } else {
             const int sh = S.shower[sg];
-            if (dp.nx > 0) {   // ground cell = floor(G_cells + r / d); rounding < 3e-5 cells
+            if (c_hist) {   // ground cell = floor(G_cells + r / d); rounding < 3e-5 cells
                 const float4 D = S.segD[sg];
                 const int ix = (int)floorf(D.x + fmaf(rx, dp.inv_dx, D.y));
                 const int iy = (int)floorf(D.z + fmaf(ry, dp.inv_dy, D.w));
@@ -874,9 +881,9 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                     hist_add(op, (unsigned int)(sh * dp.ny * dp.nx + bin), b);
                 }
             }
-            if (dp.n_tel > 0) {
+            if (c_tel) {
                 // arrival direction: n sin(theta) conserved, azimuth kept
-                const float sc = ap.refraction ? (1.0f + Q.z) * ap.inv_n_obs : 1.0f;
+                const float sc = c_refr ? (1.0f + Q.z) * ap.inv_n_obs : 1.0f;
                 const float s2 = (ux * ux + uy * uy) * (sc * sc);
                 // the narrowest hash that serves; when every active lane's arrival fits the
                 // first, its fields are constant operands (no indexed parameter loads)
@@ -884,7 +891,7 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                 auto detect = [&](const TelHash& H, const bool hashed) {
                 if (!hashed || (x >= H.bx0 && x < H.bx1 && y >= H.by0 && y < H.by1)) {
                     float ugz = uz;
-                    if (ap.refraction) {
+                    if (c_refr) {
                         const float c2 = fmaxf(1.0f - s2, 1e-30f);
                         ugz = -c2 * rsqrtf(c2);
                     }
@@ -903,7 +910,7 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                             ddz = T4.z;
                             r = T4.w;
                         });
-                    if (tel >= 0 && dp.cam_n > 0) {
+                    if (tel >= 0 && c_cam) {
                         const float4 T4 = __ldg(dp.tel + tel);
                         const float2 TL = __ldg(dp.tel_lo + tel);
                         pix = camera_pixel(dp, (T4.x - Cg.x) + ((TL.x - Cg.y) - rx),
@@ -917,7 +924,7 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                 if (tel >= 0) {
                     const size_t slot = (size_t)sh * dp.n_tel + tel;
                     atomicAdd(op.tel_counts + slot, (unsigned long long)b);
-                    if (op.tel_time) atomicAdd(op.tel_time + slot, (double)b * (S.t0[sg] + (double)t_rel));
+                    if (c_time) atomicAdd(op.tel_time + slot, (double)b * (S.t0[sg] + (double)t_rel));
                     if (pix >= 0) atomicAdd(op.camera + (slot * dp.cam_n * dp.cam_n + pix), (unsigned long long)b);
                 }
             }
@@ -959,18 +966,18 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
         two_sum(y, yl, y, yl);
         t_rel = fmaf(cp.ct, kInvC, t_rel);
         float Tr = 1.0f;
-        if (ap.transmission) {
+        if (c_trans) {
             const float il2 = inv_l * inv_l;
             const float kA = ap.kA0 * ex2_approx(ap.aer_alpha * lg2_approx(ap.lamA_nm * inv_l));
             Tr = ex2_approx(-(cp.X * (ap.kR0 * il2 * il2) + cp.A * kA));
         }
         if (status != CS_ST_LANDED) {
             // turned above the ground: missed
-        } else if (ap.transmission && !(u3 < Tr)) {
+        } else if (c_trans && !(u3 < Tr)) {
             status = CS_ST_ABSORBED;
         } else {
             const int sh = S.shower[sg];
-            if (dp.nx > 0) {
+            if (c_hist) {
                 const int ix = (int)floorf(((x - dp.hx0_hi) + (xl - dp.hx0_lo)) * dp.inv_dx);
                 const int iy = (int)floorf(((y - dp.hy0_hi) + (yl - dp.hy0_lo)) * dp.inv_dy);
                 if (ix >= 0 && ix < dp.nx && iy >= 0 && iy < dp.ny) {
@@ -978,9 +985,9 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                     hist_add(op, (unsigned int)(sh * dp.ny * dp.nx + bin), b);
                 }
             }
-            if (dp.n_tel > 0) {
+            if (c_tel) {
                 // arrival direction in the unrolled frame: n u_a and n rho u_chi conserved
-                const float ratio = ap.refraction ? (1.0f + delta_at(ap, dz)) * ap.inv_n_obs : 1.0f;   // n_e / n_g
+                const float ratio = c_refr ? (1.0f + delta_at(ap, dz)) * ap.inv_n_obs : 1.0f;   // n_e / n_g
                 const float uga = ratio * ua, ugc = ratio * fmaf(dz, irg, 1.0f) * uchi;
                 const float ugz = -sqrtf(fmaxf(1.0f - uga * uga - ugc * ugc, 0.0f));
                 const float ugx = ugc * erx - uga * ery, ugy = ugc * ery + uga * erx;
@@ -1004,7 +1011,7 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                             ddz = T4.z;
                             r = T4.w;
                         });
-                    if (tel >= 0 && dp.cam_n > 0) {
+                    if (tel >= 0 && c_cam) {
                         const float4 T4 = __ldg(dp.tel + tel);
                         const float2 TL = __ldg(dp.tel_lo + tel);
                         pix = camera_pixel(dp, (T4.x - x) + (TL.x - xl), (T4.y - y) + (TL.y - yl), T4.z, ugx, ugy, ugz);
@@ -1017,7 +1024,7 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                 if (tel >= 0) {
                     const size_t slot = (size_t)sh * dp.n_tel + tel;
                     atomicAdd(op.tel_counts + slot, (unsigned long long)b);
-                    if (op.tel_time) atomicAdd(op.tel_time + slot, (double)b * (S.t0[sg] + (double)t_rel));
+                    if (c_time) atomicAdd(op.tel_time + slot, (double)b * (S.t0[sg] + (double)t_rel));
                     if (pix >= 0) atomicAdd(op.camera + (slot * dp.cam_n * dp.cam_n + pix), (unsigned long long)b);
                 }
             }
@@ -1039,12 +1046,12 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
             two_sum(Cc.z, Dd.z + oz, Gz, Gzl);
         };
         set_G(fmaf(ell, Px, tt * ux), fmaf(ell, Py, tt * uy), fmaf(ell, Pz, tt * uz));
-        if (pp.lv3) {   // LV3 photon pre-filter (Sec. 4.3.4): the straight line's landing point
+        if (c_lv3) {   // LV3 photon pre-filter (Sec. 4.3.4): the straight line's landing point
             const float sx = Gx - pp.lv3_c[0], sy = Gy - pp.lv3_c[1], sz = Gz - pp.lv3_c[2];
             if (fmaf(sx, sx, fmaf(sy, sy, sz * sz)) > pp.lv3_r2) status = CS_ST_LV3;
         }
         float GR = 0.0f, Gt = 0.0f, Tr = 1.0f;
-        const bool stepper = TR && ap.refraction;
+        const bool stepper = TR && c_refr;
         bool direct = false;   // landing point from the path's central angle
         // G = E + (r_g cos Phi - r_e) v_E + r_g sin Phi h_E, with
         // r_g cos Phi - r_e = -(dz + 2 r_g sin^2(Phi / 2)) and h_E = (u + cos v_E) / sin
@@ -1064,7 +1071,7 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
         // below the top of the atmosphere) it always does; straight lines, the stepper and
         // photons beyond the tables are checked.
         if (status == CS_ST_LANDED) {
-            if (!ap.refraction) {   // the straight line: r_g > r_e sin(psi) <=> r_e (1 - sin) > dz
+            if (!c_refr) {   // the straight line: r_g > r_e sin(psi) <=> r_e (1 - sin) > dz
                 const float s0 = sqrtf(sin2);
                 if (!(fmaf(re, cos_z * cos_z / (1.0f + s0), -dz) > 0.0f)) status = CS_ST_NO_GROUND;
             } else if ((stepper || (MODE == kModeExact && beyond)) && !sph_reaches(ap.self, dz, cos_z, sqrtf(sin2))) {
@@ -1082,21 +1089,21 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                     land_at(sp.x * ap.inv_rg);
                 }
                 Tr = 1.0f;
-                if (ap.transmission) {
+                if (c_trans) {
                     const float il2 = inv_l * inv_l;
                     const float kA = ap.kA0 * ex2_approx(ap.aer_alpha * lg2_approx(ap.lamA_nm * inv_l));
                     Tr = ex2_approx(-(sp.z * (ap.kR0 * il2 * il2) + sp.w * kA));
                 }
             } else if (MODE == kModeExact && beyond) {   // the exact path, integrated for this photon
                 const float4 f = exact_fields_sph(ap.self, dz, cos_z, sqrtf(sin2));
-                Tr = ap.transmission ? transmission_T(ap, f.z, f.w, inv_l, inv_uz) : 1.0f;
-                if (ap.refraction) {
+                Tr = c_trans ? transmission_T(ap, f.z, f.w, inv_l, inv_uz) : 1.0f;
+                if (c_refr) {
                     direct = true;
                     land_at(f.x);
                     Gt = f.y;   // c t_path itself
                 }
             } else {
-                correction_fields<SURR>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
+                correction_fields<SURR, FIX>(ap, use_net, net, dz, w, inv_l, inv_uz, GR, Gt, Tr);
             }
         }
         if (status == CS_ST_LANDED) {
@@ -1110,7 +1117,7 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
             ty *= tn;
             tz *= tn;
             float path = direct ? Gt : tt;
-            if (ap.refraction && !direct) {   // arc-length correction along the ground, delay
+            if (c_refr && !direct) {   // arc-length correction along the ground, delay
                 const float dR = stepper ? GR : GR * inv_uz * inv_uz * inv_uz * sqrtf(sin2);
                 Gxl = fmaf(dR, tx, Gxl);
                 Gyl = fmaf(dR, ty, Gyl);
@@ -1132,11 +1139,11 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
             y = Gy;
             yl = fmaf(-Gy, om, Gyl);
             const float xs = x + xl, ys = y + yl;   // single floats for the box and hash tests
-            if (ap.transmission && !(u3 < Tr)) {
+            if (c_trans && !(u3 < Tr)) {
                 status = CS_ST_ABSORBED;
             } else {
                 const int sh = S.shower[sg];
-                if (dp.nx > 0) {
+                if (c_hist) {
                     const int ix = (int)floorf(((x - dp.hx0_hi) + (xl - dp.hx0_lo)) * dp.inv_dx);
                     const int iy = (int)floorf(((y - dp.hy0_hi) + (yl - dp.hy0_lo)) * dp.inv_dy);
                     if (ix >= 0 && ix < dp.nx && iy >= 0 && iy < dp.ny) {
@@ -1144,9 +1151,9 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                         hist_add(op, (unsigned int)(sh * dp.ny * dp.nx + bin), b);
                     }
                 }
-                if (dp.n_tel > 0) {
+                if (c_tel) {
                     float ugx = ux, ugy = uy, ugz = uz;
-                    if (ap.refraction) {   // Bouguer: n r sin(psi) conserved in the plane of travel
+                    if (c_refr) {   // Bouguer: n r sin(psi) conserved in the plane of travel
                         const float sin_g = (1.0f + Q.z) * ap.inv_n_obs * re * irg * sqrtf(sin2);
                         const float cos_g = sqrtf(fmaxf(1.0f - sin_g * sin_g, 0.0f));
                         ugx = -cos_g * gvx + sin_g * tx;
@@ -1170,7 +1177,7 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                                 delta3(T3, ddx, ddy, ddz);
                                 r = T3.w;
                             });
-                        if (tel >= 0 && dp.cam_n > 0) {
+                        if (tel >= 0 && c_cam) {
                             const float4 T3 = __ldg(dp.tel3 + tel);
                             pix = camera_pixel(dp, (T3.x - Gx) - Gxl, (T3.y - Gy) - Gyl, (T3.z - Gz) - Gzl, ugx, ugy, ugz);
                             pix = optics_survival(dp, pp, gid, k, i, inv_l, pix);
@@ -1182,7 +1189,7 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                     if (tel >= 0) {
                         const size_t slot = (size_t)sh * dp.n_tel + tel;
                         atomicAdd(op.tel_counts + slot, (unsigned long long)b);
-                        if (op.tel_time) atomicAdd(op.tel_time + slot, (double)b * (S.t0[sg] + (double)t_rel));
+                        if (c_time) atomicAdd(op.tel_time + slot, (double)b * (S.t0[sg] + (double)t_rel));
                         if (pix >= 0) atomicAdd(op.camera + (slot * dp.cam_n * dp.cam_n + pix), (unsigned long long)b);
                     }
                 }
@@ -1230,11 +1237,17 @@ __device__ __forceinline__ void mark_group(unsigned int* scratch, long long n_wt
 // bunches of the others from their keyed draws, and propagates the bunches
 // beyond the tables along the exact path, 32 at a time per warp.
 template <bool SURR, bool SPH, int MINB, bool REC, bool FL = false, bool TR = false, bool EX = false,
-          int NT = SURR ? kThreadsSur : kThreads>
+          bool FIX = false, int NT = SURR ? kThreadsSur : kThreads>
 __global__ void __launch_bounds__(NT, MINB)
 propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, const OutParams op,
                  unsigned int* scratch, const SurrogateView sv) {
     static_assert(!(EX && SURR), "the exact pass runs the exact-tracer form");
+    // The exact pass is launched as a programmatic dependent of the photon kernel: its blocks
+    // become resident as the photon kernel's retire and wait here for its completion (and its
+    // memory); the photon kernel lets it launch from the start.  Without the launch attribute
+    // both instructions are no-ops.
+    if (EX) asm volatile("griddepcontrol.wait;" ::: "memory");
+    else asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (EX && __ldcg(scratch + 2) == 0) return;   // no tile holds a bunch beyond the tables
     unsigned int* const tile_ctr = scratch + (EX ? 1 : 0);
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1363,7 +1376,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                     if constexpr (!EX) {
                         for (int p = lane; p < wn; p += 32) {
                             const unsigned int e = W.map[p];
-                            any_beyond |= bunch<false, SPH, REC, FL, TR>(W, (int)(e & ((1u << kQBits) - 1)),
+                            any_beyond |= bunch<false, SPH, REC, FL, TR, kModeMain, FIX>(W, (int)(e & ((1u << kQBits) - 1)),
                                                                          (int)(e >> kQBits), true, base, pp, ap, dp,
                                                                          op, sv, tcs, T);
                         }
@@ -1569,8 +1582,19 @@ cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp
     auto go = [&](auto kernel, int threads) { kernel<<<grid, threads, smem, stream>>>(pp, ap, dp, op, ctr, sv); };
     const bool rec = op.records != nullptr;
     // the exact tracer's instances: emission (Cherenkov or fluorescence) x tracer (tables or stepper)
+    // the standard configuration (refraction, transmission and tables; histogram, telescopes and
+    // time sums; no LV3 filter, no camera optics) has its own instances, with those tests folded
+    const bool fix = ap.refraction && ap.transmission && ap.use_tables && !pp.lv3 && dp.cam_n == 0 && dp.nx > 0 &&
+                     dp.n_tel > 0 && op.tel_time != nullptr;
     auto exact = [&](auto sph, auto fl, auto tr) {
         constexpr bool S = decltype(sph)::value, F = decltype(fl)::value, T = decltype(tr)::value;
+        if constexpr (!F && !T) {
+            if (fix) {
+                rec ? go(propagate_kernel<false, S, 4, true, false, false, false, true>, kThreads)
+                    : go(propagate_kernel<false, S, 4, false, false, false, false, true>, kThreads);
+                return;
+            }
+        }
         rec ? go(propagate_kernel<false, S, 4, true, F, T>, kThreads) : go(propagate_kernel<false, S, 4, false, F, T>, kThreads);
     };
     using t_ = std::true_type;
@@ -1592,7 +1616,30 @@ cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp
     if (ap.use_tables && !(tr && ap.refraction)) {
         const long long n_wtiles = (pp.n + kWTile - 1) / kWTile;
         const unsigned grid_x = (unsigned)std::max<long long>(1, std::min<long long>(n_wtiles, (long long)device_sm_count() * 4));
-        auto pass = [&](auto kernel) { kernel<<<grid_x, kThreads, kSmemExact, stream>>>(pp, ap, dp, op, ctr, sv); };
+        // outside a stream capture, as a programmatic dependent launch (it overlaps the photon
+        // kernel's tail: for most workloads the pass finds nothing to do)
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        CS_CUDA_TRY(cudaStreamIsCapturing(stream, &cap));
+        auto pass = [&](auto kernel) {
+            if (cap != cudaStreamCaptureStatusNone) {
+                kernel<<<grid_x, kThreads, kSmemExact, stream>>>(pp, ap, dp, op, ctr, sv);
+                return;
+            }
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(grid_x);
+            cfg.blockDim = dim3(kThreads);
+            cfg.dynamicSmemBytes = kSmemExact;
+            cfg.stream = stream;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            if (cudaLaunchKernelEx(&cfg, kernel, pp, ap, dp, op, ctr, sv) != cudaSuccess) {
+                cudaGetLastError();   // the attribute refused: an ordinary stream-ordered launch
+                kernel<<<grid_x, kThreads, kSmemExact, stream>>>(pp, ap, dp, op, ctr, sv);
+            }
+        };
         if (ap.spherical) {
             if (fl) rec ? pass(propagate_kernel<false, true, 4, true, true, false, true>) : pass(propagate_kernel<false, true, 4, false, true, false, true>);
             else rec ? pass(propagate_kernel<false, true, 4, true, false, false, true>) : pass(propagate_kernel<false, true, 4, false, false, false, true>);
@@ -1613,6 +1660,10 @@ cudaError_t set_exact_smem(int smem) {
     if (!T) {   // the exact pass of the table-tracer instances
         if (e == cudaSuccess) e = cudaFuncSetAttribute(propagate_kernel<false, S, 4, false, F, false, true>, attr, smem);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(propagate_kernel<false, S, 4, true, F, false, true>, attr, smem);
+    }
+    if (!T && !F) {   // the fixed-configuration instances
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(propagate_kernel<false, S, 4, false, false, false, false, true>, attr, smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(propagate_kernel<false, S, 4, true, false, false, false, true>, attr, smem);
     }
     return e;
 }
