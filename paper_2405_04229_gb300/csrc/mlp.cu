@@ -265,15 +265,27 @@ __global__ void loss_grad_kernel(const float* __restrict__ Y, const float* __res
     }
 }
 
-// out[j] = sum over r = 0 .. rows - 1 of part[r * stride + j], in row order
-// (deterministic); one thread per column j < width.
-__global__ void sum_rows_kernel(const float* __restrict__ part, int rows, int stride, int width,
-                                float* __restrict__ out) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= width) return;
-    float t = 0.0f;
-    for (int r = 0; r < rows; ++r) t += part[(size_t)r * stride + j];
-    out[j] = t;
+// out[j] = sum over r = 0 .. rows - 1 of part[r * stride + j]; one block of
+// kSumThreads per column j = blockIdx.x: thread t adds rows t, t + kSumThreads,
+// ... in order, then a fixed pairwise tree over the threads (deterministic).
+constexpr int kSumThreads = 128;
+__global__ void __launch_bounds__(kSumThreads) sum_rows_kernel(const float* __restrict__ part, int rows, int stride,
+                                                               float* __restrict__ out) {
+    __shared__ float red[kSumThreads];
+    const int j = blockIdx.x, t = threadIdx.x;
+    float acc = 0.0f;
+    for (int r = t; r < rows; r += kSumThreads) acc += part[(size_t)r * stride + j];
+    red[t] = acc;
+    __syncthreads();
+#pragma unroll
+    for (int h = kSumThreads / 2; h > 0; h >>= 1) {
+        if (t < h) red[t] += red[t + h];
+        __syncthreads();
+    }
+    if (t == 0) out[j] = red[0];
+}
+void sum_rows(const float* part, int rows, int stride, int width, float* out, cudaStream_t s) {
+    sum_rows_kernel<<<width, kSumThreads, 0, s>>>(part, rows, stride, out);
 }
 
 // Sum of the split-K slices of a gradient GEMM into dst (leading dimension ldc).
@@ -305,28 +317,26 @@ __global__ void tanh_back_kernel(const float* __restrict__ dH, const float* __re
     if (threadIdx.x < 64) bpart[blockIdx.x * 64 + u] = (red[0][u] + red[1][u]) + (red[2][u] + red[3][u]);
 }
 
-__global__ void grad_w1_kernel(const float* __restrict__ dZ, const float* __restrict__ X, int B, float* __restrict__ grad) {
-    __shared__ float red[8][kNIn];
-    const int u = blockIdx.x;
-    float s[kNIn] = {0.0f, 0.0f, 0.0f};
-    for (int r = threadIdx.x; r < B; r += blockDim.x) {
+// Layer-1 weight gradient, stage 1: block b sums dZ[r][u] x[r][c] over its 256
+// rows r (reads of dZ coalesced along u) into part[b][u * 3 + c]; stage 2 is
+// sum_rows over the blocks.
+constexpr int kW1Rows = 256;
+__global__ void __launch_bounds__(256) grad_w1_part_kernel(const float* __restrict__ dZ, const float* __restrict__ X,
+                                                            int B, float* __restrict__ part) {
+    __shared__ float red[4][kHid * kNIn];
+    const int u = threadIdx.x & (kHid - 1), q = threadIdx.x >> 6;   // 4 row phases x 64 units
+    const int r0 = blockIdx.x * kW1Rows, r1 = min(B, r0 + kW1Rows);
+    float acc[kNIn] = {0.0f, 0.0f, 0.0f};
+    for (int r = r0 + q; r < r1; r += 4) {
         const float z = dZ[(size_t)r * kHid + u];
 #pragma unroll
-        for (int c = 0; c < kNIn; ++c) s[c] += z * X[(size_t)r * kNIn + c];
+        for (int c = 0; c < kNIn; ++c) acc[c] = fmaf(z, X[(size_t)r * kNIn + c], acc[c]);
     }
 #pragma unroll
-    for (int c = 0; c < kNIn; ++c) {
-        float v = s[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][c] = v;
-    }
+    for (int c = 0; c < kNIn; ++c) red[q][u * kNIn + c] = acc[c];
     __syncthreads();
-    if (threadIdx.x < kNIn) {
-        float t = 0.0f;
-        for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) t += red[wi][threadIdx.x];
-        grad[kOffW1 + u * kNIn + threadIdx.x] = t;
-    }
+    for (int j = threadIdx.x; j < kHid * kNIn; j += blockDim.x)
+        part[(size_t)blockIdx.x * (kHid * kNIn) + j] = (red[0][j] + red[1][j]) + (red[2][j] + red[3][j]);
 }
 
 // Adam (bias-corrected) on the FP32 masters; keeps the padding at zero.
@@ -478,9 +488,12 @@ struct Work {
     float* part;   // reduction scratch, work_part_floats(B)
 };
 
-int grad_splits(int B) { return std::max(1, B / 2048); }
+// split-K slices of the weight-gradient GEMMs: 128 rows of the batch each, so that a 32768-row
+// batch keeps 256 blocks busy (the output tile is a single 64 x 64 one)
+int grad_splits(int B) { return std::max(1, std::min(B / 128, 1024)); }
 size_t work_part_floats(int B) {
-    return (size_t)grad_splits(B) * kHid * kHid + (size_t)((B + 63) / 64) * 64 + (size_t)((B + 255) / 256) * 4;
+    return (size_t)grad_splits(B) * kHid * kHid + (size_t)((B + 63) / 64) * 64 + (size_t)((B + 255) / 256) * 4 +
+           (size_t)((B + kW1Rows - 1) / kW1Rows) * kHid * kNIn;
 }
 
 void forward(const float* X, int B, const float* pr, const Work& w, cudaStream_t s) {
@@ -501,10 +514,11 @@ void backward(const float* X, const float* T, const float* Wt, int B, const floa
         gemm<true, true, true, true, 3>(dOut, n_out, In, kHid, gpart, kHid, n_out, kHid, B, nullptr, s, splits);
         sum_slices_kernel<<<(n_out * kHid + 255) / 256, 256, 0, s>>>(gpart, splits, n_out, kHid, dst, kHid);
     };
-    auto bgrad = [&](float* dst) { sum_rows_kernel<<<1, 64, 0, s>>>(bpart, nb64, 64, 64, dst); };
+    float* w1part = lpart + (size_t)nb256 * 4;                 // per-block layer-1 weight-gradient partials
+    auto bgrad = [&](float* dst) { sum_rows(bpart, nb64, 64, 64, dst, s); };
     loss_grad_kernel<<<nb256, 256, 0, s>>>(w.Y, T, Wt, B, w.dY, lpart);
-    sum_rows_kernel<<<1, 32, 0, s>>>(lpart, nb256, 4, 1, w.loss);
-    sum_rows_kernel<<<1, 32, 0, s>>>(lpart + 1, nb256, 4, kNOut, g + kOffB4);
+    sum_rows(lpart, nb256, 4, 1, w.loss, s);
+    sum_rows(lpart + 1, nb256, 4, kNOut, g + kOffB4, s);
     // layer 4: dW4 = dY^T H3, dH3 = dY W4
     wgrad(w.dY, kNOutP, w.H3, g + kOffW4);
     gemm<false, true, true, false, 0>(w.dY, kNOutP, pr + kOffW4, kHid, w.dH, kHid, B, kHid, kNOutP, nullptr, s);
@@ -521,7 +535,9 @@ void backward(const float* X, const float* T, const float* Wt, int B, const floa
     tanh_back_kernel<<<nb64, 256, 0, s>>>(w.dH, w.H1, B, w.dZ, bpart);
     bgrad(g + kOffB1);
     // layer 1 (3 inputs)
-    grad_w1_kernel<<<kHid, 256, 0, s>>>(w.dZ, X, B, g);
+    const int nw1 = (B + kW1Rows - 1) / kW1Rows;
+    grad_w1_part_kernel<<<nw1, 256, 0, s>>>(w.dZ, X, B, w1part);
+    sum_rows(w1part, nw1, kHid * kNIn, kHid * kNIn, g + kOffW1, s);
 }
 
 cs_status alloc(void** p, size_t bytes) {
