@@ -154,6 +154,8 @@ struct PropParams {
     uint32_t fl_thr[8];
     uint32_t rk[20];   // Philox key schedule: round r uses rk[2r], rk[2r + 1]
     int tiles_per_bit; // warp tiles (32 segments) per bit of the exact pass's tile map
+    unsigned int q_cap; // entries of the exact pass's bunch queue (0: tile map only)
+    unsigned int q_off; // its offset in the scratch, in 32-bit words (a multiple of 4)
 };
 
 // The atmosphere in FP64, as the table builder integrates it.

@@ -129,7 +129,9 @@ __device__ __noinline__ float4 exact_fields_planar(const AtmParams* __restrict__
         const float xb = next_cut(ap, xa, dz);
         const float mid = 0.5f * (xa + xb), half = 0.5f * (xb - xa);
         const PieceLaw law = piece_law(ap, mid);
-#pragma unroll 1
+        // unrolled: the points' special-function chains overlap (a few photons beyond the
+        // tables leave one warp to integrate them, so latency, not issue, sets its time)
+#pragma unroll
         for (int g = 0; g < 16; ++g) {
             const float gx = c_gl16_x[g & 7], y = (g < 8) ? fmaf(-half, gx, mid) : fmaf(half, gx, mid);
             const float wt = half * c_gl16_w[g & 7];
@@ -198,7 +200,9 @@ __device__ __noinline__ float4 exact_fields_sph(const AtmParams* __restrict__ g,
         const float xb = next_cut(ap, xa, dz);
         const float mid = 0.5f * (xa + xb), half = 0.5f * (xb - xa);
         const PieceLaw law = piece_law(ap, mid);
-#pragma unroll 1
+        // unrolled: the points' special-function chains overlap (a few photons beyond the
+        // tables leave one warp to integrate them, so latency, not issue, sets its time)
+#pragma unroll
         for (int g = 0; g < 16; ++g) {
             const float gx = c_gl16_x[g & 7], y = (g < 8) ? fmaf(-half, gx, mid) : fmaf(half, gx, mid);
             const float wt = half * c_gl16_w[g & 7];

@@ -213,7 +213,9 @@ void gemm(const float* A, int lda, const float* B, int ldb, float* C, int ldc, i
         attr_device = dev;
     }
     const int kchunk = ((K + splits - 1) / splits + 31) / 32 * 32;
-    dim3 grid((N + kGmN - 1) / kGmN, (M + kGmM - 1) / kGmM, (K + kchunk - 1) / kchunk);
+    // split-K (EPI 3): exactly `splits` slices, so that the caller's fixed-order sum reads every one
+    // of them (a slice past K, when the rounding of kchunk leaves one, stores zeros)
+    dim3 grid((N + kGmN - 1) / kGmN, (M + kGmM - 1) / kGmM, EPI == 3 ? splits : (K + kchunk - 1) / kchunk);
     gemm_kernel<A_KM, B_KN, SA, SB, EPI><<<grid, 128, kGmSmem, s>>>(A, lda, B, ldb, C, ldc, M, N, K, kchunk, bias);
 }
 

@@ -193,7 +193,7 @@ __device__ __forceinline__ int substep_count(float L, float sh, float sl) {
 template <bool SPH, bool FL, typename SM>
 __device__ __forceinline__ int import_segment(SM& S, int t, const cs_segment* seg, const PropParams& pp,
                                               const AtmParams& ap, const DetParams& dp, unsigned int& invalid,
-                                              unsigned int& dropped) {
+                                              unsigned int& dropped, bool filter = true) {
     const double2* src = reinterpret_cast<const double2*>(seg);
     const double2 xy = __ldg(src), zt = __ldg(src + 1);
     const float4 dir = __ldg(reinterpret_cast<const float4*>(src + 2));
@@ -205,7 +205,7 @@ __device__ __forceinline__ int import_segment(SM& S, int t, const cs_segment* se
                        isfinite(dir.y) && isfinite(dir.z) && isfinite(dir.w) && dir.w > 0.0f && g > 0.0f &&
                        g < 1.0f && isfinite(z) && dir.z < 0.99f && fabsf(n2 - 1.0f) <= 1e-4f &&
                        shower < (unsigned int)dp.n_showers;
-    if (!valid) {
+    if (filter && !valid) {
         invalid += 1;
         return 0;
     }
@@ -233,7 +233,7 @@ __device__ __forceinline__ int import_segment(SM& S, int t, const cs_segment* se
         const float rr = sqrtf(rho2 + a * a);
         const float lift = rho2 / (rr + a);
         const float Hs = Hs_hi + (Hs_lo + lift);
-        if (pp.lv1 && lv1_drop<true>(pp, dp, x_hi, x_lo, y_hi, y_lo, z_hi, z_lo, Hs, Px, Py, Pz)) {
+        if (filter && pp.lv1 && lv1_drop<true>(pp, dp, x_hi, x_lo, y_hi, y_lo, z_hi, z_lo, Hs, Px, Py, Pz)) {
             dropped += 1;
             return 0;
         }
@@ -251,7 +251,7 @@ __device__ __forceinline__ int import_segment(SM& S, int t, const cs_segment* se
         S.bunch[t] = pp.shower_bunch ? __ldg(pp.shower_bunch + shower) : pp.bunch;
         return K;
     }
-    if (pp.lv1 && lv1_drop<false>(pp, dp, x_hi, x_lo, y_hi, y_lo, z_hi, z_lo, Hs_hi + Hs_lo, Px, Py, Pz)) {
+    if (filter && pp.lv1 && lv1_drop<false>(pp, dp, x_hi, x_lo, y_hi, y_lo, z_hi, z_lo, Hs_hi + Hs_lo, Px, Py, Pz)) {
         dropped += 1;
         return 0;
     }
@@ -1205,16 +1205,26 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
 }
 
 // Per-launch scratch (zeroed before the photon kernel): the photon kernel's
-// work counter, the exact pass's cursor, the number of listed groups and a
-// pad word; then one bit per group of pp.tiles_per_bit warp tiles (32
-// segments) that hold a bunch beyond the correction tables, and the list of
-// the marked groups (each entered once, when its bit is first set).
+// work counter, the exact pass's cursor, the number of listed groups and the
+// number of queued bunches; then one bit per group of pp.tiles_per_bit warp
+// tiles (32 segments) that hold a bunch beyond the correction tables the
+// queue could not take, the list of the marked groups (each entered once,
+// when its bit is first set), and the queue of bunches beyond the tables
+// ({segment index lo, hi, sub-step, bunch} per entry, 16-byte aligned).
 constexpr int kScratchCounters = 4;
 __host__ __device__ constexpr size_t scratch_groups(long long n_wtiles, int tiles_per_bit) {
     return (size_t)((n_wtiles + tiles_per_bit - 1) / tiles_per_bit);
 }
-__host__ __device__ constexpr size_t scratch_words(long long n_wtiles, int tiles_per_bit) {
-    return kScratchCounters + (scratch_groups(n_wtiles, tiles_per_bit) + 31) / 32 + scratch_groups(n_wtiles, tiles_per_bit);
+__host__ __device__ constexpr size_t scratch_queue_off(long long n_wtiles, int tiles_per_bit) {
+    return (kScratchCounters + (scratch_groups(n_wtiles, tiles_per_bit) + 31) / 32 + scratch_groups(n_wtiles, tiles_per_bit) +
+            3) & ~(size_t)3;
+}
+__host__ __device__ constexpr size_t scratch_words(long long n_wtiles, int tiles_per_bit, unsigned int q_cap = 0) {
+    return scratch_queue_off(n_wtiles, tiles_per_bit) + 4 * (size_t)q_cap;
+}
+// Queue entries for n_wtiles warp tiles: eight per tile, at most 2^22 (64 MB).
+__host__ __device__ constexpr unsigned int queue_cap(long long n_wtiles) {
+    return (unsigned int)(n_wtiles * 8 < (1ll << 22) ? (n_wtiles * 8 > 4096 ? n_wtiles * 8 : 4096) : (1ll << 22));
 }
 // The part that must start at zero: the counters and the map (the list is written before it is read).
 __host__ __device__ constexpr size_t scratch_zero_words(long long n_wtiles, int tiles_per_bit) {
@@ -1248,7 +1258,7 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
     // both instructions are no-ops.
     if (EX) asm volatile("griddepcontrol.wait;" ::: "memory");
     else asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    if (EX && __ldcg(scratch + 2) == 0) return;   // no tile holds a bunch beyond the tables
+    if (EX && __ldcg(scratch + 2) == 0 && __ldcg(scratch + 3) == 0) return;   // no bunch beyond the tables
     unsigned int* const tile_ctr = scratch + (EX ? 1 : 0);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
@@ -1376,9 +1386,30 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                     if constexpr (!EX) {
                         for (int p = lane; p < wn; p += 32) {
                             const unsigned int e = W.map[p];
-                            any_beyond |= bunch<false, SPH, REC, FL, TR, kModeMain, FIX>(W, (int)(e & ((1u << kQBits) - 1)),
-                                                                         (int)(e >> kQBits), true, base, pp, ap, dp,
-                                                                         op, sv, tcs, T);
+                            const int qs = (int)(e & ((1u << kQBits) - 1)), ib = (int)(e >> kQBits);
+                            const bool bey = bunch<false, SPH, REC, FL, TR, kModeMain, FIX>(W, qs, ib, true, base, pp, ap,
+                                                                                           dp, op, sv, tcs, T);
+                            // a bunch beyond the tables goes to the exact pass's queue (one
+                            // reservation per warp round); when the queue is full its tile is
+                            // marked, and the exact pass then skips the tile's queued entries
+                            const unsigned int am = __activemask(), m = __ballot_sync(am, bey);
+                            if (m) {
+                                const int leader = __ffs(am) - 1;
+                                unsigned int slot0 = 0;
+                                if (lane == leader) slot0 = pp.q_cap ? atomicAdd(scratch + 3, (unsigned int)__popc(m)) : 0xFFFFFFFFu;
+                                slot0 = __shfl_sync(am, slot0, leader);
+                                if (bey) {
+                                    const unsigned int slot = slot0 + (unsigned int)__popc(m & ((1u << lane) - 1u));
+                                    if (slot0 != 0xFFFFFFFFu && slot >= slot0 && slot < pp.q_cap) {
+                                        const int segk = __float_as_int(W.sub[qs].w);
+                                        const unsigned long long li = (unsigned long long)(base + (segk & ((1 << kKShift) - 1)));
+                                        reinterpret_cast<uint4*>(scratch + pp.q_off)[slot] =
+                                            make_uint4((uint32_t)li, (uint32_t)(li >> 32), (uint32_t)(segk >> kKShift), (uint32_t)ib);
+                                    } else {
+                                        any_beyond = true;
+                                    }
+                                }
+                            }
                         }
                     } else {
                         // rounds of 32 bunches: those beyond the tables are queued (in the map
@@ -1432,13 +1463,38 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                 process_tile(tile);
             }
         } else {
-            // the exact pass takes the marked groups from their list (none: nothing to do)
+            // the exact pass takes the queued bunches 32 at a time, then the marked groups
+            // from their list (the cursor runs over both)
             const unsigned int n_listed = __ldcg(scratch + 2);
-            const unsigned int* list = scratch + kScratchCounters + (scratch_groups(n_wtiles, pp.tiles_per_bit) + 31) / 32;
-            while (n_listed > 0) {
+            const unsigned int n_q = min(__ldcg(scratch + 3), pp.q_cap), n_qc = (n_q + 31) / 32;
+            const unsigned int* bits = scratch + kScratchCounters;
+            const unsigned int* list = bits + (scratch_groups(n_wtiles, pp.tiles_per_bit) + 31) / 32;
+            for (;;) {
                 unsigned int idx = 0;
                 if (lane == 0) idx = atomicAdd(tile_ctr, 1u);
                 idx = __shfl_sync(0xffffffffu, idx, 0);
+                if (idx < n_qc) {
+                    // lane j: queue entry 32 idx + j, its segment in slot j, its sub-step in slot j
+                    const unsigned int qe = idx * 32u + (unsigned int)lane;
+                    bool act = qe < n_q;
+                    uint4 ent = make_uint4(0u, 0u, 0u, 0u);
+                    if (act) ent = __ldcg(reinterpret_cast<const uint4*>(scratch + pp.q_off) + qe);
+                    const long long li = (long long)(((unsigned long long)ent.y << 32) | ent.x);
+                    if (act) {   // a tile the queue overflowed on is the group pass's
+                        const unsigned long long g = (unsigned long long)(li / kWTile) / (unsigned long long)pp.tiles_per_bit;
+                        if ((__ldcg(bits + (g >> 5)) >> (g & 31)) & 1u) act = false;
+                    }
+                    const long long base_l = li - lane;   // so that base + slot is the segment's index
+                    if (act) {
+                        import_segment<SPH, FL>(W, lane, pp.segs + li, pp, ap, dp, invalid, dropped, false);
+                        substep<SPH, FL>(W, lane, lane, (int)ent.z, base_l, pp, ap);
+                        bunch<false, SPH, REC, FL, TR, kModeExact>(W, lane, (int)ent.w, true, base_l, pp, ap, dp, op, sv,
+                                                                   tcs, T);
+                    }
+                    __syncwarp();
+                    continue;
+                }
+                idx -= n_qc;
                 if (idx >= n_listed) break;
                 const long long g = (long long)__ldcg(list + idx);
                 const long long t_end = std::min<long long>((g + 1) * pp.tiles_per_bit, n_wtiles);
@@ -1893,7 +1949,10 @@ cs_status launch(const cs_segment* d_segs, size_t n, const cs_atmosphere* atm, c
     const long long tiles = ((long long)n + kTile - 1) / kTile;
     const long long grid = std::min<long long>(tiles, (long long)device_sm_count() * per_sm);
     pp.tiles_per_bit = 1;
-    const size_t bytes = scratch_words((pp.n + kWTile - 1) / kWTile, 1) * sizeof(unsigned int);
+    const long long n_wtiles = (pp.n + kWTile - 1) / kWTile;
+    pp.q_cap = queue_cap(n_wtiles);
+    pp.q_off = (unsigned int)scratch_queue_off(n_wtiles, 1);
+    const size_t bytes = scratch_words(n_wtiles, 1, pp.q_cap) * sizeof(unsigned int);
     unsigned int* scratch = nullptr;
     if ((st = scratch_alloc(bytes, stream, &scratch)) != CS_OK) return st;
     CS_CUDA_TRY(cudaMemsetAsync(scratch, 0, scratch_zero_words((pp.n + kWTile - 1) / kWTile, 1) * sizeof(unsigned int), stream));
@@ -2112,6 +2171,8 @@ extern "C" cs_status cs_propagate_noalloc(const cs_segment* segs, size_t n, cons
     const long long grid = std::min<long long>(tiles, (long long)device_sm_count() * per_sm);
     const long long n_wtiles = ((long long)n + kWTile - 1) / kWTile;
     pp.tiles_per_bit = (int)std::max<long long>(1, (n_wtiles + kNoAllocBits - 1) / kNoAllocBits);
+    pp.q_cap = 0;   // no queue in the fixed array: every bunch beyond the tables marks its group
+    pp.q_off = 0;
     // the array keeps the previous call's counters and map: start this call's at zero
     CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, scratch_zero_words(n_wtiles, pp.tiles_per_bit) * sizeof(unsigned int), stream));
     return launch_kernel((unsigned)grid, stream, pp, atm->p, dp, op, ctr, o.surrogate, o.tc_poll_limit);
@@ -2146,7 +2207,10 @@ cs_status check_device_call(const cs_segment* segs, size_t n, const cs_atmospher
 }
 
 // Bytes of the per-launch scratch for n segments (one map bit per warp tile).
-size_t scratch_bytes(size_t n) { return scratch_words(((long long)n + kWTile - 1) / kWTile, 1) * sizeof(unsigned int); }
+size_t scratch_bytes(size_t n) {
+    const long long n_wtiles = ((long long)n + kWTile - 1) / kWTile;
+    return scratch_words(n_wtiles, 1, queue_cap(n_wtiles)) * sizeof(unsigned int);
+}
 
 // Grid of the persistent launch; also sets the kernel's shared-memory limit
 // (host-side calls kept out of stream capture).
@@ -2182,6 +2246,8 @@ cs_status enqueue(const cs_segment* segs, size_t n, const cs_atmosphere* atm, co
     pp.s_max = (float)o.s_max;
     set_filters(pp, o, det->p, atm->p);
     pp.tiles_per_bit = 1;
+    pp.q_cap = queue_cap(((long long)n + kWTile - 1) / kWTile);
+    pp.q_off = (unsigned int)scratch_queue_off(((long long)n + kWTile - 1) / kWTile, 1);
     CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, scratch_zero_words(((long long)n + kWTile - 1) / kWTile, 1) * sizeof(unsigned int),
                                 stream));
     return launch_kernel(grid, stream, pp, atm->p, dp, op, ctr, o.surrogate, o.tc_poll_limit);
