@@ -13,6 +13,7 @@ constexpr double kAlpha = 7.2973525693e-3;  // fine-structure constant
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kLog2e = 1.4426950408889634;
 constexpr int kMaxLayers = 8;
+constexpr int kHashLevels = 3;   // telescope hash levels (zenith reach 45, 75, 82 deg)
 constexpr int kMaxNodes = 128;     // tabulated atmosphere
 constexpr double kTableRhoRef = 1.225e-3;   // [g/cm^3]: density = kTableRhoRef (n - 1) / kappa
 
@@ -100,9 +101,10 @@ struct DetParams {
     const float4* tel;    // {x_hi, y_hi, z - h_obs, radius}
     const float2* tel_lo; // {x_lo, y_lo}
     const float4* tel3;   // spherical: centre in frame coordinates and radius
-    // two hashes: hash[0] for arrivals up to 45 deg (small cells, mostly empty),
-    // hash[1] up to 75 deg; steeper arrivals test every sphere
-    TelHash hash[2];
+    // three hashes: hash[0] for arrivals up to 45 deg (small cells, mostly empty),
+    // hash[1] up to 75 deg (the tables' domain), hash[2] up to 82 deg (the photons
+    // beyond the tables, in the exact pass); steeper arrivals test every sphere
+    TelHash hash[kHashLevels];
     // last-mile optics: mirror focal length, (aperture radius)^2, camera radius,
     // pixels per metre on the camera, and the telescope frame (axis a, e1 = a x z-hat, e2 = a x e1)
     int cam_n;

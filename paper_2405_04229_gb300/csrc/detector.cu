@@ -13,7 +13,8 @@
 namespace {
 
 // the two hash levels serve arrivals up to 45 and 75 degrees zenith
-constexpr double kHashTheta[2] = {45.0 * 3.14159265358979323846 / 180.0, 75.0 * 3.14159265358979323846 / 180.0};
+constexpr double kHashTheta[cs::kHashLevels] = {45.0 * 3.14159265358979323846 / 180.0, 75.0 * 3.14159265358979323846 / 180.0,
+                                                  82.0 * 3.14159265358979323846 / 180.0};
 
 void split(double v, float* hi, float* lo) {
     *hi = (float)v;
@@ -123,10 +124,10 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
                                   (float)t[3]);
         }
     }
-    std::vector<int2> range[2];
-    std::vector<int> cell_tel[2];
-    std::vector<float4> cell_data[2];
-    for (int level = 0; level < 2 && d->n_tel > 0; ++level) {
+    std::vector<int2> range[cs::kHashLevels];
+    std::vector<int> cell_tel[cs::kHashLevels];
+    std::vector<float4> cell_data[cs::kHashLevels];
+    for (int level = 0; level < cs::kHashLevels && d->n_tel > 0; ++level) {
         cs::TelHash& H = p.hash[level];
         const double theta_h = kHashTheta[level];
         double reach_max = 0.0, x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
@@ -195,8 +196,8 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
     const size_t o_tel = 0;
     const size_t o_lo = align_up(o_tel + tel.size() * sizeof(float4));
     const size_t o_t3 = align_up(o_lo + tel_lo.size() * sizeof(float2));
-    size_t o_rg[2], o_ct[2], o_cd[2], end = align_up(o_t3 + tel3.size() * sizeof(float4));
-    for (int level = 0; level < 2; ++level) {
+    size_t o_rg[cs::kHashLevels], o_ct[cs::kHashLevels], o_cd[cs::kHashLevels], end = align_up(o_t3 + tel3.size() * sizeof(float4));
+    for (int level = 0; level < cs::kHashLevels; ++level) {
         o_rg[level] = end;
         o_ct[level] = align_up(o_rg[level] + (range[level].size() + 1) * sizeof(int2));
         o_cd[level] = align_up(o_ct[level] + (cell_tel[level].size() + 1) * sizeof(int));
@@ -210,7 +211,7 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
     if (!tel.empty()) memcpy(host.data() + o_tel, tel.data(), tel.size() * sizeof(float4));
     if (!tel_lo.empty()) memcpy(host.data() + o_lo, tel_lo.data(), tel_lo.size() * sizeof(float2));
     if (!tel3.empty()) memcpy(host.data() + o_t3, tel3.data(), tel3.size() * sizeof(float4));
-    for (int level = 0; level < 2; ++level) {
+    for (int level = 0; level < cs::kHashLevels; ++level) {
         if (!range[level].empty()) memcpy(host.data() + o_rg[level], range[level].data(), range[level].size() * sizeof(int2));
         if (!cell_tel[level].empty())
             memcpy(host.data() + o_ct[level], cell_tel[level].data(), cell_tel[level].size() * sizeof(int));
@@ -222,7 +223,7 @@ extern "C" cs_status cs_detector_create(const cs_detector_desc* d, cs_detector**
     p.tel = (const float4*)(base + o_tel);
     p.tel_lo = (const float2*)(base + o_lo);
     p.tel3 = p.spherical ? (const float4*)(base + o_t3) : nullptr;
-    for (int level = 0; level < 2; ++level) {
+    for (int level = 0; level < cs::kHashLevels; ++level) {
         p.hash[level].cell_range = (const int2*)(base + o_rg[level]);
         p.hash[level].cell_tel = (const int*)(base + o_ct[level]);
         p.hash[level].cell_data = (const float4*)(base + o_cd[level]);

@@ -920,7 +920,7 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                 }
                 };
                 if (__all_sync(__activemask(), lvl0)) detect(dp.hash[0], true);
-                else detect(dp.hash[lvl0 ? 0 : 1], s2 <= dp.hash[1].sin2_max);
+                else detect(dp.hash[lvl0 ? 0 : (s2 <= dp.hash[1].sin2_max ? 1 : 2)], s2 <= dp.hash[2].sin2_max);
                 if (tel >= 0) {
                     const size_t slot = (size_t)sh * dp.n_tel + tel;
                     atomicAdd(op.tel_counts + slot, (unsigned long long)b);
@@ -1020,7 +1020,7 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                 }
                 };
                 if (__all_sync(__activemask(), lvl0)) detect(dp.hash[0], true);
-                else detect(dp.hash[lvl0 ? 0 : 1], sg2 <= dp.hash[1].sin2_max);
+                else detect(dp.hash[lvl0 ? 0 : (sg2 <= dp.hash[1].sin2_max ? 1 : 2)], sg2 <= dp.hash[2].sin2_max);
                 if (tel >= 0) {
                     const size_t slot = (size_t)sh * dp.n_tel + tel;
                     atomicAdd(op.tel_counts + slot, (unsigned long long)b);
@@ -1185,7 +1185,7 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                     }
                     };
                     if (__all_sync(__activemask(), lvl0)) detect(dp.hash[0], true);
-                    else detect(dp.hash[lvl0 ? 0 : 1], sg2 <= dp.hash[1].sin2_max);
+                    else detect(dp.hash[lvl0 ? 0 : (sg2 <= dp.hash[1].sin2_max ? 1 : 2)], sg2 <= dp.hash[2].sin2_max);
                     if (tel >= 0) {
                         const size_t slot = (size_t)sh * dp.n_tel + tel;
                         atomicAdd(op.tel_counts + slot, (unsigned long long)b);
