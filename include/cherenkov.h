@@ -531,7 +531,8 @@ cs_status cs_mlp_loss_grad(const float* params, const float* x, const float* t, 
  * what cs_propagate_ex does with opts->device_ptrs = 1 (opts must say so;
  * host pointers are rejected with CS_ERR_INVALID_ARG), but its only scratch,
  * the dynamic scheduler's work counters and the exact pass's map and list of
- * warp tiles with bunches beyond the correction tables, lives in a 67.6 KB array
+ * warp tiles with bunches beyond the correction tables (no bunch queue: the
+ * exact pass regenerates the marked tiles), lives in a 67.6 KB array
  * that the library declares statically on every device that loads it (held
  * until the process exits) instead of in memory the library allocates.  It
  * calls no cudaMalloc, cudaFree or pool allocation.
