@@ -1390,24 +1390,22 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                             const bool bey = bunch<false, SPH, REC, FL, TR, kModeMain, FIX>(W, qs, ib, true, base, pp, ap,
                                                                                            dp, op, sv, tcs, T);
                             // a bunch beyond the tables goes to the exact pass's queue (one
-                            // reservation per warp round); when the queue is full its tile is
-                            // marked, and the exact pass then skips the tile's queued entries
-                            const unsigned int am = __activemask(), m = __ballot_sync(am, bey);
-                            if (m) {
-                                const int leader = __ffs(am) - 1;
+                            // reservation per group of converged lanes); when the queue is full its
+                            // tile is marked, and the exact pass then skips the tile's queued entries
+                            if (bey) {   // the lanes here are exactly those with a bunch to queue
+                                const unsigned int m = __activemask();
+                                const int leader = __ffs(m) - 1;
                                 unsigned int slot0 = 0;
                                 if (lane == leader) slot0 = pp.q_cap ? atomicAdd(scratch + 3, (unsigned int)__popc(m)) : 0xFFFFFFFFu;
-                                slot0 = __shfl_sync(am, slot0, leader);
-                                if (bey) {
-                                    const unsigned int slot = slot0 + (unsigned int)__popc(m & ((1u << lane) - 1u));
-                                    if (slot0 != 0xFFFFFFFFu && slot >= slot0 && slot < pp.q_cap) {
-                                        const int segk = __float_as_int(W.sub[qs].w);
-                                        const unsigned long long li = (unsigned long long)(base + (segk & ((1 << kKShift) - 1)));
-                                        reinterpret_cast<uint4*>(scratch + pp.q_off)[slot] =
-                                            make_uint4((uint32_t)li, (uint32_t)(li >> 32), (uint32_t)(segk >> kKShift), (uint32_t)ib);
-                                    } else {
-                                        any_beyond = true;
-                                    }
+                                slot0 = __shfl_sync(m, slot0, leader);
+                                const unsigned int slot = slot0 + (unsigned int)__popc(m & ((1u << lane) - 1u));
+                                if (slot0 != 0xFFFFFFFFu && slot >= slot0 && slot < pp.q_cap) {
+                                    const int segk = __float_as_int(W.sub[qs].w);
+                                    const unsigned long long li = (unsigned long long)(base + (segk & ((1 << kKShift) - 1)));
+                                    reinterpret_cast<uint4*>(scratch + pp.q_off)[slot] =
+                                        make_uint4((uint32_t)li, (uint32_t)(li >> 32), (uint32_t)(segk >> kKShift), (uint32_t)ib);
+                                } else {
+                                    any_beyond = true;
                                 }
                             }
                         }
