@@ -698,11 +698,11 @@ __device__ __forceinline__ bool bunch(const SM& S, int q, int i, bool active, lo
                                       const OutParams& op, const SurrogateView& sv, TcSmem<kThreadsSur / 128>* tcs,
                                       Tally& T) {
     // The launch configuration; FIX instances are launched only for the standard one (refraction,
-    // transmission and tables on; histogram, telescopes and time sums on; no LV3 filter and no
-    // camera optics), where these are compile-time constants instead of parameter tests.
+    // transmission and tables on; histogram, telescopes and time sums on; no camera optics), where
+    // these are compile-time constants instead of parameter tests (the LV3 switch stays a test).
     static_assert(!(FIX && (SURR || FL || TR || MODE != kModeMain)), "the fixed configuration is the exact tracer's");
     const bool c_refr = FIX || ap.refraction, c_trans = FIX || ap.transmission, c_tables = FIX || ap.use_tables;
-    const bool c_lv3 = !FIX && pp.lv3, c_cam = !FIX && dp.cam_n > 0, c_hist = FIX || dp.nx > 0;
+    const bool c_lv3 = pp.lv3 != 0, c_cam = !FIX && dp.cam_n > 0, c_hist = FIX || dp.nx > 0;
     const bool c_tel = FIX || dp.n_tel > 0, c_time = FIX || op.tel_time != nullptr;
     // ---- generation ------------------------------------------------------------
     const float4 Q = S.sub[q];
@@ -1637,8 +1637,8 @@ cs_status launch_kernel(unsigned grid, cudaStream_t stream, const PropParams& pp
     const bool rec = op.records != nullptr;
     // the exact tracer's instances: emission (Cherenkov or fluorescence) x tracer (tables or stepper)
     // the standard configuration (refraction, transmission and tables; histogram, telescopes and
-    // time sums; no LV3 filter, no camera optics) has its own instances, with those tests folded
-    const bool fix = ap.refraction && ap.transmission && ap.use_tables && !pp.lv3 && dp.cam_n == 0 && dp.nx > 0 &&
+    // time sums; no camera optics) has its own instances, with those tests folded
+    const bool fix = ap.refraction && ap.transmission && ap.use_tables && dp.cam_n == 0 && dp.nx > 0 &&
                      dp.n_tel > 0 && op.tel_time != nullptr;
     auto exact = [&](auto sph, auto fl, auto tr) {
         constexpr bool S = decltype(sph)::value, F = decltype(fl)::value, T = decltype(tr)::value;
