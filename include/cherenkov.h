@@ -331,6 +331,12 @@ typedef struct cs_opts {
      * the call reports CS_ERR_TIMEOUT (host-pointer calls directly, device-pointer and
      * streamed calls through cs_check_timeout). */
     int tc_poll_limit;
+    /* Bunches beyond the correction tables are queued by the photon kernel for the exact pass:
+     * entries per warp tile of 32 segments (0 = default 8; at least 4096 and at most 2^22
+     * entries in all, and at most the default in the batched and streamed calls; < 0 = no
+     * queue).  When the queue is full the remaining such bunches mark their warp tile, which
+     * the exact pass then regenerates whole; the results are the same either way. */
+    int exact_queue;
 } cs_opts;
 
 enum { CS_EMIT_CHERENKOV = 0, CS_EMIT_FLUORESCENCE = 1, CS_EMIT_FLUORESCENCE_HALF = 2 };

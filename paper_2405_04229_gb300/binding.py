@@ -130,7 +130,8 @@ class cs_opts(C.Structure):
                 ("lv3", C.c_int), ("lv3_centre", C.c_double * 3), ("lv3_radius", C.c_double),
                 ("lv3_margin", C.c_double), ("tracer", C.c_int), ("tracer_dh", C.c_double),
                 ("emission", C.c_int), ("fl_n_lines", C.c_int), ("fl_lines_nm", C.c_void_p),
-                ("fl_yield_per_mev", C.c_void_p), ("fl_dedx", C.c_double), ("tc_poll_limit", C.c_int)]
+                ("fl_yield_per_mev", C.c_void_p), ("fl_dedx", C.c_double), ("tc_poll_limit", C.c_int),
+                ("exact_queue", C.c_int)]
 
 
 CS_TRACER_TABLES, CS_TRACER_SNELL = 0, 1
@@ -467,7 +468,7 @@ class Detector:
 
 def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=1.0, seg_base=0,
                    records=False, record_capacity=None, blocks_per_sm=0, surrogate=None, lv1=None, lv3=None,
-                   snell_dh=None, fluorescence=None, tc_poll_limit=0, allow_timeout=False):
+                   snell_dh=None, fluorescence=None, tc_poll_limit=0, allow_timeout=False, exact_queue=0):
     """cs_propagate_ex with host numpy buffers; returns a dict of outputs (with the
     call's status, CS_ERR_TIMEOUT accepted when allow_timeout)."""
     arr = segs if isinstance(segs, np.ndarray) else pack_segments(segs)
@@ -502,6 +503,7 @@ def propagate_host(segs, atm: Atmosphere, det: Detector, seed=0, bunch=1, s_max=
         o.tracer, o.tracer_dh = CS_TRACER_SNELL, snell_dh
     keep = set_fluorescence(o, fluorescence)   # noqa: F841 (the arrays must outlive the call)
     o.tc_poll_limit = tc_poll_limit
+    o.exact_queue = exact_queue
     st = cs_propagate_ex(_dptr(arr) if len(arr) else None, len(arr), atm.handle, det.handle, seed, o, out)
     if not (allow_timeout and st == CS_ERR_TIMEOUT):
         _check(st, "cs_propagate_ex")

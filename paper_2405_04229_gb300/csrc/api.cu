@@ -91,4 +91,5 @@ extern "C" void cs_opts_default(cs_opts* o) {
     o->fl_yield_per_mev = nullptr;
     o->fl_dedx = 2.2;
     o->tc_poll_limit = 0;
+    o->exact_queue = 0;
 }

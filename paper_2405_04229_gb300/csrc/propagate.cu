@@ -1222,9 +1222,13 @@ __host__ __device__ constexpr size_t scratch_queue_off(long long n_wtiles, int t
 __host__ __device__ constexpr size_t scratch_words(long long n_wtiles, int tiles_per_bit, unsigned int q_cap = 0) {
     return scratch_queue_off(n_wtiles, tiles_per_bit) + 4 * (size_t)q_cap;
 }
-// Queue entries for n_wtiles warp tiles: eight per tile, at most 2^22 (64 MB).
-__host__ __device__ constexpr unsigned int queue_cap(long long n_wtiles) {
-    return (unsigned int)(n_wtiles * 8 < (1ll << 22) ? (n_wtiles * 8 > 4096 ? n_wtiles * 8 : 4096) : (1ll << 22));
+// Queue entries for n_wtiles warp tiles: per_tile per tile (default eight; below zero, none),
+// at least 4096 and at most 2^22 (64 MB).
+__host__ __device__ constexpr unsigned int queue_cap(long long n_wtiles, int per_tile = 0) {
+    return per_tile < 0 ? 0u
+                        : (unsigned int)(n_wtiles * (per_tile ? per_tile : 8) < (1ll << 22)
+                                             ? (n_wtiles * (per_tile ? per_tile : 8) > 4096 ? n_wtiles * (per_tile ? per_tile : 8) : 4096)
+                                             : (1ll << 22));
 }
 // The part that must start at zero: the counters and the map (the list is written before it is read).
 __host__ __device__ constexpr size_t scratch_zero_words(long long n_wtiles, int tiles_per_bit) {
@@ -1948,7 +1952,7 @@ cs_status launch(const cs_segment* d_segs, size_t n, const cs_atmosphere* atm, c
     const long long grid = std::min<long long>(tiles, (long long)device_sm_count() * per_sm);
     pp.tiles_per_bit = 1;
     const long long n_wtiles = (pp.n + kWTile - 1) / kWTile;
-    pp.q_cap = queue_cap(n_wtiles);
+    pp.q_cap = queue_cap(n_wtiles, o.exact_queue);
     pp.q_off = (unsigned int)scratch_queue_off(n_wtiles, 1);
     const size_t bytes = scratch_words(n_wtiles, 1, pp.q_cap) * sizeof(unsigned int);
     unsigned int* scratch = nullptr;
@@ -2244,7 +2248,8 @@ cs_status enqueue(const cs_segment* segs, size_t n, const cs_atmosphere* atm, co
     pp.s_max = (float)o.s_max;
     set_filters(pp, o, det->p, atm->p);
     pp.tiles_per_bit = 1;
-    pp.q_cap = queue_cap(((long long)n + kWTile - 1) / kWTile);
+    pp.q_cap = std::min(queue_cap(((long long)n + kWTile - 1) / kWTile, o.exact_queue),
+                        queue_cap(((long long)n + kWTile - 1) / kWTile));   // within the scratch's default size
     pp.q_off = (unsigned int)scratch_queue_off(((long long)n + kWTile - 1) / kWTile, 1);
     CS_CUDA_TRY(cudaMemsetAsync(ctr, 0, scratch_zero_words(((long long)n + kWTile - 1) / kWTile, 1) * sizeof(unsigned int),
                                 stream));
