@@ -57,12 +57,12 @@ def kernel_sources_hash():
     return h.hexdigest()[:16]
 
 
-def kernel_profile():
+def kernel_profile(name="propagate_kernel_traffic.txt"):
     """Per-launch DRAM traffic and pipe utilisation of the photon kernel from the
     committed ncu captures, or None when the kernel sources changed since they
     were taken."""
     try:
-        kv = dict(l.strip().split("=", 1) for l in open(os.path.join(ROOT, "profiles", "propagate_kernel_traffic.txt"))
+        kv = dict(l.strip().split("=", 1) for l in open(os.path.join(ROOT, "profiles", name))
                   if "=" in l and not l.startswith("#"))
         if kv.get("kernel_sources_sha256") == kernel_sources_hash():
             pipes = {k[len("pipe_"):]: float(v) for k, v in kv.items() if k.startswith("pipe_")}
@@ -581,7 +581,7 @@ def run_inclined(args):
                        "l2": "inputs (%.1f GB) larger than L2" % (n * seg_bytes / 1e9)},
             "counters": counters,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": kernel_profile("propagate_kernel_spherical_traffic.txt")[0],
                          "note": "per chunk launch; spherical lane-op count per bunch %d" % OPS_PER_BUNCH_SPHERICAL},
             "kernel_ms": k_ms, "cpu_baseline": cpu, "surrogate": surrogate, "e2e": e2e, "lv1_filter": lv1_res, "lv3_filter": lv3_res,
             "gpu_launches": 2 * args.steps * n_chunks, "clocks": clk.summary()}
