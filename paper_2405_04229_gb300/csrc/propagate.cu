@@ -1400,7 +1400,10 @@ propagate_kernel(const PropParams pp, const AtmParams ap, const DetParams dp, co
                                 const unsigned int m = __activemask();
                                 const int leader = __ffs(m) - 1;
                                 unsigned int slot0 = 0;
-                                if (lane == leader) slot0 = pp.q_cap ? atomicAdd(scratch + 3, (unsigned int)__popc(m)) : 0xFFFFFFFFu;
+                                // (a full queue takes no more reservations, so the 32-bit count cannot wrap)
+                                if (lane == leader)
+                                    slot0 = pp.q_cap && __ldcg(scratch + 3) < pp.q_cap ? atomicAdd(scratch + 3, (unsigned int)__popc(m))
+                                                                                       : 0xFFFFFFFFu;
                                 slot0 = __shfl_sync(m, slot0, leader);
                                 const unsigned int slot = slot0 + (unsigned int)__popc(m & ((1u << lane) - 1u));
                                 if (slot0 != 0xFFFFFFFFu && slot >= slot0 && slot < pp.q_cap) {
