@@ -26,6 +26,7 @@ def test_defaults(B):
     assert o.lv1_metric == B.CS_LV1_OFF and o.lv3 == 0
     assert o.tracer == B.CS_TRACER_TABLES and o.tracer_dh == 10.0
     assert o.emission == B.CS_EMIT_CHERENKOV and o.fl_n_lines == 0 and o.fl_dedx == 2.2
+    assert o.exact_queue == 0 and o.tc_poll_limit == 0   # default queue (8 entries per warp tile); default polls
 
 
 def test_filter_and_emission_helpers_fill_the_struct(B):
@@ -65,3 +66,13 @@ def test_bench_uses_the_capture_only_for_the_captured_sources(monkeypatch):
     assert set(pipes) >= {"issue_active", "alu", "fma"}
     monkeypatch.setattr(bench, "kernel_sources_hash", lambda: "0" * 16)
     assert bench.kernel_profile() == (None, None)   # a changed kernel reports no stale counters
+
+
+def test_bench_reads_the_inclined_chunk_traffic_scaled_from_its_capture(monkeypatch):
+    import bench
+    name = "propagate_kernel_spherical_traffic.txt"
+    kv = dict(l.strip().split("=", 1) for l in open(os.path.join(ROOT, "profiles", name)) if "=" in l and not l.startswith("#"))
+    monkeypatch.setattr(bench, "kernel_sources_hash", lambda: kv["kernel_sources_sha256"])
+    traffic, _ = bench.kernel_profile(name)
+    assert traffic == float(kv["bytes_per_launch"])
+    assert 640e6 <= traffic <= 1.2 * 640e6   # a 1e7-segment chunk reads its 640 MB of segments, little more
